@@ -1,0 +1,164 @@
+/*
+ * lcg.h — C ABI of the GB300 library for stable locally consistent grammars.
+ *
+ * The library builds, merges and expands grammars of string collections with
+ * the method of Diaz-Dominguez, "Efficient terabyte-scale text compression via
+ * stable local consistency and parallel grammar processing" (arXiv 2411.12439):
+ *
+ *   BuildGram(T, H) = G      (Sec. 3.3; the operation is stated in Sec. 1)
+ *   MergeGrams(G_a, G_b)     (Sec. 3.5-3.6)
+ *   exp(C[j]) = T_j          (Sec. 2.2)
+ *
+ * Every step runs in hand-written CUDA kernels on one GPU (sm_103a).  There is
+ * no CPU fallback: without a usable device every call returns LCG_EDEVICE.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ * - Return value: LCG_OK (0) or a negative LCG_E* code.  The message of the
+ *   last failure of a context is available from lcg_last_error().
+ * - No C++ exception crosses this boundary.
+ * - One context per host thread.  A context owns a CUDA stream on one device
+ *   (the caller's stream when one is given).  All calls are blocking: when a
+ *   call returns, its device work is complete.
+ * - Grammars are owned by the library and live in the context's device
+ *   memory until lcg_grammar_free().  Input and output buffers belong to the
+ *   caller; the library never keeps a pointer to them after a call returns.
+ * - Host pointers must be ordinary (pageable or pinned) host memory; device
+ *   pointers must be device memory of the context's device.
+ *
+ * Grammar layout (Appendix A.1, with per-level ranks)
+ * ----------------------------------------------------
+ * Level 0 is the byte alphabet, with fingerprints F^0[s] = h^0(s), s = 0..255.
+ * A level i >= 1 holds g^i rules.  Rule r (a 0-based rank in first-occurrence
+ * order, see lcg_build) has right-hand side rhs[rhs_off[r] .. rhs_off[r+1]),
+ * a sequence of level-(i-1) ranks (bytes at level 1), and fingerprint
+ * F^i[r] = h^i(rhs) of Eq. fast_hash.  rhs_off has g^i+1 uint64 entries with
+ * rhs_off[0] = 0, rhs is uint32 of length G^i = rhs_off[g^i], F^i is uint32.
+ * The start rule S -> C[1..k] is stored as the pair (c_level[j], c_rank[j]):
+ * the level and rank of the symbol that expands to string j.
+ */
+#ifndef LCG_H
+#define LCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LCG_OK         0
+#define LCG_EINVAL    -1  /* bad argument: k = 0, an empty string, bad level, ... */
+#define LCG_ENOMEM    -2  /* device or host allocation failed */
+#define LCG_ELEVELS   -3  /* the hash family has fewer functions than rounds needed */
+#define LCG_EMISMATCH -4  /* grammars built with different hash families */
+#define LCG_EOVERFLOW -5  /* a level would hold >= 2^32 rules, or a phrase >= 2^32 symbols */
+#define LCG_ETIMEOUT  -6  /* a bounded device-side wait gave up */
+#define LCG_EDEVICE   -7  /* CUDA error, or no usable device */
+#define LCG_ETABLE    -8  /* phrase table could not be sized (after internal retries) */
+
+typedef struct lcg_ctx lcg_ctx;
+typedef struct lcg_grammar lcg_grammar;
+
+/* The hash family H = {h^0, ..., h^{levels-1}} of Sec. 3.2.
+ *
+ * The paper draws, per level, a random prime p_i and a_i, b_i, c_i in [p_i]_+.
+ * This library fixes p = 2^61 - 1 for every level and takes the random draws
+ * as input: a[i], b[i], c[i] must lie in [1, 2^61 - 2].  m = 2^m_bits with
+ * 1 <= m_bits <= 32 is the fingerprint range of every level.
+ *   h^0(s)   = ((a_0 s + b_0) mod p) mod m                         (Sec. 2.4)
+ *   h^i(Q)   = ((a_i (sum_{j=1..q} F^{i-1}[Q_j] c_i^{j-1}) + b_i) mod p) mod m
+ *                                                      (Eq. lvl_hash / fast_hash)
+ * The arrays are host memory and are copied by lcg_ctx_create.  A build needs
+ * at least ceil(log2 n_max) + 1 functions (Sec. 3.2). */
+typedef struct lcg_hash_family {
+    uint32_t levels;
+    uint32_t m_bits;
+    const uint64_t* a;
+    const uint64_t* b;
+    const uint64_t* c;
+} lcg_hash_family;
+
+/* Per-round statistics of the last lcg_build / lcg_build_into of a context. */
+typedef struct lcg_round_stats {
+    uint64_t n;          /* |T^i|: symbols parsed in round i */
+    uint64_t phrases;    /* phrases found in round i (= |T^{i+1}| before retiring) */
+    uint64_t g;          /* new rules of level i */
+    uint64_t G;          /* total length of their right-hand sides */
+    uint64_t strings;    /* active strings entering round i */
+    uint64_t table_cap;  /* phrase-table slots used for round i */
+    uint32_t retries;    /* table regrowths in round i */
+    uint32_t pad;
+} lcg_round_stats;
+
+typedef struct lcg_build_stats {
+    uint32_t rounds;
+    uint32_t pad;
+    uint64_t kernel_launches;   /* kernels this library launched in the call */
+    uint64_t input_bytes;
+    lcg_round_stats round[64];
+} lcg_build_stats;
+
+/* Create a context on CUDA device `device` with hash family H.  `stream` is a
+ * cudaStream_t to run on (NULL: the context creates its own).  Returns
+ * LCG_EINVAL for a malformed family, LCG_EDEVICE when the device is not
+ * usable. */
+int lcg_ctx_create(int device, const lcg_hash_family* H, void* stream, lcg_ctx** out);
+void lcg_ctx_destroy(lcg_ctx* ctx);
+const char* lcg_last_error(const lcg_ctx* ctx);
+/* Statistics of the last build call of this context (host struct filled). */
+int lcg_last_build_stats(const lcg_ctx* ctx, lcg_build_stats* out);
+
+/* BuildGram(T, H) (Sec. 3.3).
+ * data: the k strings concatenated (uint8), `data_on_device` = 1 when it is a
+ *       device pointer, 0 when it is host memory (copied in by the call).
+ * offsets: HOST array of k+1 uint64; string j is data[offsets[j] .. offsets[j+1]).
+ * Every string must be non-empty (LCG_EINVAL otherwise).
+ * Rounds i = 1, 2, ... break every active string at the LMS positions of
+ * RandLMSPar (Eq. rand_types), give each distinct phrase of the round a rank
+ * of level i in order of first occurrence over the concatenated active strings
+ * (string index, then position), and replace the phrases by their ranks.  A
+ * string whose sequence has length one after round i is done: C[j] = (i, rank).
+ * A string of length one on input has C[j] = (0, byte).
+ * On success *out is a new device-resident grammar. */
+int lcg_build(lcg_ctx* ctx, const uint8_t* data, const uint64_t* offsets, uint32_t k,
+              int data_on_device, lcg_grammar** out);
+
+/* The parse of Appendix A.2 against a resident grammar: strings T are parsed
+ * with the same rounds as lcg_build, a phrase that is already a rule of the
+ * resident grammar keeps its rank, and new phrases are appended after the
+ * resident rules of their level in first-occurrence order.  The result is
+ * identical to lcg_merge(resident, lcg_build(T)).  `resident` is modified in
+ * place; its C grows by k entries. */
+int lcg_build_into(lcg_ctx* ctx, lcg_grammar* resident, const uint8_t* data, const uint64_t* offsets,
+                   uint32_t k, int data_on_device);
+
+/* MergeGrams(G_a, G_b) (Sec. 3.6): `a` absorbs `b` (b is left unchanged).
+ * Level by level, every rule of b whose right-hand side (rewritten into a's
+ * ranks of the level below) is a rule of a maps to that rule; the others are
+ * appended to a in b's rank order.  C_a becomes C_a . C_b.  Grammars built
+ * with different hash families give LCG_EMISMATCH. */
+int lcg_merge(lcg_ctx* ctx, lcg_grammar* a, const lcg_grammar* b);
+
+/* exp(C[j]) (Sec. 2.2).  Writes min(cap, |T_j|) bytes to `out` (device memory
+ * when out_on_device = 1, else host) and the full length to *out_len; returns
+ * LCG_EINVAL when cap < |T_j| (nothing is written then) or j >= k. */
+int lcg_decompress(lcg_ctx* ctx, const lcg_grammar* G, uint32_t j, uint8_t* out, uint64_t cap,
+                   uint64_t* out_len, int out_on_device);
+
+/* Shape of a grammar: number of strings k and of levels >= 1. */
+int lcg_grammar_shape(const lcg_grammar* G, uint32_t* k, uint32_t* nlevels);
+/* Sizes of level i >= 1: g^i rules and G^i right-hand-side symbols. */
+int lcg_level_size(const lcg_grammar* G, uint32_t level, uint64_t* g, uint64_t* Gsz);
+/* Copy level i >= 1 to host buffers of g+1, G and g entries (any may be NULL). */
+int lcg_export_level(lcg_ctx* ctx, const lcg_grammar* G, uint32_t level, uint64_t* rhs_off,
+                     uint32_t* rhs, uint32_t* F);
+/* Copy F^0 (256 entries) and C (k entries each) to host buffers. */
+int lcg_export_start(lcg_ctx* ctx, const lcg_grammar* G, uint32_t* F0, uint32_t* c_level, uint32_t* c_rank);
+void lcg_grammar_free(lcg_grammar* G);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LCG_H */

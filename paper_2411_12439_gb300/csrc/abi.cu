@@ -1,0 +1,807 @@
+// C ABI of the library (include/lcg.h): contexts, the BuildGram round driver,
+// MergeGrams, expansion and export.  Host code only orchestrates: every step
+// of the method runs in the kernels of parse.cu and grammar.cu.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lcg.h"
+#include "lcg_internal.h"
+
+using namespace lcg;
+
+// --------------------------------------------------------------------------
+// objects
+// --------------------------------------------------------------------------
+
+namespace {
+
+struct Level {
+    u64 g = 0, G = 0;          // rules and right-hand-side symbols
+    u64 cap_g = 0, cap_G = 0;  // allocated capacity
+    u64* rhs_off = nullptr;    // cap_g + 1 entries
+    u32* rhs = nullptr;
+    u32* F = nullptr;
+    void* rtab = nullptr;      // table over the rules (for parses against this grammar and merges)
+    u64 rcap = 0;
+    bool rvalid = false;
+};
+
+}  // namespace
+
+struct lcg_grammar {
+    int device = 0;
+    u64 tag = 0;
+    u32* F0 = nullptr;  // 256 fingerprints of bytes (device)
+    std::vector<Level> lv;
+    u32 k = 0, cap_k = 0;
+    u32* c_level = nullptr;
+    u32* c_rank = nullptr;
+};
+
+struct lcg_ctx {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::vector<u64> a, b, c;
+    u32 levels = 0, m_bits = 32;
+    u64 mmask = 0xffffffffull;
+    u64 tag = 0;
+    std::string err;
+    // persistent device scratch
+    DevStatus* ds = nullptr;
+    RoundCounts* rc = nullptr;
+    u64* ctr = nullptr;     // tile counter of single-pass kernels (never reset)
+    u64 ctr_val = 0;        // its value after all launched tiles ran
+    u64 epoch = 0;          // look-back epoch, one per launch
+    u64* scratch = nullptr; // small device scalars: [0] phrases, [1..2] totals
+    void* lb1 = nullptr;
+    u64 lb1_tiles = 0;
+    void* lb2 = nullptr;
+    u64 lb2_tiles = 0;
+    double ratio_hint[64] = {0};  // distinct/phrases of the last build, per level
+    lcg_build_stats stats{};
+    u64 launches = 0;
+};
+
+namespace {
+
+constexpr u64 kMaxRank = 0x7fffffffull;  // ranks are tagged with one bit in the phrase slots
+
+struct Fail {
+    int code;
+};
+
+void fail_if(lcg_ctx* ctx, bool cond, int code, const std::string& msg) {
+    if (cond) {
+        ctx->err = msg;
+        throw Fail{code};
+    }
+}
+
+void ck(lcg_ctx* ctx, cudaError_t e, const char* what) {
+    if (e != cudaSuccess) {
+        ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
+        throw Fail{e == cudaErrorMemoryAllocation ? LCG_ENOMEM : LCG_EDEVICE};
+    }
+}
+
+template <typename T>
+T* dalloc(lcg_ctx* ctx, u64 count) {
+    void* p = nullptr;
+    if (count == 0) count = 1;
+    ck(ctx, cudaMallocAsync(&p, count * sizeof(T), ctx->st), "cudaMallocAsync");
+    return (T*)p;
+}
+
+void dfree(lcg_ctx* ctx, void* p) {
+    if (p) cudaFreeAsync(p, ctx->st);
+}
+
+void sync(lcg_ctx* ctx) { ck(ctx, cudaStreamSynchronize(ctx->st), "stream synchronize"); }
+
+void check_device_status(lcg_ctx* ctx, const DevStatus& h) {
+    switch (h.error) {
+        case kErrNone: return;
+        case kErrTimeout: fail_if(ctx, true, LCG_ETIMEOUT, "a bounded device wait gave up"); break;
+        case kErrTableFull: fail_if(ctx, true, LCG_ETABLE, "phrase table full"); break;
+        case kErrPhraseLong: fail_if(ctx, true, LCG_EOVERFLOW, "phrase of 2^32 symbols or more"); break;
+        case kErrMismatch: fail_if(ctx, true, LCG_EMISMATCH, "equal rules with different fingerprints"); break;
+        default: fail_if(ctx, true, LCG_EDEVICE, "device error " + std::to_string(h.error));
+    }
+}
+
+DevStatus read_status(lcg_ctx* ctx) {
+    DevStatus h;
+    ck(ctx, cudaMemcpyAsync(&h, ctx->ds, sizeof(h), cudaMemcpyDeviceToHost, ctx->st), "read status");
+    sync(ctx);
+    return h;
+}
+
+LevelHash level_hash(const lcg_ctx* ctx, u32 i) {
+    LevelHash h;
+    h.a = ctx->a[i];
+    h.b = ctx->b[i];
+    h.c = ctx->c[i];
+    h.mmask = ctx->mmask;
+    return h;
+}
+
+u64 pow2_at_least(u64 x) {
+    u64 p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+void ensure_lb(lcg_ctx* ctx, void** lb, u64* have, u64 tiles, size_t bytes) {
+    if (tiles <= *have) return;
+    u64 want = std::max<u64>(tiles, *have * 2);
+    size_t nb = bytes / (tiles ? tiles : 1) * want;
+    if (*lb) dfree(ctx, *lb);
+    void* p = nullptr;
+    ck(ctx, cudaMallocAsync(&p, nb, ctx->st), "cudaMallocAsync lb");
+    ck(ctx, cudaMemsetAsync(p, 0, nb, ctx->st), "memset lb");
+    *lb = p;
+    *have = want;
+}
+
+// grow a level's arrays to hold `need_g` rules and `need_G` symbols
+void grow_level(lcg_ctx* ctx, Level& L, u64 need_g, u64 need_G) {
+    if (need_g > L.cap_g || L.rhs_off == nullptr) {
+        u64 cap = std::max<u64>(need_g, std::max<u64>(L.cap_g * 2, 256));
+        u64* ro = dalloc<u64>(ctx, cap + 1);
+        u32* F = dalloc<u32>(ctx, cap);
+        if (L.rhs_off) {
+            ck(ctx, cudaMemcpyAsync(ro, L.rhs_off, (L.g + 1) * sizeof(u64), cudaMemcpyDeviceToDevice, ctx->st), "copy");
+            ck(ctx, cudaMemcpyAsync(F, L.F, L.g * sizeof(u32), cudaMemcpyDeviceToDevice, ctx->st), "copy");
+            dfree(ctx, L.rhs_off);
+            dfree(ctx, L.F);
+        } else {
+            ck(ctx, cudaMemsetAsync(ro, 0, sizeof(u64), ctx->st), "memset");
+        }
+        L.rhs_off = ro;
+        L.F = F;
+        L.cap_g = cap;
+    }
+    if (need_G > L.cap_G || L.rhs == nullptr) {
+        u64 cap = std::max<u64>(need_G, std::max<u64>(L.cap_G * 2, 1024));
+        u32* r = dalloc<u32>(ctx, cap);
+        if (L.rhs) {
+            ck(ctx, cudaMemcpyAsync(r, L.rhs, L.G * sizeof(u32), cudaMemcpyDeviceToDevice, ctx->st), "copy");
+            dfree(ctx, L.rhs);
+        }
+        L.rhs = r;
+        L.cap_G = cap;
+    }
+}
+
+const u32* fprev_of(const lcg_grammar* G, u32 i) { return i == 1 ? G->F0 : G->lv[i - 2].F; }
+
+// (Re)build the table over the rules of level i so that it can take
+// `need_g` rules at load <= 1/2.
+void ensure_resident(lcg_ctx* ctx, lcg_grammar* G, u32 i, u64 need_g) {
+    Level& L = G->lv[i - 1];
+    const u64 want = pow2_at_least(std::max<u64>(2 * need_g, 1024));
+    if (L.rvalid && L.rcap >= want) return;
+    if (L.rtab) dfree(ctx, L.rtab);
+    L.rtab = dalloc<unsigned char>(ctx, want * slot_bytes());
+    L.rcap = want;
+    ck(ctx, cudaMemsetAsync(L.rtab, 0xFF, want * slot_bytes(), ctx->st), "memset table");
+    ck(ctx, launch_resident_build(L.rhs, L.rhs_off, 0, L.g, fprev_of(G, i), level_hash(ctx, i), L.rtab, want - 1,
+                                  ctx->ds, ctx->st),
+       "resident build");
+    ctx->launches++;
+    L.rvalid = true;
+}
+
+void grow_c(lcg_ctx* ctx, lcg_grammar* G, u32 need) {
+    if (need <= G->cap_k && G->c_level) return;
+    u32 cap = std::max<u32>(need, std::max<u32>(G->cap_k * 2, 16));
+    u32* cl = dalloc<u32>(ctx, cap);
+    u32* cr = dalloc<u32>(ctx, cap);
+    if (G->c_level) {
+        ck(ctx, cudaMemcpyAsync(cl, G->c_level, G->k * sizeof(u32), cudaMemcpyDeviceToDevice, ctx->st), "copy");
+        ck(ctx, cudaMemcpyAsync(cr, G->c_rank, G->k * sizeof(u32), cudaMemcpyDeviceToDevice, ctx->st), "copy");
+        dfree(ctx, G->c_level);
+        dfree(ctx, G->c_rank);
+    }
+    G->c_level = cl;
+    G->c_rank = cr;
+    G->cap_k = cap;
+}
+
+lcg_grammar* new_grammar(lcg_ctx* ctx) {
+    lcg_grammar* G = new lcg_grammar();
+    G->device = ctx->device;
+    G->tag = ctx->tag;
+    G->F0 = dalloc<u32>(ctx, 256);
+    ck(ctx, launch_h0(level_hash(ctx, 0), G->F0, ctx->st), "h0");
+    ctx->launches++;
+    return G;
+}
+
+void free_grammar_now(lcg_grammar* G) {
+    if (!G) return;
+    cudaSetDevice(G->device);
+    cudaFree(G->F0);
+    for (Level& L : G->lv) {
+        cudaFree(L.rhs_off);
+        cudaFree(L.rhs);
+        cudaFree(L.F);
+        cudaFree(L.rtab);
+    }
+    cudaFree(G->c_level);
+    cudaFree(G->c_rank);
+    delete G;
+}
+
+// --------------------------------------------------------------------------
+// BuildGram round driver
+// --------------------------------------------------------------------------
+
+void build_into(lcg_ctx* ctx, lcg_grammar* R, const uint8_t* data, const uint64_t* off, uint32_t k, int on_dev,
+                bool against_resident) {
+    fail_if(ctx, k == 0 || off == nullptr || data == nullptr, LCG_EINVAL, "empty collection");
+    fail_if(ctx, (u64)R->k + k > 0xffffffffull, LCG_EOVERFLOW, "too many strings");
+    std::vector<u64> act_src, act_len, lvl0_pos;
+    std::vector<u32> act_id, lvl0_id;
+    for (u32 j = 0; j < k; j++) {
+        fail_if(ctx, off[j + 1] <= off[j], LCG_EINVAL, "string " + std::to_string(j) + " is empty");
+        const u64 len = off[j + 1] - off[j];
+        if (len == 1) {
+            lvl0_pos.push_back(off[j] - off[0]);
+            lvl0_id.push_back(R->k + j);
+        } else {
+            act_src.push_back(off[j] - off[0]);
+            act_len.push_back(len);
+            act_id.push_back(R->k + j);
+        }
+    }
+    ctx->stats = lcg_build_stats{};
+    ctx->stats.input_bytes = off[k] - off[0];
+    const u64 launches0 = ctx->launches;
+    std::vector<void*> owned;  // freed at the end
+    auto own = [&](void* p) { owned.push_back(p); return p; };
+
+    const u64 nbytes = off[k] - off[0];
+    const unsigned char* d_in;
+    if (on_dev) {
+        d_in = data + off[0];
+    } else {
+        unsigned char* p = dalloc<unsigned char>(ctx, nbytes);
+        own(p);
+        ck(ctx, cudaMemcpyAsync(p, data + off[0], nbytes, cudaMemcpyHostToDevice, ctx->st), "copy input");
+        d_in = p;
+    }
+    const u32 kbase = R->k;
+    grow_c(ctx, R, R->k + k);
+    R->k += k;
+
+    if (!lvl0_id.empty()) {
+        u64* dpos = (u64*)own(dalloc<u64>(ctx, lvl0_pos.size()));
+        u32* dids = (u32*)own(dalloc<u32>(ctx, lvl0_id.size()));
+        ck(ctx, cudaMemcpyAsync(dpos, lvl0_pos.data(), lvl0_pos.size() * 8, cudaMemcpyHostToDevice, ctx->st), "copy");
+        ck(ctx, cudaMemcpyAsync(dids, lvl0_id.data(), lvl0_id.size() * 4, cudaMemcpyHostToDevice, ctx->st), "copy");
+        ck(ctx, launch_level0(d_in, dpos, dids, (u32)lvl0_id.size(), R->c_level, R->c_rank, ctx->st), "level0");
+        ctx->launches++;
+    }
+    (void)kbase;
+    u32 kk = (u32)act_id.size();
+    if (kk == 0) {
+        sync(ctx);
+        for (void* p : owned) dfree(ctx, p);
+        ctx->stats.kernel_launches = ctx->launches - launches0;
+        return;
+    }
+    // round-1 sequence: the active strings back to back
+    std::vector<u64> soff_h(kk + 1, 0);
+    for (u32 x = 0; x < kk; x++) soff_h[x + 1] = soff_h[x] + act_len[x];
+    const u64 n1 = soff_h[kk];
+    u64* d_soff = dalloc<u64>(ctx, kk + 1);
+    u32* d_sid = dalloc<u32>(ctx, kk);
+    ck(ctx, cudaMemcpyAsync(d_soff, soff_h.data(), (kk + 1) * 8, cudaMemcpyHostToDevice, ctx->st), "copy soff");
+    ck(ctx, cudaMemcpyAsync(d_sid, act_id.data(), kk * 4, cudaMemcpyHostToDevice, ctx->st), "copy sid");
+    const void* S = d_in;
+    void* S_owned = nullptr;
+    if (!lvl0_id.empty()) {
+        unsigned char* g = dalloc<unsigned char>(ctx, n1);
+        u64* dsrc = (u64*)own(dalloc<u64>(ctx, kk));
+        ck(ctx, cudaMemcpyAsync(dsrc, act_src.data(), kk * 8, cudaMemcpyHostToDevice, ctx->st), "copy");
+        ck(ctx, launch_gather_strings(d_in, dsrc, d_soff, kk, g, ctx->st), "gather");
+        ctx->launches++;
+        S = g;
+        S_owned = g;
+    }
+    int symb = 1;
+    u64 n = n1;
+    double prev_ratio = 0.0;
+
+    for (u32 i = 1; kk > 0; i++) {
+        fail_if(ctx, i >= ctx->levels, LCG_ELEVELS, "hash family too short: needs more than " +
+                                                         std::to_string(ctx->levels) + " functions");
+        if (R->lv.size() < i) R->lv.emplace_back();
+        lcg_round_stats& rs = ctx->stats.round[std::min<u32>(i - 1, 63)];
+        rs.n = n;
+        rs.strings = kk;
+        const u64 tiles = tiles_for(n);
+        ensure_lb(ctx, &ctx->lb1, &ctx->lb1_tiles, tiles, lb1_bytes(tiles));
+        u32* bitmap = dalloc<u32>(ctx, tiles * 256);
+        u64* tile_base = dalloc<u64>(ctx, tiles);
+        u64* soff_next = dalloc<u64>(ctx, kk + 1);
+        u32* sid_next = dalloc<u32>(ctx, kk);
+        u64* R_phr = dalloc<u64>(ctx, kk);
+        u32* R_sid = dalloc<u32>(ctx, kk);
+
+        RoundArgs a{};
+        a.sym_bytes = symb;
+        a.S = S;
+        a.n = n;
+        a.soff = d_soff;
+        a.sid = d_sid;
+        a.k = kk;
+        a.Fprev = fprev_of(R, i);
+        a.lh = level_hash(ctx, i);
+        a.level = i;
+        a.bitmap = bitmap;
+        a.tile_base = tile_base;
+        a.lb1 = ctx->lb1;
+        a.ctr = ctx->ctr;
+        a.total = ctx->scratch;
+        a.ds = ctx->ds;
+        a.soff_next = soff_next;
+        a.sid_next = sid_next;
+        a.R_phr = R_phr;
+        a.R_sid = R_sid;
+        a.rc = ctx->rc;
+        a.epoch = ++ctx->epoch;
+        a.ctr_base = ctx->ctr_val;
+        ctx->ctr_val += tiles;
+        ck(ctx, launch_breaks(a, ctx->st), "k_breaks");
+        ck(ctx, launch_strings(a, ctx->st), "k_strings");
+        ctx->launches += 2;
+        RoundCounts rc;
+        ck(ctx, cudaMemcpyAsync(&rc, ctx->rc, sizeof(rc), cudaMemcpyDeviceToHost, ctx->st), "read counts");
+        check_device_status(ctx, read_status(ctx));
+        const u64 P = rc.phrases;
+        rs.phrases = P;
+
+        Level& L = R->lv[i - 1];
+        u32* P_slot = dalloc<u32>(ctx, P);
+        u32* Tnext = dalloc<u32>(ctx, rc.n_next);
+        if (against_resident && L.g > 0) {
+            ensure_resident(ctx, R, i, L.g);
+            a.rtab = L.rtab;
+            a.rmask = L.rcap - 1;
+            a.rrhs = L.rhs;
+            a.rrhs_off = L.rhs_off;
+        }
+        // phrase table sized from the distinct/phrase ratio seen before
+        double ratio = ctx->ratio_hint[std::min<u32>(i, 63)];
+        if (ratio <= 0) ratio = (i == 1) ? 0.02 : std::min(1.0, std::max(prev_ratio * 2.0, 0.05));
+        u64 est = std::max<u64>(4096, std::min<u64>(P, (u64)(ratio * 1.5 * (double)P) + 1));
+        u64 cap = pow2_at_least(2 * est);
+        void* tab = nullptr;
+        u32 retries = 0;
+        DevStatus st;
+        while (true) {
+            fail_if(ctx, cap > (kMaxRank + 1), LCG_ETABLE, "phrase table would exceed 2^31 slots");
+            tab = dalloc<unsigned char>(ctx, cap * slot_bytes());
+            ck(ctx, cudaMemsetAsync(tab, 0xFF, cap * slot_bytes(), ctx->st), "memset table");
+            ck(ctx, cudaMemsetAsync((char*)ctx->ds + 4, 0, 4 + 16, ctx->st), "reset counters");
+            a.tab = tab;
+            a.mask = cap - 1;
+            a.claim_limit = cap / 2;
+            a.P_slot = P_slot;
+            ck(ctx, launch_phrases(a, ctx->st), "k_phrases");
+            ctx->launches++;
+            st = read_status(ctx);
+            check_device_status(ctx, st);
+            if (!st.overflow) break;
+            dfree(ctx, tab);
+            cap *= 4;
+            retries++;
+        }
+        rs.table_cap = cap;
+        rs.retries = retries;
+        const u64 g_new = st.claims, G_new = st.claim_len;
+        fail_if(ctx, L.g + g_new > kMaxRank, LCG_EOVERFLOW, "level with 2^31 rules or more");
+        rs.g = g_new;
+        rs.G = G_new;
+        prev_ratio = P ? (double)g_new / (double)P : 0.0;
+        if (i < 64) ctx->ratio_hint[i] = prev_ratio;
+        grow_level(ctx, L, L.g + g_new, L.G + G_new);
+        if (against_resident) {
+            ensure_resident(ctx, R, i, L.g + g_new);
+            a.rtab_w = L.rtab;
+            a.rmask_w = L.rcap - 1;
+        } else {
+            L.rvalid = false;
+        }
+        const u64 ntiles = name_tiles_for(P);
+        ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, ntiles, lb2_bytes(ntiles));
+        a.lb2 = ctx->lb2;
+        a.P = P;
+        a.g_base = L.g;
+        a.G_base = L.G;
+        a.rhs = L.rhs;
+        a.rhs_off = L.rhs_off;
+        a.F = L.F;
+        a.totals = ctx->scratch + 1;
+        a.epoch = ++ctx->epoch;
+        a.ctr_base = ctx->ctr_val;
+        ctx->ctr_val += ntiles;
+        ck(ctx, launch_name(a, ctx->st), "k_name");
+        a.Tnext = Tnext;
+        a.c_level = R->c_level;
+        a.c_rank = R->c_rank;
+        ck(ctx, launch_rewrite(a, ctx->st), "k_rewrite");
+        ctx->launches += 2;
+        L.g += g_new;
+        L.G += G_new;
+
+        dfree(ctx, bitmap);
+        dfree(ctx, tile_base);
+        dfree(ctx, P_slot);
+        dfree(ctx, tab);
+        dfree(ctx, R_phr);
+        dfree(ctx, R_sid);
+        dfree(ctx, d_soff);
+        dfree(ctx, d_sid);
+        if (S_owned) dfree(ctx, S_owned);
+        S = Tnext;
+        S_owned = Tnext;
+        symb = 4;
+        n = rc.n_next;
+        kk = (u32)rc.k_next;
+        d_soff = soff_next;
+        d_sid = sid_next;
+        ctx->stats.rounds = i;
+    }
+    check_device_status(ctx, read_status(ctx));
+    dfree(ctx, d_soff);
+    dfree(ctx, d_sid);
+    if (S_owned) dfree(ctx, S_owned);
+    for (void* p : owned) dfree(ctx, p);
+    ctx->stats.kernel_launches = ctx->launches - launches0;
+}
+
+// --------------------------------------------------------------------------
+// MergeGrams
+// --------------------------------------------------------------------------
+
+void merge(lcg_ctx* ctx, lcg_grammar* A, const lcg_grammar* B) {
+    fail_if(ctx, A == B, LCG_EINVAL, "cannot merge a grammar into itself");
+    fail_if(ctx, A->tag != B->tag || A->tag != ctx->tag, LCG_EMISMATCH, "grammars of different hash families");
+    fail_if(ctx, (u64)A->k + B->k > 0xffffffffull, LCG_EOVERFLOW, "too many strings");
+    const u32 kb = B->k;
+    u32* cb_rank = dalloc<u32>(ctx, kb);
+    if (kb)
+        ck(ctx, cudaMemcpyAsync(cb_rank, B->c_rank, kb * 4, cudaMemcpyDeviceToDevice, ctx->st), "copy");
+    u32* Mprev = nullptr;
+    for (u32 i = 1; i <= B->lv.size(); i++) {
+        if (A->lv.size() < i) A->lv.emplace_back();
+        Level& LA = A->lv[i - 1];
+        const Level& LB = B->lv[i - 1];
+        const u64 gb = LB.g;
+        const u32* brhs = LB.rhs;
+        u32* brhs_tmp = nullptr;
+        if (i > 1 && LB.G > 0) {
+            brhs_tmp = dalloc<u32>(ctx, LB.G);
+            ck(ctx, launch_remap(LB.rhs, LB.G, Mprev, brhs_tmp, ctx->st), "remap");
+            ctx->launches++;
+            brhs = brhs_tmp;
+        }
+        if (LA.rhs_off == nullptr) grow_level(ctx, LA, 0, 0);
+        ensure_resident(ctx, A, i, LA.g + gb);
+        u32* M = dalloc<u32>(ctx, gb);
+        u32* miss = dalloc<u32>(ctx, gb);
+        u32* mlen = dalloc<u32>(ctx, gb);
+        u64* xrank = dalloc<u64>(ctx, gb);
+        u64* xlen = dalloc<u64>(ctx, gb);
+        ck(ctx, launch_merge_lookup(brhs, LB.rhs_off, LB.F, gb, fprev_of(A, i), level_hash(ctx, i), LA.rtab,
+                                    LA.rcap - 1, LA.rhs, LA.rhs_off, LA.F, M, miss, mlen, ctx->ds, ctx->st),
+           "merge lookup");
+        u64 grid = 0;
+        const u64 stiles = std::max<u64>(1, scan2_tiles_for(gb));
+        ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, stiles, scan2_lb_bytes(stiles));
+        ck(ctx, launch_scan2(miss, mlen, gb, xrank, xlen, ctx->scratch + 1, ctx->lb2, ++ctx->epoch, ctx->ctr,
+                             ctx->ctr_val, ctx->ds, ctx->st, &grid),
+           "scan");
+        ctx->ctr_val += grid;
+        ctx->launches += 2;
+        u64 tot[2] = {0, 0};
+        if (gb) ck(ctx, cudaMemcpyAsync(tot, ctx->scratch + 1, 16, cudaMemcpyDeviceToHost, ctx->st), "read totals");
+        check_device_status(ctx, read_status(ctx));
+        const u64 ga = LA.g, Ga = LA.G;
+        fail_if(ctx, ga + tot[0] > kMaxRank, LCG_EOVERFLOW, "level with 2^31 rules or more");
+        grow_level(ctx, LA, ga + tot[0], Ga + tot[1]);
+        ck(ctx, launch_merge_append(brhs, LB.rhs_off, LB.F, gb, miss, xrank, xlen, ga, Ga, LA.rhs, LA.rhs_off, LA.F,
+                                    M, ga + tot[0], Ga + tot[1], ctx->st),
+           "merge append");
+        ctx->launches += 2;
+        LA.g = ga + tot[0];
+        LA.G = Ga + tot[1];
+        // the appended rules join the table of the level
+        ck(ctx, launch_resident_build(LA.rhs, LA.rhs_off, ga, tot[0], fprev_of(A, i), level_hash(ctx, i), LA.rtab,
+                                      LA.rcap - 1, ctx->ds, ctx->st),
+           "table insert");
+        ck(ctx, launch_remap_c(B->c_level, cb_rank, kb, i, M, ctx->st), "remap C");
+        ctx->launches += 2;
+        dfree(ctx, brhs_tmp);
+        dfree(ctx, miss);
+        dfree(ctx, mlen);
+        dfree(ctx, xrank);
+        dfree(ctx, xlen);
+        dfree(ctx, Mprev);
+        Mprev = M;
+    }
+    dfree(ctx, Mprev);
+    grow_c(ctx, A, A->k + kb);
+    if (kb) {
+        ck(ctx, cudaMemcpyAsync(A->c_level + A->k, B->c_level, kb * 4, cudaMemcpyDeviceToDevice, ctx->st), "copy");
+        ck(ctx, cudaMemcpyAsync(A->c_rank + A->k, cb_rank, kb * 4, cudaMemcpyDeviceToDevice, ctx->st), "copy");
+    }
+    A->k += kb;
+    dfree(ctx, cb_rank);
+    check_device_status(ctx, read_status(ctx));
+}
+
+// --------------------------------------------------------------------------
+// exp(C[j])
+// --------------------------------------------------------------------------
+
+void decompress(lcg_ctx* ctx, const lcg_grammar* G, u32 j, uint8_t* out, u64 cap, uint64_t* out_len, int on_dev) {
+    fail_if(ctx, j >= G->k, LCG_EINVAL, "string index out of range");
+    u32 lev = 0, r = 0;
+    ck(ctx, cudaMemcpyAsync(&lev, G->c_level + j, 4, cudaMemcpyDeviceToHost, ctx->st), "read C");
+    ck(ctx, cudaMemcpyAsync(&r, G->c_rank + j, 4, cudaMemcpyDeviceToHost, ctx->st), "read C");
+    sync(ctx);
+    u32* cur = dalloc<u32>(ctx, 1);
+    ck(ctx, cudaMemcpyAsync(cur, &r, 4, cudaMemcpyHostToDevice, ctx->st), "copy");
+    u64 cnt = 1;
+    for (u32 l = lev; l >= 1; l--) {
+        const Level& L = G->lv[l - 1];
+        u32* lens = dalloc<u32>(ctx, cnt);
+        u64* offs = dalloc<u64>(ctx, cnt);
+        ck(ctx, launch_rule_lens(cur, cnt, L.rhs_off, lens, ctx->st), "rule lens");
+        u64 grid = 0;
+        const u64 stiles = std::max<u64>(1, scan2_tiles_for(cnt));
+        ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, stiles, scan2_lb_bytes(stiles));
+        ck(ctx, launch_scan2(lens, nullptr, cnt, offs, nullptr, ctx->scratch + 1, ctx->lb2, ++ctx->epoch, ctx->ctr,
+                             ctx->ctr_val, ctx->ds, ctx->st, &grid),
+           "scan");
+        ctx->ctr_val += grid;
+        u64 total = 0;
+        ck(ctx, cudaMemcpyAsync(&total, ctx->scratch + 1, 8, cudaMemcpyDeviceToHost, ctx->st), "read total");
+        check_device_status(ctx, read_status(ctx));
+        u32* next = dalloc<u32>(ctx, total);
+        ck(ctx, launch_expand(cur, cnt, offs, L.rhs_off, L.rhs, next, ctx->st), "expand");
+        ctx->launches += 3;
+        dfree(ctx, lens);
+        dfree(ctx, offs);
+        dfree(ctx, cur);
+        cur = next;
+        cnt = total;
+    }
+    *out_len = cnt;
+    if (cap < cnt) {
+        dfree(ctx, cur);
+        sync(ctx);
+        fail_if(ctx, true, LCG_EINVAL, "output buffer too small");
+    }
+    if (on_dev) {
+        ck(ctx, launch_to_bytes(cur, cnt, out, ctx->st), "to bytes");
+    } else {
+        unsigned char* tmp = dalloc<unsigned char>(ctx, cnt);
+        ck(ctx, launch_to_bytes(cur, cnt, tmp, ctx->st), "to bytes");
+        ck(ctx, cudaMemcpyAsync(out, tmp, cnt, cudaMemcpyDeviceToHost, ctx->st), "copy out");
+        dfree(ctx, tmp);
+    }
+    ctx->launches++;
+    dfree(ctx, cur);
+    sync(ctx);
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------
+// C entry points
+// --------------------------------------------------------------------------
+
+#define LCG_GUARD_BEGIN try {
+#define LCG_GUARD_END                                  \
+    }                                                  \
+    catch (const Fail& f) {                            \
+        return f.code;                                 \
+    }                                                  \
+    catch (const std::bad_alloc&) {                    \
+        ctx->err = "host allocation failed";           \
+        return LCG_ENOMEM;                             \
+    }
+
+extern "C" {
+
+int lcg_ctx_create(int device, const lcg_hash_family* H, void* stream, lcg_ctx** out) {
+    if (!out) return LCG_EINVAL;
+    *out = nullptr;
+    if (!H || H->levels < 2 || H->levels > 4096 || H->m_bits < 1 || H->m_bits > 32 || !H->a || !H->b || !H->c)
+        return LCG_EINVAL;
+    for (u32 i = 0; i < H->levels; i++)
+        if (H->a[i] == 0 || H->a[i] >= kP61 || H->b[i] >= kP61 || H->c[i] == 0 || H->c[i] >= kP61)
+            return LCG_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return LCG_EDEVICE;
+    lcg_ctx* ctx = new (std::nothrow) lcg_ctx();
+    if (!ctx) return LCG_ENOMEM;
+    ctx->device = device;
+    ctx->a.assign(H->a, H->a + H->levels);
+    ctx->b.assign(H->b, H->b + H->levels);
+    ctx->c.assign(H->c, H->c + H->levels);
+    ctx->levels = H->levels;
+    ctx->m_bits = H->m_bits;
+    ctx->mmask = (H->m_bits == 32) ? 0xffffffffull : ((1ull << H->m_bits) - 1);
+    u64 tag = 1469598103934665603ull;
+    for (u32 i = 0; i < H->levels; i++) {
+        for (u64 w : {H->a[i], H->b[i], H->c[i]}) tag = (tag ^ w) * 1099511628211ull;
+    }
+    ctx->tag = (tag ^ ctx->mmask) * 1099511628211ull;
+    try {
+        ck(ctx, cudaSetDevice(device), "cudaSetDevice");
+        if (stream) {
+            ctx->st = (cudaStream_t)stream;
+        } else {
+            ck(ctx, cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking), "stream");
+            ctx->own_stream = true;
+        }
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+            u64 thr = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        ck(ctx, cudaMalloc(&ctx->ds, sizeof(DevStatus)), "cudaMalloc");
+        ck(ctx, cudaMalloc(&ctx->rc, sizeof(RoundCounts)), "cudaMalloc");
+        ck(ctx, cudaMalloc(&ctx->ctr, sizeof(u64)), "cudaMalloc");
+        ck(ctx, cudaMalloc(&ctx->scratch, 8 * sizeof(u64)), "cudaMalloc");
+        ck(ctx, cudaMemset(ctx->ds, 0, sizeof(DevStatus)), "memset");
+        ck(ctx, cudaMemset(ctx->ctr, 0, sizeof(u64)), "memset");
+        ck(ctx, cudaMemset(ctx->scratch, 0, 8 * sizeof(u64)), "memset");
+        ck(ctx, cudaDeviceSynchronize(), "sync");
+    } catch (const Fail& f) {
+        lcg_ctx_destroy(ctx);
+        return f.code;
+    }
+    *out = ctx;
+    return LCG_OK;
+}
+
+void lcg_ctx_destroy(lcg_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->st) cudaStreamSynchronize(ctx->st);
+    if (ctx->lb1) cudaFree(ctx->lb1);
+    if (ctx->lb2) cudaFree(ctx->lb2);
+    cudaFree(ctx->ds);
+    cudaFree(ctx->rc);
+    cudaFree(ctx->ctr);
+    cudaFree(ctx->scratch);
+    if (ctx->own_stream && ctx->st) cudaStreamDestroy(ctx->st);
+    delete ctx;
+}
+
+const char* lcg_last_error(const lcg_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int lcg_last_build_stats(const lcg_ctx* ctx, lcg_build_stats* out) {
+    if (!ctx || !out) return LCG_EINVAL;
+    *out = ctx->stats;
+    return LCG_OK;
+}
+
+int lcg_build(lcg_ctx* ctx, const uint8_t* data, const uint64_t* offsets, uint32_t k, int data_on_device,
+              lcg_grammar** out) {
+    if (!ctx || !out) return LCG_EINVAL;
+    *out = nullptr;
+    lcg_grammar* G = nullptr;
+    LCG_GUARD_BEGIN
+    ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    G = new_grammar(ctx);
+    build_into(ctx, G, data, offsets, k, data_on_device, false);
+    sync(ctx);
+    *out = G;
+    return LCG_OK;
+    }
+    catch (const Fail& f) {
+        cudaStreamSynchronize(ctx->st);
+        free_grammar_now(G);
+        return f.code;
+    }
+    catch (const std::bad_alloc&) {
+        ctx->err = "host allocation failed";
+        cudaStreamSynchronize(ctx->st);
+        free_grammar_now(G);
+        return LCG_ENOMEM;
+    }
+}
+
+int lcg_build_into(lcg_ctx* ctx, lcg_grammar* resident, const uint8_t* data, const uint64_t* offsets, uint32_t k,
+                   int data_on_device) {
+    if (!ctx || !resident) return LCG_EINVAL;
+    if (resident->tag != ctx->tag) {
+        ctx->err = "resident grammar of another hash family";
+        return LCG_EMISMATCH;
+    }
+    LCG_GUARD_BEGIN
+    ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    build_into(ctx, resident, data, offsets, k, data_on_device, true);
+    sync(ctx);
+    return LCG_OK;
+    LCG_GUARD_END
+}
+
+int lcg_merge(lcg_ctx* ctx, lcg_grammar* a, const lcg_grammar* b) {
+    if (!ctx || !a || !b) return LCG_EINVAL;
+    LCG_GUARD_BEGIN
+    ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    merge(ctx, a, b);
+    return LCG_OK;
+    LCG_GUARD_END
+}
+
+int lcg_decompress(lcg_ctx* ctx, const lcg_grammar* G, uint32_t j, uint8_t* out, uint64_t cap, uint64_t* out_len,
+                   int out_on_device) {
+    if (!ctx || !G || !out_len) return LCG_EINVAL;
+    LCG_GUARD_BEGIN
+    ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    decompress(ctx, G, j, out, cap, out_len, out_on_device);
+    return LCG_OK;
+    LCG_GUARD_END
+}
+
+int lcg_grammar_shape(const lcg_grammar* G, uint32_t* k, uint32_t* nlevels) {
+    if (!G) return LCG_EINVAL;
+    if (k) *k = G->k;
+    if (nlevels) *nlevels = (uint32_t)G->lv.size();
+    return LCG_OK;
+}
+
+int lcg_level_size(const lcg_grammar* G, uint32_t level, uint64_t* g, uint64_t* Gsz) {
+    if (!G || level < 1 || level > G->lv.size()) return LCG_EINVAL;
+    if (g) *g = G->lv[level - 1].g;
+    if (Gsz) *Gsz = G->lv[level - 1].G;
+    return LCG_OK;
+}
+
+int lcg_export_level(lcg_ctx* ctx, const lcg_grammar* G, uint32_t level, uint64_t* rhs_off, uint32_t* rhs,
+                     uint32_t* F) {
+    if (!ctx || !G || level < 1 || level > G->lv.size()) return LCG_EINVAL;
+    LCG_GUARD_BEGIN
+    ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    const Level& L = G->lv[level - 1];
+    if (rhs_off)
+        ck(ctx, cudaMemcpyAsync(rhs_off, L.rhs_off, (L.g + 1) * 8, cudaMemcpyDeviceToHost, ctx->st), "export");
+    if (rhs && L.G) ck(ctx, cudaMemcpyAsync(rhs, L.rhs, L.G * 4, cudaMemcpyDeviceToHost, ctx->st), "export");
+    if (F && L.g) ck(ctx, cudaMemcpyAsync(F, L.F, L.g * 4, cudaMemcpyDeviceToHost, ctx->st), "export");
+    sync(ctx);
+    return LCG_OK;
+    LCG_GUARD_END
+}
+
+int lcg_export_start(lcg_ctx* ctx, const lcg_grammar* G, uint32_t* F0, uint32_t* c_level, uint32_t* c_rank) {
+    if (!ctx || !G) return LCG_EINVAL;
+    LCG_GUARD_BEGIN
+    ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (F0) ck(ctx, cudaMemcpyAsync(F0, G->F0, 256 * 4, cudaMemcpyDeviceToHost, ctx->st), "export");
+    if (c_level && G->k)
+        ck(ctx, cudaMemcpyAsync(c_level, G->c_level, G->k * 4, cudaMemcpyDeviceToHost, ctx->st), "export");
+    if (c_rank && G->k)
+        ck(ctx, cudaMemcpyAsync(c_rank, G->c_rank, G->k * 4, cudaMemcpyDeviceToHost, ctx->st), "export");
+    sync(ctx);
+    return LCG_OK;
+    LCG_GUARD_END
+}
+
+void lcg_grammar_free(lcg_grammar* G) { free_grammar_now(G); }
+
+}  // extern "C"

@@ -1,0 +1,280 @@
+// Device-side building blocks shared by the kernels of the library:
+// arithmetic modulo the Mersenne prime 2^61-1, the phrase table, the
+// decoupled look-back used by the single-pass scans, and the device status
+// word through which bounded waits report failure.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lcg {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+// --------------------------------------------------------------------------
+// arithmetic modulo p = 2^61 - 1
+// --------------------------------------------------------------------------
+
+constexpr u64 kP61 = 2305843009213693951ull;
+
+// a * b mod p for a, b < p.  Mersenne folding: with x = a*b = x_hi 2^61 + x_lo,
+// 2^61 = 1 (mod p) gives x = x_hi + x_lo (mod p); both parts are < 2^61, so
+// one conditional subtraction finishes the reduction.
+__device__ __forceinline__ u64 mulmod61(u64 a, u64 b) {
+    u64 lo = a * b;
+    u64 hi = __umul64hi(a, b);
+    u64 r = (lo & kP61) + ((lo >> 61) | (hi << 3));
+    return r >= kP61 ? r - kP61 : r;
+}
+
+__device__ __forceinline__ u64 addmod61(u64 a, u64 b) {  // a, b < p
+    u64 r = a + b;
+    return r >= kP61 ? r - kP61 : r;
+}
+
+// Level hash parameters of one level (Sec. 3.2).
+struct LevelHash {
+    u64 a, b, c;
+    u64 mmask;  // m - 1
+};
+
+// ((a * H + b) mod p) mod m for a polynomial value H < p (Eq. fast_hash).
+__device__ __forceinline__ u32 finish_hash(const LevelHash& h, u64 H) {
+    return (u32)(addmod61(mulmod61(h.a, H), h.b) & h.mmask);
+}
+
+// 64-bit finaliser of MurmurHash3 (public domain): spreads a value's bits.
+__device__ __forceinline__ u64 fmix64(u64 k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+// --------------------------------------------------------------------------
+// device status
+// --------------------------------------------------------------------------
+
+enum DevError : u32 {
+    kErrNone = 0,
+    kErrTimeout = 1,      // a bounded wait ran out
+    kErrTableFull = 2,    // a probe sequence visited every slot
+    kErrPhraseLong = 3,   // a phrase of >= 2^32 symbols
+    kErrMismatch = 4,     // equal right-hand sides with different fingerprints
+    kErrRankOverflow = 5, // a level with >= 2^32 rules
+};
+
+struct DevStatus {
+    u32 error;        // first DevError seen
+    u32 overflow;     // phrase table passed its load limit (host regrows)
+    u64 claims;       // slots claimed in the current table pass
+    u64 claim_len;    // total length of the claimed phrases
+    u64 aux[5];
+};
+
+__device__ __forceinline__ void set_error(DevStatus* st, u32 code) {
+    atomicCAS(&st->error, 0u, code);
+}
+
+__device__ __forceinline__ u32 vload(const volatile u32* p) { return *p; }
+__device__ __forceinline__ u64 vload(const volatile u64* p) { return *p; }
+
+constexpr u64 kSpinLimit = 1ull << 22;  // bounded waits: a few seconds at most
+
+// --------------------------------------------------------------------------
+// phrase table
+// --------------------------------------------------------------------------
+//
+// Open addressing with linear probing over 32-byte slots.  The first 16 bytes
+// {key, ref} are claimed together with one 128-bit compare-and-swap, so a
+// thread that finds a key always finds the content reference with it.
+//   key   : (min(len, 2^24-1) << 40) | 40-bit hash of the content (bit 0 clear);
+//           kEmpty when free.  Equal keys are only a filter: a hit is confirmed
+//           by comparing the phrase contents symbol by symbol.
+//   ref   : position of an occurrence of the phrase in the round's sequence;
+//           after naming it holds the phrase's rank.
+//   minp  : smallest phrase index among the occurrences (atomicMin), which
+//           decides first-occurrence naming.
+//   len   : phrase length; fp: its fingerprint h^i.
+struct __align__(16) Slot {
+    u64 key;
+    u64 ref;
+    u64 minp;
+    u32 len;
+    u32 fp;
+};
+static_assert(sizeof(Slot) == 32, "slot size");
+
+constexpr u64 kEmpty = ~0ull;
+constexpr u64 kLenSat = (1ull << 24) - 1;
+
+__device__ __forceinline__ u64 make_key(u64 H, u64 len) {
+    u64 h = fmix64(H ^ (len * 0x9E3779B97F4A7C15ull)) & 0xFFFFFFFFFEull;
+    u64 l = len < kLenSat ? len : kLenSat;
+    return (l << 40) | h;
+}
+
+__device__ __forceinline__ u64 key_home(u64 key) { return fmix64(key); }
+
+// 128-bit compare-and-swap on {key, ref} (sm_90+).  Returns the old pair.
+__device__ __forceinline__ void cas128(Slot* s, u64 cmp_key, u64 cmp_ref, u64 new_key, u64 new_ref,
+                                       u64& old_key, u64& old_ref) {
+    asm volatile(
+        "{\n\t"
+        ".reg .b128 c, n, d;\n\t"
+        "mov.b128 c, {%2, %3};\n\t"
+        "mov.b128 n, {%4, %5};\n\t"
+        "atom.relaxed.gpu.global.cas.b128 d, [%6], c, n;\n\t"
+        "mov.b128 {%0, %1}, d;\n\t"
+        "}"
+        : "=l"(old_key), "=l"(old_ref)
+        : "l"(cmp_key), "l"(cmp_ref), "l"(new_key), "l"(new_ref), "l"(s)
+        : "memory");
+}
+
+__device__ __forceinline__ u64 ld_relaxed(const u64* p) {
+    u64 v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// --------------------------------------------------------------------------
+// decoupled look-back (single-pass prefix sums over tiles in launch order)
+// --------------------------------------------------------------------------
+//
+// Each tile publishes its aggregate, then its inclusive prefix, in an
+// LBSlot.  The flag word carries the launch epoch so that slots left by an
+// earlier launch read as "not yet published": no clearing between launches.
+// Tiles take their index from a counter in launch order, so a tile only ever
+// waits on tiles already running.
+
+template <int NV>
+struct LBSlot {
+    u64 flag;  // (epoch << 2) | state, state 1 = aggregate, 2 = inclusive prefix
+    u64 agg[NV];
+    u64 incl[NV];
+};
+
+// Block-wide: every thread passes the tile's aggregate in `agg` (only thread 0's
+// value is used) and receives the exclusive prefix in `excl`.  Needs
+// blockDim.x >= 32.  On a timeout the error is set and the prefix is 0.
+template <int NV>
+__device__ void block_lookback(LBSlot<NV>* st, u64 tile, u64 epoch, const u64 (&agg)[NV], u64 (&excl)[NV],
+                               DevStatus* ds) {
+    __shared__ u64 s_excl[NV];
+    if (threadIdx.x < 32) {
+        const u32 lane = threadIdx.x;
+        volatile LBSlot<NV>* vs = st;
+        u64 acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) acc[v] = 0;
+        if (tile == 0) {
+            if (lane == 0) {
+#pragma unroll
+                for (int v = 0; v < NV; v++) { vs[0].agg[v] = agg[v]; vs[0].incl[v] = agg[v]; }
+                __threadfence();
+                vs[0].flag = (epoch << 2) | 2;
+            }
+        } else {
+            if (lane == 0) {
+#pragma unroll
+                for (int v = 0; v < NV; v++) vs[tile].agg[v] = agg[v];
+                __threadfence();
+                vs[tile].flag = (epoch << 2) | 1;
+            }
+            long long base = (long long)tile - 1;
+            bool failed = false;
+            while (true) {
+                long long idx = base - (long long)lane;
+                u32 state = 2;  // virtual tiles before 0: inclusive, value 0
+                if (idx >= 0) {
+                    u64 it = 0;
+                    while (true) {
+                        u64 f = vs[idx].flag;
+                        if ((f >> 2) == epoch && (f & 3) != 0) { state = (u32)(f & 3); break; }
+                        if (++it > kSpinLimit || vload(&ds->error) != 0) { state = 0; break; }
+                    }
+                }
+                if (__any_sync(0xffffffffu, state == 0)) { failed = true; break; }
+                u32 incl_mask = __ballot_sync(0xffffffffu, state == 2);
+                __threadfence();
+                int first = incl_mask ? __ffs(incl_mask) - 1 : 31;
+                u64 val[NV];
+#pragma unroll
+                for (int v = 0; v < NV; v++) {
+                    val[v] = 0;
+                    if (idx >= 0 && (int)lane <= first) val[v] = (state == 2) ? vs[idx].incl[v] : vs[idx].agg[v];
+                    for (int o = 16; o > 0; o >>= 1) val[v] += __shfl_down_sync(0xffffffffu, val[v], o);
+                    acc[v] += val[v];
+                }
+                if (incl_mask) break;
+                base -= 32;
+            }
+            if (failed) {
+                if (lane == 0) set_error(ds, kErrTimeout);
+#pragma unroll
+                for (int v = 0; v < NV; v++) acc[v] = 0;
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int v = 0; v < NV; v++) vs[tile].incl[v] = acc[v] + agg[v];
+                __threadfence();
+                vs[tile].flag = (epoch << 2) | 2;
+            }
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int v = 0; v < NV; v++) s_excl[v] = acc[v];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < NV; v++) excl[v] = s_excl[v];
+    __syncthreads();
+}
+
+// Tile index in launch order from a counter that is never reset: the host
+// passes the counter's value at launch (`ctr_base`).
+__device__ __forceinline__ u64 dynamic_tile(u64* ctr, u64 ctr_base) {
+    __shared__ u64 s_tile;
+    if (threadIdx.x == 0) s_tile = atomicAdd(ctr, 1ull) - ctr_base;
+    __syncthreads();
+    u64 t = s_tile;
+    __syncthreads();
+    return t;
+}
+
+// Block-wide exclusive scan of one u64 per thread (blockDim.x a multiple of 32,
+// at most 1024).  Returns the exclusive prefix; `total` gets the block sum.
+__device__ __forceinline__ u64 block_excl_scan(u64 x, u64& total) {
+    __shared__ u64 s_warp[32];
+    __shared__ u64 s_total;
+    const u32 lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    u64 incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        u64 y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        u64 w = lane < nw ? s_warp[lane] : 0;
+        u64 wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            u64 y = __shfl_up_sync(0xffffffffu, wi, o);
+            if ((int)lane >= o) wi += y;
+        }
+        if (lane < nw) s_warp[lane] = wi - w;  // exclusive warp offsets
+        if (lane == nw - 1) s_total = wi;
+    }
+    __syncthreads();
+    u64 res = s_warp[wid] + incl - x;
+    total = s_total;
+    __syncthreads();
+    return res;
+}
+
+}  // namespace lcg

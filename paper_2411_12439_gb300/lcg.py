@@ -1,0 +1,237 @@
+"""Thin Python binding of the C ABI in ``include/lcg.h`` (argument marshalling only).
+
+Every operation runs in the CUDA library ``liblcg_gb300.so``.  There is no
+fallback: if the library is missing or no CUDA device is usable, the calls
+raise ``LCGError``.
+
+Inputs are either host arrays (numpy, bytes) or CUDA tensors (torch.uint8 on
+the context's device); offsets are always host uint64 arrays of k+1 entries.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LCG_OK = 0
+_ERRORS = {
+    -1: "LCG_EINVAL", -2: "LCG_ENOMEM", -3: "LCG_ELEVELS", -4: "LCG_EMISMATCH",
+    -5: "LCG_EOVERFLOW", -6: "LCG_ETIMEOUT", -7: "LCG_EDEVICE", -8: "LCG_ETABLE",
+}
+SYMBOLS = [
+    "lcg_ctx_create", "lcg_ctx_destroy", "lcg_last_error", "lcg_last_build_stats", "lcg_build", "lcg_build_into",
+    "lcg_merge", "lcg_decompress", "lcg_grammar_shape", "lcg_level_size", "lcg_export_level", "lcg_export_start",
+    "lcg_grammar_free",
+]
+
+
+class LCGError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class HashFamilyC(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_uint32), ("m_bits", ctypes.c_uint32), ("a", ctypes.c_void_p),
+                ("b", ctypes.c_void_p), ("c", ctypes.c_void_p)]
+
+
+class RoundStatsC(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("phrases", ctypes.c_uint64), ("g", ctypes.c_uint64),
+                ("G", ctypes.c_uint64), ("strings", ctypes.c_uint64), ("table_cap", ctypes.c_uint64),
+                ("retries", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+
+
+class BuildStatsC(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("kernel_launches", ctypes.c_uint64),
+                ("input_bytes", ctypes.c_uint64), ("round", RoundStatsC * 64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liblcg_gb300.so (building it first when it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise LCGError(-7, f"CUDA library not built: {_build.LIB}")
+    lib = ctypes.CDLL(_build.LIB)
+    P, U32, U64, I = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    lib.lcg_ctx_create.argtypes = [I, ctypes.POINTER(HashFamilyC), P, PP]
+    lib.lcg_ctx_destroy.argtypes = [P]
+    lib.lcg_ctx_destroy.restype = None
+    lib.lcg_last_error.argtypes = [P]
+    lib.lcg_last_error.restype = ctypes.c_char_p
+    lib.lcg_last_build_stats.argtypes = [P, ctypes.POINTER(BuildStatsC)]
+    lib.lcg_build.argtypes = [P, P, P, U32, I, PP]
+    lib.lcg_build_into.argtypes = [P, P, P, P, U32, I]
+    lib.lcg_merge.argtypes = [P, P, P]
+    lib.lcg_decompress.argtypes = [P, P, U32, P, U64, ctypes.POINTER(U64), I]
+    lib.lcg_grammar_shape.argtypes = [P, ctypes.POINTER(U32), ctypes.POINTER(U32)]
+    lib.lcg_level_size.argtypes = [P, U32, ctypes.POINTER(U64), ctypes.POINTER(U64)]
+    lib.lcg_export_level.argtypes = [P, P, U32, P, P, P]
+    lib.lcg_export_start.argtypes = [P, P, P, P, P]
+    lib.lcg_grammar_free.argtypes = [P]
+    lib.lcg_grammar_free.restype = None
+    for name in SYMBOLS:
+        if name not in ("lcg_ctx_destroy", "lcg_last_error", "lcg_grammar_free"):
+            getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def _np_ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data) if a.size else ctypes.c_void_p(0)
+
+
+def _data_arg(data):
+    """(pointer, on_device, keepalive) of a uint8 host array or CUDA tensor."""
+    try:
+        import torch
+        if isinstance(data, torch.Tensor):
+            if data.dtype != torch.uint8 or not data.is_contiguous():
+                raise LCGError(-1, "data must be a contiguous uint8 tensor")
+            return ctypes.c_void_p(data.data_ptr()), int(data.is_cuda), data
+    except ImportError:
+        pass
+    if isinstance(data, (bytes, bytearray)):
+        data = np.frombuffer(data, dtype=np.uint8)
+    arr = np.ascontiguousarray(data, dtype=np.uint8)
+    return _np_ptr(arr), 0, arr
+
+
+class Context:
+    """A device, a stream and a hash family (``lcg_ctx``)."""
+
+    def __init__(self, hash_family, device: int = 0, stream=None):
+        lib = load()
+        self._keep = [np.ascontiguousarray(x, dtype=np.uint64) for x in (hash_family.a, hash_family.b, hash_family.c)]
+        hfc = HashFamilyC(int(hash_family.levels), int(hash_family.m_bits), *[_np_ptr(x) for x in self._keep])
+        h = ctypes.c_void_p(0)
+        st = ctypes.c_void_p(stream) if stream is not None else ctypes.c_void_p(0)
+        rc = lib.lcg_ctx_create(int(device), ctypes.byref(hfc), st, ctypes.byref(h))
+        if rc != LCG_OK:
+            raise LCGError(rc, "lcg_ctx_create failed")
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().lcg_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != LCG_OK:
+            msg = load().lcg_last_error(self._h)
+            raise LCGError(rc, msg.decode() if msg else "")
+
+    def build(self, data, offsets) -> "Grammar":
+        """lcg_build: BuildGram over the strings data[offsets[j]:offsets[j+1]]."""
+        ptr, on_dev, keep = _data_arg(data)
+        off = np.ascontiguousarray(offsets, dtype=np.uint64)
+        h = ctypes.c_void_p(0)
+        self._check(load().lcg_build(self._h, ptr, _np_ptr(off), off.shape[0] - 1, on_dev, ctypes.byref(h)))
+        del keep
+        return Grammar(self, h)
+
+    def build_into(self, grammar: "Grammar", data, offsets) -> None:
+        """lcg_build_into: parse against (and extend) a resident grammar."""
+        ptr, on_dev, keep = _data_arg(data)
+        off = np.ascontiguousarray(offsets, dtype=np.uint64)
+        self._check(load().lcg_build_into(self._h, grammar._h, ptr, _np_ptr(off), off.shape[0] - 1, on_dev))
+        del keep
+
+    def merge(self, a: "Grammar", b: "Grammar") -> "Grammar":
+        """lcg_merge: a absorbs b (in place); returns a."""
+        self._check(load().lcg_merge(self._h, a._h, b._h))
+        return a
+
+    def last_build_stats(self) -> dict:
+        st = BuildStatsC()
+        self._check(load().lcg_last_build_stats(self._h, ctypes.byref(st)))
+        rounds = [{f: int(getattr(st.round[i], f)) for f in ("n", "phrases", "g", "G", "strings", "table_cap",
+                                                             "retries")} for i in range(min(st.rounds, 64))]
+        return {"rounds": int(st.rounds), "kernel_launches": int(st.kernel_launches),
+                "input_bytes": int(st.input_bytes), "per_round": rounds}
+
+
+class Grammar:
+    """A device-resident grammar (``lcg_grammar``), owned by the library."""
+
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self._h = handle
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().lcg_grammar_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        k, nl = ctypes.c_uint32(0), ctypes.c_uint32(0)
+        self.ctx._check(load().lcg_grammar_shape(self._h, ctypes.byref(k), ctypes.byref(nl)))
+        return int(k.value), int(nl.value)
+
+    def level_size(self, level: int):
+        g, G = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        self.ctx._check(load().lcg_level_size(self._h, level, ctypes.byref(g), ctypes.byref(G)))
+        return int(g.value), int(G.value)
+
+    def export(self) -> dict:
+        """Host copy in the oracle's export format."""
+        lib = load()
+        k, nl = self.shape
+        levels = []
+        for i in range(1, nl + 1):
+            g, G = self.level_size(i)
+            ro = np.zeros(g + 1, dtype=np.uint64)
+            rhs = np.zeros(max(G, 1), dtype=np.uint32)
+            F = np.zeros(max(g, 1), dtype=np.uint32)
+            self.ctx._check(lib.lcg_export_level(self.ctx._h, self._h, i, _np_ptr(ro), _np_ptr(rhs), _np_ptr(F)))
+            levels.append({"g": g, "rhs_off": ro, "rhs": rhs[:G], "F": F[:g]})
+        F0 = np.zeros(256, dtype=np.uint32)
+        cl = np.zeros(max(k, 1), dtype=np.uint32)
+        cr = np.zeros(max(k, 1), dtype=np.uint32)
+        self.ctx._check(lib.lcg_export_start(self.ctx._h, self._h, _np_ptr(F0), _np_ptr(cl), _np_ptr(cr)))
+        return {"F0": F0, "levels": levels, "c_level": cl[:k], "c_rank": cr[:k]}
+
+    def decompress(self, j: int, out=None):
+        """exp(C[j]) as bytes (host), or into a CUDA uint8 tensor ``out``."""
+        lib = load()
+        n = ctypes.c_uint64(0)
+        if out is not None:
+            ptr, on_dev, keep = _data_arg(out)
+            self.ctx._check(lib.lcg_decompress(self.ctx._h, self._h, j, ptr, out.numel(), ctypes.byref(n), on_dev))
+            return int(n.value)
+        rc = lib.lcg_decompress(self.ctx._h, self._h, j, None, 0, ctypes.byref(n), 0)
+        need = int(n.value)
+        if rc != LCG_OK and need == 0:
+            self.ctx._check(rc)
+        buf = np.zeros(max(need, 1), dtype=np.uint8)
+        self.ctx._check(lib.lcg_decompress(self.ctx._h, self._h, j, _np_ptr(buf), need, ctypes.byref(n), 0))
+        return buf[:need].tobytes()
