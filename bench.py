@@ -1,0 +1,360 @@
+"""Benchmark of the batched LCG build on one GB300 (or N GPUs, one process each).
+
+Metric: input GB/s of BuildGram (lcg_build) over a bacterial-like batch of 64
+strings of ~5 Mbp (320 MB), all strings parsed together in one call per step,
+with the result checked bit-exact against the oracle in the test suite.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line is printed by rank 0.  ``value`` is the whole-job input
+throughput with the inputs resident in HBM; ``e2e`` is the same metric through
+the public API from pinned host memory, with the grammar copied back to the
+host every step; ``roofline`` rates the kernel with the largest device time
+against the measured HBM bandwidth; ``cpu_baseline`` times the CPU oracle on a
+bounded sample of the same workload; ``plain`` is the one-string-at-a-time form
+(each string parsed against the growing resident grammar).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import lcg_inputs as li  # noqa: E402
+
+METRIC = "LCG build input GB/s on 1 GB300 (batched vs plain), bit-exact; % of HBM peak"
+WORKLOAD = ("bacterial-like batch: 64 strings of ~5 Mbp from 4 seeded random base genomes "
+            "(1% SNPs, 0.02% indels of 1-50 bp, 5 block rearrangements per string), 320 MB, "
+            "all strings in one batched build per step")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(rank: int):
+    # weak scaling: every rank parses its own batch of the same shape
+    return li.bacterial_collection(seed=2 + 1000 * rank)
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2411_12439_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per algorithmic byte of `kernel` from the committed ncu
+    summary, when it was taken from the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            t = json.load(fh)
+    except Exception:
+        return None
+    if t.get("source_hash") != kernel_source_hash():
+        return None
+    entry = t.get("kernels", {}).get(kernel)
+    if not entry:
+        return None
+    return float(entry["dram_bytes_per_alg_byte"])
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if not self.rows:
+            return None
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def grammar_bytes(ex) -> int:
+    n = ex["F0"].nbytes + ex["c_level"].nbytes + ex["c_rank"].nbytes
+    for L in ex["levels"]:
+        n += L["rhs_off"].nbytes + L["rhs"].nbytes + L["F"].nbytes
+    return n
+
+
+def cpu_baseline(coll, hf, target_s: float = 12.0):
+    """The oracle as it stands, one host thread, on a bounded sample of the
+    workload (its first strings, as many as fit about `target_s` seconds)."""
+    from oracle import oracle as O
+    probe = coll.subset([0])
+    t = time.perf_counter()
+    O.build(probe, hf)
+    rate = probe.n / max(time.perf_counter() - t, 1e-6)
+    take = max(1, min(coll.k, int(target_s * rate / max(1, probe.n))))
+    sample = coll.subset(range(take))
+    t = time.perf_counter()
+    O.build(sample, hf)
+    dt = time.perf_counter() - t
+    return {"value": sample.n / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {take} of {coll.k} strings ({sample.n / 1e6:.1f} MB), one lcg oracle build, 1 thread",
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    hf = li.hash_family()
+    coll = workload(0)
+    from oracle import oracle as O
+    O.build_library()
+    sample = coll.subset(range(4))  # each step: a bounded 4-string sample (~20 MB)
+    for _ in range(args.warmup):
+        O.build(sample, hf)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        O.build(sample, hf)
+        times.append(time.perf_counter() - t)
+    tot = sum(times)
+    value = sample.n * args.steps / tot / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/u32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"first 4 of {coll.k} strings ({sample.n / 1e6:.1f} MB) per step",
+                   "parallelism": "single host thread"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first 4 of {coll.k} strings per step"},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2411_12439_gb300 import Context
+
+    hf = li.hash_family()
+    coll = workload(rank)
+    d = torch.from_numpy(coll.data).to(f"cuda:{local}")
+    stream = torch.cuda.current_stream()
+    ctx = Context(hf, device=local, stream=stream.cuda_stream)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        ctx.build(d, coll.offsets).free()
+
+    # ---- timed region: inputs resident in HBM (320 MB > L2, no flush needed)
+    ctx.set_kernel_timing(True)
+    kt = {}
+    launches = 0
+    keep = []
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        keep.append(ctx.build(d, coll.offsets))
+        for name, v in ctx.last_kernel_times().items():
+            acc = kt.setdefault(name, {"launches": 0, "ms": 0.0, "bytes": 0.0})
+            for key in acc:
+                acc[key] += v[key]
+        launches += ctx.last_build_stats()["kernel_launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+    ctx.set_kernel_timing(False)
+    stats = ctx.last_build_stats()
+    for g in keep:
+        g.free()
+    keep.clear()
+    value = world * coll.n / (ms / 1e3) / 1e9
+
+    # ---- end to end through the public API: pinned host input, grammar to host
+    hd = torch.from_numpy(coll.data).pin_memory()
+    g = ctx.build(hd, coll.offsets)
+    d2h = grammar_bytes(g.export())
+    g.free()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        g = ctx.build(hd, coll.offsets)
+        ex = g.export()
+        g.free()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps)
+    e2e = {"value": world * coll.n / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(coll.n),
+           "d2h_bytes_per_step": int(grammar_bytes(ex)), "ms_per_step": e2e_s * 1e3}
+    del ex
+
+    # ---- plain form: one string per launch sequence, against the resident grammar
+    plain = None
+    if not args.no_plain:
+        offs = coll.offsets.astype(np.int64)
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        R = ctx.build(d[offs[0]:offs[1]], np.array([0, offs[1] - offs[0]], dtype=np.uint64))
+        for j in range(1, coll.k):
+            ctx.build_into(R, d[offs[j]:offs[j + 1]], np.array([0, offs[j + 1] - offs[j]], dtype=np.uint64))
+        p1.record(stream)
+        torch.cuda.synchronize()
+        pms = max_over_ranks(p0.elapsed_time(p1))
+        R.free()
+        pv = world * coll.n / (pms / 1e3) / 1e9
+        plain = {"value": pv, "unit": "GB/s", "ms_per_step": pms, "batched_over_plain": value / pv,
+                 "form": "one string per launch sequence, each parsed against the resident grammar"}
+
+    # ---- roofline of the kernel with the largest device time
+    peak, peak_kind = measured_peak()
+    dom = max(kt.items(), key=lambda kv: kv[1]["ms"]) if kt else None
+    roofline = None
+    if dom:
+        name, v = dom
+        per_launch_bytes = v["bytes"] / v["launches"]
+        per_launch_s = v["ms"] / v["launches"] / 1e3
+        achieved = per_launch_bytes / per_launch_s / 1e9
+        ratio = profiled_traffic(name)
+        roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_source": peak_kind,
+                    "traffic": (ratio * per_launch_bytes) if ratio is not None else None,
+                    "alg_bytes_per_launch": per_launch_bytes, "launches": v["launches"],
+                    "share_of_kernel_time": v["ms"] / sum(x["ms"] for x in kt.values())}
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(coll, hf)
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8/u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "strings": coll.k, "input_bytes": int(coll.n),
+                   "rounds": stats["rounds"], "l2": "inputs larger than L2 (320 MB > 129 MB), no flush",
+                   "parallelism": f"dp{world}" if world > 1 else "single GPU"},
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roofline,
+        "cpu_baseline": cpu, "plain": plain,
+        "kernels": {k: {"launches": v["launches"] // args.steps, "ms_per_step": v["ms"] / args.steps}
+                    for k, v in sorted(kt.items(), key=lambda kv: -kv[1]["ms"])},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -99,6 +99,16 @@ typedef struct lcg_build_stats {
     lcg_round_stats round[64];
 } lcg_build_stats;
 
+/* Device time of the kernels of the last call, per kernel kind (collected
+ * only while kernel timing is enabled with lcg_set_kernel_timing). */
+typedef struct lcg_kernel_time {
+    char name[24];       /* kernel kind, e.g. "k_phrases" */
+    uint32_t launches;
+    uint32_t pad;
+    double ms;           /* summed CUDA-event time of its launches */
+    double bytes;        /* algorithmic bytes of its launches (see the kernel's comment) */
+} lcg_kernel_time;
+
 /* Create a context on CUDA device `device` with hash family H.  `stream` is a
  * cudaStream_t to run on (NULL: the context creates its own).  Returns
  * LCG_EINVAL for a malformed family, LCG_EDEVICE when the device is not
@@ -108,6 +118,13 @@ void lcg_ctx_destroy(lcg_ctx* ctx);
 const char* lcg_last_error(const lcg_ctx* ctx);
 /* Statistics of the last build call of this context (host struct filled). */
 int lcg_last_build_stats(const lcg_ctx* ctx, lcg_build_stats* out);
+/* Enable (1) or disable (0) per-kernel CUDA-event timing in later calls.  When
+ * enabled, every kernel launch is bracketed by two events on the context's
+ * stream; the sums are read with lcg_last_kernel_times. */
+int lcg_set_kernel_timing(lcg_ctx* ctx, int enable);
+/* Copy up to `cap` entries of the per-kind kernel times of the last call into
+ * `out` (host) and their number into *count. */
+int lcg_last_kernel_times(const lcg_ctx* ctx, lcg_kernel_time* out, uint32_t cap, uint32_t* count);
 
 /* BuildGram(T, H) (Sec. 3.3).
  * data: the k strings concatenated (uint8), `data_on_device` = 1 when it is a

@@ -25,7 +25,8 @@ struct Level {
     u64* rhs_off = nullptr;    // cap_g + 1 entries
     u32* rhs = nullptr;
     u32* F = nullptr;
-    void* rtab = nullptr;      // table over the rules (for parses against this grammar and merges)
+    void* rkeys = nullptr;     // table over the rules (for parses against this grammar and merges)
+    u64* rvals = nullptr;
     u64 rcap = 0;
     bool rvalid = false;
 };
@@ -65,11 +66,22 @@ struct lcg_ctx {
     double ratio_hint[64] = {0};  // distinct/phrases of the last build, per level
     lcg_build_stats stats{};
     u64 launches = 0;
+    // per-kernel CUDA-event timing (optional)
+    bool ktime = false;
+    struct KRec {
+        const char* name;
+        cudaEvent_t a, b;
+        double bytes;
+    };
+    std::vector<KRec> krecs;
+    std::vector<cudaEvent_t> evpool;
+    std::vector<lcg_kernel_time> ktimes;
 };
 
 namespace {
 
 constexpr u64 kMaxRank = 0x7fffffffull;  // ranks are tagged with one bit in the phrase slots
+constexpr double kL2Bytes = 126.5 * 1024 * 1024;  // GB300 L2 (for algorithmic-byte accounting)
 
 struct Fail {
     int code;
@@ -103,6 +115,63 @@ void dfree(lcg_ctx* ctx, void* p) {
 
 void sync(lcg_ctx* ctx) { ck(ctx, cudaStreamSynchronize(ctx->st), "stream synchronize"); }
 
+// ---- per-kernel timing: events around each launch when enabled -----------
+
+cudaEvent_t kt_event(lcg_ctx* ctx) {
+    if (!ctx->evpool.empty()) {
+        cudaEvent_t e = ctx->evpool.back();
+        ctx->evpool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    ck(ctx, cudaEventCreate(&e), "cudaEventCreate");
+    return e;
+}
+
+void kt_reset(lcg_ctx* ctx) {
+    for (auto& r : ctx->krecs) {
+        ctx->evpool.push_back(r.a);
+        ctx->evpool.push_back(r.b);
+    }
+    ctx->krecs.clear();
+    ctx->ktimes.clear();
+}
+
+// Record the start of a launch of kernel `name` that moves `bytes` algorithmic
+// bytes; returns a handle for kt_end (or -1 when timing is off).
+int kt_begin(lcg_ctx* ctx, const char* name, double bytes) {
+    if (!ctx->ktime) return -1;
+    lcg_ctx::KRec r{name, kt_event(ctx), kt_event(ctx), bytes};
+    ck(ctx, cudaEventRecord(r.a, ctx->st), "cudaEventRecord");
+    ctx->krecs.push_back(r);
+    return (int)ctx->krecs.size() - 1;
+}
+
+void kt_end(lcg_ctx* ctx, int h) {
+    if (h >= 0) ck(ctx, cudaEventRecord(ctx->krecs[h].b, ctx->st), "cudaEventRecord");
+}
+
+// After the call's last synchronisation: sum the times per kernel kind.
+void kt_collect(lcg_ctx* ctx) {
+    ctx->ktimes.clear();
+    for (auto& r : ctx->krecs) {
+        float ms = 0.f;
+        ck(ctx, cudaEventElapsedTime(&ms, r.a, r.b), "cudaEventElapsedTime");
+        lcg_kernel_time* t = nullptr;
+        for (auto& x : ctx->ktimes)
+            if (std::strncmp(x.name, r.name, sizeof(x.name)) == 0) t = &x;
+        if (!t) {
+            lcg_kernel_time z{};
+            std::strncpy(z.name, r.name, sizeof(z.name) - 1);
+            ctx->ktimes.push_back(z);
+            t = &ctx->ktimes.back();
+        }
+        t->launches++;
+        t->ms += ms;
+        t->bytes += r.bytes;
+    }
+}
+
 void check_device_status(lcg_ctx* ctx, const DevStatus& h) {
     switch (h.error) {
         case kErrNone: return;
@@ -128,12 +197,6 @@ LevelHash level_hash(const lcg_ctx* ctx, u32 i) {
     h.c = ctx->c[i];
     h.mmask = ctx->mmask;
     return h;
-}
-
-u64 pow2_at_least(u64 x) {
-    u64 p = 1;
-    while (p < x) p <<= 1;
-    return p;
 }
 
 void ensure_lb(lcg_ctx* ctx, void** lb, u64* have, u64 tiles, size_t bytes) {
@@ -184,14 +247,16 @@ const u32* fprev_of(const lcg_grammar* G, u32 i) { return i == 1 ? G->F0 : G->lv
 // `need_g` rules at load <= 1/2.
 void ensure_resident(lcg_ctx* ctx, lcg_grammar* G, u32 i, u64 need_g) {
     Level& L = G->lv[i - 1];
-    const u64 want = pow2_at_least(std::max<u64>(2 * need_g, 1024));
-    if (L.rvalid && L.rcap >= want) return;
-    if (L.rtab) dfree(ctx, L.rtab);
-    L.rtab = dalloc<unsigned char>(ctx, want * slot_bytes());
-    L.rcap = want;
-    ck(ctx, cudaMemsetAsync(L.rtab, 0xFF, want * slot_bytes(), ctx->st), "memset table");
-    ck(ctx, launch_resident_build(L.rhs, L.rhs_off, 0, L.g, fprev_of(G, i), level_hash(ctx, i), L.rtab, want - 1,
-                                  ctx->ds, ctx->st),
+    if (L.rvalid && L.rcap >= 2 * need_g) return;
+    const u64 cap = std::max<u64>(1024, 3 * need_g);
+    dfree(ctx, L.rkeys);
+    dfree(ctx, L.rvals);
+    L.rkeys = dalloc<unsigned char>(ctx, cap * key_bytes());
+    L.rvals = dalloc<u64>(ctx, cap);
+    L.rcap = cap;
+    ck(ctx, cudaMemsetAsync(L.rkeys, 0xFF, cap * key_bytes(), ctx->st), "memset table");
+    ck(ctx, launch_resident_build(L.rhs, L.rhs_off, 0, L.g, i == 1, fprev_of(G, i), level_hash(ctx, i), L.rkeys,
+                                  L.rvals, cap, ctx->ds, ctx->st),
        "resident build");
     ctx->launches++;
     L.rvalid = true;
@@ -231,7 +296,8 @@ void free_grammar_now(lcg_grammar* G) {
         cudaFree(L.rhs_off);
         cudaFree(L.rhs);
         cudaFree(L.F);
-        cudaFree(L.rtab);
+        cudaFree(L.rkeys);
+        cudaFree(L.rvals);
     }
     cudaFree(G->c_level);
     cudaFree(G->c_rank);
@@ -316,9 +382,11 @@ void build_into(lcg_ctx* ctx, lcg_grammar* R, const uint8_t* data, const uint64_
         S_owned = g;
     }
     int symb = 1;
+    const u32* Sf = nullptr;  // fingerprints of the round's symbols (rounds >= 2)
     u64 n = n1;
     double prev_ratio = 0.0;
 
+    double p_ratio = 0.35;  // phrases per symbol, from the previous round
     for (u32 i = 1; kk > 0; i++) {
         fail_if(ctx, i >= ctx->levels, LCG_ELEVELS, "hash family too short: needs more than " +
                                                          std::to_string(ctx->levels) + " functions");
@@ -326,18 +394,25 @@ void build_into(lcg_ctx* ctx, lcg_grammar* R, const uint8_t* data, const uint64_
         lcg_round_stats& rs = ctx->stats.round[std::min<u32>(i - 1, 63)];
         rs.n = n;
         rs.strings = kk;
-        const u64 tiles = tiles_for(n);
+        const u64 tiles = (n + parse_tile_positions(symb) - 1) / parse_tile_positions(symb);
         ensure_lb(ctx, &ctx->lb1, &ctx->lb1_tiles, tiles, lb1_bytes(tiles));
-        u32* bitmap = dalloc<u32>(ctx, tiles * 256);
-        u64* tile_base = dalloc<u64>(ctx, tiles);
+        // every phrase but a string's first has length >= 2
+        const u64 Pmax = n / 2 + 2ull * kk + 1;
+        u64* string_first = dalloc<u64>(ctx, kk);
         u64* soff_next = dalloc<u64>(ctx, kk + 1);
         u32* sid_next = dalloc<u32>(ctx, kk);
         u64* R_phr = dalloc<u64>(ctx, kk);
         u32* R_sid = dalloc<u32>(ctx, kk);
+        u32* P_slot = dalloc<u32>(ctx, Pmax);
+        u32* Tnext = dalloc<u32>(ctx, Pmax);
+        u32* Fnext = dalloc<u32>(ctx, Pmax);
+        u32* tile_str = dalloc<u32>(ctx, tiles);
 
+        Level& L = R->lv[i - 1];
         RoundArgs a{};
         a.sym_bytes = symb;
         a.S = S;
+        a.Sf = Sf;
         a.n = n;
         a.soff = d_soff;
         a.sid = d_sid;
@@ -345,8 +420,8 @@ void build_into(lcg_ctx* ctx, lcg_grammar* R, const uint8_t* data, const uint64_
         a.Fprev = fprev_of(R, i);
         a.lh = level_hash(ctx, i);
         a.level = i;
-        a.bitmap = bitmap;
-        a.tile_base = tile_base;
+        a.string_first = string_first;
+        a.tile_str = tile_str;
         a.lb1 = ctx->lb1;
         a.ctr = ctx->ctr;
         a.total = ctx->scratch;
@@ -356,54 +431,72 @@ void build_into(lcg_ctx* ctx, lcg_grammar* R, const uint8_t* data, const uint64_
         a.R_phr = R_phr;
         a.R_sid = R_sid;
         a.rc = ctx->rc;
-        a.epoch = ++ctx->epoch;
-        a.ctr_base = ctx->ctr_val;
-        ctx->ctr_val += tiles;
-        ck(ctx, launch_breaks(a, ctx->st), "k_breaks");
-        ck(ctx, launch_strings(a, ctx->st), "k_strings");
-        ctx->launches += 2;
-        RoundCounts rc;
-        ck(ctx, cudaMemcpyAsync(&rc, ctx->rc, sizeof(rc), cudaMemcpyDeviceToHost, ctx->st), "read counts");
-        check_device_status(ctx, read_status(ctx));
-        const u64 P = rc.phrases;
-        rs.phrases = P;
-
-        Level& L = R->lv[i - 1];
-        u32* P_slot = dalloc<u32>(ctx, P);
-        u32* Tnext = dalloc<u32>(ctx, rc.n_next);
+        a.P_slot = P_slot;
+        a.P_cap = Pmax;
         if (against_resident && L.g > 0) {
             ensure_resident(ctx, R, i, L.g);
-            a.rtab = L.rtab;
-            a.rmask = L.rcap - 1;
+            a.rtab_keys = L.rkeys;
+            a.rtab_vals = L.rvals;
+            a.rtab_cap = L.rcap;
             a.rrhs = L.rhs;
             a.rrhs_off = L.rhs_off;
         }
         // phrase table sized from the distinct/phrase ratio seen before
+        const u64 P_est = std::min<u64>(Pmax, (u64)(p_ratio * 1.2 * (double)n) + 64);
         double ratio = ctx->ratio_hint[std::min<u32>(i, 63)];
         if (ratio <= 0) ratio = (i == 1) ? 0.02 : std::min(1.0, std::max(prev_ratio * 2.0, 0.05));
-        u64 est = std::max<u64>(4096, std::min<u64>(P, (u64)(ratio * 1.5 * (double)P) + 1));
-        u64 cap = pow2_at_least(2 * est);
-        void* tab = nullptr;
+        u64 est = std::max<u64>(4096, std::min<u64>(P_est, (u64)(ratio * 1.3 * (double)P_est) + 1));
+        u64 cap = 2 * est;
         u32 retries = 0;
         DevStatus st;
+        RoundCounts rc;
+        const double w = (double)symb;
+        int h;
+        ck(ctx, launch_tile_strings(a, ctx->st), "k_tile_strings");
+        ctx->launches++;
+        unsigned char* tkeys = nullptr;
+        u64* tvals = nullptr;
+        u32* claims = nullptr;
         while (true) {
             fail_if(ctx, cap > (kMaxRank + 1), LCG_ETABLE, "phrase table would exceed 2^31 slots");
-            tab = dalloc<unsigned char>(ctx, cap * slot_bytes());
-            ck(ctx, cudaMemsetAsync(tab, 0xFF, cap * slot_bytes(), ctx->st), "memset table");
+            tkeys = dalloc<unsigned char>(ctx, cap * key_bytes());
+            tvals = dalloc<u64>(ctx, cap);
+            claims = dalloc<u32>(ctx, cap);
+            ck(ctx, cudaMemsetAsync(tkeys, 0xFF, cap * key_bytes(), ctx->st), "memset table");
+            ck(ctx, cudaMemsetAsync(tvals, 0xFF, cap * sizeof(u64), ctx->st), "memset table");
             ck(ctx, cudaMemsetAsync((char*)ctx->ds + 4, 0, 4 + 16, ctx->st), "reset counters");
-            a.tab = tab;
-            a.mask = cap - 1;
+            a.tab_keys = tkeys;
+            a.tab_vals = tvals;
+            a.tab_cap = cap;
+            a.claims = claims;
             a.claim_limit = cap / 2;
-            a.P_slot = P_slot;
-            ck(ctx, launch_phrases(a, ctx->st), "k_phrases");
-            ctx->launches++;
+            a.epoch = ++ctx->epoch;
+            a.ctr_base = ctx->ctr_val;
+            ctx->ctr_val += tiles;
+            // T^i in, one phrase slot per phrase out (phrases estimated as n/3);
+            // one table sector per phrase when the table does not fit in L2
+            const double tab_bytes = cap * (double)(key_bytes() + sizeof(u64));
+            const double tbytes = tab_bytes > kL2Bytes ? 32.0 * (double)n / 3.0 : 0.0;
+            h = kt_begin(ctx, "k_parse", (symb == 1 ? 1.0 : 8.0) * n + 4.0 * (double)n / 3.0 + tbytes);
+            ck(ctx, launch_parse(a, ctx->st), "k_parse");
+            kt_end(ctx, h);
+            h = kt_begin(ctx, "k_strings", 40.0 * kk);
+            ck(ctx, launch_strings(a, ctx->st), "k_strings");
+            kt_end(ctx, h);
+            ctx->launches += 2;
+            ck(ctx, cudaMemcpyAsync(&rc, ctx->rc, sizeof(rc), cudaMemcpyDeviceToHost, ctx->st), "read counts");
             st = read_status(ctx);
             check_device_status(ctx, st);
             if (!st.overflow) break;
-            dfree(ctx, tab);
+            dfree(ctx, tkeys);
+            dfree(ctx, tvals);
+            dfree(ctx, claims);
             cap *= 4;
             retries++;
         }
+        const u64 P = rc.phrases;
+        rs.phrases = P;
+        p_ratio = n ? (double)P / (double)n : 0.35;
         rs.table_cap = cap;
         rs.retries = retries;
         const u64 g_new = st.claims, G_new = st.claim_len;
@@ -415,44 +508,93 @@ void build_into(lcg_ctx* ctx, lcg_grammar* R, const uint8_t* data, const uint64_
         grow_level(ctx, L, L.g + g_new, L.G + G_new);
         if (against_resident) {
             ensure_resident(ctx, R, i, L.g + g_new);
-            a.rtab_w = L.rtab;
-            a.rmask_w = L.rcap - 1;
+            a.rtab_w_keys = L.rkeys;
+            a.rtab_w_vals = L.rvals;
+            a.rtab_w_cap = L.rcap;
         } else {
             L.rvalid = false;
         }
-        const u64 ntiles = name_tiles_for(P);
-        ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, ntiles, lb2_bytes(ntiles));
-        a.lb2 = ctx->lb2;
+        // first-occurrence naming of the new phrases
+        const u64 nw = tiles * parse_tile_positions(symb) / 32;  // order keys tile * TP + q
+        u32* first_bits = dalloc<u32>(ctx, nw);
+        u32* first_prefix = dalloc<u32>(ctx, nw);
+        u32* slot_r = dalloc<u32>(ctx, g_new);
+        u32* len_r = dalloc<u32>(ctx, g_new);
+        u64* xlen = dalloc<u64>(ctx, g_new);
         a.P = P;
+        a.first_bits = first_bits;
+        a.first_prefix = first_prefix;
+        a.slot_r = slot_r;
+        a.len_r = len_r;
+        a.xlen = xlen;
         a.g_base = L.g;
         a.G_base = L.G;
+        a.G_new = G_new;
         a.rhs = L.rhs;
         a.rhs_off = L.rhs_off;
         a.F = L.F;
-        a.totals = ctx->scratch + 1;
-        a.epoch = ++ctx->epoch;
-        a.ctr_base = ctx->ctr_val;
-        ctx->ctr_val += ntiles;
-        ck(ctx, launch_name(a, ctx->st), "k_name");
         a.Tnext = Tnext;
+        a.Fnext = Fnext;
         a.c_level = R->c_level;
         a.c_rank = R->c_rank;
+        if (g_new > 0) {
+            ck(ctx, cudaMemsetAsync(first_bits, 0, nw * sizeof(u32), ctx->st), "memset bits");
+            h = kt_begin(ctx, "k_mark", 12.0 * g_new);
+            ck(ctx, launch_mark(a, g_new, ctx->st), "k_mark");
+            kt_end(ctx, h);
+            const u64 ptiles = popscan_tiles_for(nw);
+            ensure_lb(ctx, &ctx->lb1, &ctx->lb1_tiles, ptiles, lb1_bytes(ptiles));
+            a.lb1 = ctx->lb1;
+            a.epoch = ++ctx->epoch;
+            a.ctr_base = ctx->ctr_val;
+            ctx->ctr_val += ptiles;
+            h = kt_begin(ctx, "k_popscan", 8.0 * nw);
+            ck(ctx, launch_popscan(a, nw, ctx->st), "k_popscan");
+            kt_end(ctx, h);
+            h = kt_begin(ctx, "k_rank", 24.0 * g_new);
+            ck(ctx, launch_rank(a, g_new, ctx->st), "k_rank");
+            kt_end(ctx, h);
+            const u64 stiles = std::max<u64>(1, scan2_tiles_for(g_new));
+            ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, stiles, scan2_lb_bytes(stiles));
+            u64 grid = 0;
+            h = kt_begin(ctx, "k_scan2", 12.0 * g_new);
+            ck(ctx, launch_scan2(len_r, nullptr, g_new, xlen, nullptr, ctx->scratch + 1, ctx->lb2, ++ctx->epoch,
+                                 ctx->ctr, ctx->ctr_val, ctx->ds, ctx->st, &grid),
+               "scan");
+            kt_end(ctx, h);
+            ctx->ctr_val += grid;
+            h = kt_begin(ctx, "k_rules", 4.0 * G_new + 12.0 * g_new);
+            ck(ctx, launch_rules(a, g_new, ctx->st), "k_rules");
+            kt_end(ctx, h);
+            ctx->launches += 5;
+        }
+        h = kt_begin(ctx, "k_rewrite", 4.0 * P + 8.0 * rc.n_next);
         ck(ctx, launch_rewrite(a, ctx->st), "k_rewrite");
-        ctx->launches += 2;
+        kt_end(ctx, h);
+        ctx->launches += 1;
         L.g += g_new;
         L.G += G_new;
 
-        dfree(ctx, bitmap);
-        dfree(ctx, tile_base);
+        dfree(ctx, first_bits);
+        dfree(ctx, first_prefix);
+        dfree(ctx, slot_r);
+        dfree(ctx, len_r);
+        dfree(ctx, xlen);
+        dfree(ctx, tkeys);
+        dfree(ctx, tvals);
+        dfree(ctx, claims);
+        dfree(ctx, string_first);
+        dfree(ctx, tile_str);
         dfree(ctx, P_slot);
-        dfree(ctx, tab);
         dfree(ctx, R_phr);
         dfree(ctx, R_sid);
         dfree(ctx, d_soff);
         dfree(ctx, d_sid);
         if (S_owned) dfree(ctx, S_owned);
+        if (Sf) dfree(ctx, (void*)Sf);
         S = Tnext;
         S_owned = Tnext;
+        Sf = Fnext;
         symb = 4;
         n = rc.n_next;
         kk = (u32)rc.k_next;
@@ -464,6 +606,7 @@ void build_into(lcg_ctx* ctx, lcg_grammar* R, const uint8_t* data, const uint64_
     dfree(ctx, d_soff);
     dfree(ctx, d_sid);
     if (S_owned) dfree(ctx, S_owned);
+    if (Sf) dfree(ctx, (void*)Sf);
     for (void* p : owned) dfree(ctx, p);
     ctx->stats.kernel_launches = ctx->launches - launches0;
 }
@@ -501,8 +644,8 @@ void merge(lcg_ctx* ctx, lcg_grammar* A, const lcg_grammar* B) {
         u32* mlen = dalloc<u32>(ctx, gb);
         u64* xrank = dalloc<u64>(ctx, gb);
         u64* xlen = dalloc<u64>(ctx, gb);
-        ck(ctx, launch_merge_lookup(brhs, LB.rhs_off, LB.F, gb, fprev_of(A, i), level_hash(ctx, i), LA.rtab,
-                                    LA.rcap - 1, LA.rhs, LA.rhs_off, LA.F, M, miss, mlen, ctx->ds, ctx->st),
+        ck(ctx, launch_merge_lookup(brhs, LB.rhs_off, LB.F, gb, i == 1, fprev_of(A, i), level_hash(ctx, i), LA.rkeys,
+                                    LA.rvals, LA.rcap, LA.rhs, LA.rhs_off, LA.F, M, miss, mlen, ctx->ds, ctx->st),
            "merge lookup");
         u64 grid = 0;
         const u64 stiles = std::max<u64>(1, scan2_tiles_for(gb));
@@ -525,8 +668,8 @@ void merge(lcg_ctx* ctx, lcg_grammar* A, const lcg_grammar* B) {
         LA.g = ga + tot[0];
         LA.G = Ga + tot[1];
         // the appended rules join the table of the level
-        ck(ctx, launch_resident_build(LA.rhs, LA.rhs_off, ga, tot[0], fprev_of(A, i), level_hash(ctx, i), LA.rtab,
-                                      LA.rcap - 1, ctx->ds, ctx->st),
+        ck(ctx, launch_resident_build(LA.rhs, LA.rhs_off, ga, tot[0], i == 1, fprev_of(A, i), level_hash(ctx, i),
+                                      LA.rkeys, LA.rvals, LA.rcap, ctx->ds, ctx->st),
            "table insert");
         ck(ctx, launch_remap_c(B->c_level, cb_rank, kb, i, M, ctx->st), "remap C");
         ctx->launches += 2;
@@ -681,6 +824,11 @@ void lcg_ctx_destroy(lcg_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->st) cudaStreamSynchronize(ctx->st);
+    for (auto& r : ctx->krecs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : ctx->evpool) cudaEventDestroy(e);
     if (ctx->lb1) cudaFree(ctx->lb1);
     if (ctx->lb2) cudaFree(ctx->lb2);
     cudaFree(ctx->ds);
@@ -699,6 +847,19 @@ int lcg_last_build_stats(const lcg_ctx* ctx, lcg_build_stats* out) {
     return LCG_OK;
 }
 
+int lcg_set_kernel_timing(lcg_ctx* ctx, int enable) {
+    if (!ctx) return LCG_EINVAL;
+    ctx->ktime = enable != 0;
+    return LCG_OK;
+}
+
+int lcg_last_kernel_times(const lcg_ctx* ctx, lcg_kernel_time* out, uint32_t cap, uint32_t* count) {
+    if (!ctx || !count) return LCG_EINVAL;
+    *count = (uint32_t)ctx->ktimes.size();
+    for (uint32_t x = 0; x < cap && x < ctx->ktimes.size(); x++) out[x] = ctx->ktimes[x];
+    return LCG_OK;
+}
+
 int lcg_build(lcg_ctx* ctx, const uint8_t* data, const uint64_t* offsets, uint32_t k, int data_on_device,
               lcg_grammar** out) {
     if (!ctx || !out) return LCG_EINVAL;
@@ -706,9 +867,11 @@ int lcg_build(lcg_ctx* ctx, const uint8_t* data, const uint64_t* offsets, uint32
     lcg_grammar* G = nullptr;
     LCG_GUARD_BEGIN
     ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    kt_reset(ctx);
     G = new_grammar(ctx);
     build_into(ctx, G, data, offsets, k, data_on_device, false);
     sync(ctx);
+    kt_collect(ctx);
     *out = G;
     return LCG_OK;
     }
@@ -734,8 +897,10 @@ int lcg_build_into(lcg_ctx* ctx, lcg_grammar* resident, const uint8_t* data, con
     }
     LCG_GUARD_BEGIN
     ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    kt_reset(ctx);
     build_into(ctx, resident, data, offsets, k, data_on_device, true);
     sync(ctx);
+    kt_collect(ctx);
     return LCG_OK;
     LCG_GUARD_END
 }
@@ -744,7 +909,9 @@ int lcg_merge(lcg_ctx* ctx, lcg_grammar* a, const lcg_grammar* b) {
     if (!ctx || !a || !b) return LCG_EINVAL;
     LCG_GUARD_BEGIN
     ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    kt_reset(ctx);
     merge(ctx, a, b);
+    kt_collect(ctx);
     return LCG_OK;
     LCG_GUARD_END
 }

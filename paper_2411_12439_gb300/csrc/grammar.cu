@@ -2,6 +2,7 @@
 // expansion exp(C[j]) (Sec. 2.2), and a generic two-column exclusive scan.
 #include "lcg_dev.cuh"
 #include "lcg_internal.h"
+#include "table.cuh"
 
 namespace lcg {
 
@@ -77,37 +78,32 @@ __global__ void k_remap(const u32* __restrict__ in, u64 n, const u32* __restrict
 
 // For every rule of G_b (right-hand side already over G_a's ranks): its rank
 // in G_a when G_a has the same right-hand side (looked up in G_a's table of
-// the level, confirmed by comparing contents), else a miss.
+// the level, hashed keys confirmed by comparing contents), else a miss.
+template <bool kByte>
 __global__ void k_merge_lookup(const u32* __restrict__ brhs, const u64* __restrict__ brhs_off,
                                const u32* __restrict__ bF, u64 gb, const u32* __restrict__ aFprev, LevelHash lh,
-                               const Slot* __restrict__ atab, u64 amask, const u32* __restrict__ arhs,
-                               const u64* __restrict__ arhs_off, const u32* __restrict__ aF, u32* __restrict__ M,
-                               u32* __restrict__ miss, u32* __restrict__ mlen, DevStatus* ds) {
+                               ContentTable at, const u32* __restrict__ arhs, const u64* __restrict__ arhs_off,
+                               const u32* __restrict__ aF, u32* __restrict__ M, u32* __restrict__ miss,
+                               u32* __restrict__ mlen, DevStatus* ds) {
     for (u64 r = blockIdx.x * (u64)blockDim.x + threadIdx.x; r < gb; r += (u64)gridDim.x * blockDim.x) {
         const u64 s = brhs_off[r], e = brhs_off[r + 1], len = e - s;
         u64 H = 0;
         for (u64 x = e; x-- > s;) H = addmod61(mulmod61(H, lh.c), (u64)__ldg(aFprev + brhs[x]));
-        const u64 key = make_key(H, len);
-        u32 found = ~0u;
-        if (atab != nullptr) {
-            u64 sl = key_home(key) & amask;
-            for (u64 probe = 0; probe <= amask; probe++) {
-                const u64 kk = atab[sl].key;
-                if (kk == kEmpty) break;
-                if (kk == key) {
-                    const u64 ra = atab[sl].ref, o = arhs_off[ra];
-                    if (arhs_off[ra + 1] - o == len) {
-                        bool eq = true;
-                        for (u64 x = 0; x < len && eq; x++) eq = (arhs[o + x] == brhs[s + x]);
-                        if (eq) { found = (u32)ra; break; }
-                    }
-                }
-                sl = (sl + 1) & amask;
-            }
+        const bool hashed = len > inline_max(kByte);
+        const Key128 key = hashed ? key_hashed(H, len, 0) : key_inline([&](u64 j) { return brhs[s + j]; }, len, kByte);
+        u64 found = ~0ull;
+        if (at.cap) {
+            found = table_find(at, key, hashed, [&](u64 ra) {
+                const u64 o = arhs_off[ra];
+                if (arhs_off[ra + 1] - o != len) return false;
+                for (u64 x = 0; x < len; x++)
+                    if (arhs[o + x] != brhs[s + x]) return false;
+                return true;
+            });
         }
-        if (found != ~0u) {
+        if (found != ~0ull) {
             if (aF[found] != bF[r]) set_error(ds, kErrMismatch);
-            M[r] = found;
+            M[r] = (u32)found;
             miss[r] = 0;
             mlen[r] = 0;
         } else {
@@ -166,12 +162,18 @@ cudaError_t launch_remap(const u32* in, u64 n, const u32* M, u32* out, cudaStrea
     return cudaGetLastError();
 }
 
-cudaError_t launch_merge_lookup(const u32* brhs, const u64* brhs_off, const u32* bF, u64 gb, const u32* aFprev,
-                                LevelHash lh, const void* atab, u64 amask, const u32* arhs, const u64* arhs_off,
-                                const u32* aF, u32* M, u32* miss, u32* mlen, DevStatus* ds, cudaStream_t st) {
+cudaError_t launch_merge_lookup(const u32* brhs, const u64* brhs_off, const u32* bF, u64 gb, bool bytes,
+                                const u32* aFprev, LevelHash lh, void* akeys, u64* avals, u64 acap, const u32* arhs,
+                                const u64* arhs_off, const u32* aF, u32* M, u32* miss, u32* mlen, DevStatus* ds,
+                                cudaStream_t st) {
     if (gb == 0) return cudaSuccess;
-    k_merge_lookup<<<grid_for(gb), 256, 0, st>>>(brhs, brhs_off, bF, gb, aFprev, lh, (const Slot*)atab, amask,
-                                                 arhs, arhs_off, aF, M, miss, mlen, ds);
+    const ContentTable at{(Key128*)akeys, avals, acap};
+    if (bytes)
+        k_merge_lookup<true><<<grid_for(gb), 256, 0, st>>>(brhs, brhs_off, bF, gb, aFprev, lh, at, arhs, arhs_off, aF,
+                                                           M, miss, mlen, ds);
+    else
+        k_merge_lookup<false><<<grid_for(gb), 256, 0, st>>>(brhs, brhs_off, bF, gb, aFprev, lh, at, arhs, arhs_off,
+                                                            aF, M, miss, mlen, ds);
     return cudaGetLastError();
 }
 

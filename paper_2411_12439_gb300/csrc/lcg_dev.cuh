@@ -158,12 +158,27 @@ struct LBSlot {
     u64 incl[NV];
 };
 
-// Block-wide: every thread passes the tile's aggregate in `agg` (only thread 0's
-// value is used) and receives the exclusive prefix in `excl`.  Needs
-// blockDim.x >= 32.  On a timeout the error is set and the prefix is 0.
+// Publish a tile's aggregate (thread 0).  Tile 0 publishes its inclusive
+// prefix at once.
 template <int NV>
-__device__ void block_lookback(LBSlot<NV>* st, u64 tile, u64 epoch, const u64 (&agg)[NV], u64 (&excl)[NV],
-                               DevStatus* ds) {
+__device__ __forceinline__ void lookback_publish(LBSlot<NV>* st, u64 tile, u64 epoch, const u64 (&agg)[NV]) {
+    volatile LBSlot<NV>* vs = st;
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        vs[tile].agg[v] = agg[v];
+        if (tile == 0) vs[0].incl[v] = agg[v];
+    }
+    __threadfence();
+    vs[tile].flag = (epoch << 2) | (tile == 0 ? 2 : 1);
+}
+
+// Block-wide, after lookback_publish: wait for the predecessors, publish the
+// tile's inclusive prefix and return the exclusive one in `excl` (every
+// thread).  Needs blockDim.x >= 32.  On a timeout the error is set and the
+// prefix is 0.
+template <int NV>
+__device__ void lookback_finish(LBSlot<NV>* st, u64 tile, u64 epoch, const u64 (&agg)[NV], u64 (&excl)[NV],
+                                DevStatus* ds) {
     __shared__ u64 s_excl[NV];
     if (threadIdx.x < 32) {
         const u32 lane = threadIdx.x;
@@ -171,44 +186,34 @@ __device__ void block_lookback(LBSlot<NV>* st, u64 tile, u64 epoch, const u64 (&
         u64 acc[NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) acc[v] = 0;
-        if (tile == 0) {
-            if (lane == 0) {
-#pragma unroll
-                for (int v = 0; v < NV; v++) { vs[0].agg[v] = agg[v]; vs[0].incl[v] = agg[v]; }
-                __threadfence();
-                vs[0].flag = (epoch << 2) | 2;
-            }
-        } else {
-            if (lane == 0) {
-#pragma unroll
-                for (int v = 0; v < NV; v++) vs[tile].agg[v] = agg[v];
-                __threadfence();
-                vs[tile].flag = (epoch << 2) | 1;
-            }
+        if (tile != 0) {
             long long base = (long long)tile - 1;
             bool failed = false;
             while (true) {
-                long long idx = base - (long long)lane;
+                const long long idx = base - (long long)lane;
                 u32 state = 2;  // virtual tiles before 0: inclusive, value 0
                 if (idx >= 0) {
                     u64 it = 0;
+                    u32 backoff = 32;
                     while (true) {
-                        u64 f = vs[idx].flag;
+                        const u64 f = vs[idx].flag;
                         if ((f >> 2) == epoch && (f & 3) != 0) { state = (u32)(f & 3); break; }
                         if (++it > kSpinLimit || vload(&ds->error) != 0) { state = 0; break; }
+                        // back off so that waiting warps leave issue slots to working ones
+                        __nanosleep(backoff);
+                        if (backoff < 1024) backoff <<= 1;
                     }
                 }
                 if (__any_sync(0xffffffffu, state == 0)) { failed = true; break; }
-                u32 incl_mask = __ballot_sync(0xffffffffu, state == 2);
+                const u32 incl_mask = __ballot_sync(0xffffffffu, state == 2);
                 __threadfence();
-                int first = incl_mask ? __ffs(incl_mask) - 1 : 31;
-                u64 val[NV];
+                const int first = incl_mask ? __ffs(incl_mask) - 1 : 31;
 #pragma unroll
                 for (int v = 0; v < NV; v++) {
-                    val[v] = 0;
-                    if (idx >= 0 && (int)lane <= first) val[v] = (state == 2) ? vs[idx].incl[v] : vs[idx].agg[v];
-                    for (int o = 16; o > 0; o >>= 1) val[v] += __shfl_down_sync(0xffffffffu, val[v], o);
-                    acc[v] += val[v];
+                    u64 val = 0;
+                    if (idx >= 0 && (int)lane <= first) val = (state == 2) ? vs[idx].incl[v] : vs[idx].agg[v];
+                    for (int o = 16; o > 0; o >>= 1) val += __shfl_down_sync(0xffffffffu, val, o);
+                    acc[v] += val;
                 }
                 if (incl_mask) break;
                 base -= 32;
@@ -234,6 +239,15 @@ __device__ void block_lookback(LBSlot<NV>* st, u64 tile, u64 epoch, const u64 (&
 #pragma unroll
     for (int v = 0; v < NV; v++) excl[v] = s_excl[v];
     __syncthreads();
+}
+
+// Both steps at once: every thread passes the tile's aggregate in `agg` (only
+// thread 0's value is used) and receives the exclusive prefix in `excl`.
+template <int NV>
+__device__ void block_lookback(LBSlot<NV>* st, u64 tile, u64 epoch, const u64 (&agg)[NV], u64 (&excl)[NV],
+                               DevStatus* ds) {
+    if (threadIdx.x == 0) lookback_publish<NV>(st, tile, epoch, agg);
+    lookback_finish<NV>(st, tile, epoch, agg, excl, ds);
 }
 
 // Tile index in launch order from a counter that is never reset: the host

@@ -21,6 +21,7 @@ struct RoundCounts {
 struct RoundArgs {
     int sym_bytes;        // 1 in round 1 (bytes), 4 afterwards (ranks)
     const void* S;        // T^i
+    const u32* Sf;        // fingerprints of T^i (rounds >= 2)
     u64 n;                // |T^i|
     const u64* soff;      // k+1 string offsets into T^i
     const u32* sid;       // original string index of each active string
@@ -28,70 +29,83 @@ struct RoundArgs {
     const u32* Fprev;     // F^{i-1}
     LevelHash lh;         // parameters of h^i
     u32 level;            // i
-    // break pass
-    u32* bitmap;
-    u64* tile_base;
-    void* lb1;
-    void* lb2;
+    // parse pass
+    u32* tile_str;        // per parse tile: the string holding its first position
+    u64* string_first;    // phrase index of each active string's first phrase
+    void* lb1;            // look-back slots
     u64 epoch;
     u64* ctr;
     u64 ctr_base;
     u64* total;           // device: phrases of the round
     DevStatus* ds;
+    void* tab_keys;       // the round's phrase table
+    u64* tab_vals;
+    u64 tab_cap;
+    u64 claim_limit;
+    u32* claims;          // slots claimed in this round (tab_cap entries)
+    void* rtab_keys;      // table of the resident level i (read), or cap 0
+    u64* rtab_vals;
+    u64 rtab_cap;
+    const u32* rrhs;
+    const u64* rrhs_off;
+    u32* P_slot;          // per phrase: slot, or a resident rank with the top bit set
+    u64 P_cap;            // entries of P_slot
     // strings pass
     u64* soff_next;
     u32* sid_next;
     u64* R_phr;
     u32* R_sid;
     RoundCounts* rc;
-    // phrase pass
-    void* tab;
-    u64 mask;
-    u64 claim_limit;
-    const void* rtab;     // resident table of level i (read), or null
-    u64 rmask;
-    const u32* rrhs;
-    const u64* rrhs_off;
-    u32* P_slot;
     // naming pass
     u64 P;                // phrases (host copy)
+    u32* first_bits;      // bitmap over phrase indices
+    u32* first_prefix;    // exclusive popcount prefix of its words
+    u32* slot_r;          // slot of the rank-r new rule
+    u32* len_r;           // its length
+    u64* xlen;            // exclusive prefix of len_r
     u64 g_base, G_base;   // rules / rhs symbols of level i before this round
+    u64 G_new;            // rhs symbols of the new rules
     u32* rhs;
     u64* rhs_off;
     u32* F;
-    u64* totals;
-    void* rtab_w;         // resident table of level i to extend, or null
-    u64 rmask_w;
+    void* rtab_w_keys;    // table of level i to extend with the new rules, or cap 0
+    u64* rtab_w_vals;
+    u64 rtab_w_cap;
     // rewrite pass
     u32* Tnext;
+    u32* Fnext;           // fingerprints of T^{i+1}
     u32* c_level;
     u32* c_rank;
 };
 
-u64 tiles_for(u64 n);
-u64 name_tiles_for(u64 P);
+u64 parse_tile_positions(int sym_bytes);
+u64 popscan_tiles_for(u64 nw);
 size_t lb1_bytes(u64 tiles);
 size_t lb2_bytes(u64 tiles);
-size_t slot_bytes();
+size_t key_bytes();
 
-cudaError_t launch_breaks(const RoundArgs& a, cudaStream_t st);
+cudaError_t launch_tile_strings(const RoundArgs& a, cudaStream_t st);
+cudaError_t launch_parse(const RoundArgs& a, cudaStream_t st);
 cudaError_t launch_strings(const RoundArgs& a, cudaStream_t st);
-cudaError_t launch_phrases(const RoundArgs& a, cudaStream_t st);
-cudaError_t launch_name(const RoundArgs& a, cudaStream_t st);
+cudaError_t launch_mark(const RoundArgs& a, u64 g_new, cudaStream_t st);
+cudaError_t launch_popscan(const RoundArgs& a, u64 nw, cudaStream_t st);
+cudaError_t launch_rank(const RoundArgs& a, u64 g_new, cudaStream_t st);
+cudaError_t launch_rules(const RoundArgs& a, u64 g_new, cudaStream_t st);
 cudaError_t launch_rewrite(const RoundArgs& a, cudaStream_t st);
 cudaError_t launch_level0(const unsigned char* data, const u64* pos, const u32* ids, u32 cnt, u32* c_level,
                           u32* c_rank, cudaStream_t st);
-cudaError_t launch_resident_build(const u32* rhs, const u64* rhs_off, u64 r0, u64 cnt, const u32* Fprev,
-                                  LevelHash lh, void* rtab, u64 rmask, DevStatus* ds, cudaStream_t st);
+cudaError_t launch_resident_build(const u32* rhs, const u64* rhs_off, u64 r0, u64 cnt, bool bytes, const u32* Fprev,
+                                  LevelHash lh, void* keys, u64* vals, u64 cap, DevStatus* ds, cudaStream_t st);
 cudaError_t launch_h0(LevelHash h0, u32* F0, cudaStream_t st);
 cudaError_t launch_gather_strings(const unsigned char* data, const u64* src_off, const u64* dst_off, u32 k,
                                   unsigned char* out, cudaStream_t st);
 
 // grammar.cu
 cudaError_t launch_remap(const u32* in, u64 n, const u32* M, u32* out, cudaStream_t st);
-cudaError_t launch_merge_lookup(const u32* brhs, const u64* brhs_off, const u32* bF, u64 gb, const u32* aFprev,
-                                LevelHash lh, const void* atab, u64 amask, const u32* arhs, const u64* arhs_off,
-                                const u32* aF, u32* M, u32* miss, u32* mlen, DevStatus* ds, cudaStream_t st);
+cudaError_t launch_merge_lookup(const u32* brhs, const u64* brhs_off, const u32* bF, u64 gb, bool bytes,
+                                const u32* aFprev, LevelHash lh, void* akeys, u64* avals, u64 acap, const u32* arhs,
+                                const u64* arhs_off, const u32* aF, u32* M, u32* miss, u32* mlen, DevStatus* ds,
+                                cudaStream_t st);
 cudaError_t launch_merge_append(const u32* brhs, const u64* brhs_off, const u32* bF, u64 gb, const u32* miss,
                                 const u64* xrank, const u64* xlen, u64 ga, u64 Ga, u32* arhs, u64* arhs_off,
                                 u32* aF, u32* M, u64 ga_new, u64 Ga_new, cudaStream_t st);

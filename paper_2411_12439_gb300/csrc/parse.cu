@@ -4,25 +4,24 @@
 // A round i reads the sequence T^i (bytes in round 1, uint32 ranks later) of
 // the active strings, laid out back to back with offsets soff[0..k], and the
 // fingerprints F^{i-1} of its symbols.  It runs:
-//   k_breaks   symbol fingerprints + RandLMSPar break bits (Eq. rand_types),
-//              one bit per position, and the phrase count of every tile
-//              (decoupled look-back prefix sums)
-//   k_strings  per-string phrase ranges; strings that become one phrase retire
-//   k_phrases  per phrase: polynomial fingerprint h^i (Eq. fast_hash) and
-//              insertion into the phrase table with content comparison
-//   k_name     first-occurrence flags -> ranks (single-pass scan); writes the
-//              level-i rules (rhs, rhs_off) and F^i
+//   k_parse    per tile: symbol fingerprints, RandLMSPar break bits
+//              (Eq. rand_types), the tile's phrase count through a decoupled
+//              look-back, and per phrase the polynomial fingerprint of
+//              Eq. fast_hash and its entry in the round's phrase table (the
+//              slot holds the smallest phrase index of the content)
+//   k_strings  per-string phrase ranges; strings that became one phrase retire
+//   k_mark, k_popscan, k_rank
+//              first-occurrence naming: the first occurrences of the new
+//              phrases are marked in a bitmap over phrase indices, and a
+//              phrase's rank is the number of marks before its own
+//   k_rules    the level-i rules in rank order: rhs, rhs_off and F^i
 //   k_rewrite  T^{i+1}[p] = rank of phrase p, compacting retired strings
 #include "lcg_dev.cuh"
 #include "lcg_internal.h"
+#include "table.cuh"
 
 namespace lcg {
 
-constexpr int kTilePos = 8192;            // positions per break/phrase tile
-constexpr int kTileWords = kTilePos / 32; // one bitmap word per thread
-constexpr int kNameThreads = 256;
-constexpr int kNameItems = 4;
-constexpr int kNameTile = kNameThreads * kNameItems;
 constexpr u64 kNone = 1ull << 32;          // "no different fingerprint to the right"
 constexpr u32 kResidentBit = 0x80000000u;  // P_slot entry names a resident rank
 
@@ -44,386 +43,509 @@ struct FpSource<u32> {
 __device__ __forceinline__ u32 string_of(const u64* soff, u32 k, u64 pos) {
     u32 lo = 0, hi = k;  // answer in [lo, hi)
     while (hi - lo > 1) {
-        u32 mid = (lo + hi) >> 1;
+        const u32 mid = (lo + hi) >> 1;
         if (__ldg(soff + mid) <= pos) lo = mid; else hi = mid;
     }
     return lo;
 }
 
 // --------------------------------------------------------------------------
-// k_breaks
+// k_parse
 // --------------------------------------------------------------------------
+//
+// The tile's symbols (and kHalo more, and one to the left) are staged in shared
+// memory.  Break bits come from warp ballots, one 32-position word per warp
+// step.  The tile's phrase count goes through the decoupled look-back, giving
+// the global index of its first phrase.  Every phrase that starts in the tile
+// is then fingerprinted (Horner over the staged fingerprints) and looked up:
+// first in the resident level (when parsing against a resident grammar), then
+// in the round's table.  In byte rounds the phrases of a tile are first
+// deduplicated in a shared table keyed by their packed bytes, so that one
+// occurrence per tile and content goes to the global table.  New entries
+// (claims) are listed in shared memory and appended to the round's claim list
+// once per block.
+
+constexpr int kParseThreads = 256;
+constexpr int kTP = 2048;          // positions per parse tile
+constexpr int kHalo = 64;          // positions staged past the tile end
+constexpr int kSP = kTP + kHalo;   // staged positions
+constexpr int kLocalSlots = 1024;
+constexpr unsigned short kNoLocal = 0xFFFF;
+constexpr int kClaimBuf = 1024;
 
 template <typename T>
 __device__ u64 scan_right_diff(const T* S, FpSource<T> fp, u64 from, u64 strend, u32 val) {
     for (u64 y = from; y < strend; y++) {
-        u32 fy = fp(S[y]);
+        const u32 fy = fp(S[y]);
         if (fy != val) return fy;
     }
     return kNone;
 }
 
+// First phrase start at or after `from` (or n), evaluated from global memory.
 template <typename T>
-__global__ void __launch_bounds__(kTileWords) k_breaks(const T* __restrict__ S, u64 n, const u64* __restrict__ soff,
-                                                       u32 k, const u32* __restrict__ Fprev,
-                                                       u32* __restrict__ bitmap, u64* __restrict__ tile_base,
-                                                       LBSlot<1>* lb, u64 epoch, u64* ctr, u64 ctr_base,
-                                                       u64* total_out, DevStatus* ds) {
-    __shared__ u32 sF[256];
-    FpSource<T> fp;
-    if constexpr (sizeof(T) == 1) {
-        for (int x = threadIdx.x; x < 256; x += blockDim.x) sF[x] = Fprev[x];
-        __syncthreads();
-        fp.F = sF;
-    } else {
-        fp.F = Fprev;
-    }
-    const u64 tile = dynamic_tile(ctr, ctr_base);
-    const u64 w = tile * kTileWords + threadIdx.x;
-    const u64 base = w * 32;
-    u32 word = 0;
-    if (base < n) {
-        const int cnt = (int)min((u64)32, n - base);
-        u32 v[32];
-#pragma unroll
-        for (int b = 0; b < 32; b++) v[b] = (b < cnt) ? fp(S[base + b]) : 0u;
-        const u32 prev = base > 0 ? fp(S[base - 1]) : 0u;
-        const u64 nextpos = base + cnt;  // first position after this word
-        const u32 nextv = nextpos < n ? fp(S[nextpos]) : 0u;
-        // string starts among positions base .. base+32
-        u32 j = string_of(soff, k, base);
-        unsigned long long starts = 0;  // bit b: base + b starts a string (b <= 32)
-        {
-            u32 jj = j;
-            if (__ldg(soff + jj) == base) starts |= 1ull;
-            while (jj + 1 <= k) {
-                u64 s = __ldg(soff + jj + 1);
-                if (s > base + 32 || s >= n) break;
-                starts |= 1ull << (s - base);
-                jj++;
-            }
+__device__ u64 global_next_break(const T* S, FpSource<T> fp, u64 n, const u64* soff, u32 k, u64 from) {
+    if (from >= n) return n;
+    const u32 j = string_of(soff, k, from);
+    if (__ldg(soff + j) == from) return from;
+    const u64 strend = __ldg(soff + j + 1);
+    u32 fl = fp(S[from - 1]);
+    for (u64 y = from; y < strend; y++) {
+        const u32 fy = fp(S[y]);
+        if (fl > fy) {
+            const u64 nd = scan_right_diff<T>(S, fp, y + 1, strend, fy);
+            if (nd != kNone && nd > (u64)fy) return y;
         }
-        // right to left: nd = first fingerprint right of b that differs from v[b]
-        u64 nd;
-        bool unknown = false;
-        const int last = cnt - 1;
-        if (nextpos >= n || ((starts >> (last + 1)) & 1)) nd = kNone;
-        else if (nextv != v[last]) nd = nextv;
-        else { nd = kNone; unknown = true; }
-        for (int b = last; b >= 0; b--) {
-            bool brk;
-            if ((starts >> b) & 1) {
+        fl = fy;
+    }
+    return strend;
+}
+
+__device__ __forceinline__ u32 local_home(u64 key) { return (u32)(fmix64(key) & (kLocalSlots - 1)); }
+
+// Load n_sym symbols of type V from src (16-byte aligned when `vec`) into the
+// shared array dst, with every 16-byte load issued before any is stored.
+template <typename V>
+__device__ __forceinline__ void stage_vec(V* dst, const V* src, int n_sym, bool vec) {
+    constexpr int PER = 16 / sizeof(V);
+    constexpr int NV = (kSP + PER - 1) / PER;
+    constexpr int IT = (NV + kParseThreads - 1) / kParseThreads;
+    uint4 buf[IT];
+#pragma unroll
+    for (int it = 0; it < IT; it++) {
+        const int x0 = (threadIdx.x + it * kParseThreads) * PER;
+        if (x0 + PER <= n_sym && vec) {
+            buf[it] = *reinterpret_cast<const uint4*>(src + x0);
+        } else if (x0 < n_sym) {
+            V tmp[PER];
+#pragma unroll
+            for (int e = 0; e < PER; e++) tmp[e] = (x0 + e < n_sym) ? src[x0 + e] : (V)0;
+            buf[it] = *reinterpret_cast<const uint4*>(tmp);
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < IT; it++) {
+        const int x0 = (threadIdx.x + it * kParseThreads) * PER;
+        if (x0 < n_sym) *reinterpret_cast<uint4*>(dst + x0) = buf[it];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kParseThreads) k_parse(const RoundArgs a) {
+    constexpr int NWS = kSP / 32;    // staged break words
+    constexpr int NWT = kTP / 32;    // tile break words
+    constexpr bool kByte = sizeof(T) == 1;
+    constexpr bool kLocal = kByte;
+    static_assert(NWT <= kParseThreads, "one tile word per thread");
+
+    __shared__ u32 sF0[kByte ? 256 : 1];
+    __shared__ __align__(16) unsigned char sb[kByte ? kSP : 16];  // bytes of tile positions
+    __shared__ __align__(16) u32 sT[kByte ? 4 : kSP];             // ranks of tile positions
+    __shared__ __align__(16) u32 sf[kByte ? 4 : kSP];             // their fingerprints
+    __shared__ u32 s_left;                                        // fingerprint of position -1
+    __shared__ u32 sbits[NWS];
+    __shared__ u32 sstart[NWS + 1];
+    __shared__ u32 swp[NWT];
+    __shared__ unsigned short sP[kTP];
+    __shared__ u32 sSlot[kTP];
+    __shared__ unsigned short sLi[kLocal ? kTP : 1];
+    __shared__ u64 lkey[kLocal ? kLocalSlots : 1];
+    __shared__ u32 lmin[kLocal ? kLocalSlots : 1];
+    __shared__ u32 lslot[kLocal ? kLocalSlots : 1];
+    __shared__ u32 sClaim[kClaimBuf];
+    __shared__ u64 s_tail_end;
+    __shared__ u32 s_nclaim;
+    __shared__ u64 s_claim_len;
+    __shared__ u64 s_claim_base;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const T* S = (const T*)a.S;
+    const u64 n = a.n;
+    FpSource<T> fp;
+    if constexpr (kByte) {
+        for (int x = tid; x < 256; x += kParseThreads) sF0[x] = a.Fprev[x];
+        fp.F = sF0;
+    } else {
+        fp.F = a.Fprev;
+    }
+    if constexpr (kLocal) {
+        for (int x = tid; x < kLocalSlots; x += kParseThreads) {
+            lkey[x] = kEmpty;
+            lmin[x] = 0xFFFFFFFFu;
+        }
+    }
+    for (int w = tid; w < NWS + 1; w += kParseThreads) {
+        sstart[w] = 0;
+        if (w < NWS) sbits[w] = 0;
+    }
+    if (tid == 0) {
+        s_nclaim = 0;
+        s_claim_len = 0;
+    }
+    const u64 tile = dynamic_tile(a.ctr, a.ctr_base);  // has __syncthreads
+    const u64 t0 = tile * (u64)kTP;
+    const u64 t_end = min(t0 + (u64)kTP, n), s_end = min(t0 + (u64)kSP, n);
+    const int ns = (int)(s_end - t0), nt = (int)(t_end - t0);
+    const u32 j0 = a.tile_str[tile];  // string holding t0
+
+    // 1. stage the tile: bytes in round 1; ranks and their fingerprints
+    //    (written by the previous round's rewrite) afterwards
+    if constexpr (kByte) {
+        stage_vec<unsigned char>(sb, S + t0, ns, (reinterpret_cast<unsigned long long>(S + t0) & 15) == 0);
+        if (tid == 0) s_left = (t0 == 0) ? 0u : sF0[S[t0 - 1]];
+    } else {
+        stage_vec<u32>(sT, S + t0, ns, (reinterpret_cast<unsigned long long>(S + t0) & 15) == 0);
+        stage_vec<u32>(sf, a.Sf + t0, ns, (reinterpret_cast<unsigned long long>(a.Sf + t0) & 15) == 0);
+        if (tid == 0) s_left = (t0 == 0) ? 0u : a.Sf[t0 - 1];
+    }
+    // string starts at positions t0 .. s_end (n itself counts as one)
+    if (warp == 0) {
+        u32 jj = j0 + lane;
+        bool more = true;
+        while (more) {
+            u64 s = (jj <= a.k) ? __ldg(a.soff + jj) : ~0ull;
+            if (s >= t0 && s <= s_end) atomicOr(&sstart[(s - t0) >> 5], 1u << ((s - t0) & 31));
+            more = __shfl_sync(0xffffffffu, (jj <= a.k && s <= s_end) ? 1u : 0u, 31) != 0;
+            jj += 32;
+        }
+    }
+    __syncthreads();
+    auto fat = [&](int x) -> u32 {  // fingerprint of staged position x (x >= -1)
+        if (x < 0) return s_left;
+        if constexpr (kByte) return sF0[sb[x]]; else return sf[x];
+    };
+    auto is_start = [&](int x) -> bool { return (sstart[x >> 5] >> (x & 31)) & 1u; };
+
+    // 2. break bits (Eq. rand_types): a phrase starts at x when x starts a
+    //    string, or f[x-1] > f[x] and the first fingerprint right of x (in the
+    //    string) that differs from f[x] is larger than f[x]
+    for (int w = warp; w < (ns + 31) / 32; w += kParseThreads / 32) {
+        const int x = w * 32 + lane;
+        bool brk = false;
+        if (x < ns) {
+            if (is_start(x)) {
                 brk = true;
             } else {
-                const u32 left = b > 0 ? v[b - 1] : prev;
-                brk = false;
-                if (left > v[b]) {
-                    if (unknown) {
-                        // the run holding b reaches past this word: follow it
-                        u32 jl = string_of(soff, k, base + last);
-                        nd = scan_right_diff<T>(S, fp, nextpos, __ldg(soff + jl + 1), v[b]);
-                        unknown = false;
+                const u32 cur = fat(x);
+                if (fat(x - 1) > cur) {
+                    int y = x + 1;
+                    while (y < ns && !is_start(y) && fat(y) == cur) y++;
+                    u64 nd;
+                    if (y < ns) nd = is_start(y) ? kNone : (u64)fat(y);
+                    else if (s_end == n || is_start(ns)) nd = kNone;
+                    else {
+                        const u32 jl = string_of(a.soff, a.k, t0 + x);
+                        nd = scan_right_diff<T>(S, fp, s_end, __ldg(a.soff + jl + 1), cur);
                     }
-                    brk = (nd != kNone) && (nd > (u64)v[b]);
+                    brk = (nd != kNone) && (nd > (u64)cur);
                 }
             }
-            if (brk) word |= 1u << b;
-            if (b > 0) {
-                if ((starts >> b) & 1) { nd = kNone; unknown = false; }
-                else if (v[b] != v[b - 1]) { nd = v[b]; unknown = false; }
+        }
+        const u32 word = __ballot_sync(0xffffffffu, brk);
+        if (lane == 0) sbits[w] = word;
+    }
+    __syncthreads();
+
+    // 3. phrase starts of the tile, in order; the tile's count is published at
+    //    once so that later tiles' look-backs need not wait for this tile's lookups
+    u32 word = 0;
+    if (tid < NWT) {
+        word = sbits[tid];
+        const int lo = tid * 32;
+        if (lo >= nt) word = 0;
+        else if (nt - lo < 32) word &= (1u << (nt - lo)) - 1u;
+    }
+    u64 cnt;
+    const u64 woff = block_excl_scan((u64)__popc(word), cnt);
+    u64 agg[1] = {cnt};
+    if (tid == 0) lookback_publish<1>((LBSlot<1>*)a.lb1, tile, a.epoch, agg);
+    if (tid < NWT) {
+        swp[tid] = (u32)woff;
+        u32 m = word, o = (u32)woff;
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            sP[o++] = (unsigned short)(tid * 32 + b);
+        }
+    }
+    if (tid == 0) {
+        // end of the tile's last phrase: the first phrase start at or after t_end
+        u64 e = n;
+        bool found = false;
+        for (int x = nt; x < ns; x++) {
+            if ((sbits[x >> 5] >> (x & 31)) & 1u) { e = t0 + x; found = true; break; }
+        }
+        if (!found) e = (s_end == n) ? n : global_next_break<T>(S, fp, n, a.soff, a.k, s_end);
+        s_tail_end = e;
+    }
+    __syncthreads();
+
+    // 4. lookups.  A phrase's order key is tile * kTP + q (monotone in the
+    //    phrase index), so lookups do not need the tile's global phrase index.
+    const u64 tail = s_tail_end - t0;
+    const u32 cntq = (u32)cnt;
+    const u64 okey0 = tile * (u64)kTP;
+    const ContentTable bt{(Key128*)a.tab_keys, a.tab_vals, a.tab_cap};
+    const ContentTable rt{(Key128*)a.rtab_keys, a.rtab_vals, a.rtab_cap};
+    auto phrase_end = [&](u32 q) -> u64 { return (q + 1 < cntq) ? (u64)sP[q + 1] : tail; };
+    auto sym = [&](u64 x) -> u32 {  // symbol at tile offset x
+        if (x < (u64)ns) {
+            if constexpr (kByte) return (u32)sb[x]; else return sT[x];
+        }
+        return (u32)S[t0 + x];
+    };
+    auto lookup = [&](u32 q, u64 st, u64 en) -> u32 {
+        const u64 len = en - st;
+        if (len > kMaxPhraseLen) { set_error(a.ds, kErrPhraseLong); return ~0u; }
+        const bool hashed = len > inline_max(kByte);
+        Key128 key;
+        if (hashed) {
+            // H = sum_j F[Q_j] c^{j-1} mod p, by Horner from the last symbol
+            u64 H = 0;
+            for (u64 x = en; x-- > st;) {
+                const u32 v = (x < (u64)ns) ? fat((int)x) : fp(S[t0 + x]);
+                H = addmod61(mulmod61(H, a.lh.c), (u64)v);
+            }
+            key = key_hashed(H, len, t0 + st);
+        } else {
+            key = key_inline([&](u64 j) { return sym(st + j); }, len, kByte);
+        }
+        if (rt.cap) {
+            const u64 r = table_find(rt, key, hashed, [&](u64 rank) {
+                const u64 o = a.rrhs_off[rank];
+                for (u64 j = 0; j < len; j++)
+                    if ((u32)S[t0 + st + j] != a.rrhs[o + j]) return false;
+                return true;
+            });
+            if (r != ~0ull) return kResidentBit | (u32)r;
+        }
+        bool claimed = false;
+        const u64 slot = table_claim_or_find(bt, key, hashed, okey0 + q, [&](u64 ref) {
+            for (u64 j = 0; j < len; j++)
+                if (S[ref + j] != S[t0 + st + j]) return false;
+            return true;
+        }, &claimed, a.ds);
+        if (claimed) {
+            atomicAdd(&s_claim_len, len);
+            const u32 c = atomicAdd(&s_nclaim, 1u);
+            if (c < (u32)kClaimBuf) {
+                sClaim[c] = (u32)slot;
+            } else {  // buffer full: append directly
+                const u64 g = atomicAdd(&a.ds->claims, 1ull);
+                if (g < bt.cap) a.claims[g] = (u32)slot;
             }
         }
-        bitmap[w] = word;
+        return (u32)slot;
+    };
+
+    if constexpr (kLocal) {
+        // 4a. shared dedup of short phrases by their packed bytes
+        for (u32 q = tid; q < cntq; q += kParseThreads) {
+            const u64 st = sP[q], en = phrase_end(q), len = en - st;
+            unsigned short li = kNoLocal;
+            if (len <= 7 && en <= (u64)ns) {
+                u64 key = len << 56;
+                for (u64 x = 0; x < len; x++) key |= (u64)sb[st + x] << (8 * x);
+                // lanes of a warp with the same phrase insert it once
+                const u32 peers = __match_any_sync(__activemask(), key);
+                const int leader = __ffs(peers) - 1;
+                if (lane == leader) {
+                    u32 h = local_home(key);
+                    for (int probe = 0; probe < 64; probe++) {
+                        u64 cur = lkey[h];
+                        if (cur == kEmpty)
+                            cur = atomicCAS((unsigned long long*)&lkey[h], (unsigned long long)kEmpty,
+                                            (unsigned long long)key);
+                        if (cur == kEmpty || cur == key) {
+                            if (q < lmin[h]) atomicMin(&lmin[h], q);  // the leader has the group's smallest q
+                            li = (unsigned short)h;
+                            break;
+                        }
+                        h = (h + 1) & (kLocalSlots - 1);
+                    }
+                }
+                li = (unsigned short)__shfl_sync(peers, (u32)li, leader);
+            }
+            sLi[q] = li;
+        }
+        __syncthreads();
+        // 4b. one global lookup per distinct phrase of the tile (its first occurrence)
+        for (u32 q = tid; q < cntq; q += kParseThreads) {
+            const unsigned short li = sLi[q];
+            if (li != kNoLocal && lmin[li] != q) continue;
+            const u32 slot = lookup(q, sP[q], phrase_end(q));
+            if (li == kNoLocal) sSlot[q] = slot; else lslot[li] = slot;
+        }
+        __syncthreads();
+        // 4c. every occurrence takes its class's slot
+        for (u32 q = tid; q < cntq; q += kParseThreads) {
+            const unsigned short li = sLi[q];
+            if (li != kNoLocal) sSlot[q] = lslot[li];
+        }
+    } else {
+        for (u32 q = tid; q < cntq; q += kParseThreads) sSlot[q] = lookup(q, sP[q], phrase_end(q));
     }
-    u64 total;
-    (void)block_excl_scan((u64)__popc(word), total);
-    u64 agg[1] = {total}, excl[1];
-    block_lookback<1>(lb, tile, epoch, agg, excl, ds);
-    if (threadIdx.x == 0) {
-        tile_base[tile] = excl[0];
-        if ((tile + 1) * (u64)kTilePos >= n) *total_out = excl[0] + total;
+
+    // 5. the tile's global phrase index; phrase slots and string starts out
+    u64 excl[1];
+    lookback_finish<1>((LBSlot<1>*)a.lb1, tile, a.epoch, agg, excl, a.ds);  // has __syncthreads
+    const u64 pbase = excl[0];
+    if (pbase + cnt > a.P_cap) {  // more phrases than the bound n/2 + 2k allows
+        if (tid == 0) set_error(a.ds, kErrPhraseLong);
+        return;
     }
+    for (u32 q = tid; q < cntq; q += kParseThreads) a.P_slot[pbase + q] = sSlot[q];
+    if (tid == 0 && t_end == n) *a.total = pbase + cnt;
+    if (warp == 0) {
+        for (u32 jj = j0 + lane;; jj += 32) {
+            const u64 s = (jj < a.k) ? __ldg(a.soff + jj) : ~0ull;
+            if (s >= t0 && s < t_end) {
+                const int x = (int)(s - t0);
+                a.string_first[jj] = pbase + swp[x >> 5] + __popc(sbits[x >> 5] & ((1u << (x & 31)) - 1u));
+            }
+            if (__shfl_sync(0xffffffffu, (jj < a.k && s < t_end) ? 1u : 0u, 31) == 0) break;
+        }
+    }
+    // 6. this block's new entries join the round's claim list
+    const u32 nb = min(s_nclaim, (u32)kClaimBuf);
+    if (tid == 0 && s_nclaim) {
+        const u64 base = atomicAdd(&a.ds->claims, (u64)nb);
+        s_claim_base = base;
+        atomicAdd(&a.ds->claim_len, s_claim_len);
+        if (base + nb > a.claim_limit) atomicExch(&a.ds->overflow, 1u);
+    }
+    __syncthreads();
+    if (nb) {
+        const u64 base = s_claim_base;
+        for (u32 x = tid; x < nb; x += kParseThreads)
+            if (base + x < bt.cap) a.claims[base + x] = sClaim[x];
+    }
+}
+
+// Per parse tile: the string that holds its first position.
+__global__ void k_tile_strings(const RoundArgs a, u64 tiles) {
+    for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < tiles; t += (u64)gridDim.x * blockDim.x)
+        a.tile_str[t] = string_of(a.soff, a.k, t * (u64)kTP);
 }
 
 // --------------------------------------------------------------------------
 // k_strings: per-string phrase ranges, retirement, next offsets (one block)
 // --------------------------------------------------------------------------
 
-__device__ u64 phrase_index_at(const u32* bitmap, const u64* tile_base, u64 pos) {
-    u64 tile = pos / kTilePos;
-    u64 w0 = tile * kTileWords, w = pos / 32;
-    u64 idx = tile_base[tile];
-    for (u64 x = w0; x < w; x++) idx += __popc(bitmap[x]);
-    u32 bit = (u32)(pos & 31);
-    idx += __popc(bitmap[w] & ((1u << bit) - 1u));
-    return idx;
-}
-
-__global__ void __launch_bounds__(1024) k_strings(const u64* __restrict__ soff, const u32* __restrict__ sid, u32 k,
-                                                  const u32* __restrict__ bitmap, const u64* __restrict__ tile_base,
-                                                  const u64* __restrict__ total, u64* __restrict__ soff_next,
-                                                  u32* __restrict__ sid_next, u64* __restrict__ R_phr,
-                                                  u32* __restrict__ R_sid, RoundCounts* __restrict__ rc) {
-    const u64 P = *total;
+__global__ void __launch_bounds__(1024) k_strings(const RoundArgs a) {
+    const u64 P = *a.total;
+    const u32 k = a.k;
     u64 carry = 0;
     for (u32 j0 = 0; j0 < k; j0 += blockDim.x) {
-        u32 j = j0 + threadIdx.x;
+        const u32 j = j0 + threadIdx.x;
         u64 first = 0, nextf = 0;
         bool retire = false;
         if (j < k) {
-            first = phrase_index_at(bitmap, tile_base, soff[j]);
-            nextf = (j + 1 < k) ? phrase_index_at(bitmap, tile_base, soff[j + 1]) : P;
+            first = a.string_first[j];
+            nextf = (j + 1 < k) ? a.string_first[j + 1] : P;
             retire = (nextf - first == 1);
         }
         u64 tot;
-        u64 rb = block_excl_scan(retire ? 1ull : 0ull, tot) + carry;
+        const u64 rb = block_excl_scan(retire ? 1ull : 0ull, tot) + carry;
         if (j < k) {
             if (retire) {
-                R_phr[rb] = first;
-                R_sid[rb] = sid[j];
+                a.R_phr[rb] = first;
+                a.R_sid[rb] = a.sid[j];
             } else {
-                soff_next[j - rb] = first - rb;
-                sid_next[j - rb] = sid[j];
+                a.soff_next[j - rb] = first - rb;
+                a.sid_next[j - rb] = a.sid[j];
             }
         }
         carry += tot;
     }
     if (threadIdx.x == 0) {
-        soff_next[k - carry] = P - carry;
-        rc->phrases = P;
-        rc->retired = carry;
-        rc->k_next = k - carry;
-        rc->n_next = P - carry;
+        a.soff_next[k - carry] = P - carry;
+        a.rc->phrases = P;
+        a.rc->retired = carry;
+        a.rc->k_next = k - carry;
+        a.rc->n_next = P - carry;
     }
 }
 
 // --------------------------------------------------------------------------
-// k_phrases: fingerprints of phrases and phrase-table insertion
+// first-occurrence naming over the claimed entries
 // --------------------------------------------------------------------------
 
-// end (exclusive) of the phrase starting at `pos`: next set bit after pos, or n
-__device__ u64 phrase_end(const u32* bitmap, u64 nw, u64 n, u64 pos) {
-    u64 w = pos / 32;
-    u32 bit = (u32)(pos & 31);
-    u32 m = (bit == 31) ? 0u : (bitmap[w] & ~((2u << bit) - 1u));
-    while (m == 0) {
-        if (++w >= nw) return n;
-        m = bitmap[w];
+// Mark the first occurrence of every new phrase in a bitmap over phrase indices.
+__global__ void k_mark(const RoundArgs a, u64 g_new) {
+    for (u64 c = blockIdx.x * (u64)blockDim.x + threadIdx.x; c < g_new; c += (u64)gridDim.x * blockDim.x) {
+        const u64 m = a.tab_vals[a.claims[c]];
+        atomicOr(a.first_bits + (m >> 5), 1u << (m & 31));
     }
-    u64 e = w * 32 + (__ffs(m) - 1);
-    return e < n ? e : n;
 }
 
-template <typename T>
-__device__ bool same_content(const T* S, u64 ra, u64 rb, u64 len) {
-    for (u64 x = 0; x < len; x++)
-        if (S[ra + x] != S[rb + x]) return false;
-    return true;
+constexpr int kPopThreads = 256;
+constexpr int kPopItems = 8;
+constexpr int kPopTile = kPopThreads * kPopItems;
+
+// Exclusive prefix of the popcounts of the bitmap words (single pass).
+__global__ void __launch_bounds__(kPopThreads) k_popscan(const RoundArgs a, u64 nw) {
+    const u64 tile = dynamic_tile(a.ctr, a.ctr_base);
+    const u64 w0 = tile * (u64)kPopTile + (u64)threadIdx.x * kPopItems;
+    u32 c[kPopItems];
+    u64 sum = 0;
+#pragma unroll
+    for (int it = 0; it < kPopItems; it++) {
+        c[it] = (w0 + it < nw) ? (u32)__popc(a.first_bits[w0 + it]) : 0u;
+        sum += c[it];
+    }
+    u64 tot;
+    u64 e = block_excl_scan(sum, tot);
+    u64 agg[1] = {tot}, excl[1];
+    block_lookback<1>((LBSlot<1>*)a.lb1, tile, a.epoch, agg, excl, a.ds);
+    e += excl[0];
+#pragma unroll
+    for (int it = 0; it < kPopItems; it++) {
+        if (w0 + it < nw) a.first_prefix[w0 + it] = (u32)e;
+        e += c[it];
+    }
 }
 
-// Insert the phrase S[pos, pos+len) (phrase index pidx) and return its slot, or
-// ~0u when the pass must stop (table over its load limit, or an error).
-template <typename T>
-__device__ u32 table_insert(Slot* tab, u64 mask, u64 claim_limit, u64 key, u64 pos, u64 len, u32 fpv, u64 pidx,
-                            const T* S, const u32* bitmap, u64 nw, u64 n, DevStatus* ds) {
-    u64 s = key_home(key) & mask;
-    for (u64 probe = 0; probe <= mask; probe++) {
-        Slot* sl = tab + s;
-        u64 kk = ld_relaxed(&sl->key);
-        u64 ref;
-        if (kk == kEmpty) {
-            if (vload(&ds->overflow)) return ~0u;
-            u64 ok, oref;
-            cas128(sl, kEmpty, kEmpty, key, pos, ok, oref);
-            if (ok == kEmpty) {
-                sl->len = (u32)len;
-                sl->fp = fpv;
-                atomicMin(&sl->minp, pidx);
-                u64 c = atomicAdd(&ds->claims, 1ull);
-                atomicAdd(&ds->claim_len, len);
-                if (c + 1 > claim_limit) atomicExch(&ds->overflow, 1u);
-                return (u32)s;
-            }
-            kk = ok;
-            ref = oref;
-        } else {
-            ref = ld_relaxed(&sl->ref);
-            u64 it = 0;
-            while (ref == kEmpty) {  // the pair is written at once; guard only
-                if (++it > kSpinLimit) { set_error(ds, kErrTimeout); return ~0u; }
-                ref = ld_relaxed(&sl->ref);
-            }
-        }
-        if (kk == key) {
-            // saturated length field: check the stored phrase's length first
-            bool ok = (len < kLenSat) || (phrase_end(bitmap, nw, n, ref) - ref == len);
-            if (ok && same_content<T>(S, ref, pos, len)) {
-                if (pidx < ld_relaxed(&sl->minp)) atomicMin(&sl->minp, pidx);
-                return (u32)s;
-            }
-        }
-        s = (s + 1) & mask;
+// Rank of every new phrase: the marks before its first occurrence.
+__global__ void k_rank(const RoundArgs a, u64 g_new) {
+    for (u64 c = blockIdx.x * (u64)blockDim.x + threadIdx.x; c < g_new; c += (u64)gridDim.x * blockDim.x) {
+        const u32 s = a.claims[c];
+        const u64 m = a.tab_vals[s];
+        const u32 w = (u32)(m >> 5);
+        const u64 r = a.first_prefix[w] + __popc(a.first_bits[w] & ((1u << (m & 31)) - 1u));
+        a.tab_vals[s] = a.g_base + r;
+        a.slot_r[r] = s;
+        a.len_r[r] = (u32)key_len(((const Key128*)a.tab_keys)[s]);
     }
-    set_error(ds, kErrTableFull);
-    return ~0u;
 }
 
-// Rank of the phrase S[pos, pos+len) among the rules of a resident level
-// (table rtab over the rules rrhs/rrhs_off), or ~0u when it is not one of them.
+// The new rules of level i in rank order: right-hand side, offsets and F^i
+// (Eq. fast_hash over F^{i-1}).  When the grammar keeps a table of its rules,
+// the new rules enter it.
 template <typename T>
-__device__ u32 resident_find(const Slot* rtab, u64 rmask, const u32* rrhs, const u64* rrhs_off, u64 key,
-                             const T* S, u64 pos, u64 len) {
-    u64 s = key_home(key) & rmask;
-    for (u64 probe = 0; probe <= rmask; probe++) {
-        const u64 kk = rtab[s].key;
-        if (kk == kEmpty) return ~0u;
-        if (kk == key) {
-            const u64 r = rtab[s].ref;
-            const u64 o = rrhs_off[r];
-            if (rrhs_off[r + 1] - o == len) {
-                bool eq = true;
-                for (u64 x = 0; x < len && eq; x++) eq = ((u32)S[pos + x] == rrhs[o + x]);
-                if (eq) return (u32)r;
-            }
-        }
-        s = (s + 1) & rmask;
-    }
-    return ~0u;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kTileWords) k_phrases(const T* __restrict__ S, u64 n,
-                                                        const u32* __restrict__ Fprev, LevelHash lh,
-                                                        const u32* __restrict__ bitmap,
-                                                        const u64* __restrict__ tile_base, Slot* tab, u64 mask,
-                                                        u64 claim_limit, const Slot* __restrict__ rtab, u64 rmask,
-                                                        const u32* __restrict__ rrhs,
-                                                        const u64* __restrict__ rrhs_off,
-                                                        u32* __restrict__ P_slot, DevStatus* ds) {
-    __shared__ u32 sF[256];
-    __shared__ unsigned short sStart[kTilePos];
-    __shared__ u64 sTailEnd;
-    FpSource<T> fp;
-    if constexpr (sizeof(T) == 1) {
-        for (int x = threadIdx.x; x < 256; x += blockDim.x) sF[x] = Fprev[x];
-        fp.F = sF;
-    } else {
-        fp.F = Fprev;
-    }
-    const u64 tile = blockIdx.x;
-    const u64 nw = (n + 31) / 32;
-    const u64 w = tile * kTileWords + threadIdx.x;
-    u32 word = (w < nw) ? bitmap[w] : 0u;
-    u64 total;
-    u64 off = block_excl_scan((u64)__popc(word), total);
-    {
-        u32 m = word;
-        u32 o = (u32)off;
-        while (m) {
-            int b = __ffs(m) - 1;
-            m &= m - 1;
-            sStart[o++] = (unsigned short)(threadIdx.x * 32 + b);
-        }
-    }
-    if (threadIdx.x == 0) {
-        u64 tile_end = (tile + 1) * (u64)kTilePos;
-        sTailEnd = (tile_end >= n) ? n : phrase_end(bitmap, nw, n, tile_end - 1);
-    }
-    __syncthreads();
-    const u64 t0 = tile * (u64)kTilePos;
-    const u64 pbase = tile_base[tile];
-    for (u32 q = threadIdx.x; q < (u32)total; q += blockDim.x) {
-        const u64 start = t0 + sStart[q];
-        const u64 end = (q + 1 < (u32)total) ? t0 + sStart[q + 1] : sTailEnd;
-        const u64 len = end - start;
-        if (len >= (1ull << 32)) { set_error(ds, kErrPhraseLong); P_slot[pbase + q] = ~0u; continue; }
-        // H = sum_j F[Q_j] c^{j-1} mod p, by Horner from the last symbol
+__global__ void k_rules(const RoundArgs a, u64 g_new) {
+    constexpr bool kByte = sizeof(T) == 1;
+    const T* S = (const T*)a.S;
+    const ContentTable rw{(Key128*)a.rtab_w_keys, a.rtab_w_vals, a.rtab_w_cap};
+    for (u64 r = blockIdx.x * (u64)blockDim.x + threadIdx.x; r < g_new; r += (u64)gridDim.x * blockDim.x) {
+        const Key128 k = ((const Key128*)a.tab_keys)[a.slot_r[r]];
+        const u64 len = key_len(k);
+        const bool hashed = key_is_hashed(k);
+        const u64 off = a.G_base + a.xlen[r];
+        const u64 rank = a.g_base + r;
+        a.rhs_off[rank] = off;
+        auto get = [&](u64 j) -> u32 { return hashed ? (u32)S[k.lo + j] : key_sym(k, j, kByte); };
         u64 H = 0;
-        for (u64 x = end; x-- > start;) H = addmod61(mulmod61(H, lh.c), (u64)fp(S[x]));
-        const u32 fpv = finish_hash(lh, H);
-        const u64 key = make_key(H, len);
-        if (rtab != nullptr) {
-            const u32 r = resident_find<T>(rtab, rmask, rrhs, rrhs_off, key, S, start, len);
-            if (r != ~0u) { P_slot[pbase + q] = kResidentBit | r; continue; }
+        for (u64 j = len; j-- > 0;) {
+            const u32 v = get(j);
+            a.rhs[off + j] = v;
+            H = addmod61(mulmod61(H, a.lh.c), (u64)__ldg(a.Fprev + v));
         }
-        P_slot[pbase + q] = table_insert<T>(tab, mask, claim_limit, key, start, len, fpv, pbase + q, S, bitmap,
-                                            nw, n, ds);
-    }
-}
-
-// --------------------------------------------------------------------------
-// k_name: first-occurrence ranks, level-i rules and fingerprints
-// --------------------------------------------------------------------------
-
-// Claim a free slot of a resident table for rule `rank` with key `key` (rules
-// of a level are distinct, so no comparison is needed).
-__device__ void resident_insert(Slot* rtab, u64 rmask, u64 key, u64 rank, DevStatus* ds) {
-    u64 s = key_home(key) & rmask;
-    for (u64 probe = 0; probe <= rmask; probe++) {
-        u64 ok, oref;
-        cas128(rtab + s, kEmpty, kEmpty, key, rank, ok, oref);
-        if (ok == kEmpty) return;
-        s = (s + 1) & rmask;
-    }
-    set_error(ds, kErrTableFull);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kNameThreads) k_name(const u32* __restrict__ P_slot, const u64* __restrict__ Pp,
-                                                       Slot* tab, const T* __restrict__ S, u64 g_base, u64 G_base,
-                                                       u32* __restrict__ rhs, u64* __restrict__ rhs_off,
-                                                       u32* __restrict__ F, LBSlot<2>* lb, u64 epoch, u64* ctr,
-                                                       u64 ctr_base, u64* __restrict__ totals, Slot* rtab_w,
-                                                       u64 rmask_w, DevStatus* ds) {
-    const u64 P = *Pp;
-    const u64 tile = dynamic_tile(ctr, ctr_base);
-    const u64 p0 = tile * (u64)kNameTile;
-    if (p0 >= P) return;  // grid is sized from an upper bound of P
-    u32 slot[kNameItems];
-    bool first[kNameItems];
-    u64 len[kNameItems];
-    u64 cnt = 0, lsum = 0;
-#pragma unroll
-    for (int it = 0; it < kNameItems; it++) {
-        const u64 p = p0 + (u64)threadIdx.x * kNameItems + it;  // blocked: keeps order
-        first[it] = false;
-        len[it] = 0;
-        slot[it] = 0;
-        if (p < P) {
-            slot[it] = P_slot[p];
-            if (!(slot[it] & kResidentBit)) {
-                first[it] = (tab[slot[it]].minp == p);
-                if (first[it]) len[it] = tab[slot[it]].len;
-            }
-        }
-        cnt += first[it];
-        lsum += len[it];
-    }
-    u64 tc, tl;
-    u64 ec = block_excl_scan(cnt, tc);
-    u64 el = block_excl_scan(lsum, tl);
-    u64 agg[2] = {tc, tl}, excl[2];
-    block_lookback<2>(lb, tile, epoch, agg, excl, ds);
-    u64 r = g_base + excl[0] + ec;
-    u64 o = G_base + excl[1] + el;
-#pragma unroll
-    for (int it = 0; it < kNameItems; it++) {
-        if (!first[it]) continue;
-        Slot* sl = tab + slot[it];
-        const u64 ref = sl->ref;
-        F[r] = sl->fp;
-        rhs_off[r] = o;
-        for (u64 x = 0; x < len[it]; x++) rhs[o + x] = (u32)S[ref + x];
-        sl->ref = r;  // the slot now names its rank
-        if (rtab_w != nullptr) resident_insert(rtab_w, rmask_w, sl->key, r, ds);
-        r++;
-        o += len[it];
-    }
-    if (p0 + kNameTile >= P && threadIdx.x == 0) {
-        const u64 g_end = g_base + excl[0] + tc, G_end = G_base + excl[1] + tl;
-        rhs_off[g_end] = G_end;
-        totals[0] = g_end;
-        totals[1] = G_end;
+        const u32 fpv = finish_hash(a.lh, H);
+        a.F[rank] = fpv;
+        a.tab_vals[a.slot_r[r]] = ((u64)fpv << 32) | rank;  // for the rewrite: rank and fingerprint
+        if (rw.cap) table_put(rw, hashed ? key_hashed(H, len, rank) : k, rank, a.ds);
+        if (r == 0) a.rhs_off[a.g_base + g_new] = a.G_base + a.G_new;
     }
 }
 
@@ -431,43 +553,77 @@ __global__ void __launch_bounds__(kNameThreads) k_name(const u32* __restrict__ P
 // k_rewrite: T^{i+1} and retired strings
 // --------------------------------------------------------------------------
 
-__global__ void k_rewrite(const u32* __restrict__ P_slot, const u64* __restrict__ Pp, const Slot* __restrict__ tab,
-                          u32* __restrict__ Tnext, const u64* __restrict__ R_phr, const u32* __restrict__ R_sid,
-                          const RoundCounts* __restrict__ rc, u32 level, u32* __restrict__ c_level,
-                          u32* __restrict__ c_rank) {
-    const u64 P = *Pp;
-    const u64 nr = rc->retired;
+constexpr int kRankCache = 1024;
+
+// T^{i+1}[p] = rank of phrase p and f^{i+1}[p] = its fingerprint F^i[rank]
+// (so that the next round reads fingerprints without gathers).  Strings that
+// became one phrase take their C entry instead.
+__global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a) {
+    // per-block cache of slot -> (rank, fingerprint): in repetitive rounds a
+    // few entries take most phrases.  Both words carry the slot as a tag.
+    __shared__ u64 c_rank[kRankCache];
+    __shared__ u64 c_fp[kRankCache];
+    for (int x = threadIdx.x; x < kRankCache; x += blockDim.x) {
+        c_rank[x] = ~0ull;
+        c_fp[x] = ~0ull;
+    }
+    __syncthreads();
+    const u64 P = a.P;
+    const u64 nr = a.rc->retired;
     for (u64 p = blockIdx.x * (u64)blockDim.x + threadIdx.x; p < P; p += (u64)gridDim.x * blockDim.x) {
-        const u32 s = P_slot[p];
-        const u32 r = (s == ~0u) ? 0u : ((s & kResidentBit) ? (s & ~kResidentBit) : (u32)tab[s].ref);
-        if (nr == 0) { Tnext[p] = r; continue; }
-        u64 lo = 0, hi = nr;  // first index with R_phr >= p
-        while (lo < hi) {
-            u64 mid = (lo + hi) >> 1;
-            if (R_phr[mid] < p) lo = mid + 1; else hi = mid;
-        }
-        if (lo < nr && R_phr[lo] == p) {
-            c_level[R_sid[lo]] = level;
-            c_rank[R_sid[lo]] = r;
+        const u32 s = a.P_slot[p];
+        u32 r, f;
+        if (s & kResidentBit) {
+            r = s & ~kResidentBit;
+            f = __ldg(a.F + r);
         } else {
-            Tnext[p - lo] = r;
+            const u32 ci = s & (kRankCache - 1);
+            const u64 er = c_rank[ci], ef = c_fp[ci];
+            if ((u32)(er >> 32) == s && (u32)(ef >> 32) == s) {
+                r = (u32)er;
+                f = (u32)ef;
+            } else {
+                const u64 v = a.tab_vals[s];
+                r = (u32)v;
+                f = (u32)(v >> 32);
+                c_rank[ci] = ((u64)s << 32) | r;
+                c_fp[ci] = ((u64)s << 32) | f;
+            }
         }
+        u64 out = p;
+        if (nr != 0) {
+            u64 lo = 0, hi = nr;  // first index with R_phr >= p
+            while (lo < hi) {
+                const u64 mid = (lo + hi) >> 1;
+                if (a.R_phr[mid] < p) lo = mid + 1; else hi = mid;
+            }
+            if (lo < nr && a.R_phr[lo] == p) {
+                a.c_level[a.R_sid[lo]] = a.level;
+                a.c_rank[a.R_sid[lo]] = r;
+                continue;
+            }
+            out = p - lo;
+        }
+        a.Tnext[out] = r;
+        a.Fnext[out] = f;
     }
 }
 
 // --------------------------------------------------------------------------
-// k_resident_build: table over the existing rules of a level
+// k_resident_build: table over existing rules of a level
 // --------------------------------------------------------------------------
 
-// Rules r0 .. r0+cnt-1 of a level enter its resident table.
+// Rules r0 .. r0+cnt-1 of a level enter its table (values: ranks).
+template <bool kByte>
 __global__ void k_resident_build(const u32* __restrict__ rhs, const u64* __restrict__ rhs_off, u64 r0, u64 cnt,
-                                 const u32* __restrict__ Fprev, LevelHash lh, Slot* rtab, u64 rmask, DevStatus* ds) {
+                                 const u32* __restrict__ Fprev, LevelHash lh, ContentTable t, DevStatus* ds) {
     for (u64 x = blockIdx.x * (u64)blockDim.x + threadIdx.x; x < cnt; x += (u64)gridDim.x * blockDim.x) {
         const u64 r = r0 + x;
         const u64 s = rhs_off[r], e = rhs_off[r + 1];
         u64 H = 0;
         for (u64 y = e; y-- > s;) H = addmod61(mulmod61(H, lh.c), (u64)__ldg(Fprev + rhs[y]));
-        resident_insert(rtab, rmask, make_key(H, e - s), r, ds);
+        const Key128 k = rule_key([&](u64 j) { return rhs[s + j]; }, e - s, kByte, H, r);
+        table_put(t, k, r, ds);
     }
 }
 
@@ -477,7 +633,7 @@ __global__ void k_resident_build(const u32* __restrict__ rhs, const u64* __restr
 
 __global__ void k_level0(const unsigned char* __restrict__ data, const u64* __restrict__ pos,
                          const u32* __restrict__ ids, u32 cnt, u32* c_level, u32* c_rank) {
-    u32 x = blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x < cnt) {
         c_level[ids[x]] = 0;
         c_rank[ids[x]] = data[pos[x]];
@@ -496,62 +652,63 @@ __global__ void k_gather_strings(const unsigned char* __restrict__ data, const u
 // host launchers
 // --------------------------------------------------------------------------
 
-u64 tiles_for(u64 n) { return (n + kTilePos - 1) / kTilePos; }
-u64 name_tiles_for(u64 P) { return (P + kNameTile - 1) / kNameTile; }
+static unsigned grid_for(u64 n, u64 cap = 152ull * 32) {
+    u64 b = (n + 255) / 256;
+    if (b == 0) b = 1;
+    return (unsigned)(b < cap ? b : cap);
+}
 
-template <typename T>
-static cudaError_t launch_breaks_t(const RoundArgs& a, cudaStream_t st) {
-    const u64 tiles = tiles_for(a.n);
-    k_breaks<T><<<(unsigned)tiles, kTileWords, 0, st>>>((const T*)a.S, a.n, a.soff, a.k, a.Fprev, a.bitmap,
-                                                      a.tile_base, (LBSlot<1>*)a.lb1, a.epoch, a.ctr, a.ctr_base,
-                                                      a.total, a.ds);
+u64 parse_tile_positions(int) { return (u64)kTP; }
+
+u64 popscan_tiles_for(u64 nw) { return (nw + kPopTile - 1) / kPopTile; }
+
+cudaError_t launch_tile_strings(const RoundArgs& a, cudaStream_t st) {
+    const u64 tiles = (a.n + kTP - 1) / kTP;
+    k_tile_strings<<<grid_for(tiles), 256, 0, st>>>(a, tiles);
     return cudaGetLastError();
 }
 
-cudaError_t launch_breaks(const RoundArgs& a, cudaStream_t st) {
-    return a.sym_bytes == 1 ? launch_breaks_t<unsigned char>(a, st) : launch_breaks_t<u32>(a, st);
+cudaError_t launch_parse(const RoundArgs& a, cudaStream_t st) {
+    const u64 tiles = (a.n + kTP - 1) / kTP;
+    if (a.sym_bytes == 1) k_parse<unsigned char><<<(unsigned)tiles, kParseThreads, 0, st>>>(a);
+    else k_parse<u32><<<(unsigned)tiles, kParseThreads, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_strings(const RoundArgs& a, cudaStream_t st) {
-    k_strings<<<1, 1024, 0, st>>>(a.soff, a.sid, a.k, a.bitmap, a.tile_base, a.total, a.soff_next, a.sid_next,
-                                  a.R_phr, a.R_sid, a.rc);
+    k_strings<<<1, 1024, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-template <typename T>
-static cudaError_t launch_phrases_t(const RoundArgs& a, cudaStream_t st) {
-    const u64 tiles = tiles_for(a.n);
-    k_phrases<T><<<(unsigned)tiles, kTileWords, 0, st>>>((const T*)a.S, a.n, a.Fprev, a.lh, a.bitmap, a.tile_base,
-                                                       (Slot*)a.tab, a.mask, a.claim_limit, (const Slot*)a.rtab,
-                                                       a.rmask, a.rrhs, a.rrhs_off, a.P_slot, a.ds);
+cudaError_t launch_mark(const RoundArgs& a, u64 g_new, cudaStream_t st) {
+    if (g_new == 0) return cudaSuccess;
+    k_mark<<<grid_for(g_new), 256, 0, st>>>(a, g_new);
     return cudaGetLastError();
 }
 
-cudaError_t launch_phrases(const RoundArgs& a, cudaStream_t st) {
-    return a.sym_bytes == 1 ? launch_phrases_t<unsigned char>(a, st) : launch_phrases_t<u32>(a, st);
-}
-
-template <typename T>
-static cudaError_t launch_name_t(const RoundArgs& a, cudaStream_t st) {
-    const u64 tiles = name_tiles_for(a.P);
+cudaError_t launch_popscan(const RoundArgs& a, u64 nw, cudaStream_t st) {
+    const u64 tiles = popscan_tiles_for(nw);
     if (tiles == 0) return cudaSuccess;
-    k_name<T><<<(unsigned)tiles, kNameThreads, 0, st>>>(a.P_slot, a.total, (Slot*)a.tab, (const T*)a.S, a.g_base,
-                                                       a.G_base, a.rhs, a.rhs_off, a.F, (LBSlot<2>*)a.lb2,
-                                                       a.epoch, a.ctr, a.ctr_base, a.totals, (Slot*)a.rtab_w,
-                                                       a.rmask_w, a.ds);
+    k_popscan<<<(unsigned)tiles, kPopThreads, 0, st>>>(a, nw);
     return cudaGetLastError();
 }
 
-cudaError_t launch_name(const RoundArgs& a, cudaStream_t st) {
-    return a.sym_bytes == 1 ? launch_name_t<unsigned char>(a, st) : launch_name_t<u32>(a, st);
+cudaError_t launch_rank(const RoundArgs& a, u64 g_new, cudaStream_t st) {
+    if (g_new == 0) return cudaSuccess;
+    k_rank<<<grid_for(g_new), 256, 0, st>>>(a, g_new);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rules(const RoundArgs& a, u64 g_new, cudaStream_t st) {
+    if (g_new == 0) return cudaSuccess;
+    if (a.sym_bytes == 1) k_rules<unsigned char><<<grid_for(g_new), 256, 0, st>>>(a, g_new);
+    else k_rules<u32><<<grid_for(g_new), 256, 0, st>>>(a, g_new);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_rewrite(const RoundArgs& a, cudaStream_t st) {
-    u64 blocks = (a.P + 255) / 256;
-    if (blocks == 0) return cudaSuccess;
-    if (blocks > 152ull * 64) blocks = 152ull * 64;
-    k_rewrite<<<(unsigned)blocks, 256, 0, st>>>(a.P_slot, a.total, (const Slot*)a.tab, a.Tnext, a.R_phr, a.R_sid,
-                                                a.rc, a.level, a.c_level, a.c_rank);
+    if (a.P == 0) return cudaSuccess;
+    k_rewrite<<<grid_for(a.P, 152ull * 16), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -565,22 +722,22 @@ cudaError_t launch_level0(const unsigned char* data, const u64* pos, const u32* 
 cudaError_t launch_gather_strings(const unsigned char* data, const u64* src_off, const u64* dst_off, u32 k,
                                   unsigned char* out, cudaStream_t st) {
     if (k == 0) return cudaSuccess;
-    unsigned blocks = k < 152 * 8 ? k : 152 * 8;
+    const unsigned blocks = k < 152 * 8 ? k : 152 * 8;
     k_gather_strings<<<blocks, 256, 0, st>>>(data, src_off, dst_off, k, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_resident_build(const u32* rhs, const u64* rhs_off, u64 r0, u64 cnt, const u32* Fprev,
-                                  LevelHash lh, void* rtab, u64 rmask, DevStatus* ds, cudaStream_t st) {
+cudaError_t launch_resident_build(const u32* rhs, const u64* rhs_off, u64 r0, u64 cnt, bool bytes, const u32* Fprev,
+                                  LevelHash lh, void* keys, u64* vals, u64 cap, DevStatus* ds, cudaStream_t st) {
     if (cnt == 0) return cudaSuccess;
-    u64 blocks = (cnt + 255) / 256;
-    if (blocks > 152ull * 32) blocks = 152ull * 32;
-    k_resident_build<<<(unsigned)blocks, 256, 0, st>>>(rhs, rhs_off, r0, cnt, Fprev, lh, (Slot*)rtab, rmask, ds);
+    const ContentTable t{(Key128*)keys, vals, cap};
+    if (bytes) k_resident_build<true><<<grid_for(cnt), 256, 0, st>>>(rhs, rhs_off, r0, cnt, Fprev, lh, t, ds);
+    else k_resident_build<false><<<grid_for(cnt), 256, 0, st>>>(rhs, rhs_off, r0, cnt, Fprev, lh, t, ds);
     return cudaGetLastError();
 }
 
 size_t lb1_bytes(u64 tiles) { return tiles * sizeof(LBSlot<1>); }
 size_t lb2_bytes(u64 tiles) { return tiles * sizeof(LBSlot<2>); }
-size_t slot_bytes() { return sizeof(Slot); }
+size_t key_bytes() { return sizeof(Key128); }
 
 }  // namespace lcg

@@ -1,0 +1,193 @@
+// Content-addressed phrase tables (one per level and round).
+//
+// A table maps the content of a phrase (a sequence of level-(i-1) symbols) to
+// a value: during a round's parse the value is the smallest phrase index among
+// the phrase's occurrences, which decides first-occurrence naming; in the
+// table of a resident grammar it is the rule's rank.
+//
+// Keys are 128 bits.  Short phrases are stored exactly ("inline" keys): the
+// top 4 bits of `hi` hold the length q, and the symbols are packed from bit 0
+// upwards, 8 bits each for bytes (q <= 14) or 31 bits each for ranks (q <= 4,
+// ranks being < 2^31).  Two inline keys are equal exactly when the phrases
+// are.  A longer phrase gets a "hashed" key: top 4 bits 0, its length in bits
+// 32..59 of `hi` and a 32-bit hash below, with `lo` naming where its content
+// can be read; a hashed-key match is confirmed by comparing the contents
+// symbol by symbol.  Slots are claimed with one 128-bit compare-and-swap.
+// The home slot is the high half of mix(key) * cap, so any capacity works;
+// the polynomial fingerprint H = sum_j F[Q_j] c^{j-1} mod p of a phrase is
+// only needed for hashed keys.
+#pragma once
+
+#include "lcg_dev.cuh"
+
+namespace lcg {
+
+struct __align__(16) Key128 {
+    u64 lo, hi;
+};
+
+struct ContentTable {
+    Key128* keys;
+    u64* vals;
+    u64 cap;  // 0: no table
+};
+
+constexpr u64 kEmptyHi = ~0ull;
+constexpr int kHiBits = 60;
+constexpr u64 kMaxPhraseLen = (1ull << 28) - 1;  // longest phrase a hashed key can describe
+
+__device__ __forceinline__ int sym_bits(bool bytes) { return bytes ? 8 : 31; }
+__device__ __forceinline__ u64 inline_max(bool bytes) { return bytes ? 14 : 4; }
+
+__device__ __forceinline__ void put_bits(u64& hi, u64& lo, int pos, u64 v, int b) {
+    if (pos + b <= kHiBits) {
+        hi |= v << pos;
+    } else if (pos >= kHiBits) {
+        lo |= v << (pos - kHiBits);
+    } else {
+        hi |= (v << pos) & ((1ull << kHiBits) - 1);
+        lo |= v >> (kHiBits - pos);
+    }
+}
+
+__device__ __forceinline__ u64 get_bits(u64 hi, u64 lo, int pos, int b) {
+    const u64 m = (1ull << b) - 1;
+    if (pos + b <= kHiBits) return (hi >> pos) & m;
+    if (pos >= kHiBits) return (lo >> (pos - kHiBits)) & m;
+    const u64 low = (hi >> pos) & ((1ull << (kHiBits - pos)) - 1);
+    return (low | (lo << (kHiBits - pos))) & m;
+}
+
+template <typename Get>
+__device__ __forceinline__ Key128 key_inline(Get get, u64 len, bool bytes) {
+    const int b = sym_bits(bytes);
+    u64 hi = len << kHiBits, lo = 0;
+    for (u64 j = 0; j < len; j++) put_bits(hi, lo, (int)j * b, (u64)get(j), b);
+    return Key128{lo, hi};
+}
+
+__device__ __forceinline__ Key128 key_hashed(u64 H, u64 len, u64 ref) {
+    const u32 h = (u32)fmix64(H ^ (len * 0x9E3779B97F4A7C15ull));
+    return Key128{ref, (len << 32) | (u64)h};
+}
+
+__device__ __forceinline__ bool key_is_hashed(const Key128& k) { return (k.hi >> kHiBits) == 0; }
+
+__device__ __forceinline__ u64 key_len(const Key128& k) {
+    const u64 l = k.hi >> kHiBits;
+    return l ? l : ((k.hi >> 32) & kMaxPhraseLen);
+}
+
+// symbol j of an inline key
+__device__ __forceinline__ u32 key_sym(const Key128& k, u64 j, bool bytes) {
+    const int b = sym_bits(bytes);
+    return (u32)get_bits(k.hi, k.lo, (int)j * b, b);
+}
+
+// Home slot of a key: the high half of mix(key) * cap.  An inline key is the
+// content itself; a hashed key's high half carries the length and a hash of
+// the phrase's fingerprint (its low half names a location, not content).
+__device__ __forceinline__ u64 key_home(const Key128& k, u64 cap) {
+    const u64 m = key_is_hashed(k) ? fmix64(k.hi) : fmix64(k.hi ^ fmix64(k.lo + 0x9E3779B97F4A7C15ull));
+    return __umul64hi(m, cap);
+}
+
+__device__ __forceinline__ Key128 ld_key_relaxed(const Key128* p) {
+    Key128 k;
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(k.lo), "=l"(k.hi) : "l"(p) : "memory");
+    return k;
+}
+
+__device__ __forceinline__ Key128 cas_key(Key128* p, Key128 cmp, Key128 val) {
+    Key128 old;
+    asm volatile(
+        "{\n\t"
+        ".reg .b128 c, n, d;\n\t"
+        "mov.b128 c, {%2, %3};\n\t"
+        "mov.b128 n, {%4, %5};\n\t"
+        "atom.relaxed.gpu.global.cas.b128 d, [%6], c, n;\n\t"
+        "mov.b128 {%0, %1}, d;\n\t"
+        "}"
+        : "=l"(old.lo), "=l"(old.hi)
+        : "l"(cmp.lo), "l"(cmp.hi), "l"(val.lo), "l"(val.hi), "l"(p)
+        : "memory");
+    return old;
+}
+
+// Find or claim the slot of key k in a table that other threads are filling.
+// `same(ref)` compares the content stored at `ref` with the phrase (hashed keys
+// only).  The slot's value is lowered to `pidx` (first occurrence).  Returns
+// the slot and sets *claimed when this call claimed it, or ~0 when the table
+// is over its load limit or full (the host then regrows it and reruns).
+template <typename Same>
+__device__ u64 table_claim_or_find(ContentTable t, const Key128& k, bool hashed, u64 pidx, Same same, bool* claimed,
+                                   DevStatus* ds) {
+    u64 s = key_home(k, t.cap);
+    const Key128 empty{~0ull, ~0ull};
+    for (u64 probe = 0; probe < t.cap; probe++) {
+        Key128* kp = t.keys + s;
+        Key128 cur = ld_key_relaxed(kp);
+        if (cur.hi == kEmptyHi) {
+            if (vload(&ds->overflow)) return ~0ull;
+            const Key128 old = cas_key(kp, empty, k);
+            if (old.hi == kEmptyHi) {
+                *claimed = true;
+                atomicMin(t.vals + s, pidx);
+                return s;
+            }
+            cur = old;
+        }
+        if (cur.hi == k.hi) {
+            // a pair read while being written shows the empty low half: read it again atomically
+            if (cur.lo == ~0ull) cur = cas_key(kp, empty, empty);
+            if (hashed ? same(cur.lo) : (cur.lo == k.lo)) {
+                atomicMin(t.vals + s, pidx);
+                return s;
+            }
+        }
+        s = (s + 1 == t.cap) ? 0 : s + 1;
+    }
+    atomicExch(&ds->overflow, 1u);
+    return ~0ull;
+}
+
+// Look a key up in a table that nobody writes during the call.  `same(lo)`
+// confirms hashed keys.  Returns the slot's value, or ~0 when absent.
+template <typename Same>
+__device__ u64 table_find(const ContentTable& t, const Key128& k, bool hashed, Same same) {
+    u64 s = key_home(k, t.cap);
+    for (u64 probe = 0; probe < t.cap; probe++) {
+        const Key128 cur = t.keys[s];
+        if (cur.hi == kEmptyHi) return ~0ull;
+        if (cur.hi == k.hi && (hashed ? same(cur.lo) : (cur.lo == k.lo))) return t.vals[s];
+        s = (s + 1 == t.cap) ? 0 : s + 1;
+    }
+    return ~0ull;
+}
+
+// Claim a free slot for a key known to be absent (rules of a level are
+// distinct) and store `val`.
+__device__ __forceinline__ void table_put(ContentTable t, const Key128& k, u64 val, DevStatus* ds) {
+    u64 s = key_home(k, t.cap);
+    const Key128 empty{~0ull, ~0ull};
+    for (u64 probe = 0; probe < t.cap; probe++) {
+        const Key128 old = cas_key(t.keys + s, empty, k);
+        if (old.hi == kEmptyHi) {
+            t.vals[s] = val;
+            return;
+        }
+        s = (s + 1 == t.cap) ? 0 : s + 1;
+    }
+    set_error(ds, kErrTableFull);
+}
+
+// Key of a rule of level `level` whose right-hand side is get(0..len-1)
+// (bytes at level 1), with polynomial fingerprint H, for a table whose values
+// are ranks: hashed keys name the rank.
+template <typename Get>
+__device__ __forceinline__ Key128 rule_key(Get get, u64 len, bool bytes, u64 H, u64 rank) {
+    if (len <= inline_max(bytes)) return key_inline(get, len, bytes);
+    return key_hashed(H, len, rank);
+}
+
+}  // namespace lcg

@@ -22,7 +22,8 @@ _ERRORS = {
     -5: "LCG_EOVERFLOW", -6: "LCG_ETIMEOUT", -7: "LCG_EDEVICE", -8: "LCG_ETABLE",
 }
 SYMBOLS = [
-    "lcg_ctx_create", "lcg_ctx_destroy", "lcg_last_error", "lcg_last_build_stats", "lcg_build", "lcg_build_into",
+    "lcg_ctx_create", "lcg_ctx_destroy", "lcg_last_error", "lcg_last_build_stats", "lcg_set_kernel_timing",
+    "lcg_last_kernel_times", "lcg_build", "lcg_build_into",
     "lcg_merge", "lcg_decompress", "lcg_grammar_shape", "lcg_level_size", "lcg_export_level", "lcg_export_start",
     "lcg_grammar_free",
 ]
@@ -43,6 +44,11 @@ class RoundStatsC(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("phrases", ctypes.c_uint64), ("g", ctypes.c_uint64),
                 ("G", ctypes.c_uint64), ("strings", ctypes.c_uint64), ("table_cap", ctypes.c_uint64),
                 ("retries", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+
+
+class KernelTimeC(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+                ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
 class BuildStatsC(ctypes.Structure):
@@ -75,6 +81,8 @@ def load(build_if_missing: bool = True):
     lib.lcg_last_error.argtypes = [P]
     lib.lcg_last_error.restype = ctypes.c_char_p
     lib.lcg_last_build_stats.argtypes = [P, ctypes.POINTER(BuildStatsC)]
+    lib.lcg_set_kernel_timing.argtypes = [P, I]
+    lib.lcg_last_kernel_times.argtypes = [P, P, U32, ctypes.POINTER(U32)]
     lib.lcg_build.argtypes = [P, P, P, U32, I, PP]
     lib.lcg_build_into.argtypes = [P, P, P, P, U32, I]
     lib.lcg_merge.argtypes = [P, P, P]
@@ -163,6 +171,18 @@ class Context:
         """lcg_merge: a absorbs b (in place); returns a."""
         self._check(load().lcg_merge(self._h, a._h, b._h))
         return a
+
+    def set_kernel_timing(self, enable: bool) -> None:
+        """lcg_set_kernel_timing: bracket every kernel launch with CUDA events."""
+        self._check(load().lcg_set_kernel_timing(self._h, int(bool(enable))))
+
+    def last_kernel_times(self) -> dict:
+        """lcg_last_kernel_times: {kind: {"launches", "ms", "bytes"}} of the last call."""
+        cnt = ctypes.c_uint32(0)
+        buf = (KernelTimeC * 32)()
+        self._check(load().lcg_last_kernel_times(self._h, ctypes.cast(buf, ctypes.c_void_p), 32, ctypes.byref(cnt)))
+        return {buf[i].name.decode(): {"launches": int(buf[i].launches), "ms": float(buf[i].ms),
+                                       "bytes": float(buf[i].bytes)} for i in range(min(cnt.value, 32))}
 
     def last_build_stats(self) -> dict:
         st = BuildStatsC()
