@@ -64,6 +64,7 @@ struct lcg_ctx {
     void* lb2 = nullptr;
     u64 lb2_tiles = 0;
     double ratio_hint[64] = {0};  // distinct/phrases of the last build, per level
+    double p_hint[64] = {0};      // phrases/symbols of the last build, per level
     lcg_build_stats stats{};
     u64 launches = 0;
     // per-kernel CUDA-event timing (optional)
@@ -403,7 +404,9 @@ void build_into(lcg_ctx* ctx, lcg_grammar* R, const uint8_t* data, const uint64_
         u32* sid_next = dalloc<u32>(ctx, kk);
         u64* R_phr = dalloc<u64>(ctx, kk);
         u32* R_sid = dalloc<u32>(ctx, kk);
-        u32* P_slot = dalloc<u32>(ctx, Pmax);
+        u32* P_slot = dalloc<u32>(ctx, tiles * parse_tile_positions(symb));
+        u32* tile_cnt = dalloc<u32>(ctx, tiles);
+        u64* tile_pfx = dalloc<u64>(ctx, tiles);
         u32* Tnext = dalloc<u32>(ctx, Pmax);
         u32* Fnext = dalloc<u32>(ctx, Pmax);
         u32* tile_str = dalloc<u32>(ctx, tiles);
@@ -422,6 +425,8 @@ void build_into(lcg_ctx* ctx, lcg_grammar* R, const uint8_t* data, const uint64_
         a.level = i;
         a.string_first = string_first;
         a.tile_str = tile_str;
+        a.tile_cnt = tile_cnt;
+        a.tile_pfx = tile_pfx;
         a.lb1 = ctx->lb1;
         a.ctr = ctx->ctr;
         a.total = ctx->scratch;
@@ -432,7 +437,6 @@ void build_into(lcg_ctx* ctx, lcg_grammar* R, const uint8_t* data, const uint64_
         a.R_sid = R_sid;
         a.rc = ctx->rc;
         a.P_slot = P_slot;
-        a.P_cap = Pmax;
         if (against_resident && L.g > 0) {
             ensure_resident(ctx, R, i, L.g);
             a.rtab_keys = L.rkeys;
@@ -441,12 +445,20 @@ void build_into(lcg_ctx* ctx, lcg_grammar* R, const uint8_t* data, const uint64_
             a.rrhs = L.rhs;
             a.rrhs_off = L.rhs_off;
         }
-        // phrase table sized from the distinct/phrase ratio seen before
-        const u64 P_est = std::min<u64>(Pmax, (u64)(p_ratio * 1.2 * (double)n) + 64);
-        double ratio = ctx->ratio_hint[std::min<u32>(i, 63)];
-        if (ratio <= 0) ratio = (i == 1) ? 0.02 : std::min(1.0, std::max(prev_ratio * 2.0, 0.05));
-        u64 est = std::max<u64>(4096, std::min<u64>(P_est, (u64)(ratio * 1.3 * (double)P_est) + 1));
-        u64 cap = 2 * est;
+        // Phrase table: sized from the distinct/phrase ratio of this level in the
+        // context's previous build when there is one (load about 0.7, so that
+        // the table stays in L2), else from a generous guess; an overflowing
+        // table is regrown and the round rerun.
+        const double hint = ctx->ratio_hint[std::min<u32>(i, 63)];
+        u64 cap;
+        if (hint > 0) {
+            const u64 P_est = std::min<u64>(Pmax, (u64)(ctx->p_hint[std::min<u32>(i, 63)] * (double)n) + 64);
+            cap = std::max<u64>(8192, (u64)(hint * (double)P_est / 0.7) + 1024);
+        } else {
+            const u64 P_est = std::min<u64>(Pmax, (u64)(p_ratio * 1.2 * (double)n) + 64);
+            const double ratio = (i == 1) ? 0.02 : std::min(1.0, std::max(prev_ratio * 2.0, 0.05));
+            cap = 2 * std::max<u64>(4096, std::min<u64>(P_est, (u64)(ratio * 1.3 * (double)P_est) + 1));
+        }
         u32 retries = 0;
         DevStatus st;
         RoundCounts rc;
@@ -469,10 +481,7 @@ void build_into(lcg_ctx* ctx, lcg_grammar* R, const uint8_t* data, const uint64_
             a.tab_vals = tvals;
             a.tab_cap = cap;
             a.claims = claims;
-            a.claim_limit = cap / 2;
-            a.epoch = ++ctx->epoch;
-            a.ctr_base = ctx->ctr_val;
-            ctx->ctr_val += tiles;
+            a.claim_limit = cap - cap / 5;
             // T^i in, one phrase slot per phrase out (phrases estimated as n/3);
             // one table sector per phrase when the table does not fit in L2
             const double tab_bytes = cap * (double)(key_bytes() + sizeof(u64));
@@ -480,10 +489,20 @@ void build_into(lcg_ctx* ctx, lcg_grammar* R, const uint8_t* data, const uint64_
             h = kt_begin(ctx, "k_parse", (symb == 1 ? 1.0 : 8.0) * n + 4.0 * (double)n / 3.0 + tbytes);
             ck(ctx, launch_parse(a, ctx->st), "k_parse");
             kt_end(ctx, h);
+            // global index of every tile's first phrase, and the round's phrase count
+            const u64 stiles = std::max<u64>(1, scan2_tiles_for(tiles));
+            ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, stiles, scan2_lb_bytes(stiles));
+            u64 grid = 0;
+            h = kt_begin(ctx, "k_scan2", 12.0 * tiles);
+            ck(ctx, launch_scan2(tile_cnt, nullptr, tiles, tile_pfx, nullptr, ctx->scratch, ctx->lb2, ++ctx->epoch,
+                                 ctx->ctr, ctx->ctr_val, ctx->ds, ctx->st, &grid),
+               "scan");
+            kt_end(ctx, h);
+            ctx->ctr_val += grid;
             h = kt_begin(ctx, "k_strings", 40.0 * kk);
             ck(ctx, launch_strings(a, ctx->st), "k_strings");
             kt_end(ctx, h);
-            ctx->launches += 2;
+            ctx->launches += 3;
             ck(ctx, cudaMemcpyAsync(&rc, ctx->rc, sizeof(rc), cudaMemcpyDeviceToHost, ctx->st), "read counts");
             st = read_status(ctx);
             check_device_status(ctx, st);
@@ -496,6 +515,8 @@ void build_into(lcg_ctx* ctx, lcg_grammar* R, const uint8_t* data, const uint64_
         }
         const u64 P = rc.phrases;
         rs.phrases = P;
+        // every phrase but a string's first has length >= 2 (Sec. 3.4)
+        fail_if(ctx, P > Pmax, LCG_EDEVICE, "round produced more phrases than its bound");
         p_ratio = n ? (double)P / (double)n : 0.35;
         rs.table_cap = cap;
         rs.retries = retries;
@@ -504,7 +525,10 @@ void build_into(lcg_ctx* ctx, lcg_grammar* R, const uint8_t* data, const uint64_
         rs.g = g_new;
         rs.G = G_new;
         prev_ratio = P ? (double)g_new / (double)P : 0.0;
-        if (i < 64) ctx->ratio_hint[i] = prev_ratio;
+        if (i < 64) {
+            ctx->ratio_hint[i] = prev_ratio;
+            ctx->p_hint[i] = n ? (double)P / (double)n : 0.0;
+        }
         grow_level(ctx, L, L.g + g_new, L.G + G_new);
         if (against_resident) {
             ensure_resident(ctx, R, i, L.g + g_new);
@@ -585,6 +609,8 @@ void build_into(lcg_ctx* ctx, lcg_grammar* R, const uint8_t* data, const uint64_
         dfree(ctx, claims);
         dfree(ctx, string_first);
         dfree(ctx, tile_str);
+        dfree(ctx, tile_cnt);
+        dfree(ctx, tile_pfx);
         dfree(ctx, P_slot);
         dfree(ctx, R_phr);
         dfree(ctx, R_sid);

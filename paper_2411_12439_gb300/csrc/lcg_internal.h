@@ -31,7 +31,9 @@ struct RoundArgs {
     u32 level;            // i
     // parse pass
     u32* tile_str;        // per parse tile: the string holding its first position
-    u64* string_first;    // phrase index of each active string's first phrase
+    u32* tile_cnt;        // per parse tile: phrases starting in it
+    u64* tile_pfx;        // exclusive prefix of tile_cnt: global index of a tile's first phrase
+    u64* string_first;    // order key (tile * TP + q) of each active string's first phrase
     void* lb1;            // look-back slots
     u64 epoch;
     u64* ctr;
@@ -48,8 +50,8 @@ struct RoundArgs {
     u64 rtab_cap;
     const u32* rrhs;
     const u64* rrhs_off;
-    u32* P_slot;          // per phrase: slot, or a resident rank with the top bit set
-    u64 P_cap;            // entries of P_slot
+    u32* P_slot;          // per phrase, tile-major (tile * TP + q): slot, or a resident rank
+                          // with the top bit set
     // strings pass
     u64* soff_next;
     u32* sid_next;

@@ -69,8 +69,9 @@ constexpr int kParseThreads = 256;
 constexpr int kTP = 2048;          // positions per parse tile
 constexpr int kHalo = 64;          // positions staged past the tile end
 constexpr int kSP = kTP + kHalo;   // staged positions
-constexpr int kLocalSlots = 1024;
-constexpr unsigned short kNoLocal = 0xFFFF;
+constexpr int kCacheBits = 11;
+constexpr int kCacheSlots = 1 << kCacheBits;  // per-block phrase cache (byte rounds)
+constexpr int kCacheProbes = 8;
 constexpr int kClaimBuf = 1024;
 
 template <typename T>
@@ -101,7 +102,6 @@ __device__ u64 global_next_break(const T* S, FpSource<T> fp, u64 n, const u64* s
     return strend;
 }
 
-__device__ __forceinline__ u32 local_home(u64 key) { return (u32)(fmix64(key) & (kLocalSlots - 1)); }
 
 // Load n_sym symbols of type V from src (16-byte aligned when `vec`) into the
 // shared array dst, with every 16-byte load issued before any is stored.
@@ -131,7 +131,7 @@ __device__ __forceinline__ void stage_vec(V* dst, const V* src, int n_sym, bool 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kParseThreads) k_parse(const RoundArgs a) {
+__global__ void __launch_bounds__(kParseThreads) k_parse(const RoundArgs a, u64 ntiles) {
     constexpr int NWS = kSP / 32;    // staged break words
     constexpr int NWT = kTP / 32;    // tile break words
     constexpr bool kByte = sizeof(T) == 1;
@@ -147,11 +147,10 @@ __global__ void __launch_bounds__(kParseThreads) k_parse(const RoundArgs a) {
     __shared__ u32 sstart[NWS + 1];
     __shared__ u32 swp[NWT];
     __shared__ unsigned short sP[kTP];
-    __shared__ u32 sSlot[kTP];
-    __shared__ unsigned short sLi[kLocal ? kTP : 1];
-    __shared__ u64 lkey[kLocal ? kLocalSlots : 1];
-    __shared__ u32 lmin[kLocal ? kLocalSlots : 1];
-    __shared__ u32 lslot[kLocal ? kLocalSlots : 1];
+    // byte rounds: per-block cache of phrase (packed bytes) -> slot, kept across
+    // the block's tiles; val = (iteration << 43) | (q << 31) | slot
+    __shared__ u64 ckey[kLocal ? kCacheSlots : 1];
+    __shared__ u64 cval[kLocal ? kCacheSlots : 1];
     __shared__ u32 sClaim[kClaimBuf];
     __shared__ u64 s_tail_end;
     __shared__ u32 s_nclaim;
@@ -168,257 +167,256 @@ __global__ void __launch_bounds__(kParseThreads) k_parse(const RoundArgs a) {
     } else {
         fp.F = a.Fprev;
     }
-    if constexpr (kLocal) {
-        for (int x = tid; x < kLocalSlots; x += kParseThreads) {
-            lkey[x] = kEmpty;
-            lmin[x] = 0xFFFFFFFFu;
-        }
-    }
-    for (int w = tid; w < NWS + 1; w += kParseThreads) {
-        sstart[w] = 0;
-        if (w < NWS) sbits[w] = 0;
-    }
-    if (tid == 0) {
-        s_nclaim = 0;
-        s_claim_len = 0;
-    }
-    const u64 tile = dynamic_tile(a.ctr, a.ctr_base);  // has __syncthreads
-    const u64 t0 = tile * (u64)kTP;
-    const u64 t_end = min(t0 + (u64)kTP, n), s_end = min(t0 + (u64)kSP, n);
-    const int ns = (int)(s_end - t0), nt = (int)(t_end - t0);
-    const u32 j0 = a.tile_str[tile];  // string holding t0
-
-    // 1. stage the tile: bytes in round 1; ranks and their fingerprints
-    //    (written by the previous round's rewrite) afterwards
-    if constexpr (kByte) {
-        stage_vec<unsigned char>(sb, S + t0, ns, (reinterpret_cast<unsigned long long>(S + t0) & 15) == 0);
-        if (tid == 0) s_left = (t0 == 0) ? 0u : sF0[S[t0 - 1]];
-    } else {
-        stage_vec<u32>(sT, S + t0, ns, (reinterpret_cast<unsigned long long>(S + t0) & 15) == 0);
-        stage_vec<u32>(sf, a.Sf + t0, ns, (reinterpret_cast<unsigned long long>(a.Sf + t0) & 15) == 0);
-        if (tid == 0) s_left = (t0 == 0) ? 0u : a.Sf[t0 - 1];
-    }
-    // string starts at positions t0 .. s_end (n itself counts as one)
-    if (warp == 0) {
-        u32 jj = j0 + lane;
-        bool more = true;
-        while (more) {
-            u64 s = (jj <= a.k) ? __ldg(a.soff + jj) : ~0ull;
-            if (s >= t0 && s <= s_end) atomicOr(&sstart[(s - t0) >> 5], 1u << ((s - t0) & 31));
-            more = __shfl_sync(0xffffffffu, (jj <= a.k && s <= s_end) ? 1u : 0u, 31) != 0;
-            jj += 32;
-        }
-    }
-    __syncthreads();
-    auto fat = [&](int x) -> u32 {  // fingerprint of staged position x (x >= -1)
-        if (x < 0) return s_left;
-        if constexpr (kByte) return sF0[sb[x]]; else return sf[x];
-    };
-    auto is_start = [&](int x) -> bool { return (sstart[x >> 5] >> (x & 31)) & 1u; };
-
-    // 2. break bits (Eq. rand_types): a phrase starts at x when x starts a
-    //    string, or f[x-1] > f[x] and the first fingerprint right of x (in the
-    //    string) that differs from f[x] is larger than f[x]
-    for (int w = warp; w < (ns + 31) / 32; w += kParseThreads / 32) {
-        const int x = w * 32 + lane;
-        bool brk = false;
-        if (x < ns) {
-            if (is_start(x)) {
-                brk = true;
-            } else {
-                const u32 cur = fat(x);
-                if (fat(x - 1) > cur) {
-                    int y = x + 1;
-                    while (y < ns && !is_start(y) && fat(y) == cur) y++;
-                    u64 nd;
-                    if (y < ns) nd = is_start(y) ? kNone : (u64)fat(y);
-                    else if (s_end == n || is_start(ns)) nd = kNone;
-                    else {
-                        const u32 jl = string_of(a.soff, a.k, t0 + x);
-                        nd = scan_right_diff<T>(S, fp, s_end, __ldg(a.soff + jl + 1), cur);
-                    }
-                    brk = (nd != kNone) && (nd > (u64)cur);
-                }
-            }
-        }
-        const u32 word = __ballot_sync(0xffffffffu, brk);
-        if (lane == 0) sbits[w] = word;
-    }
-    __syncthreads();
-
-    // 3. phrase starts of the tile, in order; the tile's count is published at
-    //    once so that later tiles' look-backs need not wait for this tile's lookups
-    u32 word = 0;
-    if (tid < NWT) {
-        word = sbits[tid];
-        const int lo = tid * 32;
-        if (lo >= nt) word = 0;
-        else if (nt - lo < 32) word &= (1u << (nt - lo)) - 1u;
-    }
-    u64 cnt;
-    const u64 woff = block_excl_scan((u64)__popc(word), cnt);
-    u64 agg[1] = {cnt};
-    if (tid == 0) lookback_publish<1>((LBSlot<1>*)a.lb1, tile, a.epoch, agg);
-    if (tid < NWT) {
-        swp[tid] = (u32)woff;
-        u32 m = word, o = (u32)woff;
-        while (m) {
-            const int b = __ffs(m) - 1;
-            m &= m - 1;
-            sP[o++] = (unsigned short)(tid * 32 + b);
-        }
-    }
-    if (tid == 0) {
-        // end of the tile's last phrase: the first phrase start at or after t_end
-        u64 e = n;
-        bool found = false;
-        for (int x = nt; x < ns; x++) {
-            if ((sbits[x >> 5] >> (x & 31)) & 1u) { e = t0 + x; found = true; break; }
-        }
-        if (!found) e = (s_end == n) ? n : global_next_break<T>(S, fp, n, a.soff, a.k, s_end);
-        s_tail_end = e;
-    }
-    __syncthreads();
-
-    // 4. lookups.  A phrase's order key is tile * kTP + q (monotone in the
-    //    phrase index), so lookups do not need the tile's global phrase index.
-    const u64 tail = s_tail_end - t0;
-    const u32 cntq = (u32)cnt;
-    const u64 okey0 = tile * (u64)kTP;
     const ContentTable bt{(Key128*)a.tab_keys, a.tab_vals, a.tab_cap};
     const ContentTable rt{(Key128*)a.rtab_keys, a.rtab_vals, a.rtab_cap};
-    auto phrase_end = [&](u32 q) -> u64 { return (q + 1 < cntq) ? (u64)sP[q + 1] : tail; };
-    auto sym = [&](u64 x) -> u32 {  // symbol at tile offset x
-        if (x < (u64)ns) {
-            if constexpr (kByte) return (u32)sb[x]; else return sT[x];
-        }
-        return (u32)S[t0 + x];
-    };
-    auto lookup = [&](u32 q, u64 st, u64 en) -> u32 {
-        const u64 len = en - st;
-        if (len > kMaxPhraseLen) { set_error(a.ds, kErrPhraseLong); return ~0u; }
-        const bool hashed = len > inline_max(kByte);
-        Key128 key;
-        if (hashed) {
-            // H = sum_j F[Q_j] c^{j-1} mod p, by Horner from the last symbol
-            u64 H = 0;
-            for (u64 x = en; x-- > st;) {
-                const u32 v = (x < (u64)ns) ? fat((int)x) : fp(S[t0 + x]);
-                H = addmod61(mulmod61(H, a.lh.c), (u64)v);
-            }
-            key = key_hashed(H, len, t0 + st);
-        } else {
-            key = key_inline([&](u64 j) { return sym(st + j); }, len, kByte);
-        }
-        if (rt.cap) {
-            const u64 r = table_find(rt, key, hashed, [&](u64 rank) {
-                const u64 o = a.rrhs_off[rank];
-                for (u64 j = 0; j < len; j++)
-                    if ((u32)S[t0 + st + j] != a.rrhs[o + j]) return false;
-                return true;
-            });
-            if (r != ~0ull) return kResidentBit | (u32)r;
-        }
-        bool claimed = false;
-        const u64 slot = table_claim_or_find(bt, key, hashed, okey0 + q, [&](u64 ref) {
-            for (u64 j = 0; j < len; j++)
-                if (S[ref + j] != S[t0 + st + j]) return false;
-            return true;
-        }, &claimed, a.ds);
-        if (claimed) {
-            atomicAdd(&s_claim_len, len);
-            const u32 c = atomicAdd(&s_nclaim, 1u);
-            if (c < (u32)kClaimBuf) {
-                sClaim[c] = (u32)slot;
-            } else {  // buffer full: append directly
-                const u64 g = atomicAdd(&a.ds->claims, 1ull);
-                if (g < bt.cap) a.claims[g] = (u32)slot;
-            }
-        }
-        return (u32)slot;
-    };
-
     if constexpr (kLocal) {
-        // 4a. shared dedup of short phrases by their packed bytes
-        for (u32 q = tid; q < cntq; q += kParseThreads) {
-            const u64 st = sP[q], en = phrase_end(q), len = en - st;
-            unsigned short li = kNoLocal;
-            if (len <= 7 && en <= (u64)ns) {
-                u64 key = len << 56;
-                for (u64 x = 0; x < len; x++) key |= (u64)sb[st + x] << (8 * x);
-                // lanes of a warp with the same phrase insert it once
-                const u32 peers = __match_any_sync(__activemask(), key);
-                const int leader = __ffs(peers) - 1;
-                if (lane == leader) {
-                    u32 h = local_home(key);
-                    for (int probe = 0; probe < 64; probe++) {
-                        u64 cur = lkey[h];
-                        if (cur == kEmpty)
-                            cur = atomicCAS((unsigned long long*)&lkey[h], (unsigned long long)kEmpty,
-                                            (unsigned long long)key);
-                        if (cur == kEmpty || cur == key) {
-                            if (q < lmin[h]) atomicMin(&lmin[h], q);  // the leader has the group's smallest q
-                            li = (unsigned short)h;
-                            break;
+        for (int x = tid; x < kCacheSlots; x += kParseThreads) {
+            ckey[x] = kEmpty;
+            cval[x] = ~0ull;
+        }
+    }
+
+    // persistent blocks: tiles blockIdx.x, blockIdx.x + gridDim.x, ...  Tiles
+    // do not depend on one another.
+    u64 iter = 0;
+    for (u64 tile = blockIdx.x; tile < ntiles; tile += gridDim.x, iter++) {
+        for (int w = tid; w < NWS + 1; w += kParseThreads) {
+            sstart[w] = 0;
+            if (w < NWS) sbits[w] = 0;
+        }
+        if (tid == 0) {
+            s_nclaim = 0;
+            s_claim_len = 0;
+        }
+        const u64 t0 = tile * (u64)kTP;
+        const u64 t_end = min(t0 + (u64)kTP, n), s_end = min(t0 + (u64)kSP, n);
+        const int ns = (int)(s_end - t0), nt = (int)(t_end - t0);
+        const u32 j0 = a.tile_str[tile];  // string holding t0
+        __syncthreads();
+
+        // 1. stage the tile: bytes in round 1; ranks and their fingerprints
+        //    (written by the previous round's rewrite) afterwards
+        if constexpr (kByte) {
+            stage_vec<unsigned char>(sb, S + t0, ns, (reinterpret_cast<unsigned long long>(S + t0) & 15) == 0);
+            if (tid == 0) s_left = (t0 == 0) ? 0u : sF0[S[t0 - 1]];
+        } else {
+            stage_vec<u32>(sT, S + t0, ns, (reinterpret_cast<unsigned long long>(S + t0) & 15) == 0);
+            stage_vec<u32>(sf, a.Sf + t0, ns, (reinterpret_cast<unsigned long long>(a.Sf + t0) & 15) == 0);
+            if (tid == 0) s_left = (t0 == 0) ? 0u : a.Sf[t0 - 1];
+        }
+        // string starts at positions t0 .. s_end (n itself counts as one)
+        if (warp == 0) {
+            u32 jj = j0 + lane;
+            bool more = true;
+            while (more) {
+                const u64 s = (jj <= a.k) ? __ldg(a.soff + jj) : ~0ull;
+                if (s >= t0 && s <= s_end) atomicOr(&sstart[(s - t0) >> 5], 1u << ((s - t0) & 31));
+                more = __shfl_sync(0xffffffffu, (jj <= a.k && s <= s_end) ? 1u : 0u, 31) != 0;
+                jj += 32;
+            }
+        }
+        __syncthreads();
+        auto fat = [&](int x) -> u32 {  // fingerprint of staged position x (x >= -1)
+            if (x < 0) return s_left;
+            if constexpr (kByte) return sF0[sb[x]]; else return sf[x];
+        };
+        auto is_start = [&](int x) -> bool { return (sstart[x >> 5] >> (x & 31)) & 1u; };
+
+        // 2. break bits (Eq. rand_types): a phrase starts at x when x starts a
+        //    string, or f[x-1] > f[x] and the first fingerprint right of x (in
+        //    the string) that differs from f[x] is larger than f[x]
+        for (int w = warp; w < (ns + 31) / 32; w += kParseThreads / 32) {
+            const int x = w * 32 + lane;
+            bool brk = false;
+            if (x < ns) {
+                if (is_start(x)) {
+                    brk = true;
+                } else {
+                    const u32 cur = fat(x);
+                    if (fat(x - 1) > cur) {
+                        int y = x + 1;
+                        while (y < ns && !is_start(y) && fat(y) == cur) y++;
+                        u64 nd;
+                        if (y < ns) nd = is_start(y) ? kNone : (u64)fat(y);
+                        else if (s_end == n || is_start(ns)) nd = kNone;
+                        else {
+                            const u32 jl = string_of(a.soff, a.k, t0 + x);
+                            nd = scan_right_diff<T>(S, fp, s_end, __ldg(a.soff + jl + 1), cur);
                         }
-                        h = (h + 1) & (kLocalSlots - 1);
+                        brk = (nd != kNone) && (nd > (u64)cur);
                     }
                 }
-                li = (unsigned short)__shfl_sync(peers, (u32)li, leader);
             }
-            sLi[q] = li;
+            const u32 word = __ballot_sync(0xffffffffu, brk);
+            if (lane == 0) sbits[w] = word;
         }
         __syncthreads();
-        // 4b. one global lookup per distinct phrase of the tile (its first occurrence)
-        for (u32 q = tid; q < cntq; q += kParseThreads) {
-            const unsigned short li = sLi[q];
-            if (li != kNoLocal && lmin[li] != q) continue;
-            const u32 slot = lookup(q, sP[q], phrase_end(q));
-            if (li == kNoLocal) sSlot[q] = slot; else lslot[li] = slot;
-        }
-        __syncthreads();
-        // 4c. every occurrence takes its class's slot
-        for (u32 q = tid; q < cntq; q += kParseThreads) {
-            const unsigned short li = sLi[q];
-            if (li != kNoLocal) sSlot[q] = lslot[li];
-        }
-    } else {
-        for (u32 q = tid; q < cntq; q += kParseThreads) sSlot[q] = lookup(q, sP[q], phrase_end(q));
-    }
 
-    // 5. the tile's global phrase index; phrase slots and string starts out
-    u64 excl[1];
-    lookback_finish<1>((LBSlot<1>*)a.lb1, tile, a.epoch, agg, excl, a.ds);  // has __syncthreads
-    const u64 pbase = excl[0];
-    if (pbase + cnt > a.P_cap) {  // more phrases than the bound n/2 + 2k allows
-        if (tid == 0) set_error(a.ds, kErrPhraseLong);
-        return;
-    }
-    for (u32 q = tid; q < cntq; q += kParseThreads) a.P_slot[pbase + q] = sSlot[q];
-    if (tid == 0 && t_end == n) *a.total = pbase + cnt;
-    if (warp == 0) {
-        for (u32 jj = j0 + lane;; jj += 32) {
-            const u64 s = (jj < a.k) ? __ldg(a.soff + jj) : ~0ull;
-            if (s >= t0 && s < t_end) {
-                const int x = (int)(s - t0);
-                a.string_first[jj] = pbase + swp[x >> 5] + __popc(sbits[x >> 5] & ((1u << (x & 31)) - 1u));
-            }
-            if (__shfl_sync(0xffffffffu, (jj < a.k && s < t_end) ? 1u : 0u, 31) == 0) break;
+        // 3. phrase starts of the tile, in order
+        u32 word = 0;
+        if (tid < NWT) {
+            word = sbits[tid];
+            const int lo = tid * 32;
+            if (lo >= nt) word = 0;
+            else if (nt - lo < 32) word &= (1u << (nt - lo)) - 1u;
         }
-    }
-    // 6. this block's new entries join the round's claim list
-    const u32 nb = min(s_nclaim, (u32)kClaimBuf);
-    if (tid == 0 && s_nclaim) {
-        const u64 base = atomicAdd(&a.ds->claims, (u64)nb);
-        s_claim_base = base;
-        atomicAdd(&a.ds->claim_len, s_claim_len);
-        if (base + nb > a.claim_limit) atomicExch(&a.ds->overflow, 1u);
-    }
-    __syncthreads();
-    if (nb) {
-        const u64 base = s_claim_base;
-        for (u32 x = tid; x < nb; x += kParseThreads)
-            if (base + x < bt.cap) a.claims[base + x] = sClaim[x];
+        u64 cnt;
+        const u64 woff = block_excl_scan((u64)__popc(word), cnt);
+        if (tid < NWT) {
+            swp[tid] = (u32)woff;
+            u32 m = word, o = (u32)woff;
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                sP[o++] = (unsigned short)(tid * 32 + b);
+            }
+        }
+        if (tid == 0) {
+            // end of the tile's last phrase: the first phrase start at or after t_end
+            u64 e = n;
+            bool found = false;
+            for (int w = nt >> 5; w < (ns + 31) >> 5 && !found; w++) {
+                u32 m = sbits[w];
+                if (w == (nt >> 5)) m &= ~((1u << (nt & 31)) - 1u);
+                if (m) { e = t0 + (u64)(w * 32 + __ffs(m) - 1); found = true; }
+            }
+            if (!found) e = (s_end == n) ? n : global_next_break<T>(S, fp, n, a.soff, a.k, s_end);
+            s_tail_end = e;
+        }
+        __syncthreads();
+
+        // 4. lookups.  A phrase's order key is tile * kTP + q: it orders phrases
+        //    like their global index, and names the phrase's slot in the
+        //    tile-major P_slot array.
+        const u64 tail = s_tail_end - t0;
+        const u32 cntq = (u32)cnt;
+        const u64 okey0 = tile * (u64)kTP;
+        auto phrase_end = [&](u32 q) -> u64 { return (q + 1 < cntq) ? (u64)sP[q + 1] : tail; };
+        auto sym = [&](u64 x) -> u32 {  // symbol at tile offset x
+            if (x < (u64)ns) {
+                if constexpr (kByte) return (u32)sb[x]; else return sT[x];
+            }
+            return (u32)S[t0 + x];
+        };
+        auto lookup = [&](u32 q, u64 st, u64 en) -> u32 {
+            const u64 len = en - st;
+            if (len > kMaxPhraseLen) { set_error(a.ds, kErrPhraseLong); return ~0u; }
+            const bool hashed = len > inline_max(kByte);
+            Key128 key;
+            if (hashed) {
+                // H = sum_j F[Q_j] c^{j-1} mod p, by Horner from the last symbol
+                u64 H = 0;
+                for (u64 x = en; x-- > st;) {
+                    const u32 v = (x < (u64)ns) ? fat((int)x) : fp(S[t0 + x]);
+                    H = addmod61(mulmod61(H, a.lh.c), (u64)v);
+                }
+                key = key_hashed(H, len, t0 + st);
+            } else {
+                key = key_inline([&](u64 j) { return sym(st + j); }, len, kByte);
+            }
+            if (rt.cap) {
+                const u64 r = table_find(rt, key, hashed, [&](u64 rank) {
+                    const u64 o = a.rrhs_off[rank];
+                    for (u64 j = 0; j < len; j++)
+                        if ((u32)S[t0 + st + j] != a.rrhs[o + j]) return false;
+                    return true;
+                });
+                if (r != ~0ull) return kResidentBit | (u32)r;
+            }
+            bool claimed = false;
+            const u64 slot = table_claim_or_find(bt, key, hashed, okey0 + q, [&](u64 ref) {
+                for (u64 j = 0; j < len; j++)
+                    if (S[ref + j] != S[t0 + st + j]) return false;
+                return true;
+            }, &claimed, a.ds);
+            if (claimed) {
+                atomicAdd(&s_claim_len, len);
+                const u32 c = atomicAdd(&s_nclaim, 1u);
+                if (c < (u32)kClaimBuf) {
+                    sClaim[c] = (u32)slot;
+                } else {  // buffer full: append directly
+                    const u64 g = atomicAdd(&a.ds->claims, 1ull);
+                    if (g < bt.cap) a.claims[g] = (u32)slot;
+                }
+            }
+            return (u32)slot;
+        };
+
+        if constexpr (kLocal) {
+            // Short phrases go through the block's cache.  A hit on an entry
+            // made in an earlier tile of this block, or by an earlier
+            // occurrence in this tile, needs nothing more: that occurrence is
+            // already registered in the table.  Otherwise the slot's first
+            // occurrence is lowered to this phrase's order key.
+            for (u32 q = tid; q < cntq; q += kParseThreads) {
+                const u64 st = sP[q], en = phrase_end(q), len = en - st;
+                u32 slot = ~0u;
+                if (len <= 7 && en <= (u64)ns) {
+                    u64 key = len << 56;
+                    for (u64 x = 0; x < len; x++) key |= (u64)sb[st + x] << (8 * x);
+                    const u32 h0 = (u32)((key * 0x9E3779B97F4A7C15ull) >> (64 - kCacheBits));
+                    u32 h = h0;
+                    int free_h = -1;
+                    for (int probe = 0; probe < kCacheProbes; probe++) {
+                        const u64 k = ckey[h];
+                        if (k == key) {
+                            const u64 v = cval[h];
+                            if (v != ~0ull) {
+                                slot = (u32)(v & 0x7FFFFFFFull);
+                                const u64 vit = v >> 43, vq = (v >> 31) & 0xFFF;
+                                if (vit == (iter & 0x1FFFFF) && vq > q) atomicMin(a.tab_vals + slot, okey0 + q);
+                            }
+                            break;
+                        }
+                        if (k == kEmpty) { free_h = (int)h; break; }
+                        h = (h + 1) & (kCacheSlots - 1);
+                    }
+                    if (slot == ~0u) {
+                        slot = lookup(q, st, en);
+                        if (free_h >= 0 && slot != ~0u && !(slot & kResidentBit)) {
+                            const u64 old = atomicCAS((unsigned long long*)&ckey[free_h],
+                                                      (unsigned long long)kEmpty, (unsigned long long)key);
+                            if (old == kEmpty) cval[free_h] = ((iter & 0x1FFFFF) << 43) | ((u64)q << 31) | slot;
+                        }
+                    }
+                } else {
+                    slot = lookup(q, st, en);
+                }
+                a.P_slot[okey0 + q] = slot;
+            }
+        } else {
+            for (u32 q = tid; q < cntq; q += kParseThreads) a.P_slot[okey0 + q] = lookup(q, sP[q], phrase_end(q));
+        }
+        __syncthreads();
+
+        // 5. outputs: phrase slots (tile-major), the tile's phrase count, and
+        //    the order key of the first phrase of every string starting here
+        if (tid == 0) a.tile_cnt[tile] = cntq;
+        if (warp == 0) {
+            for (u32 jj = j0 + lane;; jj += 32) {
+                const u64 s = (jj < a.k) ? __ldg(a.soff + jj) : ~0ull;
+                if (s >= t0 && s < t_end) {
+                    const int x = (int)(s - t0);
+                    a.string_first[jj] = okey0 + swp[x >> 5] + __popc(sbits[x >> 5] & ((1u << (x & 31)) - 1u));
+                }
+                if (__shfl_sync(0xffffffffu, (jj < a.k && s < t_end) ? 1u : 0u, 31) == 0) break;
+            }
+        }
+        // 6. this tile's new entries join the round's claim list
+        const u32 nb = min(s_nclaim, (u32)kClaimBuf);
+        if (tid == 0 && s_nclaim) {
+            const u64 base = atomicAdd(&a.ds->claims, (u64)nb);
+            s_claim_base = base;
+            atomicAdd(&a.ds->claim_len, s_claim_len);
+            if (base + nb > a.claim_limit) atomicExch(&a.ds->overflow, 1u);
+        }
+        __syncthreads();
+        if (nb) {
+            const u64 base = s_claim_base;
+            for (u32 x = tid; x < nb; x += kParseThreads)
+                if (base + x < bt.cap) a.claims[base + x] = sClaim[x];
+        }
+        __syncthreads();
     }
 }
 
@@ -441,8 +439,9 @@ __global__ void __launch_bounds__(1024) k_strings(const RoundArgs a) {
         u64 first = 0, nextf = 0;
         bool retire = false;
         if (j < k) {
-            first = a.string_first[j];
-            nextf = (j + 1 < k) ? a.string_first[j + 1] : P;
+            auto index_of = [&](u64 ok) { return a.tile_pfx[ok / kTP] + ok % kTP; };
+            first = index_of(a.string_first[j]);
+            nextf = (j + 1 < k) ? index_of(a.string_first[j + 1]) : P;
             retire = (nextf - first == 1);
         }
         u64 tot;
@@ -558,7 +557,7 @@ constexpr int kRankCache = 1024;
 // T^{i+1}[p] = rank of phrase p and f^{i+1}[p] = its fingerprint F^i[rank]
 // (so that the next round reads fingerprints without gathers).  Strings that
 // became one phrase take their C entry instead.
-__global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a) {
+__global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) {
     // per-block cache of slot -> (rank, fingerprint): in repetitive rounds a
     // few entries take most phrases.  Both words carry the slot as a tag.
     __shared__ u64 c_rank[kRankCache];
@@ -568,44 +567,48 @@ __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a) {
         c_fp[x] = ~0ull;
     }
     __syncthreads();
-    const u64 P = a.P;
     const u64 nr = a.rc->retired;
-    for (u64 p = blockIdx.x * (u64)blockDim.x + threadIdx.x; p < P; p += (u64)gridDim.x * blockDim.x) {
-        const u32 s = a.P_slot[p];
-        u32 r, f;
-        if (s & kResidentBit) {
-            r = s & ~kResidentBit;
-            f = __ldg(a.F + r);
-        } else {
-            const u32 ci = s & (kRankCache - 1);
-            const u64 er = c_rank[ci], ef = c_fp[ci];
-            if ((u32)(er >> 32) == s && (u32)(ef >> 32) == s) {
-                r = (u32)er;
-                f = (u32)ef;
+    for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const u32 cnt = a.tile_cnt[t];
+        const u64 pbase = a.tile_pfx[t];
+        for (u32 q = threadIdx.x; q < cnt; q += blockDim.x) {
+            const u64 p = pbase + q;
+            const u32 s = a.P_slot[t * (u64)kTP + q];
+            u32 r, f;
+            if (s & kResidentBit) {
+                r = s & ~kResidentBit;
+                f = __ldg(a.F + r);
             } else {
-                const u64 v = a.tab_vals[s];
-                r = (u32)v;
-                f = (u32)(v >> 32);
-                c_rank[ci] = ((u64)s << 32) | r;
-                c_fp[ci] = ((u64)s << 32) | f;
+                const u32 ci = s & (kRankCache - 1);
+                const u64 er = c_rank[ci], ef = c_fp[ci];
+                if ((u32)(er >> 32) == s && (u32)(ef >> 32) == s) {
+                    r = (u32)er;
+                    f = (u32)ef;
+                } else {
+                    const u64 v = a.tab_vals[s];
+                    r = (u32)v;
+                    f = (u32)(v >> 32);
+                    c_rank[ci] = ((u64)s << 32) | r;
+                    c_fp[ci] = ((u64)s << 32) | f;
+                }
             }
+            u64 out = p;
+            if (nr != 0) {
+                u64 lo = 0, hi = nr;  // first index with R_phr >= p
+                while (lo < hi) {
+                    const u64 mid = (lo + hi) >> 1;
+                    if (a.R_phr[mid] < p) lo = mid + 1; else hi = mid;
+                }
+                if (lo < nr && a.R_phr[lo] == p) {
+                    a.c_level[a.R_sid[lo]] = a.level;
+                    a.c_rank[a.R_sid[lo]] = r;
+                    continue;
+                }
+                out = p - lo;
+            }
+            a.Tnext[out] = r;
+            a.Fnext[out] = f;
         }
-        u64 out = p;
-        if (nr != 0) {
-            u64 lo = 0, hi = nr;  // first index with R_phr >= p
-            while (lo < hi) {
-                const u64 mid = (lo + hi) >> 1;
-                if (a.R_phr[mid] < p) lo = mid + 1; else hi = mid;
-            }
-            if (lo < nr && a.R_phr[lo] == p) {
-                a.c_level[a.R_sid[lo]] = a.level;
-                a.c_rank[a.R_sid[lo]] = r;
-                continue;
-            }
-            out = p - lo;
-        }
-        a.Tnext[out] = r;
-        a.Fnext[out] = f;
     }
 }
 
@@ -668,10 +671,24 @@ cudaError_t launch_tile_strings(const RoundArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <typename T>
+static unsigned persistent_grid(u64 tiles) {
+    static int occ = 0, sms = 0;
+    if (occ == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_parse<T>, kParseThreads, 0);
+        if (occ <= 0) occ = 1;
+    }
+    const u64 g = (u64)occ * (u64)sms;
+    return (unsigned)(tiles < g ? (tiles ? tiles : 1) : g);
+}
+
 cudaError_t launch_parse(const RoundArgs& a, cudaStream_t st) {
     const u64 tiles = (a.n + kTP - 1) / kTP;
-    if (a.sym_bytes == 1) k_parse<unsigned char><<<(unsigned)tiles, kParseThreads, 0, st>>>(a);
-    else k_parse<u32><<<(unsigned)tiles, kParseThreads, 0, st>>>(a);
+    if (a.sym_bytes == 1) k_parse<unsigned char><<<persistent_grid<unsigned char>(tiles), kParseThreads, 0, st>>>(a, tiles);
+    else k_parse<u32><<<persistent_grid<u32>(tiles), kParseThreads, 0, st>>>(a, tiles);
     return cudaGetLastError();
 }
 
@@ -708,7 +725,9 @@ cudaError_t launch_rules(const RoundArgs& a, u64 g_new, cudaStream_t st) {
 
 cudaError_t launch_rewrite(const RoundArgs& a, cudaStream_t st) {
     if (a.P == 0) return cudaSuccess;
-    k_rewrite<<<grid_for(a.P, 152ull * 16), 256, 0, st>>>(a);
+    const u64 tiles = (a.n + kTP - 1) / kTP;
+    const u64 g = tiles < 152ull * 8 ? tiles : 152ull * 8;
+    k_rewrite<<<(unsigned)g, 256, 0, st>>>(a, tiles);
     return cudaGetLastError();
 }
 
