@@ -50,6 +50,8 @@ def parse_args():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--profile-builds", type=int, default=0,
+                   help="only run this many batched builds of the workload and exit (for profiler captures)")
     return p.parse_args()
 
 
@@ -237,6 +239,12 @@ def run_ours(args):
         t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{local}")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
+
+    if args.profile_builds:
+        for _ in range(args.profile_builds):
+            ctx.build(d, coll.offsets).free()
+        torch.cuda.synchronize()
+        return 0
 
     for _ in range(args.warmup):
         ctx.build(d, coll.offsets).free()
