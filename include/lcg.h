@@ -163,6 +163,25 @@ int lcg_merge(lcg_ctx* ctx, lcg_grammar* a, const lcg_grammar* b);
 int lcg_decompress(lcg_ctx* ctx, const lcg_grammar* G, uint32_t j, uint8_t* out, uint64_t cap,
                    uint64_t* out_len, int out_on_device);
 
+/* exp(C[j]) like lcg_decompress, but without allocating any device memory.
+ * This entry point has no counterpart in the paper; it is a library service.
+ * It is for callers that cannot allocate device memory at the time of the
+ * call, e.g. code running while a stream is being captured into a CUDA graph,
+ * allocator or memory-pressure callbacks, or services that reserve their
+ * device memory up front.  Its scratch is a static device array of about
+ * 20 MiB, which every GPU that loads the library keeps until the process
+ * exits.  The context and the grammar must already exist.
+ * out_dev: DEVICE buffer of `cap` bytes; *out_len receives |T_j|.
+ * Limits and errors: strings longer than 1048576 bytes are rejected with
+ * LCG_EOVERFLOW (use lcg_decompress); cap < |T_j| gives LCG_EINVAL.
+ * The first call on a device takes the scratch's device address
+ * (cudaGetSymbolAddress): make that first call before any stream capture.
+ * All calls share the scratch: calls whose device work overlaps (other
+ * threads, other contexts or streams) race and must be serialised by the
+ * caller.  The call is blocking. */
+int lcg_decompress_static(lcg_ctx* ctx, const lcg_grammar* G, uint32_t j, uint8_t* out_dev, uint64_t cap,
+                          uint64_t* out_len);
+
 /* Shape of a grammar: number of strings k and of levels >= 1. */
 int lcg_grammar_shape(const lcg_grammar* G, uint32_t* k, uint32_t* nlevels);
 /* Sizes of level i >= 1: g^i rules and G^i right-hand-side symbols. */

@@ -774,6 +774,88 @@ void decompress(lcg_ctx* ctx, const lcg_grammar* G, u32 j, uint8_t* out, u64 cap
     sync(ctx);
 }
 
+// --------------------------------------------------------------------------
+// exp(C[j]) without allocation: scratch in a static device array
+// --------------------------------------------------------------------------
+//
+// For callers that must not allocate device memory (code running while a
+// stream is being captured into a CUDA graph, allocator callbacks, services
+// that reserve all device memory up front).  The scratch lives in this
+// file-scope array, which every GPU that loads the library holds until the
+// process exits.  Its address is taken once per device with
+// cudaGetSymbolAddress (host code cannot use the array's name as a device
+// address).  Every call shares the array: calls that overlap on the GPU race.
+
+constexpr u64 kStaticMaxSymbols = 1ull << 20;  // longest string expanded: 1 MiB
+constexpr u64 kStaticLbTiles = 1024;           // look-back slots for one scan of kStaticMaxSymbols
+
+struct StaticScratch {
+    u32 cur[kStaticMaxSymbols];
+    u32 next[kStaticMaxSymbols];
+    u32 lens[kStaticMaxSymbols];
+    u64 offs[kStaticMaxSymbols];
+    u64 totals[2];
+    unsigned char lb[kStaticLbTiles * 48];
+};
+
+static __device__ __align__(256) unsigned char g_static_scratch[sizeof(StaticScratch)];
+
+StaticScratch* static_scratch_of_device(lcg_ctx* ctx) {
+    static StaticScratch* addr[256] = {nullptr};
+    fail_if(ctx, ctx->device < 0 || ctx->device >= 256, LCG_EDEVICE, "device index out of range");
+    if (!addr[ctx->device]) {
+        void* p = nullptr;
+        ck(ctx, cudaGetSymbolAddress(&p, g_static_scratch), "cudaGetSymbolAddress");
+        addr[ctx->device] = (StaticScratch*)p;
+    }
+    return addr[ctx->device];
+}
+
+void decompress_static(lcg_ctx* ctx, const lcg_grammar* G, u32 j, uint8_t* out, u64 cap, uint64_t* out_len) {
+    static_assert(scan2_lb_bytes_static(kStaticLbTiles) <= kStaticLbTiles * 48, "look-back slots");
+    fail_if(ctx, j >= G->k, LCG_EINVAL, "string index out of range");
+    StaticScratch* sc = static_scratch_of_device(ctx);
+    u32 lev = 0, r = 0;
+    ck(ctx, cudaMemcpyAsync(&lev, G->c_level + j, 4, cudaMemcpyDeviceToHost, ctx->st), "read C");
+    ck(ctx, cudaMemcpyAsync(&r, G->c_rank + j, 4, cudaMemcpyDeviceToHost, ctx->st), "read C");
+    sync(ctx);
+    u32* cur = sc->cur;
+    u32* nxt = sc->next;
+    ck(ctx, cudaMemcpyAsync(cur, &r, 4, cudaMemcpyHostToDevice, ctx->st), "copy");
+    u64 cnt = 1;
+    for (u32 l = lev; l >= 1; l--) {
+        const Level& L = G->lv[l - 1];
+        ck(ctx, launch_rule_lens(cur, cnt, L.rhs_off, sc->lens, ctx->st), "rule lens");
+        // the look-back slots left by an earlier call (any context) must not
+        // look published
+        ck(ctx, cudaMemsetAsync(sc->lb, 0, sizeof(sc->lb), ctx->st), "clear look-back");
+        u64 grid = 0;
+        ck(ctx, launch_scan2(sc->lens, nullptr, cnt, sc->offs, nullptr, sc->totals, sc->lb, ++ctx->epoch, ctx->ctr,
+                             ctx->ctr_val, ctx->ds, ctx->st, &grid),
+           "scan");
+        ctx->ctr_val += grid;
+        u64 total = 0;
+        ck(ctx, cudaMemcpyAsync(&total, sc->totals, 8, cudaMemcpyDeviceToHost, ctx->st), "read total");
+        check_device_status(ctx, read_status(ctx));
+        if (total > kStaticMaxSymbols) {
+            *out_len = total;  // a lower bound of the string's length
+            fail_if(ctx, true, LCG_EOVERFLOW,
+                    "string longer than the static scratch allows (1048576 symbols); use lcg_decompress");
+        }
+        ck(ctx, launch_expand(cur, cnt, sc->offs, L.rhs_off, L.rhs, nxt, ctx->st), "expand");
+        ctx->launches += 3;
+        u32* t = cur;
+        cur = nxt;
+        nxt = t;
+        cnt = total;
+    }
+    *out_len = cnt;
+    fail_if(ctx, cap < cnt, LCG_EINVAL, "output buffer too small");
+    ck(ctx, launch_to_bytes(cur, cnt, out, ctx->st), "to bytes");
+    ctx->launches++;
+    sync(ctx);
+}
+
 }  // namespace
 
 // --------------------------------------------------------------------------
@@ -948,6 +1030,16 @@ int lcg_decompress(lcg_ctx* ctx, const lcg_grammar* G, uint32_t j, uint8_t* out,
     LCG_GUARD_BEGIN
     ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
     decompress(ctx, G, j, out, cap, out_len, out_on_device);
+    return LCG_OK;
+    LCG_GUARD_END
+}
+
+int lcg_decompress_static(lcg_ctx* ctx, const lcg_grammar* G, uint32_t j, uint8_t* out_dev, uint64_t cap,
+                          uint64_t* out_len) {
+    if (!ctx || !G || !out_dev || !out_len) return LCG_EINVAL;
+    LCG_GUARD_BEGIN
+    ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    decompress_static(ctx, G, j, out_dev, cap, out_len);
     return LCG_OK;
     LCG_GUARD_END
 }

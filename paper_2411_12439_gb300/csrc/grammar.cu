@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan2(const u32* __restrict__ 
 }
 
 u64 scan2_tiles_for(u64 n) { return (n + kScanTile - 1) / kScanTile; }
-size_t scan2_lb_bytes(u64 tiles) { return tiles * sizeof(LBSlot<2>); }
+size_t scan2_lb_bytes(u64 tiles) { return scan2_lb_bytes_static(tiles); }
 
 cudaError_t launch_scan2(const u32* in0, const u32* in1, u64 n, u64* out0, u64* out1, u64* totals, void* lb,
                          u64 epoch, u64* ctr, u64 ctr_base, DevStatus* ds, cudaStream_t st, u64* grid_out) {

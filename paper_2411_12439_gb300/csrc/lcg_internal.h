@@ -120,5 +120,6 @@ cudaError_t launch_scan2(const u32* in0, const u32* in1, u64 n, u64* out0, u64* 
                          u64 epoch, u64* ctr, u64 ctr_base, DevStatus* ds, cudaStream_t st, u64* grid_out);
 u64 scan2_tiles_for(u64 n);
 size_t scan2_lb_bytes(u64 tiles);
+constexpr size_t scan2_lb_bytes_static(u64 tiles) { return tiles * sizeof(LBSlot<2>); }
 
 }  // namespace lcg

@@ -24,7 +24,7 @@ _ERRORS = {
 SYMBOLS = [
     "lcg_ctx_create", "lcg_ctx_destroy", "lcg_last_error", "lcg_last_build_stats", "lcg_set_kernel_timing",
     "lcg_last_kernel_times", "lcg_build", "lcg_build_into",
-    "lcg_merge", "lcg_decompress", "lcg_grammar_shape", "lcg_level_size", "lcg_export_level", "lcg_export_start",
+    "lcg_merge", "lcg_decompress", "lcg_decompress_static", "lcg_grammar_shape", "lcg_level_size", "lcg_export_level", "lcg_export_start",
     "lcg_grammar_free",
 ]
 
@@ -87,6 +87,7 @@ def load(build_if_missing: bool = True):
     lib.lcg_build_into.argtypes = [P, P, P, P, U32, I]
     lib.lcg_merge.argtypes = [P, P, P]
     lib.lcg_decompress.argtypes = [P, P, U32, P, U64, ctypes.POINTER(U64), I]
+    lib.lcg_decompress_static.argtypes = [P, P, U32, P, U64, ctypes.POINTER(U64)]
     lib.lcg_grammar_shape.argtypes = [P, ctypes.POINTER(U32), ctypes.POINTER(U32)]
     lib.lcg_level_size.argtypes = [P, U32, ctypes.POINTER(U64), ctypes.POINTER(U64)]
     lib.lcg_export_level.argtypes = [P, P, U32, P, P, P]
@@ -239,6 +240,16 @@ class Grammar:
         cr = np.zeros(max(k, 1), dtype=np.uint32)
         self.ctx._check(lib.lcg_export_start(self.ctx._h, self._h, _np_ptr(F0), _np_ptr(cl), _np_ptr(cr)))
         return {"F0": F0, "levels": levels, "c_level": cl[:k], "c_rank": cr[:k]}
+
+    def decompress_static(self, j: int, out) -> int:
+        """lcg_decompress_static: exp(C[j]) into the CUDA uint8 tensor ``out``
+        using the library's static scratch (no device allocation)."""
+        ptr, on_dev, keep = _data_arg(out)
+        if not on_dev:
+            raise LCGError(-1, "lcg_decompress_static writes device memory only")
+        n = ctypes.c_uint64(0)
+        self.ctx._check(load().lcg_decompress_static(self.ctx._h, self._h, j, ptr, out.numel(), ctypes.byref(n)))
+        return int(n.value)
 
     def decompress(self, j: int, out=None):
         """exp(C[j]) as bytes (host), or into a CUDA uint8 tensor ``out``."""
