@@ -63,8 +63,14 @@ struct lcg_ctx {
     u64 lb1_tiles = 0;
     void* lb2 = nullptr;
     u64 lb2_tiles = 0;
-    double ratio_hint[64] = {0};  // distinct/phrases of the last build, per level
-    double p_hint[64] = {0};      // phrases/symbols of the last build, per level
+    double ratio_hint[64] = {0};  // new rules per phrase in the last build, per level
+    double p_hint[64] = {0};      // phrases per symbol in the last build, per level
+    double glen_hint[64] = {0};   // symbols per new rule in the last build, per level
+    u32 hint_rounds = 0;          // rounds of the last build (0: none yet)
+    // per-round device status, counts and totals (rounds enqueued without syncs)
+    DevStatus* ds_arr = nullptr;
+    RoundCounts* rc_arr = nullptr;
+    u64* tot_arr = nullptr;
     lcg_build_stats stats{};
     u64 launches = 0;
     // per-kernel CUDA-event timing (optional)
@@ -82,6 +88,7 @@ struct lcg_ctx {
 namespace {
 
 constexpr u64 kMaxRank = 0x7fffffffull;  // ranks are tagged with one bit in the phrase slots
+constexpr u32 kMaxRounds = 63;
 constexpr double kL2Bytes = 126.5 * 1024 * 1024;  // GB300 L2 (for algorithmic-byte accounting)
 
 struct Fail {
@@ -309,8 +316,449 @@ void free_grammar_now(lcg_grammar* G) {
 // BuildGram round driver
 // --------------------------------------------------------------------------
 
+void record_hints(lcg_ctx* ctx, u32 i, u64 n, u64 P, u64 g, u64 G) {
+    if (i >= 64) return;
+    ctx->ratio_hint[i] = P ? (double)g / (double)P : 0.0;
+    ctx->p_hint[i] = n ? (double)P / (double)n : 0.0;
+    ctx->glen_hint[i] = g ? (double)G / (double)g : 2.0;
+}
+
+// The sequence a round reads: T^i, its fingerprints (rounds >= 2) and the
+// offsets and ids of its active strings.
+struct RoundInput {
+    const void* S;
+    void* S_owned;
+    const u32* Sf;
+    int symb;
+    u64 n;          // |T^i| (host value when known)
+    u32 kk;         // active strings (host value when known)
+    u64* soff;
+    u32* sid;
+    const u64* d_n;  // device values, for rounds enqueued without a sync
+    const u64* d_k;
+};
+
+struct Retry {};
+
+void free_round_input(lcg_ctx* ctx, RoundInput& in) {
+    dfree(ctx, in.soff);
+    dfree(ctx, in.sid);
+    if (in.S_owned) dfree(ctx, in.S_owned);
+    if (in.Sf) dfree(ctx, (void*)in.Sf);
+    in.soff = nullptr;
+    in.sid = nullptr;
+    in.S_owned = nullptr;
+    in.Sf = nullptr;
+}
+
+// Buffers of one round.
+struct RoundBufs {
+    u64 tiles = 0, Pmax = 0, cap = 0, g_alloc = 0;
+    u64* string_first = nullptr;
+    u64* soff_next = nullptr;
+    u32* sid_next = nullptr;
+    u64* R_phr = nullptr;
+    u32* R_sid = nullptr;
+    u32* P_slot = nullptr;
+    u32* tile_cnt = nullptr;
+    u64* tile_pfx = nullptr;
+    u32* Tnext = nullptr;
+    u32* Fnext = nullptr;
+    u32* tile_str = nullptr;
+    unsigned char* tkeys = nullptr;
+    u64* tvals = nullptr;
+    u32* claims = nullptr;
+    u32* first_bits = nullptr;
+    u32* first_prefix = nullptr;
+    u32* slot_r = nullptr;
+    u32* len_r = nullptr;
+    u64* xlen = nullptr;
+};
+
+void alloc_round(lcg_ctx* ctx, RoundBufs& b, u64 n_bound, u32 kk) {
+    b.tiles = (n_bound + parse_tile_positions(1) - 1) / parse_tile_positions(1);
+    // every phrase but a string's first has length >= 2
+    b.Pmax = n_bound / 2 + 2ull * kk + 1;
+    b.string_first = dalloc<u64>(ctx, kk);
+    b.soff_next = dalloc<u64>(ctx, kk + 1);
+    b.sid_next = dalloc<u32>(ctx, kk);
+    b.R_phr = dalloc<u64>(ctx, kk);
+    b.R_sid = dalloc<u32>(ctx, kk);
+    b.P_slot = dalloc<u32>(ctx, b.tiles * parse_tile_positions(1));
+    b.tile_cnt = dalloc<u32>(ctx, b.tiles);
+    b.tile_pfx = dalloc<u64>(ctx, b.tiles);
+    b.Tnext = dalloc<u32>(ctx, b.Pmax);
+    b.Fnext = dalloc<u32>(ctx, b.Pmax);
+    b.tile_str = dalloc<u32>(ctx, b.tiles);
+}
+
+void alloc_table(lcg_ctx* ctx, RoundBufs& b, u64 cap) {
+    b.cap = cap;
+    b.tkeys = dalloc<unsigned char>(ctx, cap * key_bytes());
+    b.tvals = dalloc<u64>(ctx, cap);
+    b.claims = dalloc<u32>(ctx, cap);
+    ck(ctx, cudaMemsetAsync(b.tkeys, 0xFF, cap * key_bytes(), ctx->st), "memset table");
+    ck(ctx, cudaMemsetAsync(b.tvals, 0xFF, cap * sizeof(u64), ctx->st), "memset table");
+}
+
+void free_table(lcg_ctx* ctx, RoundBufs& b) {
+    dfree(ctx, b.tkeys);
+    dfree(ctx, b.tvals);
+    dfree(ctx, b.claims);
+    b.tkeys = nullptr;
+    b.tvals = nullptr;
+    b.claims = nullptr;
+}
+
+void alloc_naming(lcg_ctx* ctx, RoundBufs& b, u64 g_alloc) {
+    b.g_alloc = g_alloc;
+    const u64 nw = b.tiles * parse_tile_positions(1) / 32;  // order keys tile * TP + q
+    b.first_bits = dalloc<u32>(ctx, nw);
+    b.first_prefix = dalloc<u32>(ctx, nw);
+    b.slot_r = dalloc<u32>(ctx, g_alloc);
+    b.len_r = dalloc<u32>(ctx, g_alloc);
+    b.xlen = dalloc<u64>(ctx, g_alloc);
+    ck(ctx, cudaMemsetAsync(b.first_bits, 0, nw * sizeof(u32), ctx->st), "memset bits");
+}
+
+// Free a round's buffers except those that become the next round's input.
+void free_round(lcg_ctx* ctx, RoundBufs& b) {
+    for (void* p : {(void*)b.string_first, (void*)b.R_phr, (void*)b.R_sid, (void*)b.P_slot, (void*)b.tile_cnt,
+                    (void*)b.tile_pfx, (void*)b.tile_str, (void*)b.first_bits, (void*)b.first_prefix,
+                    (void*)b.slot_r, (void*)b.len_r, (void*)b.xlen})
+        dfree(ctx, p);
+    free_table(ctx, b);
+}
+
+RoundArgs round_args(lcg_ctx* ctx, lcg_grammar* R, const RoundInput& in, RoundBufs& b, u32 i) {
+    RoundArgs a{};
+    a.sym_bytes = in.symb;
+    a.S = in.S;
+    a.Sf = in.Sf;
+    a.n = in.n;
+    a.d_n = in.d_n;
+    a.soff = in.soff;
+    a.sid = in.sid;
+    a.k = in.kk;
+    a.d_k = in.d_k;
+    a.Fprev = fprev_of(R, i);
+    a.lh = level_hash(ctx, i);
+    a.level = i;
+    a.tiles_bound = b.tiles;
+    a.string_first = b.string_first;
+    a.tile_str = b.tile_str;
+    a.tile_cnt = b.tile_cnt;
+    a.tile_pfx = b.tile_pfx;
+    a.ctr = ctx->ctr;
+    a.ds = ctx->ds_arr + (i - 1);
+    a.rc = ctx->rc_arr + (i - 1);
+    a.total = ctx->tot_arr + 3 * (i - 1);  // [0] phrases; [1], [2] scratch of the scans
+    a.d_tiles = &a.rc->tiles;
+    a.d_gnew = &a.ds->claims;
+    a.d_Gnew = &a.ds->claim_len;
+    a.soff_next = b.soff_next;
+    a.sid_next = b.sid_next;
+    a.R_phr = b.R_phr;
+    a.R_sid = b.R_sid;
+    a.P_slot = b.P_slot;
+    a.T_cap = b.Pmax;
+    a.Tnext = b.Tnext;
+    a.Fnext = b.Fnext;
+    a.c_level = R->c_level;
+    a.c_rank = R->c_rank;
+    return a;
+}
+
+void set_table(RoundArgs& a, RoundBufs& b) {
+    a.tab_keys = b.tkeys;
+    a.tab_vals = b.tvals;
+    a.tab_cap = b.cap;
+    a.claims = b.claims;
+    a.claim_limit = b.cap - b.cap / 5;
+}
+
+// Parse: tile strings, k_parse, tile scan, strings.
+void enqueue_parse(lcg_ctx* ctx, RoundArgs& a, u64 n_for_bytes) {
+    ck(ctx, launch_tile_strings(a, ctx->st), "k_tile_strings");
+    const double tab_bytes = a.tab_cap * (double)(key_bytes() + sizeof(u64));
+    const double tbytes = tab_bytes > kL2Bytes ? 32.0 * (double)n_for_bytes / 3.0 : 0.0;
+    int h = kt_begin(ctx, "k_parse",
+                     (a.sym_bytes == 1 ? 1.0 : 8.0) * n_for_bytes + 4.0 * (double)n_for_bytes / 3.0 + tbytes);
+    ck(ctx, launch_parse(a, ctx->st), "k_parse");
+    kt_end(ctx, h);
+    const u64 stiles = std::max<u64>(1, scan2_tiles_for(a.tiles_bound));
+    ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, stiles, scan2_lb_bytes(stiles));
+    u64 grid = 0;
+    h = kt_begin(ctx, "k_scan2", 12.0 * (double)a.tiles_bound);
+    ck(ctx, launch_scan2(a.tile_cnt, nullptr, a.tiles_bound, a.tile_pfx, nullptr, a.total, ctx->lb2, ++ctx->epoch,
+                         ctx->ctr, ctx->ctr_val, a.ds, ctx->st, &grid, a.d_tiles),
+       "scan");
+    kt_end(ctx, h);
+    ctx->ctr_val += grid;
+    h = kt_begin(ctx, "k_strings", 40.0 * a.k);
+    ck(ctx, launch_strings(a, ctx->st), "k_strings");
+    kt_end(ctx, h);
+    ctx->launches += 4;
+}
+
+// Naming and rewrite: mark, popcount scan, rank, length scan, rules, rewrite.
+void enqueue_naming(lcg_ctx* ctx, RoundArgs& a, RoundBufs& b, double g_bytes, double G_bytes, double P_bytes) {
+    a.first_bits = b.first_bits;
+    a.first_prefix = b.first_prefix;
+    a.slot_r = b.slot_r;
+    a.len_r = b.len_r;
+    a.xlen = b.xlen;
+    a.g_alloc = b.g_alloc;
+    const u64 g_grid = std::max<u64>(1, b.g_alloc);
+    int h = kt_begin(ctx, "k_mark", 12.0 * g_bytes);
+    ck(ctx, launch_mark(a, g_grid, ctx->st), "k_mark");
+    kt_end(ctx, h);
+    const u64 nw = b.tiles * parse_tile_positions(1) / 32;
+    const u64 ptiles = std::max<u64>(1, popscan_tiles_for(nw));
+    ensure_lb(ctx, &ctx->lb1, &ctx->lb1_tiles, ptiles, lb1_bytes(ptiles));
+    a.lb1 = ctx->lb1;
+    a.epoch = ++ctx->epoch;
+    a.ctr_base = ctx->ctr_val;
+    ctx->ctr_val += ptiles;
+    h = kt_begin(ctx, "k_popscan", 8.0 * (double)nw);
+    ck(ctx, launch_popscan(a, nw, ctx->st), "k_popscan");
+    kt_end(ctx, h);
+    h = kt_begin(ctx, "k_rank", 24.0 * g_bytes);
+    ck(ctx, launch_rank(a, g_grid, ctx->st), "k_rank");
+    kt_end(ctx, h);
+    const u64 stiles = std::max<u64>(1, scan2_tiles_for(g_grid));
+    ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, stiles, scan2_lb_bytes(stiles));
+    u64 grid = 0;
+    h = kt_begin(ctx, "k_scan2", 12.0 * g_bytes);
+    ck(ctx, launch_scan2(b.len_r, nullptr, g_grid, b.xlen, nullptr, a.total + 1, ctx->lb2, ++ctx->epoch, ctx->ctr,
+                         ctx->ctr_val, a.ds, ctx->st, &grid, a.d_gnew),
+       "scan");
+    kt_end(ctx, h);
+    ctx->ctr_val += grid;
+    h = kt_begin(ctx, "k_rules", 4.0 * G_bytes + 12.0 * g_bytes);
+    ck(ctx, launch_rules(a, g_grid, ctx->st), "k_rules");
+    kt_end(ctx, h);
+    h = kt_begin(ctx, "k_rewrite", 12.0 * P_bytes);
+    ck(ctx, launch_rewrite(a, ctx->st), "k_rewrite");
+    kt_end(ctx, h);
+    ctx->launches += 6;
+}
+
+void next_input(lcg_ctx* ctx, RoundInput& in, RoundBufs& b) {
+    dfree(ctx, in.soff);
+    dfree(ctx, in.sid);
+    if (in.S_owned) dfree(ctx, in.S_owned);
+    if (in.Sf) dfree(ctx, (void*)in.Sf);
+    in.S = b.Tnext;
+    in.S_owned = b.Tnext;
+    in.Sf = b.Fnext;
+    in.symb = 4;
+    in.soff = b.soff_next;
+    in.sid = b.sid_next;
+}
+
+// One round with a host synchronisation after the parse: the table is
+// regrown and the parse rerun until it fits, and all later sizes are exact.
+void round_sync(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32 i, bool against_resident, double& prev_ratio,
+                double& p_ratio) {
+    fail_if(ctx, i >= ctx->levels || i > kMaxRounds,
+            LCG_ELEVELS, "hash family too short: needs more than " + std::to_string(ctx->levels) + " functions");
+    if (R->lv.size() < i) R->lv.emplace_back();
+    lcg_round_stats& rs = ctx->stats.round[std::min<u32>(i - 1, 63)];
+    const u64 n = in.n;
+    rs.n = n;
+    rs.strings = in.kk;
+    RoundBufs b;
+    alloc_round(ctx, b, n, in.kk);
+    const u64 tiles = b.tiles;
+    ensure_lb(ctx, &ctx->lb1, &ctx->lb1_tiles, tiles, lb1_bytes(tiles));
+    Level& L = R->lv[i - 1];
+    RoundArgs a = round_args(ctx, R, in, b, i);
+    a.d_n = nullptr;
+    a.d_k = nullptr;
+    if (against_resident && L.g > 0) {
+        ensure_resident(ctx, R, i, L.g);
+        a.rtab_keys = L.rkeys;
+        a.rtab_vals = L.rvals;
+        a.rtab_cap = L.rcap;
+        a.rrhs = L.rhs;
+        a.rrhs_off = L.rhs_off;
+    }
+    // Phrase table: sized from the distinct/phrase ratio of this level in the
+    // context's previous build when there is one (load about 0.7, so that the
+    // table stays in L2), else from a generous guess; an overflowing table is
+    // regrown and the parse rerun.
+    const double hint = ctx->ratio_hint[std::min<u32>(i, 63)];
+    u64 cap;
+    if (hint > 0) {
+        const u64 P_est = std::min<u64>(b.Pmax, (u64)(ctx->p_hint[std::min<u32>(i, 63)] * (double)n) + 64);
+        cap = std::max<u64>(8192, (u64)(hint * (double)P_est / 0.7) + 1024);
+    } else {
+        const u64 P_est = std::min<u64>(b.Pmax, (u64)(p_ratio * 1.2 * (double)n) + 64);
+        const double ratio = (i == 1) ? 0.02 : std::min(1.0, std::max(prev_ratio * 2.0, 0.05));
+        cap = 2 * std::max<u64>(4096, std::min<u64>(P_est, (u64)(ratio * 1.3 * (double)P_est) + 1));
+    }
+    u32 retries = 0;
+    DevStatus st;
+    RoundCounts rc;
+    while (true) {
+        fail_if(ctx, cap > (kMaxRank + 1), LCG_ETABLE, "phrase table would exceed 2^31 slots");
+        alloc_table(ctx, b, cap);
+        ck(ctx, cudaMemsetAsync(a.ds, 0, sizeof(DevStatus), ctx->st), "reset counters");
+        set_table(a, b);
+        enqueue_parse(ctx, a, n);
+        ck(ctx, cudaMemcpyAsync(&rc, a.rc, sizeof(rc), cudaMemcpyDeviceToHost, ctx->st), "read counts");
+        ck(ctx, cudaMemcpyAsync(&st, a.ds, sizeof(st), cudaMemcpyDeviceToHost, ctx->st), "read status");
+        sync(ctx);
+        check_device_status(ctx, st);
+        if (!st.overflow) break;
+        free_table(ctx, b);
+        cap *= 4;
+        retries++;
+    }
+    const u64 P = rc.phrases;
+    rs.phrases = P;
+    fail_if(ctx, P > b.Pmax, LCG_EDEVICE, "round produced more phrases than its bound");
+    p_ratio = n ? (double)P / (double)n : 0.35;
+    rs.table_cap = cap;
+    rs.retries = retries;
+    const u64 g_new = st.claims, G_new = st.claim_len;
+    fail_if(ctx, L.g + g_new > kMaxRank, LCG_EOVERFLOW, "level with 2^31 rules or more");
+    rs.g = g_new;
+    rs.G = G_new;
+    prev_ratio = P ? (double)g_new / (double)P : 0.0;
+    record_hints(ctx, i, n, P, g_new, G_new);
+    grow_level(ctx, L, L.g + g_new, L.G + G_new);
+    if (against_resident) {
+        ensure_resident(ctx, R, i, L.g + g_new);
+        a.rtab_w_keys = L.rkeys;
+        a.rtab_w_vals = L.rvals;
+        a.rtab_w_cap = L.rcap;
+    } else {
+        L.rvalid = false;
+    }
+    alloc_naming(ctx, b, g_new);
+    a.g_base = L.g;
+    a.G_base = L.G;
+    a.cap_g = L.cap_g;
+    a.cap_G = L.cap_G;
+    a.rhs = L.rhs;
+    a.rhs_off = L.rhs_off;
+    a.F = L.F;
+    enqueue_naming(ctx, a, b, (double)g_new, (double)G_new, (double)P);
+    L.g += g_new;
+    L.G += G_new;
+    free_round(ctx, b);
+    next_input(ctx, in, b);
+    in.n = rc.n_next;
+    in.kk = (u32)rc.k_next;
+    ctx->stats.rounds = i;
+}
+
+// The rounds of a fresh build, enqueued without host synchronisation, with
+// every size planned from the context's previous build (phrases per symbol,
+// new rules per phrase, symbols per rule).  Kernels read the actual sizes from
+// the device and flag a round that outgrows its buffers.  Returns 0, or -1
+// when a round did not fit (the build must then be redone round by round);
+// `i` becomes the first round not yet run, and `in` its input.
+int rounds_async(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32& i) {
+    const u32 planned = std::min<u32>(ctx->hint_rounds, std::min<u32>(ctx->levels - 1, kMaxRounds));
+    u64 n_bound = in.n, n_est = in.n;
+    const u32 kk = in.kk;
+    std::vector<u64> g_base(planned + 1), G_base(planned + 1);
+    for (u32 r = 1; r <= planned; r++) {
+        if (R->lv.size() < r) R->lv.emplace_back();
+        Level& L = R->lv[r - 1];
+        RoundBufs b;
+        alloc_round(ctx, b, n_bound, kk);
+        ensure_lb(ctx, &ctx->lb1, &ctx->lb1_tiles, b.tiles, lb1_bytes(b.tiles));
+        RoundArgs a = round_args(ctx, R, in, b, r);
+        // a round stops early when the one before it failed
+        if (r > 1) a.ds_prev = ctx->ds_arr + (r - 2);
+        const double P_est = ctx->p_hint[r] * (double)n_est;
+        const double g_est = ctx->ratio_hint[r] * P_est;
+        const double G_est = ctx->glen_hint[r] * g_est;
+        const u64 cap = std::max<u64>(8192, (u64)(g_est * 1.1 / 0.7) + 1024);
+        alloc_table(ctx, b, std::min<u64>(cap, kMaxRank + 1));
+        set_table(a, b);
+        enqueue_parse(ctx, a, n_est);
+        const u64 g_alloc = (u64)(g_est * 1.25) + 1024;
+        grow_level(ctx, L, L.g + g_alloc, L.G + (u64)(G_est * 1.25) + 4096);
+        L.rvalid = false;
+        alloc_naming(ctx, b, g_alloc);
+        g_base[r] = L.g;
+        G_base[r] = L.G;
+        a.g_base = L.g;
+        a.G_base = L.G;
+        a.cap_g = L.cap_g;
+        a.cap_G = L.cap_G;
+        a.rhs = L.rhs;
+        a.rhs_off = L.rhs_off;
+        a.F = L.F;
+        enqueue_naming(ctx, a, b, g_est, G_est, P_est);
+        free_round(ctx, b);
+        next_input(ctx, in, b);
+        in.d_n = &a.rc->n_next;
+        in.d_k = &a.rc->k_next;
+        n_bound = b.Pmax;
+        n_est = (u64)P_est + 64;
+    }
+    std::vector<DevStatus> st(planned);
+    std::vector<RoundCounts> rc(planned);
+    ck(ctx, cudaMemcpyAsync(st.data(), ctx->ds_arr, planned * sizeof(DevStatus), cudaMemcpyDeviceToHost, ctx->st),
+       "read status");
+    ck(ctx, cudaMemcpyAsync(rc.data(), ctx->rc_arr, planned * sizeof(RoundCounts), cudaMemcpyDeviceToHost, ctx->st),
+       "read counts");
+    sync(ctx);
+    for (u32 r = 0; r < planned; r++) {
+        if (st[r].overflow || st[r].error == kErrCapacity || st[r].error == kErrHalted) return -1;
+        check_device_status(ctx, st[r]);
+    }
+    // rounds past the last active string (the data needed fewer rounds than
+    // the previous build) leave empty levels: drop them
+    u32 used = planned;
+    for (u32 r = 1; r <= planned; r++) {
+        const u64 k_in = (r == 1) ? kk : rc[r - 2].k_next;
+        if (k_in == 0) { used = r - 1; break; }
+    }
+    while (R->lv.size() > used && R->lv.back().g == 0 && g_base.size() > R->lv.size()) {
+        Level& L = R->lv.back();
+        if (st[R->lv.size() - 1].claims != 0) break;
+        dfree(ctx, L.rhs_off);
+        dfree(ctx, L.rhs);
+        dfree(ctx, L.F);
+        dfree(ctx, L.rkeys);
+        dfree(ctx, L.rvals);
+        R->lv.pop_back();
+    }
+    u64 n = in.n;
+    for (u32 r = 1; r <= used; r++) {
+        Level& L = R->lv[r - 1];
+        const DevStatus& s = st[r - 1];
+        const RoundCounts& c = rc[r - 1];
+        fail_if(ctx, L.g + s.claims > kMaxRank, LCG_EOVERFLOW, "level with 2^31 rules or more");
+        L.g = g_base[r] + s.claims;
+        L.G = G_base[r] + s.claim_len;
+        lcg_round_stats& rs = ctx->stats.round[r - 1];
+        rs.n = n;
+        rs.strings = (r == 1) ? kk : rc[r - 2].k_next;
+        rs.phrases = c.phrases;
+        rs.g = s.claims;
+        rs.G = s.claim_len;
+        record_hints(ctx, r, n, c.phrases, s.claims, s.claim_len);
+        n = c.n_next;
+        ctx->stats.rounds = r;
+    }
+    in.n = rc[planned - 1].n_next;
+    in.kk = (u32)rc[planned - 1].k_next;
+    in.d_n = nullptr;
+    in.d_k = nullptr;
+    i = planned + 1;
+    return 0;
+}
+
 void build_into(lcg_ctx* ctx, lcg_grammar* R, const uint8_t* data, const uint64_t* off, uint32_t k, int on_dev,
-                bool against_resident) {
+                bool against_resident, bool allow_async) {
     fail_if(ctx, k == 0 || off == nullptr || data == nullptr, LCG_EINVAL, "empty collection");
     fail_if(ctx, (u64)R->k + k > 0xffffffffull, LCG_EOVERFLOW, "too many strings");
     std::vector<u64> act_src, act_len, lvl0_pos;
@@ -382,257 +830,32 @@ void build_into(lcg_ctx* ctx, lcg_grammar* R, const uint8_t* data, const uint64_
         S = g;
         S_owned = g;
     }
-    int symb = 1;
-    const u32* Sf = nullptr;  // fingerprints of the round's symbols (rounds >= 2)
-    u64 n = n1;
-    double prev_ratio = 0.0;
-
-    double p_ratio = 0.35;  // phrases per symbol, from the previous round
-    for (u32 i = 1; kk > 0; i++) {
-        fail_if(ctx, i >= ctx->levels, LCG_ELEVELS, "hash family too short: needs more than " +
-                                                         std::to_string(ctx->levels) + " functions");
-        if (R->lv.size() < i) R->lv.emplace_back();
-        lcg_round_stats& rs = ctx->stats.round[std::min<u32>(i - 1, 63)];
-        rs.n = n;
-        rs.strings = kk;
-        const u64 tiles = (n + parse_tile_positions(symb) - 1) / parse_tile_positions(symb);
-        ensure_lb(ctx, &ctx->lb1, &ctx->lb1_tiles, tiles, lb1_bytes(tiles));
-        // every phrase but a string's first has length >= 2
-        const u64 Pmax = n / 2 + 2ull * kk + 1;
-        u64* string_first = dalloc<u64>(ctx, kk);
-        u64* soff_next = dalloc<u64>(ctx, kk + 1);
-        u32* sid_next = dalloc<u32>(ctx, kk);
-        u64* R_phr = dalloc<u64>(ctx, kk);
-        u32* R_sid = dalloc<u32>(ctx, kk);
-        u32* P_slot = dalloc<u32>(ctx, tiles * parse_tile_positions(symb));
-        u32* tile_cnt = dalloc<u32>(ctx, tiles);
-        u64* tile_pfx = dalloc<u64>(ctx, tiles);
-        u32* Tnext = dalloc<u32>(ctx, Pmax);
-        u32* Fnext = dalloc<u32>(ctx, Pmax);
-        u32* tile_str = dalloc<u32>(ctx, tiles);
-
-        Level& L = R->lv[i - 1];
-        RoundArgs a{};
-        a.sym_bytes = symb;
-        a.S = S;
-        a.Sf = Sf;
-        a.n = n;
-        a.soff = d_soff;
-        a.sid = d_sid;
-        a.k = kk;
-        a.Fprev = fprev_of(R, i);
-        a.lh = level_hash(ctx, i);
-        a.level = i;
-        a.string_first = string_first;
-        a.tile_str = tile_str;
-        a.tile_cnt = tile_cnt;
-        a.tile_pfx = tile_pfx;
-        a.lb1 = ctx->lb1;
-        a.ctr = ctx->ctr;
-        a.total = ctx->scratch;
-        a.ds = ctx->ds;
-        a.soff_next = soff_next;
-        a.sid_next = sid_next;
-        a.R_phr = R_phr;
-        a.R_sid = R_sid;
-        a.rc = ctx->rc;
-        a.P_slot = P_slot;
-        if (against_resident && L.g > 0) {
-            ensure_resident(ctx, R, i, L.g);
-            a.rtab_keys = L.rkeys;
-            a.rtab_vals = L.rvals;
-            a.rtab_cap = L.rcap;
-            a.rrhs = L.rhs;
-            a.rrhs_off = L.rhs_off;
+    RoundInput in{};
+    in.S = S;
+    in.S_owned = S_owned;
+    in.Sf = nullptr;
+    in.symb = 1;
+    in.n = n1;
+    in.kk = kk;
+    in.soff = d_soff;
+    in.sid = d_sid;
+    ck(ctx, cudaMemsetAsync(ctx->ds_arr, 0, kMaxRounds * sizeof(DevStatus), ctx->st), "reset status");
+    ck(ctx, cudaMemsetAsync(ctx->rc_arr, 0, kMaxRounds * sizeof(RoundCounts), ctx->st), "reset counts");
+    u32 i = 1;
+    if (allow_async && !against_resident && ctx->hint_rounds > 0) {
+        const int r = rounds_async(ctx, R, in, i);
+        if (r < 0) {
+            // a round outgrew its estimate: the caller starts again with synchronised rounds
+            free_round_input(ctx, in);
+            for (void* p : owned) dfree(ctx, p);
+            throw Retry{};
         }
-        // Phrase table: sized from the distinct/phrase ratio of this level in the
-        // context's previous build when there is one (load about 0.7, so that
-        // the table stays in L2), else from a generous guess; an overflowing
-        // table is regrown and the round rerun.
-        const double hint = ctx->ratio_hint[std::min<u32>(i, 63)];
-        u64 cap;
-        if (hint > 0) {
-            const u64 P_est = std::min<u64>(Pmax, (u64)(ctx->p_hint[std::min<u32>(i, 63)] * (double)n) + 64);
-            cap = std::max<u64>(8192, (u64)(hint * (double)P_est / 0.7) + 1024);
-        } else {
-            const u64 P_est = std::min<u64>(Pmax, (u64)(p_ratio * 1.2 * (double)n) + 64);
-            const double ratio = (i == 1) ? 0.02 : std::min(1.0, std::max(prev_ratio * 2.0, 0.05));
-            cap = 2 * std::max<u64>(4096, std::min<u64>(P_est, (u64)(ratio * 1.3 * (double)P_est) + 1));
-        }
-        u32 retries = 0;
-        DevStatus st;
-        RoundCounts rc;
-        const double w = (double)symb;
-        int h;
-        ck(ctx, launch_tile_strings(a, ctx->st), "k_tile_strings");
-        ctx->launches++;
-        unsigned char* tkeys = nullptr;
-        u64* tvals = nullptr;
-        u32* claims = nullptr;
-        while (true) {
-            fail_if(ctx, cap > (kMaxRank + 1), LCG_ETABLE, "phrase table would exceed 2^31 slots");
-            tkeys = dalloc<unsigned char>(ctx, cap * key_bytes());
-            tvals = dalloc<u64>(ctx, cap);
-            claims = dalloc<u32>(ctx, cap);
-            ck(ctx, cudaMemsetAsync(tkeys, 0xFF, cap * key_bytes(), ctx->st), "memset table");
-            ck(ctx, cudaMemsetAsync(tvals, 0xFF, cap * sizeof(u64), ctx->st), "memset table");
-            ck(ctx, cudaMemsetAsync((char*)ctx->ds + 4, 0, 4 + 16, ctx->st), "reset counters");
-            a.tab_keys = tkeys;
-            a.tab_vals = tvals;
-            a.tab_cap = cap;
-            a.claims = claims;
-            a.claim_limit = cap - cap / 5;
-            // T^i in, one phrase slot per phrase out (phrases estimated as n/3);
-            // one table sector per phrase when the table does not fit in L2
-            const double tab_bytes = cap * (double)(key_bytes() + sizeof(u64));
-            const double tbytes = tab_bytes > kL2Bytes ? 32.0 * (double)n / 3.0 : 0.0;
-            h = kt_begin(ctx, "k_parse", (symb == 1 ? 1.0 : 8.0) * n + 4.0 * (double)n / 3.0 + tbytes);
-            ck(ctx, launch_parse(a, ctx->st), "k_parse");
-            kt_end(ctx, h);
-            // global index of every tile's first phrase, and the round's phrase count
-            const u64 stiles = std::max<u64>(1, scan2_tiles_for(tiles));
-            ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, stiles, scan2_lb_bytes(stiles));
-            u64 grid = 0;
-            h = kt_begin(ctx, "k_scan2", 12.0 * tiles);
-            ck(ctx, launch_scan2(tile_cnt, nullptr, tiles, tile_pfx, nullptr, ctx->scratch, ctx->lb2, ++ctx->epoch,
-                                 ctx->ctr, ctx->ctr_val, ctx->ds, ctx->st, &grid),
-               "scan");
-            kt_end(ctx, h);
-            ctx->ctr_val += grid;
-            h = kt_begin(ctx, "k_strings", 40.0 * kk);
-            ck(ctx, launch_strings(a, ctx->st), "k_strings");
-            kt_end(ctx, h);
-            ctx->launches += 3;
-            ck(ctx, cudaMemcpyAsync(&rc, ctx->rc, sizeof(rc), cudaMemcpyDeviceToHost, ctx->st), "read counts");
-            st = read_status(ctx);
-            check_device_status(ctx, st);
-            if (!st.overflow) break;
-            dfree(ctx, tkeys);
-            dfree(ctx, tvals);
-            dfree(ctx, claims);
-            cap *= 4;
-            retries++;
-        }
-        const u64 P = rc.phrases;
-        rs.phrases = P;
-        // every phrase but a string's first has length >= 2 (Sec. 3.4)
-        fail_if(ctx, P > Pmax, LCG_EDEVICE, "round produced more phrases than its bound");
-        p_ratio = n ? (double)P / (double)n : 0.35;
-        rs.table_cap = cap;
-        rs.retries = retries;
-        const u64 g_new = st.claims, G_new = st.claim_len;
-        fail_if(ctx, L.g + g_new > kMaxRank, LCG_EOVERFLOW, "level with 2^31 rules or more");
-        rs.g = g_new;
-        rs.G = G_new;
-        prev_ratio = P ? (double)g_new / (double)P : 0.0;
-        if (i < 64) {
-            ctx->ratio_hint[i] = prev_ratio;
-            ctx->p_hint[i] = n ? (double)P / (double)n : 0.0;
-        }
-        grow_level(ctx, L, L.g + g_new, L.G + G_new);
-        if (against_resident) {
-            ensure_resident(ctx, R, i, L.g + g_new);
-            a.rtab_w_keys = L.rkeys;
-            a.rtab_w_vals = L.rvals;
-            a.rtab_w_cap = L.rcap;
-        } else {
-            L.rvalid = false;
-        }
-        // first-occurrence naming of the new phrases
-        const u64 nw = tiles * parse_tile_positions(symb) / 32;  // order keys tile * TP + q
-        u32* first_bits = dalloc<u32>(ctx, nw);
-        u32* first_prefix = dalloc<u32>(ctx, nw);
-        u32* slot_r = dalloc<u32>(ctx, g_new);
-        u32* len_r = dalloc<u32>(ctx, g_new);
-        u64* xlen = dalloc<u64>(ctx, g_new);
-        a.P = P;
-        a.first_bits = first_bits;
-        a.first_prefix = first_prefix;
-        a.slot_r = slot_r;
-        a.len_r = len_r;
-        a.xlen = xlen;
-        a.g_base = L.g;
-        a.G_base = L.G;
-        a.G_new = G_new;
-        a.rhs = L.rhs;
-        a.rhs_off = L.rhs_off;
-        a.F = L.F;
-        a.Tnext = Tnext;
-        a.Fnext = Fnext;
-        a.c_level = R->c_level;
-        a.c_rank = R->c_rank;
-        if (g_new > 0) {
-            ck(ctx, cudaMemsetAsync(first_bits, 0, nw * sizeof(u32), ctx->st), "memset bits");
-            h = kt_begin(ctx, "k_mark", 12.0 * g_new);
-            ck(ctx, launch_mark(a, g_new, ctx->st), "k_mark");
-            kt_end(ctx, h);
-            const u64 ptiles = popscan_tiles_for(nw);
-            ensure_lb(ctx, &ctx->lb1, &ctx->lb1_tiles, ptiles, lb1_bytes(ptiles));
-            a.lb1 = ctx->lb1;
-            a.epoch = ++ctx->epoch;
-            a.ctr_base = ctx->ctr_val;
-            ctx->ctr_val += ptiles;
-            h = kt_begin(ctx, "k_popscan", 8.0 * nw);
-            ck(ctx, launch_popscan(a, nw, ctx->st), "k_popscan");
-            kt_end(ctx, h);
-            h = kt_begin(ctx, "k_rank", 24.0 * g_new);
-            ck(ctx, launch_rank(a, g_new, ctx->st), "k_rank");
-            kt_end(ctx, h);
-            const u64 stiles = std::max<u64>(1, scan2_tiles_for(g_new));
-            ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, stiles, scan2_lb_bytes(stiles));
-            u64 grid = 0;
-            h = kt_begin(ctx, "k_scan2", 12.0 * g_new);
-            ck(ctx, launch_scan2(len_r, nullptr, g_new, xlen, nullptr, ctx->scratch + 1, ctx->lb2, ++ctx->epoch,
-                                 ctx->ctr, ctx->ctr_val, ctx->ds, ctx->st, &grid),
-               "scan");
-            kt_end(ctx, h);
-            ctx->ctr_val += grid;
-            h = kt_begin(ctx, "k_rules", 4.0 * G_new + 12.0 * g_new);
-            ck(ctx, launch_rules(a, g_new, ctx->st), "k_rules");
-            kt_end(ctx, h);
-            ctx->launches += 5;
-        }
-        h = kt_begin(ctx, "k_rewrite", 4.0 * P + 8.0 * rc.n_next);
-        ck(ctx, launch_rewrite(a, ctx->st), "k_rewrite");
-        kt_end(ctx, h);
-        ctx->launches += 1;
-        L.g += g_new;
-        L.G += G_new;
-
-        dfree(ctx, first_bits);
-        dfree(ctx, first_prefix);
-        dfree(ctx, slot_r);
-        dfree(ctx, len_r);
-        dfree(ctx, xlen);
-        dfree(ctx, tkeys);
-        dfree(ctx, tvals);
-        dfree(ctx, claims);
-        dfree(ctx, string_first);
-        dfree(ctx, tile_str);
-        dfree(ctx, tile_cnt);
-        dfree(ctx, tile_pfx);
-        dfree(ctx, P_slot);
-        dfree(ctx, R_phr);
-        dfree(ctx, R_sid);
-        dfree(ctx, d_soff);
-        dfree(ctx, d_sid);
-        if (S_owned) dfree(ctx, S_owned);
-        if (Sf) dfree(ctx, (void*)Sf);
-        S = Tnext;
-        S_owned = Tnext;
-        Sf = Fnext;
-        symb = 4;
-        n = rc.n_next;
-        kk = (u32)rc.k_next;
-        d_soff = soff_next;
-        d_sid = sid_next;
-        ctx->stats.rounds = i;
     }
+    double prev_ratio = 0.0, p_ratio = 0.35;
+    for (; in.kk > 0; i++) round_sync(ctx, R, in, i, against_resident, prev_ratio, p_ratio);
     check_device_status(ctx, read_status(ctx));
-    dfree(ctx, d_soff);
-    dfree(ctx, d_sid);
-    if (S_owned) dfree(ctx, S_owned);
-    if (Sf) dfree(ctx, (void*)Sf);
+    ctx->hint_rounds = ctx->stats.rounds;
+    free_round_input(ctx, in);
     for (void* p : owned) dfree(ctx, p);
     ctx->stats.kernel_launches = ctx->launches - launches0;
 }
@@ -916,6 +1139,9 @@ int lcg_ctx_create(int device, const lcg_hash_family* H, void* stream, lcg_ctx**
         ck(ctx, cudaMalloc(&ctx->rc, sizeof(RoundCounts)), "cudaMalloc");
         ck(ctx, cudaMalloc(&ctx->ctr, sizeof(u64)), "cudaMalloc");
         ck(ctx, cudaMalloc(&ctx->scratch, 8 * sizeof(u64)), "cudaMalloc");
+        ck(ctx, cudaMalloc(&ctx->ds_arr, kMaxRounds * sizeof(DevStatus)), "cudaMalloc");
+        ck(ctx, cudaMalloc(&ctx->rc_arr, kMaxRounds * sizeof(RoundCounts)), "cudaMalloc");
+        ck(ctx, cudaMalloc(&ctx->tot_arr, 3 * kMaxRounds * sizeof(u64)), "cudaMalloc");
         ck(ctx, cudaMemset(ctx->ds, 0, sizeof(DevStatus)), "memset");
         ck(ctx, cudaMemset(ctx->ctr, 0, sizeof(u64)), "memset");
         ck(ctx, cudaMemset(ctx->scratch, 0, 8 * sizeof(u64)), "memset");
@@ -943,6 +1169,9 @@ void lcg_ctx_destroy(lcg_ctx* ctx) {
     cudaFree(ctx->rc);
     cudaFree(ctx->ctr);
     cudaFree(ctx->scratch);
+    cudaFree(ctx->ds_arr);
+    cudaFree(ctx->rc_arr);
+    cudaFree(ctx->tot_arr);
     if (ctx->own_stream && ctx->st) cudaStreamDestroy(ctx->st);
     delete ctx;
 }
@@ -977,7 +1206,17 @@ int lcg_build(lcg_ctx* ctx, const uint8_t* data, const uint64_t* offsets, uint32
     ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
     kt_reset(ctx);
     G = new_grammar(ctx);
-    build_into(ctx, G, data, offsets, k, data_on_device, false);
+    try {
+        build_into(ctx, G, data, offsets, k, data_on_device, false, true);
+    } catch (const Retry&) {
+        // the rounds planned from the previous build did not fit: round by round
+        sync(ctx);
+        free_grammar_now(G);
+        G = nullptr;
+        kt_reset(ctx);
+        G = new_grammar(ctx);
+        build_into(ctx, G, data, offsets, k, data_on_device, false, false);
+    }
     sync(ctx);
     kt_collect(ctx);
     *out = G;
@@ -1006,7 +1245,7 @@ int lcg_build_into(lcg_ctx* ctx, lcg_grammar* resident, const uint8_t* data, con
     LCG_GUARD_BEGIN
     ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
     kt_reset(ctx);
-    build_into(ctx, resident, data, offsets, k, data_on_device, true);
+    build_into(ctx, resident, data, offsets, k, data_on_device, true, false);
     sync(ctx);
     kt_collect(ctx);
     return LCG_OK;

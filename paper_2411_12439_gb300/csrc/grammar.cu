@@ -17,8 +17,10 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 __global__ void __launch_bounds__(kScanThreads) k_scan2(const u32* __restrict__ in0, const u32* __restrict__ in1,
                                                         u64 n, u64* __restrict__ out0, u64* __restrict__ out1,
                                                         u64* __restrict__ totals, LBSlot<2>* lb, u64 epoch, u64* ctr,
-                                                        u64 ctr_base, DevStatus* ds) {
+                                                        u64 ctr_base, DevStatus* ds, const u64* n_dev) {
     const u64 tile = dynamic_tile(ctr, ctr_base);
+    if (n_dev != nullptr) n = min(*n_dev, n);
+    if (tile > 0 && tile * (u64)kScanTile >= n) return;  // beyond the count read on the device
     const u64 p0 = tile * (u64)kScanTile + (u64)threadIdx.x * kScanItems;
     u32 a[kScanItems], b[kScanItems];
     u64 sa = 0, sb = 0;
@@ -57,12 +59,13 @@ u64 scan2_tiles_for(u64 n) { return (n + kScanTile - 1) / kScanTile; }
 size_t scan2_lb_bytes(u64 tiles) { return scan2_lb_bytes_static(tiles); }
 
 cudaError_t launch_scan2(const u32* in0, const u32* in1, u64 n, u64* out0, u64* out1, u64* totals, void* lb,
-                         u64 epoch, u64* ctr, u64 ctr_base, DevStatus* ds, cudaStream_t st, u64* grid_out) {
+                         u64 epoch, u64* ctr, u64 ctr_base, DevStatus* ds, cudaStream_t st, u64* grid_out,
+                         const u64* n_dev) {
     u64 tiles = scan2_tiles_for(n);
     if (tiles == 0) tiles = 1;
     *grid_out = tiles;
     k_scan2<<<(unsigned)tiles, kScanThreads, 0, st>>>(in0, in1, n, out0, out1, totals, (LBSlot<2>*)lb, epoch, ctr,
-                                                      ctr_base, ds);
+                                                      ctr_base, ds, n_dev);
     return cudaGetLastError();
 }
 

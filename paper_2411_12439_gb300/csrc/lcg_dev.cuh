@@ -65,6 +65,8 @@ enum DevError : u32 {
     kErrPhraseLong = 3,   // a phrase of >= 2^32 symbols
     kErrMismatch = 4,     // equal right-hand sides with different fingerprints
     kErrRankOverflow = 5, // a level with >= 2^32 rules
+    kErrCapacity = 6,     // a round outgrew the buffers it was given (rounds enqueued without a sync)
+    kErrHalted = 7,       // an earlier round failed; this one did no work
 };
 
 struct DevStatus {

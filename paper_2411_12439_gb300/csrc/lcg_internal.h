@@ -16,20 +16,26 @@ struct RoundCounts {
     u64 retired;  // strings that became one symbol
     u64 k_next;   // strings still active
     u64 n_next;   // |T^{i+1}|
+    u64 tiles;    // parse tiles of the round
+    u64 pad[3];
 };
 
 struct RoundArgs {
     int sym_bytes;        // 1 in round 1 (bytes), 4 afterwards (ranks)
     const void* S;        // T^i
     const u32* Sf;        // fingerprints of T^i (rounds >= 2)
-    u64 n;                // |T^i|
+    u64 n;                // |T^i| (when d_n is null)
+    const u64* d_n;       // |T^i| on the device (rounds enqueued without a host sync), or null
     const u64* soff;      // k+1 string offsets into T^i
     const u32* sid;       // original string index of each active string
-    u32 k;
+    u32 k;                // active strings (when d_k is null)
+    const u64* d_k;       // active strings on the device, or null
     const u32* Fprev;     // F^{i-1}
     LevelHash lh;         // parameters of h^i
     u32 level;            // i
     // parse pass
+    u64 tiles_bound;      // parse tiles the buffers were sized for
+    u64* d_tiles;         // parse tiles of the round (written by k_tile_strings)
     u32* tile_str;        // per parse tile: the string holding its first position
     u32* tile_cnt;        // per parse tile: phrases starting in it
     u64* tile_pfx;        // exclusive prefix of tile_cnt: global index of a tile's first phrase
@@ -58,15 +64,19 @@ struct RoundArgs {
     u64* R_phr;
     u32* R_sid;
     RoundCounts* rc;
+    const DevStatus* ds_prev;  // status of the round before (rounds enqueued without a sync), or null
     // naming pass
-    u64 P;                // phrases (host copy)
+    const u64* d_gnew;    // new rules of the round (device: the claim count)
+    const u64* d_Gnew;    // their total length (device)
+    u64 g_alloc;          // entries of slot_r, len_r, xlen
+    u64 cap_g, cap_G;     // capacity of the level's arrays
     u32* first_bits;      // bitmap over phrase indices
     u32* first_prefix;    // exclusive popcount prefix of its words
     u32* slot_r;          // slot of the rank-r new rule
     u32* len_r;           // its length
     u64* xlen;            // exclusive prefix of len_r
     u64 g_base, G_base;   // rules / rhs symbols of level i before this round
-    u64 G_new;            // rhs symbols of the new rules
+
     u32* rhs;
     u64* rhs_off;
     u32* F;
@@ -74,6 +84,7 @@ struct RoundArgs {
     u64* rtab_w_vals;
     u64 rtab_w_cap;
     // rewrite pass
+    u64 T_cap;            // entries of Tnext / Fnext
     u32* Tnext;
     u32* Fnext;           // fingerprints of T^{i+1}
     u32* c_level;
@@ -89,10 +100,10 @@ size_t key_bytes();
 cudaError_t launch_tile_strings(const RoundArgs& a, cudaStream_t st);
 cudaError_t launch_parse(const RoundArgs& a, cudaStream_t st);
 cudaError_t launch_strings(const RoundArgs& a, cudaStream_t st);
-cudaError_t launch_mark(const RoundArgs& a, u64 g_new, cudaStream_t st);
-cudaError_t launch_popscan(const RoundArgs& a, u64 nw, cudaStream_t st);
-cudaError_t launch_rank(const RoundArgs& a, u64 g_new, cudaStream_t st);
-cudaError_t launch_rules(const RoundArgs& a, u64 g_new, cudaStream_t st);
+cudaError_t launch_mark(const RoundArgs& a, u64 g_grid, cudaStream_t st);
+cudaError_t launch_popscan(const RoundArgs& a, u64 nw_bound, cudaStream_t st);
+cudaError_t launch_rank(const RoundArgs& a, u64 g_grid, cudaStream_t st);
+cudaError_t launch_rules(const RoundArgs& a, u64 g_grid, cudaStream_t st);
 cudaError_t launch_rewrite(const RoundArgs& a, cudaStream_t st);
 cudaError_t launch_level0(const unsigned char* data, const u64* pos, const u32* ids, u32 cnt, u32* c_level,
                           u32* c_rank, cudaStream_t st);
@@ -116,8 +127,11 @@ cudaError_t launch_rule_lens(const u32* cur, u64 cnt, const u64* rhs_off, u32* l
 cudaError_t launch_expand(const u32* cur, u64 cnt, const u64* offs, const u64* rhs_off, const u32* rhs, u32* next,
                           cudaStream_t st);
 cudaError_t launch_to_bytes(const u32* cur, u64 cnt, unsigned char* out, cudaStream_t st);
+// Exclusive scan of n elements; when n_dev is given the count is min(*n_dev, n)
+// read on the device (n then only bounds the grid).
 cudaError_t launch_scan2(const u32* in0, const u32* in1, u64 n, u64* out0, u64* out1, u64* totals, void* lb,
-                         u64 epoch, u64* ctr, u64 ctr_base, DevStatus* ds, cudaStream_t st, u64* grid_out);
+                         u64 epoch, u64* ctr, u64 ctr_base, DevStatus* ds, cudaStream_t st, u64* grid_out,
+                         const u64* n_dev = nullptr);
 u64 scan2_tiles_for(u64 n);
 size_t scan2_lb_bytes(u64 tiles);
 constexpr size_t scan2_lb_bytes_static(u64 tiles) { return tiles * sizeof(LBSlot<2>); }

@@ -39,6 +39,27 @@ struct FpSource<u32> {
     __device__ __forceinline__ u32 operator()(u32 s) const { return __ldg(F + s); }
 };
 
+// Sizes of a round: from the device when the round was enqueued without a
+// host synchronisation, else from the arguments.
+__device__ __forceinline__ u64 round_n(const RoundArgs& a) { return a.d_n ? *a.d_n : a.n; }
+__device__ __forceinline__ u32 round_k(const RoundArgs& a) { return a.d_k ? (u32)*a.d_k : a.k; }
+
+// A round stops as soon as it, or the round before it, has failed (an error,
+// or a phrase table past its load limit): its inputs and buffers can no longer
+// be trusted, and the host discards or reruns it.  Called by every thread of a
+// block; the answer is the same for the whole block.
+__device__ bool round_halted(const RoundArgs& a) {
+    __shared__ int s_halt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool h = vload(&a.ds->error) != 0 || vload(&a.ds->overflow) != 0;
+        if (a.ds_prev) h = h || vload(&a.ds_prev->error) != 0 || vload(&a.ds_prev->overflow) != 0;
+        s_halt = h ? 1 : 0;
+    }
+    __syncthreads();
+    return s_halt != 0;
+}
+
 // index of the string holding position `pos`: largest j with soff[j] <= pos
 __device__ __forceinline__ u32 string_of(const u64* soff, u32 k, u64 pos) {
     u32 lo = 0, hi = k;  // answer in [lo, hi)
@@ -159,7 +180,9 @@ __global__ void __launch_bounds__(kParseThreads) k_parse(const RoundArgs a, u64 
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const T* S = (const T*)a.S;
-    const u64 n = a.n;
+    const u64 n = round_n(a);
+    const u32 kact = round_k(a);
+    ntiles = min(ntiles, (n + kTP - 1) / kTP);
     FpSource<T> fp;
     if constexpr (kByte) {
         for (int x = tid; x < 256; x += kParseThreads) sF0[x] = a.Fprev[x];
@@ -180,6 +203,7 @@ __global__ void __launch_bounds__(kParseThreads) k_parse(const RoundArgs a, u64 
     // do not depend on one another.
     u64 iter = 0;
     for (u64 tile = blockIdx.x; tile < ntiles; tile += gridDim.x, iter++) {
+        if (round_halted(a)) break;
         for (int w = tid; w < NWS + 1; w += kParseThreads) {
             sstart[w] = 0;
             if (w < NWS) sbits[w] = 0;
@@ -209,9 +233,9 @@ __global__ void __launch_bounds__(kParseThreads) k_parse(const RoundArgs a, u64 
             u32 jj = j0 + lane;
             bool more = true;
             while (more) {
-                const u64 s = (jj <= a.k) ? __ldg(a.soff + jj) : ~0ull;
+                const u64 s = (jj <= kact) ? __ldg(a.soff + jj) : ~0ull;
                 if (s >= t0 && s <= s_end) atomicOr(&sstart[(s - t0) >> 5], 1u << ((s - t0) & 31));
-                more = __shfl_sync(0xffffffffu, (jj <= a.k && s <= s_end) ? 1u : 0u, 31) != 0;
+                more = __shfl_sync(0xffffffffu, (jj <= kact && s <= s_end) ? 1u : 0u, 31) != 0;
                 jj += 32;
             }
         }
@@ -240,7 +264,7 @@ __global__ void __launch_bounds__(kParseThreads) k_parse(const RoundArgs a, u64 
                         if (y < ns) nd = is_start(y) ? kNone : (u64)fat(y);
                         else if (s_end == n || is_start(ns)) nd = kNone;
                         else {
-                            const u32 jl = string_of(a.soff, a.k, t0 + x);
+                            const u32 jl = string_of(a.soff, kact, t0 + x);
                             nd = scan_right_diff<T>(S, fp, s_end, __ldg(a.soff + jl + 1), cur);
                         }
                         brk = (nd != kNone) && (nd > (u64)cur);
@@ -280,7 +304,7 @@ __global__ void __launch_bounds__(kParseThreads) k_parse(const RoundArgs a, u64 
                 if (w == (nt >> 5)) m &= ~((1u << (nt & 31)) - 1u);
                 if (m) { e = t0 + (u64)(w * 32 + __ffs(m) - 1); found = true; }
             }
-            if (!found) e = (s_end == n) ? n : global_next_break<T>(S, fp, n, a.soff, a.k, s_end);
+            if (!found) e = (s_end == n) ? n : global_next_break<T>(S, fp, n, a.soff, kact, s_end);
             s_tail_end = e;
         }
         __syncthreads();
@@ -394,12 +418,12 @@ __global__ void __launch_bounds__(kParseThreads) k_parse(const RoundArgs a, u64 
         if (tid == 0) a.tile_cnt[tile] = cntq;
         if (warp == 0) {
             for (u32 jj = j0 + lane;; jj += 32) {
-                const u64 s = (jj < a.k) ? __ldg(a.soff + jj) : ~0ull;
+                const u64 s = (jj < kact) ? __ldg(a.soff + jj) : ~0ull;
                 if (s >= t0 && s < t_end) {
                     const int x = (int)(s - t0);
                     a.string_first[jj] = okey0 + swp[x >> 5] + __popc(sbits[x >> 5] & ((1u << (x & 31)) - 1u));
                 }
-                if (__shfl_sync(0xffffffffu, (jj < a.k && s < t_end) ? 1u : 0u, 31) == 0) break;
+                if (__shfl_sync(0xffffffffu, (jj < kact && s < t_end) ? 1u : 0u, 31) == 0) break;
             }
         }
         // 6. this tile's new entries join the round's claim list
@@ -422,8 +446,20 @@ __global__ void __launch_bounds__(kParseThreads) k_parse(const RoundArgs a, u64 
 
 // Per parse tile: the string that holds its first position.
 __global__ void k_tile_strings(const RoundArgs a, u64 tiles) {
+    const u64 n = round_n(a);
+    const u32 k = round_k(a);
+    const u64 nt = (n + kTP - 1) / kTP;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *a.d_tiles = nt;
+        if (a.ds_prev && (vload(&a.ds_prev->error) != 0 || vload(&a.ds_prev->overflow) != 0))
+            set_error(a.ds, kErrHalted);
+        else if (nt > tiles)
+            set_error(a.ds, kErrCapacity);
+    }
+    if (round_halted(a)) return;
+    tiles = min(tiles, nt);
     for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < tiles; t += (u64)gridDim.x * blockDim.x)
-        a.tile_str[t] = string_of(a.soff, a.k, t * (u64)kTP);
+        a.tile_str[t] = string_of(a.soff, k, t * (u64)kTP);
 }
 
 // --------------------------------------------------------------------------
@@ -431,8 +467,9 @@ __global__ void k_tile_strings(const RoundArgs a, u64 tiles) {
 // --------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(1024) k_strings(const RoundArgs a) {
+    if (round_halted(a)) return;
     const u64 P = *a.total;
-    const u32 k = a.k;
+    const u32 k = round_k(a);
     u64 carry = 0;
     for (u32 j0 = 0; j0 < k; j0 += blockDim.x) {
         const u32 j = j0 + threadIdx.x;
@@ -471,9 +508,27 @@ __global__ void __launch_bounds__(1024) k_strings(const RoundArgs a) {
 // --------------------------------------------------------------------------
 
 // Mark the first occurrence of every new phrase in a bitmap over phrase indices.
-__global__ void k_mark(const RoundArgs a, u64 g_new) {
+// Number of new rules of the round, bounded by the naming arrays.
+__device__ __forceinline__ u64 round_gnew(const RoundArgs& a) {
+    const u64 g = *a.d_gnew;
+    if (g > a.g_alloc) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_error(a.ds, kErrCapacity);
+        return a.g_alloc;
+    }
+    return g;
+}
+
+__global__ void k_mark(const RoundArgs a) {
+    if (round_halted(a)) return;
+    const u64 g_new = round_gnew(a);
+    const u64 keys = a.tiles_bound * (u64)kTP;  // order keys the bitmap covers
     for (u64 c = blockIdx.x * (u64)blockDim.x + threadIdx.x; c < g_new; c += (u64)gridDim.x * blockDim.x) {
-        const u64 m = a.tab_vals[a.claims[c]];
+        const u32 s = a.claims[c];
+        const u64 m = s < a.tab_cap ? a.tab_vals[s] : ~0ull;
+        if (m >= keys) {
+            set_error(a.ds, kErrCapacity);
+            continue;
+        }
         atomicOr(a.first_bits + (m >> 5), 1u << (m & 31));
     }
 }
@@ -485,6 +540,8 @@ constexpr int kPopTile = kPopThreads * kPopItems;
 // Exclusive prefix of the popcounts of the bitmap words (single pass).
 __global__ void __launch_bounds__(kPopThreads) k_popscan(const RoundArgs a, u64 nw) {
     const u64 tile = dynamic_tile(a.ctr, a.ctr_base);
+    nw = min(nw, *a.d_tiles * (u64)(kTP / 32));
+    if (tile > 0 && tile * (u64)kPopTile >= nw) return;  // beyond the count read on the device
     const u64 w0 = tile * (u64)kPopTile + (u64)threadIdx.x * kPopItems;
     u32 c[kPopItems];
     u64 sum = 0;
@@ -506,12 +563,15 @@ __global__ void __launch_bounds__(kPopThreads) k_popscan(const RoundArgs a, u64 
 }
 
 // Rank of every new phrase: the marks before its first occurrence.
-__global__ void k_rank(const RoundArgs a, u64 g_new) {
+__global__ void k_rank(const RoundArgs a) {
+    if (round_halted(a)) return;
+    const u64 g_new = round_gnew(a);
     for (u64 c = blockIdx.x * (u64)blockDim.x + threadIdx.x; c < g_new; c += (u64)gridDim.x * blockDim.x) {
         const u32 s = a.claims[c];
         const u64 m = a.tab_vals[s];
         const u32 w = (u32)(m >> 5);
         const u64 r = a.first_prefix[w] + __popc(a.first_bits[w] & ((1u << (m & 31)) - 1u));
+        if (r >= g_new) { set_error(a.ds, kErrCapacity); continue; }
         a.tab_vals[s] = a.g_base + r;
         a.slot_r[r] = s;
         a.len_r[r] = (u32)key_len(((const Key128*)a.tab_keys)[s]);
@@ -522,12 +582,24 @@ __global__ void k_rank(const RoundArgs a, u64 g_new) {
 // (Eq. fast_hash over F^{i-1}).  When the grammar keeps a table of its rules,
 // the new rules enter it.
 template <typename T>
-__global__ void k_rules(const RoundArgs a, u64 g_new) {
+__global__ void k_rules(const RoundArgs a) {
     constexpr bool kByte = sizeof(T) == 1;
     const T* S = (const T*)a.S;
     const ContentTable rw{(Key128*)a.rtab_w_keys, a.rtab_w_vals, a.rtab_w_cap};
+    if (round_halted(a)) return;
+    const u64 g_new = round_gnew(a);
+    const u64 G_new = *a.d_Gnew;
+    if (a.g_base + g_new > a.cap_g || a.G_base + G_new > a.cap_G) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_error(a.ds, kErrCapacity);
+        return;
+    }
     for (u64 r = blockIdx.x * (u64)blockDim.x + threadIdx.x; r < g_new; r += (u64)gridDim.x * blockDim.x) {
-        const Key128 k = ((const Key128*)a.tab_keys)[a.slot_r[r]];
+        const u32 slot = a.slot_r[r];
+        if (slot >= a.tab_cap) {
+            set_error(a.ds, kErrCapacity);
+            continue;
+        }
+        const Key128 k = ((const Key128*)a.tab_keys)[slot];
         const u64 len = key_len(k);
         const bool hashed = key_is_hashed(k);
         const u64 off = a.G_base + a.xlen[r];
@@ -542,9 +614,9 @@ __global__ void k_rules(const RoundArgs a, u64 g_new) {
         }
         const u32 fpv = finish_hash(a.lh, H);
         a.F[rank] = fpv;
-        a.tab_vals[a.slot_r[r]] = ((u64)fpv << 32) | rank;  // for the rewrite: rank and fingerprint
+        a.tab_vals[slot] = ((u64)fpv << 32) | rank;  // for the rewrite: rank and fingerprint
         if (rw.cap) table_put(rw, hashed ? key_hashed(H, len, rank) : k, rank, a.ds);
-        if (r == 0) a.rhs_off[a.g_base + g_new] = a.G_base + a.G_new;
+        if (r == 0) a.rhs_off[a.g_base + g_new] = a.G_base + G_new;
     }
 }
 
@@ -562,12 +634,16 @@ __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) 
     // few entries take most phrases.  Both words carry the slot as a tag.
     __shared__ u64 c_rank[kRankCache];
     __shared__ u64 c_fp[kRankCache];
+    if (round_halted(a)) return;
     for (int x = threadIdx.x; x < kRankCache; x += blockDim.x) {
         c_rank[x] = ~0ull;
         c_fp[x] = ~0ull;
     }
     __syncthreads();
     const u64 nr = a.rc->retired;
+    ntiles = min(ntiles, *a.d_tiles);
+    // ranks of the level after this round (never past its arrays)
+    const u64 g_total = min(a.g_base + *a.d_gnew, a.cap_g);
     for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const u32 cnt = a.tile_cnt[t];
         const u64 pbase = a.tile_pfx[t];
@@ -575,7 +651,10 @@ __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) 
             const u64 p = pbase + q;
             const u32 s = a.P_slot[t * (u64)kTP + q];
             u32 r, f;
-            if (s & kResidentBit) {
+            if (s == ~0u) {  // the round's table overflowed: the round is discarded
+                r = 0;
+                f = 0;
+            } else if (s & kResidentBit) {
                 r = s & ~kResidentBit;
                 f = __ldg(a.F + r);
             } else {
@@ -592,6 +671,10 @@ __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) 
                     c_fp[ci] = ((u64)s << 32) | f;
                 }
             }
+            if (r >= g_total) {  // an entry that got no rank: only after a capacity error
+                set_error(a.ds, kErrCapacity);
+                r = 0;
+            }
             u64 out = p;
             if (nr != 0) {
                 u64 lo = 0, hi = nr;  // first index with R_phr >= p
@@ -605,6 +688,10 @@ __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) 
                     continue;
                 }
                 out = p - lo;
+            }
+            if (out >= a.T_cap) {
+                set_error(a.ds, kErrCapacity);
+                continue;
             }
             a.Tnext[out] = r;
             a.Fnext[out] = f;
@@ -666,8 +753,7 @@ u64 parse_tile_positions(int) { return (u64)kTP; }
 u64 popscan_tiles_for(u64 nw) { return (nw + kPopTile - 1) / kPopTile; }
 
 cudaError_t launch_tile_strings(const RoundArgs& a, cudaStream_t st) {
-    const u64 tiles = (a.n + kTP - 1) / kTP;
-    k_tile_strings<<<grid_for(tiles), 256, 0, st>>>(a, tiles);
+    k_tile_strings<<<grid_for(a.tiles_bound), 256, 0, st>>>(a, a.tiles_bound);
     return cudaGetLastError();
 }
 
@@ -686,7 +772,7 @@ static unsigned persistent_grid(u64 tiles) {
 }
 
 cudaError_t launch_parse(const RoundArgs& a, cudaStream_t st) {
-    const u64 tiles = (a.n + kTP - 1) / kTP;
+    const u64 tiles = a.tiles_bound;
     if (a.sym_bytes == 1) k_parse<unsigned char><<<persistent_grid<unsigned char>(tiles), kParseThreads, 0, st>>>(a, tiles);
     else k_parse<u32><<<persistent_grid<u32>(tiles), kParseThreads, 0, st>>>(a, tiles);
     return cudaGetLastError();
@@ -697,36 +783,32 @@ cudaError_t launch_strings(const RoundArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_mark(const RoundArgs& a, u64 g_new, cudaStream_t st) {
-    if (g_new == 0) return cudaSuccess;
-    k_mark<<<grid_for(g_new), 256, 0, st>>>(a, g_new);
+cudaError_t launch_mark(const RoundArgs& a, u64 g_grid, cudaStream_t st) {
+    k_mark<<<grid_for(g_grid), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_popscan(const RoundArgs& a, u64 nw, cudaStream_t st) {
-    const u64 tiles = popscan_tiles_for(nw);
-    if (tiles == 0) return cudaSuccess;
-    k_popscan<<<(unsigned)tiles, kPopThreads, 0, st>>>(a, nw);
+cudaError_t launch_popscan(const RoundArgs& a, u64 nw_bound, cudaStream_t st) {
+    u64 tiles = popscan_tiles_for(nw_bound);
+    if (tiles == 0) tiles = 1;
+    k_popscan<<<(unsigned)tiles, kPopThreads, 0, st>>>(a, nw_bound);
     return cudaGetLastError();
 }
 
-cudaError_t launch_rank(const RoundArgs& a, u64 g_new, cudaStream_t st) {
-    if (g_new == 0) return cudaSuccess;
-    k_rank<<<grid_for(g_new), 256, 0, st>>>(a, g_new);
+cudaError_t launch_rank(const RoundArgs& a, u64 g_grid, cudaStream_t st) {
+    k_rank<<<grid_for(g_grid), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_rules(const RoundArgs& a, u64 g_new, cudaStream_t st) {
-    if (g_new == 0) return cudaSuccess;
-    if (a.sym_bytes == 1) k_rules<unsigned char><<<grid_for(g_new), 256, 0, st>>>(a, g_new);
-    else k_rules<u32><<<grid_for(g_new), 256, 0, st>>>(a, g_new);
+cudaError_t launch_rules(const RoundArgs& a, u64 g_grid, cudaStream_t st) {
+    if (a.sym_bytes == 1) k_rules<unsigned char><<<grid_for(g_grid), 256, 0, st>>>(a);
+    else k_rules<u32><<<grid_for(g_grid), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_rewrite(const RoundArgs& a, cudaStream_t st) {
-    if (a.P == 0) return cudaSuccess;
-    const u64 tiles = (a.n + kTP - 1) / kTP;
-    const u64 g = tiles < 152ull * 8 ? tiles : 152ull * 8;
+    const u64 tiles = a.tiles_bound;
+    const u64 g = tiles < 152ull * 8 ? (tiles ? tiles : 1) : 152ull * 8;
     k_rewrite<<<(unsigned)g, 256, 0, st>>>(a, tiles);
     return cudaGetLastError();
 }

@@ -157,3 +157,22 @@ def test_bacterial_batch_full_size(ctx, hf):
     0.02% indels, 5 rearrangements), all in one batched build."""
     coll = li.bacterial_collection()
     check_build(ctx, hf, coll)
+
+
+def test_repeated_builds_on_one_context(hf):
+    """A context's second build enqueues all rounds without host syncs, sized
+    from the first build; when the data differ the planned rounds are too many,
+    too few or too small, and the build must still equal the oracle."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_12439_gb300 import Context
+    ctx = Context(hf, device=0)
+    small = li.tiny_dna_collection(base_len=20_000, k=3)
+    big = li.tiny_dna_collection(base_len=300_000, k=5, snp=1e-2)
+    rng = np.random.default_rng(8)
+    text = li.from_strings([li.zipf_text(rng, 150_000), li.zipf_text(rng, 90_000)])
+    for coll in (big, big, small, big, text, text, small, small):
+        check_build(ctx, hf, coll)
+    st = ctx.last_build_stats()
+    assert st["rounds"] >= 1
