@@ -52,6 +52,8 @@ def parse_args():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--profile-builds", type=int, default=0,
                    help="only run this many batched builds of the workload and exit (for profiler captures)")
+    p.add_argument("--profile-strings", type=int, default=0,
+                   help="with --profile-builds: only the first this many strings of the workload")
     return p.parse_args()
 
 
@@ -224,7 +226,12 @@ def run_ours(args):
     hf = li.hash_family()
     coll = workload(rank)
     d = torch.from_numpy(coll.data).to(f"cuda:{local}")
-    stream = torch.cuda.current_stream()
+    # a stream of our own: the context launches on it and the timing events
+    # are recorded on it (torch's default stream has handle 0, which would
+    # make the context create a stream of its own)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(stream)
     ctx = Context(hf, device=local, stream=stream.cuda_stream)
 
     def barrier():
@@ -241,8 +248,11 @@ def run_ours(args):
         return float(t.item())
 
     if args.profile_builds:
+        offs = coll.offsets
+        if args.profile_strings:
+            offs = offs[:min(args.profile_strings, coll.k) + 1]
         for _ in range(args.profile_builds):
-            ctx.build(d, coll.offsets).free()
+            ctx.build(d, offs).free()
         torch.cuda.synchronize()
         return 0
 

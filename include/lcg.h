@@ -93,9 +93,13 @@ typedef struct lcg_round_stats {
 
 typedef struct lcg_build_stats {
     uint32_t rounds;
-    uint32_t pad;
+    uint32_t async_rounds;      /* rounds enqueued without a host synchronisation,
+                                   sized from the context's previous build */
     uint64_t kernel_launches;   /* kernels this library launched in the call */
     uint64_t input_bytes;
+    uint32_t redone;            /* 1 when those planned rounds did not fit and the
+                                   build was redone round by round */
+    uint32_t pad;
     lcg_round_stats round[64];
 } lcg_build_stats;
 
@@ -191,6 +195,29 @@ int lcg_export_level(lcg_ctx* ctx, const lcg_grammar* G, uint32_t level, uint64_
                      uint32_t* rhs, uint32_t* F);
 /* Copy F^0 (256 entries) and C (k entries each) to host buffers. */
 int lcg_export_start(lcg_ctx* ctx, const lcg_grammar* G, uint32_t* F0, uint32_t* c_level, uint32_t* c_rank);
+
+/* A device grammar from host arrays in the layout of lcg_export_level and
+ * lcg_export_start: the way a grammar built by another process or GPU enters
+ * this context before MergeGrams (Sec. 3.6; the per-GPU grammars of a sharded
+ * collection are merged this way).
+ * k strings and nlevels levels.  For level i = 1..nlevels (array index i-1):
+ *   g[i-1]        rules;
+ *   rhs_off[i-1]  g+1 uint64 offsets, starting at 0 and strictly increasing;
+ *   rhs[i-1]      rhs_off[i-1][g] uint32 symbols, each a rank of level i-1
+ *                 (a byte value at level 1);
+ *   F[i-1]        g uint32 fingerprints F^i.
+ * c_level, c_rank: k entries; (level, rank) of exp(T_j) as in C (Sec. 3.3).
+ * F^0 is not passed: it comes from the context's hash family.
+ * All pointers are HOST pointers, read during the call and not retained; the
+ * new grammar (*out) belongs to the library.
+ * Errors: malformed arrays (offsets, a symbol or C entry naming a missing rule)
+ * give LCG_EINVAL; nlevels not below the family's length LCG_ELEVELS; every
+ * F^i[r] is recomputed on the device from the right-hand side with Eq. fast_hash
+ * and a difference (a grammar of another hash family) gives LCG_EMISMATCH.
+ * The call is blocking. */
+int lcg_import(lcg_ctx* ctx, uint32_t k, uint32_t nlevels, const uint64_t* g, const uint64_t* const* rhs_off,
+               const uint32_t* const* rhs, const uint32_t* const* F, const uint32_t* c_level, const uint32_t* c_rank,
+               lcg_grammar** out);
 void lcg_grammar_free(lcg_grammar* G);
 
 #ifdef __cplusplus

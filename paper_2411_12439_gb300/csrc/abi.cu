@@ -191,6 +191,12 @@ void check_device_status(lcg_ctx* ctx, const DevStatus& h) {
     }
 }
 
+// A call starts with a clear status: an error of an earlier call does not
+// carry over.
+void reset_status(lcg_ctx* ctx) {
+    ck(ctx, cudaMemsetAsync(ctx->ds, 0, sizeof(DevStatus), ctx->st), "reset status");
+}
+
 DevStatus read_status(lcg_ctx* ctx) {
     DevStatus h;
     ck(ctx, cudaMemcpyAsync(&h, ctx->ds, sizeof(h), cudaMemcpyDeviceToHost, ctx->st), "read status");
@@ -749,6 +755,7 @@ int rounds_async(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32& i) {
         n = c.n_next;
         ctx->stats.rounds = r;
     }
+    ctx->stats.async_rounds = used;
     in.n = rc[planned - 1].n_next;
     in.kk = (u32)rc[planned - 1].k_next;
     in.d_n = nullptr;
@@ -1205,6 +1212,7 @@ int lcg_build(lcg_ctx* ctx, const uint8_t* data, const uint64_t* offsets, uint32
     LCG_GUARD_BEGIN
     ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
     kt_reset(ctx);
+    reset_status(ctx);
     G = new_grammar(ctx);
     try {
         build_into(ctx, G, data, offsets, k, data_on_device, false, true);
@@ -1216,6 +1224,7 @@ int lcg_build(lcg_ctx* ctx, const uint8_t* data, const uint64_t* offsets, uint32
         kt_reset(ctx);
         G = new_grammar(ctx);
         build_into(ctx, G, data, offsets, k, data_on_device, false, false);
+        ctx->stats.redone = 1;
     }
     sync(ctx);
     kt_collect(ctx);
@@ -1245,6 +1254,7 @@ int lcg_build_into(lcg_ctx* ctx, lcg_grammar* resident, const uint8_t* data, con
     LCG_GUARD_BEGIN
     ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
     kt_reset(ctx);
+    reset_status(ctx);
     build_into(ctx, resident, data, offsets, k, data_on_device, true, false);
     sync(ctx);
     kt_collect(ctx);
@@ -1257,6 +1267,7 @@ int lcg_merge(lcg_ctx* ctx, lcg_grammar* a, const lcg_grammar* b) {
     LCG_GUARD_BEGIN
     ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
     kt_reset(ctx);
+    reset_status(ctx);
     merge(ctx, a, b);
     kt_collect(ctx);
     return LCG_OK;
@@ -1324,6 +1335,82 @@ int lcg_export_start(lcg_ctx* ctx, const lcg_grammar* G, uint32_t* F0, uint32_t*
     sync(ctx);
     return LCG_OK;
     LCG_GUARD_END
+}
+
+int lcg_import(lcg_ctx* ctx, uint32_t k, uint32_t nlevels, const uint64_t* g, const uint64_t* const* rhs_off,
+               const uint32_t* const* rhs, const uint32_t* const* F, const uint32_t* c_level, const uint32_t* c_rank,
+               lcg_grammar** out) {
+    if (!ctx || !out) return LCG_EINVAL;
+    *out = nullptr;
+    if (nlevels && (!g || !rhs_off || !rhs || !F)) return LCG_EINVAL;
+    if (k && (!c_level || !c_rank)) return LCG_EINVAL;
+    lcg_grammar* G = nullptr;
+    try {
+        ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+        kt_reset(ctx);
+        fail_if(ctx, nlevels >= ctx->levels, LCG_ELEVELS, "grammar has more levels than the hash family has functions");
+        // host checks: offsets, symbol ranges and C entries name existing rules
+        for (u32 i = 1; i <= nlevels; i++) {
+            const u64 gi = g[i - 1];
+            fail_if(ctx, gi > kMaxRank, LCG_EOVERFLOW, "level with 2^31 rules or more");
+            fail_if(ctx, rhs_off[i - 1] == nullptr || (gi && (rhs[i - 1] == nullptr || F[i - 1] == nullptr)),
+                    LCG_EINVAL, "missing array of level " + std::to_string(i));
+            const uint64_t* ro = rhs_off[i - 1];
+            fail_if(ctx, ro[0] != 0, LCG_EINVAL, "rhs_off of level " + std::to_string(i) + " does not start at 0");
+            for (u64 r = 0; r < gi; r++)
+                fail_if(ctx, ro[r + 1] <= ro[r], LCG_EINVAL,
+                        "rule " + std::to_string(r) + " of level " + std::to_string(i) + " is empty or misplaced");
+            const u64 prev = (i == 1) ? 256 : g[i - 2];
+            const uint32_t* x = rhs[i - 1];
+            for (u64 y = 0; y < ro[gi]; y++)
+                fail_if(ctx, x[y] >= prev, LCG_EINVAL,
+                        "level " + std::to_string(i) + " names a symbol outside level " + std::to_string(i - 1));
+        }
+        for (u32 j = 0; j < k; j++) {
+            const u32 lvl = c_level[j];
+            fail_if(ctx, lvl > nlevels, LCG_EINVAL, "C entry " + std::to_string(j) + " names a missing level");
+            const u64 lim = (lvl == 0) ? 256 : g[lvl - 1];
+            fail_if(ctx, c_rank[j] >= lim, LCG_EINVAL, "C entry " + std::to_string(j) + " names a missing rule");
+        }
+        reset_status(ctx);
+        G = new_grammar(ctx);
+        if (k) {
+            grow_c(ctx, G, k);
+            ck(ctx, cudaMemcpyAsync(G->c_level, c_level, (u64)k * 4, cudaMemcpyHostToDevice, ctx->st), "import");
+            ck(ctx, cudaMemcpyAsync(G->c_rank, c_rank, (u64)k * 4, cudaMemcpyHostToDevice, ctx->st), "import");
+            G->k = k;
+        }
+        for (u32 i = 1; i <= nlevels; i++) {
+            const u64 gi = g[i - 1], Gi = rhs_off[i - 1][gi];
+            G->lv.emplace_back();
+            Level& L = G->lv.back();
+            grow_level(ctx, L, gi, Gi);
+            ck(ctx, cudaMemcpyAsync(L.rhs_off, rhs_off[i - 1], (gi + 1) * 8, cudaMemcpyHostToDevice, ctx->st), "import");
+            if (Gi) ck(ctx, cudaMemcpyAsync(L.rhs, rhs[i - 1], Gi * 4, cudaMemcpyHostToDevice, ctx->st), "import");
+            if (gi) ck(ctx, cudaMemcpyAsync(L.F, F[i - 1], gi * 4, cudaMemcpyHostToDevice, ctx->st), "import");
+            L.g = gi;
+            L.G = Gi;
+            L.rvalid = false;
+            ck(ctx, launch_check_fp(L.rhs, L.rhs_off, gi, fprev_of(G, i), level_hash(ctx, i), L.F, ctx->ds, ctx->st),
+               "k_check_fp");
+            ctx->launches++;
+        }
+        const DevStatus st = read_status(ctx);
+        fail_if(ctx, st.error == kErrMismatch, LCG_EMISMATCH,
+                "imported fingerprints differ from those of this context's hash family");
+        check_device_status(ctx, st);
+        *out = G;
+        return LCG_OK;
+    } catch (const Fail& f) {
+        cudaStreamSynchronize(ctx->st);
+        free_grammar_now(G);
+        return f.code;
+    } catch (const std::bad_alloc&) {
+        ctx->err = "host allocation failed";
+        cudaStreamSynchronize(ctx->st);
+        free_grammar_now(G);
+        return LCG_ENOMEM;
+    }
 }
 
 void lcg_grammar_free(lcg_grammar* G) { free_grammar_now(G); }

@@ -147,6 +147,27 @@ cudaError_t launch_h0(LevelHash h0, u32* F0, cudaStream_t st) {
 }
 
 // C_b entries of level `level` move to G_a's ranks.
+// Imported rules: F^i[r] must be h^i of the rule's right-hand side
+// (Eq. fast_hash over F^{i-1}); a difference means the grammar was built with
+// another hash family (or was altered).
+__global__ void k_check_fp(const u32* __restrict__ rhs, const u64* __restrict__ rhs_off, u64 g,
+                           const u32* __restrict__ Fprev, LevelHash lh, const u32* __restrict__ F, DevStatus* ds) {
+    for (u64 r = blockIdx.x * (u64)blockDim.x + threadIdx.x; r < g; r += (u64)gridDim.x * blockDim.x) {
+        const u64 s = rhs_off[r], e = rhs_off[r + 1];
+        u64 H = 0;
+        for (u64 y = e; y-- > s;) H = addmod61(mulmod61(H, lh.c), (u64)__ldg(Fprev + rhs[y]));
+        if (finish_hash(lh, H) != F[r]) set_error(ds, kErrMismatch);
+    }
+}
+
+cudaError_t launch_check_fp(const u32* rhs, const u64* rhs_off, u64 g, const u32* Fprev, LevelHash lh, const u32* F,
+                            DevStatus* ds, cudaStream_t st) {
+    if (g == 0) return cudaSuccess;
+    const u64 b = (g + 255) / 256;
+    k_check_fp<<<(unsigned)(b < 152 * 16 ? b : 152 * 16), 256, 0, st>>>(rhs, rhs_off, g, Fprev, lh, F, ds);
+    return cudaGetLastError();
+}
+
 __global__ void k_remap_c(const u32* __restrict__ c_level, u32* __restrict__ c_rank, u32 k, u32 level,
                           const u32* __restrict__ M) {
     for (u32 j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x)

@@ -122,6 +122,8 @@ cudaError_t launch_merge_lookup(const u32* brhs, const u64* brhs_off, const u32*
 cudaError_t launch_merge_append(const u32* brhs, const u64* brhs_off, const u32* bF, u64 gb, const u32* miss,
                                 const u64* xrank, const u64* xlen, u64 ga, u64 Ga, u32* arhs, u64* arhs_off,
                                 u32* aF, u32* M, u64 ga_new, u64 Ga_new, cudaStream_t st);
+cudaError_t launch_check_fp(const u32* rhs, const u64* rhs_off, u64 g, const u32* Fprev, LevelHash lh, const u32* F,
+                            DevStatus* ds, cudaStream_t st);
 cudaError_t launch_remap_c(const u32* c_level, u32* c_rank, u32 k, u32 level, const u32* M, cudaStream_t st);
 cudaError_t launch_rule_lens(const u32* cur, u64 cnt, const u64* rhs_off, u32* lens, cudaStream_t st);
 cudaError_t launch_expand(const u32* cur, u64 cnt, const u64* offs, const u64* rhs_off, const u32* rhs, u32* next,

@@ -24,8 +24,8 @@ _ERRORS = {
 SYMBOLS = [
     "lcg_ctx_create", "lcg_ctx_destroy", "lcg_last_error", "lcg_last_build_stats", "lcg_set_kernel_timing",
     "lcg_last_kernel_times", "lcg_build", "lcg_build_into",
-    "lcg_merge", "lcg_decompress", "lcg_decompress_static", "lcg_grammar_shape", "lcg_level_size", "lcg_export_level", "lcg_export_start",
-    "lcg_grammar_free",
+    "lcg_merge", "lcg_decompress", "lcg_decompress_static", "lcg_grammar_shape", "lcg_level_size", "lcg_export_level",
+    "lcg_export_start", "lcg_import", "lcg_grammar_free",
 ]
 
 
@@ -52,8 +52,9 @@ class KernelTimeC(ctypes.Structure):
 
 
 class BuildStatsC(ctypes.Structure):
-    _fields_ = [("rounds", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("kernel_launches", ctypes.c_uint64),
-                ("input_bytes", ctypes.c_uint64), ("round", RoundStatsC * 64)]
+    _fields_ = [("rounds", ctypes.c_uint32), ("async_rounds", ctypes.c_uint32), ("kernel_launches", ctypes.c_uint64),
+                ("input_bytes", ctypes.c_uint64), ("redone", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+                ("round", RoundStatsC * 64)]
 
 
 _lib = None
@@ -92,6 +93,7 @@ def load(build_if_missing: bool = True):
     lib.lcg_level_size.argtypes = [P, U32, ctypes.POINTER(U64), ctypes.POINTER(U64)]
     lib.lcg_export_level.argtypes = [P, P, U32, P, P, P]
     lib.lcg_export_start.argtypes = [P, P, P, P, P]
+    lib.lcg_import.argtypes = [P, U32, U32, P, P, P, P, P, P, PP]
     lib.lcg_grammar_free.argtypes = [P]
     lib.lcg_grammar_free.restype = None
     for name in SYMBOLS:
@@ -173,6 +175,37 @@ class Context:
         self._check(load().lcg_merge(self._h, a._h, b._h))
         return a
 
+    def import_grammar(self, ex: dict) -> "Grammar":
+        """lcg_import: a device grammar from the host arrays of ``Grammar.export()``
+        (for example one received from another process)."""
+        levels = ex["levels"]
+        nl = len(levels)
+        g = np.array([int(L["g"]) for L in levels] or [0], dtype=np.uint64)
+        keep = []
+
+        def arr(x, dt):
+            a = np.ascontiguousarray(x, dtype=dt)
+            if a.size == 0:
+                a = np.zeros(1, dtype=dt)
+            keep.append(a)
+            return a.ctypes.data
+
+        ro = (ctypes.c_void_p * max(nl, 1))(*[arr(L["rhs_off"], np.uint64) for L in levels])
+        rhs = (ctypes.c_void_p * max(nl, 1))(*[arr(L["rhs"], np.uint32) for L in levels])
+        F = (ctypes.c_void_p * max(nl, 1))(*[arr(L["F"], np.uint32) for L in levels])
+        cl = np.ascontiguousarray(ex["c_level"], dtype=np.uint32)
+        cr = np.ascontiguousarray(ex["c_rank"], dtype=np.uint32)
+        k = int(cl.shape[0])
+        if k == 0:
+            cl = np.zeros(1, dtype=np.uint32)
+            cr = np.zeros(1, dtype=np.uint32)
+        h = ctypes.c_void_p(0)
+        self._check(load().lcg_import(self._h, k, nl, _np_ptr(g), ctypes.cast(ro, ctypes.c_void_p),
+                                      ctypes.cast(rhs, ctypes.c_void_p), ctypes.cast(F, ctypes.c_void_p),
+                                      _np_ptr(cl), _np_ptr(cr), ctypes.byref(h)))
+        del keep
+        return Grammar(self, h)
+
     def set_kernel_timing(self, enable: bool) -> None:
         """lcg_set_kernel_timing: bracket every kernel launch with CUDA events."""
         self._check(load().lcg_set_kernel_timing(self._h, int(bool(enable))))
@@ -190,7 +223,8 @@ class Context:
         self._check(load().lcg_last_build_stats(self._h, ctypes.byref(st)))
         rounds = [{f: int(getattr(st.round[i], f)) for f in ("n", "phrases", "g", "G", "strings", "table_cap",
                                                              "retries")} for i in range(min(st.rounds, 64))]
-        return {"rounds": int(st.rounds), "kernel_launches": int(st.kernel_launches),
+        return {"rounds": int(st.rounds), "async_rounds": int(st.async_rounds), "redone": bool(st.redone),
+                "kernel_launches": int(st.kernel_launches),
                 "input_bytes": int(st.input_bytes), "per_round": rounds}
 
 

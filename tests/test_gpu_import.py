@@ -1,0 +1,83 @@
+"""lcg_import and the sharded build on one GPU, through the C ABI.
+
+A grammar exported to host arrays and imported again must be the same
+grammar; a grammar of another hash family or with malformed arrays must be
+refused.  The merge tree of the sharded build is run in one process with the
+CUDA backend (the ranks in sequence), and must give the oracle's BuildGram of
+the whole collection."""
+import numpy as np
+import pytest
+
+import lcg_inputs as li
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(hf):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_12439_gb300 import Context
+    return Context(hf, device=0)
+
+
+def test_import_roundtrip(ctx, hf):
+    coll = li.tiny_dna_collection(base_len=50_000, k=4)
+    want = O.build(coll, hf).export()
+    g = ctx.import_grammar(want)
+    assert O.grammars_equal(g.export(), want)
+    for j in range(coll.k):
+        assert g.decompress(j) == coll.string(j).tobytes()
+    # an imported grammar takes part in merges and resident builds like a built one
+    more = li.tiny_dna_collection(base_len=50_000, k=6).subset([4, 5])
+    ctx.build_into(g, more.data, more.offsets)
+    both = li.from_strings([coll.string(j) for j in range(coll.k)] + [more.string(j) for j in range(more.k)])
+    assert O.grammars_equal(g.export(), O.build(both, hf).export())
+
+
+def test_import_rejects_other_family_and_malformed(ctx, hf):
+    from paper_2411_12439_gb300 import LCGError
+    coll = li.tiny_dna_collection(base_len=5_000, k=2)
+    other = O.build(coll, li.hash_family(seed=12345)).export()
+    with pytest.raises(LCGError) as e:
+        ctx.import_grammar(other)
+    assert e.value.code == -4  # LCG_EMISMATCH
+    ex = O.build(coll, hf).export()
+    bad = {**ex, "c_rank": ex["c_rank"].copy()}
+    bad["c_rank"][0] = ex["levels"][int(ex["c_level"][0]) - 1]["g"]  # one past the last rule
+    with pytest.raises(LCGError) as e:
+        ctx.import_grammar(bad)
+    assert e.value.code == -1  # LCG_EINVAL
+    lv = [dict(L) for L in ex["levels"]]
+    lv[1] = {**lv[1], "rhs": lv[1]["rhs"].copy()}
+    lv[1]["rhs"][0] = ex["levels"][0]["g"]  # a symbol outside level 1
+    with pytest.raises(LCGError) as e:
+        ctx.import_grammar({**ex, "levels": lv})
+    assert e.value.code == -1
+    # the context still works after refused calls
+    assert O.grammars_equal(ctx.import_grammar(ex).export(), ex)
+
+
+class _LocalComm:
+    def __init__(self, boxes, rank):
+        self.boxes, self.rank = boxes, rank
+
+    def send(self, buf, dst):
+        self.boxes[(self.rank, dst)] = buf
+
+    def recv(self, src):
+        return self.boxes.pop((src, self.rank))
+
+
+@pytest.mark.parametrize("world", [2, 3, 4])
+def test_sharded_build_merge_tree(ctx, hf, world):
+    from paper_2411_12439_gb300 import sharding
+    coll = li.tiny_dna_collection(base_len=120_000, k=7)
+    backend = sharding.CudaBackend(ctx)
+    boxes, out = {}, {}
+    for rank in reversed(range(world)):
+        out[rank] = sharding.build_sharded(coll.data, coll.offsets, rank, world, backend, _LocalComm(boxes, rank))
+    assert not boxes
+    assert O.grammars_equal(out[0].export(), O.build(coll, hf).export())
