@@ -93,7 +93,14 @@ constexpr int kSP = kTP + kHalo;   // staged positions
 constexpr int kCacheBits = 11;
 constexpr int kCacheSlots = 1 << kCacheBits;  // per-block phrase cache (byte rounds)
 constexpr int kCacheProbes = 8;
-constexpr int kClaimBuf = 1024;
+// New table entries of a block are listed in shared memory and appended to
+// the round's claim list once the buffer is half full (and after the block's
+// last tile), so that the global counter is touched every few tiles only.
+constexpr int kClaimBufB = 512;   // byte rounds (shared memory also holds the phrase cache)
+constexpr int kClaimBufR = 1024;  // rank rounds
+// Byte rounds: phrases that miss the block's cache are queued and looked up in
+// the global table together, so that full warps run the long lookup path.
+constexpr int kMissBuf = 512;
 
 template <typename T>
 __device__ u64 scan_right_diff(const T* S, FpSource<T> fp, u64 from, u64 strend, u32 val) {
@@ -152,12 +159,13 @@ __device__ __forceinline__ void stage_vec(V* dst, const V* src, int n_sym, bool 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kParseThreads) k_parse(const RoundArgs a, u64 ntiles) {
+__global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse(const RoundArgs a, u64 ntiles) {
     constexpr int NWS = kSP / 32;    // staged break words
     constexpr int NWT = kTP / 32;    // tile break words
     constexpr bool kByte = sizeof(T) == 1;
     constexpr bool kLocal = kByte;
     static_assert(NWT <= kParseThreads, "one tile word per thread");
+    constexpr int kClaimBuf = kByte ? kClaimBufB : kClaimBufR;
 
     __shared__ u32 sF0[kByte ? 256 : 1];
     __shared__ __align__(16) unsigned char sb[kByte ? kSP : 16];  // bytes of tile positions
@@ -173,6 +181,8 @@ __global__ void __launch_bounds__(kParseThreads) k_parse(const RoundArgs a, u64 
     __shared__ u64 ckey[kLocal ? kCacheSlots : 1];
     __shared__ u64 cval[kLocal ? kCacheSlots : 1];
     __shared__ u32 sClaim[kClaimBuf];
+    __shared__ u32 sMiss[kLocal ? kMissBuf : 1];  // q | (cache slot + 1) << 16
+    __shared__ u32 s_nmiss;
     __shared__ u64 s_tail_end;
     __shared__ u32 s_nclaim;
     __shared__ u64 s_claim_len;
@@ -198,20 +208,21 @@ __global__ void __launch_bounds__(kParseThreads) k_parse(const RoundArgs a, u64 
             cval[x] = ~0ull;
         }
     }
+    if (tid == 0) {
+        s_nclaim = 0;
+        s_claim_len = 0;
+    }
 
     // persistent blocks: tiles blockIdx.x, blockIdx.x + gridDim.x, ...  Tiles
     // do not depend on one another.
     u64 iter = 0;
     for (u64 tile = blockIdx.x; tile < ntiles; tile += gridDim.x, iter++) {
-        if (round_halted(a)) break;
+        if ((iter & 15) == 0 && round_halted(a)) break;
         for (int w = tid; w < NWS + 1; w += kParseThreads) {
             sstart[w] = 0;
             if (w < NWS) sbits[w] = 0;
         }
-        if (tid == 0) {
-            s_nclaim = 0;
-            s_claim_len = 0;
-        }
+        if (tid == 0) s_nmiss = 0;
         const u64 t0 = tile * (u64)kTP;
         const u64 t_end = min(t0 + (u64)kTP, n), s_end = min(t0 + (u64)kSP, n);
         const int ns = (int)(s_end - t0), nt = (int)(t_end - t0);
@@ -371,16 +382,31 @@ __global__ void __launch_bounds__(kParseThreads) k_parse(const RoundArgs a, u64 
             // made in an earlier tile of this block, or by an earlier
             // occurrence in this tile, needs nothing more: that occurrence is
             // already registered in the table.  Otherwise the slot's first
-            // occurrence is lowered to this phrase's order key.
+            // occurrence is lowered to this phrase's order key.  Misses are
+            // queued and looked up after the loop.
+            const u64* sb64 = reinterpret_cast<const u64*>(sb);
+            // packed bytes of a phrase of length <= 7 inside the staged bytes
+            auto short_key = [&](u32 st, u32 len) -> u64 {
+                const u32 w = st >> 3, sh = (st & 7) * 8;
+                const u64 lo = sb64[w], hi = sb64[w + 1];
+                const u64 v = sh ? (lo >> sh) | (hi << (64 - sh)) : lo;
+                return ((u64)len << 56) | (v & ((1ull << (8 * len)) - 1));
+            };
+            auto cache_insert = [&](int h, u64 key, u32 q, u32 slot) {
+                const u64 old = atomicCAS((unsigned long long*)&ckey[h], (unsigned long long)kEmpty,
+                                          (unsigned long long)key);
+                if (old == kEmpty) cval[h] = ((iter & 0x1FFFFF) << 43) | ((u64)q << 31) | slot;
+            };
             for (u32 q = tid; q < cntq; q += kParseThreads) {
-                const u64 st = sP[q], en = phrase_end(q), len = en - st;
+                const u32 st = sP[q];
+                const u64 en = phrase_end(q);
+                const u64 len = en - st;
                 u32 slot = ~0u;
-                if (len <= 7 && en <= (u64)ns) {
-                    u64 key = len << 56;
-                    for (u64 x = 0; x < len; x++) key |= (u64)sb[st + x] << (8 * x);
-                    const u32 h0 = (u32)((key * 0x9E3779B97F4A7C15ull) >> (64 - kCacheBits));
-                    u32 h = h0;
-                    int free_h = -1;
+                int free_h = -1;
+                const bool cacheable = len <= 7 && en <= (u64)ns;
+                if (cacheable) {
+                    const u64 key = short_key(st, (u32)len);
+                    u32 h = (u32)((key * 0x9E3779B97F4A7C15ull) >> (64 - kCacheBits));
                     for (int probe = 0; probe < kCacheProbes; probe++) {
                         const u64 k = ckey[h];
                         if (k == key) {
@@ -395,17 +421,30 @@ __global__ void __launch_bounds__(kParseThreads) k_parse(const RoundArgs a, u64 
                         if (k == kEmpty) { free_h = (int)h; break; }
                         h = (h + 1) & (kCacheSlots - 1);
                     }
-                    if (slot == ~0u) {
-                        slot = lookup(q, st, en);
-                        if (free_h >= 0 && slot != ~0u && !(slot & kResidentBit)) {
-                            const u64 old = atomicCAS((unsigned long long*)&ckey[free_h],
-                                                      (unsigned long long)kEmpty, (unsigned long long)key);
-                            if (old == kEmpty) cval[free_h] = ((iter & 0x1FFFFF) << 43) | ((u64)q << 31) | slot;
-                        }
-                    }
-                } else {
-                    slot = lookup(q, st, en);
                 }
+                if (slot == ~0u) {
+                    const u32 m = atomicAdd(&s_nmiss, 1u);
+                    if (m < (u32)kMissBuf) {
+                        sMiss[m] = q | ((u32)(free_h + 1) << 16);
+                        continue;
+                    }
+                    slot = lookup(q, st, en);  // queue full: at once
+                    if (cacheable && free_h >= 0 && slot != ~0u && !(slot & kResidentBit))
+                        cache_insert(free_h, short_key(st, (u32)len), q, slot);
+                }
+                a.P_slot[okey0 + q] = slot;
+            }
+            __syncthreads();
+            const u32 nm = min(s_nmiss, (u32)kMissBuf);
+            for (u32 i = tid; i < nm; i += kParseThreads) {
+                const u32 e = sMiss[i];
+                const u32 q = e & 0xFFFFu;
+                const int free_h = (int)(e >> 16) - 1;
+                const u32 st = sP[q];
+                const u64 en = phrase_end(q);
+                const u32 slot = lookup(q, st, en);
+                if (free_h >= 0 && slot != ~0u && !(slot & kResidentBit))
+                    cache_insert(free_h, short_key(st, (u32)(en - st)), q, slot);
                 a.P_slot[okey0 + q] = slot;
             }
         } else {
@@ -426,19 +465,28 @@ __global__ void __launch_bounds__(kParseThreads) k_parse(const RoundArgs a, u64 
                 if (__shfl_sync(0xffffffffu, (jj < kact && s < t_end) ? 1u : 0u, 31) == 0) break;
             }
         }
-        // 6. this tile's new entries join the round's claim list
-        const u32 nb = min(s_nclaim, (u32)kClaimBuf);
-        if (tid == 0 && s_nclaim) {
-            const u64 base = atomicAdd(&a.ds->claims, (u64)nb);
-            s_claim_base = base;
-            atomicAdd(&a.ds->claim_len, s_claim_len);
-            if (base + nb > a.claim_limit) atomicExch(&a.ds->overflow, 1u);
-        }
-        __syncthreads();
-        if (nb) {
-            const u64 base = s_claim_base;
-            for (u32 x = tid; x < nb; x += kParseThreads)
-                if (base + x < bt.cap) a.claims[base + x] = sClaim[x];
+        // 6. the block's new entries join the round's claim list when the
+        //    buffer is half full, and after the block's last tile
+        const u32 ncl = s_nclaim;
+        if (ncl >= (u32)kClaimBuf / 2 || tile + gridDim.x >= ntiles) {
+            const u32 nb = min(ncl, (u32)kClaimBuf);
+            if (tid == 0 && ncl) {
+                const u64 base = atomicAdd(&a.ds->claims, (u64)nb);
+                s_claim_base = base;
+                atomicAdd(&a.ds->claim_len, s_claim_len);
+                if (base + nb > a.claim_limit) atomicExch(&a.ds->overflow, 1u);
+            }
+            __syncthreads();
+            if (nb) {
+                const u64 base = s_claim_base;
+                for (u32 x = tid; x < nb; x += kParseThreads)
+                    if (base + x < bt.cap) a.claims[base + x] = sClaim[x];
+            }
+            __syncthreads();
+            if (tid == 0) {
+                s_nclaim = 0;
+                s_claim_len = 0;
+            }
         }
         __syncthreads();
     }

@@ -114,17 +114,23 @@ __device__ __forceinline__ Key128 cas_key(Key128* p, Key128 cmp, Key128 val) {
     return old;
 }
 
+// Longest probe sequence of a claim: far beyond what a table under its load
+// limit shows, so reaching it means the table is (nearly) full.
+constexpr u64 kMaxProbes = 4096;
+
 // Find or claim the slot of key k in a table that other threads are filling.
 // `same(ref)` compares the content stored at `ref` with the phrase (hashed keys
 // only).  The slot's value is lowered to `pidx` (first occurrence).  Returns
 // the slot and sets *claimed when this call claimed it, or ~0 when the table
-// is over its load limit or full (the host then regrows it and reruns).
+// is over its load limit or full, or the probe sequence reached kMaxProbes
+// (the host then regrows the table and reruns).
 template <typename Same>
 __device__ u64 table_claim_or_find(ContentTable t, const Key128& k, bool hashed, u64 pidx, Same same, bool* claimed,
                                    DevStatus* ds) {
     u64 s = key_home(k, t.cap);
     const Key128 empty{~0ull, ~0ull};
-    for (u64 probe = 0; probe < t.cap; probe++) {
+    const u64 limit = t.cap < kMaxProbes ? t.cap : kMaxProbes;
+    for (u64 probe = 0; probe < limit; probe++) {
         Key128* kp = t.keys + s;
         Key128 cur = ld_key_relaxed(kp);
         if (cur.hi == kEmptyHi) {
