@@ -89,6 +89,7 @@ typedef struct lcg_round_stats {
     uint64_t table_cap;  /* phrase-table slots used for round i */
     uint32_t retries;    /* table regrowths in round i */
     uint32_t pad;
+    double parse_ms;     /* device time of the round's k_parse launches (kernel timing on) */
 } lcg_round_stats;
 
 typedef struct lcg_build_stats {
@@ -218,6 +219,29 @@ int lcg_export_start(lcg_ctx* ctx, const lcg_grammar* G, uint32_t* F0, uint32_t*
 int lcg_import(lcg_ctx* ctx, uint32_t k, uint32_t nlevels, const uint64_t* g, const uint64_t* const* rhs_off,
                const uint32_t* const* rhs, const uint32_t* const* F, const uint32_t* c_level, const uint32_t* c_rank,
                lcg_grammar** out);
+/* The packed form of a grammar: one buffer, for storage and for sending a
+ * grammar to another process (the merge tree of a sharded collection).
+ * Layout (little-endian; every array starts at a multiple of 8 bytes, u32
+ * arrays are zero-padded to a multiple of 8 bytes):
+ *   u64 magic 0x4C434753, u64 k, u64 nlevels, then per level (u64 g, u64 G);
+ *   per level: u64 rhs_off[g+1], u32 rhs[G], u32 F[g];
+ *   u32 c_level[k], u32 c_rank[k], u32 F0[256].
+ * lcg_packed_size gives its size in bytes. */
+int lcg_packed_size(const lcg_grammar* G, uint64_t* bytes);
+/* Write G's packed form into the HOST buffer `out` (8-byte aligned, `cap`
+ * bytes, at least lcg_packed_size); page-locked memory lets the copies run at
+ * link speed.  Blocking.  LCG_EINVAL when the buffer is too small or
+ * misaligned. */
+int lcg_export_packed(lcg_ctx* ctx, const lcg_grammar* G, void* out, uint64_t cap);
+/* A device grammar from a packed HOST buffer of `size` bytes (8-byte
+ * aligned), with the checks of lcg_import; an F0 other than this context's
+ * gives LCG_EMISMATCH, a malformed buffer LCG_EINVAL.  Blocking. */
+int lcg_import_packed(lcg_ctx* ctx, const void* buf, uint64_t size, lcg_grammar** out);
+/* Release a grammar (NULL is ignored).  While the context that created it
+ * exists, the device memory returns to the pool in the order of that
+ * context's stream, so later calls of the context reuse it at no cost; after
+ * lcg_ctx_destroy it is freed at once.  A grammar must not be freed while a
+ * call that uses it runs on another host thread. */
 void lcg_grammar_free(lcg_grammar* G);
 
 #ifdef __cplusplus

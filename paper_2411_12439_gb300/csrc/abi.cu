@@ -35,6 +35,7 @@ struct Level {
 
 struct lcg_grammar {
     int device = 0;
+    lcg_ctx* owner = nullptr;  // the context that created it, while that context lives
     u64 tag = 0;
     u32* F0 = nullptr;  // 256 fingerprints of bytes (device)
     std::vector<Level> lv;
@@ -46,6 +47,7 @@ struct lcg_grammar {
 struct lcg_ctx {
     int device = 0;
     cudaStream_t st = nullptr;
+    std::vector<lcg_grammar*> live;  // grammars created here and not yet freed
     bool own_stream = false;
     std::vector<u64> a, b, c;
     u32 levels = 0, m_bits = 32;
@@ -79,6 +81,7 @@ struct lcg_ctx {
         const char* name;
         cudaEvent_t a, b;
         double bytes;
+        u32 round;  // BuildGram round of a parse launch, else 0
     };
     std::vector<KRec> krecs;
     std::vector<cudaEvent_t> evpool;
@@ -147,9 +150,9 @@ void kt_reset(lcg_ctx* ctx) {
 
 // Record the start of a launch of kernel `name` that moves `bytes` algorithmic
 // bytes; returns a handle for kt_end (or -1 when timing is off).
-int kt_begin(lcg_ctx* ctx, const char* name, double bytes) {
+int kt_begin(lcg_ctx* ctx, const char* name, double bytes, u32 round = 0) {
     if (!ctx->ktime) return -1;
-    lcg_ctx::KRec r{name, kt_event(ctx), kt_event(ctx), bytes};
+    lcg_ctx::KRec r{name, kt_event(ctx), kt_event(ctx), bytes, round};
     ck(ctx, cudaEventRecord(r.a, ctx->st), "cudaEventRecord");
     ctx->krecs.push_back(r);
     return (int)ctx->krecs.size() - 1;
@@ -177,6 +180,7 @@ void kt_collect(lcg_ctx* ctx) {
         t->launches++;
         t->ms += ms;
         t->bytes += r.bytes;
+        if (r.round >= 1 && r.round <= 64) ctx->stats.round[r.round - 1].parse_ms += ms;
     }
 }
 
@@ -296,25 +300,40 @@ lcg_grammar* new_grammar(lcg_ctx* ctx) {
     lcg_grammar* G = new lcg_grammar();
     G->device = ctx->device;
     G->tag = ctx->tag;
+    G->owner = ctx;
+    ctx->live.push_back(G);
     G->F0 = dalloc<u32>(ctx, 256);
     ck(ctx, launch_h0(level_hash(ctx, 0), G->F0, ctx->st), "h0");
     ctx->launches++;
     return G;
 }
 
+// Release a grammar.  While its context lives, the memory goes back to the
+// pool in the order of that context's stream (later calls reuse it without a
+// device synchronisation); otherwise it is freed at once.
 void free_grammar_now(lcg_grammar* G) {
     if (!G) return;
     cudaSetDevice(G->device);
-    cudaFree(G->F0);
-    for (Level& L : G->lv) {
-        cudaFree(L.rhs_off);
-        cudaFree(L.rhs);
-        cudaFree(L.F);
-        cudaFree(L.rkeys);
-        cudaFree(L.rvals);
+    cudaStream_t st = nullptr;
+    if (G->owner) {
+        auto& v = G->owner->live;
+        v.erase(std::remove(v.begin(), v.end(), G), v.end());
+        st = G->owner->st;
     }
-    cudaFree(G->c_level);
-    cudaFree(G->c_rank);
+    auto release = [&](void* p) {
+        if (!p) return;
+        if (st) cudaFreeAsync(p, st); else cudaFree(p);
+    };
+    release(G->F0);
+    for (Level& L : G->lv) {
+        release(L.rhs_off);
+        release(L.rhs);
+        release(L.F);
+        release(L.rkeys);
+        release(L.rvals);
+    }
+    release(G->c_level);
+    release(G->c_rank);
     delete G;
 }
 
@@ -489,7 +508,7 @@ void enqueue_parse(lcg_ctx* ctx, RoundArgs& a, u64 n_for_bytes) {
     const double tab_bytes = a.tab_cap * (double)(key_bytes() + sizeof(u64));
     const double tbytes = tab_bytes > kL2Bytes ? 32.0 * (double)n_for_bytes / 3.0 : 0.0;
     int h = kt_begin(ctx, "k_parse",
-                     (a.sym_bytes == 1 ? 1.0 : 8.0) * n_for_bytes + 4.0 * (double)n_for_bytes / 3.0 + tbytes);
+                     (a.sym_bytes == 1 ? 1.0 : 8.0) * n_for_bytes + 4.0 * (double)n_for_bytes / 3.0 + tbytes, a.level);
     ck(ctx, launch_parse(a, ctx->st), "k_parse");
     kt_end(ctx, h);
     const u64 stiles = std::max<u64>(1, scan2_tiles_for(a.tiles_bound));
@@ -671,7 +690,7 @@ int rounds_async(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32& i) {
     const u32 planned = std::min<u32>(ctx->hint_rounds, std::min<u32>(ctx->levels - 1, kMaxRounds));
     u64 n_bound = in.n, n_est = in.n;
     const u32 kk = in.kk;
-    std::vector<u64> g_base(planned + 1), G_base(planned + 1);
+    std::vector<u64> g_base(planned + 1), G_base(planned + 1), caps(planned + 1);
     for (u32 r = 1; r <= planned; r++) {
         if (R->lv.size() < r) R->lv.emplace_back();
         Level& L = R->lv[r - 1];
@@ -684,8 +703,9 @@ int rounds_async(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32& i) {
         const double P_est = ctx->p_hint[r] * (double)n_est;
         const double g_est = ctx->ratio_hint[r] * P_est;
         const double G_est = ctx->glen_hint[r] * g_est;
-        const u64 cap = std::max<u64>(8192, (u64)(g_est * 1.1 / 0.7) + 1024);
-        alloc_table(ctx, b, std::min<u64>(cap, kMaxRank + 1));
+        const u64 cap = std::min<u64>(std::max<u64>(8192, (u64)(g_est * 1.1 / 0.7) + 1024), kMaxRank + 1);
+        caps[r] = cap;
+        alloc_table(ctx, b, cap);
         set_table(a, b);
         enqueue_parse(ctx, a, n_est);
         const u64 g_alloc = (u64)(g_est * 1.25) + 1024;
@@ -749,6 +769,7 @@ int rounds_async(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32& i) {
         rs.n = n;
         rs.strings = (r == 1) ? kk : rc[r - 2].k_next;
         rs.phrases = c.phrases;
+        rs.table_cap = caps[r];
         rs.g = s.claims;
         rs.G = s.claim_len;
         record_hints(ctx, r, n, c.phrases, s.claims, s.claim_len);
@@ -1165,6 +1186,8 @@ void lcg_ctx_destroy(lcg_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->st) cudaStreamSynchronize(ctx->st);
+    for (lcg_grammar* G : ctx->live) G->owner = nullptr;  // they outlive the context
+    ctx->live.clear();
     for (auto& r : ctx->krecs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -1411,6 +1434,113 @@ int lcg_import(lcg_ctx* ctx, uint32_t k, uint32_t nlevels, const uint64_t* g, co
         free_grammar_now(G);
         return LCG_ENOMEM;
     }
+}
+
+// ---- packed form: one buffer, every section 8-byte aligned ----------------
+
+constexpr u64 kPackMagic = 0x4C434753ull;  // "LCGS"
+
+static u64 pad8(u64 b) { return (b + 7) & ~7ull; }
+
+static u64 packed_bytes(const lcg_grammar* G) {
+    const u64 nl = G->lv.size();
+    u64 b = 8 * (3 + 2 * nl);
+    for (const Level& L : G->lv) b += 8 * (L.g + 1) + pad8(4 * L.G) + pad8(4 * L.g);
+    return b + 2 * pad8(4ull * G->k) + 4 * 256;
+}
+
+int lcg_packed_size(const lcg_grammar* G, uint64_t* bytes) {
+    if (!G || !bytes) return LCG_EINVAL;
+    *bytes = packed_bytes(G);
+    return LCG_OK;
+}
+
+int lcg_export_packed(lcg_ctx* ctx, const lcg_grammar* G, void* out, uint64_t cap) {
+    if (!ctx || !G || !out) return LCG_EINVAL;
+    LCG_GUARD_BEGIN
+    ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    fail_if(ctx, ((uintptr_t)out & 7) != 0, LCG_EINVAL, "packed buffer must be 8-byte aligned");
+    fail_if(ctx, cap < packed_bytes(G), LCG_EINVAL, "packed buffer too small");
+    unsigned char* o = (unsigned char*)out;
+    u64* head = (u64*)o;
+    const u64 nl = G->lv.size();
+    head[0] = kPackMagic;
+    head[1] = G->k;
+    head[2] = nl;
+    for (u64 i = 0; i < nl; i++) {
+        head[3 + 2 * i] = G->lv[i].g;
+        head[4 + 2 * i] = G->lv[i].G;
+    }
+    u64 pos = 8 * (3 + 2 * nl);
+    auto d2h = [&](const void* src, u64 bytes, u64 span) {
+        if (bytes) ck(ctx, cudaMemcpyAsync(o + pos, src, bytes, cudaMemcpyDeviceToHost, ctx->st), "export");
+        if (span > bytes) std::memset(o + pos + bytes, 0, span - bytes);
+        pos += span;
+    };
+    for (const Level& L : G->lv) {
+        d2h(L.rhs_off, 8 * (L.g + 1), 8 * (L.g + 1));
+        d2h(L.rhs, 4 * L.G, pad8(4 * L.G));
+        d2h(L.F, 4 * L.g, pad8(4 * L.g));
+    }
+    d2h(G->c_level, 4ull * G->k, pad8(4ull * G->k));
+    d2h(G->c_rank, 4ull * G->k, pad8(4ull * G->k));
+    d2h(G->F0, 4 * 256, 4 * 256);
+    sync(ctx);
+    return LCG_OK;
+    LCG_GUARD_END
+}
+
+int lcg_import_packed(lcg_ctx* ctx, const void* buf, uint64_t size, lcg_grammar** out) {
+    if (!ctx || !buf || !out) return LCG_EINVAL;
+    *out = nullptr;
+    auto bad = [&](const char* why) {
+        ctx->err = std::string("packed grammar: ") + why;
+        return LCG_EINVAL;
+    };
+    if (((uintptr_t)buf & 7) != 0) return bad("buffer must be 8-byte aligned");
+    const unsigned char* b = (const unsigned char*)buf;
+    const u64* head = (const u64*)b;
+    if (size < 24 || head[0] != kPackMagic) return bad("not a packed grammar");
+    const u64 k = head[1], nl = head[2];
+    if (k > 0xffffffffull || nl > 4096 || size < 8 * (3 + 2 * nl)) return bad("malformed header");
+    std::vector<uint64_t> g(nl), Gs(nl);
+    std::vector<const uint64_t*> ro(nl);
+    std::vector<const uint32_t*> rhs(nl), F(nl);
+    u64 pos = 8 * (3 + 2 * nl);
+    for (u64 i = 0; i < nl; i++) {
+        g[i] = head[3 + 2 * i];
+        Gs[i] = head[4 + 2 * i];
+        if (g[i] > kMaxRank || Gs[i] > (1ull << 40)) return bad("malformed level sizes");
+        const u64 need = 8 * (g[i] + 1) + pad8(4 * Gs[i]) + pad8(4 * g[i]);
+        if (pos + need > size) return bad("truncated");
+        ro[i] = (const uint64_t*)(b + pos);
+        rhs[i] = (const uint32_t*)(b + pos + 8 * (g[i] + 1));
+        F[i] = (const uint32_t*)(b + pos + 8 * (g[i] + 1) + pad8(4 * Gs[i]));
+        if (ro[i][g[i]] != Gs[i]) return bad("level sizes disagree with the offsets");
+        pos += need;
+    }
+    if (pos + 2 * pad8(4 * k) + 4 * 256 != size) return bad("wrong size");
+    const uint32_t* cl = (const uint32_t*)(b + pos);
+    const uint32_t* cr = (const uint32_t*)(b + pos + pad8(4 * k));
+    const uint32_t* F0 = (const uint32_t*)(b + pos + 2 * pad8(4 * k));
+    lcg_grammar* G = nullptr;
+    const int rc = lcg_import(ctx, (uint32_t)k, (uint32_t)nl, g.data(), ro.data(), rhs.data(), F.data(), cl, cr, &G);
+    if (rc != LCG_OK) return rc;
+    // F^0 must be the context's too
+    uint32_t mine[256];
+    if (cudaMemcpyAsync(mine, G->F0, sizeof(mine), cudaMemcpyDeviceToHost, ctx->st) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->st) != cudaSuccess) {
+        free_grammar_now(G);
+        ctx->err = "read F0";
+        return LCG_EDEVICE;
+    }
+    if (std::memcmp(mine, F0, sizeof(mine)) != 0) {
+        free_grammar_now(G);
+        ctx->err = "packed grammar: F0 of another hash family";
+        return LCG_EMISMATCH;
+    }
+    *out = G;
+    return LCG_OK;
 }
 
 void lcg_grammar_free(lcg_grammar* G) { free_grammar_now(G); }

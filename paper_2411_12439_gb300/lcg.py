@@ -25,7 +25,7 @@ SYMBOLS = [
     "lcg_ctx_create", "lcg_ctx_destroy", "lcg_last_error", "lcg_last_build_stats", "lcg_set_kernel_timing",
     "lcg_last_kernel_times", "lcg_build", "lcg_build_into",
     "lcg_merge", "lcg_decompress", "lcg_decompress_static", "lcg_grammar_shape", "lcg_level_size", "lcg_export_level",
-    "lcg_export_start", "lcg_import", "lcg_grammar_free",
+    "lcg_export_start", "lcg_import", "lcg_packed_size", "lcg_export_packed", "lcg_import_packed", "lcg_grammar_free",
 ]
 
 
@@ -43,7 +43,7 @@ class HashFamilyC(ctypes.Structure):
 class RoundStatsC(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("phrases", ctypes.c_uint64), ("g", ctypes.c_uint64),
                 ("G", ctypes.c_uint64), ("strings", ctypes.c_uint64), ("table_cap", ctypes.c_uint64),
-                ("retries", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+                ("retries", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("parse_ms", ctypes.c_double)]
 
 
 class KernelTimeC(ctypes.Structure):
@@ -94,6 +94,9 @@ def load(build_if_missing: bool = True):
     lib.lcg_export_level.argtypes = [P, P, U32, P, P, P]
     lib.lcg_export_start.argtypes = [P, P, P, P, P]
     lib.lcg_import.argtypes = [P, U32, U32, P, P, P, P, P, P, PP]
+    lib.lcg_packed_size.argtypes = [P, ctypes.POINTER(U64)]
+    lib.lcg_export_packed.argtypes = [P, P, P, U64]
+    lib.lcg_import_packed.argtypes = [P, P, U64, PP]
     lib.lcg_grammar_free.argtypes = [P]
     lib.lcg_grammar_free.restype = None
     for name in SYMBOLS:
@@ -206,6 +209,18 @@ class Context:
         del keep
         return Grammar(self, h)
 
+    def import_packed(self, buf) -> "Grammar":
+        """lcg_import_packed: a device grammar from its packed form (a uint8
+        numpy array or a CPU uint8 tensor, 8-byte aligned)."""
+        ptr, on_dev, keep = _data_arg(buf)
+        if on_dev:
+            raise LCGError(-1, "lcg_import_packed reads host memory")
+        n = int(buf.numel() if hasattr(buf, "numel") else buf.size)
+        h = ctypes.c_void_p(0)
+        self._check(load().lcg_import_packed(self._h, ptr, n, ctypes.byref(h)))
+        del keep
+        return Grammar(self, h)
+
     def set_kernel_timing(self, enable: bool) -> None:
         """lcg_set_kernel_timing: bracket every kernel launch with CUDA events."""
         self._check(load().lcg_set_kernel_timing(self._h, int(bool(enable))))
@@ -221,8 +236,9 @@ class Context:
     def last_build_stats(self) -> dict:
         st = BuildStatsC()
         self._check(load().lcg_last_build_stats(self._h, ctypes.byref(st)))
-        rounds = [{f: int(getattr(st.round[i], f)) for f in ("n", "phrases", "g", "G", "strings", "table_cap",
-                                                             "retries")} for i in range(min(st.rounds, 64))]
+        rounds = [{**{f: int(getattr(st.round[i], f)) for f in ("n", "phrases", "g", "G", "strings", "table_cap",
+                                                                "retries")}, "parse_ms": float(st.round[i].parse_ms)}
+                  for i in range(min(st.rounds, 64))]
         return {"rounds": int(st.rounds), "async_rounds": int(st.async_rounds), "redone": bool(st.redone),
                 "kernel_launches": int(st.kernel_launches),
                 "input_bytes": int(st.input_bytes), "per_round": rounds}
@@ -274,6 +290,27 @@ class Grammar:
         cr = np.zeros(max(k, 1), dtype=np.uint32)
         self.ctx._check(lib.lcg_export_start(self.ctx._h, self._h, _np_ptr(F0), _np_ptr(cl), _np_ptr(cr)))
         return {"F0": F0, "levels": levels, "c_level": cl[:k], "c_rank": cr[:k]}
+
+    def packed_size(self) -> int:
+        n = ctypes.c_uint64(0)
+        self.ctx._check(load().lcg_packed_size(self._h, ctypes.byref(n)))
+        return int(n.value)
+
+    def export_packed(self, out=None):
+        """lcg_export_packed: the packed form in one host buffer.  ``out`` (a
+        uint8 numpy array or CPU uint8 tensor, page-locked for speed) is
+        filled and a view of its first ``packed_size()`` bytes is returned;
+        without it a new numpy array is returned."""
+        n = self.packed_size()
+        if out is None:
+            out = np.empty(n, dtype=np.uint8)
+        ptr, on_dev, keep = _data_arg(out)
+        if on_dev:
+            raise LCGError(-1, "lcg_export_packed writes host memory")
+        cap = int(out.numel() if hasattr(out, "numel") else out.size)
+        self.ctx._check(load().lcg_export_packed(self.ctx._h, self._h, ptr, cap))
+        del keep
+        return out[:n]
 
     def decompress_static(self, j: int, out) -> int:
         """lcg_decompress_static: exp(C[j]) into the CUDA uint8 tensor ``out``

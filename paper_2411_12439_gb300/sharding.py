@@ -15,15 +15,16 @@ arrays, a small fraction of the input) to a partner that imports and merges it.
 Rank 0 ends with the grammar of the collection.
 
 The grammar operations come from a ``backend`` with ``build(data, offsets)``,
-``export(g)``, ``load(exported)`` and ``merge(a, b)`` (a absorbs b; returns a),
-and the transport from a ``comm`` with ``send(buf, dst)`` / ``recv(src)`` of
-uint8 arrays.  ``CudaBackend`` and ``TorchComm`` are the ones for GPUs.
+``pack(g)`` / ``unpack(buf)`` (the packed form of lcg_export_packed) and
+``merge(a, b)`` (a absorbs b; returns a), and the transport from a ``comm``
+with ``send(buf, dst)`` / ``recv(src)`` of uint8 arrays.  ``CudaBackend`` and
+``TorchComm`` are the ones for GPUs.
 """
 from __future__ import annotations
 
 import numpy as np
 
-_MAGIC = 0x4C434753  # "LCGS"
+_MAGIC = 0x4C434753  # "LCGS": the packed form of lcg_export_packed
 
 
 def shard_by_bytes(offsets, world: int) -> list[tuple[int, int]]:
@@ -40,14 +41,21 @@ def shard_by_bytes(offsets, world: int) -> list[tuple[int, int]]:
         return [(0, k)] + [(k, k)] * (world - 1)
     mid = (off[:-1] + off[1:]) / 2.0 - off[0]
     owner = np.minimum((mid * world / total).astype(np.int64), world - 1)
-    owner = np.maximum.accumulate(owner)  # monotone (it already is; guards rounding)
     cuts = np.searchsorted(owner, np.arange(world + 1), side="left")
-    cuts[-1] = k
     return [(int(cuts[r]), int(cuts[r + 1])) for r in range(world)]
 
 
+def _pad8(a: np.ndarray) -> np.ndarray:
+    b = a.view(np.uint8)
+    r = (-b.size) % 8
+    return np.concatenate([b, np.zeros(r, dtype=np.uint8)]) if r else b
+
+
 def pack(ex: dict | None) -> np.ndarray:
-    """One uint8 buffer holding an exported grammar (None: no strings)."""
+    """The packed form (the layout of lcg_export_packed: a u64 header, then
+    per level rhs_off, rhs and F, then C and F0, every array starting at a
+    multiple of 8 bytes) of an exported grammar; None gives an empty buffer
+    (a rank without strings)."""
     if ex is None:
         return np.zeros(0, dtype=np.uint8)
     levels = ex["levels"]
@@ -58,16 +66,16 @@ def pack(ex: dict | None) -> np.ndarray:
     parts = [np.asarray(head, dtype=np.uint64).view(np.uint8)]
     for L in levels:
         parts.append(np.ascontiguousarray(L["rhs_off"], dtype=np.uint64).view(np.uint8))
-        parts.append(np.ascontiguousarray(L["rhs"], dtype=np.uint32).view(np.uint8))
-        parts.append(np.ascontiguousarray(L["F"], dtype=np.uint32).view(np.uint8))
-    parts.append(np.ascontiguousarray(ex["c_level"], dtype=np.uint32).view(np.uint8))
-    parts.append(np.ascontiguousarray(ex["c_rank"], dtype=np.uint32).view(np.uint8))
+        parts.append(_pad8(np.ascontiguousarray(L["rhs"], dtype=np.uint32)))
+        parts.append(_pad8(np.ascontiguousarray(L["F"], dtype=np.uint32)))
+    parts.append(_pad8(np.ascontiguousarray(ex["c_level"], dtype=np.uint32)))
+    parts.append(_pad8(np.ascontiguousarray(ex["c_rank"], dtype=np.uint32)))
     parts.append(np.ascontiguousarray(ex["F0"], dtype=np.uint32).view(np.uint8))
     return np.concatenate(parts)
 
 
-def unpack(buf: np.ndarray) -> dict | None:
-    """Inverse of ``pack``."""
+def unpack(buf) -> dict | None:
+    """Inverse of ``pack`` (also reads the buffers of lcg_export_packed)."""
     buf = np.ascontiguousarray(buf, dtype=np.uint8)
     if buf.size == 0:
         return None
@@ -78,8 +86,8 @@ def unpack(buf: np.ndarray) -> dict | None:
         nb = n * np.dtype(dt).itemsize
         if pos + nb > buf.size:
             raise ValueError("truncated grammar buffer")
-        a = buf[pos:pos + nb].view(dt).copy()
-        pos += nb
+        a = buf[pos:pos + nb].copy().view(dt)
+        pos += nb + (-nb) % 8
         return a
 
     magic, k, nl = (int(x) for x in take(3, np.uint64))
@@ -106,15 +114,13 @@ def merge_tree(grammar, rank: int, world: int, backend, comm):
     stride = 1
     while stride < world:
         if rank % (2 * stride) == stride:
-            comm.send(pack(None if grammar is None else backend.export(grammar)), rank - stride)
+            comm.send(np.zeros(0, dtype=np.uint8) if grammar is None else backend.pack(grammar), rank - stride)
             return None
         if rank % (2 * stride) == 0 and rank + stride < world:
-            other = unpack(comm.recv(rank + stride))
-            if other is not None:
-                if grammar is None:
-                    grammar = backend.load(other)
-                else:
-                    grammar = backend.merge(grammar, backend.load(other))
+            buf = comm.recv(rank + stride)
+            if buf.size:
+                other = backend.unpack(buf)
+                grammar = other if grammar is None else backend.merge(grammar, other)
         stride *= 2
     return grammar if rank == 0 else None
 
@@ -144,11 +150,11 @@ class CudaBackend:
     def build(self, data, offsets):
         return self.ctx.build(data, offsets)
 
-    def export(self, g) -> dict:
-        return g.export()
+    def pack(self, g) -> np.ndarray:
+        return np.asarray(g.export_packed())
 
-    def load(self, ex: dict):
-        return self.ctx.import_grammar(ex)
+    def unpack(self, buf):
+        return self.ctx.import_packed(np.ascontiguousarray(buf, dtype=np.uint8))
 
     def merge(self, a, b):
         self.ctx.merge(a, b)

@@ -24,11 +24,13 @@ class OracleBackend:
                              offsets=np.ascontiguousarray(offsets, dtype=np.uint64))
         return self.O.build(coll, self.hf)
 
-    def export(self, g):
-        return g.export()
+    def pack(self, g):
+        from paper_2411_12439_gb300 import sharding
+        return sharding.pack(g.export())
 
-    def load(self, ex):
-        return self.O.from_export(ex, self.tag)
+    def unpack(self, buf):
+        from paper_2411_12439_gb300 import sharding
+        return self.O.from_export(sharding.unpack(buf), self.tag)
 
     def merge(self, a, b):
         return a.merge(b)

@@ -81,3 +81,27 @@ def test_sharded_build_merge_tree(ctx, hf, world):
         out[rank] = sharding.build_sharded(coll.data, coll.offsets, rank, world, backend, _LocalComm(boxes, rank))
     assert not boxes
     assert O.grammars_equal(out[0].export(), O.build(coll, hf).export())
+
+
+def test_packed_form_matches_oracle_and_roundtrips(ctx, hf):
+    from paper_2411_12439_gb300 import LCGError, sharding
+    coll = li.tiny_dna_collection(base_len=60_000, k=5)
+    og = O.build(coll, hf)
+    g = ctx.build(coll.data, coll.offsets)
+    buf = np.asarray(g.export_packed())
+    assert buf.size == g.packed_size()
+    assert np.array_equal(buf, sharding.pack(og.export()))  # same bytes as the layout written out in Python
+    back = ctx.import_packed(buf)
+    assert O.grammars_equal(back.export(), og.export())
+    with pytest.raises(LCGError) as e:
+        ctx.import_packed(buf[:-8].copy())
+    assert e.value.code == -1
+    other = sharding.pack(O.build(coll, li.hash_family(seed=777)).export())
+    with pytest.raises(LCGError) as e:
+        ctx.import_packed(other)
+    assert e.value.code == -4
+    # into a caller's (page-locked) buffer
+    import torch
+    pinned = torch.empty(buf.size + 64, dtype=torch.uint8).pin_memory()
+    view = g.export_packed(pinned)
+    assert np.array_equal(view.numpy(), buf)
