@@ -96,6 +96,7 @@ constexpr int kCacheProbes = 8;
 // New table entries of a block are listed in shared memory and appended to
 // the round's claim list once the buffer is half full (and after the block's
 // last tile), so that the global counter is touched every few tiles only.
+constexpr int kChunk = (kSP + kParseThreads - 1) / kParseThreads;  // positions per thread in the break pass
 constexpr int kClaimBufB = 512;   // byte rounds (shared memory also holds the phrase cache)
 constexpr int kClaimBufR = 1024;  // rank rounds
 // Byte rounds: phrases that miss the block's cache are queued and looked up in
@@ -181,7 +182,9 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
     __shared__ u64 ckey[kLocal ? kCacheSlots : 1];
     __shared__ u64 cval[kLocal ? kCacheSlots : 1];
     __shared__ u32 sClaim[kClaimBuf];
-    __shared__ u32 sMiss[kLocal ? kMissBuf : 1];  // q | (cache slot + 1) << 16
+    // q | (cache slot + 1) << 16; during the break pass it holds the chunk summaries
+    __shared__ __align__(8) u32 sMiss[kLocal ? kMissBuf : 1];
+    __shared__ u64 sSummR[kLocal ? 1 : kParseThreads];
     __shared__ u32 s_nmiss;
     __shared__ u64 s_tail_end;
     __shared__ u32 s_nclaim;
@@ -259,31 +262,76 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
 
         // 2. break bits (Eq. rand_types): a phrase starts at x when x starts a
         //    string, or f[x-1] > f[x] and the first fingerprint right of x (in
-        //    the string) that differs from f[x] is larger than f[x]
-        for (int w = warp; w < (ns + 31) / 32; w += kParseThreads / 32) {
-            const int x = w * 32 + lane;
-            bool brk = false;
-            if (x < ns) {
-                if (is_start(x)) {
-                    brk = true;
-                } else {
-                    const u32 cur = fat(x);
-                    if (fat(x - 1) > cur) {
-                        int y = x + 1;
-                        while (y < ns && !is_start(y) && fat(y) == cur) y++;
-                        u64 nd;
-                        if (y < ns) nd = is_start(y) ? kNone : (u64)fat(y);
-                        else if (s_end == n || is_start(ns)) nd = kNone;
-                        else {
-                            const u32 jl = string_of(a.soff, kact, t0 + x);
-                            nd = scan_right_diff<T>(S, fp, s_end, __ldg(a.soff + jl + 1), cur);
-                        }
-                        brk = (nd != kNone) && (nd > (u64)cur);
+        //    the string) that differs from f[x] is larger than f[x].
+        //    Thread t takes the kChunk positions from t * kChunk on, holds their
+        //    fingerprints in registers and walks them right to left.  The first
+        //    differing fingerprint right of its last position comes from the
+        //    next chunk: its first position, else the chunk's summary (the
+        //    first later position of that chunk that starts a string or
+        //    differs from its first fingerprint), else the chunk after.
+        {
+            constexpr int C = kChunk;
+            constexpr u64 kUnres = 1ull << 33;  // summary: the chunk is one run
+            static_assert(C * kParseThreads >= kSP, "chunks cover the staged positions");
+            u64* summ = kLocal ? reinterpret_cast<u64*>(sMiss) : sSummR;
+            const int x0 = tid * C;
+            u32 f[C + 1];
+            u32 stm = 0;  // bit i: position x0 + i starts a string
+#pragma unroll
+            for (int i = 0; i <= C; i++) {
+                const int x = x0 + i;
+                f[i] = (x < ns) ? fat(x) : 0u;
+                if (x <= ns && is_start(x)) stm |= 1u << i;
+            }
+            u64 sm = kUnres;
+#pragma unroll
+            for (int i = C - 1; i >= 1; i--)
+                if (x0 + i < ns) {
+                    if ((stm >> i) & 1u) sm = kNone;
+                    else if (f[i] != f[0]) sm = f[i];
+                }
+            summ[tid] = sm;
+            __syncthreads();
+            // first fingerprint other than v at or after position y (in the
+            // string), or kNone
+            auto nd_from = [&](int y, u32 v) -> u64 {
+                while (true) {
+                    if (y >= ns) {
+                        if (s_end == n || is_start(ns)) return kNone;
+                        const u32 jl = string_of(a.soff, kact, t0 + (u64)ns - 1);
+                        return scan_right_diff<T>(S, fp, s_end, __ldg(a.soff + jl + 1), v);
+                    }
+                    if (is_start(y)) return kNone;
+                    const u32 fy = fat(y);
+                    if (fy != v) return fy;
+                    const u64 c = summ[y / C];
+                    if (c != kUnres) return c;
+                    y = min(y + C, ns);
+                }
+            };
+            u32 bits = 0;
+            if (x0 < ns) {
+                u64 nd = 0;
+                u32 fl = 0;
+#pragma unroll
+                for (int i = C - 1; i >= 0; i--) {
+                    const int x = x0 + i;
+                    if (x < ns) {
+                        if (i == C - 1 || x + 1 >= ns) nd = nd_from(x + 1, f[i]);
+                        else if ((stm >> (i + 1)) & 1u) nd = kNone;
+                        else if (f[i + 1] != f[i]) nd = f[i + 1];
+                        // else: nd of position x + 1 (the value in nd) carries over
+                        fl = (i == 0) ? fat(x0 - 1) : f[i - 1];
+                        const bool brk = ((stm >> i) & 1u) || (fl > f[i] && nd != kNone && nd > (u64)f[i]);
+                        if (brk) bits |= 1u << i;
                     }
                 }
             }
-            const u32 word = __ballot_sync(0xffffffffu, brk);
-            if (lane == 0) sbits[w] = word;
+            if (bits) {  // set bits lie below ns <= NWS * 32
+                atomicOr(&sbits[x0 >> 5], bits << (x0 & 31));
+                if ((x0 & 31) + C > 32 && (bits >> (32 - (x0 & 31))) != 0)
+                    atomicOr(&sbits[(x0 >> 5) + 1], bits >> (32 - (x0 & 31)));
+            }
         }
         __syncthreads();
 
