@@ -54,6 +54,9 @@ def parse_args():
                    help="only run this many batched builds of the workload and exit (for profiler captures)")
     p.add_argument("--profile-strings", type=int, default=0,
                    help="with --profile-builds: only the first this many strings of the workload")
+    p.add_argument("--profile-warmup", type=int, default=0,
+                   help="with --profile-builds: builds run before the profiler range "
+                        "(cudaProfilerStart/Stop; use ncu --profile-from-start off)")
     return p.parse_args()
 
 
@@ -244,9 +247,14 @@ def run_ours(args):
         offs = coll.offsets
         if args.profile_strings:
             offs = offs[:min(args.profile_strings, coll.k) + 1]
+        for _ in range(args.profile_warmup):
+            ctx.build(d, offs).free()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
         for _ in range(args.profile_builds):
             ctx.build(d, offs).free()
         torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
         return 0
 
     for _ in range(args.warmup):

@@ -455,9 +455,17 @@ void free_round(lcg_ctx* ctx, RoundBufs& b) {
     free_table(ctx, b);
 }
 
+// Bits that hold every rank below `count` (at least 1).
+int rank_width(u64 count) {
+    int w = 1;
+    while (w < 31 && (1ull << w) < count) w++;
+    return w;
+}
+
 RoundArgs round_args(lcg_ctx* ctx, lcg_grammar* R, const RoundInput& in, RoundBufs& b, u32 i) {
     RoundArgs a{};
     a.sym_bytes = in.symb;
+    a.sym_w = in.symb == 1 ? 8 : 31;
     a.S = in.S;
     a.Sf = in.Sf;
     a.n = in.n;
@@ -601,6 +609,9 @@ void round_sync(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32 i, bool agains
     RoundArgs a = round_args(ctx, R, in, b, i);
     a.d_n = nullptr;
     a.d_k = nullptr;
+    // inline keys as narrow as the level below allows; tables of resident
+    // grammars keep the full width
+    if (i > 1 && !against_resident) a.sym_w = rank_width(R->lv[i - 2].g);
     if (against_resident && L.g > 0) {
         ensure_resident(ctx, R, i, L.g);
         a.rtab_keys = L.rkeys;
@@ -700,6 +711,8 @@ int rounds_async(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32& i) {
         RoundArgs a = round_args(ctx, R, in, b, r);
         // a round stops early when the one before it failed
         if (r > 1) a.ds_prev = ctx->ds_arr + (r - 2);
+        // every rank of the level below is under its capacity
+        if (r > 1) a.sym_w = rank_width(R->lv[r - 2].cap_g);
         const double P_est = ctx->p_hint[r] * (double)n_est;
         const double g_est = ctx->ratio_hint[r] * P_est;
         const double G_est = ctx->glen_hint[r] * g_est;

@@ -92,8 +92,9 @@ __global__ void k_merge_lookup(const u32* __restrict__ brhs, const u64* __restri
         const u64 s = brhs_off[r], e = brhs_off[r + 1], len = e - s;
         u64 H = 0;
         for (u64 x = e; x-- > s;) H = addmod61(mulmod61(H, lh.c), (u64)__ldg(aFprev + brhs[x]));
-        const bool hashed = len > inline_max(kByte);
-        const Key128 key = hashed ? key_hashed(H, len, 0) : key_inline([&](u64 j) { return brhs[s + j]; }, len, kByte);
+        const int w = kByte ? 8 : kRankBits;
+        const bool hashed = len > inline_max(w);
+        const Key128 key = hashed ? key_hashed(H, len, 0) : key_inline([&](u64 j) { return brhs[s + j]; }, len, w);
         u64 found = ~0ull;
         if (at.cap) {
             found = table_find(at, key, hashed, [&](u64 ra) {

@@ -22,6 +22,7 @@ struct RoundCounts {
 
 struct RoundArgs {
     int sym_bytes;        // 1 in round 1 (bytes), 4 afterwards (ranks)
+    int sym_w;            // bits per symbol in the round's inline keys (every symbol < 2^sym_w)
     const void* S;        // T^i
     const u32* Sf;        // fingerprints of T^i (rounds >= 2)
     u64 n;                // |T^i| (when d_n is null)

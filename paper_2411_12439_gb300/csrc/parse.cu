@@ -335,23 +335,23 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
         }
         __syncthreads();
 
-        // 3. phrase starts of the tile, in order
-        u32 word = 0;
-        if (tid < NWT) {
-            word = sbits[tid];
-            const int lo = tid * 32;
-            if (lo >= nt) word = 0;
-            else if (nt - lo < 32) word &= (1u << (nt - lo)) - 1u;
-        }
+        // 3. phrase starts of the tile, in order: four threads per break word,
+        //    eight bits each
+        static_assert(NWT * 4 == kParseThreads, "four threads per tile word");
+        const int wq = tid >> 2, bq = (tid & 3) * 8;
+        u32 word = sbits[wq];
+        if (wq * 32 >= nt) word = 0;
+        else if (nt - wq * 32 < 32) word &= (1u << (nt - wq * 32)) - 1u;
+        const u32 part = (word >> bq) & 0xFFu;
         u64 cnt;
-        const u64 woff = block_excl_scan((u64)__popc(word), cnt);
-        if (tid < NWT) {
-            swp[tid] = (u32)woff;
-            u32 m = word, o = (u32)woff;
+        const u64 poff = block_excl_scan((u64)__popc(part), cnt);
+        if ((tid & 3) == 0) swp[wq] = (u32)poff;
+        {
+            u32 m = part, o = (u32)poff;
             while (m) {
                 const int b = __ffs(m) - 1;
                 m &= m - 1;
-                sP[o++] = (unsigned short)(tid * 32 + b);
+                sP[o++] = (unsigned short)(wq * 32 + bq + b);
             }
         }
         if (tid == 0) {
@@ -381,10 +381,12 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
             }
             return (u32)S[t0 + x];
         };
-        auto lookup = [&](u32 q, u64 st, u64 en) -> u32 {
+        // the slot of phrase q = [st, en); *claimed when this call made the entry
+        auto lookup = [&](u32 q, u64 st, u64 en, bool* claimed) -> u32 {
+            *claimed = false;
             const u64 len = en - st;
             if (len > kMaxPhraseLen) { set_error(a.ds, kErrPhraseLong); return ~0u; }
-            const bool hashed = len > inline_max(kByte);
+            const bool hashed = len > inline_max(a.sym_w);
             Key128 key;
             if (hashed) {
                 // H = sum_j F[Q_j] c^{j-1} mod p, by Horner from the last symbol
@@ -395,7 +397,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                 }
                 key = key_hashed(H, len, t0 + st);
             } else {
-                key = key_inline([&](u64 j) { return sym(st + j); }, len, kByte);
+                key = key_inline([&](u64 j) { return sym(st + j); }, len, a.sym_w);
             }
             if (rt.cap) {
                 const u64 r = table_find(rt, key, hashed, [&](u64 rank) {
@@ -406,23 +408,42 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                 });
                 if (r != ~0ull) return kResidentBit | (u32)r;
             }
-            bool claimed = false;
             const u64 slot = table_claim_or_find(bt, key, hashed, okey0 + q, [&](u64 ref) {
                 for (u64 j = 0; j < len; j++)
                     if (S[ref + j] != S[t0 + st + j]) return false;
                 return true;
-            }, &claimed, a.ds);
-            if (claimed) {
-                atomicAdd(&s_claim_len, len);
-                const u32 c = atomicAdd(&s_nclaim, 1u);
-                if (c < (u32)kClaimBuf) {
-                    sClaim[c] = (u32)slot;
-                } else {  // buffer full: append directly
-                    const u64 g = atomicAdd(&a.ds->claims, 1ull);
-                    if (g < bt.cap) a.claims[g] = (u32)slot;
-                }
-            }
+            }, claimed, a.ds);
             return (u32)slot;
+        };
+        // New entries join the block's claim buffer (or, when it is full, the
+        // round's list at once).  claim_warp is called by all lanes of a warp
+        // together and makes one shared-memory update per warp.
+        auto claim_one = [&](u32 slot, u64 len, u32 c) {
+            if (c < (u32)kClaimBuf) {
+                sClaim[c] = slot;
+            } else {
+                const u64 g = atomicAdd(&a.ds->claims, 1ull);
+                if (g < bt.cap) a.claims[g] = slot;
+            }
+        };
+        auto claim_warp = [&](bool claimed, u32 slot, u64 len) {
+            const unsigned m = __ballot_sync(0xffffffffu, claimed);
+            if (m == 0) return;
+            u64 sum = claimed ? len : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            const int leader = __ffs(m) - 1;
+            u32 base = 0;
+            if (lane == leader) {
+                base = atomicAdd(&s_nclaim, (u32)__popc(m));
+                atomicAdd(&s_claim_len, sum);
+            }
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (claimed) claim_one(slot, len, base + (u32)__popc(m & ((1u << lane) - 1u)));
+        };
+        auto claim_single = [&](u32 slot, u64 len) {
+            atomicAdd(&s_claim_len, len);
+            claim_one(slot, len, atomicAdd(&s_nclaim, 1u));
         };
 
         if constexpr (kLocal) {
@@ -476,7 +497,9 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                         sMiss[m] = q | ((u32)(free_h + 1) << 16);
                         continue;
                     }
-                    slot = lookup(q, st, en);  // queue full: at once
+                    bool claimed;
+                    slot = lookup(q, st, en, &claimed);  // queue full: at once
+                    if (claimed) claim_single(slot, len);
                     if (cacheable && free_h >= 0 && slot != ~0u && !(slot & kResidentBit))
                         cache_insert(free_h, short_key(st, (u32)len), q, slot);
                 }
@@ -484,19 +507,39 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
             }
             __syncthreads();
             const u32 nm = min(s_nmiss, (u32)kMissBuf);
-            for (u32 i = tid; i < nm; i += kParseThreads) {
-                const u32 e = sMiss[i];
-                const u32 q = e & 0xFFFFu;
-                const int free_h = (int)(e >> 16) - 1;
-                const u32 st = sP[q];
-                const u64 en = phrase_end(q);
-                const u32 slot = lookup(q, st, en);
-                if (free_h >= 0 && slot != ~0u && !(slot & kResidentBit))
-                    cache_insert(free_h, short_key(st, (u32)(en - st)), q, slot);
-                a.P_slot[okey0 + q] = slot;
+            for (u32 i0 = 0; i0 < nm; i0 += kParseThreads) {  // whole warps take each step
+                const u32 i = i0 + tid;
+                bool claimed = false;
+                u32 slot = ~0u;
+                u64 len = 0;
+                if (i < nm) {
+                    const u32 e = sMiss[i];
+                    const u32 q = e & 0xFFFFu;
+                    const int free_h = (int)(e >> 16) - 1;
+                    const u32 st = sP[q];
+                    const u64 en = phrase_end(q);
+                    len = en - st;
+                    slot = lookup(q, st, en, &claimed);
+                    if (free_h >= 0 && slot != ~0u && !(slot & kResidentBit))
+                        cache_insert(free_h, short_key(st, (u32)len), q, slot);
+                    a.P_slot[okey0 + q] = slot;
+                }
+                claim_warp(claimed, slot, len);
             }
         } else {
-            for (u32 q = tid; q < cntq; q += kParseThreads) a.P_slot[okey0 + q] = lookup(q, sP[q], phrase_end(q));
+            for (u32 q0 = 0; q0 < cntq; q0 += kParseThreads) {  // whole warps take each step
+                const u32 q = q0 + tid;
+                bool claimed = false;
+                u32 slot = ~0u;
+                u64 len = 0;
+                if (q < cntq) {
+                    const u64 st = sP[q], en = phrase_end(q);
+                    len = en - st;
+                    slot = lookup(q, st, en, &claimed);
+                    a.P_slot[okey0 + q] = slot;
+                }
+                claim_warp(claimed, slot, len);
+            }
         }
         __syncthreads();
 
@@ -701,7 +744,7 @@ __global__ void k_rules(const RoundArgs a) {
         const u64 off = a.G_base + a.xlen[r];
         const u64 rank = a.g_base + r;
         a.rhs_off[rank] = off;
-        auto get = [&](u64 j) -> u32 { return hashed ? (u32)S[k.lo + j] : key_sym(k, j, kByte); };
+        auto get = [&](u64 j) -> u32 { return hashed ? (u32)S[k.lo + j] : key_sym(k, j, a.sym_w); };
         u64 H = 0;
         for (u64 j = len; j-- > 0;) {
             const u32 v = get(j);
@@ -808,7 +851,7 @@ __global__ void k_resident_build(const u32* __restrict__ rhs, const u64* __restr
         const u64 s = rhs_off[r], e = rhs_off[r + 1];
         u64 H = 0;
         for (u64 y = e; y-- > s;) H = addmod61(mulmod61(H, lh.c), (u64)__ldg(Fprev + rhs[y]));
-        const Key128 k = rule_key([&](u64 j) { return rhs[s + j]; }, e - s, kByte, H, r);
+        const Key128 k = rule_key([&](u64 j) { return rhs[s + j]; }, e - s, kByte ? 8 : kRankBits, H, r);
         table_put(t, k, r, ds);
     }
 }

@@ -7,9 +7,9 @@
 //
 // Keys are 128 bits.  Short phrases are stored exactly ("inline" keys): the
 // top 4 bits of `hi` hold the length q, and the symbols are packed from bit 0
-// upwards, 8 bits each for bytes (q <= 14) or 31 bits each for ranks (q <= 4,
-// ranks being < 2^31).  Two inline keys are equal exactly when the phrases
-// are.  A longer phrase gets a "hashed" key: top 4 bits 0, its length in bits
+// upwards in the 124 bits left, w bits each (8 for bytes; for ranks the width
+// of the level below, at most 31), so q <= min(15, 124 / w).  Two inline keys
+// of one width are equal exactly when the phrases are.  A longer phrase gets a "hashed" key: top 4 bits 0, its length in bits
 // 32..59 of `hi` and a 32-bit hash below, with `lo` naming where its content
 // can be read; a hashed-key match is confirmed by comparing the contents
 // symbol by symbol.  Slots are claimed with one 128-bit compare-and-swap.
@@ -36,8 +36,15 @@ constexpr u64 kEmptyHi = ~0ull;
 constexpr int kHiBits = 60;
 constexpr u64 kMaxPhraseLen = (1ull << 28) - 1;  // longest phrase a hashed key can describe
 
-__device__ __forceinline__ int sym_bits(bool bytes) { return bytes ? 8 : 31; }
-__device__ __forceinline__ u64 inline_max(bool bytes) { return bytes ? 14 : 4; }
+// Bits per symbol in inline keys: 8 for bytes; for ranks a width w with every
+// rank of the level below < 2^w.  A round's own table uses the smallest such w
+// (so that more phrases fit inline); tables that outlive a round (resident
+// grammars, merges) use kRankBits.
+constexpr int kRankBits = 31;
+__device__ __forceinline__ u64 inline_max(int w) {
+    const int m = 124 / w;
+    return m < 15 ? (u64)m : 15ull;
+}
 
 __device__ __forceinline__ void put_bits(u64& hi, u64& lo, int pos, u64 v, int b) {
     if (pos + b <= kHiBits) {
@@ -59,8 +66,7 @@ __device__ __forceinline__ u64 get_bits(u64 hi, u64 lo, int pos, int b) {
 }
 
 template <typename Get>
-__device__ __forceinline__ Key128 key_inline(Get get, u64 len, bool bytes) {
-    const int b = sym_bits(bytes);
+__device__ __forceinline__ Key128 key_inline(Get get, u64 len, int b) {
     u64 hi = len << kHiBits, lo = 0;
     for (u64 j = 0; j < len; j++) put_bits(hi, lo, (int)j * b, (u64)get(j), b);
     return Key128{lo, hi};
@@ -79,8 +85,7 @@ __device__ __forceinline__ u64 key_len(const Key128& k) {
 }
 
 // symbol j of an inline key
-__device__ __forceinline__ u32 key_sym(const Key128& k, u64 j, bool bytes) {
-    const int b = sym_bits(bytes);
+__device__ __forceinline__ u32 key_sym(const Key128& k, u64 j, int b) {
     return (u32)get_bits(k.hi, k.lo, (int)j * b, b);
 }
 
@@ -191,8 +196,8 @@ __device__ __forceinline__ void table_put(ContentTable t, const Key128& k, u64 v
 // (bytes at level 1), with polynomial fingerprint H, for a table whose values
 // are ranks: hashed keys name the rank.
 template <typename Get>
-__device__ __forceinline__ Key128 rule_key(Get get, u64 len, bool bytes, u64 H, u64 rank) {
-    if (len <= inline_max(bytes)) return key_inline(get, len, bytes);
+__device__ __forceinline__ Key128 rule_key(Get get, u64 len, int w, u64 H, u64 rank) {
+    if (len <= inline_max(w)) return key_inline(get, len, w);
     return key_hashed(H, len, rank);
 }
 
