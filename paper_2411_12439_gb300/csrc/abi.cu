@@ -390,6 +390,9 @@ struct RoundBufs {
     u32* Tnext = nullptr;
     u32* Fnext = nullptr;
     u32* tile_str = nullptr;
+    u32* brk = nullptr;
+    u32* sbm = nullptr;
+    u64 sbm_words = 0;
     unsigned char* tkeys = nullptr;
     u64* tvals = nullptr;
     u32* claims = nullptr;
@@ -415,6 +418,10 @@ void alloc_round(lcg_ctx* ctx, RoundBufs& b, u64 n_bound, u32 kk) {
     b.Tnext = dalloc<u32>(ctx, b.Pmax);
     b.Fnext = dalloc<u32>(ctx, b.Pmax);
     b.tile_str = dalloc<u32>(ctx, b.tiles);
+    b.brk = dalloc<u32>(ctx, b.tiles * parse_tile_positions(1) / 32);
+    b.sbm_words = b.tiles * parse_tile_positions(1) / 32 + 2;  // positions 0 .. n inclusive
+    b.sbm = dalloc<u32>(ctx, b.sbm_words);
+    ck(ctx, cudaMemsetAsync(b.sbm, 0, b.sbm_words * sizeof(u32), ctx->st), "memset starts");
 }
 
 void alloc_table(lcg_ctx* ctx, RoundBufs& b, u64 cap) {
@@ -449,7 +456,8 @@ void alloc_naming(lcg_ctx* ctx, RoundBufs& b, u64 g_alloc) {
 // Free a round's buffers except those that become the next round's input.
 void free_round(lcg_ctx* ctx, RoundBufs& b) {
     for (void* p : {(void*)b.string_first, (void*)b.R_phr, (void*)b.R_sid, (void*)b.P_slot, (void*)b.tile_cnt,
-                    (void*)b.tile_pfx, (void*)b.tile_str, (void*)b.first_bits, (void*)b.first_prefix,
+                    (void*)b.tile_pfx, (void*)b.tile_str, (void*)b.brk, (void*)b.sbm, (void*)b.first_bits,
+                    (void*)b.first_prefix,
                     (void*)b.slot_r, (void*)b.len_r, (void*)b.xlen})
         dfree(ctx, p);
     free_table(ctx, b);
@@ -480,6 +488,9 @@ RoundArgs round_args(lcg_ctx* ctx, lcg_grammar* R, const RoundInput& in, RoundBu
     a.tiles_bound = b.tiles;
     a.string_first = b.string_first;
     a.tile_str = b.tile_str;
+    a.brk = b.brk;
+    a.sbm = b.sbm;
+    a.sbm_words = b.sbm_words;
     a.tile_cnt = b.tile_cnt;
     a.tile_pfx = b.tile_pfx;
     a.ctr = ctx->ctr;
@@ -513,10 +524,14 @@ void set_table(RoundArgs& a, RoundBufs& b) {
 // Parse: tile strings, k_parse, tile scan, strings.
 void enqueue_parse(lcg_ctx* ctx, RoundArgs& a, u64 n_for_bytes) {
     ck(ctx, launch_tile_strings(a, ctx->st), "k_tile_strings");
+    int hb = kt_begin(ctx, "k_breaks", (a.sym_bytes == 1 ? 1.0 : 4.0) * n_for_bytes + (double)n_for_bytes / 8.0);
+    ck(ctx, launch_breaks(a, ctx->st), "k_breaks");
+    kt_end(ctx, hb);
     const double tab_bytes = a.tab_cap * (double)(key_bytes() + sizeof(u64));
     const double tbytes = tab_bytes > kL2Bytes ? 32.0 * (double)n_for_bytes / 3.0 : 0.0;
     int h = kt_begin(ctx, "k_parse",
-                     (a.sym_bytes == 1 ? 1.0 : 8.0) * n_for_bytes + 4.0 * (double)n_for_bytes / 3.0 + tbytes, a.level);
+                     (a.sym_bytes == 1 ? 1.0 : 4.0) * n_for_bytes + (double)n_for_bytes / 8.0 +
+                         4.0 * (double)n_for_bytes / 3.0 + tbytes, a.level);
     ck(ctx, launch_parse(a, ctx->st), "k_parse");
     kt_end(ctx, h);
     const u64 stiles = std::max<u64>(1, scan2_tiles_for(a.tiles_bound));
@@ -531,7 +546,7 @@ void enqueue_parse(lcg_ctx* ctx, RoundArgs& a, u64 n_for_bytes) {
     h = kt_begin(ctx, "k_strings", 40.0 * a.k);
     ck(ctx, launch_strings(a, ctx->st), "k_strings");
     kt_end(ctx, h);
-    ctx->launches += 4;
+    ctx->launches += 5;
 }
 
 // Naming and rewrite: mark, popcount scan, rank, length scan, rules, rewrite.

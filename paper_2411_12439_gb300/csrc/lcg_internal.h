@@ -37,6 +37,9 @@ struct RoundArgs {
     // parse pass
     u64 tiles_bound;      // parse tiles the buffers were sized for
     u64* d_tiles;         // parse tiles of the round (written by k_tile_strings)
+    u32* brk;             // break bitmap of T^i (k_breaks), 64 words per parse tile
+    u32* sbm;             // bitmap of string starts of T^i (and of n)
+    u64 sbm_words;
     u32* tile_str;        // per parse tile: the string holding its first position
     u32* tile_cnt;        // per parse tile: phrases starting in it
     u64* tile_pfx;        // exclusive prefix of tile_cnt: global index of a tile's first phrase
@@ -99,6 +102,7 @@ size_t lb2_bytes(u64 tiles);
 size_t key_bytes();
 
 cudaError_t launch_tile_strings(const RoundArgs& a, cudaStream_t st);
+cudaError_t launch_breaks(const RoundArgs& a, cudaStream_t st);
 cudaError_t launch_parse(const RoundArgs& a, cudaStream_t st);
 cudaError_t launch_strings(const RoundArgs& a, cudaStream_t st);
 cudaError_t launch_mark(const RoundArgs& a, u64 g_grid, cudaStream_t st);

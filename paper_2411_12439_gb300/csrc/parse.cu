@@ -96,7 +96,6 @@ constexpr int kCacheProbes = 8;
 // New table entries of a block are listed in shared memory and appended to
 // the round's claim list once the buffer is half full (and after the block's
 // last tile), so that the global counter is touched every few tiles only.
-constexpr int kChunk = (kSP + kParseThreads - 1) / kParseThreads;  // positions per thread in the break pass
 constexpr int kClaimBufB = 512;   // byte rounds (shared memory also holds the phrase cache)
 constexpr int kClaimBufR = 1024;  // rank rounds
 // Byte rounds: phrases that miss the block's cache are queued and looked up in
@@ -111,26 +110,6 @@ __device__ u64 scan_right_diff(const T* S, FpSource<T> fp, u64 from, u64 strend,
     }
     return kNone;
 }
-
-// First phrase start at or after `from` (or n), evaluated from global memory.
-template <typename T>
-__device__ u64 global_next_break(const T* S, FpSource<T> fp, u64 n, const u64* soff, u32 k, u64 from) {
-    if (from >= n) return n;
-    const u32 j = string_of(soff, k, from);
-    if (__ldg(soff + j) == from) return from;
-    const u64 strend = __ldg(soff + j + 1);
-    u32 fl = fp(S[from - 1]);
-    for (u64 y = from; y < strend; y++) {
-        const u32 fy = fp(S[y]);
-        if (fl > fy) {
-            const u64 nd = scan_right_diff<T>(S, fp, y + 1, strend, fy);
-            if (nd != kNone && nd > (u64)fy) return y;
-        }
-        fl = fy;
-    }
-    return strend;
-}
-
 
 // Load n_sym symbols of type V from src (16-byte aligned when `vec`) into the
 // shared array dst, with every 16-byte load issued before any is stored.
@@ -159,6 +138,139 @@ __device__ __forceinline__ void stage_vec(V* dst, const V* src, int n_sym, bool 
     }
 }
 
+// --------------------------------------------------------------------------
+// k_breaks: the round's break bitmap (Eq. rand_types)
+// --------------------------------------------------------------------------
+//
+// A phrase starts at x when x starts a string, or f[x-1] > f[x] and the first
+// fingerprint right of x (within the string) that differs from f[x] is larger
+// than f[x].  Thread t of a block step decides kBrkPer consecutive positions
+// from registers, right to left; two threads make one word of the bitmap.  The
+// first differing fingerprint right of a thread's last position comes from the
+// next thread's first position, else from that thread's summary (the first
+// later position of its kBrkPer that starts a string or differs from its first
+// fingerprint), else from the thread after; past the block step it is read
+// from global memory.
+
+constexpr int kBrkThreads = 256;
+constexpr int kBrkPer = 16;                                // positions per thread
+constexpr u64 kBrkSpan = (u64)kBrkThreads * kBrkPer;      // positions per block step
+static_assert(kBrkSpan % kTP == 0, "a block step starts a parse tile");
+
+template <typename T>
+__global__ void __launch_bounds__(kBrkThreads) k_breaks(const RoundArgs a, u64 nblocks) {
+    constexpr bool kByte = sizeof(T) == 1;
+    constexpr u64 kUnres = 1ull << 33;  // summary: the thread's positions are one run
+    constexpr int P = kBrkPer;
+    constexpr int SW = (int)(kBrkSpan / 32);  // string-start words of a step
+    __shared__ u32 sF0[kByte ? 256 : 1];
+    __shared__ u32 sst[SW + 1];  // string starts at base .. base + kBrkSpan
+    __shared__ u64 ssum[kBrkThreads];
+    __shared__ u32 sfirst[kBrkThreads];  // fingerprint of each thread's first position
+    if (round_halted(a)) return;
+    const T* S = (const T*)a.S;
+    const u32* Sf = a.Sf;
+    const u64 n = round_n(a);
+    const u32 k = round_k(a);
+    const int tid = threadIdx.x, lane = tid & 31;
+    if constexpr (kByte)
+        for (int x = tid; x < 256; x += kBrkThreads) sF0[x] = a.Fprev[x];
+    auto fpos = [&](u64 x) -> u32 {  // fingerprint of position x < n
+        if constexpr (kByte) return sF0[S[x]]; else return __ldg(Sf + x);
+    };
+    const bool aligned = kByte ? (reinterpret_cast<unsigned long long>(S) & 15) == 0
+                               : (reinterpret_cast<unsigned long long>(Sf) & 15) == 0;
+    nblocks = min(nblocks, (n + kBrkSpan - 1) / kBrkSpan);
+    for (u64 b = blockIdx.x; b < nblocks; b += gridDim.x) {
+        const u64 base = b * kBrkSpan;
+        const u64 bend = min(base + kBrkSpan, n);
+        // string starts at base .. base + kBrkSpan (bitmap of k_tile_strings;
+        // n counts as one)
+        for (int w = tid; w <= SW; w += kBrkThreads) {
+            const u64 gw = base / 32 + (u64)w;
+            sst[w] = gw < a.sbm_words ? __ldg(a.sbm + gw) : 0u;
+        }
+        const u64 x0 = base + (u64)P * (u64)tid;
+        u32 f[P];
+        if (aligned && x0 + P <= n) {
+            if constexpr (kByte) {
+                const uint4 v = *reinterpret_cast<const uint4*>(S + x0);
+                const u32 w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int i = 0; i < P; i++) f[i] = sF0[(w[i >> 2] >> (8 * (i & 3))) & 0xFFu];
+            } else {
+#pragma unroll
+                for (int q = 0; q < P / 4; q++) {
+                    const uint4 v = *reinterpret_cast<const uint4*>(Sf + x0 + 4 * q);
+                    f[4 * q] = v.x;
+                    f[4 * q + 1] = v.y;
+                    f[4 * q + 2] = v.z;
+                    f[4 * q + 3] = v.w;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < P; i++) f[i] = (x0 + i < n) ? fpos(x0 + i) : 0u;
+        }
+        __syncthreads();  // sst loaded
+        // starts at x0 .. x0 + P (P + 1 bits)
+        const int sb0 = P * tid;
+        const u64 win = (u64)sst[sb0 >> 5] | ((u64)sst[(sb0 >> 5) + 1] << 32);
+        const u32 stm = (u32)((win >> (sb0 & 31)) & ((1ull << (P + 1)) - 1));
+        u64 sm = kUnres;
+#pragma unroll
+        for (int i = P - 1; i >= 1; i--)
+            if (x0 + i < bend) {
+                if ((stm >> i) & 1u) sm = kNone;
+                else if (f[i] != f[0]) sm = f[i];
+            }
+        ssum[tid] = sm;
+        sfirst[tid] = f[0];
+        // f of position x0 - 1: the previous thread's last, or global memory
+        u32 fprev = __shfl_up_sync(0xffffffffu, f[P - 1], 1);
+        if (lane == 0 && x0 > 0 && x0 - 1 < n) fprev = fpos(x0 - 1);
+        __syncthreads();
+        // first fingerprint other than v at or after position y (a thread's
+        // first position, or past the block step), within the string; or kNone
+        auto nd_from = [&](u64 y, u32 v) -> u64 {
+            while (y < bend) {
+                const u32 t = (u32)((y - base) / P);
+                const u32 bit = (u32)(y - base);
+                if ((sst[bit >> 5] >> (bit & 31)) & 1u) return kNone;
+                if (sfirst[t] != v) return sfirst[t];
+                if (ssum[t] != kUnres) return ssum[t];
+                y += P;
+            }
+            if (y >= n) return kNone;
+            // past the block step: follow the run in global memory to its string's end
+            const u32 j = string_of(a.soff, k, y - 1);
+            const u64 strend = __ldg(a.soff + j + 1);
+            if (y >= strend) return kNone;
+            return scan_right_diff<T>(S, FpSource<T>{kByte ? sF0 : a.Fprev}, y, strend, v);
+        };
+        u32 bits = 0;
+        if (x0 < bend) {
+            u64 nd = 0;
+#pragma unroll
+            for (int i = P - 1; i >= 0; i--) {
+                const u64 x = x0 + (u64)i;
+                if (x < bend) {
+                    if (i == P - 1 || x + 1 >= bend) nd = ((stm >> (i + 1)) & 1u) ? kNone : nd_from(x + 1, f[i]);
+                    else if ((stm >> (i + 1)) & 1u) nd = kNone;
+                    else if (f[i + 1] != f[i]) nd = f[i + 1];
+                    // else: the run goes on, nd of x + 1 carries over
+                    const u32 fl = (i == 0) ? fprev : f[i - 1];
+                    if (((stm >> i) & 1u) || (fl > f[i] && nd != kNone && nd > (u64)f[i])) bits |= 1u << i;
+                }
+            }
+        }
+        // two threads per word (P = 16)
+        const u32 hi = __shfl_down_sync(0xffffffffu, bits, 1);
+        if ((tid & 1) == 0 && x0 < bend) a.brk[x0 >> 5] = bits | (hi << 16);
+        __syncthreads();
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse(const RoundArgs a, u64 ntiles) {
     constexpr int NWS = kSP / 32;    // staged break words
@@ -171,10 +283,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
     __shared__ u32 sF0[kByte ? 256 : 1];
     __shared__ __align__(16) unsigned char sb[kByte ? kSP : 16];  // bytes of tile positions
     __shared__ __align__(16) u32 sT[kByte ? 4 : kSP];             // ranks of tile positions
-    __shared__ __align__(16) u32 sf[kByte ? 4 : kSP];             // their fingerprints
-    __shared__ u32 s_left;                                        // fingerprint of position -1
     __shared__ u32 sbits[NWS];
-    __shared__ u32 sstart[NWS + 1];
     __shared__ u32 swp[NWT];
     __shared__ unsigned short sP[kTP];
     // byte rounds: per-block cache of phrase (packed bytes) -> slot, kept across
@@ -182,9 +291,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
     __shared__ u64 ckey[kLocal ? kCacheSlots : 1];
     __shared__ u64 cval[kLocal ? kCacheSlots : 1];
     __shared__ u32 sClaim[kClaimBuf];
-    // q | (cache slot + 1) << 16; during the break pass it holds the chunk summaries
-    __shared__ __align__(8) u32 sMiss[kLocal ? kMissBuf : 1];
-    __shared__ u64 sSummR[kLocal ? 1 : kParseThreads];
+    __shared__ u32 sMiss[kLocal ? kMissBuf : 1];  // q | (cache slot + 1) << 16
     __shared__ u32 s_nmiss;
     __shared__ u64 s_tail_end;
     __shared__ u32 s_nclaim;
@@ -195,6 +302,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
     const T* S = (const T*)a.S;
     const u64 n = round_n(a);
     const u32 kact = round_k(a);
+    const u64 nwords = (n + 31) / 32;  // words of the break bitmap
     ntiles = min(ntiles, (n + kTP - 1) / kTP);
     FpSource<T> fp;
     if constexpr (kByte) {
@@ -221,117 +329,22 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
     u64 iter = 0;
     for (u64 tile = blockIdx.x; tile < ntiles; tile += gridDim.x, iter++) {
         if ((iter & 15) == 0 && round_halted(a)) break;
-        for (int w = tid; w < NWS + 1; w += kParseThreads) {
-            sstart[w] = 0;
-            if (w < NWS) sbits[w] = 0;
-        }
         if (tid == 0) s_nmiss = 0;
         const u64 t0 = tile * (u64)kTP;
         const u64 t_end = min(t0 + (u64)kTP, n), s_end = min(t0 + (u64)kSP, n);
         const int ns = (int)(s_end - t0), nt = (int)(t_end - t0);
         const u32 j0 = a.tile_str[tile];  // string holding t0
-        __syncthreads();
 
-        // 1. stage the tile: bytes in round 1; ranks and their fingerprints
-        //    (written by the previous round's rewrite) afterwards
+        // 1. stage the tile's symbols (bytes in round 1, ranks afterwards) and
+        //    its break words (k_breaks)
         if constexpr (kByte) {
             stage_vec<unsigned char>(sb, S + t0, ns, (reinterpret_cast<unsigned long long>(S + t0) & 15) == 0);
-            if (tid == 0) s_left = (t0 == 0) ? 0u : sF0[S[t0 - 1]];
         } else {
             stage_vec<u32>(sT, S + t0, ns, (reinterpret_cast<unsigned long long>(S + t0) & 15) == 0);
-            stage_vec<u32>(sf, a.Sf + t0, ns, (reinterpret_cast<unsigned long long>(a.Sf + t0) & 15) == 0);
-            if (tid == 0) s_left = (t0 == 0) ? 0u : a.Sf[t0 - 1];
         }
-        // string starts at positions t0 .. s_end (n itself counts as one)
-        if (warp == 0) {
-            u32 jj = j0 + lane;
-            bool more = true;
-            while (more) {
-                const u64 s = (jj <= kact) ? __ldg(a.soff + jj) : ~0ull;
-                if (s >= t0 && s <= s_end) atomicOr(&sstart[(s - t0) >> 5], 1u << ((s - t0) & 31));
-                more = __shfl_sync(0xffffffffu, (jj <= kact && s <= s_end) ? 1u : 0u, 31) != 0;
-                jj += 32;
-            }
-        }
-        __syncthreads();
-        auto fat = [&](int x) -> u32 {  // fingerprint of staged position x (x >= -1)
-            if (x < 0) return s_left;
-            if constexpr (kByte) return sF0[sb[x]]; else return sf[x];
-        };
-        auto is_start = [&](int x) -> bool { return (sstart[x >> 5] >> (x & 31)) & 1u; };
-
-        // 2. break bits (Eq. rand_types): a phrase starts at x when x starts a
-        //    string, or f[x-1] > f[x] and the first fingerprint right of x (in
-        //    the string) that differs from f[x] is larger than f[x].
-        //    Thread t takes the kChunk positions from t * kChunk on, holds their
-        //    fingerprints in registers and walks them right to left.  The first
-        //    differing fingerprint right of its last position comes from the
-        //    next chunk: its first position, else the chunk's summary (the
-        //    first later position of that chunk that starts a string or
-        //    differs from its first fingerprint), else the chunk after.
-        {
-            constexpr int C = kChunk;
-            constexpr u64 kUnres = 1ull << 33;  // summary: the chunk is one run
-            static_assert(C * kParseThreads >= kSP, "chunks cover the staged positions");
-            u64* summ = kLocal ? reinterpret_cast<u64*>(sMiss) : sSummR;
-            const int x0 = tid * C;
-            u32 f[C + 1];
-            u32 stm = 0;  // bit i: position x0 + i starts a string
-#pragma unroll
-            for (int i = 0; i <= C; i++) {
-                const int x = x0 + i;
-                f[i] = (x < ns) ? fat(x) : 0u;
-                if (x <= ns && is_start(x)) stm |= 1u << i;
-            }
-            u64 sm = kUnres;
-#pragma unroll
-            for (int i = C - 1; i >= 1; i--)
-                if (x0 + i < ns) {
-                    if ((stm >> i) & 1u) sm = kNone;
-                    else if (f[i] != f[0]) sm = f[i];
-                }
-            summ[tid] = sm;
-            __syncthreads();
-            // first fingerprint other than v at or after position y (in the
-            // string), or kNone
-            auto nd_from = [&](int y, u32 v) -> u64 {
-                while (true) {
-                    if (y >= ns) {
-                        if (s_end == n || is_start(ns)) return kNone;
-                        const u32 jl = string_of(a.soff, kact, t0 + (u64)ns - 1);
-                        return scan_right_diff<T>(S, fp, s_end, __ldg(a.soff + jl + 1), v);
-                    }
-                    if (is_start(y)) return kNone;
-                    const u32 fy = fat(y);
-                    if (fy != v) return fy;
-                    const u64 c = summ[y / C];
-                    if (c != kUnres) return c;
-                    y = min(y + C, ns);
-                }
-            };
-            u32 bits = 0;
-            if (x0 < ns) {
-                u64 nd = 0;
-                u32 fl = 0;
-#pragma unroll
-                for (int i = C - 1; i >= 0; i--) {
-                    const int x = x0 + i;
-                    if (x < ns) {
-                        if (i == C - 1 || x + 1 >= ns) nd = nd_from(x + 1, f[i]);
-                        else if ((stm >> (i + 1)) & 1u) nd = kNone;
-                        else if (f[i + 1] != f[i]) nd = f[i + 1];
-                        // else: nd of position x + 1 (the value in nd) carries over
-                        fl = (i == 0) ? fat(x0 - 1) : f[i - 1];
-                        const bool brk = ((stm >> i) & 1u) || (fl > f[i] && nd != kNone && nd > (u64)f[i]);
-                        if (brk) bits |= 1u << i;
-                    }
-                }
-            }
-            if (bits) {  // set bits lie below ns <= NWS * 32
-                atomicOr(&sbits[x0 >> 5], bits << (x0 & 31));
-                if ((x0 & 31) + C > 32 && (bits >> (32 - (x0 & 31))) != 0)
-                    atomicOr(&sbits[(x0 >> 5) + 1], bits >> (32 - (x0 & 31)));
-            }
+        for (int w = tid; w < NWS; w += kParseThreads) {
+            const u64 gw = t0 / 32 + (u64)w;
+            sbits[w] = gw < nwords ? __ldg(a.brk + gw) : 0u;
         }
         __syncthreads();
 
@@ -363,7 +376,12 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                 if (w == (nt >> 5)) m &= ~((1u << (nt & 31)) - 1u);
                 if (m) { e = t0 + (u64)(w * 32 + __ffs(m) - 1); found = true; }
             }
-            if (!found) e = (s_end == n) ? n : global_next_break<T>(S, fp, n, a.soff, kact, s_end);
+            // past the staged words (s_end < n is then a multiple of 32): the
+            // bitmap in global memory
+            for (u64 gw = s_end / 32; !found && s_end < n && gw < nwords; gw++) {
+                const u32 m = __ldg(a.brk + gw);
+                if (m) { e = min(n, gw * 32 + (u64)(__ffs(m) - 1)); found = true; }
+            }
             s_tail_end = e;
         }
         __syncthreads();
@@ -391,10 +409,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
             if (hashed) {
                 // H = sum_j F[Q_j] c^{j-1} mod p, by Horner from the last symbol
                 u64 H = 0;
-                for (u64 x = en; x-- > st;) {
-                    const u32 v = (x < (u64)ns) ? fat((int)x) : fp(S[t0 + x]);
-                    H = addmod61(mulmod61(H, a.lh.c), (u64)v);
-                }
+                for (u64 x = en; x-- > st;) H = addmod61(mulmod61(H, a.lh.c), (u64)fp(sym(x)));
                 key = key_hashed(H, len, t0 + st);
             } else {
                 key = key_inline([&](u64 j) { return sym(st + j); }, len, a.sym_w);
@@ -599,6 +614,11 @@ __global__ void k_tile_strings(const RoundArgs a, u64 tiles) {
     tiles = min(tiles, nt);
     for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < tiles; t += (u64)gridDim.x * blockDim.x)
         a.tile_str[t] = string_of(a.soff, k, t * (u64)kTP);
+    // bitmap of string starts (and of n), zeroed by the host
+    for (u64 j = blockIdx.x * (u64)blockDim.x + threadIdx.x; j <= k; j += (u64)gridDim.x * blockDim.x) {
+        const u64 s0 = __ldg(a.soff + j);
+        if ((s0 >> 5) < a.sbm_words) atomicOr(a.sbm + (s0 >> 5), 1u << (s0 & 31));
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -908,6 +928,27 @@ static unsigned persistent_grid(u64 tiles) {
     }
     const u64 g = (u64)occ * (u64)sms;
     return (unsigned)(tiles < g ? (tiles ? tiles : 1) : g);
+}
+
+template <typename T>
+static unsigned breaks_grid(u64 blocks) {
+    static int occ = 0, sms = 0;
+    if (occ == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_breaks<T>, kBrkThreads, 0);
+        if (occ <= 0) occ = 1;
+    }
+    const u64 cap = (u64)occ * (u64)sms;
+    return (unsigned)(blocks < cap ? (blocks ? blocks : 1) : cap);
+}
+
+cudaError_t launch_breaks(const RoundArgs& a, cudaStream_t st) {
+    const u64 blocks = (a.tiles_bound * (u64)kTP + kBrkSpan - 1) / kBrkSpan;
+    if (a.sym_bytes == 1) k_breaks<unsigned char><<<breaks_grid<unsigned char>(blocks), kBrkThreads, 0, st>>>(a, blocks);
+    else k_breaks<u32><<<breaks_grid<u32>(blocks), kBrkThreads, 0, st>>>(a, blocks);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_parse(const RoundArgs& a, cudaStream_t st) {
