@@ -142,31 +142,44 @@ __device__ __forceinline__ void stage_vec(V* dst, const V* src, int n_sym, bool 
 // k_breaks: the round's break bitmap (Eq. rand_types)
 // --------------------------------------------------------------------------
 //
-// A phrase starts at x when x starts a string, or f[x-1] > f[x] and the first
-// fingerprint right of x (within the string) that differs from f[x] is larger
-// than f[x].  Thread t of a block step decides kBrkPer consecutive positions
-// from registers, right to left; two threads make one word of the bitmap.  The
-// first differing fingerprint right of a thread's last position comes from the
-// next thread's first position, else from that thread's summary (the first
-// later position of its kBrkPer that starts a string or differs from its first
-// fingerprint), else from the thread after; past the block step it is read
-// from global memory.
+// A phrase starts at x when x starts a string, or f[x-1] > f[x] and x has
+// type S: the first fingerprint right of x (within the string) that differs
+// from f[x] is larger than f[x].  Thread t of a block step owns the 32
+// positions of bitmap word t and works on bit masks: gt / lt mark positions
+// whose right neighbour (in the string) is larger / smaller, stop marks
+// positions whose right neighbour starts a string (or is past the end).  A
+// position's type is decided by the first of these at or above it, so the S
+// mask is gt spread down over the undecided positions (five doubling steps).
+// Positions above the thread's last decision take the type of the next
+// thread's first position, found through per-thread summaries (and, past the
+// block step, in global memory).  Then breaks = starts | ((lt << 1) & S), bit 0
+// using f of the position before.
 
 constexpr int kBrkThreads = 256;
-constexpr int kBrkPer = 16;                                // positions per thread
-constexpr u64 kBrkSpan = (u64)kBrkThreads * kBrkPer;      // positions per block step
+constexpr u64 kBrkSpan = (u64)kBrkThreads * 32;  // positions per block step
 static_assert(kBrkSpan % kTP == 0, "a block step starts a parse tile");
+
+// Spread the bits of `src` down over the positions of `pass` (positions that
+// take the value of the position above): bit i of the result is src[j] for
+// the first j >= i with pass[j] == 0, when that j is at most 31.
+__device__ __forceinline__ u32 spread_down(u32 src, u32 pass) {
+    u32 y = src, m = pass;
+#pragma unroll
+    for (int k = 1; k < 32; k <<= 1) {
+        y |= (y >> k) & m;
+        m &= m >> k;
+    }
+    return y;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kBrkThreads) k_breaks(const RoundArgs a, u64 nblocks) {
     constexpr bool kByte = sizeof(T) == 1;
-    constexpr u64 kUnres = 1ull << 33;  // summary: the thread's positions are one run
-    constexpr int P = kBrkPer;
-    constexpr int SW = (int)(kBrkSpan / 32);  // string-start words of a step
+    constexpr u32 kTypeU = 0, kTypeS = 1, kTypeL = 2, kUndecided = 3;
+    constexpr int SW = kBrkThreads;  // string-start words of a step
     __shared__ u32 sF0[kByte ? 256 : 1];
-    __shared__ u32 sst[SW + 1];  // string starts at base .. base + kBrkSpan
-    __shared__ u64 ssum[kBrkThreads];
-    __shared__ u32 sfirst[kBrkThreads];  // fingerprint of each thread's first position
+    __shared__ u32 sst[SW + 1];      // string starts at base .. base + kBrkSpan
+    __shared__ u32 sfirst[kBrkThreads];  // type of each thread's first position
     if (round_halted(a)) return;
     const T* S = (const T*)a.S;
     const u32* Sf = a.Sf;
@@ -181,26 +194,29 @@ __global__ void __launch_bounds__(kBrkThreads) k_breaks(const RoundArgs a, u64 n
     const bool aligned = kByte ? (reinterpret_cast<unsigned long long>(S) & 15) == 0
                                : (reinterpret_cast<unsigned long long>(Sf) & 15) == 0;
     nblocks = min(nblocks, (n + kBrkSpan - 1) / kBrkSpan);
+    if constexpr (kByte) __syncthreads();
     for (u64 b = blockIdx.x; b < nblocks; b += gridDim.x) {
         const u64 base = b * kBrkSpan;
         const u64 bend = min(base + kBrkSpan, n);
-        // string starts at base .. base + kBrkSpan (bitmap of k_tile_strings;
-        // n counts as one)
+        // string starts (bitmap of k_tile_strings; n counts as one)
         for (int w = tid; w <= SW; w += kBrkThreads) {
             const u64 gw = base / 32 + (u64)w;
             sst[w] = gw < a.sbm_words ? __ldg(a.sbm + gw) : 0u;
         }
-        const u64 x0 = base + (u64)P * (u64)tid;
-        u32 f[P];
-        if (aligned && x0 + P <= n) {
+        const u64 x0 = base + 32ull * (u64)tid;
+        u32 f[32];
+        if (aligned && x0 + 32 <= n) {
             if constexpr (kByte) {
-                const uint4 v = *reinterpret_cast<const uint4*>(S + x0);
-                const u32 w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                for (int i = 0; i < P; i++) f[i] = sF0[(w[i >> 2] >> (8 * (i & 3))) & 0xFFu];
+                for (int h = 0; h < 2; h++) {
+                    const uint4 v = *reinterpret_cast<const uint4*>(S + x0 + 16 * h);
+                    const u32 w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int i = 0; i < 16; i++) f[16 * h + i] = sF0[(w[i >> 2] >> (8 * (i & 3))) & 0xFFu];
+                }
             } else {
 #pragma unroll
-                for (int q = 0; q < P / 4; q++) {
+                for (int q = 0; q < 8; q++) {
                     const uint4 v = *reinterpret_cast<const uint4*>(Sf + x0 + 4 * q);
                     f[4 * q] = v.x;
                     f[4 * q + 1] = v.y;
@@ -210,63 +226,68 @@ __global__ void __launch_bounds__(kBrkThreads) k_breaks(const RoundArgs a, u64 n
             }
         } else {
 #pragma unroll
-            for (int i = 0; i < P; i++) f[i] = (x0 + i < n) ? fpos(x0 + i) : 0u;
+            for (int i = 0; i < 32; i++) f[i] = (x0 + i < n) ? fpos(x0 + i) : 0u;
         }
-        __syncthreads();  // sst loaded
-        // starts at x0 .. x0 + P (P + 1 bits)
-        const int sb0 = P * tid;
-        const u64 win = (u64)sst[sb0 >> 5] | ((u64)sst[(sb0 >> 5) + 1] << 32);
-        const u32 stm = (u32)((win >> (sb0 & 31)) & ((1ull << (P + 1)) - 1));
-        u64 sm = kUnres;
-#pragma unroll
-        for (int i = P - 1; i >= 1; i--)
-            if (x0 + i < bend) {
-                if ((stm >> i) & 1u) sm = kNone;
-                else if (f[i] != f[0]) sm = f[i];
-            }
-        ssum[tid] = sm;
-        sfirst[tid] = f[0];
-        // f of position x0 - 1: the previous thread's last, or global memory
-        u32 fprev = __shfl_up_sync(0xffffffffu, f[P - 1], 1);
+        // f of the position after the thread's last, and of the one before its first
+        u32 fnext = __shfl_down_sync(0xffffffffu, f[0], 1);
+        u32 fprev = __shfl_up_sync(0xffffffffu, f[31], 1);
+        if (lane == 31 && x0 + 32 < n) fnext = fpos(x0 + 32);
         if (lane == 0 && x0 > 0 && x0 - 1 < n) fprev = fpos(x0 - 1);
-        __syncthreads();
-        // first fingerprint other than v at or after position y (a thread's
-        // first position, or past the block step), within the string; or kNone
-        auto nd_from = [&](u64 y, u32 v) -> u64 {
-            while (y < bend) {
-                const u32 t = (u32)((y - base) / P);
-                const u32 bit = (u32)(y - base);
-                if ((sst[bit >> 5] >> (bit & 31)) & 1u) return kNone;
-                if (sfirst[t] != v) return sfirst[t];
-                if (ssum[t] != kUnres) return ssum[t];
-                y += P;
-            }
-            if (y >= n) return kNone;
-            // past the block step: follow the run in global memory to its string's end
-            const u32 j = string_of(a.soff, k, y - 1);
-            const u64 strend = __ldg(a.soff + j + 1);
-            if (y >= strend) return kNone;
-            return scan_right_diff<T>(S, FpSource<T>{kByte ? sF0 : a.Fprev}, y, strend, v);
-        };
-        u32 bits = 0;
-        if (x0 < bend) {
-            u64 nd = 0;
+        __syncthreads();  // sst loaded
+        const u32 st = sst[tid];                      // starts at x0 .. x0 + 31
+        const u32 st_next = (sst[tid + 1] & 1u);      // start at x0 + 32
+        // masks over the thread's positions: right neighbour larger, smaller,
+        // or a string start / the end of the sequence
+        const u32 stop = (st >> 1) | (st_next << 31);
+        u32 gt = 0, lt = 0;
 #pragma unroll
-            for (int i = P - 1; i >= 0; i--) {
-                const u64 x = x0 + (u64)i;
-                if (x < bend) {
-                    if (i == P - 1 || x + 1 >= bend) nd = ((stm >> (i + 1)) & 1u) ? kNone : nd_from(x + 1, f[i]);
-                    else if ((stm >> (i + 1)) & 1u) nd = kNone;
-                    else if (f[i + 1] != f[i]) nd = f[i + 1];
-                    // else: the run goes on, nd of x + 1 carries over
-                    const u32 fl = (i == 0) ? fprev : f[i - 1];
-                    if (((stm >> i) & 1u) || (fl > f[i] && nd != kNone && nd > (u64)f[i])) bits |= 1u << i;
-                }
-            }
+        for (int i = 0; i < 31; i++) {
+            gt |= (u32)(f[i + 1] > f[i]) << i;
+            lt |= (u32)(f[i + 1] < f[i]) << i;
         }
-        // two threads per word (P = 16)
-        const u32 hi = __shfl_down_sync(0xffffffffu, bits, 1);
-        if ((tid & 1) == 0 && x0 < bend) a.brk[x0 >> 5] = bits | (hi << 16);
+        gt |= (u32)(fnext > f[31]) << 31;
+        lt |= (u32)(fnext < f[31]) << 31;
+        gt &= ~stop;
+        lt &= ~stop;
+        const u32 dec = gt | lt | stop;  // positions whose type is decided here
+        u32 sm = spread_down(gt, ~dec);
+        u32 lm = spread_down(lt, ~dec);
+        // type of the thread's first position (or undecided: one run throughout)
+        sfirst[tid] = dec == 0 ? kUndecided : (sm & 1u) ? kTypeS : (lm & 1u) ? kTypeL : kTypeU;
+        __syncthreads();
+        if (dec != (u32)~0u && ((dec >> 31) & 1u) == 0) {
+            // positions above the last decision take the type of position x0 + 32
+            u32 carry = kTypeU;
+            u64 y = x0 + 32;
+            u32 t = (u32)tid + 1;
+            while (true) {
+                if (y >= bend) {
+                    if (y >= n) { carry = kTypeU; break; }
+                    // past the block step: first fingerprint after the run, in global memory
+                    const u32 v = f[31];
+                    const u32 j = string_of(a.soff, k, y - 1);
+                    const u64 strend = __ldg(a.soff + j + 1);
+                    u64 nd = kNone;
+                    if (y < strend) nd = scan_right_diff<T>(S, FpSource<T>{kByte ? sF0 : a.Fprev}, y, strend, v);
+                    carry = nd == kNone ? kTypeU : (nd > (u64)v ? kTypeS : kTypeL);
+                    break;
+                }
+                const u32 c = sfirst[t];
+                if (c != kUndecided) { carry = c; break; }
+                y += 32;
+                t++;
+            }
+            const int hi = 31 - __clz(dec | 1u);  // highest decided position (or 0)
+            const u32 top = dec == 0 ? ~0u : ~((2u << hi) - 1u);
+            if (carry == kTypeS) sm |= top;
+            if (carry == kTypeL) lm |= top;
+        }
+        u32 bits = st | ((lt << 1) & sm);
+        if (fprev > f[0] && (sm & 1u)) bits |= 1u;
+        if (x0 < bend) {
+            if (bend - x0 < 32) bits &= (1u << (bend - x0)) - 1u;
+            a.brk[x0 >> 5] = bits;
+        }
         __syncthreads();
     }
 }
@@ -784,6 +805,7 @@ __global__ void k_rules(const RoundArgs a) {
 // --------------------------------------------------------------------------
 
 constexpr int kRankCache = 1024;
+constexpr int kRwUnroll = 4;
 
 // T^{i+1}[p] = rank of phrase p and f^{i+1}[p] = its fingerprint F^i[rank]
 // (so that the next round reads fingerprints without gathers).  Strings that
@@ -806,54 +828,85 @@ __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) 
     for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const u32 cnt = a.tile_cnt[t];
         const u64 pbase = a.tile_pfx[t];
-        for (u32 q = threadIdx.x; q < cnt; q += blockDim.x) {
-            const u64 p = pbase + q;
-            const u32 s = a.P_slot[t * (u64)kTP + q];
-            u32 r, f;
-            if (s == ~0u) {  // the round's table overflowed: the round is discarded
-                r = 0;
-                f = 0;
-            } else if (s & kResidentBit) {
-                r = s & ~kResidentBit;
-                f = __ldg(a.F + r);
-            } else {
-                const u32 ci = s & (kRankCache - 1);
-                const u64 er = c_rank[ci], ef = c_fp[ci];
-                if ((u32)(er >> 32) == s && (u32)(ef >> 32) == s) {
-                    r = (u32)er;
-                    f = (u32)ef;
+        const u32* ps = a.P_slot + t * (u64)kTP;
+        // kRwUnroll phrases per thread at a time: their table reads are issued
+        // together
+        for (u32 q0 = threadIdx.x; q0 < cnt; q0 += kRwUnroll * blockDim.x) {
+            u32 s[kRwUnroll], r[kRwUnroll], f[kRwUnroll];
+            bool need[kRwUnroll];
+#pragma unroll
+            for (int u = 0; u < kRwUnroll; u++) {
+                const u32 q = q0 + (u32)u * blockDim.x;
+                s[u] = q < cnt ? ps[q] : ~0u;
+            }
+#pragma unroll
+            for (int u = 0; u < kRwUnroll; u++) {
+                need[u] = false;
+                r[u] = 0;
+                f[u] = 0;
+                if (s[u] == ~0u) continue;  // no phrase, or the round's table overflowed
+                if (s[u] & kResidentBit) {
+                    r[u] = s[u] & ~kResidentBit;
+                    need[u] = true;
                 } else {
-                    const u64 v = a.tab_vals[s];
-                    r = (u32)v;
-                    f = (u32)(v >> 32);
-                    c_rank[ci] = ((u64)s << 32) | r;
-                    c_fp[ci] = ((u64)s << 32) | f;
+                    const u32 ci = s[u] & (kRankCache - 1);
+                    const u64 er = c_rank[ci], ef = c_fp[ci];
+                    if ((u32)(er >> 32) == s[u] && (u32)(ef >> 32) == s[u]) {
+                        r[u] = (u32)er;
+                        f[u] = (u32)ef;
+                    } else {
+                        need[u] = true;
+                    }
                 }
             }
-            if (r >= g_total) {  // an entry that got no rank: only after a capacity error
-                set_error(a.ds, kErrCapacity);
-                r = 0;
-            }
-            u64 out = p;
-            if (nr != 0) {
-                u64 lo = 0, hi = nr;  // first index with R_phr >= p
-                while (lo < hi) {
-                    const u64 mid = (lo + hi) >> 1;
-                    if (a.R_phr[mid] < p) lo = mid + 1; else hi = mid;
+            u64 v[kRwUnroll];
+#pragma unroll
+            for (int u = 0; u < kRwUnroll; u++)
+                v[u] = !need[u] ? 0ull : (s[u] & kResidentBit) ? (u64)__ldg(a.F + r[u]) << 32 : a.tab_vals[s[u]];
+#pragma unroll
+            for (int u = 0; u < kRwUnroll; u++) {
+                if (!need[u]) continue;
+                if (s[u] & kResidentBit) {
+                    f[u] = (u32)(v[u] >> 32);
+                } else {
+                    r[u] = (u32)v[u];
+                    f[u] = (u32)(v[u] >> 32);
+                    const u32 ci = s[u] & (kRankCache - 1);
+                    c_rank[ci] = ((u64)s[u] << 32) | r[u];
+                    c_fp[ci] = ((u64)s[u] << 32) | f[u];
                 }
-                if (lo < nr && a.R_phr[lo] == p) {
-                    a.c_level[a.R_sid[lo]] = a.level;
-                    a.c_rank[a.R_sid[lo]] = r;
+            }
+#pragma unroll
+            for (int u = 0; u < kRwUnroll; u++) {
+                const u32 q = q0 + (u32)u * blockDim.x;
+                if (q >= cnt) continue;
+                u32 rr = r[u];
+                if (rr >= g_total) {  // an entry that got no rank: only after a capacity error
+                    set_error(a.ds, kErrCapacity);
+                    rr = 0;
+                }
+                const u64 p = pbase + q;
+                u64 out = p;
+                if (nr != 0) {
+                    u64 lo = 0, hi = nr;  // first index with R_phr >= p
+                    while (lo < hi) {
+                        const u64 mid = (lo + hi) >> 1;
+                        if (a.R_phr[mid] < p) lo = mid + 1; else hi = mid;
+                    }
+                    if (lo < nr && a.R_phr[lo] == p) {
+                        a.c_level[a.R_sid[lo]] = a.level;
+                        a.c_rank[a.R_sid[lo]] = rr;
+                        continue;
+                    }
+                    out = p - lo;
+                }
+                if (out >= a.T_cap) {
+                    set_error(a.ds, kErrCapacity);
                     continue;
                 }
-                out = p - lo;
+                a.Tnext[out] = rr;
+                a.Fnext[out] = f[u];
             }
-            if (out >= a.T_cap) {
-                set_error(a.ds, kErrCapacity);
-                continue;
-            }
-            a.Tnext[out] = r;
-            a.Fnext[out] = f;
         }
     }
 }
