@@ -54,6 +54,11 @@ def parse_args():
                    help="only run this many batched builds of the workload and exit (for profiler captures)")
     p.add_argument("--profile-strings", type=int, default=0,
                    help="with --profile-builds: only the first this many strings of the workload")
+    p.add_argument("--write-traffic", default="",
+                   help="ncu CSV (dram__bytes_read.sum, dram__bytes_write.sum per launch) of "
+                        "--profile-builds 1 with the same --profile-strings / --profile-warmup: writes "
+                        "profiles/traffic.json with DRAM bytes per algorithmic byte per kernel kind")
+    p.add_argument("--traffic-command", default="", help="the ncu command recorded in profiles/traffic.json")
     p.add_argument("--profile-warmup", type=int, default=0,
                    help="with --profile-builds: builds run before the profiler range "
                         "(cudaProfilerStart/Stop; use ncu --profile-from-start off)")
@@ -367,8 +372,65 @@ def run_ours(args):
     return 0
 
 
+def _ncu_dram_bytes(path: str) -> dict:
+    """Sum of dram__bytes_read.sum + dram__bytes_write.sum per kernel kind
+    (the name before any template argument list) in an ncu --csv log."""
+    import csv
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
+    with open(path) as fh:
+        rows = list(csv.reader(fh))
+    head = next(i for i, r in enumerate(rows) if "Kernel Name" in r and "Metric Name" in r)
+    hdr = rows[head]
+    ki, mi, ui, vi, ii = (hdr.index(x) for x in ("Kernel Name", "Metric Name", "Metric Unit", "Metric Value", "ID"))
+    out = {}
+    for r in rows[head + 1:]:
+        if len(r) <= vi or r[mi] not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        kind = r[ki].split("(")[0].split("<")[0].replace("void ", "").split("::")[-1]
+        e = out.setdefault(kind, {"dram_bytes": 0.0, "launch_ids": set()})
+        e["dram_bytes"] += float(r[vi].replace(",", "")) * scale.get(r[ui], 1.0)
+        e["launch_ids"].add(r[ii])
+    return {k: {"dram_bytes": v["dram_bytes"], "launches": len(v["launch_ids"])} for k, v in out.items()}
+
+
+def write_traffic(args):
+    """profiles/traffic.json from an ncu capture of one profiled build: the
+    algorithmic bytes of the same build come from the library's kernel timing."""
+    import torch
+    from paper_2411_12439_gb300 import Context
+    dram = _ncu_dram_bytes(args.write_traffic)
+    hf = li.hash_family()
+    coll = workload(0)
+    offs = coll.offsets[:min(args.profile_strings, coll.k) + 1] if args.profile_strings else coll.offsets
+    d = torch.from_numpy(coll.data).cuda()
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = Context(hf, device=0, stream=stream.cuda_stream)
+    for _ in range(args.profile_warmup):
+        ctx.build(d, offs).free()
+    ctx.set_kernel_timing(True)
+    ctx.build(d, offs).free()
+    kt = ctx.last_kernel_times()
+    kernels = {}
+    for kind, v in dram.items():
+        if kind in kt and kt[kind]["bytes"] > 0:
+            kernels[kind] = {"launches": v["launches"], "dram_bytes": v["dram_bytes"], "alg_bytes": kt[kind]["bytes"],
+                             "dram_bytes_per_alg_byte": v["dram_bytes"] / kt[kind]["bytes"]}
+    out = {"source_hash": kernel_source_hash(), "command": args.traffic_command,
+           "workload": WORKLOAD + (f" (first {args.profile_strings} strings)" if args.profile_strings else ""),
+           "input_bytes": int(offs[-1] - offs[0]), "kernels": kernels}
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    with open(path, "w") as fh:
+        json.dump(out, fh, indent=1)
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.write_traffic:
+        return write_traffic(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
