@@ -123,7 +123,7 @@ __device__ __forceinline__ void stage_vec(V* dst, const V* src, int n_sym, bool 
     for (int it = 0; it < IT; it++) {
         const int x0 = (threadIdx.x + it * kParseThreads) * PER;
         if (x0 + PER <= n_sym && vec) {
-            buf[it] = *reinterpret_cast<const uint4*>(src + x0);
+            buf[it] = __ldcs(reinterpret_cast<const uint4*>(src + x0));  // streamed once: evict first
         } else if (x0 < n_sym) {
             V tmp[PER];
 #pragma unroll
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kBrkThreads) k_breaks(const RoundArgs a, u64 n
             if constexpr (kByte) {
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
-                    const uint4 v = *reinterpret_cast<const uint4*>(S + x0 + 16 * h);
+                    const uint4 v = __ldcs(reinterpret_cast<const uint4*>(S + x0 + 16 * h));
                     const u32 w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                     for (int i = 0; i < 16; i++) f[16 * h + i] = sF0[(w[i >> 2] >> (8 * (i & 3))) & 0xFFu];
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kBrkThreads) k_breaks(const RoundArgs a, u64 n
             } else {
 #pragma unroll
                 for (int q = 0; q < 8; q++) {
-                    const uint4 v = *reinterpret_cast<const uint4*>(Sf + x0 + 4 * q);
+                    const uint4 v = __ldcs(reinterpret_cast<const uint4*>(Sf + x0 + 4 * q));
                     f[4 * q] = v.x;
                     f[4 * q + 1] = v.y;
                     f[4 * q + 2] = v.z;
@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                     if (cacheable && free_h >= 0 && slot != ~0u && !(slot & kResidentBit))
                         cache_insert(free_h, short_key(st, (u32)len), q, slot);
                 }
-                a.P_slot[okey0 + q] = slot;
+                __stcs(a.P_slot + okey0 + q, slot);
             }
             __syncthreads();
             const u32 nm = min(s_nmiss, (u32)kMissBuf);
@@ -558,7 +558,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                     slot = lookup(q, st, en, &claimed);
                     if (free_h >= 0 && slot != ~0u && !(slot & kResidentBit))
                         cache_insert(free_h, short_key(st, (u32)len), q, slot);
-                    a.P_slot[okey0 + q] = slot;
+                    __stcs(a.P_slot + okey0 + q, slot);
                 }
                 claim_warp(claimed, slot, len);
             }
@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                     const u64 st = sP[q], en = phrase_end(q);
                     len = en - st;
                     slot = lookup(q, st, en, &claimed);
-                    a.P_slot[okey0 + q] = slot;
+                    __stcs(a.P_slot + okey0 + q, slot);
                 }
                 claim_warp(claimed, slot, len);
             }
@@ -837,7 +837,7 @@ __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) 
 #pragma unroll
             for (int u = 0; u < kRwUnroll; u++) {
                 const u32 q = q0 + (u32)u * blockDim.x;
-                s[u] = q < cnt ? ps[q] : ~0u;
+                s[u] = q < cnt ? __ldcs(ps + q) : ~0u;
             }
 #pragma unroll
             for (int u = 0; u < kRwUnroll; u++) {
@@ -904,8 +904,8 @@ __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) 
                     set_error(a.ds, kErrCapacity);
                     continue;
                 }
-                a.Tnext[out] = rr;
-                a.Fnext[out] = f[u];
+                __stcs(a.Tnext + out, rr);
+                __stcs(a.Fnext + out, f[u]);
             }
         }
     }
