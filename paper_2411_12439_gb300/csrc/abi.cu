@@ -25,8 +25,7 @@ struct Level {
     u64* rhs_off = nullptr;    // cap_g + 1 entries
     u32* rhs = nullptr;
     u32* F = nullptr;
-    void* rkeys = nullptr;     // table over the rules (for parses against this grammar and merges)
-    u64* rvals = nullptr;
+    void* rtab = nullptr;      // table over the rules (for parses against this grammar and merges)
     u64 rcap = 0;
     bool rvalid = false;
 };
@@ -267,14 +266,12 @@ void ensure_resident(lcg_ctx* ctx, lcg_grammar* G, u32 i, u64 need_g) {
     Level& L = G->lv[i - 1];
     if (L.rvalid && L.rcap >= 2 * need_g) return;
     const u64 cap = std::max<u64>(1024, 3 * need_g);
-    dfree(ctx, L.rkeys);
-    dfree(ctx, L.rvals);
-    L.rkeys = dalloc<unsigned char>(ctx, cap * key_bytes());
-    L.rvals = dalloc<u64>(ctx, cap);
+    dfree(ctx, L.rtab);
+    L.rtab = dalloc<unsigned char>(ctx, cap * slot_bytes());
     L.rcap = cap;
-    ck(ctx, cudaMemsetAsync(L.rkeys, 0xFF, cap * key_bytes(), ctx->st), "memset table");
-    ck(ctx, launch_resident_build(L.rhs, L.rhs_off, 0, L.g, i == 1, fprev_of(G, i), level_hash(ctx, i), L.rkeys,
-                                  L.rvals, cap, ctx->ds, ctx->st),
+    ck(ctx, cudaMemsetAsync(L.rtab, 0xFF, cap * slot_bytes(), ctx->st), "memset table");
+    ck(ctx, launch_resident_build(L.rhs, L.rhs_off, 0, L.g, i == 1, fprev_of(G, i), level_hash(ctx, i), L.rtab,
+                                  cap, ctx->ds, ctx->st),
        "resident build");
     ctx->launches++;
     L.rvalid = true;
@@ -329,8 +326,7 @@ void free_grammar_now(lcg_grammar* G) {
         release(L.rhs_off);
         release(L.rhs);
         release(L.F);
-        release(L.rkeys);
-        release(L.rvals);
+        release(L.rtab);
     }
     release(G->c_level);
     release(G->c_rank);
@@ -393,8 +389,8 @@ struct RoundBufs {
     u32* brk = nullptr;
     u32* sbm = nullptr;
     u64 sbm_words = 0;
-    unsigned char* tkeys = nullptr;
-    u64* tvals = nullptr;
+    unsigned char* tab = nullptr;  // phrase table: cap slots
+    u64* rv = nullptr;             // per slot: (F^i << 32) | rank, once named
     u32* claims = nullptr;
     u32* first_bits = nullptr;
     u32* first_prefix = nullptr;
@@ -426,19 +422,18 @@ void alloc_round(lcg_ctx* ctx, RoundBufs& b, u64 n_bound, u32 kk) {
 
 void alloc_table(lcg_ctx* ctx, RoundBufs& b, u64 cap) {
     b.cap = cap;
-    b.tkeys = dalloc<unsigned char>(ctx, cap * key_bytes());
-    b.tvals = dalloc<u64>(ctx, cap);
+    b.tab = dalloc<unsigned char>(ctx, cap * slot_bytes());
+    b.rv = dalloc<u64>(ctx, cap);
     b.claims = dalloc<u32>(ctx, cap);
-    ck(ctx, cudaMemsetAsync(b.tkeys, 0xFF, cap * key_bytes(), ctx->st), "memset table");
-    ck(ctx, cudaMemsetAsync(b.tvals, 0xFF, cap * sizeof(u64), ctx->st), "memset table");
+    ck(ctx, cudaMemsetAsync(b.tab, 0xFF, cap * slot_bytes(), ctx->st), "memset table");
 }
 
 void free_table(lcg_ctx* ctx, RoundBufs& b) {
-    dfree(ctx, b.tkeys);
-    dfree(ctx, b.tvals);
+    dfree(ctx, b.tab);
+    dfree(ctx, b.rv);
     dfree(ctx, b.claims);
-    b.tkeys = nullptr;
-    b.tvals = nullptr;
+    b.tab = nullptr;
+    b.rv = nullptr;
     b.claims = nullptr;
 }
 
@@ -514,8 +509,8 @@ RoundArgs round_args(lcg_ctx* ctx, lcg_grammar* R, const RoundInput& in, RoundBu
 }
 
 void set_table(RoundArgs& a, RoundBufs& b) {
-    a.tab_keys = b.tkeys;
-    a.tab_vals = b.tvals;
+    a.tab = b.tab;
+    a.rv = b.rv;
     a.tab_cap = b.cap;
     a.claims = b.claims;
     a.claim_limit = b.cap - b.cap / 5;
@@ -527,7 +522,7 @@ void enqueue_parse(lcg_ctx* ctx, RoundArgs& a, u64 n_for_bytes) {
     int hb = kt_begin(ctx, "k_breaks", (a.sym_bytes == 1 ? 1.0 : 4.0) * n_for_bytes + (double)n_for_bytes / 8.0);
     ck(ctx, launch_breaks(a, ctx->st), "k_breaks");
     kt_end(ctx, hb);
-    const double tab_bytes = a.tab_cap * (double)(key_bytes() + sizeof(u64));
+    const double tab_bytes = a.tab_cap * (double)slot_bytes();
     const double tbytes = tab_bytes > kL2Bytes ? 32.0 * (double)n_for_bytes / 3.0 : 0.0;
     int h = kt_begin(ctx, "k_parse",
                      (a.sym_bytes == 1 ? 1.0 : 4.0) * n_for_bytes + (double)n_for_bytes / 8.0 +
@@ -629,8 +624,7 @@ void round_sync(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32 i, bool agains
     if (i > 1 && !against_resident) a.sym_w = rank_width(R->lv[i - 2].g);
     if (against_resident && L.g > 0) {
         ensure_resident(ctx, R, i, L.g);
-        a.rtab_keys = L.rkeys;
-        a.rtab_vals = L.rvals;
+        a.rtab = L.rtab;
         a.rtab_cap = L.rcap;
         a.rrhs = L.rhs;
         a.rrhs_off = L.rhs_off;
@@ -682,8 +676,7 @@ void round_sync(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32 i, bool agains
     grow_level(ctx, L, L.g + g_new, L.G + G_new);
     if (against_resident) {
         ensure_resident(ctx, R, i, L.g + g_new);
-        a.rtab_w_keys = L.rkeys;
-        a.rtab_w_vals = L.rvals;
+        a.rtab_w = L.rtab;
         a.rtab_w_cap = L.rcap;
     } else {
         L.rvalid = false;
@@ -781,8 +774,7 @@ int rounds_async(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32& i) {
         dfree(ctx, L.rhs_off);
         dfree(ctx, L.rhs);
         dfree(ctx, L.F);
-        dfree(ctx, L.rkeys);
-        dfree(ctx, L.rvals);
+        dfree(ctx, L.rtab);
         R->lv.pop_back();
     }
     u64 n = in.n;
@@ -949,8 +941,8 @@ void merge(lcg_ctx* ctx, lcg_grammar* A, const lcg_grammar* B) {
         u32* mlen = dalloc<u32>(ctx, gb);
         u64* xrank = dalloc<u64>(ctx, gb);
         u64* xlen = dalloc<u64>(ctx, gb);
-        ck(ctx, launch_merge_lookup(brhs, LB.rhs_off, LB.F, gb, i == 1, fprev_of(A, i), level_hash(ctx, i), LA.rkeys,
-                                    LA.rvals, LA.rcap, LA.rhs, LA.rhs_off, LA.F, M, miss, mlen, ctx->ds, ctx->st),
+        ck(ctx, launch_merge_lookup(brhs, LB.rhs_off, LB.F, gb, i == 1, fprev_of(A, i), level_hash(ctx, i), LA.rtab,
+                                    LA.rcap, LA.rhs, LA.rhs_off, LA.F, M, miss, mlen, ctx->ds, ctx->st),
            "merge lookup");
         u64 grid = 0;
         const u64 stiles = std::max<u64>(1, scan2_tiles_for(gb));
@@ -974,7 +966,7 @@ void merge(lcg_ctx* ctx, lcg_grammar* A, const lcg_grammar* B) {
         LA.G = Ga + tot[1];
         // the appended rules join the table of the level
         ck(ctx, launch_resident_build(LA.rhs, LA.rhs_off, ga, tot[0], i == 1, fprev_of(A, i), level_hash(ctx, i),
-                                      LA.rkeys, LA.rvals, LA.rcap, ctx->ds, ctx->st),
+                                      LA.rtab, LA.rcap, ctx->ds, ctx->st),
            "table insert");
         ck(ctx, launch_remap_c(B->c_level, cb_rank, kb, i, M, ctx->st), "remap C");
         ctx->launches += 2;

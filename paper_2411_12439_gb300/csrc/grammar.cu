@@ -188,11 +188,11 @@ cudaError_t launch_remap(const u32* in, u64 n, const u32* M, u32* out, cudaStrea
 }
 
 cudaError_t launch_merge_lookup(const u32* brhs, const u64* brhs_off, const u32* bF, u64 gb, bool bytes,
-                                const u32* aFprev, LevelHash lh, void* akeys, u64* avals, u64 acap, const u32* arhs,
+                                const u32* aFprev, LevelHash lh, void* aslots, u64 acap, const u32* arhs,
                                 const u64* arhs_off, const u32* aF, u32* M, u32* miss, u32* mlen, DevStatus* ds,
                                 cudaStream_t st) {
     if (gb == 0) return cudaSuccess;
-    const ContentTable at{(Key128*)akeys, avals, acap};
+    const ContentTable at{(Slot*)aslots, acap};
     if (bytes)
         k_merge_lookup<true><<<grid_for(gb), 256, 0, st>>>(brhs, brhs_off, bF, gb, aFprev, lh, at, arhs, arhs_off, aF,
                                                            M, miss, mlen, ds);

@@ -86,62 +86,8 @@ __device__ __forceinline__ u64 vload(const volatile u64* p) { return *p; }
 
 constexpr u64 kSpinLimit = 1ull << 22;  // bounded waits: a few seconds at most
 
-// --------------------------------------------------------------------------
-// phrase table
-// --------------------------------------------------------------------------
-//
-// Open addressing with linear probing over 32-byte slots.  The first 16 bytes
-// {key, ref} are claimed together with one 128-bit compare-and-swap, so a
-// thread that finds a key always finds the content reference with it.
-//   key   : (min(len, 2^24-1) << 40) | 40-bit hash of the content (bit 0 clear);
-//           kEmpty when free.  Equal keys are only a filter: a hit is confirmed
-//           by comparing the phrase contents symbol by symbol.
-//   ref   : position of an occurrence of the phrase in the round's sequence;
-//           after naming it holds the phrase's rank.
-//   minp  : smallest phrase index among the occurrences (atomicMin), which
-//           decides first-occurrence naming.
-//   len   : phrase length; fp: its fingerprint h^i.
-struct __align__(16) Slot {
-    u64 key;
-    u64 ref;
-    u64 minp;
-    u32 len;
-    u32 fp;
-};
-static_assert(sizeof(Slot) == 32, "slot size");
-
+// Empty marker of 64-bit keys in shared-memory caches.
 constexpr u64 kEmpty = ~0ull;
-constexpr u64 kLenSat = (1ull << 24) - 1;
-
-__device__ __forceinline__ u64 make_key(u64 H, u64 len) {
-    u64 h = fmix64(H ^ (len * 0x9E3779B97F4A7C15ull)) & 0xFFFFFFFFFEull;
-    u64 l = len < kLenSat ? len : kLenSat;
-    return (l << 40) | h;
-}
-
-__device__ __forceinline__ u64 key_home(u64 key) { return fmix64(key); }
-
-// 128-bit compare-and-swap on {key, ref} (sm_90+).  Returns the old pair.
-__device__ __forceinline__ void cas128(Slot* s, u64 cmp_key, u64 cmp_ref, u64 new_key, u64 new_ref,
-                                       u64& old_key, u64& old_ref) {
-    asm volatile(
-        "{\n\t"
-        ".reg .b128 c, n, d;\n\t"
-        "mov.b128 c, {%2, %3};\n\t"
-        "mov.b128 n, {%4, %5};\n\t"
-        "atom.relaxed.gpu.global.cas.b128 d, [%6], c, n;\n\t"
-        "mov.b128 {%0, %1}, d;\n\t"
-        "}"
-        : "=l"(old_key), "=l"(old_ref)
-        : "l"(cmp_key), "l"(cmp_ref), "l"(new_key), "l"(new_ref), "l"(s)
-        : "memory");
-}
-
-__device__ __forceinline__ u64 ld_relaxed(const u64* p) {
-    u64 v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
 
 // --------------------------------------------------------------------------
 // decoupled look-back (single-pass prefix sums over tiles in launch order)

@@ -50,13 +50,11 @@ struct RoundArgs {
     u64 ctr_base;
     u64* total;           // device: phrases of the round
     DevStatus* ds;
-    void* tab_keys;       // the round's phrase table
-    u64* tab_vals;
+    void* tab;            // the round's phrase table (32-byte slots)
     u64 tab_cap;
     u64 claim_limit;
     u32* claims;          // slots claimed in this round (tab_cap entries)
-    void* rtab_keys;      // table of the resident level i (read), or cap 0
-    u64* rtab_vals;
+    void* rtab;           // table of the resident level i (read), or cap 0
     u64 rtab_cap;
     const u32* rrhs;
     const u64* rrhs_off;
@@ -78,14 +76,14 @@ struct RoundArgs {
     u32* first_prefix;    // exclusive popcount prefix of its words
     u32* slot_r;          // slot of the rank-r new rule
     u32* len_r;           // its length
+    u64* rv;              // per table slot: (F^i << 32) | rank of its rule (k_rules, read by k_rewrite)
     u64* xlen;            // exclusive prefix of len_r
     u64 g_base, G_base;   // rules / rhs symbols of level i before this round
 
     u32* rhs;
     u64* rhs_off;
     u32* F;
-    void* rtab_w_keys;    // table of level i to extend with the new rules, or cap 0
-    u64* rtab_w_vals;
+    void* rtab_w;         // table of level i to extend with the new rules, or cap 0
     u64 rtab_w_cap;
     // rewrite pass
     u64 T_cap;            // entries of Tnext / Fnext
@@ -99,7 +97,7 @@ u64 parse_tile_positions(int sym_bytes);
 u64 popscan_tiles_for(u64 nw);
 size_t lb1_bytes(u64 tiles);
 size_t lb2_bytes(u64 tiles);
-size_t key_bytes();
+size_t slot_bytes();  // bytes of one phrase-table slot
 
 cudaError_t launch_tile_strings(const RoundArgs& a, cudaStream_t st);
 cudaError_t launch_breaks(const RoundArgs& a, cudaStream_t st);
@@ -113,7 +111,7 @@ cudaError_t launch_rewrite(const RoundArgs& a, cudaStream_t st);
 cudaError_t launch_level0(const unsigned char* data, const u64* pos, const u32* ids, u32 cnt, u32* c_level,
                           u32* c_rank, cudaStream_t st);
 cudaError_t launch_resident_build(const u32* rhs, const u64* rhs_off, u64 r0, u64 cnt, bool bytes, const u32* Fprev,
-                                  LevelHash lh, void* keys, u64* vals, u64 cap, DevStatus* ds, cudaStream_t st);
+                                  LevelHash lh, void* slots, u64 cap, DevStatus* ds, cudaStream_t st);
 cudaError_t launch_h0(LevelHash h0, u32* F0, cudaStream_t st);
 cudaError_t launch_gather_strings(const unsigned char* data, const u64* src_off, const u64* dst_off, u32 k,
                                   unsigned char* out, cudaStream_t st);
@@ -121,7 +119,7 @@ cudaError_t launch_gather_strings(const unsigned char* data, const u64* src_off,
 // grammar.cu
 cudaError_t launch_remap(const u32* in, u64 n, const u32* M, u32* out, cudaStream_t st);
 cudaError_t launch_merge_lookup(const u32* brhs, const u64* brhs_off, const u32* bF, u64 gb, bool bytes,
-                                const u32* aFprev, LevelHash lh, void* akeys, u64* avals, u64 acap, const u32* arhs,
+                                const u32* aFprev, LevelHash lh, void* aslots, u64 acap, const u32* arhs,
                                 const u64* arhs_off, const u32* aF, u32* M, u32* miss, u32* mlen, DevStatus* ds,
                                 cudaStream_t st);
 cudaError_t launch_merge_append(const u32* brhs, const u64* brhs_off, const u32* bF, u64 gb, const u32* miss,

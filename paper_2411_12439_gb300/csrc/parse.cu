@@ -332,8 +332,8 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
     } else {
         fp.F = a.Fprev;
     }
-    const ContentTable bt{(Key128*)a.tab_keys, a.tab_vals, a.tab_cap};
-    const ContentTable rt{(Key128*)a.rtab_keys, a.rtab_vals, a.rtab_cap};
+    const ContentTable bt{(Slot*)a.tab, a.tab_cap};
+    const ContentTable rt{(Slot*)a.rtab, a.rtab_cap};
     if constexpr (kLocal) {
         for (int x = tid; x < kCacheSlots; x += kParseThreads) {
             ckey[x] = kEmpty;
@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                             if (v != ~0ull) {
                                 slot = (u32)(v & 0x7FFFFFFFull);
                                 const u64 vit = v >> 43, vq = (v >> 31) & 0xFFF;
-                                if (vit == (iter & 0x1FFFFF) && vq > q) atomicMin(a.tab_vals + slot, okey0 + q);
+                                if (vit == (iter & 0x1FFFFF) && vq > q) atomicMin(&bt.slots[slot].val, okey0 + q);
                             }
                             break;
                         }
@@ -704,7 +704,7 @@ __global__ void k_mark(const RoundArgs a) {
     const u64 keys = a.tiles_bound * (u64)kTP;  // order keys the bitmap covers
     for (u64 c = blockIdx.x * (u64)blockDim.x + threadIdx.x; c < g_new; c += (u64)gridDim.x * blockDim.x) {
         const u32 s = a.claims[c];
-        const u64 m = s < a.tab_cap ? a.tab_vals[s] : ~0ull;
+        const u64 m = s < a.tab_cap ? ((const Slot*)a.tab)[s].val : ~0ull;
         if (m >= keys) {
             set_error(a.ds, kErrCapacity);
             continue;
@@ -748,13 +748,13 @@ __global__ void k_rank(const RoundArgs a) {
     const u64 g_new = round_gnew(a);
     for (u64 c = blockIdx.x * (u64)blockDim.x + threadIdx.x; c < g_new; c += (u64)gridDim.x * blockDim.x) {
         const u32 s = a.claims[c];
-        const u64 m = a.tab_vals[s];
+        Slot* slots = (Slot*)a.tab;
+        const u64 m = slots[s].val;
         const u32 w = (u32)(m >> 5);
         const u64 r = a.first_prefix[w] + __popc(a.first_bits[w] & ((1u << (m & 31)) - 1u));
         if (r >= g_new) { set_error(a.ds, kErrCapacity); continue; }
-        a.tab_vals[s] = a.g_base + r;
         a.slot_r[r] = s;
-        a.len_r[r] = (u32)key_len(((const Key128*)a.tab_keys)[s]);
+        a.len_r[r] = (u32)key_len(slots[s].key);
     }
 }
 
@@ -765,7 +765,8 @@ template <typename T>
 __global__ void k_rules(const RoundArgs a) {
     constexpr bool kByte = sizeof(T) == 1;
     const T* S = (const T*)a.S;
-    const ContentTable rw{(Key128*)a.rtab_w_keys, a.rtab_w_vals, a.rtab_w_cap};
+    const ContentTable rw{(Slot*)a.rtab_w, a.rtab_w_cap};
+    Slot* slots = (Slot*)a.tab;
     if (round_halted(a)) return;
     const u64 g_new = round_gnew(a);
     const u64 G_new = *a.d_Gnew;
@@ -779,7 +780,7 @@ __global__ void k_rules(const RoundArgs a) {
             set_error(a.ds, kErrCapacity);
             continue;
         }
-        const Key128 k = ((const Key128*)a.tab_keys)[slot];
+        const Key128 k = slots[slot].key;
         const u64 len = key_len(k);
         const bool hashed = key_is_hashed(k);
         const u64 off = a.G_base + a.xlen[r];
@@ -794,7 +795,7 @@ __global__ void k_rules(const RoundArgs a) {
         }
         const u32 fpv = finish_hash(a.lh, H);
         a.F[rank] = fpv;
-        a.tab_vals[slot] = ((u64)fpv << 32) | rank;  // for the rewrite: rank and fingerprint
+        a.rv[slot] = ((u64)fpv << 32) | rank;  // for the rewrite: rank and fingerprint, dense by slot
         if (rw.cap) table_put(rw, hashed ? key_hashed(H, len, rank) : k, rank, a.ds);
         if (r == 0) a.rhs_off[a.g_base + g_new] = a.G_base + G_new;
     }
@@ -862,7 +863,7 @@ __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) 
             u64 v[kRwUnroll];
 #pragma unroll
             for (int u = 0; u < kRwUnroll; u++)
-                v[u] = !need[u] ? 0ull : (s[u] & kResidentBit) ? (u64)__ldg(a.F + r[u]) << 32 : a.tab_vals[s[u]];
+                v[u] = !need[u] ? 0ull : (s[u] & kResidentBit) ? (u64)__ldg(a.F + r[u]) << 32 : a.rv[s[u]];
 #pragma unroll
             for (int u = 0; u < kRwUnroll; u++) {
                 if (!need[u]) continue;
@@ -1062,9 +1063,9 @@ cudaError_t launch_gather_strings(const unsigned char* data, const u64* src_off,
 }
 
 cudaError_t launch_resident_build(const u32* rhs, const u64* rhs_off, u64 r0, u64 cnt, bool bytes, const u32* Fprev,
-                                  LevelHash lh, void* keys, u64* vals, u64 cap, DevStatus* ds, cudaStream_t st) {
+                                  LevelHash lh, void* slots, u64 cap, DevStatus* ds, cudaStream_t st) {
     if (cnt == 0) return cudaSuccess;
-    const ContentTable t{(Key128*)keys, vals, cap};
+    const ContentTable t{(Slot*)slots, cap};
     if (bytes) k_resident_build<true><<<grid_for(cnt), 256, 0, st>>>(rhs, rhs_off, r0, cnt, Fprev, lh, t, ds);
     else k_resident_build<false><<<grid_for(cnt), 256, 0, st>>>(rhs, rhs_off, r0, cnt, Fprev, lh, t, ds);
     return cudaGetLastError();
@@ -1072,6 +1073,6 @@ cudaError_t launch_resident_build(const u32* rhs, const u64* rhs_off, u64 r0, u6
 
 size_t lb1_bytes(u64 tiles) { return tiles * sizeof(LBSlot<1>); }
 size_t lb2_bytes(u64 tiles) { return tiles * sizeof(LBSlot<2>); }
-size_t key_bytes() { return sizeof(Key128); }
+size_t slot_bytes() { return sizeof(Slot); }
 
 }  // namespace lcg

@@ -26,9 +26,17 @@ struct __align__(16) Key128 {
     u64 lo, hi;
 };
 
+// A slot holds its 128-bit key and its 64-bit value in one 32-byte sector, so
+// that a lookup and the update of the value touch one sector.
+struct __align__(32) Slot {
+    Key128 key;
+    u64 val;
+    u64 spare;
+};
+static_assert(sizeof(Slot) == 32, "one sector per slot");
+
 struct ContentTable {
-    Key128* keys;
-    u64* vals;
+    Slot* slots;
     u64 cap;  // 0: no table
 };
 
@@ -136,14 +144,14 @@ __device__ u64 table_claim_or_find(ContentTable t, const Key128& k, bool hashed,
     const Key128 empty{~0ull, ~0ull};
     const u64 limit = t.cap < kMaxProbes ? t.cap : kMaxProbes;
     for (u64 probe = 0; probe < limit; probe++) {
-        Key128* kp = t.keys + s;
+        Key128* kp = &t.slots[s].key;
         Key128 cur = ld_key_relaxed(kp);
         if (cur.hi == kEmptyHi) {
             if (vload(&ds->overflow)) return ~0ull;
             const Key128 old = cas_key(kp, empty, k);
             if (old.hi == kEmptyHi) {
                 *claimed = true;
-                atomicMin(t.vals + s, pidx);
+                atomicMin(&t.slots[s].val, pidx);
                 return s;
             }
             cur = old;
@@ -152,7 +160,7 @@ __device__ u64 table_claim_or_find(ContentTable t, const Key128& k, bool hashed,
             // a pair read while being written shows the empty low half: read it again atomically
             if (cur.lo == ~0ull) cur = cas_key(kp, empty, empty);
             if (hashed ? same(cur.lo) : (cur.lo == k.lo)) {
-                atomicMin(t.vals + s, pidx);
+                atomicMin(&t.slots[s].val, pidx);
                 return s;
             }
         }
@@ -168,9 +176,9 @@ template <typename Same>
 __device__ u64 table_find(const ContentTable& t, const Key128& k, bool hashed, Same same) {
     u64 s = key_home(k, t.cap);
     for (u64 probe = 0; probe < t.cap; probe++) {
-        const Key128 cur = t.keys[s];
+        const Key128 cur = t.slots[s].key;
         if (cur.hi == kEmptyHi) return ~0ull;
-        if (cur.hi == k.hi && (hashed ? same(cur.lo) : (cur.lo == k.lo))) return t.vals[s];
+        if (cur.hi == k.hi && (hashed ? same(cur.lo) : (cur.lo == k.lo))) return t.slots[s].val;
         s = (s + 1 == t.cap) ? 0 : s + 1;
     }
     return ~0ull;
@@ -182,9 +190,9 @@ __device__ __forceinline__ void table_put(ContentTable t, const Key128& k, u64 v
     u64 s = key_home(k, t.cap);
     const Key128 empty{~0ull, ~0ull};
     for (u64 probe = 0; probe < t.cap; probe++) {
-        const Key128 old = cas_key(t.keys + s, empty, k);
+        const Key128 old = cas_key(&t.slots[s].key, empty, k);
         if (old.hi == kEmptyHi) {
-            t.vals[s] = val;
+            t.slots[s].val = val;
             return;
         }
         s = (s + 1 == t.cap) ? 0 : s + 1;
