@@ -107,7 +107,7 @@ typedef struct lcg_build_stats {
 /* Device time of the kernels of the last call, per kernel kind (collected
  * only while kernel timing is enabled with lcg_set_kernel_timing). */
 typedef struct lcg_kernel_time {
-    char name[24];       /* kernel kind, e.g. "k_phrases" */
+    char name[24];       /* kernel kind, e.g. "k_parse" */
     uint32_t launches;
     uint32_t pad;
     double ms;           /* summed CUDA-event time of its launches */
@@ -123,9 +123,11 @@ void lcg_ctx_destroy(lcg_ctx* ctx);
 const char* lcg_last_error(const lcg_ctx* ctx);
 /* Statistics of the last build call of this context (host struct filled). */
 int lcg_last_build_stats(const lcg_ctx* ctx, lcg_build_stats* out);
-/* Enable (1) or disable (0) per-kernel CUDA-event timing in later calls.  When
- * enabled, every kernel launch is bracketed by two events on the context's
- * stream; the sums are read with lcg_last_kernel_times. */
+/* Per-kernel CUDA-event timing in later calls: 0 off, 1 every kernel launch,
+ * 2 only the parse launches (k_parse, the kernel with most device time; few
+ * events, so the call's own time is barely changed).  Timed launches are
+ * bracketed by two events on the context's stream; the sums are read with
+ * lcg_last_kernel_times.  Other values give LCG_EINVAL. */
 int lcg_set_kernel_timing(lcg_ctx* ctx, int enable);
 /* Copy up to `cap` entries of the per-kind kernel times of the last call into
  * `out` (host) and their number into *count. */

@@ -75,7 +75,7 @@ struct lcg_ctx {
     lcg_build_stats stats{};
     u64 launches = 0;
     // per-kernel CUDA-event timing (optional)
-    bool ktime = false;
+    int ktime = 0;  // 0 off, 1 every launch, 2 parse launches only
     struct KRec {
         const char* name;
         cudaEvent_t a, b;
@@ -150,7 +150,7 @@ void kt_reset(lcg_ctx* ctx) {
 // Record the start of a launch of kernel `name` that moves `bytes` algorithmic
 // bytes; returns a handle for kt_end (or -1 when timing is off).
 int kt_begin(lcg_ctx* ctx, const char* name, double bytes, u32 round = 0) {
-    if (!ctx->ktime) return -1;
+    if (ctx->ktime == 0 || (ctx->ktime == 2 && std::strcmp(name, "k_parse") != 0)) return -1;
     lcg_ctx::KRec r{name, kt_event(ctx), kt_event(ctx), bytes, round};
     ck(ctx, cudaEventRecord(r.a, ctx->st), "cudaEventRecord");
     ctx->krecs.push_back(r);
@@ -1235,8 +1235,8 @@ int lcg_last_build_stats(const lcg_ctx* ctx, lcg_build_stats* out) {
 }
 
 int lcg_set_kernel_timing(lcg_ctx* ctx, int enable) {
-    if (!ctx) return LCG_EINVAL;
-    ctx->ktime = enable != 0;
+    if (!ctx || enable < 0 || enable > 2) return LCG_EINVAL;
+    ctx->ktime = enable;
     return LCG_OK;
 }
 

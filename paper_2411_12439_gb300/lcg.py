@@ -221,9 +221,10 @@ class Context:
         del keep
         return Grammar(self, h)
 
-    def set_kernel_timing(self, enable: bool) -> None:
-        """lcg_set_kernel_timing: bracket every kernel launch with CUDA events."""
-        self._check(load().lcg_set_kernel_timing(self._h, int(bool(enable))))
+    def set_kernel_timing(self, mode) -> None:
+        """lcg_set_kernel_timing: 0/False off, 1/True every kernel launch,
+        2 only the parse launches."""
+        self._check(load().lcg_set_kernel_timing(self._h, int(mode)))
 
     def last_kernel_times(self) -> dict:
         """lcg_last_kernel_times: {kind: {"launches", "ms", "bytes"}} of the last call."""
