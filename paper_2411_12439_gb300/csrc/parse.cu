@@ -98,9 +98,12 @@ constexpr int kCacheProbes = 8;
 // last tile), so that the global counter is touched every few tiles only.
 constexpr int kClaimBufB = 512;   // byte rounds (shared memory also holds the phrase cache)
 constexpr int kClaimBufR = 1024;  // rank rounds
-// Byte rounds: phrases that miss the block's cache are queued and looked up in
-// the global table together, so that full warps run the long lookup path.
-constexpr int kMissBuf = 512;
+// Byte rounds: phrases that miss the block's cache are queued with their keys
+// and looked up in the global table together once the queue is half full, so
+// that full warps run the long lookup path, every few tiles.
+constexpr int kMissBuf = 256;
+constexpr int kMissFlush = 64;  // queued misses that trigger a lookup pass
+constexpr u64 kOkeyBits = 44;  // order keys are below 2^44
 
 template <typename T>
 __device__ u64 scan_right_diff(const T* S, FpSource<T> fp, u64 from, u64 strend, u32 val) {
@@ -308,11 +311,13 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
     __shared__ u32 swp[NWT];
     __shared__ unsigned short sP[kTP];
     // byte rounds: per-block cache of phrase (packed bytes) -> slot, kept across
-    // the block's tiles; val = (iteration << 43) | (q << 31) | slot
+    // the block's tiles (its entries always come from earlier tiles)
     __shared__ u64 ckey[kLocal ? kCacheSlots : 1];
-    __shared__ u64 cval[kLocal ? kCacheSlots : 1];
+    __shared__ u32 cval[kLocal ? kCacheSlots : 1];
     __shared__ u32 sClaim[kClaimBuf];
-    __shared__ u32 sMiss[kLocal ? kMissBuf : 1];  // q | (cache slot + 1) << 16
+    // byte rounds: queued cache misses: key, and order key | (cache slot + 1) << kOkeyBits
+    __shared__ Key128 sMissKey[kLocal ? kMissBuf : 1];
+    __shared__ u64 sMissOk[kLocal ? kMissBuf : 1];
     __shared__ u32 s_nmiss;
     __shared__ u64 s_tail_end;
     __shared__ u32 s_nclaim;
@@ -337,12 +342,13 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
     if constexpr (kLocal) {
         for (int x = tid; x < kCacheSlots; x += kParseThreads) {
             ckey[x] = kEmpty;
-            cval[x] = ~0ull;
+            cval[x] = ~0u;
         }
     }
     if (tid == 0) {
         s_nclaim = 0;
         s_claim_len = 0;
+        s_nmiss = 0;
     }
 
     // persistent blocks: tiles blockIdx.x, blockIdx.x + gridDim.x, ...  Tiles
@@ -350,7 +356,6 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
     u64 iter = 0;
     for (u64 tile = blockIdx.x; tile < ntiles; tile += gridDim.x, iter++) {
         if ((iter & 15) == 0 && round_halted(a)) break;
-        if (tid == 0) s_nmiss = 0;
         const u64 t0 = tile * (u64)kTP;
         const u64 t_end = min(t0 + (u64)kTP, n), s_end = min(t0 + (u64)kSP, n);
         const int ns = (int)(s_end - t0), nt = (int)(t_end - t0);
@@ -421,35 +426,51 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
             return (u32)S[t0 + x];
         };
         // the slot of phrase q = [st, en); *claimed when this call made the entry
-        auto lookup = [&](u32 q, u64 st, u64 en, bool* claimed) -> u32 {
-            *claimed = false;
+        // key of phrase [st, en) (tile offsets); *ok = false for one too long
+        auto make_key = [&](u64 st, u64 en, bool* ok) -> Key128 {
             const u64 len = en - st;
-            if (len > kMaxPhraseLen) { set_error(a.ds, kErrPhraseLong); return ~0u; }
-            const bool hashed = len > inline_max(a.sym_w);
-            Key128 key;
-            if (hashed) {
+            *ok = len <= kMaxPhraseLen;
+            if (!*ok) {
+                set_error(a.ds, kErrPhraseLong);
+                return Key128{0, 0};
+            }
+            if (len > inline_max(a.sym_w)) {
                 // H = sum_j F[Q_j] c^{j-1} mod p, by Horner from the last symbol
                 u64 H = 0;
                 for (u64 x = en; x-- > st;) H = addmod61(mulmod61(H, a.lh.c), (u64)fp(sym(x)));
-                key = key_hashed(H, len, t0 + st);
-            } else {
-                key = key_inline([&](u64 j) { return sym(st + j); }, len, a.sym_w);
+                return key_hashed(H, len, t0 + st);
             }
+            return key_inline([&](u64 j) { return sym(st + j); }, len, a.sym_w);
+        };
+        // The slot of a phrase given its key and order key (a hashed key names
+        // the phrase's position in S); *claimed when this call made the entry.
+        auto lookup_key = [&](const Key128& key, u64 okey, bool* claimed) -> u32 {
+            *claimed = false;
+            const bool hashed = key_is_hashed(key);
+            const u64 len = key_len(key), pos = key.lo;
             if (rt.cap) {
                 const u64 r = table_find(rt, key, hashed, [&](u64 rank) {
                     const u64 o = a.rrhs_off[rank];
                     for (u64 j = 0; j < len; j++)
-                        if ((u32)S[t0 + st + j] != a.rrhs[o + j]) return false;
+                        if ((u32)S[pos + j] != a.rrhs[o + j]) return false;
                     return true;
                 });
                 if (r != ~0ull) return kResidentBit | (u32)r;
             }
-            const u64 slot = table_claim_or_find(bt, key, hashed, okey0 + q, [&](u64 ref) {
+            return (u32)table_claim_or_find(bt, key, hashed, okey, [&](u64 ref) {
                 for (u64 j = 0; j < len; j++)
-                    if (S[ref + j] != S[t0 + st + j]) return false;
+                    if (S[ref + j] != S[pos + j]) return false;
                 return true;
             }, claimed, a.ds);
-            return (u32)slot;
+        };
+        auto lookup = [&](u32 q, u64 st, u64 en, bool* claimed) -> u32 {
+            bool ok;
+            const Key128 key = make_key(st, en, &ok);
+            if (!ok) {
+                *claimed = false;
+                return ~0u;
+            }
+            return lookup_key(key, okey0 + q, claimed);
         };
         // New entries join the block's claim buffer (or, when it is full, the
         // round's list at once).  claim_warp is called by all lanes of a warp
@@ -483,12 +504,11 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
         };
 
         if constexpr (kLocal) {
-            // Short phrases go through the block's cache.  A hit on an entry
-            // made in an earlier tile of this block, or by an earlier
-            // occurrence in this tile, needs nothing more: that occurrence is
-            // already registered in the table.  Otherwise the slot's first
-            // occurrence is lowered to this phrase's order key.  Misses are
-            // queued and looked up after the loop.
+            // Short phrases go through the block's cache.  Its entries come
+            // from earlier tiles of the block, whose phrases precede this
+            // tile's: a hit needs nothing more.  Misses are queued with their
+            // keys and looked up in the global table together once the queue
+            // is half full (and after the block's last tile).
             const u64* sb64 = reinterpret_cast<const u64*>(sb);
             // packed bytes of a phrase of length <= 7 inside the staged bytes
             auto short_key = [&](u32 st, u32 len) -> u64 {
@@ -497,10 +517,22 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                 const u64 v = sh ? (lo >> sh) | (hi << (64 - sh)) : lo;
                 return ((u64)len << 56) | (v & ((1ull << (8 * len)) - 1));
             };
-            auto cache_insert = [&](int h, u64 key, u32 q, u32 slot) {
-                const u64 old = atomicCAS((unsigned long long*)&ckey[h], (unsigned long long)kEmpty,
-                                          (unsigned long long)key);
-                if (old == kEmpty) cval[h] = ((iter & 0x1FFFFF) << 43) | ((u64)q << 31) | slot;
+            // the inline key of a phrase of length <= 15 inside the staged
+            // bytes: its bytes as one little-endian number B, B mod 2^60 (with
+            // the length above) in hi and B >> 60 in lo (the layout of
+            // key_inline for 8-bit symbols)
+            auto byte_key = [&](u32 st, u32 len) -> Key128 {
+                const u32 w = st >> 3, sh = (st & 7) * 8;
+                const u64 x0 = sb64[w], x1 = sb64[w + 1], x2 = sb64[w + 2];
+                u64 b0 = sh ? (x0 >> sh) | (x1 << (64 - sh)) : x0;
+                u64 b1 = sh ? (x1 >> sh) | (x2 << (64 - sh)) : x1;
+                if (len < 8) {
+                    b0 &= (1ull << (8 * len)) - 1;
+                    b1 = 0;
+                } else if (len < 16) {
+                    b1 &= (1ull << (8 * (len - 8))) - 1;
+                }
+                return Key128{(b0 >> 60) | (b1 << 4), (b0 & ((1ull << 60) - 1)) | ((u64)len << 60)};
             };
             for (u32 q = tid; q < cntq; q += kParseThreads) {
                 const u32 st = sP[q];
@@ -508,59 +540,68 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                 const u64 len = en - st;
                 u32 slot = ~0u;
                 int free_h = -1;
-                const bool cacheable = len <= 7 && en <= (u64)ns;
-                if (cacheable) {
+                if (len <= 7 && en <= (u64)ns) {
                     const u64 key = short_key(st, (u32)len);
                     u32 h = (u32)((key * 0x9E3779B97F4A7C15ull) >> (64 - kCacheBits));
                     for (int probe = 0; probe < kCacheProbes; probe++) {
                         const u64 k = ckey[h];
                         if (k == key) {
-                            const u64 v = cval[h];
-                            if (v != ~0ull) {
-                                slot = (u32)(v & 0x7FFFFFFFull);
-                                const u64 vit = v >> 43, vq = (v >> 31) & 0xFFF;
-                                if (vit == (iter & 0x1FFFFF) && vq > q) atomicMin(&bt.slots[slot].val, okey0 + q);
-                            }
+                            slot = cval[h];
                             break;
                         }
-                        if (k == kEmpty) { free_h = (int)h; break; }
+                        if (k == kEmpty) {
+                            free_h = (int)h;
+                            break;
+                        }
                         h = (h + 1) & (kCacheSlots - 1);
                     }
                 }
                 if (slot == ~0u) {
-                    const u32 m = atomicAdd(&s_nmiss, 1u);
-                    if (m < (u32)kMissBuf) {
-                        sMiss[m] = q | ((u32)(free_h + 1) << 16);
-                        continue;
+                    bool ok = true;
+                    const Key128 key = (len <= 15 && en <= (u64)ns) ? byte_key(st, (u32)len) : make_key(st, en, &ok);
+                    if (ok) {
+                        const u32 m = atomicAdd(&s_nmiss, 1u);
+                        if (m < (u32)kMissBuf) {
+                            sMissKey[m] = key;
+                            sMissOk[m] = (okey0 + q) | ((u64)(free_h + 1) << kOkeyBits);
+                            continue;
+                        }
+                        bool claimed;  // queue full: at once (no cache entry)
+                        slot = lookup_key(key, okey0 + q, &claimed);
+                        if (claimed) claim_single(slot, len);
                     }
-                    bool claimed;
-                    slot = lookup(q, st, en, &claimed);  // queue full: at once
-                    if (claimed) claim_single(slot, len);
-                    if (cacheable && free_h >= 0 && slot != ~0u && !(slot & kResidentBit))
-                        cache_insert(free_h, short_key(st, (u32)len), q, slot);
                 }
                 __stcs(a.P_slot + okey0 + q, slot);
             }
             __syncthreads();
-            const u32 nm = min(s_nmiss, (u32)kMissBuf);
-            for (u32 i0 = 0; i0 < nm; i0 += kParseThreads) {  // whole warps take each step
-                const u32 i = i0 + tid;
-                bool claimed = false;
-                u32 slot = ~0u;
-                u64 len = 0;
-                if (i < nm) {
-                    const u32 e = sMiss[i];
-                    const u32 q = e & 0xFFFFu;
-                    const int free_h = (int)(e >> 16) - 1;
-                    const u32 st = sP[q];
-                    const u64 en = phrase_end(q);
-                    len = en - st;
-                    slot = lookup(q, st, en, &claimed);
-                    if (free_h >= 0 && slot != ~0u && !(slot & kResidentBit))
-                        cache_insert(free_h, short_key(st, (u32)len), q, slot);
-                    __stcs(a.P_slot + okey0 + q, slot);
+            const u32 nq = s_nmiss;
+            if (nq >= (u32)kMissFlush || tile + gridDim.x >= ntiles) {
+                const u32 nm = min(nq, (u32)kMissBuf);
+                for (u32 i0 = 0; i0 < nm; i0 += kParseThreads) {  // whole warps take each step
+                    const u32 i = i0 + tid;
+                    bool claimed = false;
+                    u32 slot = ~0u;
+                    u64 len = 0;
+                    if (i < nm) {
+                        const Key128 key = sMissKey[i];
+                        const u64 meta = sMissOk[i];
+                        const u64 okey = meta & ((1ull << kOkeyBits) - 1);
+                        const int free_h = (int)(meta >> kOkeyBits) - 1;
+                        len = key_len(key);
+                        slot = lookup_key(key, okey, &claimed);
+                        if (free_h >= 0 && slot != ~0u && !(slot & kResidentBit)) {
+                            // inline byte key of length <= 7 -> the cache's packed form
+                            const u64 ck = (len << 56) | (key.hi & ((1ull << (8 * len)) - 1));
+                            const u64 old = atomicCAS((unsigned long long*)&ckey[free_h], (unsigned long long)kEmpty,
+                                                      (unsigned long long)ck);
+                            if (old == kEmpty) cval[free_h] = slot;
+                        }
+                        __stcs(a.P_slot + okey, slot);
+                    }
+                    claim_warp(claimed, slot, len);
                 }
-                claim_warp(claimed, slot, len);
+                __syncthreads();
+                if (tid == 0) s_nmiss = 0;
             }
         } else {
             for (u32 q0 = 0; q0 < cntq; q0 += kParseThreads) {  // whole warps take each step
