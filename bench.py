@@ -49,6 +49,7 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--profile-builds", type=int, default=0,
                    help="only run this many batched builds of the workload and exit (for profiler captures)")
@@ -215,6 +216,37 @@ def run_reference(args):
     return 0
 
 
+SERVING_WORKLOAD = ("serving stream: Poisson arrivals of strings with lognormal lengths (median 1 Mbp, sigma 1.5) "
+                    "clipped to [10 kbp, 20 Mbp]; 80% windows of 8 seeded 20 Mbp genomes with 0.1-1% SNPs, "
+                    "20% Zipf(1.1) byte text with copied blocks; 2 lanes, merged into a device-resident grammar")
+
+
+def run_serving(hf, device: int, capacity_gbs: float, count: int = 300, load: float = 0.8) -> dict:
+    """The serving loop on a seeded stream, arrivals paced so that the offered
+    input rate is ``load`` times ``capacity_gbs``: p50 / p99 latency and the
+    input GB/s from first arrival to last completion."""
+    from paper_2411_12439_gb300 import serving
+    stream = li.serving_stream(seed=5, count=count + 4, rate_hz=1.0, n_bases=8, base_len=20_000_000,
+                               len_max=20_000_000)
+    mean_len = float(np.mean([r.data.shape[0] for r in stream]))
+    rate = load * capacity_gbs * 1e9 / mean_len  # requests per second
+    backend = serving.CudaBackend(hf, device=device, lanes=2)
+    srv = serving.Server(backend, lanes=2, max_batch_bytes=64 << 20)
+    srv.start()
+    warm = [srv.submit(r.data) for r in stream[:4]]
+    srv.drain(warm, timeout=120)
+    reqs = serving.replay(srv, stream[4:], time_scale=1.0 / rate)  # arrival_s was drawn at 1 request/s
+    ok = srv.drain(reqs, timeout=600)
+    srv.stop()
+    st = serving.latency_stats(reqs)
+    return {"workload": SERVING_WORKLOAD, "requests": st.get("requests"), "load": load,
+            "offered_gbs": load * capacity_gbs, "gbs": st.get("gbs"),
+            "p50_ms": 1e3 * st["p50_s"] if "p50_s" in st else None,
+            "p99_ms": 1e3 * st["p99_s"] if "p99_s" in st else None,
+            "batches": len(srv.batches), "errors": len(srv.errors) + (0 if ok else 1),
+            "resident_strings": backend.size(srv.resident)}
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -368,6 +400,9 @@ def run_ours(args):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(coll, hf)
+    serving_line = None
+    if world == 1 and not args.no_serving:
+        serving_line = run_serving(hf, local, value)
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -376,7 +411,7 @@ def run_ours(args):
                    "rounds": stats["rounds"], "l2": "inputs larger than L2 (320 MB > 129 MB), no flush",
                    "parallelism": f"dp{world}" if world > 1 else "single GPU"},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roofline,
-        "cpu_baseline": cpu, "plain": plain,
+        "cpu_baseline": cpu, "plain": plain, "serving": serving_line,
         "kernels": {k: {"launches": v["launches"] // v["builds"], "ms_per_step": v["ms"] / v["builds"]}
                     for k, v in sorted(breakdown.items(), key=lambda kv: -kv[1]["ms"])},
     }

@@ -221,6 +221,14 @@ int lcg_export_start(lcg_ctx* ctx, const lcg_grammar* G, uint32_t* F0, uint32_t*
 int lcg_import(lcg_ctx* ctx, uint32_t k, uint32_t nlevels, const uint64_t* g, const uint64_t* const* rhs_off,
                const uint32_t* const* rhs, const uint32_t* const* F, const uint32_t* c_level, const uint32_t* c_rank,
                lcg_grammar** out);
+/* Roots of strings j0 .. j0+count-1 of G: C[j] = (level[x], rank[x]) and the
+ * fingerprint fp[x] = F^level[rank] of exp(T_j) (F^0 for a string of length
+ * one).  The fingerprint depends on the string's content only (Eq. fast_hash):
+ * it is the same whichever strings the grammar holds besides T_j.  Outputs are
+ * HOST arrays of `count` entries.  LCG_EINVAL when j0 + count > k.  Blocking. */
+int lcg_string_roots(lcg_ctx* ctx, const lcg_grammar* G, uint32_t j0, uint32_t count, uint32_t* level,
+                     uint32_t* rank, uint32_t* fp);
+
 /* The packed form of a grammar: one buffer, for storage and for sending a
  * grammar to another process (the merge tree of a sharded collection).
  * Layout (little-endian; every array starts at a multiple of 8 bytes, u32

@@ -1456,6 +1456,36 @@ int lcg_import(lcg_ctx* ctx, uint32_t k, uint32_t nlevels, const uint64_t* g, co
     }
 }
 
+int lcg_string_roots(lcg_ctx* ctx, const lcg_grammar* G, uint32_t j0, uint32_t count, uint32_t* level,
+                     uint32_t* rank, uint32_t* fp) {
+    if (!ctx || !G || (count && (!level || !rank || !fp))) return LCG_EINVAL;
+    if ((u64)j0 + count > G->k) {
+        ctx->err = "string index out of range";
+        return LCG_EINVAL;
+    }
+    if (count == 0) return LCG_OK;
+    LCG_GUARD_BEGIN
+    ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    fail_if(ctx, G->lv.size() > 64, LCG_ELEVELS, "grammar with more than 64 levels");
+    FTable ft{};
+    ft.F[0] = G->F0;
+    for (u32 i = 1; i <= G->lv.size(); i++) ft.F[i] = G->lv[i - 1].F;
+    ft.n = (u32)G->lv.size() + 1;
+    u32* d = dalloc<u32>(ctx, 3ull * count);
+    ck(ctx, launch_roots(G->c_level, G->c_rank, j0, count, ft, d, ctx->st), "k_roots");
+    std::vector<u32> h(3ull * count);
+    ck(ctx, cudaMemcpyAsync(h.data(), d, h.size() * 4, cudaMemcpyDeviceToHost, ctx->st), "roots");
+    dfree(ctx, d);
+    sync(ctx);
+    for (u32 x = 0; x < count; x++) {
+        level[x] = h[3 * x];
+        rank[x] = h[3 * x + 1];
+        fp[x] = h[3 * x + 2];
+    }
+    return LCG_OK;
+    LCG_GUARD_END
+}
+
 // ---- packed form: one buffer, every section 8-byte aligned ----------------
 
 constexpr u64 kPackMagic = 0x4C434753ull;  // "LCGS"

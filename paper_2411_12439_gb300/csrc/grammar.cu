@@ -169,6 +169,25 @@ cudaError_t launch_check_fp(const u32* rhs, const u64* rhs_off, u64 g, const u32
     return cudaGetLastError();
 }
 
+// Root of strings j0 .. j0+cnt-1: C[j] = (level, rank) and the fingerprint
+// F^level[rank] of exp(T_j) (Eq. fast_hash: it depends on the content only).
+__global__ void k_roots(const u32* __restrict__ c_level, const u32* __restrict__ c_rank, u32 j0, u32 cnt, FTable ft,
+                        u32* __restrict__ out) {
+    for (u32 x = blockIdx.x * blockDim.x + threadIdx.x; x < cnt; x += gridDim.x * blockDim.x) {
+        const u32 lvl = c_level[j0 + x], r = c_rank[j0 + x];
+        out[3 * x] = lvl;
+        out[3 * x + 1] = r;
+        out[3 * x + 2] = lvl < ft.n ? __ldg(ft.F[lvl] + r) : 0u;
+    }
+}
+
+cudaError_t launch_roots(const u32* c_level, const u32* c_rank, u32 j0, u32 cnt, const FTable& ft, u32* out,
+                         cudaStream_t st) {
+    if (cnt == 0) return cudaSuccess;
+    k_roots<<<(cnt + 255) / 256 < 1024 ? (cnt + 255) / 256 : 1024, 256, 0, st>>>(c_level, c_rank, j0, cnt, ft, out);
+    return cudaGetLastError();
+}
+
 __global__ void k_remap_c(const u32* __restrict__ c_level, u32* __restrict__ c_rank, u32 k, u32 level,
                           const u32* __restrict__ M) {
     for (u32 j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x)

@@ -127,6 +127,13 @@ cudaError_t launch_merge_append(const u32* brhs, const u64* brhs_off, const u32*
                                 u32* aF, u32* M, u64 ga_new, u64 Ga_new, cudaStream_t st);
 cudaError_t launch_check_fp(const u32* rhs, const u64* rhs_off, u64 g, const u32* Fprev, LevelHash lh, const u32* F,
                             DevStatus* ds, cudaStream_t st);
+// F arrays of a grammar by level (F[0] = F^0).
+struct FTable {
+    const u32* F[65];
+    u32 n;
+};
+cudaError_t launch_roots(const u32* c_level, const u32* c_rank, u32 j0, u32 cnt, const FTable& ft, u32* out,
+                         cudaStream_t st);
 cudaError_t launch_remap_c(const u32* c_level, u32* c_rank, u32 k, u32 level, const u32* M, cudaStream_t st);
 cudaError_t launch_rule_lens(const u32* cur, u64 cnt, const u64* rhs_off, u32* lens, cudaStream_t st);
 cudaError_t launch_expand(const u32* cur, u64 cnt, const u64* offs, const u64* rhs_off, const u32* rhs, u32* next,

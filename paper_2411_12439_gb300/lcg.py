@@ -25,7 +25,8 @@ SYMBOLS = [
     "lcg_ctx_create", "lcg_ctx_destroy", "lcg_last_error", "lcg_last_build_stats", "lcg_set_kernel_timing",
     "lcg_last_kernel_times", "lcg_build", "lcg_build_into",
     "lcg_merge", "lcg_decompress", "lcg_decompress_static", "lcg_grammar_shape", "lcg_level_size", "lcg_export_level",
-    "lcg_export_start", "lcg_import", "lcg_packed_size", "lcg_export_packed", "lcg_import_packed", "lcg_grammar_free",
+    "lcg_export_start", "lcg_string_roots", "lcg_import", "lcg_packed_size", "lcg_export_packed", "lcg_import_packed",
+    "lcg_grammar_free",
 ]
 
 
@@ -93,6 +94,7 @@ def load(build_if_missing: bool = True):
     lib.lcg_level_size.argtypes = [P, U32, ctypes.POINTER(U64), ctypes.POINTER(U64)]
     lib.lcg_export_level.argtypes = [P, P, U32, P, P, P]
     lib.lcg_export_start.argtypes = [P, P, P, P, P]
+    lib.lcg_string_roots.argtypes = [P, P, U32, U32, P, P, P]
     lib.lcg_import.argtypes = [P, U32, U32, P, P, P, P, P, P, PP]
     lib.lcg_packed_size.argtypes = [P, ctypes.POINTER(U64)]
     lib.lcg_export_packed.argtypes = [P, P, P, U64]
@@ -291,6 +293,17 @@ class Grammar:
         cr = np.zeros(max(k, 1), dtype=np.uint32)
         self.ctx._check(lib.lcg_export_start(self.ctx._h, self._h, _np_ptr(F0), _np_ptr(cl), _np_ptr(cr)))
         return {"F0": F0, "levels": levels, "c_level": cl[:k], "c_rank": cr[:k]}
+
+    def roots(self, j0: int = 0, count=None):
+        """lcg_string_roots: (level, rank, fingerprint) arrays of strings j0 ..
+        j0 + count - 1 (the fingerprint depends on the string's content only)."""
+        k, _ = self.shape
+        count = k - j0 if count is None else count
+        lv = np.zeros(max(count, 1), dtype=np.uint32)
+        rk = np.zeros(max(count, 1), dtype=np.uint32)
+        fp = np.zeros(max(count, 1), dtype=np.uint32)
+        self.ctx._check(load().lcg_string_roots(self.ctx._h, self._h, j0, count, _np_ptr(lv), _np_ptr(rk), _np_ptr(fp)))
+        return lv[:count], rk[:count], fp[:count]
 
     def packed_size(self) -> int:
         n = ctypes.c_uint64(0)

@@ -1,0 +1,245 @@
+"""Serving loop: continuous batching of string-compression requests on one GPU.
+
+Requests (strings) arrive at any time.  ``lanes`` workers, each with its own
+context and CUDA stream, take batches from the queue of pending requests: a
+worker that becomes free admits pending requests, oldest first, while the
+batch stays under ``max_batch_bytes`` and the device-memory estimate of all
+running batches stays under the budget, and runs the batch's BuildGram
+(Sec. 3.3) at once, so that requests arriving while other batches are on the
+GPU start as soon as a lane and memory are free, and their work overlaps on
+the device.  Each finished batch is merged (MergeGrams, Sec. 3.6) into the
+grammar kept resident on the device.
+
+A request's result is the root of its string: the level of its C entry and
+the fingerprint of its expansion (F^level[rank], Eq. fast_hash), which depend
+on the string's content only and are therefore the same whether the string
+was parsed alone or in any mix; plus the string's index in the resident
+grammar, from which it can be expanded.
+
+Memory admission: the context's allocations come from a stream-ordered pool
+that keeps freed memory, so the free memory the driver reports does not come
+back after a batch.  The server therefore keeps its own account: a budget
+(a fraction of the device memory free when it starts) and, per running batch,
+``mem_factor`` times its input bytes.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+
+import numpy as np
+
+
+class Request:
+    """One string to compress.  ``result`` is (level, fingerprint) of its
+    root, ``index`` its string index in the resident grammar, ``latency`` the
+    seconds from submission to completion."""
+
+    def __init__(self, data, t_submit: float):
+        self.data = np.ascontiguousarray(np.frombuffer(data, dtype=np.uint8) if isinstance(data, (bytes, bytearray))
+                                         else data, dtype=np.uint8)
+        self.t_submit = t_submit
+        self.t_start = None
+        self.t_done = None
+        self.result = None
+        self.index = None
+        self.error = None
+        self.batch = None
+        self._done = threading.Event()
+
+    @property
+    def n(self) -> int:
+        return int(self.data.shape[0])
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_submit
+
+    def wait(self, timeout=None) -> bool:
+        return self._done.wait(timeout)
+
+
+class CudaBackend:
+    """Grammar operations on the GPU: one context per lane (each with its own
+    stream) for builds, and one context that owns the resident grammar."""
+
+    def __init__(self, hash_family, device: int = 0, lanes: int = 2):
+        from .lcg import Context
+        self.device = device
+        self.res_ctx = Context(hash_family, device=device)
+        self.ctxs = [Context(hash_family, device=device) for _ in range(lanes)]
+
+    def empty(self):
+        return self.res_ctx.import_grammar({"levels": [], "c_level": np.zeros(0, np.uint32),
+                                            "c_rank": np.zeros(0, np.uint32), "F0": np.zeros(256, np.uint32)})
+
+    def build(self, lane: int, data: np.ndarray, offsets: np.ndarray):
+        return self.ctxs[lane].build(data, offsets)
+
+    def roots(self, lane: int, g):
+        lv, _, fp = g.roots()
+        return lv, fp
+
+    def merge(self, resident, g):
+        self.res_ctx.merge(resident, g)
+        return resident
+
+    def size(self, g) -> int:
+        return g.shape[0]
+
+    def free(self, g):
+        g.free()
+
+    def memory_budget(self, fraction: float) -> int:
+        import torch
+        free, _ = torch.cuda.mem_get_info(self.device)
+        return int(free * fraction)
+
+
+class Server:
+    """Continuous-batching request loop over a grammar kept resident on the
+    device.  ``submit`` may be called from any thread; ``start`` runs the
+    lanes in background threads, ``stop`` ends them after the pending work."""
+
+    def __init__(self, backend, lanes: int = 2, max_batch_bytes: int = 64 << 20, mem_factor: float = 12.0,
+                 budget_bytes: int | None = None, budget_fraction: float = 0.5):
+        self.backend = backend
+        self.lanes = lanes
+        self.max_batch_bytes = max_batch_bytes
+        self.mem_factor = mem_factor
+        self.budget = budget_bytes if budget_bytes is not None else backend.memory_budget(budget_fraction)
+        self.resident = backend.empty()
+        self._pending = collections.deque()
+        self._cv = threading.Condition()
+        self._merge_lock = threading.Lock()
+        self._inflight = 0.0
+        self._running = False
+        self._threads = []
+        self.batches = []  # (lane, number of requests, input bytes, t_start, t_end)
+        self.errors = []
+
+    # -- requests -------------------------------------------------------------
+    def submit(self, data) -> Request:
+        r = Request(data, time.perf_counter())
+        if r.n == 0:
+            r.error = "empty string"
+            r.t_done = r.t_submit
+            r._done.set()
+            return r
+        with self._cv:
+            self._pending.append(r)
+            self._cv.notify_all()
+        return r
+
+    # -- lanes ----------------------------------------------------------------
+    def start(self):
+        self._running = True
+        for lane in range(self.lanes):
+            t = threading.Thread(target=self._lane, args=(lane,), daemon=True)
+            t.start()
+            self._threads.append(t)
+
+    def stop(self, timeout: float | None = None):
+        with self._cv:
+            self._running = False
+            self._cv.notify_all()
+        for t in self._threads:
+            t.join(timeout)
+        self._threads = []
+
+    def drain(self, requests, timeout: float | None = None) -> bool:
+        """Wait until every request in ``requests`` has its result."""
+        end = None if timeout is None else time.perf_counter() + timeout
+        for r in requests:
+            left = None if end is None else max(0.0, end - time.perf_counter())
+            if not r.wait(left):
+                return False
+        return True
+
+    def _take_batch(self):
+        """Admit pending requests, oldest first, into a batch (under the lock)."""
+        batch, nbytes = [], 0
+        while self._pending:
+            r = self._pending[0]
+            need = self.mem_factor * (nbytes + r.n)
+            if batch and (nbytes + r.n > self.max_batch_bytes or self._inflight + need > self.budget):
+                break
+            if not batch and self._inflight > 0 and self._inflight + need > self.budget:
+                break  # wait for memory: another batch is running
+            self._pending.popleft()
+            batch.append(r)
+            nbytes += r.n
+        return batch, nbytes
+
+    def _lane(self, lane: int):
+        while True:
+            with self._cv:
+                while True:
+                    batch, nbytes = self._take_batch() if self._pending else ([], 0)
+                    if batch:
+                        est = self.mem_factor * nbytes
+                        self._inflight += est
+                        break
+                    if not self._running and not self._pending:
+                        return
+                    self._cv.wait(0.05)
+            t0 = time.perf_counter()
+            for r in batch:
+                r.t_start = t0
+            try:
+                offsets = np.zeros(len(batch) + 1, dtype=np.uint64)
+                np.cumsum([r.n for r in batch], out=offsets[1:])
+                data = np.concatenate([r.data for r in batch])
+                g = self.backend.build(lane, data, offsets)
+                levels, fps = self.backend.roots(lane, g)
+                with self._merge_lock:
+                    base = self.backend.size(self.resident)
+                    self.resident = self.backend.merge(self.resident, g)
+                self.backend.free(g)
+                t1 = time.perf_counter()
+                for j, r in enumerate(batch):
+                    r.result = (int(levels[j]), int(fps[j]))
+                    r.index = base + j
+                    r.batch = len(self.batches)
+                    r.t_done = t1
+            except Exception as e:  # the batch's requests fail; the lane goes on
+                t1 = time.perf_counter()
+                self.errors.append(repr(e))
+                for r in batch:
+                    r.error = repr(e)
+                    r.t_done = t1
+            with self._cv:
+                self._inflight -= est
+                self.batches.append((lane, len(batch), nbytes, t0, t1))
+                self._cv.notify_all()
+            for r in batch:
+                r._done.set()
+
+
+def latency_stats(requests) -> dict:
+    """p50 / p99 / mean latency (seconds) and input GB/s over the span from the
+    first submission to the last completion."""
+    done = [r for r in requests if r.t_done is not None and r.error is None]
+    if not done:
+        return {"requests": 0}
+    lat = np.array([r.latency for r in done])
+    span = max(r.t_done for r in done) - min(r.t_submit for r in done)
+    nbytes = sum(r.n for r in done)
+    return {"requests": len(done), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "input_bytes": int(nbytes), "span_s": float(span),
+            "gbs": nbytes / span / 1e9 if span > 0 else None}
+
+
+def replay(server: Server, stream, time_scale: float = 1.0):
+    """Submit the requests of ``stream`` (objects with ``arrival_s`` and
+    ``data``) at their arrival times, scaled by ``time_scale``; returns the
+    Request objects."""
+    t0 = time.perf_counter()
+    out = []
+    for item in stream:
+        delay = item.arrival_s * time_scale - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        out.append(server.submit(item.data))
+    return out

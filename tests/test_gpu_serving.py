@@ -1,0 +1,60 @@
+"""The serving loop on the GPU: two lanes (contexts on their own streams)
+build batches of requests that arrive while other batches run, merge them into
+the device-resident grammar, and every request's root (level and fingerprint
+of its expansion) equals the root of the same string parsed alone.  The
+resident grammar equals the oracle's BuildGram over the strings in merge order,
+and strings expand from it to their bytes."""
+import numpy as np
+import pytest
+
+import lcg_inputs as li
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+def _stream(seed, count):
+    rng = np.random.default_rng(seed)
+    bases = [li.random_dna(rng, 2_000_000) for _ in range(3)]
+    out, t = [], 0.0
+    for i in range(count):
+        t += float(rng.exponential(0.003))
+        n = int(np.clip(rng.lognormal(np.log(60_000), 1.2), 2, 1_500_000))
+        if i % 5 == 4:
+            data = np.frombuffer(li.zipf_text(rng, n).tobytes(), dtype=np.uint8)
+        else:
+            b = bases[int(rng.integers(0, 3))]
+            s0 = int(rng.integers(0, b.shape[0] - n))
+            data = li.apply_snps(rng, b[s0:s0 + n], float(rng.uniform(0.001, 0.01)))
+        out.append(li.Request(t, data, "x"))
+    return out
+
+
+def test_serving_alone_and_in_the_mix(hf):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_12439_gb300 import Context, serving
+    stream = _stream(21, 36)
+    backend = serving.CudaBackend(hf, device=0, lanes=2)
+    srv = serving.Server(backend, lanes=2, max_batch_bytes=3 << 20)
+    srv.start()
+    reqs = serving.replay(srv, stream)
+    assert srv.drain(reqs, timeout=300)
+    srv.stop()
+    assert not srv.errors, srv.errors
+    assert len(srv.batches) > 2
+    alone_ctx = Context(hf, device=0)
+    for r in reqs:
+        g = alone_ctx.build(r.data, np.array([0, r.n], dtype=np.uint64))
+        lv, _, fp = g.roots()
+        assert r.result == (int(lv[0]), int(fp[0]))
+        g.free()
+    order = sorted(reqs, key=lambda r: r.index)
+    assert [r.index for r in order] == list(range(len(reqs)))
+    want = O.build(li.from_strings([r.data for r in order]), hf).export()
+    assert O.grammars_equal(srv.resident.export(), want)
+    for r in order[::7]:
+        assert srv.resident.decompress(r.index) == r.data.tobytes()
+    st = serving.latency_stats(reqs)
+    assert st["requests"] == len(reqs) and st["p99_s"] >= st["p50_s"] > 0
