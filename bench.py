@@ -244,6 +244,11 @@ def run_serving(hf, device: int, capacity_gbs: float, count: int = 300, load: fl
             "p50_ms": 1e3 * st["p50_s"] if "p50_s" in st else None,
             "p99_ms": 1e3 * st["p99_s"] if "p99_s" in st else None,
             "batches": len(srv.batches), "errors": len(srv.errors) + (0 if ok else 1),
+            "batch_ms": {k: 1e3 * float(np.mean([p[k] for p in srv.phases])) for k in ("gather", "build", "roots", "merge")}
+            if srv.phases else None,
+            "builds_redone": sum(p.get("redone", 0) for p in srv.phases),
+            "builds_planned": sum(1 for p in srv.phases if p.get("async_rounds", 0) > 0),
+            "table_regrowths": sum(p.get("retries", 0) for p in srv.phases),
             "resident_strings": backend.size(srv.resident)}
 
 

@@ -102,6 +102,9 @@ typedef struct lcg_build_stats {
                                    build was redone round by round */
     uint32_t pad;
     lcg_round_stats round[64];
+    double plan_slack;          /* the context's multiplier of planned buffer sizes after
+                                   the call: it grows after a plan that did not fit and
+                                   shrinks back towards 1 while plans fit */
 } lcg_build_stats;
 
 /* Device time of the kernels of the last call, per kernel kind (collected

@@ -47,6 +47,7 @@ struct lcg_ctx {
     int device = 0;
     cudaStream_t st = nullptr;
     std::vector<lcg_grammar*> live;  // grammars created here and not yet freed
+    double plan_slack = 1.0;         // multiplier of the planned buffer sizes (adaptive)
     bool own_stream = false;
     std::vector<u64> a, b, c;
     u32 levels = 0, m_bits = 32;
@@ -724,13 +725,16 @@ int rounds_async(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32& i) {
         const double P_est = ctx->p_hint[r] * (double)n_est;
         const double g_est = ctx->ratio_hint[r] * P_est;
         const double G_est = ctx->glen_hint[r] * g_est;
-        const u64 cap = std::min<u64>(std::max<u64>(8192, (u64)(g_est * 1.1 / 0.7) + 1024), kMaxRank + 1);
+        // slack over the estimates: 10-25 % times the context's plan slack,
+        // which grows after a plan that did not fit and shrinks while plans fit
+        const double sl = ctx->plan_slack;
+        const u64 cap = std::min<u64>(std::max<u64>(8192, (u64)(g_est * 1.1 * sl / 0.7) + 1024), kMaxRank + 1);
         caps[r] = cap;
         alloc_table(ctx, b, cap);
         set_table(a, b);
         enqueue_parse(ctx, a, n_est);
-        const u64 g_alloc = (u64)(g_est * 1.25) + 1024;
-        grow_level(ctx, L, L.g + g_alloc, L.G + (u64)(G_est * 1.25) + 4096);
+        const u64 g_alloc = (u64)(g_est * 1.25 * sl) + 1024;
+        grow_level(ctx, L, L.g + g_alloc, L.G + (u64)(G_est * 1.25 * sl) + 4096);
         L.rvalid = false;
         alloc_naming(ctx, b, g_alloc);
         g_base[r] = L.g;
@@ -1259,7 +1263,9 @@ int lcg_build(lcg_ctx* ctx, const uint8_t* data, const uint64_t* offsets, uint32
     G = new_grammar(ctx);
     try {
         build_into(ctx, G, data, offsets, k, data_on_device, false, true);
+        if (ctx->stats.async_rounds > 0) ctx->plan_slack = std::max(1.0, ctx->plan_slack * 0.97);
     } catch (const Retry&) {
+        ctx->plan_slack = std::min(4.0, ctx->plan_slack * 1.6);
         // the rounds planned from the previous build did not fit: round by round
         sync(ctx);
         free_grammar_now(G);
@@ -1269,6 +1275,7 @@ int lcg_build(lcg_ctx* ctx, const uint8_t* data, const uint64_t* offsets, uint32
         build_into(ctx, G, data, offsets, k, data_on_device, false, false);
         ctx->stats.redone = 1;
     }
+    ctx->stats.plan_slack = ctx->plan_slack;
     sync(ctx);
     kt_collect(ctx);
     *out = G;

@@ -144,6 +144,8 @@ __device__ u64 table_claim_or_find(ContentTable t, const Key128& k, bool hashed,
     const Key128 empty{~0ull, ~0ull};
     const u64 limit = t.cap < kMaxProbes ? t.cap : kMaxProbes;
     for (u64 probe = 0; probe < limit; probe++) {
+        // once the table is over its load limit the pass is rerun: stop early
+        if ((probe & 63) == 63 && vload(&ds->overflow)) return ~0ull;
         Key128* kp = &t.slots[s].key;
         Key128 cur = ld_key_relaxed(kp);
         if (cur.hi == kEmptyHi) {

@@ -55,7 +55,7 @@ class KernelTimeC(ctypes.Structure):
 class BuildStatsC(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_uint32), ("async_rounds", ctypes.c_uint32), ("kernel_launches", ctypes.c_uint64),
                 ("input_bytes", ctypes.c_uint64), ("redone", ctypes.c_uint32), ("pad", ctypes.c_uint32),
-                ("round", RoundStatsC * 64)]
+                ("round", RoundStatsC * 64), ("plan_slack", ctypes.c_double)]
 
 
 _lib = None
@@ -243,6 +243,7 @@ class Context:
                                                                 "retries")}, "parse_ms": float(st.round[i].parse_ms)}
                   for i in range(min(st.rounds, 64))]
         return {"rounds": int(st.rounds), "async_rounds": int(st.async_rounds), "redone": bool(st.redone),
+                "plan_slack": float(st.plan_slack),
                 "kernel_launches": int(st.kernel_launches),
                 "input_bytes": int(st.input_bytes), "per_round": rounds}
 

@@ -69,17 +69,39 @@ class CudaBackend:
         self.device = device
         self.res_ctx = Context(hash_family, device=device)
         self.ctxs = [Context(hash_family, device=device) for _ in range(lanes)]
+        self.staging = [None] * lanes
 
     def empty(self):
         return self.res_ctx.import_grammar({"levels": [], "c_level": np.zeros(0, np.uint32),
                                             "c_rank": np.zeros(0, np.uint32), "F0": np.zeros(256, np.uint32)})
 
-    def build(self, lane: int, data: np.ndarray, offsets: np.ndarray):
+    def gather(self, lane: int, parts, total: int):
+        """The batch's strings back to back in the lane's page-locked host
+        buffer (grown as needed), so that the build's upload runs at link
+        speed."""
+        import torch
+        buf = self.staging[lane]
+        if buf is None or buf.numel() < total:
+            buf = torch.empty(max(total, 1 << 20) * 5 // 4, dtype=torch.uint8).pin_memory()
+            self.staging[lane] = buf
+        view = buf.numpy()
+        pos = 0
+        for x in parts:
+            view[pos:pos + x.shape[0]] = x
+            pos += x.shape[0]
+        return buf[:total]
+
+    def build(self, lane: int, data, offsets: np.ndarray):
         return self.ctxs[lane].build(data, offsets)
 
     def roots(self, lane: int, g):
         lv, _, fp = g.roots()
         return lv, fp
+
+    def build_info(self, lane: int) -> dict:
+        st = self.ctxs[lane].last_build_stats()
+        return {"rounds": st["rounds"], "async_rounds": st["async_rounds"], "redone": int(st["redone"]),
+                "retries": sum(r["retries"] for r in st["per_round"])}
 
     def merge(self, resident, g):
         self.res_ctx.merge(resident, g)
@@ -117,6 +139,7 @@ class Server:
         self._running = False
         self._threads = []
         self.batches = []  # (lane, number of requests, input bytes, t_start, t_end)
+        self.phases = []   # per batch: seconds spent gathering, building, reading roots, merging
         self.errors = []
 
     # -- requests -------------------------------------------------------------
@@ -190,14 +213,20 @@ class Server:
             try:
                 offsets = np.zeros(len(batch) + 1, dtype=np.uint64)
                 np.cumsum([r.n for r in batch], out=offsets[1:])
-                data = np.concatenate([r.data for r in batch])
+                data = self.backend.gather(lane, [r.data for r in batch], int(offsets[-1]))
+                ta = time.perf_counter()
                 g = self.backend.build(lane, data, offsets)
+                tb = time.perf_counter()
                 levels, fps = self.backend.roots(lane, g)
+                tc = time.perf_counter()
                 with self._merge_lock:
                     base = self.backend.size(self.resident)
                     self.resident = self.backend.merge(self.resident, g)
                 self.backend.free(g)
                 t1 = time.perf_counter()
+                ph = {"gather": ta - t0, "build": tb - ta, "roots": tc - tb, "merge": t1 - tc}
+                ph.update(self.backend.build_info(lane))
+                self.phases.append(ph)
                 for j, r in enumerate(batch):
                     r.result = (int(levels[j]), int(fps[j]))
                     r.index = base + j

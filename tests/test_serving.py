@@ -22,6 +22,9 @@ class OracleBackend:
         return O.from_export({"levels": [], "c_level": np.zeros(0, np.uint32), "c_rank": np.zeros(0, np.uint32),
                               "F0": self.F0}, self.tag)
 
+    def gather(self, lane, parts, total):
+        return np.concatenate(parts)
+
     def build(self, lane, data, offsets):
         self.builds += 1
         return O.build(li.Collection(data=data, offsets=offsets), self.hf)
@@ -35,6 +38,9 @@ class OracleBackend:
 
     def merge(self, resident, g):
         return resident.merge(g)
+
+    def build_info(self, lane):
+        return {}
 
     def size(self, g):
         return g.k
