@@ -65,9 +65,9 @@ struct lcg_ctx {
     u64 lb1_tiles = 0;
     void* lb2 = nullptr;
     u64 lb2_tiles = 0;
-    double ratio_hint[64] = {0};  // new rules per phrase in the last build, per level
-    double p_hint[64] = {0};      // phrases per symbol in the last build, per level
-    double glen_hint[64] = {0};   // symbols per new rule in the last build, per level
+    double ratio_hint[64] = {0};  // new rules per phrase, per level (decaying maximum over builds)
+    double p_hint[64] = {0};      // phrases per symbol, per level (decaying maximum)
+    double glen_hint[64] = {0};   // symbols per new rule, per level (decaying maximum)
     u32 hint_rounds = 0;          // rounds of the last build (0: none yet)
     // per-round device status, counts and totals (rounds enqueued without syncs)
     DevStatus* ds_arr = nullptr;
@@ -338,11 +338,15 @@ void free_grammar_now(lcg_grammar* G) {
 // BuildGram round driver
 // --------------------------------------------------------------------------
 
+// Per-round ratios that size the next build's buffers: the largest seen,
+// decaying by 10 % per build, so that a context that sees collections of
+// changing make-up (a serving loop) keeps plans that fit.
 void record_hints(lcg_ctx* ctx, u32 i, u64 n, u64 P, u64 g, u64 G) {
     if (i >= 64) return;
-    ctx->ratio_hint[i] = P ? (double)g / (double)P : 0.0;
-    ctx->p_hint[i] = n ? (double)P / (double)n : 0.0;
-    ctx->glen_hint[i] = g ? (double)G / (double)g : 2.0;
+    auto keep = [](double old, double x) { return std::max(x, 0.9 * old); };
+    ctx->ratio_hint[i] = keep(ctx->ratio_hint[i], P ? (double)g / (double)P : 0.0);
+    ctx->p_hint[i] = keep(ctx->p_hint[i], n ? (double)P / (double)n : 0.0);
+    ctx->glen_hint[i] = keep(ctx->glen_hint[i], g ? (double)G / (double)g : 2.0);
 }
 
 // The sequence a round reads: T^i, its fingerprints (rounds >= 2) and the

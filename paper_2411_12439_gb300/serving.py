@@ -27,6 +27,7 @@ from __future__ import annotations
 import collections
 import threading
 import time
+import warnings
 
 import numpy as np
 
@@ -84,11 +85,9 @@ class CudaBackend:
         if buf is None or buf.numel() < total:
             buf = torch.empty(max(total, 1 << 20) * 5 // 4, dtype=torch.uint8).pin_memory()
             self.staging[lane] = buf
-        view = buf.numpy()
-        pos = 0
-        for x in parts:
-            view[pos:pos + x.shape[0]] = x
-            pos += x.shape[0]
+        with warnings.catch_warnings():  # read-only request bytes are only read here
+            warnings.filterwarnings("ignore", message="The given NumPy array is not writable")
+            torch.cat([torch.from_numpy(x) for x in parts], out=buf[:total])
         return buf[:total]
 
     def build(self, lane: int, data, offsets: np.ndarray):
