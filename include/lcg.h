@@ -132,6 +132,24 @@ int lcg_last_build_stats(const lcg_ctx* ctx, lcg_build_stats* out);
  * bracketed by two events on the context's stream; the sums are read with
  * lcg_last_kernel_times.  Other values give LCG_EINVAL. */
 int lcg_set_kernel_timing(lcg_ctx* ctx, int enable);
+/* Launch and sizing parameters of later builds (picked by an autotuner, e.g.
+ * paper_2411_12439_gb300/autotune.py; the results do not depend on them):
+ *   table_load          phrase-table slots per expected new rule is 1 / table_load
+ *                       (0.3 .. 0.78; a table past 0.8 is regrown and the round rerun);
+ *   parse_blocks_per_sm resident k_parse blocks per SM, 0 = as many as fit;
+ *   miss_flush          byte rounds: queued cache misses that trigger a lookup pass
+ *                       (32 .. 256).
+ * Defaults: 0.7, 0, 64.  Out-of-range values give LCG_EINVAL. */
+typedef struct lcg_tuning {
+    double table_load;
+    uint32_t parse_blocks_per_sm;
+    uint32_t miss_flush;
+    uint32_t pad;
+    uint32_t pad2;
+} lcg_tuning;
+int lcg_set_tuning(lcg_ctx* ctx, const lcg_tuning* t);
+int lcg_get_tuning(const lcg_ctx* ctx, lcg_tuning* t);
+
 /* Copy up to `cap` entries of the per-kind kernel times of the last call into
  * `out` (host) and their number into *count. */
 int lcg_last_kernel_times(const lcg_ctx* ctx, lcg_kernel_time* out, uint32_t cap, uint32_t* count);

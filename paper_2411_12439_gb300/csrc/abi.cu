@@ -48,6 +48,7 @@ struct lcg_ctx {
     cudaStream_t st = nullptr;
     std::vector<lcg_grammar*> live;  // grammars created here and not yet freed
     double plan_slack = 1.0;         // multiplier of the planned buffer sizes (adaptive)
+    lcg_tuning tuning{0.7, 0, 64, 0};  // table load, k_parse blocks per SM, miss flush
     bool own_stream = false;
     std::vector<u64> a, b, c;
     u32 levels = 0, m_bits = 32;
@@ -485,6 +486,8 @@ RoundArgs round_args(lcg_ctx* ctx, lcg_grammar* R, const RoundInput& in, RoundBu
     a.Fprev = fprev_of(R, i);
     a.lh = level_hash(ctx, i);
     a.level = i;
+    a.parse_blocks = ctx->tuning.parse_blocks_per_sm;
+    a.miss_flush = ctx->tuning.miss_flush;
     a.tiles_bound = b.tiles;
     a.string_first = b.string_first;
     a.tile_str = b.tile_str;
@@ -642,7 +645,7 @@ void round_sync(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32 i, bool agains
     u64 cap;
     if (hint > 0) {
         const u64 P_est = std::min<u64>(b.Pmax, (u64)(ctx->p_hint[std::min<u32>(i, 63)] * (double)n) + 64);
-        cap = std::max<u64>(8192, (u64)(hint * (double)P_est / 0.7) + 1024);
+        cap = std::max<u64>(8192, (u64)(hint * (double)P_est / ctx->tuning.table_load) + 1024);
     } else {
         const u64 P_est = std::min<u64>(b.Pmax, (u64)(p_ratio * 1.2 * (double)n) + 64);
         const double ratio = (i == 1) ? 0.02 : std::min(1.0, std::max(prev_ratio * 2.0, 0.05));
@@ -732,7 +735,8 @@ int rounds_async(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32& i) {
         // slack over the estimates: 10-25 % times the context's plan slack,
         // which grows after a plan that did not fit and shrinks while plans fit
         const double sl = ctx->plan_slack;
-        const u64 cap = std::min<u64>(std::max<u64>(8192, (u64)(g_est * 1.1 * sl / 0.7) + 1024), kMaxRank + 1);
+        const u64 cap = std::min<u64>(std::max<u64>(8192, (u64)(g_est * 1.1 * sl / ctx->tuning.table_load) + 1024),
+                                      kMaxRank + 1);
         caps[r] = cap;
         alloc_table(ctx, b, cap);
         set_table(a, b);
@@ -1245,6 +1249,26 @@ int lcg_last_build_stats(const lcg_ctx* ctx, lcg_build_stats* out) {
 int lcg_set_kernel_timing(lcg_ctx* ctx, int enable) {
     if (!ctx || enable < 0 || enable > 2) return LCG_EINVAL;
     ctx->ktime = enable;
+    return LCG_OK;
+}
+
+int lcg_set_tuning(lcg_ctx* ctx, const lcg_tuning* t) {
+    if (!ctx || !t) return LCG_EINVAL;
+    const int maxb = std::max(parse_max_blocks(1), parse_max_blocks(4));
+    if (!(t->table_load >= 0.3 && t->table_load <= 0.78) || t->parse_blocks_per_sm > (uint32_t)maxb ||
+        t->miss_flush < 32 || t->miss_flush > 256) {
+        ctx->err = "tuning out of range: table_load in [0.3, 0.78], parse_blocks_per_sm <= " + std::to_string(maxb) +
+                   ", miss_flush in [32, 256]";
+        return LCG_EINVAL;
+    }
+    ctx->tuning = *t;
+    ctx->tuning.pad = 0;
+    return LCG_OK;
+}
+
+int lcg_get_tuning(const lcg_ctx* ctx, lcg_tuning* t) {
+    if (!ctx || !t) return LCG_EINVAL;
+    *t = ctx->tuning;
     return LCG_OK;
 }
 

@@ -102,7 +102,7 @@ constexpr int kClaimBufR = 1024;  // rank rounds
 // and looked up in the global table together once the queue is half full, so
 // that full warps run the long lookup path, every few tiles.
 constexpr int kMissBuf = 256;
-constexpr int kMissFlush = 64;  // queued misses that trigger a lookup pass
+constexpr int kMissFlushDefault = 64;  // queued misses that trigger a lookup pass
 constexpr u64 kOkeyBits = 44;  // order keys are below 2^44
 
 template <typename T>
@@ -575,7 +575,8 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
             }
             __syncthreads();
             const u32 nq = s_nmiss;
-            if (nq >= (u32)kMissFlush || tile + gridDim.x >= ntiles) {
+            if (nq >= min(a.miss_flush ? a.miss_flush : (u32)kMissFlushDefault, (u32)kMissBuf) ||
+                tile + gridDim.x >= ntiles) {
                 const u32 nm = min(nq, (u32)kMissBuf);
                 for (u32 i0 = 0; i0 < nm; i0 += kParseThreads) {  // whole warps take each step
                     const u32 i = i0 + tid;
@@ -1012,7 +1013,7 @@ cudaError_t launch_tile_strings(const RoundArgs& a, cudaStream_t st) {
 }
 
 template <typename T>
-static unsigned persistent_grid(u64 tiles) {
+static int parse_occupancy(int* sms_out) {
     static int occ = 0, sms = 0;
     if (occ == 0) {
         int dev = 0;
@@ -1021,8 +1022,22 @@ static unsigned persistent_grid(u64 tiles) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_parse<T>, kParseThreads, 0);
         if (occ <= 0) occ = 1;
     }
-    const u64 g = (u64)occ * (u64)sms;
+    if (sms_out) *sms_out = sms;
+    return occ;
+}
+
+// Persistent grid: `per_sm` blocks per SM (0 or more than fit: as many as fit).
+template <typename T>
+static unsigned persistent_grid(u64 tiles, u32 per_sm) {
+    int sms = 0;
+    const int occ = parse_occupancy<T>(&sms);
+    const u64 b = (per_sm == 0 || per_sm > (u32)occ) ? (u64)occ : (u64)per_sm;
+    const u64 g = b * (u64)sms;
     return (unsigned)(tiles < g ? (tiles ? tiles : 1) : g);
+}
+
+int parse_max_blocks(int sym_bytes) {
+    return sym_bytes == 1 ? parse_occupancy<unsigned char>(nullptr) : parse_occupancy<u32>(nullptr);
 }
 
 template <typename T>
@@ -1048,8 +1063,10 @@ cudaError_t launch_breaks(const RoundArgs& a, cudaStream_t st) {
 
 cudaError_t launch_parse(const RoundArgs& a, cudaStream_t st) {
     const u64 tiles = a.tiles_bound;
-    if (a.sym_bytes == 1) k_parse<unsigned char><<<persistent_grid<unsigned char>(tiles), kParseThreads, 0, st>>>(a, tiles);
-    else k_parse<u32><<<persistent_grid<u32>(tiles), kParseThreads, 0, st>>>(a, tiles);
+    if (a.sym_bytes == 1)
+        k_parse<unsigned char><<<persistent_grid<unsigned char>(tiles, a.parse_blocks), kParseThreads, 0, st>>>(a, tiles);
+    else
+        k_parse<u32><<<persistent_grid<u32>(tiles, a.parse_blocks), kParseThreads, 0, st>>>(a, tiles);
     return cudaGetLastError();
 }
 

@@ -23,6 +23,7 @@ _ERRORS = {
 }
 SYMBOLS = [
     "lcg_ctx_create", "lcg_ctx_destroy", "lcg_last_error", "lcg_last_build_stats", "lcg_set_kernel_timing",
+    "lcg_set_tuning", "lcg_get_tuning",
     "lcg_last_kernel_times", "lcg_build", "lcg_build_into",
     "lcg_merge", "lcg_decompress", "lcg_decompress_static", "lcg_grammar_shape", "lcg_level_size", "lcg_export_level",
     "lcg_export_start", "lcg_string_roots", "lcg_import", "lcg_packed_size", "lcg_export_packed", "lcg_import_packed",
@@ -50,6 +51,11 @@ class RoundStatsC(ctypes.Structure):
 class KernelTimeC(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_uint32), ("pad", ctypes.c_uint32),
                 ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+class TuningC(ctypes.Structure):
+    _fields_ = [("table_load", ctypes.c_double), ("parse_blocks_per_sm", ctypes.c_uint32),
+                ("miss_flush", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("pad2", ctypes.c_uint32)]
 
 
 class BuildStatsC(ctypes.Structure):
@@ -84,6 +90,8 @@ def load(build_if_missing: bool = True):
     lib.lcg_last_error.restype = ctypes.c_char_p
     lib.lcg_last_build_stats.argtypes = [P, ctypes.POINTER(BuildStatsC)]
     lib.lcg_set_kernel_timing.argtypes = [P, I]
+    lib.lcg_set_tuning.argtypes = [P, ctypes.POINTER(TuningC)]
+    lib.lcg_get_tuning.argtypes = [P, ctypes.POINTER(TuningC)]
     lib.lcg_last_kernel_times.argtypes = [P, P, U32, ctypes.POINTER(U32)]
     lib.lcg_build.argtypes = [P, P, P, U32, I, PP]
     lib.lcg_build_into.argtypes = [P, P, P, P, U32, I]
@@ -222,6 +230,24 @@ class Context:
         self._check(load().lcg_import_packed(self._h, ptr, n, ctypes.byref(h)))
         del keep
         return Grammar(self, h)
+
+    def tuning(self) -> dict:
+        """lcg_get_tuning: the launch and sizing parameters of later builds."""
+        t = TuningC()
+        self._check(load().lcg_get_tuning(self._h, ctypes.byref(t)))
+        return {"table_load": float(t.table_load), "parse_blocks_per_sm": int(t.parse_blocks_per_sm),
+                "miss_flush": int(t.miss_flush)}
+
+    def set_tuning(self, **kw) -> None:
+        """lcg_set_tuning: change some of table_load, parse_blocks_per_sm,
+        miss_flush (the others keep their values)."""
+        cur = self.tuning()
+        unknown = set(kw) - set(cur)
+        if unknown:
+            raise LCGError(-1, f"unknown tuning parameters {sorted(unknown)}")
+        cur.update(kw)
+        t = TuningC(float(cur["table_load"]), int(cur["parse_blocks_per_sm"]), int(cur["miss_flush"]), 0, 0)
+        self._check(load().lcg_set_tuning(self._h, ctypes.byref(t)))
 
     def set_kernel_timing(self, mode) -> None:
         """lcg_set_kernel_timing: 0/False off, 1/True every kernel launch,

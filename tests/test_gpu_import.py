@@ -105,3 +105,29 @@ def test_packed_form_matches_oracle_and_roundtrips(ctx, hf):
     pinned = torch.empty(buf.size + 64, dtype=torch.uint8).pin_memory()
     view = g.export_packed(pinned)
     assert np.array_equal(view.numpy(), buf)
+
+
+def test_tuning_changes_speed_not_results(hf):
+    """Builds under other launch and sizing parameters give the same grammar;
+    out-of-range parameters are refused; the autotuner leaves a valid setting."""
+    torch = pytest.importorskip("torch")
+    from paper_2411_12439_gb300 import Context, LCGError, autotune
+    ctx = Context(hf, device=0)
+    coll = li.tiny_dna_collection(base_len=150_000, k=5)
+    text = li.from_strings([li.zipf_text(np.random.default_rng(9), 120_000)])
+    want = {id(c): O.build(c, hf).export() for c in (coll, text)}
+    for tun in ({"table_load": 0.3, "parse_blocks_per_sm": 1, "miss_flush": 32},
+                {"table_load": 0.78, "parse_blocks_per_sm": 2, "miss_flush": 256},
+                {"table_load": 0.7, "parse_blocks_per_sm": 0, "miss_flush": 64}):
+        ctx.set_tuning(**tun)
+        assert ctx.tuning() == tun
+        for c in (coll, text, coll):
+            assert O.grammars_equal(ctx.build(c.data, c.offsets).export(), want[id(c)])
+    for bad in ({"table_load": 0.9}, {"miss_flush": 8}, {"parse_blocks_per_sm": 999}):
+        with pytest.raises(LCGError) as e:
+            ctx.set_tuning(**bad)
+        assert e.value.code == -1
+    d = torch.from_numpy(coll.data).cuda()
+    rep = autotune.autotune(ctx, d, coll.offsets, reps=2, sweeps=1)
+    assert rep["tuning"] == ctx.tuning() and rep["ms"] > 0 and len(rep["trials"]) > 3
+    assert O.grammars_equal(ctx.build(d, coll.offsets).export(), want[id(coll)])
