@@ -100,7 +100,9 @@ typedef struct lcg_build_stats {
     uint64_t input_bytes;
     uint32_t redone;            /* 1 when those planned rounds did not fit and the
                                    build was redone round by round */
-    uint32_t pad;
+    uint32_t graph;             /* 0: the rounds ran as launches; 1: they were captured
+                                   into the context's CUDA graph and launched; 2: the
+                                   graph captured for an earlier build was launched */
     lcg_round_stats round[64];
     double plan_slack;          /* the context's multiplier of planned buffer sizes after
                                    the call: it grows after a plan that did not fit and
@@ -148,6 +150,15 @@ typedef struct lcg_tuning {
     uint32_t pad2;
 } lcg_tuning;
 int lcg_set_tuning(lcg_ctx* ctx, const lcg_tuning* t);
+/* Run later lcg_build calls whose rounds are planned without host
+ * synchronisation as one CUDA graph (1) or as launches (0, the default).  The
+ * first build of a shape (device input buffer, string lengths, plan) captures
+ * the graph; later builds of that shape launch it, provided the grammar of the
+ * previous launch has been freed (the graph writes the grammar into its own
+ * allocations, at the same addresses every time); otherwise, and for inputs in
+ * host memory or with strings of length one, the build runs as launches.
+ * Results do not depend on it. */
+int lcg_set_graph(lcg_ctx* ctx, int enable);
 int lcg_get_tuning(const lcg_ctx* ctx, lcg_tuning* t);
 
 /* Copy up to `cap` entries of the per-kind kernel times of the last call into

@@ -2,6 +2,7 @@
 // MergeGrams, expansion and export.  Host code only orchestrates: every step
 // of the method runs in the kernels of parse.cu and grammar.cu.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -43,8 +44,14 @@ struct lcg_grammar {
     u32* c_rank = nullptr;
 };
 
+namespace {
+struct GraphBuild;
+}
+
 struct lcg_ctx {
     int device = 0;
+    bool use_graph = false;              // builds may run as a captured CUDA graph
+    GraphBuild* graph = nullptr;         // the graph of the last shape
     cudaStream_t st = nullptr;
     std::vector<lcg_grammar*> live;  // grammars created here and not yet freed
     double plan_slack = 1.0;         // multiplier of the planned buffer sizes (adaptive)
@@ -78,11 +85,13 @@ struct lcg_ctx {
     u64 launches = 0;
     // per-kernel CUDA-event timing (optional)
     int ktime = 0;  // 0 off, 1 every launch, 2 parse launches only
+    bool capturing = false;              // the stream is being captured into a graph
     struct KRec {
         const char* name;
         cudaEvent_t a, b;
         double bytes;
         u32 round;  // BuildGram round of a parse launch, else 0
+        bool graph;  // the events belong to a captured graph
     };
     std::vector<KRec> krecs;
     std::vector<cudaEvent_t> evpool;
@@ -140,8 +149,15 @@ cudaEvent_t kt_event(lcg_ctx* ctx) {
     return e;
 }
 
+// Under stream capture a plain record only marks a dependency; an external
+// record becomes an event node that the graph records at every launch.
+cudaError_t record_event(lcg_ctx* ctx, cudaEvent_t e) {
+    return ctx->capturing ? cudaEventRecordWithFlags(e, ctx->st, cudaEventRecordExternal) : cudaEventRecord(e, ctx->st);
+}
+
 void kt_reset(lcg_ctx* ctx) {
     for (auto& r : ctx->krecs) {
+        if (r.graph) continue;  // recorded by a graph's event nodes: the graph owns them
         ctx->evpool.push_back(r.a);
         ctx->evpool.push_back(r.b);
     }
@@ -153,14 +169,14 @@ void kt_reset(lcg_ctx* ctx) {
 // bytes; returns a handle for kt_end (or -1 when timing is off).
 int kt_begin(lcg_ctx* ctx, const char* name, double bytes, u32 round = 0) {
     if (ctx->ktime == 0 || (ctx->ktime == 2 && std::strcmp(name, "k_parse") != 0)) return -1;
-    lcg_ctx::KRec r{name, kt_event(ctx), kt_event(ctx), bytes, round};
-    ck(ctx, cudaEventRecord(r.a, ctx->st), "cudaEventRecord");
+    lcg_ctx::KRec r{name, kt_event(ctx), kt_event(ctx), bytes, round, false};
+    ck(ctx, record_event(ctx, r.a), "cudaEventRecord");
     ctx->krecs.push_back(r);
     return (int)ctx->krecs.size() - 1;
 }
 
 void kt_end(lcg_ctx* ctx, int h) {
-    if (h >= 0) ck(ctx, cudaEventRecord(ctx->krecs[h].b, ctx->st), "cudaEventRecord");
+    if (h >= 0) ck(ctx, record_event(ctx, ctx->krecs[h].b), "cudaEventRecord");
 }
 
 // After the call's last synchronisation: sum the times per kernel kind.
@@ -218,10 +234,21 @@ LevelHash level_hash(const lcg_ctx* ctx, u32 i) {
     return h;
 }
 
+// The planned rounds did not fit (or a graph capture had to be abandoned):
+// the build is redone round by round.
+struct Retry {};
+
+void destroy_graph(lcg_ctx* ctx);
+
 void ensure_lb(lcg_ctx* ctx, void** lb, u64* have, u64 tiles, size_t bytes) {
     if (tiles <= *have) return;
     u64 want = std::max<u64>(tiles, *have * 2);
     size_t nb = bytes / (tiles ? tiles : 1) * want;
+    // a graph being captured has its buffers sized beforehand; should one
+    // not fit, the capture is abandoned and the build runs round by round
+    if (ctx->capturing) throw Retry{};
+    // a captured graph uses the current look-back buffers: it goes with them
+    if (*lb && ctx->graph) destroy_graph(ctx);
     if (*lb) dfree(ctx, *lb);
     void* p = nullptr;
     ck(ctx, cudaMallocAsync(&p, nb, ctx->st), "cudaMallocAsync lb");
@@ -295,17 +322,23 @@ void grow_c(lcg_ctx* ctx, lcg_grammar* G, u32 need) {
     G->cap_k = cap;
 }
 
-lcg_grammar* new_grammar(lcg_ctx* ctx) {
+// A grammar with no strings yet: F^0 on the device.  `registered`: the
+// context tracks it (every grammar handed to a caller).
+lcg_grammar* new_grammar(lcg_ctx* ctx, bool registered = true) {
     lcg_grammar* G = new lcg_grammar();
     G->device = ctx->device;
     G->tag = ctx->tag;
-    G->owner = ctx;
-    ctx->live.push_back(G);
+    if (registered) {
+        G->owner = ctx;
+        ctx->live.push_back(G);
+    }
     G->F0 = dalloc<u32>(ctx, 256);
     ck(ctx, launch_h0(level_hash(ctx, 0), G->F0, ctx->st), "h0");
     ctx->launches++;
     return G;
 }
+
+void graph_grammar_freed(lcg_ctx* ctx, const lcg_grammar* G);
 
 // Release a grammar.  While its context lives, the memory goes back to the
 // pool in the order of that context's stream (later calls reuse it without a
@@ -318,6 +351,7 @@ void free_grammar_now(lcg_grammar* G) {
         auto& v = G->owner->live;
         v.erase(std::remove(v.begin(), v.end(), G), v.end());
         st = G->owner->st;
+        graph_grammar_freed(G->owner, G);
     }
     auto release = [&](void* p) {
         if (!p) return;
@@ -363,13 +397,15 @@ struct RoundInput {
     u32* sid;
     const u64* d_n;  // device values, for rounds enqueued without a sync
     const u64* d_k;
+    bool own_offsets = true;  // soff / sid are this build's to free
 };
 
-struct Retry {};
 
 void free_round_input(lcg_ctx* ctx, RoundInput& in) {
-    dfree(ctx, in.soff);
-    dfree(ctx, in.sid);
+    if (in.own_offsets) {
+        dfree(ctx, in.soff);
+        dfree(ctx, in.sid);
+    }
     if (in.S_owned) dfree(ctx, in.S_owned);
     if (in.Sf) dfree(ctx, (void*)in.Sf);
     in.soff = nullptr;
@@ -596,8 +632,11 @@ void enqueue_naming(lcg_ctx* ctx, RoundArgs& a, RoundBufs& b, double g_bytes, do
 }
 
 void next_input(lcg_ctx* ctx, RoundInput& in, RoundBufs& b) {
-    dfree(ctx, in.soff);
-    dfree(ctx, in.sid);
+    if (in.own_offsets) {
+        dfree(ctx, in.soff);
+        dfree(ctx, in.sid);
+    }
+    in.own_offsets = true;
     if (in.S_owned) dfree(ctx, in.S_owned);
     if (in.Sf) dfree(ctx, (void*)in.Sf);
     in.S = b.Tnext;
@@ -707,46 +746,86 @@ void round_sync(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32 i, bool agains
     ctx->stats.rounds = i;
 }
 
-// The rounds of a fresh build, enqueued without host synchronisation, with
-// every size planned from the context's previous build (phrases per symbol,
-// new rules per phrase, symbols per rule).  Kernels read the actual sizes from
-// the device and flag a round that outgrows its buffers.  Returns 0, or -1
-// when a round did not fit (the build must then be redone round by round);
-// `i` becomes the first round not yet run, and `in` its input.
-int rounds_async(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32& i) {
-    const u32 planned = std::min<u32>(ctx->hint_rounds, std::min<u32>(ctx->levels - 1, kMaxRounds));
-    u64 n_bound = in.n, n_est = in.n;
-    const u32 kk = in.kk;
-    std::vector<u64> g_base(planned + 1), G_base(planned + 1), caps(planned + 1);
+// Sizes of the rounds of a build enqueued without host synchronisation,
+// planned from the context's hints (new rules per phrase, phrases per symbol,
+// symbols per rule of each level) and its plan slack.
+struct RoundPlan {
+    u64 n_bound = 0, n_est = 0, cap = 0, g_alloc = 0, G_alloc = 0;
+    double P_est = 0, g_est = 0, G_est = 0;
+};
+
+// x rounded up to a step of 2^(1/4) (about 19 %): plans from slightly
+// different hints get the same buffers, so a captured graph can be reused.
+u64 bucket(u64 x) {
+    if (x <= 16) return x;
+    const int e = 63 - __builtin_clzll(x);
+    const u64 b = 1ull << e;
+    for (const double f : {1.0, 1.189207115, 1.414213562, 1.681792831, 2.0}) {
+        const u64 v = (u64)std::ceil((double)b * f);
+        if (v >= x) return v;
+    }
+    return 2 * b;
+}
+
+std::vector<RoundPlan> plan_rounds(lcg_ctx* ctx, u64 n1, u32 kk, u32 planned) {
+    std::vector<RoundPlan> v(planned + 1);
+    u64 n_bound = n1, n_est = n1;
     for (u32 r = 1; r <= planned; r++) {
+        RoundPlan& p = v[r];
+        p.n_bound = n_bound;
+        p.n_est = n_est;
+        p.P_est = ctx->p_hint[r] * (double)n_est;
+        p.g_est = ctx->ratio_hint[r] * p.P_est;
+        p.G_est = ctx->glen_hint[r] * p.g_est;
+        // slack over the estimates: 10-25 % times the context's plan slack,
+        // which grows after a plan that did not fit and shrinks while plans fit
+        const double sl = ctx->plan_slack;
+        p.cap = std::min<u64>(bucket(std::max<u64>(8192, (u64)(p.g_est * 1.1 * sl / ctx->tuning.table_load) + 1024)),
+                              kMaxRank + 1);
+        p.g_alloc = bucket((u64)(p.g_est * 1.25 * sl) + 1024);
+        p.G_alloc = bucket((u64)(p.G_est * 1.25 * sl) + 4096);
+        n_bound = n_bound / 2 + 2ull * kk + 1;  // every phrase but a string's first has length >= 2
+        n_est = (u64)p.P_est + 64;
+    }
+    return v;
+}
+
+// Rounds enqueued without host synchronisation, between their enqueueing and
+// the reading of their statuses.
+struct AsyncRounds {
+    u32 planned = 0, kk = 0;
+    std::vector<RoundPlan> plan;
+    std::vector<u64> g_base, G_base;
+};
+
+// Enqueue the planned rounds of a fresh build: every size comes from the plan;
+// kernels read the actual sizes from the device and flag a round that
+// outgrows its buffers.
+void rounds_async_enqueue(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, AsyncRounds& ar) {
+    const u32 planned = ar.planned;
+    const u32 kk = ar.kk;
+    ar.g_base.assign(planned + 1, 0);
+    ar.G_base.assign(planned + 1, 0);
+    for (u32 r = 1; r <= planned; r++) {
+        const RoundPlan& p = ar.plan[r];
         if (R->lv.size() < r) R->lv.emplace_back();
         Level& L = R->lv[r - 1];
         RoundBufs b;
-        alloc_round(ctx, b, n_bound, kk);
+        alloc_round(ctx, b, p.n_bound, kk);
         ensure_lb(ctx, &ctx->lb1, &ctx->lb1_tiles, b.tiles, lb1_bytes(b.tiles));
         RoundArgs a = round_args(ctx, R, in, b, r);
         // a round stops early when the one before it failed
         if (r > 1) a.ds_prev = ctx->ds_arr + (r - 2);
         // every rank of the level below is under its capacity
         if (r > 1) a.sym_w = rank_width(R->lv[r - 2].cap_g);
-        const double P_est = ctx->p_hint[r] * (double)n_est;
-        const double g_est = ctx->ratio_hint[r] * P_est;
-        const double G_est = ctx->glen_hint[r] * g_est;
-        // slack over the estimates: 10-25 % times the context's plan slack,
-        // which grows after a plan that did not fit and shrinks while plans fit
-        const double sl = ctx->plan_slack;
-        const u64 cap = std::min<u64>(std::max<u64>(8192, (u64)(g_est * 1.1 * sl / ctx->tuning.table_load) + 1024),
-                                      kMaxRank + 1);
-        caps[r] = cap;
-        alloc_table(ctx, b, cap);
+        alloc_table(ctx, b, p.cap);
         set_table(a, b);
-        enqueue_parse(ctx, a, n_est);
-        const u64 g_alloc = (u64)(g_est * 1.25 * sl) + 1024;
-        grow_level(ctx, L, L.g + g_alloc, L.G + (u64)(G_est * 1.25 * sl) + 4096);
+        enqueue_parse(ctx, a, p.n_est);
+        grow_level(ctx, L, L.g + p.g_alloc, L.G + p.G_alloc);
         L.rvalid = false;
-        alloc_naming(ctx, b, g_alloc);
-        g_base[r] = L.g;
-        G_base[r] = L.G;
+        alloc_naming(ctx, b, p.g_alloc);
+        ar.g_base[r] = L.g;
+        ar.G_base[r] = L.G;
         a.g_base = L.g;
         a.G_base = L.G;
         a.cap_g = L.cap_g;
@@ -754,14 +833,21 @@ int rounds_async(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32& i) {
         a.rhs = L.rhs;
         a.rhs_off = L.rhs_off;
         a.F = L.F;
-        enqueue_naming(ctx, a, b, g_est, G_est, P_est);
+        enqueue_naming(ctx, a, b, p.g_est, p.G_est, p.P_est);
         free_round(ctx, b);
         next_input(ctx, in, b);
         in.d_n = &a.rc->n_next;
         in.d_k = &a.rc->k_next;
-        n_bound = b.Pmax;
-        n_est = (u64)P_est + 64;
     }
+}
+
+// After the enqueued rounds: read their statuses and counts (one host
+// synchronisation), set the levels' sizes and the build statistics.  Returns
+// 0, or -1 when a round did not fit (the build must then be redone round by
+// round); `i` becomes the first round not yet run, and `in` its input.
+int rounds_async_finish(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, const AsyncRounds& ar, u32& i) {
+    const u32 planned = ar.planned;
+    const u32 kk = ar.kk;
     std::vector<DevStatus> st(planned);
     std::vector<RoundCounts> rc(planned);
     ck(ctx, cudaMemcpyAsync(st.data(), ctx->ds_arr, planned * sizeof(DevStatus), cudaMemcpyDeviceToHost, ctx->st),
@@ -780,7 +866,7 @@ int rounds_async(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32& i) {
         const u64 k_in = (r == 1) ? kk : rc[r - 2].k_next;
         if (k_in == 0) { used = r - 1; break; }
     }
-    while (R->lv.size() > used && R->lv.back().g == 0 && g_base.size() > R->lv.size()) {
+    while (R->lv.size() > used && R->lv.back().g == 0 && ar.g_base.size() > R->lv.size()) {
         Level& L = R->lv.back();
         if (st[R->lv.size() - 1].claims != 0) break;
         dfree(ctx, L.rhs_off);
@@ -795,13 +881,13 @@ int rounds_async(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32& i) {
         const DevStatus& s = st[r - 1];
         const RoundCounts& c = rc[r - 1];
         fail_if(ctx, L.g + s.claims > kMaxRank, LCG_EOVERFLOW, "level with 2^31 rules or more");
-        L.g = g_base[r] + s.claims;
-        L.G = G_base[r] + s.claim_len;
+        L.g = ar.g_base[r] + s.claims;
+        L.G = ar.G_base[r] + s.claim_len;
         lcg_round_stats& rs = ctx->stats.round[r - 1];
         rs.n = n;
         rs.strings = (r == 1) ? kk : rc[r - 2].k_next;
         rs.phrases = c.phrases;
-        rs.table_cap = caps[r];
+        rs.table_cap = ar.plan[r].cap;
         rs.g = s.claims;
         rs.G = s.claim_len;
         record_hints(ctx, r, n, c.phrases, s.claims, s.claim_len);
@@ -815,6 +901,245 @@ int rounds_async(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32& i) {
     in.d_k = nullptr;
     i = planned + 1;
     return 0;
+}
+
+u32 planned_rounds(const lcg_ctx* ctx) {
+    return std::min<u32>(ctx->hint_rounds, std::min<u32>(ctx->levels - 1, kMaxRounds));
+}
+
+// The rounds of a fresh build, enqueued without host synchronisation and
+// planned from the context's previous builds.
+int rounds_async(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32& i) {
+    AsyncRounds ar;
+    ar.planned = planned_rounds(ctx);
+    ar.kk = in.kk;
+    ar.plan = plan_rounds(ctx, in.n, in.kk, ar.planned);
+    rounds_async_enqueue(ctx, R, in, ar);
+    return rounds_async_finish(ctx, R, in, ar, i);
+}
+
+// ---- the rounds of a build as one CUDA graph ------------------------------
+//
+// A context's builds of one shape (the same device input buffer, string
+// lengths and plan) can run as one captured graph: the first such build
+// captures every round's allocations, memsets and launches (the planned
+// rounds, as enqueued without host synchronisation), later builds launch it.
+// The graph writes the grammar into its own allocations, which keep their
+// addresses at every launch: a launch therefore waits until the grammar of
+// the previous launch has been freed (a serving loop's build -> use -> free),
+// and otherwise the build runs as launches.  The graph resets the single-pass
+// tile counter and the look-back flags it uses; the string offsets of round 1
+// are uploaded to buffers outside the graph before each launch.
+
+struct GraphBuild {
+    // what the launches depend on
+    const unsigned char* d_in = nullptr;
+    u64 n1 = 0;
+    u32 k = 0;
+    std::vector<u64> lens;
+    std::vector<double> key;  // hints, slack, tuning, levels of the plan
+    // round-1 offsets and ids, outside the graph
+    u64* soff = nullptr;
+    u32* sid = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    lcg_grammar shape;  // host description of the grammar a launch writes
+    AsyncRounds ar;
+    u64 ctr_end = 0;    // tile counter after a launch
+    u64 launches = 0;   // kernels per launch
+    std::vector<lcg_ctx::KRec> krecs;  // timing events recorded by the graph
+    lcg_grammar* live = nullptr;       // grammar of the last launch, until freed
+};
+
+// What a graph's launches depend on besides the input: the planned buffer
+// sizes (in steps of about 19 %) and the launch parameters.
+std::vector<double> graph_key(lcg_ctx* ctx, u64 n1, u32 kk, u32 planned) {
+    std::vector<double> k{(double)planned, (double)ctx->tuning.parse_blocks_per_sm, (double)ctx->tuning.miss_flush,
+                          (double)ctx->ktime};
+    const std::vector<RoundPlan> plan = plan_rounds(ctx, n1, kk, planned);
+    for (u32 r = 1; r <= planned; r++) {
+        k.push_back((double)plan[r].cap);
+        k.push_back((double)plan[r].g_alloc);
+        k.push_back((double)plan[r].G_alloc);
+    }
+    return k;
+}
+
+void destroy_graph(lcg_ctx* ctx) {
+    GraphBuild* gb = ctx->graph;
+    if (!gb) return;
+    cudaStreamSynchronize(ctx->st);
+    if (gb->exec) cudaGraphExecDestroy(gb->exec);
+    if (gb->graph) cudaGraphDestroy(gb->graph);
+    for (auto& r : gb->krecs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    if (gb->soff) cudaFreeAsync(gb->soff, ctx->st);
+    if (gb->sid) cudaFreeAsync(gb->sid, ctx->st);
+    // a live grammar of the graph keeps its memory (freed with the grammar)
+    delete gb;
+    ctx->graph = nullptr;
+}
+
+void graph_grammar_freed(lcg_ctx* ctx, const lcg_grammar* G) {
+    if (ctx->graph && ctx->graph->live == G) ctx->graph->live = nullptr;
+}
+
+// Capture the planned rounds of a build of this shape (nothing runs yet).
+void capture_graph(lcg_ctx* ctx, const unsigned char* d_in, const std::vector<u64>& lens, u32 planned,
+                   std::vector<double> key) {
+    destroy_graph(ctx);
+    const u32 k = (u32)lens.size();
+    u64 n1 = 0;
+    for (u64 x : lens) n1 += x;
+    std::vector<RoundPlan> plan = plan_rounds(ctx, n1, k, planned);
+    // look-back buffers and timing events for every launch, made before the
+    // capture (the graph must not reallocate them)
+    u64 t1 = 1, t2 = 1;
+    for (u32 r = 1; r <= planned; r++) {
+        const RoundPlan& p = plan[r];
+        const u64 tiles = (p.n_bound + parse_tile_positions(1) - 1) / parse_tile_positions(1);
+        t1 = std::max({t1, tiles, popscan_tiles_for(tiles * parse_tile_positions(1) / 32)});
+        t2 = std::max({t2, scan2_tiles_for(tiles), scan2_tiles_for(std::max<u64>(1, p.g_alloc))});
+    }
+    ensure_lb(ctx, &ctx->lb1, &ctx->lb1_tiles, t1, lb1_bytes(t1));
+    ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, t2, scan2_lb_bytes(t2));
+    auto* gb = new GraphBuild;
+    ctx->graph = gb;
+    gb->d_in = d_in;
+    gb->k = k;
+    gb->lens = lens;
+    gb->key = std::move(key);
+    gb->n1 = n1;
+    gb->soff = dalloc<u64>(ctx, k + 1);
+    gb->sid = dalloc<u32>(ctx, k);
+    gb->ar.planned = planned;
+    gb->ar.kk = k;
+    gb->ar.plan = std::move(plan);
+    if (ctx->ktime)
+        while (ctx->evpool.size() < 24ull * planned + 8) {
+            cudaEvent_t e;
+            ck(ctx, cudaEventCreate(&e), "cudaEventCreate");
+            ctx->evpool.push_back(e);
+        }
+    sync(ctx);
+    const size_t krec0 = ctx->krecs.size();
+    const u64 launches0 = ctx->launches;
+    const u64 ctr_before = ctx->ctr_val;  // the device counter until the graph runs
+    ck(ctx, cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal), "begin capture");
+    ctx->capturing = true;
+    lcg_grammar* T = nullptr;
+    try {
+        ck(ctx, cudaMemsetAsync(ctx->ctr, 0, sizeof(u64), ctx->st), "reset tile counter");
+        ctx->ctr_val = 0;
+        ck(ctx, cudaMemsetAsync(ctx->lb1, 0, lb1_bytes(ctx->lb1_tiles), ctx->st), "reset look-back");
+        ck(ctx, cudaMemsetAsync(ctx->lb2, 0, scan2_lb_bytes(ctx->lb2_tiles), ctx->st), "reset look-back");
+        T = new_grammar(ctx, false);
+        grow_c(ctx, T, k);
+        T->k = k;
+        ck(ctx, cudaMemsetAsync(ctx->ds_arr, 0, kMaxRounds * sizeof(DevStatus), ctx->st), "reset status");
+        ck(ctx, cudaMemsetAsync(ctx->rc_arr, 0, kMaxRounds * sizeof(RoundCounts), ctx->st), "reset counts");
+        RoundInput in{};
+        in.S = d_in;
+        in.symb = 1;
+        in.n = gb->n1;
+        in.kk = k;
+        in.soff = gb->soff;
+        in.sid = gb->sid;
+        in.own_offsets = false;
+        rounds_async_enqueue(ctx, T, in, gb->ar);
+        free_round_input(ctx, in);  // the last round's outputs: the graph's own allocations
+    } catch (...) {
+        ctx->capturing = false;
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(ctx->st, &g);
+        if (g) cudaGraphDestroy(g);
+        delete T;
+        ctx->ctr_val = ctr_before;
+        destroy_graph(ctx);
+        throw;
+    }
+    ctx->capturing = false;
+    const cudaError_t e = cudaStreamEndCapture(ctx->st, &gb->graph);
+    gb->ctr_end = ctx->ctr_val;
+    ctx->ctr_val = ctr_before;
+    if (e != cudaSuccess) {
+        delete T;
+        destroy_graph(ctx);
+        ck(ctx, e, "end capture");
+    }
+    gb->shape = *T;
+    delete T;  // host object only: its device arrays are the graph's allocations
+    gb->launches = ctx->launches - launches0;
+    for (size_t x = krec0; x < ctx->krecs.size(); x++) {
+        gb->krecs.push_back(ctx->krecs[x]);
+        gb->krecs.back().graph = true;
+    }
+    ctx->krecs.resize(krec0);
+    const cudaError_t ei = cudaGraphInstantiate(&gb->exec, gb->graph, 0);
+    if (ei != cudaSuccess) {
+        destroy_graph(ctx);
+        ck(ctx, ei, "instantiate graph");
+    }
+}
+
+// A build as a launch of the context's graph (captured first when the shape
+// is new).  Returns the grammar, or nullptr when the build must run as
+// launches (the graph's last grammar is still in use); throws Retry when the
+// planned rounds did not fit.
+lcg_grammar* build_with_graph(lcg_ctx* ctx, const unsigned char* d_in, const std::vector<u64>& lens) {
+    const u32 k = (u32)lens.size();
+    const u32 planned = planned_rounds(ctx);
+    u64 n1 = 0;
+    for (u64 x : lens) n1 += x;
+    std::vector<double> key = graph_key(ctx, n1, k, planned);
+    GraphBuild* gb = ctx->graph;
+    const bool same = gb && gb->d_in == d_in && gb->lens == lens && gb->key == key;
+    if (same && gb->live) return nullptr;
+    const u32 mode = same ? 2 : 1;
+    if (!same) {
+        capture_graph(ctx, d_in, lens, planned, std::move(key));
+        gb = ctx->graph;
+    }
+    std::vector<u64> soff_h(k + 1, 0);
+    std::vector<u32> sid_h(k);
+    for (u32 j = 0; j < k; j++) {
+        soff_h[j + 1] = soff_h[j] + lens[j];
+        sid_h[j] = j;
+    }
+    ctx->stats = lcg_build_stats{};
+    ctx->stats.input_bytes = gb->n1;
+    ck(ctx, cudaMemcpyAsync(gb->soff, soff_h.data(), (k + 1) * sizeof(u64), cudaMemcpyHostToDevice, ctx->st),
+       "upload offsets");
+    ck(ctx, cudaMemcpyAsync(gb->sid, sid_h.data(), k * sizeof(u32), cudaMemcpyHostToDevice, ctx->st), "upload ids");
+    ck(ctx, cudaGraphLaunch(gb->exec, ctx->st), "graph launch");
+    ctx->ctr_val = gb->ctr_end;
+    ctx->launches += gb->launches;
+    for (const auto& r : gb->krecs) ctx->krecs.push_back(r);
+    lcg_grammar* G = new lcg_grammar(gb->shape);
+    G->owner = ctx;
+    ctx->live.push_back(G);
+    gb->live = G;
+    RoundInput in{};
+    in.n = gb->n1;
+    in.kk = k;
+    u32 i = 0;
+    int r;
+    try {
+        r = rounds_async_finish(ctx, G, in, gb->ar, i);
+    } catch (...) {
+        free_grammar_now(G);
+        throw;
+    }
+    if (r < 0 || in.kk > 0) {  // did not fit, or more rounds are needed: run as launches
+        free_grammar_now(G);
+        throw Retry{};
+    }
+    ctx->hint_rounds = ctx->stats.rounds;
+    ctx->stats.kernel_launches = gb->launches;
+    ctx->stats.graph = mode;
+    return G;
 }
 
 void build_into(lcg_ctx* ctx, lcg_grammar* R, const uint8_t* data, const uint64_t* off, uint32_t k, int on_dev,
@@ -1220,6 +1545,7 @@ void lcg_ctx_destroy(lcg_ctx* ctx) {
     if (ctx->st) cudaStreamSynchronize(ctx->st);
     for (lcg_grammar* G : ctx->live) G->owner = nullptr;  // they outlive the context
     ctx->live.clear();
+    destroy_graph(ctx);
     for (auto& r : ctx->krecs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -1249,6 +1575,13 @@ int lcg_last_build_stats(const lcg_ctx* ctx, lcg_build_stats* out) {
 int lcg_set_kernel_timing(lcg_ctx* ctx, int enable) {
     if (!ctx || enable < 0 || enable > 2) return LCG_EINVAL;
     ctx->ktime = enable;
+    return LCG_OK;
+}
+
+int lcg_set_graph(lcg_ctx* ctx, int enable) {
+    if (!ctx || enable < 0 || enable > 1) return LCG_EINVAL;
+    ctx->use_graph = enable != 0;
+    if (!ctx->use_graph) destroy_graph(ctx);
     return LCG_OK;
 }
 
@@ -1288,6 +1621,38 @@ int lcg_build(lcg_ctx* ctx, const uint8_t* data, const uint64_t* offsets, uint32
     ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
     kt_reset(ctx);
     reset_status(ctx);
+    if (ctx->use_graph && data_on_device && k > 0 && offsets && data && ctx->hint_rounds > 0) {
+        std::vector<u64> lens(k);
+        bool ok = true;
+        for (u32 j = 0; j < k && ok; j++) {
+            lens[j] = offsets[j + 1] - offsets[j];
+            ok = offsets[j + 1] > offsets[j] && lens[j] >= 2;  // strings of length one: not in graphs
+        }
+        if (ok) {
+            try {
+                G = build_with_graph(ctx, data + offsets[0], lens);
+            } catch (const Retry&) {
+                ctx->plan_slack = std::min(4.0, ctx->plan_slack * 1.6);
+                G = nullptr;
+                kt_reset(ctx);
+                G = new_grammar(ctx);
+                build_into(ctx, G, data, offsets, k, data_on_device, false, false);
+                ctx->stats.redone = 1;
+                ctx->stats.plan_slack = ctx->plan_slack;
+                sync(ctx);
+                kt_collect(ctx);
+                *out = G;
+                return LCG_OK;
+            }
+            if (G) {
+                ctx->plan_slack = std::max(1.0, ctx->plan_slack * 0.97);
+                ctx->stats.plan_slack = ctx->plan_slack;
+                kt_collect(ctx);
+                *out = G;
+                return LCG_OK;
+            }
+        }
+    }
     G = new_grammar(ctx);
     try {
         build_into(ctx, G, data, offsets, k, data_on_device, false, true);

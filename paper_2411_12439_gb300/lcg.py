@@ -23,7 +23,7 @@ _ERRORS = {
 }
 SYMBOLS = [
     "lcg_ctx_create", "lcg_ctx_destroy", "lcg_last_error", "lcg_last_build_stats", "lcg_set_kernel_timing",
-    "lcg_set_tuning", "lcg_get_tuning",
+    "lcg_set_tuning", "lcg_get_tuning", "lcg_set_graph",
     "lcg_last_kernel_times", "lcg_build", "lcg_build_into",
     "lcg_merge", "lcg_decompress", "lcg_decompress_static", "lcg_grammar_shape", "lcg_level_size", "lcg_export_level",
     "lcg_export_start", "lcg_string_roots", "lcg_import", "lcg_packed_size", "lcg_export_packed", "lcg_import_packed",
@@ -60,7 +60,7 @@ class TuningC(ctypes.Structure):
 
 class BuildStatsC(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_uint32), ("async_rounds", ctypes.c_uint32), ("kernel_launches", ctypes.c_uint64),
-                ("input_bytes", ctypes.c_uint64), ("redone", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+                ("input_bytes", ctypes.c_uint64), ("redone", ctypes.c_uint32), ("graph", ctypes.c_uint32),
                 ("round", RoundStatsC * 64), ("plan_slack", ctypes.c_double)]
 
 
@@ -92,6 +92,7 @@ def load(build_if_missing: bool = True):
     lib.lcg_set_kernel_timing.argtypes = [P, I]
     lib.lcg_set_tuning.argtypes = [P, ctypes.POINTER(TuningC)]
     lib.lcg_get_tuning.argtypes = [P, ctypes.POINTER(TuningC)]
+    lib.lcg_set_graph.argtypes = [P, I]
     lib.lcg_last_kernel_times.argtypes = [P, P, U32, ctypes.POINTER(U32)]
     lib.lcg_build.argtypes = [P, P, P, U32, I, PP]
     lib.lcg_build_into.argtypes = [P, P, P, P, U32, I]
@@ -249,6 +250,11 @@ class Context:
         t = TuningC(float(cur["table_load"]), int(cur["parse_blocks_per_sm"]), int(cur["miss_flush"]), 0, 0)
         self._check(load().lcg_set_tuning(self._h, ctypes.byref(t)))
 
+    def set_graph(self, enable: bool) -> None:
+        """lcg_set_graph: run later builds of a repeated shape as one captured
+        CUDA graph."""
+        self._check(load().lcg_set_graph(self._h, int(bool(enable))))
+
     def set_kernel_timing(self, mode) -> None:
         """lcg_set_kernel_timing: 0/False off, 1/True every kernel launch,
         2 only the parse launches."""
@@ -269,6 +275,7 @@ class Context:
                                                                 "retries")}, "parse_ms": float(st.round[i].parse_ms)}
                   for i in range(min(st.rounds, 64))]
         return {"rounds": int(st.rounds), "async_rounds": int(st.async_rounds), "redone": bool(st.redone),
+                "graph": int(st.graph),
                 "plan_slack": float(st.plan_slack),
                 "kernel_launches": int(st.kernel_launches),
                 "input_bytes": int(st.input_bytes), "per_round": rounds}

@@ -1,0 +1,68 @@
+"""Builds as one captured CUDA graph (lcg_set_graph): the first build of a
+shape captures the rounds, later builds of that shape launch the graph once
+the previous grammar is freed; a build while it is still alive, or of another
+shape, runs as launches or captures anew.  Every grammar equals the oracle's."""
+import numpy as np
+import pytest
+
+import lcg_inputs as li
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+def test_graph_capture_replay_and_fallback(hf):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_12439_gb300 import Context
+    ctx = Context(hf, device=0)
+    ctx.set_graph(True)
+    a = li.tiny_dna_collection(base_len=200_000, k=6)
+    b = li.from_strings([li.zipf_text(np.random.default_rng(5), 300_000), li.random_dna(np.random.default_rng(6), 9000)])
+    want = {"a": O.build(a, hf).export(), "b": O.build(b, hf).export()}
+    da, db = torch.from_numpy(a.data).cuda(), torch.from_numpy(b.data).cuda()
+
+    def build(d, c):
+        g = ctx.build(d, c.offsets)
+        return g, ctx.last_build_stats()["graph"]
+
+    g, mode = build(da, a)  # no plan yet: launches
+    assert mode == 0 and O.grammars_equal(g.export(), want["a"])
+    g.free()
+    modes = []
+    for _ in range(3):
+        g, mode = build(da, a)
+        modes.append(mode)
+        assert O.grammars_equal(g.export(), want["a"])
+        g.free()
+    assert modes[0] == 1 and modes[-1] == 2  # captured, then launched
+    g1, m1 = build(da, a)
+    g2, m2 = build(da, a)  # the graph's grammar g1 is alive: launches
+    assert m1 == 2 and m2 == 0
+    assert O.grammars_equal(g1.export(), want["a"]) and O.grammars_equal(g2.export(), want["a"])
+    g1.free()
+    g2.free()
+    for _ in range(3):  # another shape
+        g, mode = build(db, b)
+        assert O.grammars_equal(g.export(), want["b"])
+        g.free()
+    ctx.set_graph(False)
+    g, mode = build(da, a)
+    assert mode == 0 and O.grammars_equal(g.export(), want["a"])
+    g.free()
+    # the parse launches' timing events are part of the graph
+    ctx2 = Context(hf, device=0)
+    ctx2.set_graph(True)
+    ctx2.set_kernel_timing(2)
+    modes = []
+    for _ in range(4):
+        g = ctx2.build(da, a.offsets)
+        st = ctx2.last_build_stats()
+        modes.append(st["graph"])
+        assert O.grammars_equal(g.export(), want["a"])
+        kt = ctx2.last_kernel_times()
+        # planned rounds past the last one launch and find no active string
+        assert kt["k_parse"]["launches"] >= st["rounds"] and kt["k_parse"]["ms"] > 0
+        g.free()
+    assert modes == [0, 1, 2, 2]
