@@ -14,8 +14,9 @@ import numpy as np
 
 CANDIDATES = {
     "parse_blocks_per_sm": [0, 2, 3, 4],
-    "table_load": [0.5, 0.6, 0.7, 0.75],
+    "table_load": [0.4, 0.5, 0.6, 0.7],
     "miss_flush": [32, 64, 128],
+    "parse_ilp": [1, 2],
 }
 
 

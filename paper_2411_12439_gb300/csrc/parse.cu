@@ -295,8 +295,11 @@ __global__ void __launch_bounds__(kBrkThreads) k_breaks(const RoundArgs a, u64 n
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse(const RoundArgs a, u64 ntiles) {
+// ILP: phrases a thread looks up at once in rank rounds (their first table
+// reads in flight together); byte rounds take 1.
+template <typename T, int ILP>
+__global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4)
+    k_parse(const RoundArgs a, u64 ntiles) {
     constexpr int NWS = kSP / 32;    // staged break words
     constexpr int NWT = kTP / 32;    // tile break words
     constexpr bool kByte = sizeof(T) == 1;
@@ -604,7 +607,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                 __syncthreads();
                 if (tid == 0) s_nmiss = 0;
             }
-        } else {
+        } else if (ILP == 1 || rt.cap) {
             for (u32 q0 = 0; q0 < cntq; q0 += kParseThreads) {  // whole warps take each step
                 const u32 q = q0 + tid;
                 bool claimed = false;
@@ -617,6 +620,50 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                     __stcs(a.P_slot + okey0 + q, slot);
                 }
                 claim_warp(claimed, slot, len);
+            }
+        } else {
+            // ILP phrases per thread: keys and first reads of their home slots
+            // first, then each lookup goes on from its first read
+            for (u32 q0 = 0; q0 < cntq; q0 += kParseThreads * ILP) {  // whole warps take each step
+                Key128 key[ILP], cur[ILP];
+                u64 home[ILP], len[ILP];
+                bool ok[ILP];
+#pragma unroll
+                for (int u = 0; u < ILP; u++) {
+                    const u32 q = q0 + (u32)(u * kParseThreads + tid);
+                    ok[u] = false;
+                    len[u] = 0;
+                    home[u] = 0;
+                    if (q < cntq) {
+                        const u64 st = sP[q], en = phrase_end(q);
+                        len[u] = en - st;
+                        key[u] = make_key(st, en, &ok[u]);
+                        if (ok[u]) {
+                            home[u] = key_home(key[u], bt.cap);
+                            cur[u] = ld_key_relaxed(&bt.slots[home[u]].key);
+                        } else {
+                            __stcs(a.P_slot + okey0 + q, ~0u);  // too long: the round fails
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < ILP; u++) {
+                    const u32 q = q0 + (u32)(u * kParseThreads + tid);
+                    bool claimed = false;
+                    u32 slot = ~0u;
+                    if (ok[u]) {
+                        const u64 pos = key[u].lo, n_sym = len[u];
+                        slot = (u32)table_claim_or_find_at(bt, key[u], key_is_hashed(key[u]), okey0 + q,
+                                                           [&](u64 ref) {
+                                                               for (u64 j = 0; j < n_sym; j++)
+                                                                   if (S[ref + j] != S[pos + j]) return false;
+                                                               return true;
+                                                           },
+                                                           &claimed, a.ds, home[u], cur[u]);
+                        __stcs(a.P_slot + okey0 + q, slot);
+                    }
+                    claim_warp(claimed, slot, len[u]);
+                }
             }
         }
         __syncthreads();
@@ -765,22 +812,42 @@ __global__ void __launch_bounds__(kPopThreads) k_popscan(const RoundArgs a, u64 
     nw = min(nw, *a.d_tiles * (u64)(kTP / 32));
     if (tile > 0 && tile * (u64)kPopTile >= nw) return;  // beyond the count read on the device
     const u64 w0 = tile * (u64)kPopTile + (u64)threadIdx.x * kPopItems;
+    static_assert(kPopItems == 8, "two 16-byte words per thread");
+    // a thread's 8 words start at a multiple of 32 bytes of the arrays
+    const bool full = w0 + kPopItems <= nw && ((reinterpret_cast<unsigned long long>(a.first_bits) |
+                                                 reinterpret_cast<unsigned long long>(a.first_prefix)) & 15) == 0;
     u32 c[kPopItems];
+    if (full) {
+        const uint4 x0 = reinterpret_cast<const uint4*>(a.first_bits + w0)[0];
+        const uint4 x1 = reinterpret_cast<const uint4*>(a.first_bits + w0)[1];
+        c[0] = __popc(x0.x), c[1] = __popc(x0.y), c[2] = __popc(x0.z), c[3] = __popc(x0.w);
+        c[4] = __popc(x1.x), c[5] = __popc(x1.y), c[6] = __popc(x1.z), c[7] = __popc(x1.w);
+    } else {
+#pragma unroll
+        for (int it = 0; it < kPopItems; it++) c[it] = (w0 + it < nw) ? (u32)__popc(a.first_bits[w0 + it]) : 0u;
+    }
     u64 sum = 0;
 #pragma unroll
-    for (int it = 0; it < kPopItems; it++) {
-        c[it] = (w0 + it < nw) ? (u32)__popc(a.first_bits[w0 + it]) : 0u;
-        sum += c[it];
-    }
+    for (int it = 0; it < kPopItems; it++) sum += c[it];
     u64 tot;
     u64 e = block_excl_scan(sum, tot);
     u64 agg[1] = {tot}, excl[1];
     block_lookback<1>((LBSlot<1>*)a.lb1, tile, a.epoch, agg, excl, a.ds);
     e += excl[0];
+    u32 o[kPopItems];
 #pragma unroll
     for (int it = 0; it < kPopItems; it++) {
-        if (w0 + it < nw) a.first_prefix[w0 + it] = (u32)e;
+        o[it] = (u32)e;
         e += c[it];
+    }
+    if (full) {
+        uint4* dst = reinterpret_cast<uint4*>(a.first_prefix + w0);
+        dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+        dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+    } else {
+#pragma unroll
+        for (int it = 0; it < kPopItems; it++)
+            if (w0 + it < nw) a.first_prefix[w0 + it] = o[it];
     }
 }
 
@@ -868,18 +935,21 @@ __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) 
     ntiles = min(ntiles, *a.d_tiles);
     // ranks of the level after this round (never past its arrays)
     const u64 g_total = min(a.g_base + *a.d_gnew, a.cap_g);
-    for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    // one tile per warp: the tile's header reads and its first phrase reads
+    // of every warp of the SM are in flight together
+    const u32 lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+    for (u64 t = (u64)blockIdx.x * warps + (threadIdx.x >> 5); t < ntiles; t += (u64)gridDim.x * warps) {
         const u32 cnt = a.tile_cnt[t];
         const u64 pbase = a.tile_pfx[t];
         const u32* ps = a.P_slot + t * (u64)kTP;
         // kRwUnroll phrases per thread at a time: their table reads are issued
         // together
-        for (u32 q0 = threadIdx.x; q0 < cnt; q0 += kRwUnroll * blockDim.x) {
+        for (u32 q0 = lane; q0 < cnt; q0 += kRwUnroll * 32) {
             u32 s[kRwUnroll], r[kRwUnroll], f[kRwUnroll];
             bool need[kRwUnroll];
 #pragma unroll
             for (int u = 0; u < kRwUnroll; u++) {
-                const u32 q = q0 + (u32)u * blockDim.x;
+                const u32 q = q0 + (u32)u * 32;
                 s[u] = q < cnt ? __ldcs(ps + q) : ~0u;
             }
 #pragma unroll
@@ -921,7 +991,7 @@ __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) 
             }
 #pragma unroll
             for (int u = 0; u < kRwUnroll; u++) {
-                const u32 q = q0 + (u32)u * blockDim.x;
+                const u32 q = q0 + (u32)u * 32;
                 if (q >= cnt) continue;
                 u32 rr = r[u];
                 if (rr >= g_total) {  // an entry that got no rank: only after a capacity error
@@ -1012,14 +1082,14 @@ cudaError_t launch_tile_strings(const RoundArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, int ILP>
 static int parse_occupancy(int* sms_out) {
     static int occ = 0, sms = 0;
     if (occ == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_parse<T>, kParseThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_parse<T, ILP>, kParseThreads, 0);
         if (occ <= 0) occ = 1;
     }
     if (sms_out) *sms_out = sms;
@@ -1027,17 +1097,18 @@ static int parse_occupancy(int* sms_out) {
 }
 
 // Persistent grid: `per_sm` blocks per SM (0 or more than fit: as many as fit).
-template <typename T>
+template <typename T, int ILP>
 static unsigned persistent_grid(u64 tiles, u32 per_sm) {
     int sms = 0;
-    const int occ = parse_occupancy<T>(&sms);
+    const int occ = parse_occupancy<T, ILP>(&sms);
     const u64 b = (per_sm == 0 || per_sm > (u32)occ) ? (u64)occ : (u64)per_sm;
     const u64 g = b * (u64)sms;
     return (unsigned)(tiles < g ? (tiles ? tiles : 1) : g);
 }
 
-int parse_max_blocks(int sym_bytes) {
-    return sym_bytes == 1 ? parse_occupancy<unsigned char>(nullptr) : parse_occupancy<u32>(nullptr);
+int parse_max_blocks(int sym_bytes, int ilp) {
+    if (sym_bytes == 1) return parse_occupancy<unsigned char, 1>(nullptr);
+    return ilp == 2 ? parse_occupancy<u32, 2>(nullptr) : parse_occupancy<u32, 1>(nullptr);
 }
 
 template <typename T>
@@ -1064,9 +1135,12 @@ cudaError_t launch_breaks(const RoundArgs& a, cudaStream_t st) {
 cudaError_t launch_parse(const RoundArgs& a, cudaStream_t st) {
     const u64 tiles = a.tiles_bound;
     if (a.sym_bytes == 1)
-        k_parse<unsigned char><<<persistent_grid<unsigned char>(tiles, a.parse_blocks), kParseThreads, 0, st>>>(a, tiles);
+        k_parse<unsigned char, 1>
+            <<<persistent_grid<unsigned char, 1>(tiles, a.parse_blocks), kParseThreads, 0, st>>>(a, tiles);
+    else if (a.parse_ilp == 2)
+        k_parse<u32, 2><<<persistent_grid<u32, 2>(tiles, a.parse_blocks), kParseThreads, 0, st>>>(a, tiles);
     else
-        k_parse<u32><<<persistent_grid<u32>(tiles, a.parse_blocks), kParseThreads, 0, st>>>(a, tiles);
+        k_parse<u32, 1><<<persistent_grid<u32, 1>(tiles, a.parse_blocks), kParseThreads, 0, st>>>(a, tiles);
     return cudaGetLastError();
 }
 
@@ -1100,7 +1174,8 @@ cudaError_t launch_rules(const RoundArgs& a, u64 g_grid, cudaStream_t st) {
 
 cudaError_t launch_rewrite(const RoundArgs& a, cudaStream_t st) {
     const u64 tiles = a.tiles_bound;
-    const u64 g = tiles < 152ull * 8 ? (tiles ? tiles : 1) : 152ull * 8;
+    const u64 blocks = (tiles + 7) / 8;  // 8 warps per block, one tile each
+    const u64 g = blocks < 152ull * 8 ? (blocks ? blocks : 1) : 152ull * 8;
     k_rewrite<<<(unsigned)g, 256, 0, st>>>(a, tiles);
     return cudaGetLastError();
 }
