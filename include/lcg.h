@@ -140,17 +140,14 @@ int lcg_set_kernel_timing(lcg_ctx* ctx, int enable);
  *                       (0.3 .. 0.78; a table past 0.8 is regrown and the round rerun);
  *   parse_blocks_per_sm resident k_parse blocks per SM, 0 = as many as fit;
  *   miss_flush          byte rounds: queued cache misses that trigger a lookup pass
- *                       (32 .. 256);
- *   parse_ilp           rank rounds: phrases a k_parse thread looks up at once
- *                       (1 or 2; with 2 the first table reads of both are in
- *                       flight together).
- * Defaults: 0.5, 0, 64, 1.  Out-of-range values give LCG_EINVAL. */
+ *                       (32 .. 256).
+ * Defaults: 0.5, 0, 64.  Out-of-range values give LCG_EINVAL. */
 typedef struct lcg_tuning {
     double table_load;
     uint32_t parse_blocks_per_sm;
     uint32_t miss_flush;
-    uint32_t parse_ilp;
     uint32_t pad;
+    uint32_t pad2;
 } lcg_tuning;
 int lcg_set_tuning(lcg_ctx* ctx, const lcg_tuning* t);
 /* Run later lcg_build calls whose rounds are planned without host

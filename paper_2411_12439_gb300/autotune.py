@@ -16,7 +16,6 @@ CANDIDATES = {
     "parse_blocks_per_sm": [0, 2, 3, 4],
     "table_load": [0.4, 0.5, 0.6, 0.7],
     "miss_flush": [32, 64, 128],
-    "parse_ilp": [1, 2],
 }
 
 

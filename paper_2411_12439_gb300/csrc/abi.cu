@@ -55,7 +55,7 @@ struct lcg_ctx {
     cudaStream_t st = nullptr;
     std::vector<lcg_grammar*> live;  // grammars created here and not yet freed
     double plan_slack = 1.0;         // multiplier of the planned buffer sizes (adaptive)
-    lcg_tuning tuning{0.5, 0, 64, 1, 0};  // table load, k_parse blocks per SM, miss flush, rank-round ILP
+    lcg_tuning tuning{0.5, 0, 64, 0, 0};  // table load, k_parse blocks per SM, miss flush
     bool own_stream = false;
     std::vector<u64> a, b, c;
     u32 levels = 0, m_bits = 32;
@@ -524,7 +524,6 @@ RoundArgs round_args(lcg_ctx* ctx, lcg_grammar* R, const RoundInput& in, RoundBu
     a.level = i;
     a.parse_blocks = ctx->tuning.parse_blocks_per_sm;
     a.miss_flush = ctx->tuning.miss_flush;
-    a.parse_ilp = ctx->tuning.parse_ilp;
     a.tiles_bound = b.tiles;
     a.string_first = b.string_first;
     a.tile_str = b.tile_str;
@@ -956,7 +955,6 @@ struct GraphBuild {
 // sizes (in steps of about 19 %) and the launch parameters.
 std::vector<double> graph_key(lcg_ctx* ctx, u64 n1, u32 kk, u32 planned) {
     std::vector<double> k{(double)planned, (double)ctx->tuning.parse_blocks_per_sm, (double)ctx->tuning.miss_flush,
-                          (double)ctx->tuning.parse_ilp,
                           (double)ctx->ktime};
     const std::vector<RoundPlan> plan = plan_rounds(ctx, n1, kk, planned);
     for (u32 r = 1; r <= planned; r++) {
@@ -1594,16 +1592,16 @@ int lcg_set_graph(lcg_ctx* ctx, int enable) {
 
 int lcg_set_tuning(lcg_ctx* ctx, const lcg_tuning* t) {
     if (!ctx || !t) return LCG_EINVAL;
-    const int ilp = t->parse_ilp;
-    const int maxb = (ilp == 1 || ilp == 2) ? std::max(parse_max_blocks(1, 1), parse_max_blocks(4, ilp)) : 0;
-    if (!(t->table_load >= 0.3 && t->table_load <= 0.78) || (ilp != 1 && ilp != 2) ||
-        t->parse_blocks_per_sm > (uint32_t)maxb || t->miss_flush < 32 || t->miss_flush > 256) {
-        ctx->err = "tuning out of range: table_load in [0.3, 0.78], parse_ilp 1 or 2, parse_blocks_per_sm <= " +
-                   std::to_string(maxb) + ", miss_flush in [32, 256]";
+    const int maxb = std::max(parse_max_blocks(1), parse_max_blocks(4));
+    if (!(t->table_load >= 0.3 && t->table_load <= 0.78) || t->parse_blocks_per_sm > (uint32_t)maxb ||
+        t->miss_flush < 32 || t->miss_flush > 256) {
+        ctx->err = "tuning out of range: table_load in [0.3, 0.78], parse_blocks_per_sm <= " + std::to_string(maxb) +
+                   ", miss_flush in [32, 256]";
         return LCG_EINVAL;
     }
     ctx->tuning = *t;
     ctx->tuning.pad = 0;
+    ctx->tuning.pad2 = 0;
     return LCG_OK;
 }
 

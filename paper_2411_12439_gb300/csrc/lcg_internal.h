@@ -36,7 +36,6 @@ struct RoundArgs {
     u32 level;            // i
     u32 parse_blocks;     // resident k_parse blocks per SM (0: as many as fit)
     u32 miss_flush;       // byte rounds: queued cache misses that trigger a lookup pass
-    u32 parse_ilp;        // rank rounds: phrases a k_parse thread looks up at once (1 or 2)
     // parse pass
     u64 tiles_bound;      // parse tiles the buffers were sized for
     u64* d_tiles;         // parse tiles of the round (written by k_tile_strings)
@@ -105,7 +104,7 @@ size_t slot_bytes();  // bytes of one phrase-table slot
 cudaError_t launch_tile_strings(const RoundArgs& a, cudaStream_t st);
 cudaError_t launch_breaks(const RoundArgs& a, cudaStream_t st);
 cudaError_t launch_parse(const RoundArgs& a, cudaStream_t st);
-int parse_max_blocks(int sym_bytes, int ilp);  // resident k_parse blocks per SM at most
+int parse_max_blocks(int sym_bytes);  // resident k_parse blocks per SM at most
 cudaError_t launch_strings(const RoundArgs& a, cudaStream_t st);
 cudaError_t launch_mark(const RoundArgs& a, u64 g_grid, cudaStream_t st);
 cudaError_t launch_popscan(const RoundArgs& a, u64 nw_bound, cudaStream_t st);

@@ -94,10 +94,12 @@ constexpr int kCacheBits = 11;
 constexpr int kCacheSlots = 1 << kCacheBits;  // per-block phrase cache (byte rounds)
 constexpr int kCacheProbes = 8;
 // New table entries of a block are listed in shared memory and appended to
-// the round's claim list once the buffer is half full (and after the block's
-// last tile), so that the global counter is touched every few tiles only.
+// the round's claim list once the buffer is half full, or in rank rounds once
+// another tile could overflow it (a tile claims at most kTP entries), and
+// after the block's last tile, so that the global counter is touched every
+// few tiles only.
 constexpr int kClaimBufB = 512;   // byte rounds (shared memory also holds the phrase cache)
-constexpr int kClaimBufR = 1024;  // rank rounds
+constexpr int kClaimBufR = 4096;  // rank rounds
 // Byte rounds: phrases that miss the block's cache are queued with their keys
 // and looked up in the global table together once the queue is half full, so
 // that full warps run the long lookup path, every few tiles.
@@ -295,11 +297,33 @@ __global__ void __launch_bounds__(kBrkThreads) k_breaks(const RoundArgs a, u64 n
     }
 }
 
-// ILP: phrases a thread looks up at once in rank rounds (their first table
-// reads in flight together); byte rounds take 1.
-template <typename T, int ILP>
-__global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4)
-    k_parse(const RoundArgs a, u64 ntiles) {
+// Exclusive scan of one 32-bit value per thread of a kParseThreads block, with
+// one barrier: every warp scans the warp totals itself.  `s_wsum` (one word
+// per warp) must not be written again before all threads have returned.
+__device__ __forceinline__ u32 block_scan32(u32 x, u32& total, u32* s_wsum) {
+    constexpr int NW = kParseThreads / 32;
+    const u32 lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    u32 incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += y;
+    }
+    if (lane == 31) s_wsum[wid] = incl;
+    __syncthreads();
+    const u32 w = lane < (u32)NW ? s_wsum[lane] : 0u;
+    u32 wi = w;
+#pragma unroll
+    for (int o = 1; o < NW; o <<= 1) {
+        const u32 y = __shfl_up_sync(0xffffffffu, wi, o);
+        if ((int)lane >= o) wi += y;
+    }
+    total = __shfl_sync(0xffffffffu, wi, NW - 1);
+    return __shfl_sync(0xffffffffu, wi - w, wid) + incl - x;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse(const RoundArgs a, u64 ntiles) {
     constexpr int NWS = kSP / 32;    // staged break words
     constexpr int NWT = kTP / 32;    // tile break words
     constexpr bool kByte = sizeof(T) == 1;
@@ -318,6 +342,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4)
     __shared__ u64 ckey[kLocal ? kCacheSlots : 1];
     __shared__ u32 cval[kLocal ? kCacheSlots : 1];
     __shared__ u32 sClaim[kClaimBuf];
+    __shared__ u32 s_wsum[kParseThreads / 32];
     // byte rounds: queued cache misses: key, and order key | (cache slot + 1) << kOkeyBits
     __shared__ Key128 sMissKey[kLocal ? kMissBuf : 1];
     __shared__ u64 sMissOk[kLocal ? kMissBuf : 1];
@@ -356,25 +381,56 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4)
 
     // persistent blocks: tiles blockIdx.x, blockIdx.x + gridDim.x, ...  Tiles
     // do not depend on one another.
+    // Byte rounds: a tile's bytes (16 per thread), break words and string
+    // index are read into registers while the block parses the tile before it.
+    static_assert(!kByte || (kSP + 15) / 16 <= kParseThreads, "one 16-byte load per thread");
+    static_assert(NWS <= kParseThreads, "one break word per thread");
+    uint4 pf_sym = make_uint4(0u, 0u, 0u, 0u);
+    u32 pf_bits = 0, pf_j0 = 0;
+    auto fetch = [&](u64 tl) {
+        const u64 f0 = tl * (u64)kTP;
+        const int fns = (int)(min(f0 + (u64)kSP, n) - f0);
+        const int x0 = tid * 16;
+        const unsigned char* src = (const unsigned char*)S + f0;
+        if (x0 + 16 <= fns && (reinterpret_cast<unsigned long long>(src) & 15) == 0) {
+            pf_sym = __ldcs(reinterpret_cast<const uint4*>(src + x0));  // streamed once: evict first
+        } else if (x0 < fns) {
+            unsigned char tmp[16];
+#pragma unroll
+            for (int e = 0; e < 16; e++) tmp[e] = (x0 + e < fns) ? src[x0 + e] : (unsigned char)0;
+            pf_sym = *reinterpret_cast<const uint4*>(tmp);
+        }
+        const u64 gw = f0 / 32 + (u64)tid;
+        pf_bits = (tid < NWS && gw < nwords) ? __ldg(a.brk + gw) : 0u;
+        pf_j0 = a.tile_str[tl];
+    };
+
     u64 iter = 0;
     for (u64 tile = blockIdx.x; tile < ntiles; tile += gridDim.x, iter++) {
         if ((iter & 15) == 0 && round_halted(a)) break;
         const u64 t0 = tile * (u64)kTP;
         const u64 t_end = min(t0 + (u64)kTP, n), s_end = min(t0 + (u64)kSP, n);
         const int ns = (int)(s_end - t0), nt = (int)(t_end - t0);
-        const u32 j0 = a.tile_str[tile];  // string holding t0
 
         // 1. stage the tile's symbols (bytes in round 1, ranks afterwards) and
         //    its break words (k_breaks)
+        u32 j0;  // string holding t0
         if constexpr (kByte) {
-            stage_vec<unsigned char>(sb, S + t0, ns, (reinterpret_cast<unsigned long long>(S + t0) & 15) == 0);
+            if (iter == 0) fetch(tile);
+            if (tid * 16 < ns) *reinterpret_cast<uint4*>(sb + tid * 16) = pf_sym;
+            if (tid < NWS) sbits[tid] = pf_bits;
+            j0 = pf_j0;
+            if (tile + gridDim.x < ntiles) fetch(tile + gridDim.x);
         } else {
+            j0 = a.tile_str[tile];
             stage_vec<u32>(sT, S + t0, ns, (reinterpret_cast<unsigned long long>(S + t0) & 15) == 0);
+            for (int w = tid; w < NWS; w += kParseThreads) {
+                const u64 gw = t0 / 32 + (u64)w;
+                sbits[w] = gw < nwords ? __ldg(a.brk + gw) : 0u;
+            }
         }
-        for (int w = tid; w < NWS; w += kParseThreads) {
-            const u64 gw = t0 / 32 + (u64)w;
-            sbits[w] = gw < nwords ? __ldg(a.brk + gw) : 0u;
-        }
+        // offsets of the strings from j0 on, for step 5 (read now, used at the tile's end)
+        const u64 s_first = (warp == 0 && j0 + lane < kact) ? __ldg(a.soff + j0 + lane) : ~0ull;
         __syncthreads();
 
         // 3. phrase starts of the tile, in order: four threads per break word,
@@ -385,8 +441,8 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4)
         if (wq * 32 >= nt) word = 0;
         else if (nt - wq * 32 < 32) word &= (1u << (nt - wq * 32)) - 1u;
         const u32 part = (word >> bq) & 0xFFu;
-        u64 cnt;
-        const u64 poff = block_excl_scan((u64)__popc(part), cnt);
+        u32 cnt;
+        const u32 poff = block_scan32((u32)__popc(part), cnt, s_wsum);
         if ((tid & 3) == 0) swp[wq] = (u32)poff;
         {
             u32 m = part, o = (u32)poff;
@@ -607,7 +663,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4)
                 __syncthreads();
                 if (tid == 0) s_nmiss = 0;
             }
-        } else if (ILP == 1 || rt.cap) {
+        } else {
             for (u32 q0 = 0; q0 < cntq; q0 += kParseThreads) {  // whole warps take each step
                 const u32 q = q0 + tid;
                 bool claimed = false;
@@ -621,50 +677,6 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4)
                 }
                 claim_warp(claimed, slot, len);
             }
-        } else {
-            // ILP phrases per thread: keys and first reads of their home slots
-            // first, then each lookup goes on from its first read
-            for (u32 q0 = 0; q0 < cntq; q0 += kParseThreads * ILP) {  // whole warps take each step
-                Key128 key[ILP], cur[ILP];
-                u64 home[ILP], len[ILP];
-                bool ok[ILP];
-#pragma unroll
-                for (int u = 0; u < ILP; u++) {
-                    const u32 q = q0 + (u32)(u * kParseThreads + tid);
-                    ok[u] = false;
-                    len[u] = 0;
-                    home[u] = 0;
-                    if (q < cntq) {
-                        const u64 st = sP[q], en = phrase_end(q);
-                        len[u] = en - st;
-                        key[u] = make_key(st, en, &ok[u]);
-                        if (ok[u]) {
-                            home[u] = key_home(key[u], bt.cap);
-                            cur[u] = ld_key_relaxed(&bt.slots[home[u]].key);
-                        } else {
-                            __stcs(a.P_slot + okey0 + q, ~0u);  // too long: the round fails
-                        }
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < ILP; u++) {
-                    const u32 q = q0 + (u32)(u * kParseThreads + tid);
-                    bool claimed = false;
-                    u32 slot = ~0u;
-                    if (ok[u]) {
-                        const u64 pos = key[u].lo, n_sym = len[u];
-                        slot = (u32)table_claim_or_find_at(bt, key[u], key_is_hashed(key[u]), okey0 + q,
-                                                           [&](u64 ref) {
-                                                               for (u64 j = 0; j < n_sym; j++)
-                                                                   if (S[ref + j] != S[pos + j]) return false;
-                                                               return true;
-                                                           },
-                                                           &claimed, a.ds, home[u], cur[u]);
-                        __stcs(a.P_slot + okey0 + q, slot);
-                    }
-                    claim_warp(claimed, slot, len[u]);
-                }
-            }
         }
         __syncthreads();
 
@@ -673,7 +685,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4)
         if (tid == 0) a.tile_cnt[tile] = cntq;
         if (warp == 0) {
             for (u32 jj = j0 + lane;; jj += 32) {
-                const u64 s = (jj < kact) ? __ldg(a.soff + jj) : ~0ull;
+                const u64 s = (jj == j0 + lane) ? s_first : (jj < kact) ? __ldg(a.soff + jj) : ~0ull;
                 if (s >= t0 && s < t_end) {
                     const int x = (int)(s - t0);
                     a.string_first[jj] = okey0 + swp[x >> 5] + __popc(sbits[x >> 5] & ((1u << (x & 31)) - 1u));
@@ -684,7 +696,9 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4)
         // 6. the block's new entries join the round's claim list when the
         //    buffer is half full, and after the block's last tile
         const u32 ncl = s_nclaim;
-        if (ncl >= (u32)kClaimBuf / 2 || tile + gridDim.x >= ntiles) {
+        constexpr u32 kFlushAt = kByte ? (u32)kClaimBuf / 2 : (u32)(kClaimBuf - kTP);
+        static_assert(kByte || kClaimBufR >= 2 * kTP, "a rank-round tile never overflows the buffer");
+        if (ncl >= kFlushAt || tile + gridDim.x >= ntiles) {
             const u32 nb = min(ncl, (u32)kClaimBuf);
             if (tid == 0 && ncl) {
                 const u64 base = atomicAdd(&a.ds->claims, (u64)nb);
@@ -1082,14 +1096,14 @@ cudaError_t launch_tile_strings(const RoundArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <typename T, int ILP>
+template <typename T>
 static int parse_occupancy(int* sms_out) {
     static int occ = 0, sms = 0;
     if (occ == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_parse<T, ILP>, kParseThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_parse<T>, kParseThreads, 0);
         if (occ <= 0) occ = 1;
     }
     if (sms_out) *sms_out = sms;
@@ -1097,18 +1111,17 @@ static int parse_occupancy(int* sms_out) {
 }
 
 // Persistent grid: `per_sm` blocks per SM (0 or more than fit: as many as fit).
-template <typename T, int ILP>
+template <typename T>
 static unsigned persistent_grid(u64 tiles, u32 per_sm) {
     int sms = 0;
-    const int occ = parse_occupancy<T, ILP>(&sms);
+    const int occ = parse_occupancy<T>(&sms);
     const u64 b = (per_sm == 0 || per_sm > (u32)occ) ? (u64)occ : (u64)per_sm;
     const u64 g = b * (u64)sms;
     return (unsigned)(tiles < g ? (tiles ? tiles : 1) : g);
 }
 
-int parse_max_blocks(int sym_bytes, int ilp) {
-    if (sym_bytes == 1) return parse_occupancy<unsigned char, 1>(nullptr);
-    return ilp == 2 ? parse_occupancy<u32, 2>(nullptr) : parse_occupancy<u32, 1>(nullptr);
+int parse_max_blocks(int sym_bytes) {
+    return sym_bytes == 1 ? parse_occupancy<unsigned char>(nullptr) : parse_occupancy<u32>(nullptr);
 }
 
 template <typename T>
@@ -1135,12 +1148,9 @@ cudaError_t launch_breaks(const RoundArgs& a, cudaStream_t st) {
 cudaError_t launch_parse(const RoundArgs& a, cudaStream_t st) {
     const u64 tiles = a.tiles_bound;
     if (a.sym_bytes == 1)
-        k_parse<unsigned char, 1>
-            <<<persistent_grid<unsigned char, 1>(tiles, a.parse_blocks), kParseThreads, 0, st>>>(a, tiles);
-    else if (a.parse_ilp == 2)
-        k_parse<u32, 2><<<persistent_grid<u32, 2>(tiles, a.parse_blocks), kParseThreads, 0, st>>>(a, tiles);
+        k_parse<unsigned char><<<persistent_grid<unsigned char>(tiles, a.parse_blocks), kParseThreads, 0, st>>>(a, tiles);
     else
-        k_parse<u32, 1><<<persistent_grid<u32, 1>(tiles, a.parse_blocks), kParseThreads, 0, st>>>(a, tiles);
+        k_parse<u32><<<persistent_grid<u32>(tiles, a.parse_blocks), kParseThreads, 0, st>>>(a, tiles);
     return cudaGetLastError();
 }
 

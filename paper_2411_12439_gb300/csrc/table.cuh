@@ -137,22 +137,18 @@ constexpr u64 kMaxProbes = 4096;
 // the slot and sets *claimed when this call claimed it, or ~0 when the table
 // is over its load limit or full, or the probe sequence reached kMaxProbes
 // (the host then regrows the table and reruns).
-//
-// table_claim_or_find_at starts from the key `cur` already read at slot `s`
-// (the key's home), so that a thread can have the first reads of several
-// lookups in flight at once.
 template <typename Same>
-__device__ u64 table_claim_or_find_at(ContentTable t, const Key128& k, bool hashed, u64 pidx, Same same,
-                                      bool* claimed, DevStatus* ds, u64 s, Key128 cur) {
+__device__ u64 table_claim_or_find(ContentTable t, const Key128& k, bool hashed, u64 pidx, Same same, bool* claimed,
+                                   DevStatus* ds) {
+    u64 s = key_home(k, t.cap);
     const Key128 empty{~0ull, ~0ull};
     const u64 limit = t.cap < kMaxProbes ? t.cap : kMaxProbes;
     for (u64 probe = 0; probe < limit; probe++) {
         // once the table is over its load limit the pass is rerun: stop early
         if ((probe & 63) == 63 && vload(&ds->overflow)) return ~0ull;
         Key128* kp = &t.slots[s].key;
-        if (probe) cur = ld_key_relaxed(kp);
+        Key128 cur = ld_key_relaxed(kp);
         if (cur.hi == kEmptyHi) {
-            if (vload(&ds->overflow)) return ~0ull;
             const Key128 old = cas_key(kp, empty, k);
             if (old.hi == kEmptyHi) {
                 *claimed = true;
@@ -173,13 +169,6 @@ __device__ u64 table_claim_or_find_at(ContentTable t, const Key128& k, bool hash
     }
     atomicExch(&ds->overflow, 1u);
     return ~0ull;
-}
-
-template <typename Same>
-__device__ __forceinline__ u64 table_claim_or_find(ContentTable t, const Key128& k, bool hashed, u64 pidx, Same same,
-                                                   bool* claimed, DevStatus* ds) {
-    const u64 s = key_home(k, t.cap);
-    return table_claim_or_find_at(t, k, hashed, pidx, same, claimed, ds, s, ld_key_relaxed(&t.slots[s].key));
 }
 
 // Look a key up in a table that nobody writes during the call.  `same(lo)`

@@ -55,7 +55,7 @@ class KernelTimeC(ctypes.Structure):
 
 class TuningC(ctypes.Structure):
     _fields_ = [("table_load", ctypes.c_double), ("parse_blocks_per_sm", ctypes.c_uint32),
-                ("miss_flush", ctypes.c_uint32), ("parse_ilp", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+                ("miss_flush", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("pad2", ctypes.c_uint32)]
 
 
 class BuildStatsC(ctypes.Structure):
@@ -237,18 +237,17 @@ class Context:
         t = TuningC()
         self._check(load().lcg_get_tuning(self._h, ctypes.byref(t)))
         return {"table_load": float(t.table_load), "parse_blocks_per_sm": int(t.parse_blocks_per_sm),
-                "miss_flush": int(t.miss_flush), "parse_ilp": int(t.parse_ilp)}
+                "miss_flush": int(t.miss_flush)}
 
     def set_tuning(self, **kw) -> None:
         """lcg_set_tuning: change some of table_load, parse_blocks_per_sm,
-        miss_flush, parse_ilp (the others keep their values)."""
+        miss_flush (the others keep their values)."""
         cur = self.tuning()
         unknown = set(kw) - set(cur)
         if unknown:
             raise LCGError(-1, f"unknown tuning parameters {sorted(unknown)}")
         cur.update(kw)
-        t = TuningC(float(cur["table_load"]), int(cur["parse_blocks_per_sm"]), int(cur["miss_flush"]),
-                    int(cur["parse_ilp"]), 0)
+        t = TuningC(float(cur["table_load"]), int(cur["parse_blocks_per_sm"]), int(cur["miss_flush"]), 0, 0)
         self._check(load().lcg_set_tuning(self._h, ctypes.byref(t)))
 
     def set_graph(self, enable: bool) -> None:
