@@ -106,6 +106,14 @@ constexpr int kClaimBufR = 4096;  // rank rounds
 constexpr int kMissBuf = 256;
 constexpr int kMissFlushDefault = 64;  // queued misses that trigger a lookup pass
 constexpr u64 kOkeyBits = 44;  // order keys are below 2^44
+// Rank rounds read this many table slots per round trip (byte rounds look up
+// few, mostly cached phrases, and read one).
+constexpr int kProbeGroup = 2;
+// Long phrases (hashed keys) in rank rounds: fingerprints read per round
+// trip for H, and symbols per round trip when a match is confirmed by content
+// (byte rounds read staged fingerprints and take one at a time).
+constexpr int kHornerBatchR = 8;
+constexpr int kCompareBatchR = 4;
 
 template <typename T>
 __device__ u64 scan_right_diff(const T* S, FpSource<T> fp, u64 from, u64 strend, u32 val) {
@@ -330,6 +338,8 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
     constexpr bool kLocal = kByte;
     static_assert(NWT <= kParseThreads, "one tile word per thread");
     constexpr int kClaimBuf = kByte ? kClaimBufB : kClaimBufR;
+    constexpr int kHornerBatch = kByte ? 1 : kHornerBatchR;
+    constexpr int kCompareBatch = kByte ? 1 : kCompareBatchR;
 
     __shared__ u32 sF0[kByte ? 256 : 1];
     __shared__ __align__(16) unsigned char sb[kByte ? kSP : 16];  // bytes of tile positions
@@ -494,9 +504,27 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                 return Key128{0, 0};
             }
             if (len > inline_max(a.sym_w)) {
-                // H = sum_j F[Q_j] c^{j-1} mod p, by Horner from the last symbol
+                // H = sum_j F[Q_j] c^{j-1} mod p, by Horner from the last symbol;
+                // the fingerprints (staged F^0 of bytes, or the round's
+                // fingerprint stream) are read kHornerBatch at a time
                 u64 H = 0;
-                for (u64 x = en; x-- > st;) H = addmod61(mulmod61(H, a.lh.c), (u64)fp(sym(x)));
+                for (u64 x = en; x > st;) {
+                    const u64 c = min((u64)kHornerBatch, x - st);
+                    u32 f[kHornerBatch];
+#pragma unroll
+                    for (int u = 0; u < kHornerBatch; u++) {
+                        if ((u64)u < c) {
+                            if constexpr (kByte) f[u] = fp((unsigned char)sym(x - 1 - u));
+                            else f[u] = __ldg(a.Sf + t0 + x - 1 - u);
+                        } else {
+                            f[u] = 0;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kHornerBatch; u++)
+                        if ((u64)u < c) H = addmod61(mulmod61(H, a.lh.c), (u64)f[u]);
+                    x -= c;
+                }
                 return key_hashed(H, len, t0 + st);
             }
             return key_inline([&](u64 j) { return sym(st + j); }, len, a.sym_w);
@@ -516,9 +544,20 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                 });
                 if (r != ~0ull) return kResidentBit | (u32)r;
             }
-            return (u32)table_claim_or_find(bt, key, hashed, okey, [&](u64 ref) {
-                for (u64 j = 0; j < len; j++)
-                    if (S[ref + j] != S[pos + j]) return false;
+            return (u32)table_claim_or_find<kByte ? 1 : kProbeGroup>(bt, key, hashed, okey, [&](u64 ref) {
+                // both contents in global memory, kCompareBatch symbols per round trip
+                for (u64 j = 0; j < len; j += kCompareBatch) {
+                    T x[kCompareBatch], y[kCompareBatch];
+#pragma unroll
+                    for (int u = 0; u < kCompareBatch; u++) {
+                        const bool in = j + u < len;
+                        x[u] = in ? S[ref + j + u] : (T)0;
+                        y[u] = in ? S[pos + j + u] : (T)0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kCompareBatch; u++)
+                        if (x[u] != y[u]) return false;
+                }
                 return true;
             }, claimed, a.ds);
         };

@@ -130,42 +130,62 @@ __device__ __forceinline__ Key128 cas_key(Key128* p, Key128 cmp, Key128 val) {
 // Longest probe sequence of a claim: far beyond what a table under its load
 // limit shows, so reaching it means the table is (nearly) full.
 constexpr u64 kMaxProbes = 4096;
+// Slots read together (G, a power of two up to 4: at most one 128-byte line):
+// the rest of the home slot's group of G, then whole groups.  A warp waits for
+// its longest probe sequence, and a group costs one round trip instead of one
+// per slot.
 
 // Find or claim the slot of key k in a table that other threads are filling.
 // `same(ref)` compares the content stored at `ref` with the phrase (hashed keys
 // only).  The slot's value is lowered to `pidx` (first occurrence).  Returns
 // the slot and sets *claimed when this call claimed it, or ~0 when the table
 // is over its load limit or full, or the probe sequence reached kMaxProbes
-// (the host then regrows the table and reruns).
-template <typename Same>
+// (the host then regrows the table and reruns).  Slots are examined in probe
+// order, and a new key goes into the first empty one: a slot read as empty may
+// have been claimed since (the compare-and-swap then returns its key), but one
+// read as taken stays so, as keys are never removed.
+template <int G, typename Same>
 __device__ u64 table_claim_or_find(ContentTable t, const Key128& k, bool hashed, u64 pidx, Same same, bool* claimed,
                                    DevStatus* ds) {
+    static_assert(G == 1 || G == 2 || G == 4, "groups of 1, 2 or 4 slots");
     u64 s = key_home(k, t.cap);
     const Key128 empty{~0ull, ~0ull};
     const u64 limit = t.cap < kMaxProbes ? t.cap : kMaxProbes;
-    for (u64 probe = 0; probe < limit; probe++) {
+    u32 groups = 0;
+    for (u64 probe = 0; probe < limit;) {
         // once the table is over its load limit the pass is rerun: stop early
-        if ((probe & 63) == 63 && vload(&ds->overflow)) return ~0ull;
-        Key128* kp = &t.slots[s].key;
-        Key128 cur = ld_key_relaxed(kp);
-        if (cur.hi == kEmptyHi) {
-            const Key128 old = cas_key(kp, empty, k);
-            if (old.hi == kEmptyHi) {
-                *claimed = true;
-                atomicMin(&t.slots[s].val, pidx);
-                return s;
+        if ((++groups & 15) == 0 && vload(&ds->overflow)) return ~0ull;
+        const u64 gend = min((s | (u64)(G - 1)) + 1, t.cap);
+        const int m = (int)min(gend - s, limit - probe);
+        Key128 c[G];
+#pragma unroll
+        for (int j = 0; j < G; j++)
+            if (j < m) c[j] = ld_key_relaxed(&t.slots[s + j].key);
+#pragma unroll
+        for (int j = 0; j < G; j++) {
+            if (j >= m) break;
+            Key128* kp = &t.slots[s + j].key;
+            Key128 cur = c[j];
+            if (cur.hi == kEmptyHi) {
+                const Key128 old = cas_key(kp, empty, k);
+                if (old.hi == kEmptyHi) {
+                    *claimed = true;
+                    atomicMin(&t.slots[s + j].val, pidx);
+                    return s + j;
+                }
+                cur = old;
             }
-            cur = old;
-        }
-        if (cur.hi == k.hi) {
-            // a pair read while being written shows the empty low half: read it again atomically
-            if (cur.lo == ~0ull) cur = cas_key(kp, empty, empty);
-            if (hashed ? same(cur.lo) : (cur.lo == k.lo)) {
-                atomicMin(&t.slots[s].val, pidx);
-                return s;
+            if (cur.hi == k.hi) {
+                // a pair read while being written shows the empty low half: read it again atomically
+                if (cur.lo == ~0ull) cur = cas_key(kp, empty, empty);
+                if (hashed ? same(cur.lo) : (cur.lo == k.lo)) {
+                    atomicMin(&t.slots[s + j].val, pidx);
+                    return s + j;
+                }
             }
         }
-        s = (s + 1 == t.cap) ? 0 : s + 1;
+        probe += (u64)m;
+        s = (gend == t.cap) ? 0 : gend;
     }
     atomicExch(&ds->overflow, 1u);
     return ~0ull;
