@@ -7,12 +7,27 @@
 namespace lcg {
 
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 4;
+constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 // --------------------------------------------------------------------------
 // exclusive scan of two uint32 columns into uint64 (single pass)
 // --------------------------------------------------------------------------
+
+// kScanItems consecutive values of a column from p0 (16-byte loads when the
+// whole run is inside the column and aligned), zero past n or for no column.
+__device__ __forceinline__ void scan_load(const u32* in, u64 p0, u64 n, u32 (&v)[kScanItems]) {
+    if (in != nullptr && p0 + kScanItems <= n && (reinterpret_cast<unsigned long long>(in + p0) & 15) == 0) {
+#pragma unroll
+        for (int q = 0; q < kScanItems / 4; q++) {
+            const uint4 x = reinterpret_cast<const uint4*>(in + p0)[q];
+            v[4 * q] = x.x, v[4 * q + 1] = x.y, v[4 * q + 2] = x.z, v[4 * q + 3] = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int it = 0; it < kScanItems; it++) v[it] = (in != nullptr && p0 + it < n) ? in[p0 + it] : 0u;
+    }
+}
 
 __global__ void __launch_bounds__(kScanThreads) k_scan2(const u32* __restrict__ in0, const u32* __restrict__ in1,
                                                         u64 n, u64* __restrict__ out0, u64* __restrict__ out1,
@@ -23,12 +38,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan2(const u32* __restrict__ 
     if (tile > 0 && tile * (u64)kScanTile >= n) return;  // beyond the count read on the device
     const u64 p0 = tile * (u64)kScanTile + (u64)threadIdx.x * kScanItems;
     u32 a[kScanItems], b[kScanItems];
+    scan_load(in0, p0, n, a);
+    scan_load(in1, p0, n, b);
     u64 sa = 0, sb = 0;
 #pragma unroll
     for (int it = 0; it < kScanItems; it++) {
-        const u64 p = p0 + it;
-        a[it] = (p < n) ? in0[p] : 0u;
-        b[it] = (p < n && in1 != nullptr) ? in1[p] : 0u;
         sa += a[it];
         sb += b[it];
     }

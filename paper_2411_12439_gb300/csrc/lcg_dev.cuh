@@ -84,7 +84,7 @@ __device__ __forceinline__ void set_error(DevStatus* st, u32 code) {
 __device__ __forceinline__ u32 vload(const volatile u32* p) { return *p; }
 __device__ __forceinline__ u64 vload(const volatile u64* p) { return *p; }
 
-constexpr u64 kSpinLimit = 1ull << 22;  // bounded waits: a few seconds at most
+constexpr u64 kSpinLimit = 1ull << 22;  // bounded waits: about a second at most
 
 // Empty marker of 64-bit keys in shared-memory caches.
 constexpr u64 kEmpty = ~0ull;
@@ -142,14 +142,15 @@ __device__ void lookback_finish(LBSlot<NV>* st, u64 tile, u64 epoch, const u64 (
                 u32 state = 2;  // virtual tiles before 0: inclusive, value 0
                 if (idx >= 0) {
                     u64 it = 0;
-                    u32 backoff = 32;
+                    u32 backoff = 16;
                     while (true) {
                         const u64 f = vs[idx].flag;
                         if ((f >> 2) == epoch && (f & 3) != 0) { state = (u32)(f & 3); break; }
                         if (++it > kSpinLimit || vload(&ds->error) != 0) { state = 0; break; }
-                        // back off so that waiting warps leave issue slots to working ones
+                        // back off so that waiting warps leave issue slots to working
+                        // ones, but not so far that a ready predecessor waits long
                         __nanosleep(backoff);
-                        if (backoff < 1024) backoff <<= 1;
+                        if (backoff < 256) backoff <<= 1;
                     }
                 }
                 if (__any_sync(0xffffffffu, state == 0)) { failed = true; break; }

@@ -856,7 +856,7 @@ __global__ void k_mark(const RoundArgs a) {
 }
 
 constexpr int kPopThreads = 256;
-constexpr int kPopItems = 8;
+constexpr int kPopItems = 16;
 constexpr int kPopTile = kPopThreads * kPopItems;
 
 // Exclusive prefix of the popcounts of the bitmap words (single pass).
@@ -865,16 +865,17 @@ __global__ void __launch_bounds__(kPopThreads) k_popscan(const RoundArgs a, u64 
     nw = min(nw, *a.d_tiles * (u64)(kTP / 32));
     if (tile > 0 && tile * (u64)kPopTile >= nw) return;  // beyond the count read on the device
     const u64 w0 = tile * (u64)kPopTile + (u64)threadIdx.x * kPopItems;
-    static_assert(kPopItems == 8, "two 16-byte words per thread");
-    // a thread's 8 words start at a multiple of 32 bytes of the arrays
+    static_assert(kPopItems % 4 == 0, "16-byte words");
+    // a thread's words start at a multiple of 64 bytes of the arrays
     const bool full = w0 + kPopItems <= nw && ((reinterpret_cast<unsigned long long>(a.first_bits) |
                                                  reinterpret_cast<unsigned long long>(a.first_prefix)) & 15) == 0;
     u32 c[kPopItems];
     if (full) {
-        const uint4 x0 = reinterpret_cast<const uint4*>(a.first_bits + w0)[0];
-        const uint4 x1 = reinterpret_cast<const uint4*>(a.first_bits + w0)[1];
-        c[0] = __popc(x0.x), c[1] = __popc(x0.y), c[2] = __popc(x0.z), c[3] = __popc(x0.w);
-        c[4] = __popc(x1.x), c[5] = __popc(x1.y), c[6] = __popc(x1.z), c[7] = __popc(x1.w);
+#pragma unroll
+        for (int q = 0; q < kPopItems / 4; q++) {
+            const uint4 x = reinterpret_cast<const uint4*>(a.first_bits + w0)[q];
+            c[4 * q] = __popc(x.x), c[4 * q + 1] = __popc(x.y), c[4 * q + 2] = __popc(x.z), c[4 * q + 3] = __popc(x.w);
+        }
     } else {
 #pragma unroll
         for (int it = 0; it < kPopItems; it++) c[it] = (w0 + it < nw) ? (u32)__popc(a.first_bits[w0 + it]) : 0u;
@@ -895,8 +896,8 @@ __global__ void __launch_bounds__(kPopThreads) k_popscan(const RoundArgs a, u64 
     }
     if (full) {
         uint4* dst = reinterpret_cast<uint4*>(a.first_prefix + w0);
-        dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
-        dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+#pragma unroll
+        for (int q = 0; q < kPopItems / 4; q++) dst[q] = make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
     } else {
 #pragma unroll
         for (int it = 0; it < kPopItems; it++)
