@@ -968,27 +968,20 @@ __global__ void k_rules(const RoundArgs a) {
 // k_rewrite: T^{i+1} and retired strings
 // --------------------------------------------------------------------------
 
-constexpr int kRankCache = 1024;
 constexpr int kRwUnroll = 4;
 
 // T^{i+1}[p] = rank of phrase p and f^{i+1}[p] = its fingerprint F^i[rank]
 // (so that the next round reads fingerprints without gathers).  Strings that
-// became one phrase take their C entry instead.
+// became one phrase take their C entry instead.  The (fingerprint, rank) pair
+// of a slot comes from the dense array k_rules wrote (read-only here: small
+// and cached in L1 in early rounds, in L2 after its writes later on).
 __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) {
-    // per-block cache of slot -> (rank, fingerprint): in repetitive rounds a
-    // few entries take most phrases.  Both words carry the slot as a tag.
-    __shared__ u64 c_rank[kRankCache];
-    __shared__ u64 c_fp[kRankCache];
     if (round_halted(a)) return;
-    for (int x = threadIdx.x; x < kRankCache; x += blockDim.x) {
-        c_rank[x] = ~0ull;
-        c_fp[x] = ~0ull;
-    }
-    __syncthreads();
     const u64 nr = a.rc->retired;
     ntiles = min(ntiles, *a.d_tiles);
     // ranks of the level after this round (never past its arrays)
     const u64 g_total = min(a.g_base + *a.d_gnew, a.cap_g);
+    const u64* __restrict__ rv = a.rv;
     // one tile per warp: the tile's header reads and its first phrase reads
     // of every warp of the SM are in flight together
     const u32 lane = threadIdx.x & 31, warps = blockDim.x >> 5;
@@ -996,11 +989,10 @@ __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) 
         const u32 cnt = a.tile_cnt[t];
         const u64 pbase = a.tile_pfx[t];
         const u32* ps = a.P_slot + t * (u64)kTP;
-        // kRwUnroll phrases per thread at a time: their table reads are issued
-        // together
+        // kRwUnroll phrases per thread at a time: their reads are issued together
         for (u32 q0 = lane; q0 < cnt; q0 += kRwUnroll * 32) {
-            u32 s[kRwUnroll], r[kRwUnroll], f[kRwUnroll];
-            bool need[kRwUnroll];
+            u32 s[kRwUnroll];
+            u64 v[kRwUnroll];
 #pragma unroll
             for (int u = 0; u < kRwUnroll; u++) {
                 const u32 q = q0 + (u32)u * 32;
@@ -1008,46 +1000,20 @@ __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) 
             }
 #pragma unroll
             for (int u = 0; u < kRwUnroll; u++) {
-                need[u] = false;
-                r[u] = 0;
-                f[u] = 0;
-                if (s[u] == ~0u) continue;  // no phrase, or the round's table overflowed
-                if (s[u] & kResidentBit) {
-                    r[u] = s[u] & ~kResidentBit;
-                    need[u] = true;
+                if (s[u] == ~0u) {
+                    v[u] = 0;  // no phrase, or the round's table overflowed
+                } else if (s[u] & kResidentBit) {
+                    const u32 r = s[u] & ~kResidentBit;
+                    v[u] = ((u64)__ldg(a.F + r) << 32) | r;
                 } else {
-                    const u32 ci = s[u] & (kRankCache - 1);
-                    const u64 er = c_rank[ci], ef = c_fp[ci];
-                    if ((u32)(er >> 32) == s[u] && (u32)(ef >> 32) == s[u]) {
-                        r[u] = (u32)er;
-                        f[u] = (u32)ef;
-                    } else {
-                        need[u] = true;
-                    }
-                }
-            }
-            u64 v[kRwUnroll];
-#pragma unroll
-            for (int u = 0; u < kRwUnroll; u++)
-                v[u] = !need[u] ? 0ull : (s[u] & kResidentBit) ? (u64)__ldg(a.F + r[u]) << 32 : a.rv[s[u]];
-#pragma unroll
-            for (int u = 0; u < kRwUnroll; u++) {
-                if (!need[u]) continue;
-                if (s[u] & kResidentBit) {
-                    f[u] = (u32)(v[u] >> 32);
-                } else {
-                    r[u] = (u32)v[u];
-                    f[u] = (u32)(v[u] >> 32);
-                    const u32 ci = s[u] & (kRankCache - 1);
-                    c_rank[ci] = ((u64)s[u] << 32) | r[u];
-                    c_fp[ci] = ((u64)s[u] << 32) | f[u];
+                    v[u] = __ldg(rv + s[u]);
                 }
             }
 #pragma unroll
             for (int u = 0; u < kRwUnroll; u++) {
                 const u32 q = q0 + (u32)u * 32;
                 if (q >= cnt) continue;
-                u32 rr = r[u];
+                u32 rr = (u32)v[u];
                 if (rr >= g_total) {  // an entry that got no rank: only after a capacity error
                     set_error(a.ds, kErrCapacity);
                     rr = 0;
@@ -1072,7 +1038,7 @@ __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) 
                     continue;
                 }
                 __stcs(a.Tnext + out, rr);
-                __stcs(a.Fnext + out, f[u]);
+                __stcs(a.Fnext + out, (u32)(v[u] >> 32));
             }
         }
     }
