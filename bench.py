@@ -12,7 +12,9 @@ the public API from pinned host memory, with the grammar copied back to the
 host every step; ``roofline`` rates the kernel with the largest device time
 against the measured HBM bandwidth; ``cpu_baseline`` times the CPU oracle on a
 bounded sample of the same workload; ``plain`` is the one-string-at-a-time form
-(each string parsed against the growing resident grammar).
+(each string parsed against the growing resident grammar); ``rounds`` gives per
+round the symbols parsed, the device time of all its kernels and the GB/s of
+its sequence (1-byte symbols in round 1, 4-byte ranks afterwards).
 """
 from __future__ import annotations
 
@@ -358,8 +360,16 @@ def run_ours(args):
     ctx.set_graph(False)
     ctx.set_kernel_timing(1)
     breakdown = {}
+    per_round = None
     for _ in range(max(1, min(args.steps, 5))):
         ctx.build(d, coll.offsets).free()
+        rs = ctx.last_build_stats()["per_round"]
+        if per_round is None or len(per_round) != len(rs):
+            per_round = [{"symbols": r["n"], "bytes_per_symbol": 1 if i == 0 else 4, "ms": [], "parse_ms": []}
+                         for i, r in enumerate(rs)]
+        for pr, r in zip(per_round, rs):
+            pr["ms"].append(r["round_ms"])
+            pr["parse_ms"].append(r["parse_ms"])
         for name, v in ctx.last_kernel_times().items():
             acc = breakdown.setdefault(name, {"launches": 0, "ms": 0.0, "builds": 0})
             acc["launches"] += v["launches"]
@@ -368,6 +378,12 @@ def run_ours(args):
             acc["builds"] += 1
     ctx.set_kernel_timing(0)
     value = world * coll.n / (ms / 1e3) / 1e9
+    rounds_line = []
+    for i, pr in enumerate(per_round or []):
+        rms = float(np.median(pr["ms"]))
+        rounds_line.append({"round": i + 1, "symbols": int(pr["symbols"]), "ms": rms,
+                            "parse_ms": float(np.median(pr["parse_ms"])),
+                            "gbs": pr["symbols"] * pr["bytes_per_symbol"] / (rms / 1e3) / 1e9 if rms > 0 else None})
 
     # ---- end to end through the public API: pinned host input, the whole
     #      grammar to a pinned host buffer in its packed form every step
@@ -446,6 +462,7 @@ def run_ours(args):
                    "parallelism": f"dp{world}" if world > 1 else "single GPU"},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roofline,
         "cpu_baseline": cpu, "plain": plain, "serving": serving_line,
+        "rounds": rounds_line,
         "kernels": {k: {"launches": v["launches"] // v["builds"], "ms_per_step": v["ms"] / v["builds"]}
                     for k, v in sorted(breakdown.items(), key=lambda kv: -kv[1]["ms"])},
     }

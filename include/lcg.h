@@ -90,6 +90,8 @@ typedef struct lcg_round_stats {
     uint32_t retries;    /* table regrowths in round i */
     uint32_t pad;
     double parse_ms;     /* device time of the round's k_parse launches (kernel timing on) */
+    double round_ms;     /* device time of all the round's kernel launches (kernel timing
+                            mode 1; with mode 2 only k_parse is timed) */
 } lcg_round_stats;
 
 typedef struct lcg_build_stats {

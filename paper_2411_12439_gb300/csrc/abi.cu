@@ -197,7 +197,11 @@ void kt_collect(lcg_ctx* ctx) {
         t->launches++;
         t->ms += ms;
         t->bytes += r.bytes;
-        if (r.round >= 1 && r.round <= 64) ctx->stats.round[r.round - 1].parse_ms += ms;
+        if (r.round >= 1 && r.round <= 64) {
+            lcg_round_stats& rs = ctx->stats.round[r.round - 1];
+            rs.round_ms += ms;
+            if (std::strcmp(r.name, "k_parse") == 0) rs.parse_ms += ms;
+        }
     }
 }
 
@@ -562,8 +566,10 @@ void set_table(RoundArgs& a, RoundBufs& b) {
 
 // Parse: tile strings, k_parse, tile scan, strings.
 void enqueue_parse(lcg_ctx* ctx, RoundArgs& a, u64 n_for_bytes) {
+    int ht = kt_begin(ctx, "k_tile_strings", 4.0 * (double)a.tiles_bound, a.level);
     ck(ctx, launch_tile_strings(a, ctx->st), "k_tile_strings");
-    int hb = kt_begin(ctx, "k_breaks", (a.sym_bytes == 1 ? 1.0 : 4.0) * n_for_bytes + (double)n_for_bytes / 8.0);
+    kt_end(ctx, ht);
+    int hb = kt_begin(ctx, "k_breaks", (a.sym_bytes == 1 ? 1.0 : 4.0) * n_for_bytes + (double)n_for_bytes / 8.0, a.level);
     ck(ctx, launch_breaks(a, ctx->st), "k_breaks");
     kt_end(ctx, hb);
     const double tab_bytes = a.tab_cap * (double)slot_bytes();
@@ -576,13 +582,13 @@ void enqueue_parse(lcg_ctx* ctx, RoundArgs& a, u64 n_for_bytes) {
     const u64 stiles = std::max<u64>(1, scan2_tiles_for(a.tiles_bound));
     ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, stiles, scan2_lb_bytes(stiles));
     u64 grid = 0;
-    h = kt_begin(ctx, "k_scan2", 12.0 * (double)a.tiles_bound);
+    h = kt_begin(ctx, "k_scan2", 12.0 * (double)a.tiles_bound, a.level);
     ck(ctx, launch_scan2(a.tile_cnt, nullptr, a.tiles_bound, a.tile_pfx, nullptr, a.total, ctx->lb2, ++ctx->epoch,
                          ctx->ctr, ctx->ctr_val, a.ds, ctx->st, &grid, a.d_tiles),
        "scan");
     kt_end(ctx, h);
     ctx->ctr_val += grid;
-    h = kt_begin(ctx, "k_strings", 40.0 * a.k);
+    h = kt_begin(ctx, "k_strings", 40.0 * a.k, a.level);
     ck(ctx, launch_strings(a, ctx->st), "k_strings");
     kt_end(ctx, h);
     ctx->launches += 5;
@@ -597,7 +603,7 @@ void enqueue_naming(lcg_ctx* ctx, RoundArgs& a, RoundBufs& b, double g_bytes, do
     a.xlen = b.xlen;
     a.g_alloc = b.g_alloc;
     const u64 g_grid = std::max<u64>(1, b.g_alloc);
-    int h = kt_begin(ctx, "k_mark", 12.0 * g_bytes);
+    int h = kt_begin(ctx, "k_mark", 12.0 * g_bytes, a.level);
     ck(ctx, launch_mark(a, g_grid, ctx->st), "k_mark");
     kt_end(ctx, h);
     const u64 nw = b.tiles * parse_tile_positions(1) / 32;
@@ -607,25 +613,25 @@ void enqueue_naming(lcg_ctx* ctx, RoundArgs& a, RoundBufs& b, double g_bytes, do
     a.epoch = ++ctx->epoch;
     a.ctr_base = ctx->ctr_val;
     ctx->ctr_val += ptiles;
-    h = kt_begin(ctx, "k_popscan", 8.0 * (double)nw);
+    h = kt_begin(ctx, "k_popscan", 8.0 * (double)nw, a.level);
     ck(ctx, launch_popscan(a, nw, ctx->st), "k_popscan");
     kt_end(ctx, h);
-    h = kt_begin(ctx, "k_rank", 24.0 * g_bytes);
+    h = kt_begin(ctx, "k_rank", 24.0 * g_bytes, a.level);
     ck(ctx, launch_rank(a, g_grid, ctx->st), "k_rank");
     kt_end(ctx, h);
     const u64 stiles = std::max<u64>(1, scan2_tiles_for(g_grid));
     ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, stiles, scan2_lb_bytes(stiles));
     u64 grid = 0;
-    h = kt_begin(ctx, "k_scan2", 12.0 * g_bytes);
+    h = kt_begin(ctx, "k_scan2", 12.0 * g_bytes, a.level);
     ck(ctx, launch_scan2(b.len_r, nullptr, g_grid, b.xlen, nullptr, a.total + 1, ctx->lb2, ++ctx->epoch, ctx->ctr,
                          ctx->ctr_val, a.ds, ctx->st, &grid, a.d_gnew),
        "scan");
     kt_end(ctx, h);
     ctx->ctr_val += grid;
-    h = kt_begin(ctx, "k_rules", 4.0 * G_bytes + 12.0 * g_bytes);
+    h = kt_begin(ctx, "k_rules", 4.0 * G_bytes + 12.0 * g_bytes, a.level);
     ck(ctx, launch_rules(a, g_grid, ctx->st), "k_rules");
     kt_end(ctx, h);
-    h = kt_begin(ctx, "k_rewrite", 12.0 * P_bytes);
+    h = kt_begin(ctx, "k_rewrite", 12.0 * P_bytes, a.level);
     ck(ctx, launch_rewrite(a, ctx->st), "k_rewrite");
     kt_end(ctx, h);
     ctx->launches += 6;

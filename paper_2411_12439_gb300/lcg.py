@@ -45,7 +45,8 @@ class HashFamilyC(ctypes.Structure):
 class RoundStatsC(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("phrases", ctypes.c_uint64), ("g", ctypes.c_uint64),
                 ("G", ctypes.c_uint64), ("strings", ctypes.c_uint64), ("table_cap", ctypes.c_uint64),
-                ("retries", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("parse_ms", ctypes.c_double)]
+                ("retries", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("parse_ms", ctypes.c_double),
+                ("round_ms", ctypes.c_double)]
 
 
 class KernelTimeC(ctypes.Structure):
@@ -272,7 +273,8 @@ class Context:
         st = BuildStatsC()
         self._check(load().lcg_last_build_stats(self._h, ctypes.byref(st)))
         rounds = [{**{f: int(getattr(st.round[i], f)) for f in ("n", "phrases", "g", "G", "strings", "table_cap",
-                                                                "retries")}, "parse_ms": float(st.round[i].parse_ms)}
+                                                                "retries")}, "parse_ms": float(st.round[i].parse_ms),
+                   "round_ms": float(st.round[i].round_ms)}
                   for i in range(min(st.rounds, 64))]
         return {"rounds": int(st.rounds), "async_rounds": int(st.async_rounds), "redone": bool(st.redone),
                 "graph": int(st.graph),
