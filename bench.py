@@ -54,6 +54,7 @@ def parse_args():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-graph", action="store_true", help="time the builds as separate launches")
+    p.add_argument("--no-postprocess", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--profile-builds", type=int, default=0,
                    help="only run this many batched builds of the workload and exit (for profiler captures)")
@@ -385,6 +386,24 @@ def run_ours(args):
                             "parse_ms": float(np.median(pr["parse_ms"])),
                             "gbs": pr["symbols"] * pr["bytes_per_symbol"] / (rms / 1e3) / 1e9 if rms > 0 else None})
 
+    # ---- post-processing of the batch's grammar: run-length rules, then Simp
+    post = None
+    if not args.no_postprocess:
+        g = ctx.build(d, coll.offsets)
+        times = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pp = ctx.postprocess(g)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            st = pp.stats()
+            pp.free()
+        g.free()
+        pms = float(np.median(times)) * 1e3
+        post = {"ms": pms, "grammar_gbs": 4.0 * st["size_before"] / (pms / 1e3) / 1e9, **st,
+                "timing": "host clock around lcg_postprocess (it synchronises between levels)"}
+
     # ---- end to end through the public API: pinned host input, the whole
     #      grammar to a pinned host buffer in its packed form every step
     hd = torch.from_numpy(coll.data).pin_memory()
@@ -462,7 +481,7 @@ def run_ours(args):
                    "parallelism": f"dp{world}" if world > 1 else "single GPU"},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roofline,
         "cpu_baseline": cpu, "plain": plain, "serving": serving_line,
-        "rounds": rounds_line,
+        "rounds": rounds_line, "postprocess": post,
         "kernels": {k: {"launches": v["launches"] // v["builds"], "ms_per_step": v["ms"] / v["builds"]}
                     for k, v in sorted(breakdown.items(), key=lambda kv: -kv[1]["ms"])},
     }

@@ -288,6 +288,48 @@ int lcg_import_packed(lcg_ctx* ctx, const void* buf, uint64_t size, lcg_grammar*
  * call that uses it runs on another host thread. */
 void lcg_grammar_free(lcg_grammar* G);
 
+/* ---- post-processing: run-length rules (RL), then simplification (Simp) ----
+ *
+ * Sec. 2.2 (post-processing) and Sec. 4 (the tool runs RL, then Simp, on the
+ * output of BuildGram).  RL: every maximal run Y^l (l >= 2) of one symbol in
+ * the right-hand side of one rule of level i becomes a reference to a
+ * run-length rule (Y, l) of level i; the distinct pairs of a level are
+ * numbered by first occurrence (rule rank, then position).  Runs never cross
+ * rule boundaries and the roots C are left as they are.  Simp: a rule of level
+ * i that occurs exactly once in the right-hand sides of level i+1, and is
+ * neither a string's root nor the base of a run-length rule, is removed and
+ * its occurrence replaced by its right-hand side (recursively); run-length
+ * rules are never removed.
+ *
+ * The result is one grammar over global ids: 0..255 are the bytes; then, level
+ * by level, the surviving rules in rank order followed by the level's
+ * run-length rules get the ids 256, 257, ...  Rule x - 256 has kind 0 (its
+ * right-hand side is a list of ids) or kind 1 (a run-length rule stored as the
+ * two entries [base id, run length]); c[j] is the id of string j's root.  The
+ * grammar's size is the total right-hand-side length.
+ *
+ * lcg_postprocess reads G (unchanged; it may still be used, merged or freed)
+ * and returns a new device-resident object owned by the caller, freed with
+ * lcg_pp_free.  Errors: LCG_EINVAL (null arguments, another device, more than
+ * 64 levels), LCG_EOVERFLOW (2^32 output ids or more), LCG_ENOMEM, LCG_EDEVICE.
+ * lcg_pp_export copies the arrays to host buffers of sizes taken from
+ * lcg_pp_stats_of (kind: rules bytes; rhs_off: rules + 1 uint64; rhs: size
+ * uint32; c: strings uint32) and synchronises the device. */
+typedef struct lcg_pp lcg_pp;
+typedef struct lcg_pp_stats {
+    uint64_t size_before;  /* total right-hand-side length of the level grammar */
+    uint64_t size_rl;      /* after RL (a run-length rule counts two) */
+    uint64_t size;         /* after Simp: the result's size */
+    uint64_t rl_rules;     /* run-length rules created */
+    uint64_t removed;      /* rules removed by Simp */
+    uint64_t rules;        /* rules of the result (ids 256 .. 256 + rules - 1) */
+    uint64_t strings;      /* roots c[0 .. strings - 1] */
+} lcg_pp_stats;
+int lcg_postprocess(lcg_ctx* ctx, const lcg_grammar* G, lcg_pp** out);
+int lcg_pp_stats_of(const lcg_pp* pp, lcg_pp_stats* out);
+int lcg_pp_export(const lcg_pp* pp, uint8_t* kind, uint64_t* rhs_off, uint32_t* rhs, uint32_t* c);
+void lcg_pp_free(lcg_pp* pp);
+
 #ifdef __cplusplus
 }
 #endif

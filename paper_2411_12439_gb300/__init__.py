@@ -3,6 +3,6 @@
 BuildGram, MergeGrams and exp(S) run in hand-written CUDA kernels for sm_103a
 behind the C ABI of ``include/lcg.h``; this package is its Python binding.
 """
-from .lcg import Context, Grammar, LCGError, load, library_path  # noqa: F401
+from .lcg import Context, Grammar, LCGError, PPGrammar, load, library_path  # noqa: F401
 
-__all__ = ["Context", "Grammar", "LCGError", "load", "library_path"]
+__all__ = ["Context", "Grammar", "LCGError", "PPGrammar", "load", "library_path"]

@@ -1477,6 +1477,202 @@ void decompress_static(lcg_ctx* ctx, const lcg_grammar* G, u32 j, uint8_t* out, 
 }  // namespace
 
 // --------------------------------------------------------------------------
+// post-processing: RL, then Simp (kernels in post.cu)
+// --------------------------------------------------------------------------
+
+struct lcg_pp {
+    int device = 0;
+    u64 rules = 0, size = 0;
+    u32 k = 0;
+    u8* kind = nullptr;      // rules
+    u64* rhs_off = nullptr;  // rules + 1
+    u32* rhs = nullptr;      // size
+    u32* c = nullptr;        // k
+    lcg_pp_stats stats{};
+};
+
+namespace {
+
+void free_pp(lcg_pp* pp) {
+    if (!pp) return;
+    cudaSetDevice(pp->device);
+    cudaFree(pp->kind);
+    cudaFree(pp->rhs_off);
+    cudaFree(pp->rhs);
+    cudaFree(pp->c);
+    delete pp;
+}
+
+// Exclusive scan of up to two u32 columns (the library's single-pass scan);
+// returns the column totals.
+void pp_scan(lcg_ctx* ctx, const u32* in0, const u32* in1, u64 n, u64* out0, u64* out1, u64 tot[2]) {
+    tot[0] = tot[1] = 0;
+    if (n == 0) return;
+    u64 grid = 0;
+    const u64 stiles = std::max<u64>(1, scan2_tiles_for(n));
+    ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, stiles, scan2_lb_bytes(stiles));
+    ck(ctx, launch_scan2(in0, in1, n, out0, out1, ctx->scratch + 1, ctx->lb2, ++ctx->epoch, ctx->ctr, ctx->ctr_val,
+                         ctx->ds, ctx->st, &grid),
+       "scan");
+    ctx->ctr_val += grid;
+    ctx->launches++;
+    ck(ctx, cudaMemcpyAsync(tot, ctx->scratch + 1, 16, cudaMemcpyDeviceToHost, ctx->st), "read totals");
+    check_device_status(ctx, read_status(ctx));
+}
+
+// Temporary device arrays of one post-processing call, freed in stream order.
+struct PPTemps {
+    lcg_ctx* ctx;
+    std::vector<void*> ptrs;
+    template <typename T>
+    T* get(u64 n) {
+        T* p = dalloc<T>(ctx, n);
+        ptrs.push_back(p);
+        return p;
+    }
+    ~PPTemps() {
+        for (void* p : ptrs) dfree(ctx, p);
+    }
+};
+
+void set_u64(lcg_ctx* ctx, u64* dst, u64 v) {
+    ck(ctx, cudaMemcpyAsync(dst, &v, 8, cudaMemcpyHostToDevice, ctx->st), "set value");
+    sync(ctx);  // v lives on the host stack
+}
+
+lcg_pp* postprocess(lcg_ctx* ctx, const lcg_grammar* G) {
+    const u32 nl = (u32)G->lv.size();
+    fail_if(ctx, nl > (u32)kPPMaxLevels, LCG_EINVAL, "grammar with too many levels");
+    if (G->owner && G->owner != ctx) ck(ctx, cudaStreamSynchronize(G->owner->st), "grammar's stream");
+    sync(ctx);
+    reset_status(ctx);
+    PPTemps tmp{ctx, {}};
+    PPLevels lv{};
+    lv.n = nl;
+    std::vector<u32*> uses(nl);
+    u64 rl_total = 0, size_before = 0, size_rl = 0;
+    // RL, level by level
+    for (u32 i = 0; i < nl; i++) {
+        const Level& L = G->lv[i];
+        const u64 g = L.g;
+        size_before += L.G;
+        u32* out_len = tmp.get<u32>(g);
+        u32* rl_len = tmp.get<u32>(g);
+        u64* new_off = tmp.get<u64>(g + 1);
+        u64* rl_off = tmp.get<u64>(g);
+        ck(ctx, launch_rl_count(L.rhs_off, L.rhs, g, out_len, rl_len, ctx->st), "k_rl_count");
+        u64 tot[2];
+        pp_scan(ctx, out_len, rl_len, g, new_off, rl_off, tot);
+        const u64 Gn = tot[0], R = tot[1];
+        set_u64(ctx, new_off + g, Gn);
+        u32* new_rhs = tmp.get<u32>(Gn);
+        u32* run_y = tmp.get<u32>(R);
+        u32* run_len = tmp.get<u32>(R);
+        u64* run_pos = tmp.get<u64>(R);
+        u64 cap = 64;
+        while (cap < 2 * R + 16) cap <<= 1;
+        u64* keys = tmp.get<u64>(cap);
+        u64* vals = tmp.get<u64>(cap);
+        ck(ctx, cudaMemsetAsync(keys, 0xFF, cap * 8, ctx->st), "memset");
+        ck(ctx, cudaMemsetAsync(vals, 0xFF, cap * 8, ctx->st), "memset");
+        ck(ctx, launch_rl_write(L.rhs_off, L.rhs, g, new_off, rl_off, new_rhs, run_y, run_len, run_pos, keys, vals,
+                                cap - 1, ctx->ds, ctx->st),
+           "k_rl_write");
+        u32* first = tmp.get<u32>(R);
+        u64* run_first = tmp.get<u64>(R);
+        u64* rank_of = tmp.get<u64>(R);
+        ck(ctx, launch_rl_first(run_y, run_len, R, keys, vals, cap - 1, first, run_first, ctx->ds, ctx->st),
+           "k_rl_first");
+        pp_scan(ctx, first, nullptr, R, rank_of, nullptr, tot);
+        const u64 Rd = tot[0];
+        u32* rl_y = tmp.get<u32>(Rd);
+        u32* rl_l = tmp.get<u32>(Rd);
+        ck(ctx, launch_rl_fix(run_y, run_len, run_pos, run_first, rank_of, R, new_rhs, rl_y, rl_l, ctx->ds, ctx->st),
+           "k_rl_fix");
+        ctx->launches += 4;
+        lv.off[i] = new_off;
+        lv.rhs[i] = new_rhs;
+        lv.g[i] = g;
+        lv.nrl[i] = Rd;
+        lv.rl_y[i] = rl_y;
+        lv.rl_l[i] = rl_l;
+        rl_total += Rd;
+        size_rl += Gn + 2 * Rd;
+        uses[i] = tmp.get<u32>(g);
+        lv.pinned[i] = tmp.get<u8>(g);
+        ck(ctx, cudaMemsetAsync(uses[i], 0, g * 4, ctx->st), "memset");
+        ck(ctx, cudaMemsetAsync(lv.pinned[i], 0, g, ctx->st), "memset");
+    }
+    // Simp: uses, kept rules, surviving rules and their ids
+    for (u32 i = 1; i < nl; i++) {
+        ck(ctx, launch_pp_uses(lv.off[i], lv.rhs[i], lv.g[i], uses[i - 1], ctx->st), "k_pp_uses");
+        ck(ctx, launch_pp_pin_bases(lv.rl_y[i], lv.nrl[i], lv.pinned[i - 1], ctx->st), "k_pp_pin_bases");
+        ctx->launches += 2;
+    }
+    ck(ctx, launch_pp_pin_roots(G->c_level, G->c_rank, G->k, lv, ctx->st), "k_pp_pin_roots");
+    u64 next = 256, removed = 0;
+    for (u32 i = 0; i < nl; i++) {
+        u32* surv = tmp.get<u32>(lv.g[i]);
+        u64* spre = tmp.get<u64>(lv.g[i]);
+        ck(ctx, launch_pp_survive(uses[i], lv.pinned[i], lv.g[i], surv, ctx->st), "k_pp_survive");
+        u64 tot[2];
+        pp_scan(ctx, surv, nullptr, lv.g[i], spre, nullptr, tot);
+        lv.surv[i] = surv;
+        lv.spre[i] = spre;
+        lv.S[i] = tot[0];
+        lv.base[i] = next;
+        lv.explen[i] = tmp.get<u32>(lv.g[i]);
+        lv.dst[i] = tmp.get<u64>(lv.g[i]);
+        ck(ctx, cudaMemsetAsync(lv.dst[i], 0xFF, lv.g[i] * 8, ctx->st), "memset");
+        next += lv.S[i] + lv.nrl[i];
+        removed += lv.g[i] - lv.S[i];
+        ctx->launches += 2;
+    }
+    const u64 rules = next - 256;
+    fail_if(ctx, next > 0xffffffffull, LCG_EOVERFLOW, "post-processed grammar with 2^32 symbols or more");
+    u32* fin_len = tmp.get<u32>(rules);
+    for (u32 i = 0; i < nl; i++) {
+        ck(ctx, launch_pp_lengths(lv, i, fin_len, ctx->ds, ctx->st), "k_pp_explen");
+        ctx->launches += 2;
+    }
+    auto* pp = new lcg_pp;
+    pp->device = ctx->device;
+    pp->rules = rules;
+    pp->k = G->k;
+    try {
+        pp->rhs_off = dalloc<u64>(ctx, rules + 1);
+        u64 tot[2];
+        pp_scan(ctx, fin_len, nullptr, rules, pp->rhs_off, nullptr, tot);
+        pp->size = tot[0];
+        set_u64(ctx, pp->rhs_off + rules, pp->size);
+        pp->rhs = dalloc<u32>(ctx, pp->size);
+        pp->kind = dalloc<u8>(ctx, rules);
+        pp->c = dalloc<u32>(ctx, G->k);
+        for (u32 i = nl; i-- > 0;) {  // top level first: removed rules learn their place from above
+            ck(ctx, launch_pp_write(lv, i, pp->rhs_off, pp->rhs, pp->kind, ctx->ds, ctx->st), "k_pp_place");
+            ctx->launches += 2;
+        }
+        ck(ctx, launch_pp_roots(G->c_level, G->c_rank, G->k, lv, pp->c, ctx->st), "k_pp_roots");
+        ctx->launches++;
+        check_device_status(ctx, read_status(ctx));
+    } catch (...) {
+        sync(ctx);
+        free_pp(pp);
+        throw;
+    }
+    pp->stats.size_before = size_before;
+    pp->stats.size_rl = size_rl;
+    pp->stats.size = pp->size;
+    pp->stats.rl_rules = rl_total;
+    pp->stats.removed = removed;
+    pp->stats.rules = rules;
+    pp->stats.strings = G->k;
+    return pp;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------
 // C entry points
 // --------------------------------------------------------------------------
 
@@ -2006,5 +2202,34 @@ int lcg_import_packed(lcg_ctx* ctx, const void* buf, uint64_t size, lcg_grammar*
 }
 
 void lcg_grammar_free(lcg_grammar* G) { free_grammar_now(G); }
+
+int lcg_postprocess(lcg_ctx* ctx, const lcg_grammar* G, lcg_pp** out) {
+    if (!ctx || !G || !out) return LCG_EINVAL;
+    *out = nullptr;
+    LCG_GUARD_BEGIN
+    ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    fail_if(ctx, G->device != ctx->device, LCG_EINVAL, "grammar on another device");
+    *out = postprocess(ctx, G);
+    return LCG_OK;
+    LCG_GUARD_END
+}
+
+int lcg_pp_stats_of(const lcg_pp* pp, lcg_pp_stats* out) {
+    if (!pp || !out) return LCG_EINVAL;
+    *out = pp->stats;
+    return LCG_OK;
+}
+
+int lcg_pp_export(const lcg_pp* pp, uint8_t* kind, uint64_t* rhs_off, uint32_t* rhs, uint32_t* c) {
+    if (!pp || !kind || !rhs_off || (!rhs && pp->size) || (!c && pp->k)) return LCG_EINVAL;
+    if (cudaSetDevice(pp->device) != cudaSuccess) return LCG_EDEVICE;
+    bool ok = cudaMemcpy(kind, pp->kind, pp->rules, cudaMemcpyDeviceToHost) == cudaSuccess &&
+              cudaMemcpy(rhs_off, pp->rhs_off, 8 * (pp->rules + 1), cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (ok && pp->size) ok = cudaMemcpy(rhs, pp->rhs, 4 * pp->size, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (ok && pp->k) ok = cudaMemcpy(c, pp->c, 4ull * pp->k, cudaMemcpyDeviceToHost) == cudaSuccess;
+    return ok ? LCG_OK : LCG_EDEVICE;
+}
+
+void lcg_pp_free(lcg_pp* pp) { free_pp(pp); }
 
 }  // extern "C"

@@ -11,6 +11,7 @@ namespace lcg {
 
 typedef unsigned long long u64;
 typedef unsigned int u32;
+typedef unsigned char u8;
 
 // --------------------------------------------------------------------------
 // arithmetic modulo p = 2^61 - 1

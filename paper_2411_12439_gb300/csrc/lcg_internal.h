@@ -151,4 +151,43 @@ u64 scan2_tiles_for(u64 n);
 size_t scan2_lb_bytes(u64 tiles);
 constexpr size_t scan2_lb_bytes_static(u64 tiles) { return tiles * sizeof(LBSlot<2>); }
 
+// Post-processing (post.cu): the RL-rewritten levels of a grammar and what
+// Simp decides about their rules.  Passed by value to the kernels.
+constexpr int kPPMaxLevels = 64;
+struct PPLevels {
+    u32 n;                          // levels
+    const u64* off[kPPMaxLevels];   // RL-rewritten right-hand-side offsets (g + 1)
+    const u32* rhs[kPPMaxLevels];   // RL-rewritten right-hand sides (symbol, or 2^31 | run-length rule)
+    u64 g[kPPMaxLevels];            // rules of the level
+    u64 nrl[kPPMaxLevels];          // run-length rules of the level
+    const u32* rl_y[kPPMaxLevels];  // their base symbol (of the level below)
+    const u32* rl_l[kPPMaxLevels];  // and run length
+    u8* pinned[kPPMaxLevels];       // the rule is a string's root or a run-length rule's base
+    const u32* surv[kPPMaxLevels];  // the rule survives Simp
+    const u64* spre[kPPMaxLevels];  // exclusive prefix of surv
+    u32* explen[kPPMaxLevels];      // right-hand-side length with the removed rules below expanded
+    u64* dst[kPPMaxLevels];         // output position of a removed rule's expansion
+    u64 base[kPPMaxLevels];         // output id of the level's first surviving rule
+    u64 S[kPPMaxLevels];            // surviving rules of the level
+};
+
+cudaError_t launch_rl_count(const u64* off, const u32* rhs, u64 g, u32* out_len, u32* rl_len, cudaStream_t st);
+cudaError_t launch_rl_write(const u64* off, const u32* rhs, u64 g, const u64* new_off, const u64* rl_off, u32* new_rhs,
+                            u32* run_y, u32* run_len, u64* run_pos, u64* keys, u64* vals, u64 mask, DevStatus* ds,
+                            cudaStream_t st);
+cudaError_t launch_rl_first(const u32* run_y, const u32* run_len, u64 R, const u64* keys, const u64* vals, u64 mask,
+                            u32* first, u64* run_first, DevStatus* ds, cudaStream_t st);
+cudaError_t launch_rl_fix(const u32* run_y, const u32* run_len, const u64* run_pos, const u64* run_first,
+                          const u64* rank_of, u64 R, u32* new_rhs, u32* rl_y, u32* rl_l, DevStatus* ds,
+                          cudaStream_t st);
+cudaError_t launch_pp_uses(const u64* off, const u32* rhs, u64 g, u32* uses_below, cudaStream_t st);
+cudaError_t launch_pp_pin_bases(const u32* rl_y, u64 nrl, u8* pinned_below, cudaStream_t st);
+cudaError_t launch_pp_pin_roots(const u32* c_level, const u32* c_rank, u32 k, const PPLevels& lv, cudaStream_t st);
+cudaError_t launch_pp_survive(const u32* uses, const u8* pinned, u64 g, u32* surv, cudaStream_t st);
+cudaError_t launch_pp_lengths(const PPLevels& lv, u32 li, u32* fin_len, DevStatus* ds, cudaStream_t st);
+cudaError_t launch_pp_write(const PPLevels& lv, u32 li, const u64* fin_off, u32* out, u8* kind, DevStatus* ds,
+                            cudaStream_t st);
+cudaError_t launch_pp_roots(const u32* c_level, const u32* c_rank, u32 k, const PPLevels& lv, u32* c_out,
+                            cudaStream_t st);
+
 }  // namespace lcg

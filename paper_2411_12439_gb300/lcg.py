@@ -27,7 +27,7 @@ SYMBOLS = [
     "lcg_last_kernel_times", "lcg_build", "lcg_build_into",
     "lcg_merge", "lcg_decompress", "lcg_decompress_static", "lcg_grammar_shape", "lcg_level_size", "lcg_export_level",
     "lcg_export_start", "lcg_string_roots", "lcg_import", "lcg_packed_size", "lcg_export_packed", "lcg_import_packed",
-    "lcg_grammar_free",
+    "lcg_grammar_free", "lcg_postprocess", "lcg_pp_stats_of", "lcg_pp_export", "lcg_pp_free",
 ]
 
 
@@ -57,6 +57,11 @@ class KernelTimeC(ctypes.Structure):
 class TuningC(ctypes.Structure):
     _fields_ = [("table_load", ctypes.c_double), ("parse_blocks_per_sm", ctypes.c_uint32),
                 ("miss_flush", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("pad2", ctypes.c_uint32)]
+
+
+class PPStatsC(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64)
+                for f in ("size_before", "size_rl", "size", "rl_rules", "removed", "rules", "strings")]
 
 
 class BuildStatsC(ctypes.Structure):
@@ -110,9 +115,14 @@ def load(build_if_missing: bool = True):
     lib.lcg_export_packed.argtypes = [P, P, P, U64]
     lib.lcg_import_packed.argtypes = [P, P, U64, PP]
     lib.lcg_grammar_free.argtypes = [P]
+    lib.lcg_postprocess.argtypes = [P, P, PP]
+    lib.lcg_pp_stats_of.argtypes = [P, ctypes.POINTER(PPStatsC)]
+    lib.lcg_pp_export.argtypes = [P, P, P, P, P]
+    lib.lcg_pp_free.argtypes = [P]
+    lib.lcg_pp_free.restype = None
     lib.lcg_grammar_free.restype = None
     for name in SYMBOLS:
-        if name not in ("lcg_ctx_destroy", "lcg_last_error", "lcg_grammar_free"):
+        if name not in ("lcg_ctx_destroy", "lcg_last_error", "lcg_grammar_free", "lcg_pp_free"):
             getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -189,6 +199,13 @@ class Context:
         """lcg_merge: a absorbs b (in place); returns a."""
         self._check(load().lcg_merge(self._h, a._h, b._h))
         return a
+
+    def postprocess(self, g: "Grammar") -> "PPGrammar":
+        """lcg_postprocess: run-length rules, then simplification, of g (g is
+        unchanged); a new device-resident grammar over global ids."""
+        h = ctypes.c_void_p(0)
+        self._check(load().lcg_postprocess(self._h, g._h, ctypes.byref(h)))
+        return PPGrammar(h)
 
     def import_grammar(self, ex: dict) -> "Grammar":
         """lcg_import: a device grammar from the host arrays of ``Grammar.export()``
@@ -387,3 +404,41 @@ class Grammar:
         buf = np.zeros(max(need, 1), dtype=np.uint8)
         self.ctx._check(lib.lcg_decompress(self.ctx._h, self._h, j, _np_ptr(buf), need, ctypes.byref(n), 0))
         return buf[:need].tobytes()
+
+
+class PPGrammar:
+    """A post-processed grammar (lcg_postprocess) on the device."""
+
+    def __init__(self, h):
+        self._h = h
+
+    def stats(self) -> dict:
+        st = PPStatsC()
+        rc = load().lcg_pp_stats_of(self._h, ctypes.byref(st))
+        if rc != LCG_OK:
+            raise LCGError(rc, "lcg_pp_stats_of")
+        return {f: int(getattr(st, f)) for f, _ in PPStatsC._fields_}
+
+    def export(self) -> dict:
+        """Host arrays: kind (uint8, per rule), rhs_off (uint64), rhs (uint32), c (uint32)."""
+        st = self.stats()
+        kind = np.zeros(max(st["rules"], 1), dtype=np.uint8)
+        off = np.zeros(st["rules"] + 1, dtype=np.uint64)
+        rhs = np.zeros(max(st["size"], 1), dtype=np.uint32)
+        c = np.zeros(max(st["strings"], 1), dtype=np.uint32)
+        rc = load().lcg_pp_export(self._h, _np_ptr(kind), _np_ptr(off), _np_ptr(rhs), _np_ptr(c))
+        if rc != LCG_OK:
+            raise LCGError(rc, "lcg_pp_export")
+        return {"kind": kind[:st["rules"]], "rhs_off": off, "rhs": rhs[:st["size"]], "c": c[:st["strings"]]}
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().lcg_pp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
