@@ -407,6 +407,7 @@ def run_ours(args):
     # ---- end to end through the public API: pinned host input, the whole
     #      grammar to a pinned host buffer in its packed form every step
     hd = torch.from_numpy(coll.data).pin_memory()
+    ctx.set_graph(not args.no_graph)  # host input goes through the context's upload buffer
     g = ctx.build(hd, coll.offsets)
     out = torch.empty(g.packed_size() * 5 // 4 + 4096, dtype=torch.uint8).pin_memory()
     g.free()

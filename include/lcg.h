@@ -157,9 +157,11 @@ int lcg_set_tuning(lcg_ctx* ctx, const lcg_tuning* t);
  * first build of a shape (device input buffer, string lengths, plan) captures
  * the graph; later builds of that shape launch it, provided the grammar of the
  * previous launch has been freed (the graph writes the grammar into its own
- * allocations, at the same addresses every time); otherwise, and for inputs in
- * host memory or with strings of length one, the build runs as launches.
- * Results do not depend on it. */
+ * allocations, at the same addresses every time); otherwise, and for
+ * collections with strings of length one, the build runs as launches.  Input
+ * in host memory is first copied into an upload buffer that the context keeps
+ * (grown when needed), so that its builds can launch the graph too.  Results
+ * do not depend on it. */
 int lcg_set_graph(lcg_ctx* ctx, int enable);
 int lcg_get_tuning(const lcg_ctx* ctx, lcg_tuning* t);
 

@@ -86,6 +86,8 @@ struct lcg_ctx {
     // per-kernel CUDA-event timing (optional)
     int ktime = 0;  // 0 off, 1 every launch, 2 parse launches only
     bool capturing = false;              // the stream is being captured into a graph
+    unsigned char* upload = nullptr;     // host input of graph builds, at a fixed address
+    u64 upload_cap = 0;
     struct KRec {
         const char* name;
         cudaEvent_t a, b;
@@ -1752,6 +1754,7 @@ void lcg_ctx_destroy(lcg_ctx* ctx) {
     for (lcg_grammar* G : ctx->live) G->owner = nullptr;  // they outlive the context
     ctx->live.clear();
     destroy_graph(ctx);
+    if (ctx->upload) cudaFree(ctx->upload);
     for (auto& r : ctx->krecs) {
         if (r.graph) continue;  // destroyed with the graph
         cudaEventDestroy(r.a);
@@ -1829,12 +1832,36 @@ int lcg_build(lcg_ctx* ctx, const uint8_t* data, const uint64_t* offsets, uint32
     ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
     kt_reset(ctx);
     reset_status(ctx);
-    if (ctx->use_graph && data_on_device && k > 0 && offsets && data && ctx->hint_rounds > 0) {
+    std::vector<uint64_t> shifted;  // offsets into the context's upload buffer
+    if (ctx->use_graph && k > 0 && offsets && data && ctx->hint_rounds > 0) {
         std::vector<u64> lens(k);
         bool ok = true;
         for (u32 j = 0; j < k && ok; j++) {
             lens[j] = offsets[j + 1] - offsets[j];
             ok = offsets[j + 1] > offsets[j] && lens[j] >= 2;  // strings of length one: not in graphs
+        }
+        if (ok && !data_on_device) {
+            // host input: into the context's upload buffer, whose address a
+            // captured graph can keep; the build then reads it there
+            const u64 nbytes = offsets[k] - offsets[0];
+            if (ctx->upload_cap < nbytes) {
+                if (ctx->upload) {
+                    if (ctx->graph) destroy_graph(ctx);
+                    dfree(ctx, ctx->upload);
+                    ctx->upload = nullptr;
+                    ctx->upload_cap = 0;
+                }
+                const u64 cap = nbytes + nbytes / 8 + 4096;
+                ctx->upload = dalloc<unsigned char>(ctx, cap);
+                ctx->upload_cap = cap;
+            }
+            ck(ctx, cudaMemcpyAsync(ctx->upload, data + offsets[0], nbytes, cudaMemcpyHostToDevice, ctx->st),
+               "copy input");
+            shifted.resize(k + 1);
+            for (u32 j = 0; j <= k; j++) shifted[j] = offsets[j] - offsets[0];
+            data = ctx->upload;
+            offsets = shifted.data();
+            data_on_device = 1;
         }
         if (ok) {
             try {

@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan2(const u32* __restrict__ 
                                                         u64 n, u64* __restrict__ out0, u64* __restrict__ out1,
                                                         u64* __restrict__ totals, LBSlot<2>* lb, u64 epoch, u64* ctr,
                                                         u64 ctr_base, DevStatus* ds, const u64* n_dev) {
+    pdl_wait();
     const u64 tile = dynamic_tile(ctr, ctr_base);
     if (n_dev != nullptr) n = min(*n_dev, n);
     if (tile > 0 && tile * (u64)kScanTile >= n) return;  // beyond the count read on the device
@@ -78,9 +79,8 @@ cudaError_t launch_scan2(const u32* in0, const u32* in1, u64 n, u64* out0, u64* 
     u64 tiles = scan2_tiles_for(n);
     if (tiles == 0) tiles = 1;
     *grid_out = tiles;
-    k_scan2<<<(unsigned)tiles, kScanThreads, 0, st>>>(in0, in1, n, out0, out1, totals, (LBSlot<2>*)lb, epoch, ctr,
-                                                      ctr_base, ds, n_dev);
-    return cudaGetLastError();
+    return launch_pdl(k_scan2, (unsigned)tiles, kScanThreads, st, in0, in1, n, out0, out1, totals, (LBSlot<2>*)lb,
+                      epoch, ctr, ctr_base, ds, n_dev);
 }
 
 // --------------------------------------------------------------------------
@@ -152,13 +152,13 @@ __global__ void k_set_u64(u64* p, u64 v) { *p = v; }
 
 // F^0[s] = h^0(s) = ((a_0 s + b_0) mod p) mod m for every byte s (Sec. 3.2).
 __global__ void k_h0(LevelHash h0, u32* __restrict__ F0) {
+    pdl_wait();
     const u32 s = threadIdx.x;
     if (s < 256) F0[s] = (u32)(addmod61(mulmod61(h0.a, (u64)s), h0.b) & h0.mmask);
 }
 
 cudaError_t launch_h0(LevelHash h0, u32* F0, cudaStream_t st) {
-    k_h0<<<1, 256, 0, st>>>(h0, F0);
-    return cudaGetLastError();
+    return launch_pdl(k_h0, 1, 256, st, h0, F0);
 }
 
 // C_b entries of level `level` move to G_a's ranks.

@@ -78,6 +78,12 @@ struct DevStatus {
     u64 aux[5];
 };
 
+// Kernels of a build are launched with programmatic dependent launch: a grid
+// may be scheduled while the one before it drains, and waits here, before its
+// first access to memory, until that grid has finished and its writes are
+// visible.  (A no-op for a grid launched without the attribute.)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void set_error(DevStatus* st, u32 code) {
     atomicCAS(&st->error, 0u, code);
 }

@@ -187,6 +187,7 @@ __device__ __forceinline__ u32 spread_down(u32 src, u32 pass) {
 
 template <typename T>
 __global__ void __launch_bounds__(kBrkThreads) k_breaks(const RoundArgs a, u64 nblocks) {
+    pdl_wait();
     constexpr bool kByte = sizeof(T) == 1;
     constexpr u32 kTypeU = 0, kTypeS = 1, kTypeL = 2, kUndecided = 3;
     constexpr int SW = kBrkThreads;  // string-start words of a step
@@ -332,6 +333,7 @@ __device__ __forceinline__ u32 block_scan32(u32 x, u32& total, u32* s_wsum) {
 
 template <typename T>
 __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse(const RoundArgs a, u64 ntiles) {
+    pdl_wait();
     constexpr int NWS = kSP / 32;    // staged break words
     constexpr int NWT = kTP / 32;    // tile break words
     constexpr bool kByte = sizeof(T) == 1;
@@ -763,6 +765,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
 
 // Per parse tile: the string that holds its first position.
 __global__ void k_tile_strings(const RoundArgs a, u64 tiles) {
+    pdl_wait();
     const u64 n = round_n(a);
     const u32 k = round_k(a);
     const u64 nt = (n + kTP - 1) / kTP;
@@ -789,6 +792,7 @@ __global__ void k_tile_strings(const RoundArgs a, u64 tiles) {
 // --------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(1024) k_strings(const RoundArgs a) {
+    pdl_wait();
     if (round_halted(a)) return;
     const u64 P = *a.total;
     const u32 k = round_k(a);
@@ -841,6 +845,7 @@ __device__ __forceinline__ u64 round_gnew(const RoundArgs& a) {
 }
 
 __global__ void k_mark(const RoundArgs a) {
+    pdl_wait();
     if (round_halted(a)) return;
     const u64 g_new = round_gnew(a);
     const u64 keys = a.tiles_bound * (u64)kTP;  // order keys the bitmap covers
@@ -861,6 +866,7 @@ constexpr int kPopTile = kPopThreads * kPopItems;
 
 // Exclusive prefix of the popcounts of the bitmap words (single pass).
 __global__ void __launch_bounds__(kPopThreads) k_popscan(const RoundArgs a, u64 nw) {
+    pdl_wait();
     const u64 tile = dynamic_tile(a.ctr, a.ctr_base);
     nw = min(nw, *a.d_tiles * (u64)(kTP / 32));
     if (tile > 0 && tile * (u64)kPopTile >= nw) return;  // beyond the count read on the device
@@ -907,6 +913,7 @@ __global__ void __launch_bounds__(kPopThreads) k_popscan(const RoundArgs a, u64 
 
 // Rank of every new phrase: the marks before its first occurrence.
 __global__ void k_rank(const RoundArgs a) {
+    pdl_wait();
     if (round_halted(a)) return;
     const u64 g_new = round_gnew(a);
     for (u64 c = blockIdx.x * (u64)blockDim.x + threadIdx.x; c < g_new; c += (u64)gridDim.x * blockDim.x) {
@@ -926,6 +933,7 @@ __global__ void k_rank(const RoundArgs a) {
 // the new rules enter it.
 template <typename T>
 __global__ void k_rules(const RoundArgs a) {
+    pdl_wait();
     constexpr bool kByte = sizeof(T) == 1;
     const T* S = (const T*)a.S;
     const ContentTable rw{(Slot*)a.rtab_w, a.rtab_w_cap};
@@ -976,6 +984,7 @@ constexpr int kRwUnroll = 4;
 // of a slot comes from the dense array k_rules wrote (read-only here: small
 // and cached in L1 in early rounds, in L2 after its writes later on).
 __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) {
+    pdl_wait();
     if (round_halted(a)) return;
     const u64 nr = a.rc->retired;
     ntiles = min(ntiles, *a.d_tiles);
@@ -1052,6 +1061,7 @@ __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) 
 template <bool kByte>
 __global__ void k_resident_build(const u32* __restrict__ rhs, const u64* __restrict__ rhs_off, u64 r0, u64 cnt,
                                  const u32* __restrict__ Fprev, LevelHash lh, ContentTable t, DevStatus* ds) {
+    pdl_wait();
     for (u64 x = blockIdx.x * (u64)blockDim.x + threadIdx.x; x < cnt; x += (u64)gridDim.x * blockDim.x) {
         const u64 r = r0 + x;
         const u64 s = rhs_off[r], e = rhs_off[r + 1];
@@ -1068,6 +1078,7 @@ __global__ void k_resident_build(const u32* __restrict__ rhs, const u64* __restr
 
 __global__ void k_level0(const unsigned char* __restrict__ data, const u64* __restrict__ pos,
                          const u32* __restrict__ ids, u32 cnt, u32* c_level, u32* c_rank) {
+    pdl_wait();
     const u32 x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x < cnt) {
         c_level[ids[x]] = 0;
@@ -1077,6 +1088,7 @@ __global__ void k_level0(const unsigned char* __restrict__ data, const u64* __re
 
 __global__ void k_gather_strings(const unsigned char* __restrict__ data, const u64* __restrict__ src_off,
                                  const u64* __restrict__ dst_off, u32 k, unsigned char* __restrict__ out) {
+    pdl_wait();
     for (u32 j = blockIdx.x; j < k; j += gridDim.x) {
         const u64 s = src_off[j], d = dst_off[j], len = dst_off[j + 1] - dst_off[j];
         for (u64 x = threadIdx.x; x < len; x += blockDim.x) out[d + x] = data[s + x];
@@ -1098,8 +1110,7 @@ u64 parse_tile_positions(int) { return (u64)kTP; }
 u64 popscan_tiles_for(u64 nw) { return (nw + kPopTile - 1) / kPopTile; }
 
 cudaError_t launch_tile_strings(const RoundArgs& a, cudaStream_t st) {
-    k_tile_strings<<<grid_for(a.tiles_bound), 256, 0, st>>>(a, a.tiles_bound);
-    return cudaGetLastError();
+    return launch_pdl(k_tile_strings, grid_for(a.tiles_bound), 256, st, a, a.tiles_bound);
 }
 
 template <typename T>
@@ -1146,54 +1157,47 @@ static unsigned breaks_grid(u64 blocks) {
 
 cudaError_t launch_breaks(const RoundArgs& a, cudaStream_t st) {
     const u64 blocks = (a.tiles_bound * (u64)kTP + kBrkSpan - 1) / kBrkSpan;
-    if (a.sym_bytes == 1) k_breaks<unsigned char><<<breaks_grid<unsigned char>(blocks), kBrkThreads, 0, st>>>(a, blocks);
-    else k_breaks<u32><<<breaks_grid<u32>(blocks), kBrkThreads, 0, st>>>(a, blocks);
-    return cudaGetLastError();
+    if (a.sym_bytes == 1)
+        return launch_pdl(k_breaks<unsigned char>, breaks_grid<unsigned char>(blocks), kBrkThreads, st, a, blocks);
+    return launch_pdl(k_breaks<u32>, breaks_grid<u32>(blocks), kBrkThreads, st, a, blocks);
 }
 
 cudaError_t launch_parse(const RoundArgs& a, cudaStream_t st) {
     const u64 tiles = a.tiles_bound;
     if (a.sym_bytes == 1)
-        k_parse<unsigned char><<<persistent_grid<unsigned char>(tiles, a.parse_blocks), kParseThreads, 0, st>>>(a, tiles);
-    else
-        k_parse<u32><<<persistent_grid<u32>(tiles, a.parse_blocks), kParseThreads, 0, st>>>(a, tiles);
-    return cudaGetLastError();
+        return launch_pdl(k_parse<unsigned char>, persistent_grid<unsigned char>(tiles, a.parse_blocks), kParseThreads,
+                          st, a, tiles);
+    return launch_pdl(k_parse<u32>, persistent_grid<u32>(tiles, a.parse_blocks), kParseThreads, st, a, tiles);
 }
 
 cudaError_t launch_strings(const RoundArgs& a, cudaStream_t st) {
-    k_strings<<<1, 1024, 0, st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_strings, 1, 1024, st, a);
 }
 
 cudaError_t launch_mark(const RoundArgs& a, u64 g_grid, cudaStream_t st) {
-    k_mark<<<grid_for(g_grid), 256, 0, st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_mark, grid_for(g_grid), 256, st, a);
 }
 
 cudaError_t launch_popscan(const RoundArgs& a, u64 nw_bound, cudaStream_t st) {
     u64 tiles = popscan_tiles_for(nw_bound);
     if (tiles == 0) tiles = 1;
-    k_popscan<<<(unsigned)tiles, kPopThreads, 0, st>>>(a, nw_bound);
-    return cudaGetLastError();
+    return launch_pdl(k_popscan, (unsigned)tiles, kPopThreads, st, a, nw_bound);
 }
 
 cudaError_t launch_rank(const RoundArgs& a, u64 g_grid, cudaStream_t st) {
-    k_rank<<<grid_for(g_grid), 256, 0, st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_rank, grid_for(g_grid), 256, st, a);
 }
 
 cudaError_t launch_rules(const RoundArgs& a, u64 g_grid, cudaStream_t st) {
-    if (a.sym_bytes == 1) k_rules<unsigned char><<<grid_for(g_grid), 256, 0, st>>>(a);
-    else k_rules<u32><<<grid_for(g_grid), 256, 0, st>>>(a);
-    return cudaGetLastError();
+    if (a.sym_bytes == 1) return launch_pdl(k_rules<unsigned char>, grid_for(g_grid), 256, st, a);
+    return launch_pdl(k_rules<u32>, grid_for(g_grid), 256, st, a);
 }
 
 cudaError_t launch_rewrite(const RoundArgs& a, cudaStream_t st) {
     const u64 tiles = a.tiles_bound;
     const u64 blocks = (tiles + 7) / 8;  // 8 warps per block, one tile each
     const u64 g = blocks < 152ull * 8 ? (blocks ? blocks : 1) : 152ull * 8;
-    k_rewrite<<<(unsigned)g, 256, 0, st>>>(a, tiles);
-    return cudaGetLastError();
+    return launch_pdl(k_rewrite, (unsigned)g, 256, st, a, tiles);
 }
 
 cudaError_t launch_level0(const unsigned char* data, const u64* pos, const u32* ids, u32 cnt, u32* c_level,

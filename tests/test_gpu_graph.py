@@ -66,3 +66,14 @@ def test_graph_capture_replay_and_fallback(hf):
         assert kt["k_parse"]["launches"] >= st["rounds"] and kt["k_parse"]["ms"] > 0
         g.free()
     assert modes == [0, 1, 2, 2]
+    # host input: copied into the context's upload buffer, then the same graph steps
+    ctx3 = Context(hf, device=0)
+    ctx3.set_graph(True)
+    hb = torch.from_numpy(b.data).pin_memory()
+    modes = []
+    for _ in range(4):
+        g = ctx3.build(hb, b.offsets)
+        modes.append(ctx3.last_build_stats()["graph"])
+        assert O.grammars_equal(g.export(), want["b"])
+        g.free()
+    assert modes == [0, 1, 2, 2]
