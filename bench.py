@@ -235,9 +235,14 @@ def run_serving(hf, device: int, capacity_gbs: float, count: int = 300, loads=(0
     server would be; each load then gets a stream with new content."""
     from paper_2411_12439_gb300 import serving
 
+    import torch
+
     def make(seed):
-        return li.serving_stream(seed=seed, count=count, rate_hz=1.0, n_bases=8, base_len=20_000_000,
-                                 len_max=20_000_000)
+        stream = li.serving_stream(seed=seed, count=count, rate_hz=1.0, n_bases=8, base_len=20_000_000,
+                                   len_max=20_000_000)
+        for item in stream:  # requests arrive in page-locked receive buffers
+            item.data = torch.from_numpy(np.ascontiguousarray(item.data, dtype=np.uint8)).pin_memory().numpy()
+        return stream
 
     backend = serving.CudaBackend(hf, device=device, lanes=2)
     srv = serving.Server(backend, lanes=2, max_batch_bytes=192 << 20)

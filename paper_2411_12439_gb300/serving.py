@@ -66,28 +66,48 @@ class CudaBackend:
     stream) for builds, and one context that owns the resident grammar."""
 
     def __init__(self, hash_family, device: int = 0, lanes: int = 2):
+        import torch
         from .lcg import Context
         self.device = device
         self.res_ctx = Context(hash_family, device=device)
         self.ctxs = [Context(hash_family, device=device) for _ in range(lanes)]
         self.staging = [None] * lanes
+        self.dev_staging = [None] * lanes
+        self.copy_streams = [torch.cuda.Stream(device=device) for _ in range(lanes)]
 
     def empty(self):
         return self.res_ctx.import_grammar({"levels": [], "c_level": np.zeros(0, np.uint32),
                                             "c_rank": np.zeros(0, np.uint32), "F0": np.zeros(256, np.uint32)})
 
     def gather(self, lane: int, parts, total: int):
-        """The batch's strings back to back in the lane's page-locked host
-        buffer (grown as needed), so that the build's upload runs at link
-        speed."""
+        """The batch's strings back to back.  Requests received into
+        page-locked memory are copied straight into the lane's device buffer
+        (one asynchronous copy each); others are first gathered into the
+        lane's page-locked host buffer, so that the build's upload runs at
+        link speed.  Buffers grow as needed."""
         import torch
+        with warnings.catch_warnings():  # read-only request bytes are only read here
+            warnings.filterwarnings("ignore", message="The given NumPy array is not writable")
+            ts = [torch.from_numpy(x) for x in parts]
+        if all(t.is_pinned() for t in ts):
+            dev = self.dev_staging[lane]
+            if dev is None or dev.numel() < total:
+                dev = torch.empty(max(total, 1 << 20) * 5 // 4, dtype=torch.uint8, device=self.device)
+                self.dev_staging[lane] = dev
+            st = self.copy_streams[lane]
+            with torch.cuda.stream(st):
+                off = 0
+                for t in ts:
+                    n = t.numel()
+                    dev[off:off + n].copy_(t, non_blocking=True)
+                    off += n
+            st.synchronize()  # the lane's build reads the buffer on its own stream
+            return dev[:total]
         buf = self.staging[lane]
         if buf is None or buf.numel() < total:
             buf = torch.empty(max(total, 1 << 20) * 5 // 4, dtype=torch.uint8).pin_memory()
             self.staging[lane] = buf
-        with warnings.catch_warnings():  # read-only request bytes are only read here
-            warnings.filterwarnings("ignore", message="The given NumPy array is not writable")
-            torch.cat([torch.from_numpy(x) for x in parts], out=buf[:total])
+        torch.cat(ts, out=buf[:total])
         return buf[:total]
 
     def build(self, lane: int, data, offsets: np.ndarray):
