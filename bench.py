@@ -227,7 +227,8 @@ SERVING_WORKLOAD = ("serving stream: Poisson arrivals of strings with lognormal 
                     "20% Zipf(1.1) byte text with copied blocks; 2 lanes, merged into a device-resident grammar")
 
 
-def run_serving(hf, device: int, capacity_gbs: float, count: int = 300, loads=(0.25, 0.5, 0.8)) -> dict:
+def run_serving(hf, device: int, capacity_gbs: float, count: int = 300, loads=(0.25, 0.5, 0.8),
+                mode: str = "merge") -> dict:
     """The serving loop on seeded streams, arrivals paced so that the offered
     input rate is ``load`` times ``capacity_gbs``: p50 / p99 latency and the
     input GB/s from first arrival to last completion, per load.  One server
@@ -245,7 +246,7 @@ def run_serving(hf, device: int, capacity_gbs: float, count: int = 300, loads=(0
         return stream
 
     backend = serving.CudaBackend(hf, device=device, lanes=2)
-    srv = serving.Server(backend, lanes=2, max_batch_bytes=192 << 20)
+    srv = serving.Server(backend, lanes=2, max_batch_bytes=192 << 20, mode=mode)
     srv.start()
     warm = serving.replay(srv, make(50), time_scale=1e-4)
     srv.drain(warm, timeout=600)
@@ -263,12 +264,13 @@ def run_serving(hf, device: int, capacity_gbs: float, count: int = 300, loads=(0
                      "gbs": st.get("gbs"), "p50_ms": 1e3 * st["p50_s"] if "p50_s" in st else None,
                      "p99_ms": 1e3 * st["p99_s"] if "p99_s" in st else None, "batches": len(ph),
                      "errors": len(srv.errors) - e0 + (0 if ok else 1),
-                     "batch_ms": {k: 1e3 * float(np.mean([p[k] for p in ph])) for k in ("gather", "build", "roots", "merge")}
+                     "batch_ms": {k: 1e3 * float(np.mean([p.get(k, 0.0) for p in ph]))
+                                  for k in ("gather", "build", "roots", "merge", "wait")}
                      if ph else None,
                      "builds_redone": sum(p.get("redone", 0) for p in ph),
                      "table_regrowths": sum(p.get("retries", 0) for p in ph)})
     srv.stop()
-    return {"workload": SERVING_WORKLOAD, "max_batch_mb": 192, "lanes": 2,
+    return {"workload": SERVING_WORKLOAD, "max_batch_mb": 192, "lanes": 2, "mode": mode,
             "warmup": f"{count} requests of another seed", "resident_strings": backend.size(srv.resident),
             "runs": runs}
 

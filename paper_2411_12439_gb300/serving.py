@@ -126,6 +126,15 @@ class CudaBackend:
         self.res_ctx.merge(resident, g)
         return resident
 
+    def build_into(self, resident, data, offsets):
+        """The batch parsed against the resident grammar (App. A.2), on the
+        context that owns it."""
+        self.res_ctx.build_into(resident, data, offsets)
+
+    def roots_of(self, g, j0: int, count: int):
+        lv, _, fp = g.roots(j0, count)
+        return lv, fp
+
     def size(self, g) -> int:
         return g.shape[0]
 
@@ -141,10 +150,17 @@ class CudaBackend:
 class Server:
     """Continuous-batching request loop over a grammar kept resident on the
     device.  ``submit`` may be called from any thread; ``start`` runs the
-    lanes in background threads, ``stop`` ends them after the pending work."""
+    lanes in background threads, ``stop`` ends them after the pending work.
+    ``mode``: "merge" builds each batch on its lane (lanes in parallel) and
+    merges it into the resident grammar (MergeGrams, one at a time);
+    "resident" parses each batch against the resident grammar itself
+    (App. A.2, one at a time) after gathering it on its lane."""
 
     def __init__(self, backend, lanes: int = 2, max_batch_bytes: int = 64 << 20, mem_factor: float = 12.0,
-                 budget_bytes: int | None = None, budget_fraction: float = 0.5):
+                 budget_bytes: int | None = None, budget_fraction: float = 0.5, mode: str = "merge"):
+        if mode not in ("merge", "resident"):
+            raise ValueError("mode is 'merge' or 'resident'")
+        self.mode = mode
         self.backend = backend
         self.lanes = lanes
         self.max_batch_bytes = max_batch_bytes
@@ -234,17 +250,29 @@ class Server:
                 np.cumsum([r.n for r in batch], out=offsets[1:])
                 data = self.backend.gather(lane, [r.data for r in batch], int(offsets[-1]))
                 ta = time.perf_counter()
-                g = self.backend.build(lane, data, offsets)
-                tb = time.perf_counter()
-                levels, fps = self.backend.roots(lane, g)
-                tc = time.perf_counter()
-                with self._merge_lock:
-                    base = self.backend.size(self.resident)
-                    self.resident = self.backend.merge(self.resident, g)
-                self.backend.free(g)
-                t1 = time.perf_counter()
-                ph = {"gather": ta - t0, "build": tb - ta, "roots": tc - tb, "merge": t1 - tc}
-                ph.update(self.backend.build_info(lane))
+                if self.mode == "resident":
+                    # parse against the resident grammar itself: new rules are
+                    # appended to it, no merge step (one batch at a time)
+                    with self._merge_lock:
+                        tq = time.perf_counter()
+                        base = self.backend.size(self.resident)
+                        self.backend.build_into(self.resident, data, offsets)
+                        tb = time.perf_counter()
+                        levels, fps = self.backend.roots_of(self.resident, base, len(batch))
+                    tc = t1 = time.perf_counter()
+                    ph = {"gather": ta - t0, "build": tb - tq, "roots": tc - tb, "merge": 0.0, "wait": tq - ta}
+                else:
+                    g = self.backend.build(lane, data, offsets)
+                    tb = time.perf_counter()
+                    levels, fps = self.backend.roots(lane, g)
+                    tc = time.perf_counter()
+                    with self._merge_lock:
+                        base = self.backend.size(self.resident)
+                        self.resident = self.backend.merge(self.resident, g)
+                    self.backend.free(g)
+                    t1 = time.perf_counter()
+                    ph = {"gather": ta - t0, "build": tb - ta, "roots": tc - tb, "merge": t1 - tc}
+                    ph.update(self.backend.build_info(lane))
                 self.phases.append(ph)
                 for j, r in enumerate(batch):
                     r.result = (int(levels[j]), int(fps[j]))

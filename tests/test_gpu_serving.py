@@ -30,14 +30,18 @@ def _stream(seed, count):
     return out
 
 
-def test_serving_alone_and_in_the_mix(hf):
+@pytest.mark.parametrize("mode", ["merge", "resident"])
+def test_serving_alone_and_in_the_mix(hf, mode):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2411_12439_gb300 import Context, serving
     stream = _stream(21, 36)
+    if mode == "resident":  # requests received into page-locked memory: the device-side gather
+        for item in stream:
+            item.data = torch.from_numpy(np.ascontiguousarray(item.data)).pin_memory().numpy()
     backend = serving.CudaBackend(hf, device=0, lanes=2)
-    srv = serving.Server(backend, lanes=2, max_batch_bytes=3 << 20)
+    srv = serving.Server(backend, lanes=2, max_batch_bytes=3 << 20, mode=mode)
     srv.start()
     reqs = serving.replay(srv, stream)
     assert srv.drain(reqs, timeout=300)
