@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lcg.h"
 #include "lcg_internal.h"
 
@@ -245,6 +247,19 @@ LevelHash level_hash(const lcg_ctx* ctx, u32 i) {
 struct Retry {};
 
 void destroy_graph(lcg_ctx* ctx);
+
+// NVTX range for profilers (a no-op when no tool is attached): calls, rounds.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    Range(const char* what, u32 i) {
+        char b[48];
+        std::snprintf(b, sizeof(b), "%s %u", what, i);
+        nvtxRangePushA(b);
+    }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 void ensure_lb(lcg_ctx* ctx, void** lb, u64* have, u64 tiles, size_t bytes) {
     if (tiles <= *have) return;
@@ -568,6 +583,7 @@ void set_table(RoundArgs& a, RoundBufs& b) {
 
 // Parse: tile strings, k_parse, tile scan, strings.
 void enqueue_parse(lcg_ctx* ctx, RoundArgs& a, u64 n_for_bytes) {
+    const Range range("parse, round", a.level);
     int ht = kt_begin(ctx, "k_tile_strings", 4.0 * (double)a.tiles_bound, a.level);
     ck(ctx, launch_tile_strings(a, ctx->st), "k_tile_strings");
     kt_end(ctx, ht);
@@ -598,6 +614,7 @@ void enqueue_parse(lcg_ctx* ctx, RoundArgs& a, u64 n_for_bytes) {
 
 // Naming and rewrite: mark, popcount scan, rank, length scan, rules, rewrite.
 void enqueue_naming(lcg_ctx* ctx, RoundArgs& a, RoundBufs& b, double g_bytes, double G_bytes, double P_bytes) {
+    const Range range("naming, round", a.level);
     a.first_bits = b.first_bits;
     a.first_prefix = b.first_prefix;
     a.slot_r = b.slot_r;
@@ -1826,6 +1843,7 @@ int lcg_last_kernel_times(const lcg_ctx* ctx, lcg_kernel_time* out, uint32_t cap
 int lcg_build(lcg_ctx* ctx, const uint8_t* data, const uint64_t* offsets, uint32_t k, int data_on_device,
               lcg_grammar** out) {
     if (!ctx || !out) return LCG_EINVAL;
+    const Range range("lcg_build");
     *out = nullptr;
     lcg_grammar* G = nullptr;
     LCG_GUARD_BEGIN
@@ -1925,6 +1943,7 @@ int lcg_build(lcg_ctx* ctx, const uint8_t* data, const uint64_t* offsets, uint32
 int lcg_build_into(lcg_ctx* ctx, lcg_grammar* resident, const uint8_t* data, const uint64_t* offsets, uint32_t k,
                    int data_on_device) {
     if (!ctx || !resident) return LCG_EINVAL;
+    const Range range("lcg_build_into");
     if (resident->tag != ctx->tag) {
         ctx->err = "resident grammar of another hash family";
         return LCG_EMISMATCH;
@@ -1942,6 +1961,7 @@ int lcg_build_into(lcg_ctx* ctx, lcg_grammar* resident, const uint8_t* data, con
 
 int lcg_merge(lcg_ctx* ctx, lcg_grammar* a, const lcg_grammar* b) {
     if (!ctx || !a || !b) return LCG_EINVAL;
+    const Range range("lcg_merge");
     LCG_GUARD_BEGIN
     ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
     kt_reset(ctx);
@@ -1955,6 +1975,7 @@ int lcg_merge(lcg_ctx* ctx, lcg_grammar* a, const lcg_grammar* b) {
 int lcg_decompress(lcg_ctx* ctx, const lcg_grammar* G, uint32_t j, uint8_t* out, uint64_t cap, uint64_t* out_len,
                    int out_on_device) {
     if (!ctx || !G || !out_len) return LCG_EINVAL;
+    const Range range("lcg_decompress");
     LCG_GUARD_BEGIN
     ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
     decompress(ctx, G, j, out, cap, out_len, out_on_device);
@@ -2233,6 +2254,7 @@ void lcg_grammar_free(lcg_grammar* G) { free_grammar_now(G); }
 int lcg_postprocess(lcg_ctx* ctx, const lcg_grammar* G, lcg_pp** out) {
     if (!ctx || !G || !out) return LCG_EINVAL;
     *out = nullptr;
+    const Range range("lcg_postprocess");
     LCG_GUARD_BEGIN
     ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
     fail_if(ctx, G->device != ctx->device, LCG_EINVAL, "grammar on another device");

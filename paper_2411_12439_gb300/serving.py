@@ -138,6 +138,12 @@ class CudaBackend:
     def size(self, g) -> int:
         return g.shape[0]
 
+    def pack(self, g) -> np.ndarray:
+        return np.asarray(g.export_packed())
+
+    def unpack(self, buf):
+        return self.res_ctx.import_packed(np.ascontiguousarray(buf, dtype=np.uint8))
+
     def free(self, g):
         g.free()
 
@@ -189,6 +195,21 @@ class Server:
             self._pending.append(r)
             self._cv.notify_all()
         return r
+
+    # -- checkpoint -----------------------------------------------------------
+    def snapshot(self) -> np.ndarray:
+        """The resident grammar in its packed form (lcg_export_packed layout),
+        taken between merges: a checkpoint of everything served so far."""
+        with self._merge_lock:
+            return self.backend.pack(self.resident)
+
+    def restore(self, buf) -> None:
+        """Continue from a snapshot: the resident grammar becomes the packed
+        grammar ``buf`` (later requests get indexes after its strings)."""
+        g = self.backend.unpack(buf)
+        with self._merge_lock:
+            old, self.resident = self.resident, g
+        self.backend.free(old)
 
     # -- lanes ----------------------------------------------------------------
     def start(self):

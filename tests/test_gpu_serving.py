@@ -62,3 +62,30 @@ def test_serving_alone_and_in_the_mix(hf, mode):
         assert srv.resident.decompress(r.index) == r.data.tobytes()
     st = serving.latency_stats(reqs)
     assert st["requests"] == len(reqs) and st["p99_s"] >= st["p50_s"] > 0
+
+
+def test_snapshot_restore_on_the_gpu(hf):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_12439_gb300 import serving
+    stream = _stream(23, 16)
+    backend = serving.CudaBackend(hf, device=0, lanes=2)
+    first = serving.Server(backend, lanes=2, max_batch_bytes=3 << 20)
+    first.start()
+    a = serving.replay(first, stream[:8])
+    assert first.drain(a, timeout=300)
+    first.stop()
+    snap = first.snapshot()
+    second = serving.Server(serving.CudaBackend(hf, device=0, lanes=2), lanes=2, max_batch_bytes=3 << 20)
+    second.restore(snap)
+    second.start()
+    b = serving.replay(second, stream[8:])
+    assert second.drain(b, timeout=300)
+    second.stop()
+    assert not first.errors and not second.errors
+    order = sorted(a, key=lambda r: r.index) + sorted(b, key=lambda r: r.index)
+    assert [r.index for r in order] == list(range(len(order)))
+    want = O.build(li.from_strings([r.data for r in order]), hf).export()
+    assert O.grammars_equal(second.resident.export(), want)
+

@@ -51,6 +51,14 @@ class OracleBackend:
     def memory_budget(self, fraction):
         return 1 << 40
 
+    def pack(self, g):
+        from paper_2411_12439_gb300 import sharding
+        return sharding.pack(g.export())
+
+    def unpack(self, buf):
+        from paper_2411_12439_gb300 import sharding
+        return O.from_export(sharding.unpack(buf), self.tag)
+
 
 def _requests(seed, count):
     rng = np.random.default_rng(seed)
@@ -130,3 +138,27 @@ def test_empty_request_fails_alone(hf):
     srv = serving.Server(OracleBackend(hf), lanes=1)
     r = srv.submit(b"")
     assert r.wait(1) and r.error
+
+
+def test_snapshot_and_restore(hf):
+    """A snapshot of the resident grammar, restored into a new server, lets it
+    continue: the result is the grammar of all strings in merge order."""
+    backend = OracleBackend(hf)
+    first = serving.Server(backend, lanes=1, max_batch_bytes=30_000)
+    first.start()
+    reqs = serving.replay(first, _requests(41, 8))
+    assert first.drain(reqs, timeout=120)
+    first.stop()
+    snap = first.snapshot()
+    second = serving.Server(backend, lanes=2, max_batch_bytes=30_000)
+    second.restore(snap)
+    second.start()
+    more = serving.replay(second, _requests(42, 6))
+    assert second.drain(more, timeout=120)
+    second.stop()
+    assert not first.errors and not second.errors
+    order = sorted(reqs, key=lambda r: r.index) + sorted(more, key=lambda r: r.index)
+    assert [r.index for r in order] == list(range(len(order)))
+    want = O.build(li.from_strings([r.data for r in order]), hf).export()
+    assert O.grammars_equal(second.resident.export(), want)
+
