@@ -460,6 +460,9 @@ struct RoundBufs {
     u32* slot_r = nullptr;
     u32* len_r = nullptr;
     u64* xlen = nullptr;
+    u64* mkey = nullptr;
+    u64* mval = nullptr;
+    u64* rkey = nullptr;
 };
 
 void alloc_round(lcg_ctx* ctx, RoundBufs& b, u64 n_bound, u32 kk) {
@@ -508,6 +511,9 @@ void alloc_naming(lcg_ctx* ctx, RoundBufs& b, u64 g_alloc) {
     b.slot_r = dalloc<u32>(ctx, g_alloc);
     b.len_r = dalloc<u32>(ctx, g_alloc);
     b.xlen = dalloc<u64>(ctx, g_alloc);
+    b.mkey = dalloc<u64>(ctx, 2 * g_alloc);  // 16-byte keys
+    b.mval = dalloc<u64>(ctx, g_alloc);
+    b.rkey = dalloc<u64>(ctx, 2 * g_alloc);
     ck(ctx, cudaMemsetAsync(b.first_bits, 0, nw * sizeof(u32), ctx->st), "memset bits");
 }
 
@@ -516,7 +522,7 @@ void free_round(lcg_ctx* ctx, RoundBufs& b) {
     for (void* p : {(void*)b.string_first, (void*)b.R_phr, (void*)b.R_sid, (void*)b.P_slot, (void*)b.tile_cnt,
                     (void*)b.tile_pfx, (void*)b.tile_str, (void*)b.brk, (void*)b.sbm, (void*)b.first_bits,
                     (void*)b.first_prefix,
-                    (void*)b.slot_r, (void*)b.len_r, (void*)b.xlen})
+                    (void*)b.slot_r, (void*)b.len_r, (void*)b.xlen, (void*)b.mkey, (void*)b.mval, (void*)b.rkey})
         dfree(ctx, p);
     free_table(ctx, b);
 }
@@ -620,6 +626,9 @@ void enqueue_naming(lcg_ctx* ctx, RoundArgs& a, RoundBufs& b, double g_bytes, do
     a.slot_r = b.slot_r;
     a.len_r = b.len_r;
     a.xlen = b.xlen;
+    a.mkey = b.mkey;
+    a.mval = b.mval;
+    a.rkey = b.rkey;
     a.g_alloc = b.g_alloc;
     const u64 g_grid = std::max<u64>(1, b.g_alloc);
     int h = kt_begin(ctx, "k_mark", 12.0 * g_bytes, a.level);

@@ -97,6 +97,9 @@ struct RoundArgs {
     u32* first_prefix;    // exclusive popcount prefix of its words
     u32* slot_r;          // slot of the rank-r new rule
     u32* len_r;           // its length
+    void* mkey;           // claim c: its slot's key (Key128), read once by k_mark
+    u64* mval;            // claim c: its slot's value (first occurrence)
+    void* rkey;           // key of the rank-r new rule (Key128), for k_rules
     u64* rv;              // per table slot: (F^i << 32) | rank of its rule (k_rules, read by k_rewrite)
     u64* xlen;            // exclusive prefix of len_r
     u64 g_base, G_base;   // rules / rhs symbols of level i before this round

@@ -849,9 +849,18 @@ __global__ void k_mark(const RoundArgs a) {
     if (round_halted(a)) return;
     const u64 g_new = round_gnew(a);
     const u64 keys = a.tiles_bound * (u64)kTP;  // order keys the bitmap covers
+    Key128* mkey = (Key128*)a.mkey;
     for (u64 c = blockIdx.x * (u64)blockDim.x + threadIdx.x; c < g_new; c += (u64)gridDim.x * blockDim.x) {
         const u32 s = a.claims[c];
-        const u64 m = s < a.tab_cap ? ((const Slot*)a.tab)[s].val : ~0ull;
+        u64 m = ~0ull;
+        Key128 key{0, 0};
+        if (s < a.tab_cap) {  // the slot's key and value (one sector), kept in claim order for k_rank
+            const Slot* sl = (const Slot*)a.tab + s;
+            key = sl->key;
+            m = sl->val;
+        }
+        mkey[c] = key;
+        a.mval[c] = m;
         if (m >= keys) {
             set_error(a.ds, kErrCapacity);
             continue;
@@ -916,15 +925,19 @@ __global__ void k_rank(const RoundArgs a) {
     pdl_wait();
     if (round_halted(a)) return;
     const u64 g_new = round_gnew(a);
+    const Key128* mkey = (const Key128*)a.mkey;
+    Key128* rkey = (Key128*)a.rkey;
     for (u64 c = blockIdx.x * (u64)blockDim.x + threadIdx.x; c < g_new; c += (u64)gridDim.x * blockDim.x) {
         const u32 s = a.claims[c];
-        Slot* slots = (Slot*)a.tab;
-        const u64 m = slots[s].val;
+        const u64 m = a.mval[c];  // k_mark's copy of the slot, in claim order
+        if (m >= a.tiles_bound * (u64)kTP) continue;  // k_mark flagged it
+        const Key128 key = mkey[c];
         const u32 w = (u32)(m >> 5);
         const u64 r = a.first_prefix[w] + __popc(a.first_bits[w] & ((1u << (m & 31)) - 1u));
         if (r >= g_new) { set_error(a.ds, kErrCapacity); continue; }
         a.slot_r[r] = s;
-        a.len_r[r] = (u32)key_len(slots[s].key);
+        a.len_r[r] = (u32)key_len(key);
+        rkey[r] = key;
     }
 }
 
@@ -934,10 +947,8 @@ __global__ void k_rank(const RoundArgs a) {
 template <typename T>
 __global__ void k_rules(const RoundArgs a) {
     pdl_wait();
-    constexpr bool kByte = sizeof(T) == 1;
     const T* S = (const T*)a.S;
     const ContentTable rw{(Slot*)a.rtab_w, a.rtab_w_cap};
-    Slot* slots = (Slot*)a.tab;
     if (round_halted(a)) return;
     const u64 g_new = round_gnew(a);
     const u64 G_new = *a.d_Gnew;
@@ -951,7 +962,7 @@ __global__ void k_rules(const RoundArgs a) {
             set_error(a.ds, kErrCapacity);
             continue;
         }
-        const Key128 k = slots[slot].key;
+        const Key128 k = ((const Key128*)a.rkey)[r];  // the rule's key, in rank order (k_rank)
         const u64 len = key_len(k);
         const bool hashed = key_is_hashed(k);
         const u64 off = a.G_base + a.xlen[r];
