@@ -3,19 +3,30 @@
 //
 // A round i reads the sequence T^i (bytes in round 1, uint32 ranks later) of
 // the active strings, laid out back to back with offsets soff[0..k], and the
-// fingerprints F^{i-1} of its symbols.  It runs:
-//   k_parse    per tile: symbol fingerprints, RandLMSPar break bits
-//              (Eq. rand_types), the tile's phrase count through a decoupled
-//              look-back, and per phrase the polynomial fingerprint of
-//              Eq. fast_hash and its entry in the round's phrase table (the
-//              slot holds the smallest phrase index of the content)
+// fingerprints of its symbols (F^0 of the bytes in round 1; afterwards the
+// fingerprint stream the previous round's rewrite wrote).  It runs:
+//   k_tile_strings  per parse tile, the string holding its first position, and
+//                   the bitmap of string starts
+//   k_breaks   RandLMSPar break bits (Eq. rand_types) as a bitmap, 32
+//              positions per thread
+//   k_parse    per tile: the phrase starts (from the bitmap), a key per phrase
+//              (its symbols when short, else a hash of its Eq. fast_hash
+//              polynomial and its position) and its slot in the round's
+//              phrase table, whose value is the smallest phrase index of the
+//              content (content-confirmed, never by hash alone)
+//   k_scan2    tile phrase counts -> global phrase indices (single pass)
 //   k_strings  per-string phrase ranges; strings that became one phrase retire
 //   k_mark, k_popscan, k_rank
 //              first-occurrence naming: the first occurrences of the new
 //              phrases are marked in a bitmap over phrase indices, and a
 //              phrase's rank is the number of marks before its own
-//   k_rules    the level-i rules in rank order: rhs, rhs_off and F^i
-//   k_rewrite  T^{i+1}[p] = rank of phrase p, compacting retired strings
+//   k_scan2    rule lengths -> right-hand-side offsets
+//   k_rules    the level-i rules in rank order: rhs, rhs_off and F^i, and the
+//              (F^i, rank) pair of every table slot
+//   k_rewrite  T^{i+1}[p] = rank of phrase p and its fingerprint, compacting
+//              retired strings
+// Every kernel of the round starts with pdl_wait(): it is launched with
+// programmatic dependent launch after the one before it.
 #include "lcg_dev.cuh"
 #include "lcg_internal.h"
 #include "table.cuh"
@@ -74,17 +85,20 @@ __device__ __forceinline__ u32 string_of(const u64* soff, u32 k, u64 pos) {
 // k_parse
 // --------------------------------------------------------------------------
 //
-// The tile's symbols (and kHalo more, and one to the left) are staged in shared
-// memory.  Break bits come from warp ballots, one 32-position word per warp
-// step.  The tile's phrase count goes through the decoupled look-back, giving
-// the global index of its first phrase.  Every phrase that starts in the tile
-// is then fingerprinted (Horner over the staged fingerprints) and looked up:
-// first in the resident level (when parsing against a resident grammar), then
-// in the round's table.  In byte rounds the phrases of a tile are first
-// deduplicated in a shared table keyed by their packed bytes, so that one
-// occurrence per tile and content goes to the global table.  New entries
+// Persistent blocks take tiles of kTP positions.  A tile's symbols (and kHalo
+// more) and its words of the break bitmap are staged in shared memory (byte
+// rounds read the next tile's into registers while parsing the current one);
+// the phrase starts are listed in order by a block scan.  Each phrase gets a
+// key: its symbols packed exactly when they fit in 124 bits, else a hash of
+// its polynomial fingerprint H (Eq. fast_hash) with its length and position,
+// confirmed by comparing contents.  It is looked up first in the resident
+// level (when parsing against a resident grammar), then in the round's table,
+// where a new content is claimed.  In byte rounds a per-block cache of packed
+// phrases (kept across the block's tiles) answers most lookups; the phrases
+// that miss are queued and looked up together, with full warps.  The slot of
+// phrase q of tile t goes to P_slot[t * kTP + q] (its order key); new entries
 // (claims) are listed in shared memory and appended to the round's claim list
-// once per block.
+// every few tiles.
 
 constexpr int kParseThreads = 256;
 constexpr int kTP = 2048;          // positions per parse tile
