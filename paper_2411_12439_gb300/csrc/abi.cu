@@ -1,6 +1,8 @@
-// C ABI of the library (include/lcg.h): contexts, the BuildGram round driver,
-// MergeGrams, expansion and export.  Host code only orchestrates: every step
-// of the method runs in the kernels of parse.cu and grammar.cu.
+// C ABI of the library (include/lcg.h): contexts, the BuildGram round driver
+// (rounds enqueued without host synchronisation, and their CUDA graph),
+// MergeGrams, expansion, export / import and post-processing.  Host code only
+// orchestrates: every step of the method runs in the kernels of parse.cu,
+// grammar.cu and post.cu.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>

@@ -1,7 +1,8 @@
 // Device-side building blocks shared by the kernels of the library:
-// arithmetic modulo the Mersenne prime 2^61-1, the phrase table, the
-// decoupled look-back used by the single-pass scans, and the device status
-// word through which bounded waits report failure.
+// arithmetic modulo the Mersenne prime 2^61-1, the decoupled look-back used by
+// the single-pass scans, the device status word through which bounded waits
+// report failure, and the wait of programmatic dependent launch.  (The phrase
+// table is in table.cuh.)
 #pragma once
 
 #include <cstdint>
