@@ -55,8 +55,8 @@ def parse_args():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-graph", action="store_true", help="time the builds as separate launches")
     p.add_argument("--no-postprocess", action="store_true")
-    p.add_argument("--e2e-steps", type=int, default=6)
-    p.add_argument("--e2e-streams", type=int, default=2, help="contexts (streams, host threads) of the e2e steps")
+    p.add_argument("--e2e-steps", type=int, default=12)
+    p.add_argument("--e2e-streams", type=int, default=3, help="contexts (streams, host threads) of the e2e steps")
     p.add_argument("--profile-builds", type=int, default=0,
                    help="only run this many batched builds of the workload and exit (for profiler captures)")
     p.add_argument("--profile-strings", type=int, default=0,
