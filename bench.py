@@ -227,7 +227,7 @@ SERVING_WORKLOAD = ("serving stream: Poisson arrivals of strings with lognormal 
                     "20% Zipf(1.1) byte text with copied blocks; 2 lanes, merged into a device-resident grammar")
 
 
-def run_serving(hf, device: int, capacity_gbs: float, count: int = 300, loads=(0.25, 0.5, 0.8),
+def run_serving(hf, device: int, capacity_gbs: float, count: int = 300, loads=(0.1, 0.25, 0.5),
                 mode: str = "merge") -> dict:
     """The serving loop on seeded streams, arrivals paced so that the offered
     input rate is ``load`` times ``capacity_gbs``: p50 / p99 latency and the
