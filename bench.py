@@ -374,7 +374,8 @@ def run_ours(args):
         ctx.build(d, coll.offsets).free()
         rs = ctx.last_build_stats()["per_round"]
         if per_round is None or len(per_round) != len(rs):
-            per_round = [{"symbols": r["n"], "bytes_per_symbol": 1 if i == 0 else 4, "ms": [], "parse_ms": []}
+            per_round = [{"symbols": r["n"], "bytes_per_symbol": 1 if i == 0 else 4, "phrases": r["phrases"],
+                          "g": r["g"], "G": r["G"], "ms": [], "parse_ms": []}
                          for i, r in enumerate(rs)]
         for pr, r in zip(per_round, rs):
             pr["ms"].append(r["round_ms"])
@@ -388,11 +389,18 @@ def run_ours(args):
     ctx.set_kernel_timing(0)
     value = world * coll.n / (ms / 1e3) / 1e9
     rounds_line = []
+    peak_gbs, _ = measured_peak()
     for i, pr in enumerate(per_round or []):
         rms = float(np.median(pr["ms"]))
+        # algorithmic bytes of the round: its sequence read (bytes in round 1;
+        # ranks and their fingerprints later), the next sequence and its
+        # fingerprints written, and the new rules (rhs, offsets, F)
+        alg = (pr["symbols"] * (1 if i == 0 else 8) + 8 * pr["phrases"] + 4 * pr["G"] + 12 * pr["g"])
         rounds_line.append({"round": i + 1, "symbols": int(pr["symbols"]), "ms": rms,
                             "parse_ms": float(np.median(pr["parse_ms"])),
-                            "gbs": pr["symbols"] * pr["bytes_per_symbol"] / (rms / 1e3) / 1e9 if rms > 0 else None})
+                            "gbs": pr["symbols"] * pr["bytes_per_symbol"] / (rms / 1e3) / 1e9 if rms > 0 else None,
+                            "alg_bytes": int(alg),
+                            "hbm_frac": alg / (rms / 1e3) / 1e9 / peak_gbs if rms > 0 else None})
 
     # ---- post-processing of the batch's grammar: run-length rules, then Simp
     post = None
