@@ -530,6 +530,11 @@ def run_ours(args):
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roofline,
         "cpu_baseline": cpu, "plain": plain, "serving": serving_line,
         "rounds": rounds_line, "postprocess": post,
+        "path_roofline": ({"alg_bytes_per_step": sum(r["alg_bytes"] for r in rounds_line),
+                           "gbs": sum(r["alg_bytes"] for r in rounds_line) / (ms / 1e3) / 1e9,
+                           "frac": sum(r["alg_bytes"] for r in rounds_line) / (ms / 1e3) / 1e9 / measured_peak()[0],
+                           "note": "all rounds' algorithmic bytes over the timed step (HBM peak as in roofline)"}
+                          if rounds_line else None),
         "kernels": {k: {"launches": v["launches"] // v["builds"], "ms_per_step": v["ms"] / v["builds"]}
                     for k, v in sorted(breakdown.items(), key=lambda kv: -kv[1]["ms"])},
     }
