@@ -11,7 +11,8 @@ throughput with the inputs resident in HBM; ``e2e`` is the same metric through
 the public API from pinned host memory, with the grammar copied back to the
 host every step; ``roofline`` rates the kernel with the largest device time
 against the measured HBM bandwidth; ``cpu_baseline`` times the CPU oracle on a
-bounded sample of the same workload; ``plain`` is the one-string-at-a-time form
+bounded sample of the same workload, on one thread and (``cpu_baseline_threaded``)
+on every host core with the parts merged; ``plain`` is the one-string-at-a-time form
 (each string parsed against the growing resident grammar); ``rounds`` gives per
 round the symbols parsed, the device time of all its kernels and the GB/s of
 its sequence (1-byte symbols in round 1, 4-byte ranks afterwards).
@@ -186,6 +187,29 @@ def cpu_baseline(coll, hf, target_s: float = 12.0):
     dt = time.perf_counter() - t
     return {"value": sample.n / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
             "sample": f"first {take} of {coll.k} strings ({sample.n / 1e6:.1f} MB), one lcg oracle build, 1 thread",
+            "seconds": dt}
+
+
+def cpu_baseline_threaded(coll, hf, rate_1t: float, target_s: float = 10.0):
+    """The oracle on every host core, as the paper's implementation runs in
+    parallel: contiguous parts of a bounded sample, one oracle build per
+    thread, merged in a tree by the oracle's MergeGrams (the result is the
+    build of the whole sample).  ``rate_1t`` (bytes/s of one thread) sizes the
+    sample to about ``target_s`` seconds."""
+    from oracle import oracle as O
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    per = coll.n / coll.k
+    take = max(min(coll.k, cores), min(coll.k, int(target_s * rate_1t * cores / per)))
+    sample = coll.subset(range(take))
+    subs = O.split(sample, cores)
+    t = time.perf_counter()
+    g = O.build_parts(subs, hf)
+    dt = time.perf_counter() - t
+    if g.k != take:
+        raise RuntimeError("threaded oracle lost strings")
+    return {"value": sample.n / dt / 1e9, "unit": "GB/s", "cores": len(subs), "kind": "oracle",
+            "sample": f"first {take} of {coll.k} strings ({sample.n / 1e6:.1f} MB) in {len(subs)} contiguous parts, "
+                      f"one oracle build per thread, merged by the oracle MergeGrams in a tree",
             "seconds": dt}
 
 
@@ -511,9 +535,10 @@ def run_ours(args):
 
     if rank != 0:
         return 0
-    cpu = None
+    cpu = cpu_threaded = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(coll, hf)
+        cpu_threaded = cpu_baseline_threaded(coll, hf, cpu["value"] * 1e9)
     serving_line = None
     if world == 1 and not args.no_serving:
         serving_line = run_serving(hf, local, value)
@@ -528,7 +553,7 @@ def run_ours(args):
                                   else f"graph modes of the timed builds: {graph_modes}"),
                    "parallelism": f"dp{world}" if world > 1 else "single GPU"},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roofline,
-        "cpu_baseline": cpu, "plain": plain, "serving": serving_line,
+        "cpu_baseline": cpu, "cpu_baseline_threaded": cpu_threaded, "plain": plain, "serving": serving_line,
         "rounds": rounds_line, "postprocess": post,
         "path_roofline": ({"alg_bytes_per_step": sum(r["alg_bytes"] for r in rounds_line),
                            "gbs": sum(r["alg_bytes"] for r in rounds_line) / (ms / 1e3) / 1e9,

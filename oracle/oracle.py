@@ -175,6 +175,38 @@ def build(coll, hf) -> Grammar:
     return Grammar(h)
 
 
+def build_parallel(coll, hf, threads: int) -> Grammar:
+    """BuildGram over ``threads`` contiguous parts of the collection, one
+    grammar per host thread, then MergeGrams of neighbouring parts in a tree
+    until one grammar is left: the parallel construction of the paper's
+    implementation (PBuildGram, appendix "Parallel grammar construction"),
+    without its memory threshold.  Stability (Def. 1) and the merge of
+    Sec. 3.6 make the result equal to ``build(coll, hf)``; the C calls release
+    the interpreter lock, so the parts run on separate cores."""
+    return build_parts(split(coll, threads), hf)
+
+
+def split(coll, parts: int) -> list:
+    """``parts`` contiguous, non-empty sub-collections, in string order."""
+    parts = min(max(1, int(parts)), coll.k)
+    cuts = [coll.k * t // parts for t in range(parts + 1)]
+    return [coll.subset(range(cuts[t], cuts[t + 1])) for t in range(parts)]
+
+
+def build_parts(subs: list, hf) -> Grammar:
+    """BuildGram of each sub-collection on its own thread, then the tree of
+    MergeGrams in order (see ``build_parallel``)."""
+    from concurrent.futures import ThreadPoolExecutor
+    _load()
+    with ThreadPoolExecutor(len(subs)) as ex:
+        gs = list(ex.map(lambda s: build(s, hf), subs))
+        while len(gs) > 1:
+            pairs = [(gs[t], gs[t + 1]) for t in range(0, len(gs) - 1, 2)]
+            merged = list(ex.map(lambda ab: ab[0].merge(ab[1]), pairs))
+            gs = merged + ([gs[-1]] if len(gs) % 2 else [])
+    return gs[0]
+
+
 def breaks(f) -> np.ndarray:
     """Phrase starts of one string given its fingerprint sequence (Eq. rand_types)."""
     lib = _load()

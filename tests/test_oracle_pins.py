@@ -291,6 +291,17 @@ def test_merge_fold_and_associativity(hf):
     assert O.grammars_equal(left.export(), whole)
 
 
+@pytest.mark.parametrize("threads", [1, 2, 3, 5, 8, 16])
+def test_parallel_build_equals_build(hf, threads):
+    """The threaded construction (parts built on separate threads, merged in a
+    tree) is the build of the whole collection, for any number of parts,
+    including more threads than strings."""
+    rng = np.random.default_rng(21)
+    strings = [li.random_dna(rng, int(rng.integers(1, 3000))).tobytes() for _ in range(9)]
+    coll = li.from_strings(strings)
+    assert O.grammars_equal(O.build_parallel(coll, hf, threads).export(), O.build(coll, hf).export())
+
+
 def test_merge_refuses_other_hash_family(hf):
     g1 = O.build(li.from_strings([b"ACGTACGT"]), hf)
     g2 = O.build(li.from_strings([b"ACGTACGT"]), li.hash_family(seed=99))
