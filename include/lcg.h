@@ -283,6 +283,49 @@ int lcg_export_packed(lcg_ctx* ctx, const lcg_grammar* G, void* out, uint64_t ca
  * aligned), with the checks of lcg_import; an F0 other than this context's
  * gives LCG_EMISMATCH, a malformed buffer LCG_EINVAL.  Blocking. */
 int lcg_import_packed(lcg_ctx* ctx, const void* buf, uint64_t size, lcg_grammar** out);
+
+/* ---- VByte (Sec. 4, resource usage: grammar symbols stored with VBytes
+ * instead of 32-bit cells) ----
+ *
+ * A value (< 2^32) is cut into groups of 7 bits, least significant group
+ * first, one group per byte; the high bit of a byte is set when another byte
+ * of the same value follows (the LEB128 / varint layout).  A value takes
+ * 1 to 5 bytes.
+ *
+ * lcg_vbyte_encode: the VByte stream of the n values of the DEVICE array
+ * `in`, written to the DEVICE buffer `out` of `cap` bytes; *out_bytes gets the
+ * stream's length (also when `cap` is too small, which gives LCG_EINVAL and
+ * writes nothing).  Blocking.
+ * lcg_vbyte_decode: exactly `n` values from the `nbytes`-byte DEVICE stream
+ * `in` into the DEVICE array `out`.  A stream that ends inside a value, holds a
+ * value of more than 32 bits or 5 bytes, or holds another number of values
+ * gives LCG_EINVAL (the output is then undefined).  Blocking. */
+int lcg_vbyte_encode(lcg_ctx* ctx, const uint32_t* in, uint64_t n, uint8_t* out, uint64_t cap, uint64_t* out_bytes);
+int lcg_vbyte_decode(lcg_ctx* ctx, const uint8_t* in, uint64_t nbytes, uint32_t* out, uint64_t n);
+
+/* The VByte form of a grammar: the packed form with every level's rule
+ * lengths and right-hand sides in VByte.
+ * Layout (little-endian; every section starts at a multiple of 8 bytes and
+ * is zero-padded):
+ *   u64 magic 0x4C434756, u64 k, u64 nlevels,
+ *   per level: u64 g, u64 G, u64 bytes of the lengths, u64 bytes of the symbols;
+ *   per level: VByte of |rhs(X)| for the g rules in rank order,
+ *              VByte of the G right-hand-side symbols, u32 F[g];
+ *   u32 c_level[k], u32 c_rank[k], u32 F0[256].
+ * lcg_vbyte_size: its size in bytes (reads the grammar on the device;
+ * blocking).
+ * lcg_export_vbyte: writes it into `out` (`cap` bytes, 8-byte aligned; a
+ * DEVICE buffer when out_on_device, else HOST memory, page-locked for speed);
+ * *bytes (optional) gets the size.  LCG_EINVAL when the buffer is too small or
+ * misaligned.  Blocking.
+ * lcg_import_vbyte: a device grammar from a VByte form of `size` bytes (a
+ * DEVICE buffer when buf_on_device, else HOST memory; 8-byte aligned), with
+ * the checks of lcg_import: a malformed buffer or stream gives LCG_EINVAL,
+ * fingerprints or F0 of another hash family LCG_EMISMATCH.  Blocking. */
+int lcg_vbyte_size(lcg_ctx* ctx, const lcg_grammar* G, uint64_t* bytes);
+int lcg_export_vbyte(lcg_ctx* ctx, const lcg_grammar* G, void* out, uint64_t cap, int out_on_device,
+                     uint64_t* bytes);
+int lcg_import_vbyte(lcg_ctx* ctx, const void* buf, uint64_t size, int buf_on_device, lcg_grammar** out);
 /* Release a grammar (NULL is ignored).  While the context that created it
  * exists, the device memory returns to the pool in the order of that
  * context's stream, so later calls of the context reuse it at no cost; after

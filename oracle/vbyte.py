@@ -18,7 +18,9 @@ at a multiple of 8 bytes and is zero-padded):
     per level: VByte of |rhs(X)| for the g rules in rank order,
                VByte of the G right-hand-side symbols, u32 F[g];
     u32 c_level[k], u32 c_rank[k], u32 F0[256].
-Everything here is plain Python / numpy, one value at a time.
+``encode`` / ``decode`` take one value at a time in plain Python; ``encode_np``
+/ ``decode_np`` state the same definition over numpy arrays, one byte
+position at a time, and are checked against them.
 """
 from __future__ import annotations
 
@@ -79,6 +81,52 @@ def decode(buf: bytes, count: int | None = None) -> list:
     return vals
 
 
+def encode_np(values) -> bytes:
+    """``encode`` over a numpy array, one byte position at a time: value p
+    starts at the sum of the lengths before it, and its byte t holds bits
+    7t .. 7t+6, with the high bit set when t is not its last byte."""
+    v = np.asarray(values, dtype=np.uint64)
+    if v.size and int(v.max()) >= 1 << 32:
+        raise ValueError("value outside 32 bits")
+    lens = np.ones(v.shape, dtype=np.int64)
+    for t in range(1, 5):
+        lens += v >= (1 << (7 * t))
+    start = np.cumsum(lens) - lens
+    out = np.zeros(int(lens.sum()), dtype=np.uint8)
+    for t in range(5):
+        m = lens > t
+        group = (v[m] >> np.uint64(7 * t)) & np.uint64(0x7F)
+        more = np.where(lens[m] > t + 1, 0x80, 0).astype(np.uint64)
+        out[start[m] + t] = (group | more).astype(np.uint8)
+    return out.tobytes()
+
+
+def decode_np(buf, count: int | None = None) -> np.ndarray:
+    """``decode`` over a numpy array: a value ends at every byte without the
+    high bit and starts after the previous such byte."""
+    b = np.frombuffer(bytes(buf), dtype=np.uint8)
+    if b.size == 0:
+        vals = np.zeros(0, dtype=np.uint32)
+    else:
+        if b[-1] & 0x80:
+            raise ValueError("stream ends inside a value")
+        ends = np.flatnonzero((b & 0x80) == 0)
+        starts = np.concatenate(([0], ends[:-1] + 1))
+        lens = ends - starts + 1
+        if lens.max() > 5:
+            raise ValueError("value of more than 32 bits")
+        acc = np.zeros(ends.shape, dtype=np.uint64)
+        for t in range(5):
+            m = lens > t
+            acc[m] |= (b[starts[m] + t] & 0x7F).astype(np.uint64) << np.uint64(7 * t)
+        if acc.size and int(acc.max()) >= 1 << 32:
+            raise ValueError("value of more than 32 bits")
+        vals = acc.astype(np.uint32)
+    if count is not None and vals.size != count:
+        raise ValueError(f"{vals.size} values, expected {count}")
+    return vals
+
+
 def _pad8(b: bytes) -> bytes:
     return b + bytes((-len(b)) % 8)
 
@@ -90,10 +138,10 @@ def export_vbyte(ex: dict) -> bytes:
     head = struct.pack("<3Q", MAGIC, k, len(levels))
     body = b""
     for L in levels:
-        ro = [int(x) for x in L["rhs_off"]]
-        lens = encode(ro[r + 1] - ro[r] for r in range(int(L["g"])))
-        syms = encode(int(x) for x in L["rhs"])
-        head += struct.pack("<4Q", int(L["g"]), ro[-1], len(lens), len(syms))
+        ro = np.asarray(L["rhs_off"], dtype=np.uint64)
+        lens = encode_np(np.diff(ro))
+        syms = encode_np(L["rhs"])
+        head += struct.pack("<4Q", int(L["g"]), int(ro[-1]), len(lens), len(syms))
         body += _pad8(lens) + _pad8(syms) + _pad8(np.asarray(L["F"], dtype="<u4").tobytes())
     body += _pad8(np.asarray(ex["c_level"], dtype="<u4").tobytes())
     body += _pad8(np.asarray(ex["c_rank"], dtype="<u4").tobytes())
@@ -122,17 +170,16 @@ def import_vbyte(buf: bytes) -> dict:
         return s
 
     for g, G, nb_len, nb_rhs in sizes:
-        lens = decode(take(nb_len), g)
-        syms = decode(take(nb_rhs), G)
+        lens = decode_np(take(nb_len), g)
+        syms = decode_np(take(nb_rhs), G)
         F = np.frombuffer(take(4 * g), dtype="<u4").astype(np.uint32)
+        if lens.size and int(lens.min()) == 0:
+            raise ValueError("empty rule")
         ro = np.zeros(g + 1, dtype=np.uint64)
-        for r, ln in enumerate(lens):
-            if ln == 0:
-                raise ValueError("empty rule")
-            ro[r + 1] = ro[r] + ln
+        np.cumsum(lens, out=ro[1:])
         if int(ro[-1]) != G:
             raise ValueError("rule lengths disagree with G")
-        levels.append({"g": g, "rhs_off": ro, "rhs": np.array(syms, dtype=np.uint32), "F": F})
+        levels.append({"g": g, "rhs_off": ro, "rhs": syms, "F": F})
     c_level = np.frombuffer(take(4 * k), dtype="<u4").astype(np.uint32)
     c_rank = np.frombuffer(take(4 * k), dtype="<u4").astype(np.uint32)
     F0 = np.frombuffer(take(4 * 256), dtype="<u4").astype(np.uint32)

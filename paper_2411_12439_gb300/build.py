@@ -19,7 +19,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "liblcg_gb300.so")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["parse.cu", "grammar.cu", "post.cu", "abi.cu"]
+SOURCES = ["parse.cu", "grammar.cu", "post.cu", "vbyte.cu", "abi.cu"]
 
 
 def _nvcc() -> str:

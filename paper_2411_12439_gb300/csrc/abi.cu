@@ -218,6 +218,7 @@ void check_device_status(lcg_ctx* ctx, const DevStatus& h) {
         case kErrTableFull: fail_if(ctx, true, LCG_ETABLE, "phrase table full"); break;
         case kErrPhraseLong: fail_if(ctx, true, LCG_EOVERFLOW, "phrase of 2^32 symbols or more"); break;
         case kErrMismatch: fail_if(ctx, true, LCG_EMISMATCH, "equal rules with different fingerprints"); break;
+        case kErrFormat: fail_if(ctx, true, LCG_EINVAL, "malformed VByte stream"); break;
         default: fail_if(ctx, true, LCG_EDEVICE, "device error " + std::to_string(h.error));
     }
 }
@@ -2258,6 +2259,331 @@ int lcg_import_packed(lcg_ctx* ctx, const void* buf, uint64_t size, lcg_grammar*
     }
     *out = G;
     return LCG_OK;
+}
+
+// ---- VByte form (Sec. 4, resource usage) ---------------------------------
+
+constexpr u64 kVbMagic = 0x4C434756ull;  // "LCGV"
+
+static int sm_count(lcg_ctx* ctx) {
+    int sms = 0;
+    ck(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "device attribute");
+    return sms > 0 ? sms : 1;
+}
+
+// Encode one column (the u32 array `vals`, or the rule lengths of `offs`)
+// into dst; the stream's length goes to *written (device).
+static void vb_encode_col(lcg_ctx* ctx, const u32* vals, const u64* offs, u64 n, u8* dst, u64* written, bool pad,
+                          u64 nb_expect) {
+    if (n == 0) return;
+    const u64 tiles = vb_encode_tiles(n);
+    ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, tiles, scan2_lb_bytes(tiles));
+    u64 grid = 0;
+    const int h = kt_begin(ctx, "k_vb_encode", (offs ? 8.0 : 4.0) * (double)n + (double)nb_expect);
+    ck(ctx, launch_vb_encode(vals, offs, n, dst, written, pad, ctx->lb2, ++ctx->epoch, ctx->ctr, ctx->ctr_val, ctx->ds,
+                             ctx->st, &grid),
+       "k_vb_encode");
+    kt_end(ctx, h);
+    ctx->ctr_val += grid;
+    ctx->launches++;
+}
+
+// Decode nb bytes into exactly n values in [lo, hi) (vals), or into the
+// offsets of n rules whose lengths sum to expect_sum (offs).
+static void vb_decode_col(lcg_ctx* ctx, const u8* src, u64 nb, u64 n, u64 lo, u64 hi, u64 expect_sum, u32* vals,
+                          u64* offs) {
+    if (nb == 0) return;
+    const u64 tiles = vb_decode_tiles(nb);
+    ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, tiles, scan2_lb_bytes(tiles));
+    u64 grid = 0;
+    const int h = kt_begin(ctx, "k_vb_decode", (double)nb + (offs ? 8.0 * (double)(n + 1) : 4.0 * (double)n));
+    ck(ctx, launch_vb_decode(src, nb, n, lo, hi, expect_sum, vals, offs, ctx->lb2, ++ctx->epoch, ctx->ctr,
+                             ctx->ctr_val, ctx->ds, ctx->st, &grid),
+       "k_vb_decode");
+    kt_end(ctx, h);
+    ctx->ctr_val += grid;
+    ctx->launches++;
+}
+
+// Bytes of each level's two VByte streams: [2 i] rule lengths, [2 i + 1]
+// right-hand sides of level i + 1.
+static std::vector<u64> vb_section_bytes(lcg_ctx* ctx, const lcg_grammar* G) {
+    const u64 nl = G->lv.size();
+    std::vector<u64> nb(2 * nl, 0);
+    if (nl == 0) return nb;
+    u64* d = dalloc<u64>(ctx, 2 * nl);
+    ck(ctx, cudaMemsetAsync(d, 0, 16 * nl, ctx->st), "memset");
+    const int sms = sm_count(ctx);
+    for (u64 i = 0; i < nl; i++) {
+        const Level& L = G->lv[i];
+        ck(ctx, launch_vb_count(nullptr, L.rhs_off, L.g, d + 2 * i, sms, ctx->st), "k_vb_count");
+        ck(ctx, launch_vb_count(L.rhs, nullptr, L.G, d + 2 * i + 1, sms, ctx->st), "k_vb_count");
+        ctx->launches += (L.g != 0) + (L.G != 0);
+    }
+    ck(ctx, cudaMemcpyAsync(nb.data(), d, 16 * nl, cudaMemcpyDeviceToHost, ctx->st), "read sizes");
+    dfree(ctx, d);
+    sync(ctx);
+    return nb;
+}
+
+static u64 vb_total_bytes(const lcg_grammar* G, const std::vector<u64>& nb) {
+    const u64 nl = G->lv.size();
+    u64 b = 24 + 32 * nl;
+    for (u64 i = 0; i < nl; i++) b += pad8(nb[2 * i]) + pad8(nb[2 * i + 1]) + pad8(4 * G->lv[i].g);
+    return b + 2 * pad8(4ull * G->k) + 4 * 256;
+}
+
+int lcg_vbyte_encode(lcg_ctx* ctx, const uint32_t* in, uint64_t n, uint8_t* out, uint64_t cap, uint64_t* out_bytes) {
+    if (!ctx || !out_bytes || (n && (!in || !out))) return LCG_EINVAL;
+    const Range range("lcg_vbyte_encode");
+    LCG_GUARD_BEGIN
+    ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    kt_reset(ctx);
+    reset_status(ctx);
+    *out_bytes = 0;
+    if (n == 0) return LCG_OK;
+    ck(ctx, cudaMemsetAsync(ctx->scratch + 1, 0, 8, ctx->st), "memset");
+    ck(ctx, launch_vb_count(in, nullptr, n, ctx->scratch + 1, sm_count(ctx), ctx->st), "k_vb_count");
+    ctx->launches++;
+    u64 nb = 0;
+    ck(ctx, cudaMemcpyAsync(&nb, ctx->scratch + 1, 8, cudaMemcpyDeviceToHost, ctx->st), "read size");
+    sync(ctx);
+    *out_bytes = nb;
+    fail_if(ctx, cap < nb, LCG_EINVAL, "output buffer too small");
+    vb_encode_col(ctx, in, nullptr, n, out, ctx->scratch + 2, false, nb);
+    u64 wrote = 0;
+    ck(ctx, cudaMemcpyAsync(&wrote, ctx->scratch + 2, 8, cudaMemcpyDeviceToHost, ctx->st), "read size");
+    const DevStatus st = read_status(ctx);
+    kt_collect(ctx);
+    check_device_status(ctx, st);
+    fail_if(ctx, wrote != nb, LCG_EDEVICE, "encoded length differs from the count");
+    return LCG_OK;
+    LCG_GUARD_END
+}
+
+int lcg_vbyte_decode(lcg_ctx* ctx, const uint8_t* in, uint64_t nbytes, uint32_t* out, uint64_t n) {
+    if (!ctx || (nbytes && !in) || (n && !out)) return LCG_EINVAL;
+    const Range range("lcg_vbyte_decode");
+    LCG_GUARD_BEGIN
+    ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    kt_reset(ctx);
+    fail_if(ctx, nbytes < n || nbytes > 5 * n, LCG_EINVAL, "stream length does not fit the value count");
+    if (n == 0) return LCG_OK;
+    reset_status(ctx);
+    vb_decode_col(ctx, in, nbytes, n, 0, 1ull << 32, 0, out, nullptr);
+    const DevStatus st = read_status(ctx);
+    kt_collect(ctx);
+    check_device_status(ctx, st);
+    return LCG_OK;
+    LCG_GUARD_END
+}
+
+int lcg_vbyte_size(lcg_ctx* ctx, const lcg_grammar* G, uint64_t* bytes) {
+    if (!ctx || !G || !bytes) return LCG_EINVAL;
+    LCG_GUARD_BEGIN
+    ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    fail_if(ctx, G->device != ctx->device, LCG_EINVAL, "grammar on another device");
+    *bytes = vb_total_bytes(G, vb_section_bytes(ctx, G));
+    return LCG_OK;
+    LCG_GUARD_END
+}
+
+int lcg_export_vbyte(lcg_ctx* ctx, const lcg_grammar* G, void* out, uint64_t cap, int out_on_device,
+                     uint64_t* bytes) {
+    if (!ctx || !G || !out) return LCG_EINVAL;
+    const Range range("lcg_export_vbyte");
+    u8* staging = nullptr;
+    u64* written = nullptr;
+    try {
+        ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+        fail_if(ctx, G->device != ctx->device, LCG_EINVAL, "grammar on another device");
+        fail_if(ctx, ((uintptr_t)out & 7) != 0, LCG_EINVAL, "VByte buffer must be 8-byte aligned");
+        kt_reset(ctx);
+        reset_status(ctx);
+        const u64 nl = G->lv.size();
+        const std::vector<u64> nb = vb_section_bytes(ctx, G);
+        const u64 total = vb_total_bytes(G, nb);
+        if (bytes) *bytes = total;
+        fail_if(ctx, cap < total, LCG_EINVAL, "VByte buffer too small");
+        u8* dst = out_on_device ? (u8*)out : (staging = dalloc<u8>(ctx, total));
+        written = dalloc<u64>(ctx, 2 * nl + 1);
+        std::vector<u64> head(3 + 4 * nl);
+        head[0] = kVbMagic;
+        head[1] = G->k;
+        head[2] = nl;
+        for (u64 i = 0; i < nl; i++) {
+            head[3 + 4 * i] = G->lv[i].g;
+            head[4 + 4 * i] = G->lv[i].G;
+            head[5 + 4 * i] = nb[2 * i];
+            head[6 + 4 * i] = nb[2 * i + 1];
+        }
+        ck(ctx, cudaMemcpyAsync(dst, head.data(), 8 * head.size(), cudaMemcpyHostToDevice, ctx->st), "header");
+        u64 pos = 8 * head.size();
+        auto copy_u32 = [&](const u32* src, u64 n) {
+            if (n) ck(ctx, cudaMemcpyAsync(dst + pos, src, 4 * n, cudaMemcpyDeviceToDevice, ctx->st), "copy");
+            if ((4 * n) & 7) ck(ctx, cudaMemsetAsync(dst + pos + 4 * n, 0, 4, ctx->st), "pad");
+            pos += pad8(4 * n);
+        };
+        for (u64 i = 0; i < nl; i++) {
+            const Level& L = G->lv[i];
+            vb_encode_col(ctx, nullptr, L.rhs_off, L.g, dst + pos, written + 2 * i, true, nb[2 * i]);
+            pos += pad8(nb[2 * i]);
+            vb_encode_col(ctx, L.rhs, nullptr, L.G, dst + pos, written + 2 * i + 1, true, nb[2 * i + 1]);
+            pos += pad8(nb[2 * i + 1]);
+            copy_u32(L.F, L.g);
+        }
+        copy_u32(G->c_level, G->k);
+        copy_u32(G->c_rank, G->k);
+        copy_u32(G->F0, 256);
+        fail_if(ctx, pos != total, LCG_EDEVICE, "VByte layout");
+        if (!out_on_device) ck(ctx, cudaMemcpyAsync(out, dst, total, cudaMemcpyDeviceToHost, ctx->st), "export");
+        std::vector<u64> wr(2 * nl);
+        if (nl) ck(ctx, cudaMemcpyAsync(wr.data(), written, 16 * nl, cudaMemcpyDeviceToHost, ctx->st), "read sizes");
+        dfree(ctx, written);
+        written = nullptr;
+        dfree(ctx, staging);
+        staging = nullptr;
+        const DevStatus st = read_status(ctx);
+        kt_collect(ctx);
+        check_device_status(ctx, st);
+        for (u64 i = 0; i < nl; i++)
+            fail_if(ctx, (G->lv[i].g && wr[2 * i] != nb[2 * i]) || (G->lv[i].G && wr[2 * i + 1] != nb[2 * i + 1]),
+                    LCG_EDEVICE, "encoded length differs from the count");
+        return LCG_OK;
+    } catch (const Fail& f) {
+        cudaStreamSynchronize(ctx->st);
+        if (written) cudaFree(written);
+        if (staging) cudaFree(staging);
+        return f.code;
+    } catch (const std::bad_alloc&) {
+        ctx->err = "host allocation failed";
+        cudaStreamSynchronize(ctx->st);
+        if (written) cudaFree(written);
+        if (staging) cudaFree(staging);
+        return LCG_ENOMEM;
+    }
+}
+
+int lcg_import_vbyte(lcg_ctx* ctx, const void* buf, uint64_t size, int buf_on_device, lcg_grammar** out) {
+    if (!ctx || !buf || !out) return LCG_EINVAL;
+    *out = nullptr;
+    const Range range("lcg_import_vbyte");
+    lcg_grammar* G = nullptr;
+    u8* staging = nullptr;
+    try {
+        ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+        kt_reset(ctx);
+        fail_if(ctx, ((uintptr_t)buf & 7) != 0, LCG_EINVAL, "VByte buffer must be 8-byte aligned");
+        fail_if(ctx, size < 24, LCG_EINVAL, "not a VByte grammar");
+        const u8* b = (const u8*)buf;
+        auto read_host = [&](void* dst, u64 off, u64 n) {
+            if (n == 0) return;
+            if (buf_on_device) {
+                ck(ctx, cudaMemcpyAsync(dst, b + off, n, cudaMemcpyDeviceToHost, ctx->st), "read");
+                sync(ctx);
+            } else {
+                std::memcpy(dst, b + off, n);
+            }
+        };
+        u64 h3[3];
+        read_host(h3, 0, 24);
+        fail_if(ctx, h3[0] != kVbMagic, LCG_EINVAL, "not a VByte grammar");
+        const u64 k = h3[1], nl = h3[2];
+        fail_if(ctx, k > 0xffffffffull || nl > 4096 || size < 24 + 32 * nl, LCG_EINVAL, "malformed VByte header");
+        fail_if(ctx, nl >= ctx->levels, LCG_ELEVELS, "grammar has more levels than the hash family has functions");
+        std::vector<u64> hd(4 * nl);
+        read_host(hd.data(), 24, 32 * nl);
+        std::vector<u64> off_len(nl), off_rhs(nl), off_F(nl);
+        u64 pos = 24 + 32 * nl;
+        for (u64 i = 0; i < nl; i++) {
+            const u64 g = hd[4 * i], Gs = hd[4 * i + 1], nbl = hd[4 * i + 2], nbr = hd[4 * i + 3];
+            fail_if(ctx, g > kMaxRank || Gs > (1ull << 40) || Gs < g || (g == 0) != (Gs == 0), LCG_EINVAL,
+                    "malformed level sizes");
+            fail_if(ctx, nbl < g || nbl > 5 * g || nbr < Gs || nbr > 5 * Gs, LCG_EINVAL,
+                    "stream lengths do not fit the level sizes");
+            off_len[i] = pos;
+            pos += pad8(nbl);
+            off_rhs[i] = pos;
+            pos += pad8(nbr);
+            off_F[i] = pos;
+            pos += pad8(4 * g);
+            fail_if(ctx, pos > size, LCG_EINVAL, "truncated");
+        }
+        const u64 off_cl = pos, off_cr = pos + pad8(4 * k), off_F0 = pos + 2 * pad8(4 * k);
+        fail_if(ctx, off_F0 + 4 * 256 != size, LCG_EINVAL, "wrong size");
+        // C entries name existing rules
+        std::vector<uint32_t> cl(k), cr(k);
+        read_host(cl.data(), off_cl, 4 * k);
+        read_host(cr.data(), off_cr, 4 * k);
+        for (u64 j = 0; j < k; j++) {
+            fail_if(ctx, cl[j] > nl, LCG_EINVAL, "C entry " + std::to_string(j) + " names a missing level");
+            const u64 lim = cl[j] == 0 ? 256 : hd[4 * (cl[j] - 1)];
+            fail_if(ctx, cr[j] >= lim, LCG_EINVAL, "C entry " + std::to_string(j) + " names a missing rule");
+        }
+        const u8* src = b;
+        if (!buf_on_device) {
+            staging = dalloc<u8>(ctx, size);
+            ck(ctx, cudaMemcpyAsync(staging, buf, size, cudaMemcpyHostToDevice, ctx->st), "upload");
+            src = staging;
+        }
+        reset_status(ctx);
+        G = new_grammar(ctx);
+        if (k) {
+            grow_c(ctx, G, (u32)k);
+            ck(ctx, cudaMemcpyAsync(G->c_level, src + off_cl, 4 * k, cudaMemcpyDeviceToDevice, ctx->st), "import");
+            ck(ctx, cudaMemcpyAsync(G->c_rank, src + off_cr, 4 * k, cudaMemcpyDeviceToDevice, ctx->st), "import");
+            G->k = (u32)k;
+        }
+        // decode every level, and check the streams before anything reads them
+        for (u64 i = 0; i < nl; i++) {
+            const u64 g = hd[4 * i], Gs = hd[4 * i + 1];
+            G->lv.emplace_back();
+            Level& L = G->lv.back();
+            grow_level(ctx, L, g, Gs);
+            const u64 prev = i == 0 ? 256 : hd[4 * (i - 1)];
+            vb_decode_col(ctx, src + off_len[i], hd[4 * i + 2], g, 1, 1ull << 32, Gs, nullptr, L.rhs_off);
+            vb_decode_col(ctx, src + off_rhs[i], hd[4 * i + 3], Gs, 0, prev, 0, L.rhs, nullptr);
+            if (g) ck(ctx, cudaMemcpyAsync(L.F, src + off_F[i], 4 * g, cudaMemcpyDeviceToDevice, ctx->st), "import");
+            L.g = g;
+            L.G = Gs;
+            L.rvalid = false;
+        }
+        DevStatus st = read_status(ctx);
+        fail_if(ctx, st.error == kErrFormat, LCG_EINVAL, "malformed VByte form");
+        check_device_status(ctx, st);
+        for (u64 i = 0; i < nl; i++) {
+            const Level& L = G->lv[i];
+            ck(ctx, launch_check_fp(L.rhs, L.rhs_off, L.g, fprev_of(G, (u32)i + 1), level_hash(ctx, (u32)i + 1), L.F,
+                                    ctx->ds, ctx->st),
+               "k_check_fp");
+            ctx->launches++;
+        }
+        uint32_t mine[256], theirs[256];
+        ck(ctx, cudaMemcpyAsync(mine, G->F0, sizeof(mine), cudaMemcpyDeviceToHost, ctx->st), "read F0");
+        ck(ctx, cudaMemcpyAsync(theirs, src + off_F0, sizeof(theirs), cudaMemcpyDeviceToHost, ctx->st), "read F0");
+        dfree(ctx, staging);
+        staging = nullptr;
+        st = read_status(ctx);
+        kt_collect(ctx);
+        fail_if(ctx, st.error == kErrMismatch, LCG_EMISMATCH,
+                "imported fingerprints differ from those of this context's hash family");
+        check_device_status(ctx, st);
+        fail_if(ctx, std::memcmp(mine, theirs, sizeof(mine)) != 0, LCG_EMISMATCH,
+                "VByte grammar: F0 of another hash family");
+        *out = G;
+        return LCG_OK;
+    } catch (const Fail& f) {
+        cudaStreamSynchronize(ctx->st);
+        if (staging) cudaFree(staging);
+        free_grammar_now(G);
+        return f.code;
+    } catch (const std::bad_alloc&) {
+        ctx->err = "host allocation failed";
+        cudaStreamSynchronize(ctx->st);
+        if (staging) cudaFree(staging);
+        free_grammar_now(G);
+        return LCG_ENOMEM;
+    }
 }
 
 void lcg_grammar_free(lcg_grammar* G) { free_grammar_now(G); }

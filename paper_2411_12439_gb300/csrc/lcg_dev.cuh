@@ -69,6 +69,7 @@ enum DevError : u32 {
     kErrRankOverflow = 5, // a level with >= 2^32 rules
     kErrCapacity = 6,     // a round outgrew the buffers it was given (rounds enqueued without a sync)
     kErrHalted = 7,       // an earlier round failed; this one did no work
+    kErrFormat = 8,       // a malformed VByte stream
 };
 
 struct DevStatus {

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstddef>
+#include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <utility>
@@ -211,5 +212,16 @@ cudaError_t launch_pp_write(const PPLevels& lv, u32 li, const u64* fin_off, u32*
                             cudaStream_t st);
 cudaError_t launch_pp_roots(const u32* c_level, const u32* c_rank, u32 k, const PPLevels& lv, u32* c_out,
                             cudaStream_t st);
+
+// VByte codec (vbyte.cu).  A column is a u32 array (`vals`) or, when `offs`
+// is given, the rule lengths offs[p + 1] - offs[p].
+cudaError_t launch_vb_count(const u32* vals, const u64* offs, u64 n, u64* total, int sms, cudaStream_t st);
+cudaError_t launch_vb_encode(const u32* vals, const u64* offs, u64 n, u8* out, u64* nbytes_out, bool pad, void* lb,
+                             u64 epoch, u64* ctr, u64 ctr_base, DevStatus* ds, cudaStream_t st, u64* grid_out);
+cudaError_t launch_vb_decode(const u8* in, u64 nb, u64 n, u64 lo, u64 hi, u64 expect_sum, u32* vals, u64* offs,
+                             void* lb, u64 epoch, u64* ctr, u64 ctr_base, DevStatus* ds, cudaStream_t st,
+                             u64* grid_out);
+u64 vb_encode_tiles(u64 n);
+u64 vb_decode_tiles(u64 nb);
 
 }  // namespace lcg

@@ -28,6 +28,7 @@ SYMBOLS = [
     "lcg_merge", "lcg_decompress", "lcg_decompress_static", "lcg_grammar_shape", "lcg_level_size", "lcg_export_level",
     "lcg_export_start", "lcg_string_roots", "lcg_import", "lcg_packed_size", "lcg_export_packed", "lcg_import_packed",
     "lcg_grammar_free", "lcg_postprocess", "lcg_pp_stats_of", "lcg_pp_export", "lcg_pp_free",
+    "lcg_vbyte_encode", "lcg_vbyte_decode", "lcg_vbyte_size", "lcg_export_vbyte", "lcg_import_vbyte",
 ]
 
 
@@ -119,6 +120,11 @@ def load(build_if_missing: bool = True):
     lib.lcg_pp_stats_of.argtypes = [P, ctypes.POINTER(PPStatsC)]
     lib.lcg_pp_export.argtypes = [P, P, P, P, P]
     lib.lcg_pp_free.argtypes = [P]
+    lib.lcg_vbyte_encode.argtypes = [P, P, U64, P, U64, ctypes.POINTER(U64)]
+    lib.lcg_vbyte_decode.argtypes = [P, P, U64, P, U64]
+    lib.lcg_vbyte_size.argtypes = [P, P, ctypes.POINTER(U64)]
+    lib.lcg_export_vbyte.argtypes = [P, P, P, U64, I, ctypes.POINTER(U64)]
+    lib.lcg_import_vbyte.argtypes = [P, P, U64, I, PP]
     lib.lcg_pp_free.restype = None
     lib.lcg_grammar_free.restype = None
     for name in SYMBOLS:
@@ -250,6 +256,46 @@ class Context:
         del keep
         return Grammar(self, h)
 
+    def import_vbyte(self, buf) -> "Grammar":
+        """lcg_import_vbyte: a device grammar from its VByte form (a uint8 numpy
+        array, or a CPU or CUDA uint8 tensor; 8-byte aligned)."""
+        ptr, on_dev, keep = _data_arg(buf)
+        n = int(buf.numel() if hasattr(buf, "numel") else len(buf))
+        h = ctypes.c_void_p(0)
+        self._check(load().lcg_import_vbyte(self._h, ptr, n, on_dev, ctypes.byref(h)))
+        del keep
+        return Grammar(self, h)
+
+    def vbyte_encode(self, values, out=None):
+        """lcg_vbyte_encode: the VByte stream of a CUDA int32/uint32 tensor
+        (values read as unsigned 32-bit) as a CUDA uint8 tensor (a view of
+        ``out`` when given)."""
+        import torch
+        if not values.is_cuda or values.dtype not in (torch.int32, torch.uint32) or not values.is_contiguous():
+            raise LCGError(-1, "values must be a contiguous 32-bit CUDA tensor")
+        n = values.numel()
+        if out is None:
+            out = torch.empty(max(5 * n, 1), dtype=torch.uint8, device=values.device)
+        ptr, on_dev, keep = _data_arg(out)
+        if not on_dev:
+            raise LCGError(-1, "lcg_vbyte_encode writes device memory")
+        nb = ctypes.c_uint64(0)
+        self._check(load().lcg_vbyte_encode(self._h, ctypes.c_void_p(values.data_ptr()), n, ptr, out.numel(),
+                                            ctypes.byref(nb)))
+        return out[:int(nb.value)]
+
+    def vbyte_decode(self, stream, n: int, out=None):
+        """lcg_vbyte_decode: ``n`` values of a VByte stream (a CUDA uint8
+        tensor) as a CUDA int32 tensor holding the unsigned 32-bit values."""
+        import torch
+        ptr, on_dev, keep = _data_arg(stream)
+        if not on_dev:
+            raise LCGError(-1, "lcg_vbyte_decode reads device memory")
+        if out is None:
+            out = torch.empty(max(n, 1), dtype=torch.int32, device=stream.device)
+        self._check(load().lcg_vbyte_decode(self._h, ptr, stream.numel(), ctypes.c_void_p(out.data_ptr()), n))
+        return out[:n]
+
     def tuning(self) -> dict:
         """lcg_get_tuning: the launch and sizing parameters of later builds."""
         t = TuningC()
@@ -378,6 +424,30 @@ class Grammar:
         self.ctx._check(load().lcg_export_packed(self.ctx._h, self._h, ptr, cap))
         del keep
         return out[:n]
+
+    def vbyte_size(self) -> int:
+        n = ctypes.c_uint64(0)
+        self.ctx._check(load().lcg_vbyte_size(self.ctx._h, self._h, ctypes.byref(n)))
+        return int(n.value)
+
+    def export_vbyte(self, out=None, device: bool = False):
+        """lcg_export_vbyte: the VByte form in one buffer: ``out`` (a uint8
+        numpy array, CPU tensor or CUDA tensor, 8-byte aligned) or a new numpy
+        array (a new CUDA tensor when ``device``); returns a view of its first
+        ``vbyte_size()`` bytes."""
+        if out is None:
+            n = self.vbyte_size()
+            if device:
+                import torch
+                out = torch.empty(n, dtype=torch.uint8, device=f"cuda:{self.ctx.device}")
+            else:
+                out = np.empty(n, dtype=np.uint8)
+        ptr, on_dev, keep = _data_arg(out)
+        cap = int(out.numel() if hasattr(out, "numel") else out.size)
+        nb = ctypes.c_uint64(0)
+        self.ctx._check(load().lcg_export_vbyte(self.ctx._h, self._h, ptr, cap, on_dev, ctypes.byref(nb)))
+        del keep
+        return out[:int(nb.value)]
 
     def decompress_static(self, j: int, out) -> int:
         """lcg_decompress_static: exp(C[j]) into the CUDA uint8 tensor ``out``

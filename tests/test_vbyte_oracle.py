@@ -53,11 +53,25 @@ def test_roundtrip_brute_and_random():
     assert V.decode(buf, len(vals)) == vals
 
 
+def test_numpy_forms_equal_loops():
+    rng = np.random.default_rng(8)
+    for n in [0, 1, 5, 1000, 30000]:
+        v = rng.integers(0, 1 << 32, size=n, dtype=np.uint64) >> rng.integers(0, 32, size=n).astype(np.uint64)
+        v = v.astype(np.uint32)
+        buf = V.encode(v.tolist())
+        assert V.encode_np(v) == buf
+        assert V.decode_np(buf, n).tolist() == V.decode(buf, n) == v.tolist()
+    for vec in _load("vbyte_vectors.json")["vectors"]:
+        assert V.encode_np([vec["value"]]) == bytes.fromhex(vec["hex"])
+
+
 @pytest.mark.parametrize("bad", ["80", "ff", "0180", "ffffffff10", "ffffffffff01", "8080808080800"])
 def test_decode_rejects_malformed(bad):
     buf = bytes.fromhex(bad if len(bad) % 2 == 0 else bad + "0")
     with pytest.raises(ValueError):
         V.decode(buf)
+    with pytest.raises(ValueError):
+        V.decode_np(buf)
 
 
 def test_decode_rejects_wrong_count():
