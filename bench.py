@@ -15,7 +15,8 @@ bounded sample of the same workload, on one thread and (``cpu_baseline_threaded`
 on every host core with the parts merged; ``plain`` is the one-string-at-a-time form
 (each string parsed against the growing resident grammar); ``rounds`` gives per
 round the symbols parsed, the device time of all its kernels and the GB/s of
-its sequence (1-byte symbols in round 1, 4-byte ranks afterwards).
+its sequence (1-byte symbols in round 1, 4-byte ranks afterwards); ``vbyte``
+measures the VByte form of the batch's grammar (sizes, export and import).
 """
 from __future__ import annotations
 
@@ -56,10 +57,14 @@ def parse_args():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-graph", action="store_true", help="time the builds as separate launches")
     p.add_argument("--no-postprocess", action="store_true")
+    p.add_argument("--no-vbyte", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=12)
     p.add_argument("--e2e-streams", type=int, default=3, help="contexts (streams, host threads) of the e2e steps")
     p.add_argument("--profile-builds", type=int, default=0,
                    help="only run this many batched builds of the workload and exit (for profiler captures)")
+    p.add_argument("--profile-vbyte", type=int, default=0,
+                   help="only build the workload's grammar once, then run this many exports and imports of its "
+                        "VByte form inside the profiler range (after --profile-warmup untimed ones) and exit")
     p.add_argument("--profile-strings", type=int, default=0,
                    help="with --profile-builds: only the first this many strings of the workload")
     p.add_argument("--write-traffic", default="",
@@ -332,6 +337,25 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
+    if args.profile_vbyte:
+        offs = coll.offsets
+        if args.profile_strings:
+            offs = offs[:min(args.profile_strings, coll.k) + 1]
+        g = ctx.build(d, offs)
+        buf = torch.empty(g.vbyte_size(), dtype=torch.uint8, device=f"cuda:{local}")
+        for _ in range(args.profile_warmup):
+            g.export_vbyte(out=buf)
+            ctx.import_vbyte(buf).free()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        for _ in range(args.profile_vbyte):
+            g.export_vbyte(out=buf)
+            ctx.import_vbyte(buf).free()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        g.free()
+        return 0
+
     if args.profile_builds:
         offs = coll.offsets
         if args.profile_strings:
@@ -444,6 +468,68 @@ def run_ours(args):
         post = {"ms": pms, "grammar_gbs": 4.0 * st["size_before"] / (pms / 1e3) / 1e9, **st,
                 "timing": "host clock around lcg_postprocess (it synchronises between levels)"}
 
+    # ---- the VByte form of the batch's grammar (rules and rule lengths in
+    #      VByte, Sec. 4 resource usage): sizes, export / import times, and the
+    #      encode / decode kernels against the HBM peak; the import of the
+    #      export must give back the same grammar
+    vbyte_line = None
+    if not args.no_vbyte:
+        g = ctx.build(d, coll.offsets)
+        packed = g.packed_size()
+        nbytes = g.vbyte_size()
+        buf = torch.empty(nbytes, dtype=torch.uint8, device=f"cuda:{local}")
+        ex_t, im_t = [], []
+        roundtrip = None
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.export_vbyte(out=buf)
+            ex_t.append(time.perf_counter() - t0)
+            t0 = time.perf_counter()
+            h = ctx.import_vbyte(buf)
+            im_t.append(time.perf_counter() - t0)
+            if roundtrip is None:
+                a, b = g.export(), h.export()
+                roundtrip = all(np.array_equal(x[key], y[key]) for x, y in zip(a["levels"], b["levels"])
+                                for key in ("rhs_off", "rhs", "F")) and len(a["levels"]) == len(b["levels"]) \
+                    and np.array_equal(a["c_rank"], b["c_rank"]) and np.array_equal(a["c_level"], b["c_level"])
+            h.free()
+        # one more pass with every launch timed, for the kernel breakdown
+        ctx.set_kernel_timing(1)
+        enc, dec = [], []
+        for _ in range(2):
+            g.export_vbyte(out=buf)
+            enc.append(ctx.last_kernel_times())
+            ctx.import_vbyte(buf).free()
+            dec.append(ctx.last_kernel_times())
+        ctx.set_kernel_timing(0)
+        head = buf[:24].cpu().numpy().view(np.uint64)
+        nl = int(head[2])
+        lv = buf[24:24 + 32 * nl].cpu().numpy().view(np.uint64).reshape(nl, 4)
+        rules_u32 = int(sum(4 * int(G_) + 8 * (int(g_) + 1) for g_, G_, _, _ in lv))
+        rules_vb = int(sum(int(a_) + int(b_) for _, _, a_, b_ in lv))
+        g.free()
+
+        def kern(recs):
+            out = {}
+            for name in recs[0]:
+                ms = float(np.median([r[name]["ms"] for r in recs]))
+                byt = recs[0][name]["bytes"]
+                gbs = byt / (ms / 1e3) / 1e9 if ms > 0 else None
+                out[name] = {"ms": ms, "launches": recs[0][name]["launches"], "alg_bytes": int(byt), "gbs": gbs,
+                             "frac": gbs / peak_gbs if gbs else None}
+            return out
+
+        vbyte_line = {"packed_bytes": packed, "vbyte_bytes": nbytes, "ratio": nbytes / packed,
+                      "rules_u32_bytes": rules_u32, "rules_vbyte_bytes": rules_vb, "rules_ratio": rules_vb / rules_u32,
+                      "export_ms": float(np.median(ex_t)) * 1e3, "import_ms": float(np.median(im_t)) * 1e3,
+                      "export_kernels": kern(enc), "import_kernels": kern(dec), "roundtrip_equal": bool(roundtrip),
+                      "timing": "host clock around lcg_export_vbyte / lcg_import_vbyte (device buffer; both "
+                                "synchronise; kernel timing off); kernels in separate calls, CUDA events per "
+                                "launch; algorithmic bytes: k_vb_write "
+                                "values read + stream written, k_vb_dwrite stream read + values written, the "
+                                "counting kernels their input read"}
+
     # ---- end to end through the public API: pinned host input, the whole
     #      grammar to a pinned host buffer in its packed form every step.
     #      Steps run on `--e2e-streams` contexts (each with its own stream and
@@ -554,7 +640,7 @@ def run_ours(args):
                    "parallelism": f"dp{world}" if world > 1 else "single GPU"},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roofline,
         "cpu_baseline": cpu, "cpu_baseline_threaded": cpu_threaded, "plain": plain, "serving": serving_line,
-        "rounds": rounds_line, "postprocess": post,
+        "rounds": rounds_line, "postprocess": post, "vbyte": vbyte_line,
         "path_roofline": ({"alg_bytes_per_step": sum(r["alg_bytes"] for r in rounds_line),
                            "gbs": sum(r["alg_bytes"] for r in rounds_line) / (ms / 1e3) / 1e9,
                            "frac": sum(r["alg_bytes"] for r in rounds_line) / (ms / 1e3) / 1e9 / measured_peak()[0],

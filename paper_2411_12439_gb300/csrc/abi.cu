@@ -2271,37 +2271,64 @@ static int sm_count(lcg_ctx* ctx) {
     return sms > 0 ? sms : 1;
 }
 
-// Encode one column (the u32 array `vals`, or the rule lengths of `offs`)
-// into dst; the stream's length goes to *written (device).
-static void vb_encode_col(lcg_ctx* ctx, const u32* vals, const u64* offs, u64 n, u8* dst, u64* written, bool pad,
-                          u64 nb_expect) {
-    if (n == 0) return;
-    const u64 tiles = vb_encode_tiles(n);
-    ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, tiles, scan2_lb_bytes(tiles));
+// Exclusive scan of `cnt` (u32) into `off` (u64); the sum goes to totals[0].
+static void vb_scan(lcg_ctx* ctx, const u32* cnt, u64 tiles, u64* off, u64* totals) {
+    if (tiles == 0) return;
     u64 grid = 0;
-    const int h = kt_begin(ctx, "k_vb_encode", (offs ? 8.0 : 4.0) * (double)n + (double)nb_expect);
-    ck(ctx, launch_vb_encode(vals, offs, n, dst, written, pad, ctx->lb2, ++ctx->epoch, ctx->ctr, ctx->ctr_val, ctx->ds,
-                             ctx->st, &grid),
-       "k_vb_encode");
+    const u64 stiles = std::max<u64>(1, scan2_tiles_for(tiles));
+    ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, stiles, scan2_lb_bytes(stiles));
+    const int h = kt_begin(ctx, "k_scan2", 12.0 * (double)tiles);
+    ck(ctx, launch_scan2(cnt, nullptr, tiles, off, nullptr, totals, ctx->lb2, ++ctx->epoch, ctx->ctr, ctx->ctr_val,
+                         ctx->ds, ctx->st, &grid),
+       "scan");
     kt_end(ctx, h);
     ctx->ctr_val += grid;
     ctx->launches++;
 }
 
-// Decode nb bytes into exactly n values in [lo, hi) (vals), or into the
-// offsets of n rules whose lengths sum to expect_sum (offs).
-static void vb_decode_col(lcg_ctx* ctx, const u8* src, u64 nb, u64 n, u64 lo, u64 hi, u64 expect_sum, u32* vals,
-                          u64* offs) {
-    if (nb == 0) return;
-    const u64 tiles = vb_decode_tiles(nb);
-    ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, tiles, scan2_lb_bytes(tiles));
-    u64 grid = 0;
-    const int h = kt_begin(ctx, "k_vb_decode", (double)nb + (offs ? 8.0 * (double)(n + 1) : 4.0 * (double)n));
-    ck(ctx, launch_vb_decode(src, nb, n, lo, hi, expect_sum, vals, offs, ctx->lb2, ++ctx->epoch, ctx->ctr,
-                             ctx->ctr_val, ctx->ds, ctx->st, &grid),
-       "k_vb_decode");
+// Encode step 1: stream bytes per tile of one column (the u32 array `vals`,
+// or the rule lengths of `offs`), scanned into tile offsets; the column's
+// stream length goes to totals[0] (device).
+static void vb_count_col(lcg_ctx* ctx, const u32* vals, const u64* offs, u64 n, u32* tile_bytes, u64* tile_off,
+                         u64* totals) {
+    const u64 tiles = vb_encode_tiles(n);
+    if (tiles == 0) return;
+    const int h = kt_begin(ctx, "k_vb_tile_bytes", (offs ? 8.0 : 4.0) * (double)n);
+    ck(ctx, launch_vb_tile_bytes(vals, offs, n, tile_bytes, ctx->st), "k_vb_tile_bytes");
     kt_end(ctx, h);
-    ctx->ctr_val += grid;
+    ctx->launches++;
+    vb_scan(ctx, tile_bytes, tiles, tile_off, totals);
+}
+
+// Encode step 2: the column's stream at dst (nb bytes in all).
+static void vb_write_col(lcg_ctx* ctx, const u32* vals, const u64* offs, u64 n, const u64* tile_off, u8* dst, bool pad,
+                         u64 nb) {
+    if (n == 0) return;
+    const int h = kt_begin(ctx, "k_vb_write", (offs ? 8.0 : 4.0) * (double)n + (double)nb);
+    ck(ctx, launch_vb_write(vals, offs, n, tile_off, dst, pad, ctx->st), "k_vb_write");
+    kt_end(ctx, h);
+    ctx->launches++;
+}
+
+// Scratch of the decode of one column: tile counts and offsets.
+struct VbTemps {
+    u32* cnt = nullptr;
+    u64* off = nullptr;
+};
+
+// Decode nb bytes into exactly n values in [lo, hi) at vals.
+static void vb_decode_col(lcg_ctx* ctx, const u8* src, u64 nb, u64 n, u64 lo, u64 hi, u32* vals, const VbTemps& t,
+                          u64* totals) {
+    const u64 tiles = vb_decode_tiles(nb);
+    if (tiles == 0) return;
+    int h = kt_begin(ctx, "k_vb_tile_ends", (double)nb);
+    ck(ctx, launch_vb_tile_ends(src, nb, t.cnt, ctx->st), "k_vb_tile_ends");
+    kt_end(ctx, h);
+    ctx->launches++;
+    vb_scan(ctx, t.cnt, tiles, t.off, totals);
+    h = kt_begin(ctx, "k_vb_dwrite", (double)nb + 4.0 * (double)n);
+    ck(ctx, launch_vb_dwrite(src, nb, n, lo, hi, t.off, vals, ctx->ds, ctx->st), "k_vb_dwrite");
+    kt_end(ctx, h);
     ctx->launches++;
 }
 
@@ -2336,46 +2363,67 @@ static u64 vb_total_bytes(const lcg_grammar* G, const std::vector<u64>& nb) {
 int lcg_vbyte_encode(lcg_ctx* ctx, const uint32_t* in, uint64_t n, uint8_t* out, uint64_t cap, uint64_t* out_bytes) {
     if (!ctx || !out_bytes || (n && (!in || !out))) return LCG_EINVAL;
     const Range range("lcg_vbyte_encode");
-    LCG_GUARD_BEGIN
-    ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
-    kt_reset(ctx);
-    reset_status(ctx);
-    *out_bytes = 0;
-    if (n == 0) return LCG_OK;
-    ck(ctx, cudaMemsetAsync(ctx->scratch + 1, 0, 8, ctx->st), "memset");
-    ck(ctx, launch_vb_count(in, nullptr, n, ctx->scratch + 1, sm_count(ctx), ctx->st), "k_vb_count");
-    ctx->launches++;
-    u64 nb = 0;
-    ck(ctx, cudaMemcpyAsync(&nb, ctx->scratch + 1, 8, cudaMemcpyDeviceToHost, ctx->st), "read size");
-    sync(ctx);
-    *out_bytes = nb;
-    fail_if(ctx, cap < nb, LCG_EINVAL, "output buffer too small");
-    vb_encode_col(ctx, in, nullptr, n, out, ctx->scratch + 2, false, nb);
-    u64 wrote = 0;
-    ck(ctx, cudaMemcpyAsync(&wrote, ctx->scratch + 2, 8, cudaMemcpyDeviceToHost, ctx->st), "read size");
-    const DevStatus st = read_status(ctx);
-    kt_collect(ctx);
-    check_device_status(ctx, st);
-    fail_if(ctx, wrote != nb, LCG_EDEVICE, "encoded length differs from the count");
-    return LCG_OK;
-    LCG_GUARD_END
+    u32* cnt = nullptr;
+    u64* off = nullptr;
+    try {
+        ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+        kt_reset(ctx);
+        reset_status(ctx);
+        *out_bytes = 0;
+        if (n == 0) return LCG_OK;
+        const u64 tiles = vb_encode_tiles(n);
+        cnt = dalloc<u32>(ctx, tiles);
+        off = dalloc<u64>(ctx, tiles);
+        vb_count_col(ctx, in, nullptr, n, cnt, off, ctx->scratch + 1);
+        u64 nb = 0;
+        ck(ctx, cudaMemcpyAsync(&nb, ctx->scratch + 1, 8, cudaMemcpyDeviceToHost, ctx->st), "read size");
+        sync(ctx);
+        *out_bytes = nb;
+        fail_if(ctx, cap < nb, LCG_EINVAL, "output buffer too small");
+        vb_write_col(ctx, in, nullptr, n, off, out, false, nb);
+        dfree(ctx, cnt);
+        dfree(ctx, off);
+        cnt = nullptr;
+        off = nullptr;
+        const DevStatus st = read_status(ctx);
+        kt_collect(ctx);
+        check_device_status(ctx, st);
+        return LCG_OK;
+    } catch (const Fail& f) {
+        cudaStreamSynchronize(ctx->st);
+        if (cnt) cudaFree(cnt);
+        if (off) cudaFree(off);
+        return f.code;
+    }
 }
 
 int lcg_vbyte_decode(lcg_ctx* ctx, const uint8_t* in, uint64_t nbytes, uint32_t* out, uint64_t n) {
     if (!ctx || (nbytes && !in) || (n && !out)) return LCG_EINVAL;
     const Range range("lcg_vbyte_decode");
-    LCG_GUARD_BEGIN
-    ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
-    kt_reset(ctx);
-    fail_if(ctx, nbytes < n || nbytes > 5 * n, LCG_EINVAL, "stream length does not fit the value count");
-    if (n == 0) return LCG_OK;
-    reset_status(ctx);
-    vb_decode_col(ctx, in, nbytes, n, 0, 1ull << 32, 0, out, nullptr);
-    const DevStatus st = read_status(ctx);
-    kt_collect(ctx);
-    check_device_status(ctx, st);
-    return LCG_OK;
-    LCG_GUARD_END
+    VbTemps t;
+    try {
+        ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+        kt_reset(ctx);
+        fail_if(ctx, nbytes < n || nbytes > 5 * n, LCG_EINVAL, "stream length does not fit the value count");
+        if (n == 0) return LCG_OK;
+        reset_status(ctx);
+        const u64 tiles = vb_decode_tiles(nbytes);
+        t.cnt = dalloc<u32>(ctx, tiles);
+        t.off = dalloc<u64>(ctx, tiles);
+        vb_decode_col(ctx, in, nbytes, n, 0, 1ull << 32, out, t, ctx->scratch + 1);
+        dfree(ctx, t.cnt);
+        dfree(ctx, t.off);
+        t = VbTemps{};
+        const DevStatus st = read_status(ctx);
+        kt_collect(ctx);
+        check_device_status(ctx, st);
+        return LCG_OK;
+    } catch (const Fail& f) {
+        cudaStreamSynchronize(ctx->st);
+        if (t.cnt) cudaFree(t.cnt);
+        if (t.off) cudaFree(t.off);
+        return f.code;
+    }
 }
 
 int lcg_vbyte_size(lcg_ctx* ctx, const lcg_grammar* G, uint64_t* bytes) {
@@ -2392,8 +2440,7 @@ int lcg_export_vbyte(lcg_ctx* ctx, const lcg_grammar* G, void* out, uint64_t cap
                      uint64_t* bytes) {
     if (!ctx || !G || !out) return LCG_EINVAL;
     const Range range("lcg_export_vbyte");
-    u8* staging = nullptr;
-    u64* written = nullptr;
+    std::vector<void*> temps;
     try {
         ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
         fail_if(ctx, G->device != ctx->device, LCG_EINVAL, "grammar on another device");
@@ -2401,12 +2448,36 @@ int lcg_export_vbyte(lcg_ctx* ctx, const lcg_grammar* G, void* out, uint64_t cap
         kt_reset(ctx);
         reset_status(ctx);
         const u64 nl = G->lv.size();
-        const std::vector<u64> nb = vb_section_bytes(ctx, G);
+        // columns: [2 i] rule lengths, [2 i + 1] right-hand sides of level i + 1
+        std::vector<u64> base(2 * nl + 1, 0);
+        for (u64 c = 0; c < 2 * nl; c++) {
+            const Level& L = G->lv[c / 2];
+            base[c + 1] = base[c] + vb_encode_tiles(c % 2 ? L.G : L.g);
+        }
+        u32* cnt = dalloc<u32>(ctx, base[2 * nl]);
+        temps.push_back(cnt);
+        u64* off = dalloc<u64>(ctx, base[2 * nl]);
+        temps.push_back(off);
+        u64* tot = dalloc<u64>(ctx, 4 * nl + 2);
+        temps.push_back(tot);
+        ck(ctx, cudaMemsetAsync(tot, 0, 8 * (4 * nl + 2), ctx->st), "memset");
+        for (u64 c = 0; c < 2 * nl; c++) {
+            const Level& L = G->lv[c / 2];
+            if (c % 2) vb_count_col(ctx, L.rhs, nullptr, L.G, cnt + base[c], off + base[c], tot + 2 * c);
+            else vb_count_col(ctx, nullptr, L.rhs_off, L.g, cnt + base[c], off + base[c], tot + 2 * c);
+        }
+        std::vector<u64> tv(4 * nl + 2), nb(2 * nl);
+        ck(ctx, cudaMemcpyAsync(tv.data(), tot, 8 * tv.size(), cudaMemcpyDeviceToHost, ctx->st), "read sizes");
+        sync(ctx);
+        for (u64 c = 0; c < 2 * nl; c++) nb[c] = tv[2 * c];
         const u64 total = vb_total_bytes(G, nb);
         if (bytes) *bytes = total;
         fail_if(ctx, cap < total, LCG_EINVAL, "VByte buffer too small");
-        u8* dst = out_on_device ? (u8*)out : (staging = dalloc<u8>(ctx, total));
-        written = dalloc<u64>(ctx, 2 * nl + 1);
+        u8* dst = (u8*)out;
+        if (!out_on_device) {
+            dst = dalloc<u8>(ctx, total);
+            temps.push_back(dst);
+        }
         std::vector<u64> head(3 + 4 * nl);
         head[0] = kVbMagic;
         head[1] = G->k;
@@ -2426,9 +2497,9 @@ int lcg_export_vbyte(lcg_ctx* ctx, const lcg_grammar* G, void* out, uint64_t cap
         };
         for (u64 i = 0; i < nl; i++) {
             const Level& L = G->lv[i];
-            vb_encode_col(ctx, nullptr, L.rhs_off, L.g, dst + pos, written + 2 * i, true, nb[2 * i]);
+            vb_write_col(ctx, nullptr, L.rhs_off, L.g, off + base[2 * i], dst + pos, true, nb[2 * i]);
             pos += pad8(nb[2 * i]);
-            vb_encode_col(ctx, L.rhs, nullptr, L.G, dst + pos, written + 2 * i + 1, true, nb[2 * i + 1]);
+            vb_write_col(ctx, L.rhs, nullptr, L.G, off + base[2 * i + 1], dst + pos, true, nb[2 * i + 1]);
             pos += pad8(nb[2 * i + 1]);
             copy_u32(L.F, L.g);
         }
@@ -2437,29 +2508,20 @@ int lcg_export_vbyte(lcg_ctx* ctx, const lcg_grammar* G, void* out, uint64_t cap
         copy_u32(G->F0, 256);
         fail_if(ctx, pos != total, LCG_EDEVICE, "VByte layout");
         if (!out_on_device) ck(ctx, cudaMemcpyAsync(out, dst, total, cudaMemcpyDeviceToHost, ctx->st), "export");
-        std::vector<u64> wr(2 * nl);
-        if (nl) ck(ctx, cudaMemcpyAsync(wr.data(), written, 16 * nl, cudaMemcpyDeviceToHost, ctx->st), "read sizes");
-        dfree(ctx, written);
-        written = nullptr;
-        dfree(ctx, staging);
-        staging = nullptr;
+        for (void* p : temps) dfree(ctx, p);
+        temps.clear();
         const DevStatus st = read_status(ctx);
         kt_collect(ctx);
         check_device_status(ctx, st);
-        for (u64 i = 0; i < nl; i++)
-            fail_if(ctx, (G->lv[i].g && wr[2 * i] != nb[2 * i]) || (G->lv[i].G && wr[2 * i + 1] != nb[2 * i + 1]),
-                    LCG_EDEVICE, "encoded length differs from the count");
         return LCG_OK;
     } catch (const Fail& f) {
         cudaStreamSynchronize(ctx->st);
-        if (written) cudaFree(written);
-        if (staging) cudaFree(staging);
+        for (void* p : temps) cudaFree(p);
         return f.code;
     } catch (const std::bad_alloc&) {
         ctx->err = "host allocation failed";
         cudaStreamSynchronize(ctx->st);
-        if (written) cudaFree(written);
-        if (staging) cudaFree(staging);
+        for (void* p : temps) cudaFree(p);
         return LCG_ENOMEM;
     }
 }
@@ -2470,6 +2532,7 @@ int lcg_import_vbyte(lcg_ctx* ctx, const void* buf, uint64_t size, int buf_on_de
     const Range range("lcg_import_vbyte");
     lcg_grammar* G = nullptr;
     u8* staging = nullptr;
+    std::vector<void*> temps;
     try {
         ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
         kt_reset(ctx);
@@ -2526,6 +2589,22 @@ int lcg_import_vbyte(lcg_ctx* ctx, const void* buf, uint64_t size, int buf_on_de
             ck(ctx, cudaMemcpyAsync(staging, buf, size, cudaMemcpyHostToDevice, ctx->st), "upload");
             src = staging;
         }
+        // scratch for every level's decode (reused in stream order)
+        u64 max_tiles = 1, max_g = 1;
+        for (u64 i = 0; i < nl; i++) {
+            max_tiles = std::max(max_tiles, std::max(vb_decode_tiles(hd[4 * i + 2]), vb_decode_tiles(hd[4 * i + 3])));
+            max_g = std::max<u64>(max_g, hd[4 * i]);
+        }
+        VbTemps t;
+        t.cnt = dalloc<u32>(ctx, max_tiles);
+        temps.push_back(t.cnt);
+        t.off = dalloc<u64>(ctx, max_tiles);
+        temps.push_back(t.off);
+        u32* lens = dalloc<u32>(ctx, max_g);
+        temps.push_back(lens);
+        u64* tot = dalloc<u64>(ctx, 4 * nl + 2);
+        temps.push_back(tot);
+        ck(ctx, cudaMemsetAsync(tot, 0, 8 * (4 * nl + 2), ctx->st), "memset");
         reset_status(ctx);
         G = new_grammar(ctx);
         if (k) {
@@ -2541,16 +2620,26 @@ int lcg_import_vbyte(lcg_ctx* ctx, const void* buf, uint64_t size, int buf_on_de
             Level& L = G->lv.back();
             grow_level(ctx, L, g, Gs);
             const u64 prev = i == 0 ? 256 : hd[4 * (i - 1)];
-            vb_decode_col(ctx, src + off_len[i], hd[4 * i + 2], g, 1, 1ull << 32, Gs, nullptr, L.rhs_off);
-            vb_decode_col(ctx, src + off_rhs[i], hd[4 * i + 3], Gs, 0, prev, 0, L.rhs, nullptr);
-            if (g) ck(ctx, cudaMemcpyAsync(L.F, src + off_F[i], 4 * g, cudaMemcpyDeviceToDevice, ctx->st), "import");
+            if (g) {
+                // rule lengths (each >= 1), then their exclusive scan: the offsets
+                vb_decode_col(ctx, src + off_len[i], hd[4 * i + 2], g, 1, 1ull << 32, lens, t, tot + 4 * i + 2);
+                vb_scan(ctx, lens, g, L.rhs_off, tot + 4 * i);
+                ck(ctx, cudaMemcpyAsync(L.rhs_off + g, tot + 4 * i, 8, cudaMemcpyDeviceToDevice, ctx->st), "offsets");
+                vb_decode_col(ctx, src + off_rhs[i], hd[4 * i + 3], Gs, 0, prev, L.rhs, t, tot + 4 * i + 2);
+                ck(ctx, cudaMemcpyAsync(L.F, src + off_F[i], 4 * g, cudaMemcpyDeviceToDevice, ctx->st), "import");
+            }
             L.g = g;
             L.G = Gs;
             L.rvalid = false;
         }
+        std::vector<u64> tv(4 * nl + 2);
+        ck(ctx, cudaMemcpyAsync(tv.data(), tot, 8 * tv.size(), cudaMemcpyDeviceToHost, ctx->st), "read sums");
         DevStatus st = read_status(ctx);
         fail_if(ctx, st.error == kErrFormat, LCG_EINVAL, "malformed VByte form");
         check_device_status(ctx, st);
+        for (u64 i = 0; i < nl; i++)
+            fail_if(ctx, tv[4 * i] != hd[4 * i + 1], LCG_EINVAL,
+                    "rule lengths of level " + std::to_string(i + 1) + " do not add up to G");
         for (u64 i = 0; i < nl; i++) {
             const Level& L = G->lv[i];
             ck(ctx, launch_check_fp(L.rhs, L.rhs_off, L.g, fprev_of(G, (u32)i + 1), level_hash(ctx, (u32)i + 1), L.F,
@@ -2563,6 +2652,8 @@ int lcg_import_vbyte(lcg_ctx* ctx, const void* buf, uint64_t size, int buf_on_de
         ck(ctx, cudaMemcpyAsync(theirs, src + off_F0, sizeof(theirs), cudaMemcpyDeviceToHost, ctx->st), "read F0");
         dfree(ctx, staging);
         staging = nullptr;
+        for (void* p : temps) dfree(ctx, p);
+        temps.clear();
         st = read_status(ctx);
         kt_collect(ctx);
         fail_if(ctx, st.error == kErrMismatch, LCG_EMISMATCH,
@@ -2575,12 +2666,14 @@ int lcg_import_vbyte(lcg_ctx* ctx, const void* buf, uint64_t size, int buf_on_de
     } catch (const Fail& f) {
         cudaStreamSynchronize(ctx->st);
         if (staging) cudaFree(staging);
+        for (void* p : temps) cudaFree(p);
         free_grammar_now(G);
         return f.code;
     } catch (const std::bad_alloc&) {
         ctx->err = "host allocation failed";
         cudaStreamSynchronize(ctx->st);
         if (staging) cudaFree(staging);
+        for (void* p : temps) cudaFree(p);
         free_grammar_now(G);
         return LCG_ENOMEM;
     }

@@ -216,11 +216,12 @@ cudaError_t launch_pp_roots(const u32* c_level, const u32* c_rank, u32 k, const 
 // VByte codec (vbyte.cu).  A column is a u32 array (`vals`) or, when `offs`
 // is given, the rule lengths offs[p + 1] - offs[p].
 cudaError_t launch_vb_count(const u32* vals, const u64* offs, u64 n, u64* total, int sms, cudaStream_t st);
-cudaError_t launch_vb_encode(const u32* vals, const u64* offs, u64 n, u8* out, u64* nbytes_out, bool pad, void* lb,
-                             u64 epoch, u64* ctr, u64 ctr_base, DevStatus* ds, cudaStream_t st, u64* grid_out);
-cudaError_t launch_vb_decode(const u8* in, u64 nb, u64 n, u64 lo, u64 hi, u64 expect_sum, u32* vals, u64* offs,
-                             void* lb, u64 epoch, u64* ctr, u64 ctr_base, DevStatus* ds, cudaStream_t st,
-                             u64* grid_out);
+cudaError_t launch_vb_tile_bytes(const u32* vals, const u64* offs, u64 n, u32* tile_bytes, cudaStream_t st);
+cudaError_t launch_vb_write(const u32* vals, const u64* offs, u64 n, const u64* tile_off, u8* out, bool pad,
+                            cudaStream_t st);
+cudaError_t launch_vb_tile_ends(const u8* in, u64 nb, u32* tile_cnt, cudaStream_t st);
+cudaError_t launch_vb_dwrite(const u8* in, u64 nb, u64 n, u64 lo, u64 hi, const u64* cnt_off, u32* vals,
+                             DevStatus* ds, cudaStream_t st);
 u64 vb_encode_tiles(u64 n);
 u64 vb_decode_tiles(u64 nb);
 

@@ -4,21 +4,21 @@
 // is set when another byte of the same value follows (the LEB128 / varint
 // layout).
 //
-// Both directions are single-pass over tiles with a decoupled look-back:
-//   k_vb_encode: a tile of 2048 values -> byte counts -> block scan ->
-//     look-back gives the tile's byte offset; the tile's bytes are assembled
-//     in shared memory and stored with 4-byte stores (edges byte by byte), so
-//     the stream is written once, coalesced.
-//   k_vb_decode: a tile of 4096 stream bytes (plus the 8 bytes before it) in
-//     shared memory; every byte without the high bit ends a value, which is
-//     assembled from the bytes before it; counts (and, for rule lengths, the
-//     sums) are scanned across tiles by look-back and the tile's values are
-//     stored coalesced.  Malformed streams (a value of more than 32 bits, a
-//     stream that ends inside a value, a value outside the allowed range, a
-//     different number of values) set kErrFormat; no write leaves the output.
-// Rule lengths are encoded straight from the u64 offsets and decoded straight
-// into them (the lengths array never exists), so an export or import of a
-// level reads and writes each array once.
+// Both directions run in three independent streaming steps, with no wait of
+// one tile on another:
+//   encode: k_vb_tile_bytes (stream bytes of each tile of 2048 values), an
+//     exclusive scan of those counts (k_scan2), k_vb_write (each tile
+//     re-reads its values, assembles its bytes in shared memory and stores
+//     them at its offset with 4-byte stores, the edges byte by byte).  An
+//     export needs the counts anyway to lay out its sections.
+//   decode: k_vb_tile_ends (values ending in each tile of 4096 stream bytes),
+//     a scan of those counts, k_vb_dwrite (every byte without the high bit
+//     ends a value, which is assembled in registers from the bytes before it;
+//     the tile's values are staged and stored coalesced at its offset).  Malformed streams (a value of more
+//     than 32 bits or 5 bytes, a stream that ends inside a value, a value
+//     outside the allowed range, another number of values) set kErrFormat;
+//     no write leaves the output.
+// k_vb_count sizes a column without writing it (lcg_vbyte_size).
 #include "lcg_dev.cuh"
 #include "lcg_internal.h"
 
@@ -65,23 +65,12 @@ __global__ void __launch_bounds__(kVbThreads) k_vb_count(const u32* __restrict__
 }
 
 // --------------------------------------------------------------------------
-// encode
+// encode: bytes per tile, (scan of the tile counts), write
 // --------------------------------------------------------------------------
 
-// Writes the VByte stream of the n values to out[0 ..), with `pad` zeros up
-// to the next multiple of 8 bytes (the section padding), and the stream's
-// length to *nbytes_out.
+// Values of this thread (kVbItems from p0; 0 past n).
 template <bool kLens>
-__global__ void __launch_bounds__(kVbThreads) k_vb_encode(const u32* __restrict__ vals, const u64* __restrict__ offs,
-                                                          u64 n, u8* __restrict__ out, u64* __restrict__ nbytes_out,
-                                                          bool pad, LBSlot<2>* lb, u64 epoch, u64* ctr, u64 ctr_base,
-                                                          DevStatus* ds) {
-    __shared__ u8 s_out[kVbTile * 5];
-    pdl_wait();
-    const u64 tile = dynamic_tile(ctr, ctr_base);
-    const u64 p0 = tile * (u64)kVbTile + (u64)threadIdx.x * kVbItems;
-    u32 v[kVbItems];
-    u32 mine = 0;
+__device__ __forceinline__ void vb_load(const u32* vals, const u64* offs, u64 n, u64 p0, u32 (&v)[kVbItems]) {
     if (!kLens && p0 + kVbItems <= n && (reinterpret_cast<uintptr_t>(vals + p0) & 15) == 0) {
         const uint4 a = __ldg(reinterpret_cast<const uint4*>(vals + p0));
         const uint4 b = __ldg(reinterpret_cast<const uint4*>(vals + p0) + 1);
@@ -98,13 +87,54 @@ __global__ void __launch_bounds__(kVbThreads) k_vb_encode(const u32* __restrict_
 #pragma unroll
         for (int it = 0; it < kVbItems; it++) v[it] = (p0 + it < n) ? __ldg(vals + p0 + it) : 0u;
     }
+}
+
+template <bool kLens>
+__device__ __forceinline__ u32 vb_thread_bytes(const u32 (&v)[kVbItems], u64 n, u64 p0) {
+    u32 b = 0;
 #pragma unroll
-    for (int it = 0; it < kVbItems; it++) mine += (p0 + it < n) ? vb_len(v[it]) : 0u;
+    for (int it = 0; it < kVbItems; it++) b += (p0 + it < n) ? vb_len(v[it]) : 0u;
+    return b;
+}
+
+// tile_bytes[t] = bytes of the VByte stream of values [t * kVbTile, ...).
+template <bool kLens>
+__global__ void __launch_bounds__(kVbThreads) k_vb_tile_bytes(const u32* __restrict__ vals,
+                                                              const u64* __restrict__ offs, u64 n,
+                                                              u32* __restrict__ tile_bytes) {
+    pdl_wait();
+    const u64 p0 = blockIdx.x * (u64)kVbTile + (u64)threadIdx.x * kVbItems;
+    u32 v[kVbItems];
+    vb_load<kLens>(vals, offs, n, p0, v);
+    u32 b = vb_thread_bytes<kLens>(v, n, p0);
+    for (int o = 16; o > 0; o >>= 1) b += __shfl_down_sync(0xffffffffu, b, o);
+    __shared__ u32 s_w[kVbThreads / 32];
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u32 t = 0;
+        for (int w = 0; w < kVbThreads / 32; w++) t += s_w[w];
+        tile_bytes[blockIdx.x] = t;
+    }
+}
+
+// Writes the VByte stream of the n values to out[0 ..): tile t at its
+// offset tile_off[t] (exclusive scan of k_vb_tile_bytes), assembled in shared
+// memory and stored with 4-byte stores (edges byte by byte).  With `pad`, the
+// last tile adds zeros up to the next multiple of 8 bytes (section padding).
+template <bool kLens>
+__global__ void __launch_bounds__(kVbThreads) k_vb_write(const u32* __restrict__ vals, const u64* __restrict__ offs,
+                                                         u64 n, const u64* __restrict__ tile_off,
+                                                         u8* __restrict__ out, bool pad) {
+    __shared__ u8 s_out[kVbTile * 5];
+    pdl_wait();
+    const u64 tile = blockIdx.x;
+    const u64 p0 = tile * (u64)kVbTile + (u64)threadIdx.x * kVbItems;
+    const u64 base = tile_off[tile];  // issued with the value loads, used after the assembly
+    u32 v[kVbItems];
+    vb_load<kLens>(vals, offs, n, p0, v);
     u64 tile_bytes;
-    const u64 my_off = block_excl_scan(mine, tile_bytes);
-    u64 agg[2] = {tile_bytes, 0}, excl[2];
-    block_lookback<2>(lb, tile, epoch, agg, excl, ds);
-    // assemble the tile's bytes in shared memory
+    const u64 my_off = block_excl_scan(vb_thread_bytes<kLens>(v, n, p0), tile_bytes);
     u32 o = (u32)my_off;
 #pragma unroll
     for (int it = 0; it < kVbItems; it++) {
@@ -118,8 +148,7 @@ __global__ void __launch_bounds__(kVbThreads) k_vb_encode(const u32* __restrict_
         }
     }
     __syncthreads();
-    // store [base, base + tile_bytes): edge bytes one by one, the rest as words
-    u8* dst = out + excl[0];
+    u8* dst = out + base;
     const u32 tb = (u32)tile_bytes;
     const u32 head = min(tb, (u32)((4 - (reinterpret_cast<uintptr_t>(dst) & 3)) & 3));
     const u32 words = (tb - head) >> 2;
@@ -131,129 +160,140 @@ __global__ void __launch_bounds__(kVbThreads) k_vb_encode(const u32* __restrict_
         const u32 b = head + 4 * w;
         wdst[w] = (u32)s_out[b] | ((u32)s_out[b + 1] << 8) | ((u32)s_out[b + 2] << 16) | ((u32)s_out[b + 3] << 24);
     }
-    if ((tile + 1) * (u64)kVbTile >= n && threadIdx.x == 0) {
-        const u64 total = excl[0] + tile_bytes;
-        if (pad)
-            for (u64 z = total; z & 7; z++) out[z] = 0;
-        *nbytes_out = total;
-    }
+    if (pad && tile == gridDim.x - 1 && threadIdx.x == 0)
+        for (u64 z = base + tile_bytes; z & 7; z++) out[z] = 0;
 }
 
 // --------------------------------------------------------------------------
-// decode
+// decode: values per tile, (scan of the tile counts), write
 // --------------------------------------------------------------------------
 
-// The value whose last byte is sb[q]: its bytes are that byte and the
-// continuation bytes right before it.  More than 5 bytes or 32 bits sets `bad`.
-__device__ __forceinline__ u64 vb_value_at(const u8* sb, int q, bool& bad) {
-    int len = 1;
-    while (len < 6 && (sb[q - len] & 0x80u)) len++;
-    if (len > 5) {
-        bad = true;
-        len = 5;
-    }
-    // sb[q] holds the most significant group, sb[q - len + 1] the least
-    u64 x = 0;
-    for (int j = 0; j < len; j++) x = (x << 7) | (u64)(sb[q - j] & 0x7Fu);
-    if (x >= (1ull << 32)) bad = true;
-    return x;
+// High bit of each byte of a little-endian word: bit q = bit 7 of byte q
+// (the eight bits gathered into the top byte by one multiplication).
+__device__ __forceinline__ u32 vb_high_bits(u64 w) {
+    return (u32)((((w & 0x8080808080808080ull) >> 7) * 0x0102040810204080ull) >> 56);
 }
 
-// Decodes the nb-byte stream `in` into exactly n values with lo <= v < hi.
-// Values: vals[0 .. n).  Rule lengths (kLens): offs[0 .. n] with offs[0] = 0
-// and offs[r + 1] = offs[r] + length r; their sum must be `expect_sum`.
-template <bool kLens>
-__global__ void __launch_bounds__(kVbThreads) k_vb_decode(const u8* __restrict__ in, u64 nb, u64 n, u64 lo, u64 hi,
-                                                          u64 expect_sum, u32* __restrict__ vals,
-                                                          u64* __restrict__ offs, LBSlot<2>* lb, u64 epoch, u64* ctr,
-                                                          u64 ctr_base, DevStatus* ds) {
-    __shared__ __align__(16) u8 s_b[kVbHalo + kVbDecTile];
-    __shared__ u64 s_v[kVbDecTile];
+// Bytes [p0, p0 + 16) of the stream as two little-endian words (0 past nb),
+// and the mask of those that end a value (bit q: byte p0 + q).
+__device__ __forceinline__ u32 vb_load16(const u8* in, u64 nb, u64 p0, u64& w1, u64& w2) {
+    if (p0 + kVbBytes <= nb && (reinterpret_cast<uintptr_t>(in + p0) & 7) == 0) {
+        w1 = __ldg(reinterpret_cast<const unsigned long long*>(in + p0));
+        w2 = __ldg(reinterpret_cast<const unsigned long long*>(in + p0) + 1);
+    } else {
+        w1 = w2 = 0;
+#pragma unroll
+        for (int q = 0; q < kVbBytes; q++) {
+            const u64 x = (p0 + q < nb) ? (u64)__ldg(in + p0 + q) : 0ull;
+            if (q < 8) w1 |= x << (8 * q);
+            else w2 |= x << (8 * (q - 8));
+        }
+    }
+    // a byte ends a value when its high bit is clear (bytes past nb do not)
+    u32 m = ~(vb_high_bits(w1) | (vb_high_bits(w2) << 8)) & 0xFFFFu;
+    if (p0 + kVbBytes > nb) m &= (p0 >= nb) ? 0u : ((1u << (u32)(nb - p0)) - 1u);
+    return m;
+}
+
+// tile_cnt[t] = values that end in bytes [t * kVbDecTile, ...) of the stream.
+__global__ void __launch_bounds__(kVbThreads) k_vb_tile_ends(const u8* __restrict__ in, u64 nb,
+                                                             u32* __restrict__ tile_cnt) {
     pdl_wait();
-    const u64 tile = dynamic_tile(ctr, ctr_base);
+    const u64 p0 = blockIdx.x * (u64)kVbDecTile + (u64)threadIdx.x * kVbBytes;
+    u64 w1, w2;
+    u32 c = __popc(vb_load16(in, nb, p0, w1, w2));
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    __shared__ u32 s_w[kVbThreads / 32];
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u32 t = 0;
+        for (int w = 0; w < kVbThreads / 32; w++) t += s_w[w];
+        tile_cnt[blockIdx.x] = t;
+    }
+}
+
+// Decodes the nb-byte stream into exactly n values with lo <= v < hi: the
+// values ending in tile t go to vals[cnt_off[t] ...) (cnt_off: exclusive
+// scan of k_vb_tile_ends).  Each thread holds its 16 bytes and the 8 before
+// them (from the lane before, or the warp before, or global memory at a
+// tile's start; zeros before the stream, which end no value's run) in three
+// registers.  A value ending at window byte e takes the bytes after the last
+// earlier end byte: its length is one more than the run of continuation bits
+// right below e, and its groups come from the 8 bytes at e - 4 by one funnel
+// shift.  The tile's values are staged in shared memory and stored coalesced.
+__global__ void __launch_bounds__(kVbThreads) k_vb_dwrite(const u8* __restrict__ in, u64 nb, u64 n, u64 lo, u64 hi,
+                                                          const u64* __restrict__ cnt_off, u32* __restrict__ vals,
+                                                          DevStatus* ds) {
+    __shared__ u32 s_v[kVbDecTile];
+    __shared__ u64 s_tail[kVbThreads / 32];
+    pdl_wait();
+    const u64 tile = blockIdx.x;
     const u64 t0 = tile * (u64)kVbDecTile;
     const u64 p0 = t0 + (u64)threadIdx.x * kVbBytes;
-    // stage the tile (bytes past the stream read as 0) and the halo before it
-    // (bytes before the stream read as 0: an end byte stops a backward walk)
-    u8* sb = s_b + kVbHalo + threadIdx.x * kVbBytes;
-    if (p0 + kVbBytes <= nb && (reinterpret_cast<uintptr_t>(in + p0) & 7) == 0) {
-        const uint2 a = __ldg(reinterpret_cast<const uint2*>(in + p0));
-        const uint2 b = __ldg(reinterpret_cast<const uint2*>(in + p0) + 1);
-        reinterpret_cast<uint2*>(sb)[0] = a;
-        reinterpret_cast<uint2*>(sb)[1] = b;
-    } else {
+    const u32 lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // loads issued together: the tile's offset, the 8 bytes before the tile
+    // (thread 0), the thread's 16 bytes
+    const u64 base = cnt_off[tile];
+    u64 before = 0;
+    if (threadIdx.x == 0 && t0 > 0) {
+        if ((reinterpret_cast<uintptr_t>(in + t0 - 8) & 7) == 0) {
+            before = __ldg(reinterpret_cast<const unsigned long long*>(in + t0 - 8));
+        } else {
 #pragma unroll
-        for (int q = 0; q < kVbBytes; q++) sb[q] = (p0 + q < nb) ? __ldg(in + p0 + q) : (u8)0;
+            for (int q = 0; q < 8; q++) before |= (u64)__ldg(in + t0 - 8 + q) << (8 * q);
+        }
     }
-    if (threadIdx.x < kVbHalo) {
-        const long long p = (long long)t0 - kVbHalo + (long long)threadIdx.x;
-        s_b[threadIdx.x] = (p >= 0) ? __ldg(in + p) : (u8)0;
-    }
-    __syncthreads();
-    // values ending in this thread's bytes: count (and, for lengths, sum)
-    u32 ends = 0;
-#pragma unroll
-    for (int q = 0; q < kVbBytes; q++)
-        if (p0 + q < nb && (sb[q] & 0x80u) == 0) ends |= 1u << q;
-    const u32 cnt = __popc(ends);
-    u64 sum = 0;
+    u64 w1, w2;
+    const u32 ends = vb_load16(in, nb, p0, w1, w2);
+    u64 w0 = __shfl_up_sync(0xffffffffu, w2, 1);  // the 8 bytes before p0
+    if (lane == 31) s_tail[wid] = w2;
+    u64 tile_cnt;
+    const u64 my_cnt = block_excl_scan(__popc(ends), tile_cnt);  // its barriers also publish s_tail
+    if (lane == 0) w0 = (wid > 0) ? s_tail[wid - 1] : before;
+    // continuation bits of the 24-byte window (bit j: window byte j)
+    const u32 cont = vb_high_bits(w0) | (vb_high_bits(w1) << 8) | (vb_high_bits(w2) << 16);
     bool bad = false;
-    if (kLens) {
-        for (u32 m = ends; m; m &= m - 1) {
-            const u64 x = vb_value_at(sb, __ffs(m) - 1, bad);
-            sum += x;
-        }
-    }
     // the stream must end with a value's last byte
-    if (nb > 0 && p0 <= nb - 1 && nb - 1 < p0 + kVbBytes && (sb[nb - 1 - p0] & 0x80u)) bad = true;
-    u64 tile_cnt, tile_sum = 0;
-    const u64 my_cnt = block_excl_scan(cnt, tile_cnt);
-    u64 my_sum = 0;
-    if (kLens) my_sum = block_excl_scan(sum, tile_sum);
-    u64 agg[2] = {tile_cnt, tile_sum}, excl[2];
-    block_lookback<2>(lb, tile, epoch, agg, excl, ds);
-    // stage values (or running offsets) in index order, then store coalesced
-    {
-        u64 run = my_sum;
-        u32 i = (u32)my_cnt;
-        for (u32 m = ends; m; m &= m - 1) {
-            const u64 x = vb_value_at(sb, __ffs(m) - 1, bad);
-            if (x < lo || x >= hi) bad = true;
-            s_v[i++] = kLens ? run : x;
-            run += x;
+    if (p0 <= nb - 1 && nb - 1 < p0 + kVbBytes && !((ends >> (u32)(nb - 1 - p0)) & 1u)) bad = true;
+    u32 i = (u32)my_cnt;
+    for (u32 m = ends; m; m &= m - 1) {
+        const u32 e = (u32)__ffs(m) - 1 + 8;           // window byte of the value's last byte, 8 .. 23
+        const u32 run = __clz(~(cont << (32 - e)));     // continuation bytes right before it
+        u32 len = run + 1;
+        if (len > 5) {
+            bad = true;
+            len = 5;
         }
+        // the 8 window bytes from e - 4 (4 .. 19): one funnel shift of two words
+        const u32 st = e - 4, sh = (st & 7) * 8;
+        const u64 lo_w = (st < 8) ? w0 : (st < 16 ? w1 : w2);
+        const u64 hi_w = (st < 8) ? w1 : (st < 16 ? w2 : 0ull);
+        const u64 v8 = sh ? ((lo_w >> sh) | (hi_w << (64 - sh))) : lo_w;
+        // five 7-bit groups, the least significant from byte e - 4
+        const u64 y = (v8 & 0x7Full) | ((v8 >> 1) & 0x3F80ull) | ((v8 >> 2) & 0x1FC000ull) |
+                      ((v8 >> 3) & 0xFE00000ull) | ((v8 >> 4) & 0x7F0000000ull);
+        const u64 x = y >> (7 * (5 - len));
+        if (x >= (1ull << 32) || x < lo || x >= hi) bad = true;
+        s_v[i++] = (u32)x;
     }
     if (bad) set_error(ds, kErrFormat);
     __syncthreads();
-    for (u32 i = threadIdx.x; i < (u32)tile_cnt; i += kVbThreads) {
-        const u64 idx = excl[0] + i;
-        if (idx < n) {
-            if (kLens) offs[idx] = excl[1] + s_v[i];
-            else vals[idx] = (u32)s_v[i];
-        }
+    for (u32 k = threadIdx.x; k < (u32)tile_cnt; k += kVbThreads) {
+        const u64 idx = base + k;
+        if (idx < n) vals[idx] = s_v[k];
     }
-    if (t0 + kVbDecTile >= nb && threadIdx.x == 0) {
-        const u64 total = excl[0] + tile_cnt;
-        if (total != n) set_error(ds, kErrFormat);
-        if (kLens) {
-            const u64 s = excl[1] + tile_sum;
-            if (s != expect_sum) set_error(ds, kErrFormat);
-            if (total == n) offs[n] = s;
-        }
-    }
+    if (tile == gridDim.x - 1 && threadIdx.x == 0 && base + tile_cnt != n) set_error(ds, kErrFormat);
 }
 
 // --------------------------------------------------------------------------
 // launchers
 // --------------------------------------------------------------------------
 
-static unsigned vb_grid(u64 n, u64 per) {
-    u64 t = (n + per - 1) / per;
-    return (unsigned)(t ? t : 1);
-}
+static u64 vb_tiles(u64 n, u64 per) { return (n + per - 1) / per; }
 
-u64 vb_encode_tiles(u64 n) { return vb_grid(n, kVbTile); }
-u64 vb_decode_tiles(u64 nb) { return vb_grid(nb, kVbDecTile); }
+u64 vb_encode_tiles(u64 n) { return vb_tiles(n, kVbTile); }
+u64 vb_decode_tiles(u64 nb) { return vb_tiles(nb, kVbDecTile); }
 
 cudaError_t launch_vb_count(const u32* vals, const u64* offs, u64 n, u64* total, int sms, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
@@ -262,27 +302,32 @@ cudaError_t launch_vb_count(const u32* vals, const u64* offs, u64 n, u64* total,
     return launch_pdl(k_vb_count<false>, grid, kVbThreads, st, vals, offs, n, total);
 }
 
-cudaError_t launch_vb_encode(const u32* vals, const u64* offs, u64 n, u8* out, u64* nbytes_out, bool pad, void* lb,
-                             u64 epoch, u64* ctr, u64 ctr_base, DevStatus* ds, cudaStream_t st, u64* grid_out) {
-    const unsigned grid = vb_grid(n, kVbTile);
-    *grid_out = grid;
-    if (offs)
-        return launch_pdl(k_vb_encode<true>, grid, kVbThreads, st, vals, offs, n, out, nbytes_out, pad,
-                          (LBSlot<2>*)lb, epoch, ctr, ctr_base, ds);
-    return launch_pdl(k_vb_encode<false>, grid, kVbThreads, st, vals, offs, n, out, nbytes_out, pad, (LBSlot<2>*)lb,
-                      epoch, ctr, ctr_base, ds);
+cudaError_t launch_vb_tile_bytes(const u32* vals, const u64* offs, u64 n, u32* tile_bytes, cudaStream_t st) {
+    const unsigned grid = (unsigned)vb_encode_tiles(n);
+    if (grid == 0) return cudaSuccess;
+    if (offs) return launch_pdl(k_vb_tile_bytes<true>, grid, kVbThreads, st, vals, offs, n, tile_bytes);
+    return launch_pdl(k_vb_tile_bytes<false>, grid, kVbThreads, st, vals, offs, n, tile_bytes);
 }
 
-cudaError_t launch_vb_decode(const u8* in, u64 nb, u64 n, u64 lo, u64 hi, u64 expect_sum, u32* vals, u64* offs,
-                             void* lb, u64 epoch, u64* ctr, u64 ctr_base, DevStatus* ds, cudaStream_t st,
-                             u64* grid_out) {
-    const unsigned grid = vb_grid(nb, kVbDecTile);
-    *grid_out = grid;
-    if (offs)
-        return launch_pdl(k_vb_decode<true>, grid, kVbThreads, st, in, nb, n, lo, hi, expect_sum, vals, offs,
-                          (LBSlot<2>*)lb, epoch, ctr, ctr_base, ds);
-    return launch_pdl(k_vb_decode<false>, grid, kVbThreads, st, in, nb, n, lo, hi, expect_sum, vals, offs,
-                      (LBSlot<2>*)lb, epoch, ctr, ctr_base, ds);
+cudaError_t launch_vb_write(const u32* vals, const u64* offs, u64 n, const u64* tile_off, u8* out, bool pad,
+                            cudaStream_t st) {
+    const unsigned grid = (unsigned)vb_encode_tiles(n);
+    if (grid == 0) return cudaSuccess;
+    if (offs) return launch_pdl(k_vb_write<true>, grid, kVbThreads, st, vals, offs, n, tile_off, out, pad);
+    return launch_pdl(k_vb_write<false>, grid, kVbThreads, st, vals, offs, n, tile_off, out, pad);
+}
+
+cudaError_t launch_vb_tile_ends(const u8* in, u64 nb, u32* tile_cnt, cudaStream_t st) {
+    const unsigned grid = (unsigned)vb_decode_tiles(nb);
+    if (grid == 0) return cudaSuccess;
+    return launch_pdl(k_vb_tile_ends, grid, kVbThreads, st, in, nb, tile_cnt);
+}
+
+cudaError_t launch_vb_dwrite(const u8* in, u64 nb, u64 n, u64 lo, u64 hi, const u64* cnt_off, u32* vals,
+                             DevStatus* ds, cudaStream_t st) {
+    const unsigned grid = (unsigned)vb_decode_tiles(nb);
+    if (grid == 0) return cudaSuccess;
+    return launch_pdl(k_vb_dwrite, grid, kVbThreads, st, in, nb, n, lo, hi, cnt_off, vals, ds);
 }
 
 }  // namespace lcg
