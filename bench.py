@@ -555,22 +555,27 @@ def run_ours(args):
     d2h_seen = [0] * lanes
     errors = []
 
-    def e2e_lane(i):
+    def e2e_lane(i, steps):
         try:
-            for _ in range(per_lane[i]):
+            for _ in range(steps):
                 g = ectx[i].build(hd, coll.offsets)
                 d2h_seen[i] = int(g.export_packed(outs[i]).numel())
                 g.free()
         except Exception as e:  # reported below
             errors.append(repr(e))
 
+    def e2e_pass(steps):
+        threads = [threading.Thread(target=e2e_lane, args=(i, steps[i])) for i in range(lanes)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        torch.cuda.synchronize()
+
+    e2e_pass([2] * lanes)  # untimed: the lanes' steps running together once, as they will when timed
+    barrier()
     t0 = time.perf_counter()
-    threads = [threading.Thread(target=e2e_lane, args=(i,)) for i in range(lanes)]
-    for t in threads:
-        t.start()
-    for t in threads:
-        t.join()
-    torch.cuda.synchronize()
+    e2e_pass(per_lane)
     if errors:
         raise RuntimeError("end-to-end step failed: " + errors[0])
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps)
