@@ -2448,28 +2448,42 @@ int lcg_export_vbyte(lcg_ctx* ctx, const lcg_grammar* G, void* out, uint64_t cap
         kt_reset(ctx);
         reset_status(ctx);
         const u64 nl = G->lv.size();
-        // columns: [2 i] rule lengths, [2 i + 1] right-hand sides of level i + 1
-        std::vector<u64> base(2 * nl + 1, 0);
-        for (u64 c = 0; c < 2 * nl; c++) {
+        // columns: [2 i] rule lengths, [2 i + 1] right-hand sides of level i + 1;
+        // one launch per step over all of them
+        const u32 ncols = (u32)(2 * nl);
+        fail_if(ctx, ncols > (u32)kVbMaxCols, LCG_EINVAL, "too many levels");
+        std::vector<VbEncCol> cols(ncols + 1, VbEncCol{nullptr, nullptr, 0, 0, nullptr});
+        u64 T = 0;
+        for (u32 c = 0; c < ncols; c++) {
             const Level& L = G->lv[c / 2];
-            base[c + 1] = base[c] + vb_encode_tiles(c % 2 ? L.G : L.g);
+            cols[c] = (c % 2) ? VbEncCol{L.rhs, nullptr, L.G, T, nullptr} : VbEncCol{nullptr, L.rhs_off, L.g, T, nullptr};
+            T += vb_encode_tiles(cols[c].n);
         }
-        u32* cnt = dalloc<u32>(ctx, base[2 * nl]);
+        cols[ncols].tile0 = T;
+        double in_bytes = 0, out_bytes = 0;
+        for (u32 c = 0; c < ncols; c++) in_bytes += (c % 2 ? 4.0 : 8.0) * (double)cols[c].n;
+        VbEncCol* dcols = dalloc<VbEncCol>(ctx, ncols + 1);
+        temps.push_back(dcols);
+        u32* cnt = dalloc<u32>(ctx, T);
         temps.push_back(cnt);
-        u64* off = dalloc<u64>(ctx, base[2 * nl]);
+        u64* off = dalloc<u64>(ctx, T);
         temps.push_back(off);
-        u64* tot = dalloc<u64>(ctx, 4 * nl + 2);
-        temps.push_back(tot);
-        ck(ctx, cudaMemsetAsync(tot, 0, 8 * (4 * nl + 2), ctx->st), "memset");
-        for (u64 c = 0; c < 2 * nl; c++) {
-            const Level& L = G->lv[c / 2];
-            if (c % 2) vb_count_col(ctx, L.rhs, nullptr, L.G, cnt + base[c], off + base[c], tot + 2 * c);
-            else vb_count_col(ctx, nullptr, L.rhs_off, L.g, cnt + base[c], off + base[c], tot + 2 * c);
+        u64* colb = dalloc<u64>(ctx, ncols + 1);
+        temps.push_back(colb);
+        ck(ctx, cudaMemsetAsync(colb, 0, 8 * (ncols + 1), ctx->st), "memset");
+        ck(ctx, cudaMemcpyAsync(dcols, cols.data(), sizeof(VbEncCol) * (ncols + 1), cudaMemcpyHostToDevice, ctx->st),
+           "columns");
+        if (T) {
+            const int h = kt_begin(ctx, "k_vb_tile_bytes", in_bytes);
+            ck(ctx, launch_vb_tile_bytes_all(dcols, ncols, T, cnt, colb, ctx->st), "k_vb_tile_bytes");
+            kt_end(ctx, h);
+            ctx->launches++;
+            vb_scan(ctx, cnt, T, off, ctx->scratch + 1);
         }
-        std::vector<u64> tv(4 * nl + 2), nb(2 * nl);
-        ck(ctx, cudaMemcpyAsync(tv.data(), tot, 8 * tv.size(), cudaMemcpyDeviceToHost, ctx->st), "read sizes");
+        std::vector<u64> nb(ncols + 1);
+        ck(ctx, cudaMemcpyAsync(nb.data(), colb, 8 * (ncols + 1), cudaMemcpyDeviceToHost, ctx->st), "read sizes");
         sync(ctx);
-        for (u64 c = 0; c < 2 * nl; c++) nb[c] = tv[2 * c];
+        for (u32 c = 0; c < ncols; c++) out_bytes += (double)nb[c];
         const u64 total = vb_total_bytes(G, nb);
         if (bytes) *bytes = total;
         fail_if(ctx, cap < total, LCG_EINVAL, "VByte buffer too small");
@@ -2497,11 +2511,20 @@ int lcg_export_vbyte(lcg_ctx* ctx, const lcg_grammar* G, void* out, uint64_t cap
         };
         for (u64 i = 0; i < nl; i++) {
             const Level& L = G->lv[i];
-            vb_write_col(ctx, nullptr, L.rhs_off, L.g, off + base[2 * i], dst + pos, true, nb[2 * i]);
+            cols[2 * i].dst = dst + pos;
             pos += pad8(nb[2 * i]);
-            vb_write_col(ctx, L.rhs, nullptr, L.G, off + base[2 * i + 1], dst + pos, true, nb[2 * i + 1]);
+            cols[2 * i + 1].dst = dst + pos;
             pos += pad8(nb[2 * i + 1]);
             copy_u32(L.F, L.g);
+        }
+        if (T) {
+            ck(ctx, cudaMemcpyAsync(dcols, cols.data(), sizeof(VbEncCol) * (ncols + 1), cudaMemcpyHostToDevice,
+                                    ctx->st),
+               "columns");
+            const int h = kt_begin(ctx, "k_vb_write", in_bytes + out_bytes);
+            ck(ctx, launch_vb_write_all(dcols, ncols, T, off, ctx->st), "k_vb_write");
+            kt_end(ctx, h);
+            ctx->launches++;
         }
         copy_u32(G->c_level, G->k);
         copy_u32(G->c_rank, G->k);
@@ -2589,22 +2612,6 @@ int lcg_import_vbyte(lcg_ctx* ctx, const void* buf, uint64_t size, int buf_on_de
             ck(ctx, cudaMemcpyAsync(staging, buf, size, cudaMemcpyHostToDevice, ctx->st), "upload");
             src = staging;
         }
-        // scratch for every level's decode (reused in stream order)
-        u64 max_tiles = 1, max_g = 1;
-        for (u64 i = 0; i < nl; i++) {
-            max_tiles = std::max(max_tiles, std::max(vb_decode_tiles(hd[4 * i + 2]), vb_decode_tiles(hd[4 * i + 3])));
-            max_g = std::max<u64>(max_g, hd[4 * i]);
-        }
-        VbTemps t;
-        t.cnt = dalloc<u32>(ctx, max_tiles);
-        temps.push_back(t.cnt);
-        t.off = dalloc<u64>(ctx, max_tiles);
-        temps.push_back(t.off);
-        u32* lens = dalloc<u32>(ctx, max_g);
-        temps.push_back(lens);
-        u64* tot = dalloc<u64>(ctx, 4 * nl + 2);
-        temps.push_back(tot);
-        ck(ctx, cudaMemsetAsync(tot, 0, 8 * (4 * nl + 2), ctx->st), "memset");
         reset_status(ctx);
         G = new_grammar(ctx);
         if (k) {
@@ -2613,33 +2620,80 @@ int lcg_import_vbyte(lcg_ctx* ctx, const void* buf, uint64_t size, int buf_on_de
             ck(ctx, cudaMemcpyAsync(G->c_rank, src + off_cr, 4 * k, cudaMemcpyDeviceToDevice, ctx->st), "import");
             G->k = (u32)k;
         }
-        // decode every level, and check the streams before anything reads them
+        // the levels' arrays, and one decode over all columns: every level's
+        // rule lengths (into one array, scanned into the offsets afterwards)
+        // and right-hand sides
+        u64 sum_g = 0, max_g = 0;
+        for (u64 i = 0; i < nl; i++) {
+            sum_g += hd[4 * i];
+            max_g = std::max<u64>(max_g, hd[4 * i]);
+        }
+        u32* lens = dalloc<u32>(ctx, sum_g);
+        temps.push_back(lens);
+        std::vector<VbDecCol> cols;
+        std::vector<VbLevelOff> lvo;
+        u64 T = 0, gbase = 0;
         for (u64 i = 0; i < nl; i++) {
             const u64 g = hd[4 * i], Gs = hd[4 * i + 1];
             G->lv.emplace_back();
             Level& L = G->lv.back();
             grow_level(ctx, L, g, Gs);
-            const u64 prev = i == 0 ? 256 : hd[4 * (i - 1)];
-            if (g) {
-                // rule lengths (each >= 1), then their exclusive scan: the offsets
-                vb_decode_col(ctx, src + off_len[i], hd[4 * i + 2], g, 1, 1ull << 32, lens, t, tot + 4 * i + 2);
-                vb_scan(ctx, lens, g, L.rhs_off, tot + 4 * i);
-                ck(ctx, cudaMemcpyAsync(L.rhs_off + g, tot + 4 * i, 8, cudaMemcpyDeviceToDevice, ctx->st), "offsets");
-                vb_decode_col(ctx, src + off_rhs[i], hd[4 * i + 3], Gs, 0, prev, L.rhs, t, tot + 4 * i + 2);
-                ck(ctx, cudaMemcpyAsync(L.F, src + off_F[i], 4 * g, cudaMemcpyDeviceToDevice, ctx->st), "import");
-            }
             L.g = g;
             L.G = Gs;
             L.rvalid = false;
+            if (g == 0) continue;
+            const u64 prev = i == 0 ? 256 : hd[4 * (i - 1)];
+            cols.push_back(VbDecCol{src + off_len[i], hd[4 * i + 2], g, 1, 1ull << 32, lens + gbase, T});
+            T += vb_decode_tiles(hd[4 * i + 2]);
+            cols.push_back(VbDecCol{src + off_rhs[i], hd[4 * i + 3], Gs, 0, prev, L.rhs, T});
+            T += vb_decode_tiles(hd[4 * i + 3]);
+            lvo.push_back(VbLevelOff{L.rhs_off, g, Gs, gbase});
+            gbase += g;
+            ck(ctx, cudaMemcpyAsync(L.F, src + off_F[i], 4 * g, cudaMemcpyDeviceToDevice, ctx->st), "import");
         }
-        std::vector<u64> tv(4 * nl + 2);
-        ck(ctx, cudaMemcpyAsync(tv.data(), tot, 8 * tv.size(), cudaMemcpyDeviceToHost, ctx->st), "read sums");
+        const u32 ncols = (u32)cols.size();
+        fail_if(ctx, ncols > (u32)kVbMaxCols, LCG_EINVAL, "too many levels");
+        cols.push_back(VbDecCol{nullptr, 0, 0, 0, 0, nullptr, T});
+        if (T) {
+            VbDecCol* dcols = dalloc<VbDecCol>(ctx, cols.size());
+            temps.push_back(dcols);
+            VbLevelOff* dlvo = dalloc<VbLevelOff>(ctx, lvo.size());
+            temps.push_back(dlvo);
+            u32* cnt = dalloc<u32>(ctx, T);
+            temps.push_back(cnt);
+            u64* off = dalloc<u64>(ctx, T);
+            temps.push_back(off);
+            u64* gscan = dalloc<u64>(ctx, sum_g);
+            temps.push_back(gscan);
+            ck(ctx, cudaMemcpyAsync(dcols, cols.data(), sizeof(VbDecCol) * cols.size(), cudaMemcpyHostToDevice,
+                                    ctx->st),
+               "columns");
+            ck(ctx, cudaMemcpyAsync(dlvo, lvo.data(), sizeof(VbLevelOff) * lvo.size(), cudaMemcpyHostToDevice,
+                                    ctx->st),
+               "levels");
+            double nbytes = 0, nvals = 0;
+            for (u32 c = 0; c < ncols; c++) {
+                nbytes += (double)cols[c].nb;
+                nvals += (double)cols[c].n;
+            }
+            int h = kt_begin(ctx, "k_vb_tile_ends", nbytes);
+            ck(ctx, launch_vb_tile_ends_all(dcols, ncols, T, cnt, ctx->st), "k_vb_tile_ends");
+            kt_end(ctx, h);
+            vb_scan(ctx, cnt, T, off, ctx->scratch + 1);
+            h = kt_begin(ctx, "k_vb_dwrite", nbytes + 4.0 * nvals);
+            ck(ctx, launch_vb_dwrite_all(dcols, ncols, T, off, ctx->ds, ctx->st), "k_vb_dwrite");
+            kt_end(ctx, h);
+            vb_scan(ctx, lens, sum_g, gscan, ctx->scratch + 1);
+            h = kt_begin(ctx, "k_vb_offsets", 12.0 * (double)sum_g);
+            ck(ctx, launch_vb_offsets_all(dlvo, (u32)lvo.size(), max_g, gscan, ctx->scratch + 1, ctx->ds, ctx->st),
+               "k_vb_offsets");
+            kt_end(ctx, h);
+            ctx->launches += 3;
+        }
+        // the streams are checked before anything reads what they gave
         DevStatus st = read_status(ctx);
         fail_if(ctx, st.error == kErrFormat, LCG_EINVAL, "malformed VByte form");
         check_device_status(ctx, st);
-        for (u64 i = 0; i < nl; i++)
-            fail_if(ctx, tv[4 * i] != hd[4 * i + 1], LCG_EINVAL,
-                    "rule lengths of level " + std::to_string(i + 1) + " do not add up to G");
         for (u64 i = 0; i < nl; i++) {
             const Level& L = G->lv[i];
             ck(ctx, launch_check_fp(L.rhs, L.rhs_off, L.g, fprev_of(G, (u32)i + 1), level_hash(ctx, (u32)i + 1), L.F,

@@ -225,4 +225,37 @@ cudaError_t launch_vb_dwrite(const u8* in, u64 nb, u64 n, u64 lo, u64 hi, const 
 u64 vb_encode_tiles(u64 n);
 u64 vb_decode_tiles(u64 nb);
 
+// Every column of a grammar in one launch per step: tile t of a launch
+// belongs to the column c with cols[c].tile0 <= t < cols[c + 1].tile0; the
+// entry after the last column holds the launch's tile count in tile0.
+constexpr int kVbMaxCols = 2 * 64;
+struct VbEncCol {
+    const u32* vals;  // right-hand sides, or
+    const u64* offs;  // rule offsets (the column holds the lengths)
+    u64 n;            // values
+    u64 tile0;        // first tile (of 2048 values)
+    u8* dst;          // where the column's stream goes (set after the count)
+};
+struct VbDecCol {
+    const u8* src;  // the column's stream
+    u64 nb;         // its bytes
+    u64 n;          // values it must hold
+    u64 lo, hi;     // their range
+    u32* out;
+    u64 tile0;  // first tile (of 4096 bytes)
+};
+struct VbLevelOff {
+    u64* rhs_off;  // g + 1 offsets to write
+    u64 g, G;      // rules, symbols
+    u64 gbase;     // the level's first length in the scanned array
+};
+cudaError_t launch_vb_tile_bytes_all(const VbEncCol* cols, u32 ncols, u64 tiles, u32* tile_bytes, u64* col_bytes,
+                                     cudaStream_t st);
+cudaError_t launch_vb_write_all(const VbEncCol* cols, u32 ncols, u64 tiles, const u64* tile_off, cudaStream_t st);
+cudaError_t launch_vb_tile_ends_all(const VbDecCol* cols, u32 ncols, u64 tiles, u32* tile_cnt, cudaStream_t st);
+cudaError_t launch_vb_dwrite_all(const VbDecCol* cols, u32 ncols, u64 tiles, const u64* cnt_off, DevStatus* ds,
+                                 cudaStream_t st);
+cudaError_t launch_vb_offsets_all(const VbLevelOff* lv, u32 nlv, u64 max_g, const u64* scan, const u64* total,
+                                  DevStatus* ds, cudaStream_t st);
+
 }  // namespace lcg

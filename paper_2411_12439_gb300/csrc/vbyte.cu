@@ -118,6 +118,22 @@ __global__ void __launch_bounds__(kVbThreads) k_vb_tile_bytes(const u32* __restr
     }
 }
 
+// Store a tile's tb stream bytes (assembled in s_out) at dst: the bytes up to
+// a 4-byte boundary and after the last whole word one by one, the rest as
+// 4-byte words.
+__device__ __forceinline__ void vb_store_tile(u8* dst, const u8* s_out, u32 tb) {
+    const u32 head = min(tb, (u32)((4 - (reinterpret_cast<uintptr_t>(dst) & 3)) & 3));
+    const u32 words = (tb - head) >> 2;
+    const u32 tail0 = head + 4 * words;
+    if (threadIdx.x < head) dst[threadIdx.x] = s_out[threadIdx.x];
+    for (u32 t = tail0 + threadIdx.x; t < tb; t += kVbThreads) dst[t] = s_out[t];
+    u32* wdst = reinterpret_cast<u32*>(dst + head);
+    for (u32 w = threadIdx.x; w < words; w += kVbThreads) {
+        const u32 b = head + 4 * w;
+        wdst[w] = (u32)s_out[b] | ((u32)s_out[b + 1] << 8) | ((u32)s_out[b + 2] << 16) | ((u32)s_out[b + 3] << 24);
+    }
+}
+
 // Writes the VByte stream of the n values to out[0 ..): tile t at its
 // offset tile_off[t] (exclusive scan of k_vb_tile_bytes), assembled in shared
 // memory and stored with 4-byte stores (edges byte by byte).  With `pad`, the
@@ -148,18 +164,7 @@ __global__ void __launch_bounds__(kVbThreads) k_vb_write(const u32* __restrict__
         }
     }
     __syncthreads();
-    u8* dst = out + base;
-    const u32 tb = (u32)tile_bytes;
-    const u32 head = min(tb, (u32)((4 - (reinterpret_cast<uintptr_t>(dst) & 3)) & 3));
-    const u32 words = (tb - head) >> 2;
-    const u32 tail0 = head + 4 * words;
-    if (threadIdx.x < head) dst[threadIdx.x] = s_out[threadIdx.x];
-    for (u32 t = tail0 + threadIdx.x; t < tb; t += kVbThreads) dst[t] = s_out[t];
-    u32* wdst = reinterpret_cast<u32*>(dst + head);
-    for (u32 w = threadIdx.x; w < words; w += kVbThreads) {
-        const u32 b = head + 4 * w;
-        wdst[w] = (u32)s_out[b] | ((u32)s_out[b + 1] << 8) | ((u32)s_out[b + 2] << 16) | ((u32)s_out[b + 3] << 24);
-    }
+    vb_store_tile(out + base, s_out, (u32)tile_bytes);
     if (pad && tile == gridDim.x - 1 && threadIdx.x == 0)
         for (u64 z = base + tile_bytes; z & 7; z++) out[z] = 0;
 }
@@ -222,30 +227,33 @@ __global__ void __launch_bounds__(kVbThreads) k_vb_tile_ends(const u8* __restric
 // earlier end byte: its length is one more than the run of continuation bits
 // right below e, and its groups come from the 8 bytes at e - 4 by one funnel
 // shift.  The tile's values are staged in shared memory and stored coalesced.
-__global__ void __launch_bounds__(kVbThreads) k_vb_dwrite(const u8* __restrict__ in, u64 nb, u64 n, u64 lo, u64 hi,
-                                                          const u64* __restrict__ cnt_off, u32* __restrict__ vals,
-                                                          DevStatus* ds) {
-    __shared__ u32 s_v[kVbDecTile];
-    __shared__ u64 s_tail[kVbThreads / 32];
-    pdl_wait();
-    const u64 tile = blockIdx.x;
-    const u64 t0 = tile * (u64)kVbDecTile;
+// One tile of a stream (bytes [t0, t0 + 4096) of src, nb bytes in all) into
+// out[base ...): each thread holds its 16 bytes and the 8 before them (from
+// the lane before, the warp before, or global memory at the tile's start;
+// zeros before the stream, which end no value's run) in three registers.  A
+// value ending at window byte e takes the bytes after the last earlier end
+// byte: its length is one more than the run of continuation bits right below
+// e, and its groups come from the 8 bytes at e - 4 by one funnel shift.  The
+// tile's values are staged in shared memory and stored coalesced.  `last`:
+// the stream's last tile, which checks that n values were found.
+__device__ __forceinline__ void vb_decode_tile(const u8* __restrict__ src, u64 nb, u64 n, u64 lo, u64 hi, u64 t0,
+                                               u64 base, bool last, u32* __restrict__ out, u32* s_v, u64* s_tail,
+                                               DevStatus* ds) {
     const u64 p0 = t0 + (u64)threadIdx.x * kVbBytes;
     const u32 lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // loads issued together: the tile's offset, the 8 bytes before the tile
-    // (thread 0), the thread's 16 bytes
-    const u64 base = cnt_off[tile];
+    // loads issued together: the 8 bytes before the tile (thread 0), the
+    // thread's 16 bytes
     u64 before = 0;
     if (threadIdx.x == 0 && t0 > 0) {
-        if ((reinterpret_cast<uintptr_t>(in + t0 - 8) & 7) == 0) {
-            before = __ldg(reinterpret_cast<const unsigned long long*>(in + t0 - 8));
+        if ((reinterpret_cast<uintptr_t>(src + t0 - 8) & 7) == 0) {
+            before = __ldg(reinterpret_cast<const unsigned long long*>(src + t0 - 8));
         } else {
 #pragma unroll
-            for (int q = 0; q < 8; q++) before |= (u64)__ldg(in + t0 - 8 + q) << (8 * q);
+            for (int q = 0; q < 8; q++) before |= (u64)__ldg(src + t0 - 8 + q) << (8 * q);
         }
     }
     u64 w1, w2;
-    const u32 ends = vb_load16(in, nb, p0, w1, w2);
+    const u32 ends = vb_load16(src, nb, p0, w1, w2);
     u64 w0 = __shfl_up_sync(0xffffffffu, w2, 1);  // the 8 bytes before p0
     if (lane == 31) s_tail[wid] = w2;
     u64 tile_cnt;
@@ -281,9 +289,168 @@ __global__ void __launch_bounds__(kVbThreads) k_vb_dwrite(const u8* __restrict__
     __syncthreads();
     for (u32 k = threadIdx.x; k < (u32)tile_cnt; k += kVbThreads) {
         const u64 idx = base + k;
-        if (idx < n) vals[idx] = s_v[k];
+        if (idx < n) out[idx] = s_v[k];
     }
-    if (tile == gridDim.x - 1 && threadIdx.x == 0 && base + tile_cnt != n) set_error(ds, kErrFormat);
+    if (last && threadIdx.x == 0 && base + tile_cnt != n) set_error(ds, kErrFormat);
+}
+
+// Decodes the nb-byte stream into exactly n values with lo <= v < hi: the
+// values ending in tile t go to vals[cnt_off[t] ...) (cnt_off: exclusive
+// scan of k_vb_tile_ends).
+__global__ void __launch_bounds__(kVbThreads) k_vb_dwrite(const u8* __restrict__ in, u64 nb, u64 n, u64 lo, u64 hi,
+                                                          const u64* __restrict__ cnt_off, u32* __restrict__ vals,
+                                                          DevStatus* ds) {
+    __shared__ u32 s_v[kVbDecTile];
+    __shared__ u64 s_tail[kVbThreads / 32];
+    pdl_wait();
+    const u64 tile = blockIdx.x;
+    vb_decode_tile(in, nb, n, lo, hi, tile * (u64)kVbDecTile, cnt_off[tile], tile == gridDim.x - 1, vals, s_v,
+                   s_tail, ds);
+}
+
+// --------------------------------------------------------------------------
+// every column of a grammar in one launch per step
+// --------------------------------------------------------------------------
+//
+// Tile t of a launch belongs to column c with cols[c].tile0 <= t <
+// cols[c + 1].tile0 (the last entry is a sentinel holding the launch's tile
+// count); a block finds its column by binary search over the tile0 values,
+// loaded into shared memory.
+
+template <typename Col>
+__device__ __forceinline__ u32 vb_column_of(const Col* cols, u32 ncols, u64 t, u64* s_t0) {
+    for (u32 c = threadIdx.x; c <= ncols; c += blockDim.x) s_t0[c] = cols[c].tile0;
+    __syncthreads();
+    u32 lo = 0, hi = ncols;  // s_t0[lo] <= t < s_t0[hi]
+    while (hi - lo > 1) {
+        const u32 mid = (lo + hi) / 2;
+        if (s_t0[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kVbThreads) k_vb_tile_bytes_all(const VbEncCol* __restrict__ cols, u32 ncols,
+                                                                  u32* __restrict__ tile_bytes,
+                                                                  u64* __restrict__ col_bytes) {
+    __shared__ u64 s_t0[kVbMaxCols + 1];
+    __shared__ u32 s_w[kVbThreads / 32];
+    pdl_wait();
+    const u64 t = blockIdx.x;
+    const u32 c = vb_column_of(cols, ncols, t, s_t0);
+    const VbEncCol col = cols[c];
+    const u64 p0 = (t - col.tile0) * (u64)kVbTile + (u64)threadIdx.x * kVbItems;
+    u32 v[kVbItems];
+    u32 b;
+    if (col.offs) {
+        vb_load<true>(col.vals, col.offs, col.n, p0, v);
+        b = vb_thread_bytes<true>(v, col.n, p0);
+    } else {
+        vb_load<false>(col.vals, col.offs, col.n, p0, v);
+        b = vb_thread_bytes<false>(v, col.n, p0);
+    }
+    for (int o = 16; o > 0; o >>= 1) b += __shfl_down_sync(0xffffffffu, b, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u32 sum = 0;
+        for (int w = 0; w < kVbThreads / 32; w++) sum += s_w[w];
+        tile_bytes[t] = sum;
+        if (sum) atomicAdd(reinterpret_cast<unsigned long long*>(col_bytes + c), (unsigned long long)sum);
+    }
+}
+
+// Tile t of column c goes to cols[c].dst + tile_off[t] - tile_off[cols[c].tile0];
+// the last tile of each column zero-pads it to a multiple of 8 bytes.
+__global__ void __launch_bounds__(kVbThreads) k_vb_write_all(const VbEncCol* __restrict__ cols, u32 ncols,
+                                                             const u64* __restrict__ tile_off) {
+    __shared__ u64 s_t0[kVbMaxCols + 1];
+    __shared__ u8 s_out[kVbTile * 5];
+    pdl_wait();
+    const u64 t = blockIdx.x;
+    const u32 c = vb_column_of(cols, ncols, t, s_t0);
+    const VbEncCol col = cols[c];
+    const u64 base = tile_off[t] - tile_off[col.tile0];
+    const bool last = (t + 1 == s_t0[c + 1]);
+    const u64 p0 = (t - col.tile0) * (u64)kVbTile + (u64)threadIdx.x * kVbItems;
+    u32 v[kVbItems];
+    u32 mine;
+    if (col.offs) {
+        vb_load<true>(col.vals, col.offs, col.n, p0, v);
+        mine = vb_thread_bytes<true>(v, col.n, p0);
+    } else {
+        vb_load<false>(col.vals, col.offs, col.n, p0, v);
+        mine = vb_thread_bytes<false>(v, col.n, p0);
+    }
+    u64 tile_bytes;
+    const u64 my_off = block_excl_scan(mine, tile_bytes);
+    u32 o = (u32)my_off;
+#pragma unroll
+    for (int it = 0; it < kVbItems; it++) {
+        if (p0 + it < col.n) {
+            u32 x = v[it];
+            while (x >= 0x80u) {
+                s_out[o++] = (u8)(x | 0x80u);
+                x >>= 7;
+            }
+            s_out[o++] = (u8)x;
+        }
+    }
+    __syncthreads();
+    vb_store_tile(col.dst + base, s_out, (u32)tile_bytes);
+    if (last && threadIdx.x == 0)
+        for (u64 z = base + tile_bytes; z & 7; z++) col.dst[z] = 0;
+}
+
+__global__ void __launch_bounds__(kVbThreads) k_vb_tile_ends_all(const VbDecCol* __restrict__ cols, u32 ncols,
+                                                                 u32* __restrict__ tile_cnt) {
+    __shared__ u64 s_t0[kVbMaxCols + 1];
+    __shared__ u32 s_w[kVbThreads / 32];
+    pdl_wait();
+    const u64 t = blockIdx.x;
+    const u32 c = vb_column_of(cols, ncols, t, s_t0);
+    const VbDecCol col = cols[c];
+    const u64 p0 = (t - col.tile0) * (u64)kVbDecTile + (u64)threadIdx.x * kVbBytes;
+    u64 w1, w2;
+    u32 n = __popc(vb_load16(col.src, col.nb, p0, w1, w2));
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_down_sync(0xffffffffu, n, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = n;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u32 sum = 0;
+        for (int w = 0; w < kVbThreads / 32; w++) sum += s_w[w];
+        tile_cnt[t] = sum;
+    }
+}
+
+__global__ void __launch_bounds__(kVbThreads) k_vb_dwrite_all(const VbDecCol* __restrict__ cols, u32 ncols,
+                                                              const u64* __restrict__ cnt_off, DevStatus* ds) {
+    __shared__ u64 s_t0[kVbMaxCols + 1];
+    __shared__ u32 s_v[kVbDecTile];
+    __shared__ u64 s_tail[kVbThreads / 32];
+    pdl_wait();
+    const u64 t = blockIdx.x;
+    const u32 c = vb_column_of(cols, ncols, t, s_t0);
+    const VbDecCol col = cols[c];
+    const bool last = (t + 1 == s_t0[c + 1]);
+    const u64 base = cnt_off[t] - cnt_off[col.tile0];
+    const u64 t0 = (t - col.tile0) * (u64)kVbDecTile;
+    vb_decode_tile(col.src, col.nb, col.n, col.lo, col.hi, t0, base, last, col.out, s_v, s_tail, ds);
+}
+
+// Offsets of every level from the scan of all levels' rule lengths (levels
+// with rules only, in order): rhs_off[r] = scan[gbase + r] - scan[gbase],
+// rhs_off[g] = the level's length sum, which must be G (else kErrFormat).
+// blockIdx.y = level; *total = the sum of all lengths.
+__global__ void k_vb_offsets_all(const VbLevelOff* __restrict__ lv, const u64* __restrict__ scan,
+                                 const u64* __restrict__ total, u32 nlv, DevStatus* ds) {
+    pdl_wait();
+    const VbLevelOff L = lv[blockIdx.y];
+    const u64 s0 = scan[L.gbase];
+    const u64 s1 = (blockIdx.y + 1 < nlv) ? scan[lv[blockIdx.y + 1].gbase] : *total;
+    for (u64 r = blockIdx.x * (u64)blockDim.x + threadIdx.x; r <= L.g; r += (u64)gridDim.x * blockDim.x)
+        L.rhs_off[r] = (r < L.g ? scan[L.gbase + r] : s1) - s0;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && s1 - s0 != L.G) set_error(ds, kErrFormat);
 }
 
 // --------------------------------------------------------------------------
@@ -328,6 +495,35 @@ cudaError_t launch_vb_dwrite(const u8* in, u64 nb, u64 n, u64 lo, u64 hi, const 
     const unsigned grid = (unsigned)vb_decode_tiles(nb);
     if (grid == 0) return cudaSuccess;
     return launch_pdl(k_vb_dwrite, grid, kVbThreads, st, in, nb, n, lo, hi, cnt_off, vals, ds);
+}
+
+cudaError_t launch_vb_tile_bytes_all(const VbEncCol* cols, u32 ncols, u64 tiles, u32* tile_bytes, u64* col_bytes,
+                                     cudaStream_t st) {
+    if (tiles == 0) return cudaSuccess;
+    return launch_pdl(k_vb_tile_bytes_all, (unsigned)tiles, kVbThreads, st, cols, ncols, tile_bytes, col_bytes);
+}
+
+cudaError_t launch_vb_write_all(const VbEncCol* cols, u32 ncols, u64 tiles, const u64* tile_off, cudaStream_t st) {
+    if (tiles == 0) return cudaSuccess;
+    return launch_pdl(k_vb_write_all, (unsigned)tiles, kVbThreads, st, cols, ncols, tile_off);
+}
+
+cudaError_t launch_vb_tile_ends_all(const VbDecCol* cols, u32 ncols, u64 tiles, u32* tile_cnt, cudaStream_t st) {
+    if (tiles == 0) return cudaSuccess;
+    return launch_pdl(k_vb_tile_ends_all, (unsigned)tiles, kVbThreads, st, cols, ncols, tile_cnt);
+}
+
+cudaError_t launch_vb_dwrite_all(const VbDecCol* cols, u32 ncols, u64 tiles, const u64* cnt_off, DevStatus* ds,
+                                 cudaStream_t st) {
+    if (tiles == 0) return cudaSuccess;
+    return launch_pdl(k_vb_dwrite_all, (unsigned)tiles, kVbThreads, st, cols, ncols, cnt_off, ds);
+}
+
+cudaError_t launch_vb_offsets_all(const VbLevelOff* lv, u32 nlv, u64 max_g, const u64* scan, const u64* total,
+                                  DevStatus* ds, cudaStream_t st) {
+    if (nlv == 0) return cudaSuccess;
+    const unsigned gx = (unsigned)std::min<u64>((max_g + 1 + kVbThreads - 1) / kVbThreads, 4096);
+    return launch_pdl(k_vb_offsets_all, dim3(gx, nlv), dim3(kVbThreads), st, lv, scan, total, nlv, ds);
 }
 
 }  // namespace lcg
