@@ -15,10 +15,13 @@ arrays, a small fraction of the input) to a partner that imports and merges it.
 Rank 0 ends with the grammar of the collection.
 
 The grammar operations come from a ``backend`` with ``build(data, offsets)``,
-``pack(g)`` / ``unpack(buf)`` (the packed form of lcg_export_packed) and
+``pack(g)`` / ``unpack(buf)`` (a grammar as one byte buffer) and
 ``merge(a, b)`` (a absorbs b; returns a), and the transport from a ``comm``
 with ``send(buf, dst)`` / ``recv(src)`` of uint8 arrays.  ``CudaBackend`` and
-``TorchComm`` are the ones for GPUs.
+``TorchComm`` are the ones for GPUs; ``CudaBackend`` sends the packed form of
+lcg_export_packed, or the VByte form of lcg_export_vbyte (about half the
+bytes: rule lengths and right-hand sides as VBytes, Sec. 4) for links slower
+than the encode and decode.
 """
 from __future__ import annotations
 
@@ -142,19 +145,25 @@ def build_sharded(data, offsets, rank: int, world: int, backend, comm):
 
 
 class CudaBackend:
-    """Grammar operations of a ``Context`` (the CUDA path)."""
+    """Grammar operations of a ``Context`` (the CUDA path).  ``form``: the
+    exchange format, "packed" (lcg_export_packed) or "vbyte"
+    (lcg_export_vbyte)."""
 
-    def __init__(self, ctx):
+    def __init__(self, ctx, form: str = "packed"):
+        if form not in ("packed", "vbyte"):
+            raise ValueError("form is 'packed' or 'vbyte'")
         self.ctx = ctx
+        self.form = form
 
     def build(self, data, offsets):
         return self.ctx.build(data, offsets)
 
     def pack(self, g) -> np.ndarray:
-        return np.asarray(g.export_packed())
+        return np.asarray(g.export_packed() if self.form == "packed" else g.export_vbyte())
 
     def unpack(self, buf):
-        return self.ctx.import_packed(np.ascontiguousarray(buf, dtype=np.uint8))
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        return self.ctx.import_packed(buf) if self.form == "packed" else self.ctx.import_vbyte(buf)
 
     def merge(self, a, b):
         self.ctx.merge(a, b)

@@ -12,11 +12,15 @@ import numpy as np
 
 
 class OracleBackend:
-    def __init__(self, hf):
+    """The oracle's grammar operations; the exchange in the packed form, or
+    (form="vbyte") in the VByte form."""
+
+    def __init__(self, hf, form="packed"):
         from oracle import oracle as O
         self.O = O
         self.hf = hf
         self.tag = O.family_tag(hf)
+        self.form = form
 
     def build(self, data, offsets):
         import lcg_inputs as li
@@ -25,10 +29,16 @@ class OracleBackend:
         return self.O.build(coll, self.hf)
 
     def pack(self, g):
+        if self.form == "vbyte":
+            from oracle import vbyte
+            return np.frombuffer(vbyte.export_vbyte(g.export()), dtype=np.uint8).copy()
         from paper_2411_12439_gb300 import sharding
         return sharding.pack(g.export())
 
     def unpack(self, buf):
+        if self.form == "vbyte":
+            from oracle import vbyte
+            return self.O.from_export(vbyte.import_vbyte(np.asarray(buf, dtype=np.uint8).tobytes()), self.tag)
         from paper_2411_12439_gb300 import sharding
         return self.O.from_export(sharding.unpack(buf), self.tag)
 
@@ -36,7 +46,7 @@ class OracleBackend:
         return a.merge(b)
 
 
-def run(rank, world, port, strings, out, fail_ranks=(), timeout_s=60):
+def run(rank, world, port, strings, out, fail_ranks=(), timeout_s=60, form="packed"):
     import datetime
 
     import torch.distributed as dist
@@ -51,7 +61,7 @@ def run(rank, world, port, strings, out, fail_ranks=(), timeout_s=60):
         coll = li.from_strings(strings)
         if rank in fail_ranks:
             raise RuntimeError(f"rank {rank} stops before the exchange")
-        g = sharding.build_sharded(coll.data, coll.offsets, rank, world, OracleBackend(li.hash_family()),
+        g = sharding.build_sharded(coll.data, coll.offsets, rank, world, OracleBackend(li.hash_family(), form),
                                    sharding.TorchComm())
         if rank == 0:
             np.save(out, sharding.pack(g.export()))

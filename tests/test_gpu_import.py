@@ -71,11 +71,11 @@ class _LocalComm:
         return self.boxes.pop((src, self.rank))
 
 
-@pytest.mark.parametrize("world", [2, 3, 4])
-def test_sharded_build_merge_tree(ctx, hf, world):
+@pytest.mark.parametrize("world,form", [(2, "packed"), (3, "packed"), (4, "packed"), (3, "vbyte"), (4, "vbyte")])
+def test_sharded_build_merge_tree(ctx, hf, world, form):
     from paper_2411_12439_gb300 import sharding
     coll = li.tiny_dna_collection(base_len=120_000, k=7)
-    backend = sharding.CudaBackend(ctx)
+    backend = sharding.CudaBackend(ctx, form=form)
     boxes, out = {}, {}
     for rank in reversed(range(world)):
         out[rank] = sharding.build_sharded(coll.data, coll.offsets, rank, world, backend, _LocalComm(boxes, rank))

@@ -88,10 +88,11 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _run_ranks(world, strings, out, fail_ranks=(), timeout_s=60):
+def _run_ranks(world, strings, out, fail_ranks=(), timeout_s=60, form="packed"):
     ctx = mp.get_context("spawn")
     port = _free_port()
-    procs = [ctx.Process(target=sharding_worker.run, args=(r, world, port, strings, out, fail_ranks, timeout_s))
+    procs = [ctx.Process(target=sharding_worker.run,
+                         args=(r, world, port, strings, out, fail_ranks, timeout_s, form))
              for r in range(world)]
     for p in procs:
         p.start()
@@ -106,13 +107,13 @@ def _run_ranks(world, strings, out, fail_ranks=(), timeout_s=60):
     return codes
 
 
-@pytest.mark.parametrize("world", [2, 3])
-def test_merge_tree_gloo(tmp_path, hf, world):
+@pytest.mark.parametrize("world,form", [(2, "packed"), (3, "packed"), (2, "vbyte")])
+def test_merge_tree_gloo(tmp_path, hf, world, form):
     rng = np.random.default_rng(40 + world)
     base = li.random_dna(rng, 6000)
     strings = [li.apply_snps(rng, base, 0.01).tobytes() for _ in range(5)] + [b"AC", b"G"]
     out = str(tmp_path / "merged.npy")
-    codes = _run_ranks(world, strings, out)
+    codes = _run_ranks(world, strings, out, form=form)
     assert codes == [0] * world
     got = sharding.unpack(np.load(out))
     want = O.build(li.from_strings(strings), hf).export()
