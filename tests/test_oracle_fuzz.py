@@ -3,7 +3,8 @@ small alphabets, so that runs, repeats and collisions of short phrases are
 common.  Properties from the paper: every string expands to itself (Sec. 2.2);
 MergeGrams of two parts equals BuildGram of the whole collection under
 first-occurrence naming (Sec. 3.6); post-processing (RL, Simp) keeps every
-expansion and obeys its size identities."""
+expansion and obeys its size identities; the VByte codec and the VByte form of
+a grammar (Sec. 4) give back what they were given."""
 import numpy as np
 import pytest
 
@@ -66,3 +67,23 @@ def test_postprocess_keeps_expansions(strings):
     stt = pp["stats"]
     assert stt["size"] == stt["size_rl"] - stt["removed"]
     assert np.all(pp["rhs_off"][1:] >= pp["rhs_off"][:-1])
+
+
+@settings_
+@given(st.lists(st.integers(0, (1 << 32) - 1), max_size=300))
+def test_vbyte_codec_roundtrip(values):
+    from oracle import vbyte as V
+    buf = V.encode(values)
+    assert V.encode_np(np.array(values, dtype=np.uint64)) == buf
+    assert len(buf) == sum(V.encoded_length(v) for v in values)
+    assert V.decode(buf, len(values)) == values
+    assert V.decode_np(buf, len(values)).tolist() == values
+
+
+@settings_
+@given(collections())
+def test_vbyte_form_roundtrip(strings):
+    from oracle import vbyte as V
+    hf = li.hash_family()
+    ex = O.build(li.from_strings(strings), hf).export()
+    assert O.grammars_equal(V.import_vbyte(V.export_vbyte(ex)), ex)
