@@ -140,6 +140,20 @@ def test_grammar_form_of_benchmark_strings(ctx):
     g.free()
 
 
+def test_grammar_without_levels(ctx):
+    """Strings of one byte each: no level, only C and F^0."""
+    hf = li.hash_family()
+    coll = li.from_strings([b"A", b"C", b"\x00"])
+    want_ex = O.build(coll, hf).export()
+    want = V.export_vbyte(want_ex)
+    g = ctx.build(torch.from_numpy(coll.data).cuda(), coll.offsets)
+    assert g.export_vbyte().tobytes() == want
+    h = ctx.import_vbyte(np.frombuffer(want, dtype=np.uint8).copy())
+    assert O.grammars_equal(h.export(), want_ex)
+    h.free()
+    g.free()
+
+
 def test_import_rejects_damage(ctx):
     hf = li.hash_family()
     coll = _collections()["dna"]
