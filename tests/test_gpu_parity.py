@@ -154,9 +154,27 @@ def test_build_into_resident(ctx, hf):
 
 def test_bacterial_batch_full_size(ctx, hf):
     """The benchmark's workload: 64 strings of ~5 Mbp (4 base genomes, 1% SNPs,
-    0.02% indels, 5 rearrangements), all in one batched build."""
+    0.02% indels, 5 rearrangements), all in one batched build; then, as the
+    benchmark times it, later builds of the same shape as a captured CUDA
+    graph and its launches."""
+    import torch
     coll = li.bacterial_collection()
-    check_build(ctx, hf, coll)
+    want = O.build(coll, hf).export()
+    d = torch.from_numpy(coll.data).to("cuda:0")
+    g = ctx.build(d, coll.offsets)
+    assert_same(g.export(), want)
+    g.free()
+    ctx.set_graph(True)
+    modes = []
+    try:
+        for _ in range(3):
+            g = ctx.build(d, coll.offsets)
+            modes.append(ctx.last_build_stats()["graph"])
+            assert_same(g.export(), want)
+            g.free()
+    finally:
+        ctx.set_graph(False)
+    assert 2 in modes, modes  # at least one build was a launch of the captured graph
 
 
 def test_repeated_builds_on_one_context(hf):
