@@ -46,3 +46,15 @@ def test_no_device_is_reported_not_hidden():
         assert e.code == -7
     else:
         raise AssertionError("context created without a device")
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CUDA library: loading raises (there is no CPU path to fall back on)."""
+    monkeypatch.setattr(lcg, "_lib", None)
+    monkeypatch.setattr(lcg._build, "LIB", str(tmp_path / "liblcg_gb300.so"))
+    try:
+        lcg.load(build_if_missing=False)
+    except lcg.LCGError as e:
+        assert e.code == -7
+    else:
+        raise AssertionError("loaded a library that does not exist")
