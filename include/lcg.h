@@ -9,6 +9,10 @@
  *   MergeGrams(G_a, G_b)     (Sec. 3.5-3.6)
  *   exp(C[j]) = T_j          (Sec. 2.2)
  *
+ * and, on a finished grammar, the post-processing of Sec. 2.2 / Sec. 4
+ * (run-length rules, then simplification: lcg_postprocess) and its VByte form
+ * (Sec. 4, resource usage: lcg_export_vbyte / lcg_import_vbyte).
+ *
  * Every step runs in hand-written CUDA kernels on one GPU (sm_103a).  There is
  * no CPU fallback: without a usable device every call returns LCG_EDEVICE.
  *
