@@ -974,7 +974,7 @@ struct GraphBuild {
     u64 n1 = 0;
     u32 k = 0;
     std::vector<u64> lens;
-    std::vector<double> key;  // hints, slack, tuning, levels of the plan
+    std::vector<double> params;  // planned rounds and launch parameters (graph_params)
     // round-1 offsets and ids, outside the graph
     u64* soff = nullptr;
     u32* sid = nullptr;
@@ -988,18 +988,30 @@ struct GraphBuild {
     lcg_grammar* live = nullptr;       // grammar of the last launch, until freed
 };
 
-// What a graph's launches depend on besides the input: the planned buffer
-// sizes (in steps of about 19 %) and the launch parameters.
-std::vector<double> graph_key(lcg_ctx* ctx, u64 n1, u32 kk, u32 planned) {
-    std::vector<double> k{(double)planned, (double)ctx->tuning.parse_blocks_per_sm, (double)ctx->tuning.miss_flush,
-                          (double)ctx->ktime};
-    const std::vector<RoundPlan> plan = plan_rounds(ctx, n1, kk, planned);
-    for (u32 r = 1; r <= planned; r++) {
-        k.push_back((double)plan[r].cap);
-        k.push_back((double)plan[r].g_alloc);
-        k.push_back((double)plan[r].G_alloc);
+// What a graph's launches depend on besides the input and the planned buffer
+// sizes: the number of planned rounds and the launch parameters.
+std::vector<double> graph_params(lcg_ctx* ctx, u32 planned) {
+    return {(double)planned, (double)ctx->tuning.parse_blocks_per_sm, (double)ctx->tuning.miss_flush,
+            (double)ctx->ktime};
+}
+
+// A captured graph serves a new plan when each of its rounds' buffers holds
+// the new plan's (the kernels read the actual sizes from the device, so a
+// larger buffer changes nothing but memory), and its phrase tables are not
+// more than 4x the new plan's (a table far larger than needed costs its
+// clearing and L2 room).  Hints that decay and a plan slack that shrinks
+// after every build that fits therefore keep the graph; a plan that grows
+// past it, or shrinks far below it, captures a new one.
+bool plan_covers(const std::vector<RoundPlan>& have, const std::vector<RoundPlan>& need) {
+    if (have.size() != need.size()) return false;
+    for (size_t r = 1; r < have.size(); r++) {
+        const RoundPlan& h = have[r];
+        const RoundPlan& n = need[r];
+        if (h.n_bound != n.n_bound || h.cap < n.cap || h.cap > 4 * n.cap || h.g_alloc < n.g_alloc ||
+            h.G_alloc < n.G_alloc)
+            return false;
     }
-    return k;
+    return true;
 }
 
 void destroy_graph(lcg_ctx* ctx) {
@@ -1029,7 +1041,7 @@ void graph_grammar_freed(lcg_ctx* ctx, const lcg_grammar* G) {
 
 // Capture the planned rounds of a build of this shape (nothing runs yet).
 void capture_graph(lcg_ctx* ctx, const unsigned char* d_in, const std::vector<u64>& lens, u32 planned,
-                   std::vector<double> key) {
+                   std::vector<double> params) {
     destroy_graph(ctx);
     const u32 k = (u32)lens.size();
     u64 n1 = 0;
@@ -1051,7 +1063,7 @@ void capture_graph(lcg_ctx* ctx, const unsigned char* d_in, const std::vector<u6
     gb->d_in = d_in;
     gb->k = k;
     gb->lens = lens;
-    gb->key = std::move(key);
+    gb->params = std::move(params);
     gb->n1 = n1;
     gb->soff = dalloc<u64>(ctx, k + 1);
     gb->sid = dalloc<u32>(ctx, k);
@@ -1134,13 +1146,14 @@ lcg_grammar* build_with_graph(lcg_ctx* ctx, const unsigned char* d_in, const std
     const u32 planned = planned_rounds(ctx);
     u64 n1 = 0;
     for (u64 x : lens) n1 += x;
-    std::vector<double> key = graph_key(ctx, n1, k, planned);
+    std::vector<double> params = graph_params(ctx, planned);
     GraphBuild* gb = ctx->graph;
-    const bool same = gb && gb->d_in == d_in && gb->lens == lens && gb->key == key;
+    const bool same = gb && gb->d_in == d_in && gb->lens == lens && gb->params == params &&
+                      plan_covers(gb->ar.plan, plan_rounds(ctx, n1, k, planned));
     if (same && gb->live) return nullptr;
     const u32 mode = same ? 2 : 1;
     if (!same) {
-        capture_graph(ctx, d_in, lens, planned, std::move(key));
+        capture_graph(ctx, d_in, lens, planned, std::move(params));
         gb = ctx->graph;
     }
     std::vector<u64> soff_h(k + 1, 0);

@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                 const u64 v = sh ? (lo >> sh) | (hi << (64 - sh)) : lo;
                 return ((u64)len << 56) | (v & ((1ull << (8 * len)) - 1));
             };
-            // the inline key of a phrase of length <= 15 inside the staged
+            // the inline key of a phrase of length <= kInlineMax inside the staged
             // bytes: its bytes as one little-endian number B, B mod 2^60 (with
             // the length above) in hi and B >> 60 in lo (the layout of
             // key_inline for 8-bit symbols)
@@ -672,7 +672,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                 }
                 if (slot == ~0u) {
                     bool ok = true;
-                    const Key128 key = (len <= 15 && en <= (u64)ns) ? byte_key(st, (u32)len) : make_key(st, en, &ok);
+                    const Key128 key = (len <= (u64)kInlineMax && en <= (u64)ns) ? byte_key(st, (u32)len) : make_key(st, en, &ok);
                     if (ok) {
                         const u32 m = atomicAdd(&s_nmiss, 1u);
                         if (m < (u32)kMissBuf) {

@@ -8,11 +8,14 @@
 // Keys are 128 bits.  Short phrases are stored exactly ("inline" keys): the
 // top 4 bits of `hi` hold the length q, and the symbols are packed from bit 0
 // upwards in the 124 bits left, w bits each (8 for bytes; for ranks the width
-// of the level below, at most 31), so q <= min(15, 124 / w).  Two inline keys
-// of one width are equal exactly when the phrases are.  A longer phrase gets a "hashed" key: top 4 bits 0, its length in bits
-// 32..59 of `hi` and a 32-bit hash below, with `lo` naming where its content
-// can be read; a hashed-key match is confirmed by comparing the contents
-// symbol by symbol.  Slots are claimed with one 128-bit compare-and-swap.
+// of the level below, at most 31), so q <= min(14, 124 / w).  Two inline keys
+// of one width are equal exactly when the phrases are.  The length field is
+// at most 14, so no key has hi == ~0, the mark of an empty slot (tables are
+// cleared to all ones): with 15 bytes a phrase of 0xFF bytes would have
+// packed to exactly that mark.  A longer phrase gets a "hashed" key: top 4
+// bits 0, its length in bits 32..59 of `hi` and a 32-bit hash below, with `lo`
+// naming where its content can be read; a hashed-key match is confirmed by
+// comparing the contents symbol by symbol.  Slots are claimed with one 128-bit compare-and-swap.
 // The home slot is the high half of mix(key) * cap, so any capacity works;
 // the polynomial fingerprint H = sum_j F[Q_j] c^{j-1} mod p of a phrase is
 // only needed for hashed keys.
@@ -49,9 +52,10 @@ constexpr u64 kMaxPhraseLen = (1ull << 28) - 1;  // longest phrase a hashed key 
 // (so that more phrases fit inline); tables that outlive a round (resident
 // grammars, merges) use kRankBits.
 constexpr int kRankBits = 31;
+constexpr int kInlineMax = 14;
 __device__ __forceinline__ u64 inline_max(int w) {
     const int m = 124 / w;
-    return m < 15 ? (u64)m : 15ull;
+    return m < kInlineMax ? (u64)m : (u64)kInlineMax;
 }
 
 __device__ __forceinline__ void put_bits(u64& hi, u64& lo, int pos, u64 v, int b) {

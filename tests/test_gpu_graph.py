@@ -77,3 +77,37 @@ def test_graph_capture_replay_and_fallback(hf):
         assert O.grammars_equal(g.export(), want["b"])
         g.free()
     assert modes == [0, 1, 2, 2]
+
+
+def test_graph_replays_on_a_context_with_history(hf):
+    """A context that has built other collections first (its sizing hints
+    then exceed what this collection needs, and decay build by build) must
+    still launch its captured graph instead of capturing on every build."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_12439_gb300 import Context
+    ctx = Context(hf, device=0)
+    rng = np.random.default_rng(11)
+    others = [
+        li.tiny_dna_collection(base_len=300_000, k=5, snp=1e-2),
+        li.from_strings([li.zipf_text(rng, 400_000), li.zipf_text(rng, 100_000)]),
+        li.from_strings([li.random_dna(rng, 150_000) for _ in range(9)]),
+    ]
+    for c in others:
+        ctx.build(c.data, c.offsets).free()
+    a = li.tiny_dna_collection(base_len=200_000, k=6)
+    want = O.build(a, hf).export()
+    da = torch.from_numpy(a.data).cuda()
+    ctx.set_graph(True)
+    modes = []
+    for _ in range(6):
+        g = ctx.build(da, a.offsets)
+        modes.append(ctx.last_build_stats()["graph"])
+        assert O.grammars_equal(g.export(), want)
+        g.free()
+    # launches or a capture first (the plan may not fit at once), then the
+    # captured graph is launched from the second graph build on
+    first = next(i for i, m in enumerate(modes) if m == 1)
+    assert first <= 2, modes
+    assert all(m == 2 for m in modes[first + 1:]), modes
