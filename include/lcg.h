@@ -173,6 +173,18 @@ int lcg_get_tuning(const lcg_ctx* ctx, lcg_tuning* t);
  * `out` (host) and their number into *count. */
 int lcg_last_kernel_times(const lcg_ctx* ctx, lcg_kernel_time* out, uint32_t cap, uint32_t* count);
 
+/* One timed kernel launch of the last call (kernel timing on). */
+typedef struct lcg_kernel_launch {
+    char name[24];       /* kernel kind, e.g. "k_parse" */
+    uint32_t round;      /* BuildGram round of a build's launch (1 = bytes), 0 for others */
+    uint32_t pad;
+    double ms;           /* CUDA-event time of the launch */
+    double bytes;        /* algorithmic bytes of the launch */
+} lcg_kernel_launch;
+/* Copy up to `cap` of the last call's timed launches, in launch order, into
+ * `out` (host) and their number into *count. */
+int lcg_last_kernel_launches(const lcg_ctx* ctx, lcg_kernel_launch* out, uint32_t cap, uint32_t* count);
+
 /* BuildGram(T, H) (Sec. 3.3).
  * data: the k strings concatenated (uint8), `data_on_device` = 1 when it is a
  *       device pointer, 0 when it is host memory (copied in by the call).

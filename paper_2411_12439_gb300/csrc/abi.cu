@@ -102,6 +102,7 @@ struct lcg_ctx {
     std::vector<KRec> krecs;
     std::vector<cudaEvent_t> evpool;
     std::vector<lcg_kernel_time> ktimes;
+    std::vector<lcg_kernel_launch> klaunches;
 };
 
 namespace {
@@ -169,6 +170,7 @@ void kt_reset(lcg_ctx* ctx) {
     }
     ctx->krecs.clear();
     ctx->ktimes.clear();
+    ctx->klaunches.clear();
 }
 
 // Record the start of a launch of kernel `name` that moves `bytes` algorithmic
@@ -188,9 +190,16 @@ void kt_end(lcg_ctx* ctx, int h) {
 // After the call's last synchronisation: sum the times per kernel kind.
 void kt_collect(lcg_ctx* ctx) {
     ctx->ktimes.clear();
+    ctx->klaunches.clear();
     for (auto& r : ctx->krecs) {
         float ms = 0.f;
         ck(ctx, cudaEventElapsedTime(&ms, r.a, r.b), "cudaEventElapsedTime");
+        lcg_kernel_launch kl{};
+        std::strncpy(kl.name, r.name, sizeof(kl.name) - 1);
+        kl.round = r.round;
+        kl.ms = ms;
+        kl.bytes = r.bytes;
+        ctx->klaunches.push_back(kl);
         lcg_kernel_time* t = nullptr;
         for (auto& x : ctx->ktimes)
             if (std::strncmp(x.name, r.name, sizeof(x.name)) == 0) t = &x;
@@ -596,6 +605,10 @@ void enqueue_parse(lcg_ctx* ctx, RoundArgs& a, u64 n_for_bytes) {
     int ht = kt_begin(ctx, "k_tile_strings", 4.0 * (double)a.tiles_bound, a.level);
     ck(ctx, launch_tile_strings(a, ctx->st), "k_tile_strings");
     kt_end(ctx, ht);
+    // k_breaks' look-ahead words live in the look-back buffer (sized for the
+    // round's parse tiles, four per block step of k_breaks)
+    a.lb1 = ctx->lb1;
+    a.brk_epoch = ++ctx->epoch;
     int hb = kt_begin(ctx, "k_breaks", (a.sym_bytes == 1 ? 1.0 : 4.0) * n_for_bytes + (double)n_for_bytes / 8.0, a.level);
     ck(ctx, launch_breaks(a, ctx->st), "k_breaks");
     kt_end(ctx, hb);
@@ -1862,6 +1875,13 @@ int lcg_last_kernel_times(const lcg_ctx* ctx, lcg_kernel_time* out, uint32_t cap
     if (!ctx || !count) return LCG_EINVAL;
     *count = (uint32_t)ctx->ktimes.size();
     for (uint32_t x = 0; x < cap && x < ctx->ktimes.size(); x++) out[x] = ctx->ktimes[x];
+    return LCG_OK;
+}
+
+int lcg_last_kernel_launches(const lcg_ctx* ctx, lcg_kernel_launch* out, uint32_t cap, uint32_t* count) {
+    if (!ctx || !count) return LCG_EINVAL;
+    *count = (uint32_t)ctx->klaunches.size();
+    for (uint32_t x = 0; x < cap && x < ctx->klaunches.size(); x++) out[x] = ctx->klaunches[x];
     return LCG_OK;
 }
 

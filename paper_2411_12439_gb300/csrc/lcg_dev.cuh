@@ -41,6 +41,65 @@ struct LevelHash {
     u64 mmask;  // m - 1
 };
 
+// c^e mod p (square and multiply).
+__device__ __forceinline__ u64 powmod61(u64 c, u64 e) {
+    u64 r = 1;
+    while (e) {
+        if (e & 1) r = mulmod61(r, c);
+        c = mulmod61(c, c);
+        e >>= 1;
+    }
+    return r;
+}
+
+// H = sum_{j < len} v(j) c^j mod p (the polynomial of Eq. fast_hash), by a
+// whole warp: every lane calls it with the same len and c.  Lane l takes the
+// terms j = l, l + 32, ...: h_l = sum_k v(32k + l) (c^32)^k by Horner over
+// k, read 32 consecutive terms per warp step; then H = sum_l c^l h_l.
+// Every lane returns H.  v(j) must be < p.
+template <typename V>
+__device__ __forceinline__ u64 warp_poly61(V v, u64 len, u64 c) {
+    const u32 lane = threadIdx.x & 31;
+    const u64 c32 = powmod61(c, 32);
+    constexpr int U = 4;  // terms read before they enter the dependent chain
+    u64 h = 0;
+    u64 kk = (len + 31) / 32;
+    while (kk > 0) {
+        const int m = kk < (u64)U ? (int)kk : U;
+        u64 x[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const u64 j = 32 * (kk - 1 - (u64)u) + lane;
+            x[u] = (u < m && j < len) ? (u64)v(j) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (u < m) h = addmod61(mulmod61(h, c32), x[u]);
+        kk -= (u64)m;
+    }
+    h = mulmod61(h, powmod61(c, lane));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) h = addmod61(h, __shfl_xor_sync(0xffffffffu, h, o));
+    return h;
+}
+
+// a(j) == b(j) for every j < len, by a whole warp (every lane gets the answer).
+template <typename A, typename B>
+__device__ __forceinline__ bool warp_equal(A a, B b, u64 len) {
+    const u32 lane = threadIdx.x & 31;
+    constexpr int U = 8;
+    for (u64 j0 = 0; j0 < len; j0 += 32 * U) {
+        bool ok = true;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const u64 j = j0 + 32 * (u64)u + lane;
+            if (j < len) ok = ok && (a(j) == b(j));
+        }
+        if (!__all_sync(0xffffffffu, ok)) return false;
+    }
+    return true;
+}
+
 // ((a * H + b) mod p) mod m for a polynomial value H < p (Eq. fast_hash).
 __device__ __forceinline__ u32 finish_hash(const LevelHash& h, u64 H) {
     return (u32)(addmod61(mulmod61(h.a, H), h.b) & h.mmask);

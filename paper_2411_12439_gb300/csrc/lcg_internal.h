@@ -66,8 +66,9 @@ struct RoundArgs {
     u32* tile_cnt;        // per parse tile: phrases starting in it
     u64* tile_pfx;        // exclusive prefix of tile_cnt: global index of a tile's first phrase
     u64* string_first;    // order key (tile * TP + q) of each active string's first phrase
-    void* lb1;            // look-back slots
+    void* lb1;            // look-back slots (k_breaks: the heads of its block steps)
     u64 epoch;
+    u64 brk_epoch;        // epoch of k_breaks' look-ahead words
     u64* ctr;
     u64 ctr_base;
     u64* total;           // device: phrases of the round

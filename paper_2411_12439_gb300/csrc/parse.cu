@@ -128,15 +128,12 @@ constexpr int kProbeGroup = 2;
 // (byte rounds read staged fingerprints and take one at a time).
 constexpr int kHornerBatchR = 8;
 constexpr int kCompareBatchR = 4;
-
-template <typename T>
-__device__ u64 scan_right_diff(const T* S, FpSource<T> fp, u64 from, u64 strend, u32 val) {
-    for (u64 y = from; y < strend; y++) {
-        const u32 fy = fp(S[y]);
-        if (fy != val) return fy;
-    }
-    return kNone;
-}
+// Phrases longer than kLongLen (N-runs of DNA, repeated text) are hashed and
+// compared by a whole warp after the tile's other phrases: a thread alone
+// would spend a round trip per symbol on them while its block waits.  Their
+// starts are more than kLongLen apart, so a tile holds at most kLongBuf.
+constexpr int kLongLen = 32;
+constexpr int kLongBuf = kTP / (kLongLen + 1) + 1;
 
 // Load n_sym symbols of type V from src (16-byte aligned when `vec`) into the
 // shared array dst, with every 16-byte load issued before any is stored.
@@ -178,13 +175,54 @@ __device__ __forceinline__ void stage_vec(V* dst, const V* src, int n_sym, bool 
 // position's type is decided by the first of these at or above it, so the S
 // mask is gt spread down over the undecided positions (five doubling steps).
 // Positions above the thread's last decision take the type of the next
-// thread's first position, found through per-thread summaries (and, past the
-// block step, in global memory).  Then breaks = starts | ((lt << 1) & S), bit 0
-// using f of the position before.
+// thread's first position, found through per-thread summaries; past the block
+// step, the type of the next step's first position.  Then breaks = starts |
+// ((lt << 1) & S), bit 0 using f of the position before.
+//
+// A run of equal fingerprints can span many block steps (N-runs of DNA).
+// Block steps are therefore taken in decreasing order from a counter, and
+// each publishes the type of its first position (its "head") as soon as its
+// masks are known: decided, or "open" when the whole step is one run.  A step
+// whose last position is undecided reads the heads of the steps after it,
+// skipping open ones, until one is decided (a look-ahead over steps that were
+// all taken before it, so every wait ends); an open step then publishes the
+// type it found as its head.  Each step reads its own positions once, however
+// long the run.
 
 constexpr int kBrkThreads = 256;
 constexpr u64 kBrkSpan = (u64)kBrkThreads * 32;  // positions per block step
 static_assert(kBrkSpan % kTP == 0, "a block step starts a parse tile");
+
+// Head of block step b in the look-ahead words: (epoch << 8) | (state << 2) |
+// type, state 1 = open, 2 = decided.
+__device__ __forceinline__ void brk_publish(u64* heads, u64 b, u64 epoch, u32 state, u32 type) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(heads + b), "l"((epoch << 8) | (state << 2) | type)
+                 : "memory");
+}
+
+// Type of the first position of step j (the run continues into it), looking
+// further right past open steps.  `none` is the type past the last step.
+__device__ u32 brk_lookahead(const u64* heads, u64 j, u64 nsteps, u64 epoch, u32 none, DevStatus* ds) {
+    for (; j < nsteps; j++) {
+        u64 it = 0;
+        u32 backoff = 32;
+        while (true) {
+            u64 w;
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(heads + j) : "memory");
+            if ((w >> 8) == epoch) {
+                if (((w >> 2) & 3u) == 2u) return (u32)(w & 3u);
+                break;  // open: one run throughout, look at the next step
+            }
+            if (++it > kSpinLimit || vload(&ds->error) != 0) {
+                set_error(ds, kErrTimeout);
+                return none;
+            }
+            __nanosleep(backoff);
+            if (backoff < 256) backoff <<= 1;
+        }
+    }
+    return none;
+}
 
 // Spread the bits of `src` down over the positions of `pass` (positions that
 // take the value of the position above): bit i of the result is src[j] for
@@ -208,11 +246,12 @@ __global__ void __launch_bounds__(kBrkThreads) k_breaks(const RoundArgs a, u64 n
     __shared__ u32 sF0[kByte ? 256 : 1];
     __shared__ u32 sst[SW + 1];      // string starts at base .. base + kBrkSpan
     __shared__ u32 sfirst[kBrkThreads];  // type of each thread's first position
+    __shared__ u64 s_step;
+    __shared__ u32 s_open, s_carry;
     if (round_halted(a)) return;
     const T* S = (const T*)a.S;
     const u32* Sf = a.Sf;
     const u64 n = round_n(a);
-    const u32 k = round_k(a);
     const int tid = threadIdx.x, lane = tid & 31;
     if constexpr (kByte)
         for (int x = tid; x < 256; x += kBrkThreads) sF0[x] = a.Fprev[x];
@@ -222,8 +261,18 @@ __global__ void __launch_bounds__(kBrkThreads) k_breaks(const RoundArgs a, u64 n
     const bool aligned = kByte ? (reinterpret_cast<unsigned long long>(S) & 15) == 0
                                : (reinterpret_cast<unsigned long long>(Sf) & 15) == 0;
     nblocks = min(nblocks, (n + kBrkSpan - 1) / kBrkSpan);
-    if constexpr (kByte) __syncthreads();
-    for (u64 b = blockIdx.x; b < nblocks; b += gridDim.x) {
+    if (blockIdx.x >= nblocks && blockIdx.x > 0) return;  // more blocks than steps: no counter traffic
+    u64* heads = reinterpret_cast<u64*>(a.lb1);
+    const int warp = tid >> 5;
+    while (true) {
+        // the next block step, in decreasing order (the counter starts at 0 every round)
+        if (tid == 0) {
+            const u64 t = atomicAdd(&a.ds->aux[0], 1ull);
+            s_step = t < nblocks ? nblocks - 1 - t : ~0ull;
+        }
+        __syncthreads();  // also: sF0 loaded
+        const u64 b = s_step;
+        if (b == ~0ull) break;
         const u64 base = b * kBrkSpan;
         const u64 bend = min(base + kBrkSpan, n);
         // string starts (bitmap of k_tile_strings; n counts as one)
@@ -282,28 +331,40 @@ __global__ void __launch_bounds__(kBrkThreads) k_breaks(const RoundArgs a, u64 n
         u32 lm = spread_down(lt, ~dec);
         // type of the thread's first position (or undecided: one run throughout)
         sfirst[tid] = dec == 0 ? kUndecided : (sm & 1u) ? kTypeS : (lm & 1u) ? kTypeL : kTypeU;
+        const bool open = dec != (u32)~0u && ((dec >> 31) & 1u) == 0;  // positions above the last decision
+        if (tid == kBrkThreads - 1) s_open = open ? 1u : 0u;
         __syncthreads();
-        if (dec != (u32)~0u && ((dec >> 31) & 1u) == 0) {
-            // positions above the last decision take the type of position x0 + 32
-            u32 carry = kTypeU;
-            u64 y = x0 + 32;
-            u32 t = (u32)tid + 1;
-            while (true) {
-                if (y >= bend) {
-                    if (y >= n) { carry = kTypeU; break; }
-                    // past the block step: first fingerprint after the run, in global memory
-                    const u32 v = f[31];
-                    const u32 j = string_of(a.soff, k, y - 1);
-                    const u64 strend = __ldg(a.soff + j + 1);
-                    u64 nd = kNone;
-                    if (y < strend) nd = scan_right_diff<T>(S, FpSource<T>{kByte ? sF0 : a.Fprev}, y, strend, v);
-                    carry = nd == kNone ? kTypeU : (nd > (u64)v ? kTypeS : kTypeL);
+        if (warp == 0) {
+            // the step's head: the type of the first thread whose first position is decided
+            u32 head = kUndecided;
+            for (int c = 0; c < kBrkThreads / 32; c++) {
+                const u32 v = sfirst[c * 32 + lane];
+                const unsigned m = __ballot_sync(0xffffffffu, v != kUndecided);
+                if (m) {
+                    head = __shfl_sync(0xffffffffu, v, __ffs(m) - 1);
                     break;
                 }
+            }
+            if (lane == 0) {
+                brk_publish(heads, b, a.brk_epoch, head == kUndecided ? 1u : 2u, head == kUndecided ? 0u : head);
+                // type of the next step's first position (the last thread's run goes on there)
+                u32 carry = kTypeU;
+                if (bend < n && s_open) carry = brk_lookahead(heads, b + 1, nblocks, a.brk_epoch, kTypeU, a.ds);
+                if (head == kUndecided) brk_publish(heads, b, a.brk_epoch, 2u, carry);
+                s_carry = carry;
+            }
+        }
+        __syncthreads();
+        if (open) {
+            // positions above the last decision take the type of position x0 + 32:
+            // the first decided thread after this one, else the next step's head
+            u32 carry = s_carry;
+            for (int t = tid + 1; t < kBrkThreads; t++) {
                 const u32 c = sfirst[t];
-                if (c != kUndecided) { carry = c; break; }
-                y += 32;
-                t++;
+                if (c != kUndecided) {
+                    carry = c;
+                    break;
+                }
             }
             const int hi = 31 - __clz(dec | 1u);  // highest decided position (or 0)
             const u32 top = dec == 0 ? ~0u : ~((2u << hi) - 1u);
@@ -373,6 +434,8 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
     __shared__ Key128 sMissKey[kLocal ? kMissBuf : 1];
     __shared__ u64 sMissOk[kLocal ? kMissBuf : 1];
     __shared__ u32 s_nmiss;
+    __shared__ unsigned short sLong[kLongBuf];  // tile offsets (q) of the tile's long phrases
+    __shared__ u32 s_nlong;
     __shared__ u64 s_tail_end;
     __shared__ u32 s_nclaim;
     __shared__ u64 s_claim_len;
@@ -403,6 +466,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
         s_nclaim = 0;
         s_claim_len = 0;
         s_nmiss = 0;
+        s_nlong = 0;
     }
 
     // persistent blocks: tiles blockIdx.x, blockIdx.x + gridDim.x, ...  Tiles
@@ -616,6 +680,11 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
             atomicAdd(&s_claim_len, len);
             claim_one(slot, len, atomicAdd(&s_nclaim, 1u));
         };
+        auto defer_long = [&](u32 q) {
+            const u32 x = atomicAdd(&s_nlong, 1u);
+            if (x < (u32)kLongBuf) sLong[x] = (unsigned short)q;
+            else set_error(a.ds, kErrCapacity);  // not reached: long phrases start > kLongLen apart
+        };
 
         if constexpr (kLocal) {
             // Short phrases go through the block's cache.  Its entries come
@@ -652,6 +721,10 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                 const u32 st = sP[q];
                 const u64 en = phrase_end(q);
                 const u64 len = en - st;
+                if (len > (u64)kLongLen) {  // a whole warp takes it below
+                    defer_long(q);
+                    continue;
+                }
                 u32 slot = ~0u;
                 int free_h = -1;
                 if (len <= 7 && en <= (u64)ns) {
@@ -727,13 +800,64 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                 if (q < cntq) {
                     const u64 st = sP[q], en = phrase_end(q);
                     len = en - st;
-                    slot = lookup(q, st, en, &claimed);
-                    __stcs(a.P_slot + okey0 + q, slot);
+                    if (len > (u64)kLongLen) {  // a whole warp takes it below
+                        defer_long(q);
+                        len = 0;
+                    } else {
+                        slot = lookup(q, st, en, &claimed);
+                        __stcs(a.P_slot + okey0 + q, slot);
+                    }
                 }
                 claim_warp(claimed, slot, len);
             }
         }
         __syncthreads();
+
+        // 4b. long phrases, one warp each: the fingerprint polynomial H
+        //     (Eq. fast_hash) and the content comparisons of a hashed key are
+        //     spread over the warp's lanes
+        const u32 nlong = s_nlong;
+        for (u32 i = warp; i < nlong; i += kParseThreads / 32) {
+            const u32 q = sLong[i];
+            const u64 st = sP[q], en = phrase_end(q), len = en - st;
+            const u64 pos = t0 + st;  // the phrase's position in S
+            u32 slot = ~0u;
+            bool claimed = false;
+            if (len > kMaxPhraseLen) {
+                if (lane == 0) set_error(a.ds, kErrPhraseLong);
+            } else {
+                u64 H;
+                if constexpr (kByte) {
+                    H = warp_poly61([&](u64 j) -> u64 { return fp((unsigned char)sym(st + j)); }, len, a.lh.c);
+                } else {
+                    H = warp_poly61([&](u64 j) -> u64 { return __ldg(a.Sf + pos + j); }, len, a.lh.c);
+                }
+                const Key128 key = key_hashed(H, len, pos);
+                u64 r = ~0ull;
+                if (rt.cap)
+                    r = table_find_warp(rt, key, [&](u64 rank) {
+                        const u64 o = a.rrhs_off[rank];
+                        return warp_equal([&](u64 j) { return (u32)S[pos + j]; },
+                                          [&](u64 j) { return a.rrhs[o + j]; }, len);
+                    });
+                if (r != ~0ull) {
+                    slot = kResidentBit | (u32)r;
+                } else {
+                    slot = (u32)table_claim_or_find_warp(bt, key, okey0 + q, [&](u64 ref) {
+                        return warp_equal([&](u64 j) { return S[ref + j]; }, [&](u64 j) { return S[pos + j]; }, len);
+                    }, &claimed, a.ds);
+                }
+            }
+            if (lane == 0) {
+                __stcs(a.P_slot + okey0 + q, slot);
+                if (claimed) claim_single(slot, len);
+            }
+        }
+        if (nlong) {
+            __syncthreads();
+            if (tid == 0) s_nlong = 0;
+            __syncthreads();
+        }
 
         // 5. outputs: phrase slots (tile-major), the tile's phrase count, and
         //    the order key of the first phrase of every string starting here
@@ -970,30 +1094,62 @@ __global__ void k_rules(const RoundArgs a) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_error(a.ds, kErrCapacity);
         return;
     }
-    for (u64 r = blockIdx.x * (u64)blockDim.x + threadIdx.x; r < g_new; r += (u64)gridDim.x * blockDim.x) {
-        const u32 slot = a.slot_r[r];
-        if (slot >= a.tab_cap) {
-            set_error(a.ds, kErrCapacity);
-            continue;
-        }
-        const Key128 k = ((const Key128*)a.rkey)[r];  // the rule's key, in rank order (k_rank)
-        const u64 len = key_len(k);
-        const bool hashed = key_is_hashed(k);
-        const u64 off = a.G_base + a.xlen[r];
-        const u64 rank = a.g_base + r;
-        a.rhs_off[rank] = off;
-        auto get = [&](u64 j) -> u32 { return hashed ? (u32)S[k.lo + j] : key_sym(k, j, a.sym_w); };
-        u64 H = 0;
-        for (u64 j = len; j-- > 0;) {
-            const u32 v = get(j);
-            a.rhs[off + j] = v;
-            H = addmod61(mulmod61(H, a.lh.c), (u64)__ldg(a.Fprev + v));
-        }
+    // whole warps step through the ranks, so that a warp can take its long
+    // rules (more than kLongLen symbols) together after its short ones
+    const u32 lane = threadIdx.x & 31;
+    auto finish_rule = [&](u32 slot, const Key128& k, u64 len, bool hashed, u64 rank, u64 H) {
         const u32 fpv = finish_hash(a.lh, H);
         a.F[rank] = fpv;
         a.rv[slot] = ((u64)fpv << 32) | rank;  // for the rewrite: rank and fingerprint, dense by slot
         if (rw.cap) table_put(rw, hashed ? key_hashed(H, len, rank) : k, rank, a.ds);
-        if (r == 0) a.rhs_off[a.g_base + g_new] = a.G_base + G_new;
+    };
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    for (u64 r0 = blockIdx.x * (u64)blockDim.x + (threadIdx.x & ~31u); r0 < g_new; r0 += stride) {
+        const u64 r = r0 + lane;
+        bool longr = false;
+        if (r < g_new) {
+            const u32 slot = a.slot_r[r];
+            if (slot >= a.tab_cap) {
+                set_error(a.ds, kErrCapacity);
+            } else {
+                const Key128 k = ((const Key128*)a.rkey)[r];  // the rule's key, in rank order (k_rank)
+                const u64 len = key_len(k);
+                const bool hashed = key_is_hashed(k);
+                const u64 off = a.G_base + a.xlen[r];
+                const u64 rank = a.g_base + r;
+                a.rhs_off[rank] = off;
+                if (len > (u64)kLongLen) {
+                    longr = true;
+                } else {
+                    auto get = [&](u64 j) -> u32 { return hashed ? (u32)S[k.lo + j] : key_sym(k, j, a.sym_w); };
+                    u64 H = 0;
+                    for (u64 j = len; j-- > 0;) {
+                        const u32 v = get(j);
+                        a.rhs[off + j] = v;
+                        H = addmod61(mulmod61(H, a.lh.c), (u64)__ldg(a.Fprev + v));
+                    }
+                    finish_rule(slot, k, len, hashed, rank, H);
+                }
+            }
+            if (r == 0) a.rhs_off[a.g_base + g_new] = a.G_base + G_new;
+        }
+        // long rules (hashed keys: the content is read at the first occurrence
+        // k.lo), one at a time by the whole warp
+        unsigned m = __ballot_sync(0xffffffffu, longr);
+        while (m) {
+            const u64 rr = r0 + (u64)(__ffs(m) - 1);
+            m &= m - 1;
+            const u32 slot = a.slot_r[rr];
+            const Key128 k = ((const Key128*)a.rkey)[rr];
+            const u64 len = key_len(k);
+            const u64 off = a.G_base + a.xlen[rr];
+            const u64 H = warp_poly61([&](u64 j) -> u64 {
+                const u32 v = (u32)S[k.lo + j];
+                a.rhs[off + j] = v;
+                return __ldg(a.Fprev + v);
+            }, len, a.lh.c);
+            if (lane == 0) finish_rule(slot, k, len, true, a.g_base + rr, H);
+        }
     }
 }
 

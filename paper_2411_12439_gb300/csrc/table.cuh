@@ -195,6 +195,69 @@ __device__ u64 table_claim_or_find(ContentTable t, const Key128& k, bool hashed,
     return ~0ull;
 }
 
+// table_claim_or_find by a whole warp for one hashed key (a long phrase): every
+// lane calls it with the same arguments.  Lane 0 reads and claims the slots, in
+// the same probe order as table_claim_or_find (so both find a key wherever the
+// other put it); `same(ref)` is a warp-wide content comparison run by all lanes.
+// Every lane returns the slot and *claimed.
+template <typename SameWarp>
+__device__ u64 table_claim_or_find_warp(ContentTable t, const Key128& k, u64 pidx, SameWarp same, bool* claimed,
+                                        DevStatus* ds) {
+    const u32 lane = threadIdx.x & 31;
+    u64 s = key_home(k, t.cap);
+    const Key128 empty{~0ull, ~0ull};
+    const u64 limit = t.cap < kMaxProbes ? t.cap : kMaxProbes;
+    *claimed = false;
+    for (u64 probe = 0; probe < limit; probe++) {
+        Key128 cur{0, 0};
+        int took = 0, stop = 0;
+        if (lane == 0) {
+            if ((probe & 15) == 15 && vload(&ds->overflow)) stop = 1;
+            Key128* kp = &t.slots[s].key;
+            cur = ld_key_relaxed(kp);
+            if (!stop && cur.hi == kEmptyHi) {
+                const Key128 old = cas_key(kp, empty, k);
+                if (old.hi == kEmptyHi) {
+                    took = 1;
+                    atomicMin(&t.slots[s].val, pidx);
+                }
+                cur = old;
+            }
+            if (!stop && !took && cur.hi == k.hi && cur.lo == ~0ull) cur = cas_key(kp, empty, empty);
+        }
+        stop = __shfl_sync(0xffffffffu, stop, 0);
+        if (stop) return ~0ull;
+        took = __shfl_sync(0xffffffffu, took, 0);
+        if (took) {
+            *claimed = true;
+            return s;
+        }
+        cur.lo = __shfl_sync(0xffffffffu, cur.lo, 0);
+        cur.hi = __shfl_sync(0xffffffffu, cur.hi, 0);
+        if (cur.hi == k.hi && same(cur.lo)) {
+            if (lane == 0) atomicMin(&t.slots[s].val, pidx);
+            return s;
+        }
+        s = (s + 1 == t.cap) ? 0 : s + 1;
+    }
+    if (lane == 0) atomicExch(&ds->overflow, 1u);
+    return ~0ull;
+}
+
+// table_find by a whole warp for one hashed key; `same(lo)` is a warp-wide
+// comparison.  Every lane returns the value, or ~0 when absent.
+template <typename SameWarp>
+__device__ u64 table_find_warp(const ContentTable& t, const Key128& k, SameWarp same) {
+    u64 s = key_home(k, t.cap);
+    for (u64 probe = 0; probe < t.cap; probe++) {
+        const Key128 cur = t.slots[s].key;  // the same address on every lane
+        if (cur.hi == kEmptyHi) return ~0ull;
+        if (cur.hi == k.hi && same(cur.lo)) return t.slots[s].val;
+        s = (s + 1 == t.cap) ? 0 : s + 1;
+    }
+    return ~0ull;
+}
+
 // Look a key up in a table that nobody writes during the call.  `same(lo)`
 // confirms hashed keys.  Returns the slot's value, or ~0 when absent.
 template <typename Same>

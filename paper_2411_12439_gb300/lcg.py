@@ -29,6 +29,7 @@ SYMBOLS = [
     "lcg_export_start", "lcg_string_roots", "lcg_import", "lcg_packed_size", "lcg_export_packed", "lcg_import_packed",
     "lcg_grammar_free", "lcg_postprocess", "lcg_pp_stats_of", "lcg_pp_export", "lcg_pp_free",
     "lcg_vbyte_encode", "lcg_vbyte_decode", "lcg_vbyte_size", "lcg_export_vbyte", "lcg_import_vbyte",
+    "lcg_last_kernel_launches",
 ]
 
 
@@ -52,6 +53,11 @@ class RoundStatsC(ctypes.Structure):
 
 class KernelTimeC(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+                ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+class KernelLaunchC(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("round", ctypes.c_uint32), ("pad", ctypes.c_uint32),
                 ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
@@ -101,6 +107,7 @@ def load(build_if_missing: bool = True):
     lib.lcg_get_tuning.argtypes = [P, ctypes.POINTER(TuningC)]
     lib.lcg_set_graph.argtypes = [P, I]
     lib.lcg_last_kernel_times.argtypes = [P, P, U32, ctypes.POINTER(U32)]
+    lib.lcg_last_kernel_launches.argtypes = [P, P, U32, ctypes.POINTER(U32)]
     lib.lcg_build.argtypes = [P, P, P, U32, I, PP]
     lib.lcg_build_into.argtypes = [P, P, P, P, U32, I]
     lib.lcg_merge.argtypes = [P, P, P]
@@ -331,6 +338,18 @@ class Context:
         self._check(load().lcg_last_kernel_times(self._h, ctypes.cast(buf, ctypes.c_void_p), 32, ctypes.byref(cnt)))
         return {buf[i].name.decode(): {"launches": int(buf[i].launches), "ms": float(buf[i].ms),
                                        "bytes": float(buf[i].bytes)} for i in range(min(cnt.value, 32))}
+
+    def last_kernel_launches(self) -> list:
+        """lcg_last_kernel_launches: [{"name", "round", "ms", "bytes"}] of the
+        last call's timed launches, in launch order."""
+        lib = load()
+        cnt = ctypes.c_uint32(0)
+        self._check(lib.lcg_last_kernel_launches(self._h, None, 0, ctypes.byref(cnt)))
+        n = cnt.value
+        buf = (KernelLaunchC * max(n, 1))()
+        self._check(lib.lcg_last_kernel_launches(self._h, ctypes.cast(buf, ctypes.c_void_p), n, ctypes.byref(cnt)))
+        return [{"name": buf[i].name.decode(), "round": int(buf[i].round), "ms": float(buf[i].ms),
+                 "bytes": float(buf[i].bytes)} for i in range(min(n, cnt.value))]
 
     def last_build_stats(self) -> dict:
         st = BuildStatsC()
