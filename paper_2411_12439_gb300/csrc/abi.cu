@@ -449,7 +449,7 @@ void free_round_input(lcg_ctx* ctx, RoundInput& in) {
 
 // Buffers of one round.
 struct RoundBufs {
-    u64 tiles = 0, Pmax = 0, cap = 0, g_alloc = 0;
+    u64 tiles = 0, Pmax = 0, Tcap = 0, cap = 0, g_alloc = 0;
     u64* string_first = nullptr;
     u64* soff_next = nullptr;
     u32* sid_next = nullptr;
@@ -477,7 +477,16 @@ struct RoundBufs {
     u64* rkey = nullptr;
 };
 
-void alloc_round(lcg_ctx* ctx, RoundBufs& b, u64 n_bound, u32 kk) {
+// The next sequence (Tnext, Fnext) gets `t_cap` entries; 0 leaves it to
+// alloc_next (a round run with a host synchronisation knows its phrase count
+// after the parse).
+void alloc_next(lcg_ctx* ctx, RoundBufs& b, u64 t_cap) {
+    b.Tcap = std::min<u64>(t_cap, b.Pmax);
+    b.Tnext = dalloc<u32>(ctx, b.Tcap);
+    b.Fnext = dalloc<u32>(ctx, b.Tcap);
+}
+
+void alloc_round(lcg_ctx* ctx, RoundBufs& b, u64 n_bound, u32 kk, u64 t_cap) {
     b.tiles = (n_bound + parse_tile_positions(1) - 1) / parse_tile_positions(1);
     // every phrase but a string's first has length >= 2
     b.Pmax = n_bound / 2 + 2ull * kk + 1;
@@ -489,8 +498,7 @@ void alloc_round(lcg_ctx* ctx, RoundBufs& b, u64 n_bound, u32 kk) {
     b.P_slot = dalloc<u32>(ctx, b.tiles * parse_tile_positions(1));
     b.tile_cnt = dalloc<u32>(ctx, b.tiles);
     b.tile_pfx = dalloc<u64>(ctx, b.tiles);
-    b.Tnext = dalloc<u32>(ctx, b.Pmax);
-    b.Fnext = dalloc<u32>(ctx, b.Pmax);
+    if (t_cap) alloc_next(ctx, b, t_cap);
     b.tile_str = dalloc<u32>(ctx, b.tiles);
     b.brk = dalloc<u32>(ctx, b.tiles * parse_tile_positions(1) / 32);
     b.sbm_words = b.tiles * parse_tile_positions(1) / 32 + 2;  // positions 0 .. n inclusive
@@ -583,7 +591,7 @@ RoundArgs round_args(lcg_ctx* ctx, lcg_grammar* R, const RoundInput& in, RoundBu
     a.R_phr = b.R_phr;
     a.R_sid = b.R_sid;
     a.P_slot = b.P_slot;
-    a.T_cap = b.Pmax;
+    a.T_cap = b.Tcap;
     a.Tnext = b.Tnext;
     a.Fnext = b.Fnext;
     a.c_level = R->c_level;
@@ -709,7 +717,7 @@ void round_sync(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32 i, bool agains
     rs.n = n;
     rs.strings = in.kk;
     RoundBufs b;
-    alloc_round(ctx, b, n, in.kk);
+    alloc_round(ctx, b, n, in.kk, 0);
     const u64 tiles = b.tiles;
     ensure_lb(ctx, &ctx->lb1, &ctx->lb1_tiles, tiles, lb1_bytes(tiles));
     Level& L = R->lv[i - 1];
@@ -779,6 +787,10 @@ void round_sync(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32 i, bool agains
         L.rvalid = false;
     }
     alloc_naming(ctx, b, g_new);
+    alloc_next(ctx, b, P + 1);  // the next sequence: exactly the round's phrases
+    a.Tnext = b.Tnext;
+    a.Fnext = b.Fnext;
+    a.T_cap = b.Tcap;
     a.g_base = L.g;
     a.G_base = L.G;
     a.cap_g = L.cap_g;
@@ -800,7 +812,7 @@ void round_sync(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32 i, bool agains
 // planned from the context's hints (new rules per phrase, phrases per symbol,
 // symbols per rule of each level) and its plan slack.
 struct RoundPlan {
-    u64 n_bound = 0, n_est = 0, cap = 0, g_alloc = 0, G_alloc = 0;
+    u64 n_bound = 0, n_est = 0, n_alloc = 0, cap = 0, g_alloc = 0, G_alloc = 0, t_cap = 0;
     double P_est = 0, g_est = 0, G_est = 0;
 };
 
@@ -824,6 +836,9 @@ std::vector<RoundPlan> plan_rounds(lcg_ctx* ctx, u64 n1, u32 kk, u32 planned) {
         RoundPlan& p = v[r];
         p.n_bound = n_bound;
         p.n_est = n_est;
+        // the round's sequence is at most the planned next sequence of the
+        // round before (which flags a capacity error past it)
+        p.n_alloc = (r == 1) ? n_bound : std::min<u64>(n_bound, v[r - 1].t_cap);
         p.P_est = ctx->p_hint[r] * (double)n_est;
         p.g_est = ctx->ratio_hint[r] * p.P_est;
         p.G_est = ctx->glen_hint[r] * p.g_est;
@@ -834,6 +849,9 @@ std::vector<RoundPlan> plan_rounds(lcg_ctx* ctx, u64 n1, u32 kk, u32 planned) {
                               kMaxRank + 1);
         p.g_alloc = bucket((u64)(p.g_est * 1.25 * sl) + 1024);
         p.G_alloc = bucket((u64)(p.G_est * 1.25 * sl) + 4096);
+        // the next sequence: the estimated phrases with the same slack (a
+        // round past it flags a capacity error and the build is redone)
+        p.t_cap = std::min<u64>(bucket((u64)(p.P_est * 1.1 * sl) + 4096), n_bound / 2 + 2ull * kk + 1);
         n_bound = n_bound / 2 + 2ull * kk + 1;  // every phrase but a string's first has length >= 2
         n_est = (u64)p.P_est + 64;
     }
@@ -861,7 +879,7 @@ void rounds_async_enqueue(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, AsyncRou
         if (R->lv.size() < r) R->lv.emplace_back();
         Level& L = R->lv[r - 1];
         RoundBufs b;
-        alloc_round(ctx, b, p.n_bound, kk);
+        alloc_round(ctx, b, p.n_alloc, kk, p.t_cap);
         ensure_lb(ctx, &ctx->lb1, &ctx->lb1_tiles, b.tiles, lb1_bytes(b.tiles));
         RoundArgs a = round_args(ctx, R, in, b, r);
         // a round stops early when the one before it failed
@@ -1020,8 +1038,8 @@ bool plan_covers(const std::vector<RoundPlan>& have, const std::vector<RoundPlan
     for (size_t r = 1; r < have.size(); r++) {
         const RoundPlan& h = have[r];
         const RoundPlan& n = need[r];
-        if (h.n_bound != n.n_bound || h.cap < n.cap || h.cap > 4 * n.cap || h.g_alloc < n.g_alloc ||
-            h.G_alloc < n.G_alloc)
+        if (h.n_bound != n.n_bound || h.n_alloc < n.n_alloc || h.cap < n.cap || h.cap > 4 * n.cap ||
+            h.g_alloc < n.g_alloc || h.G_alloc < n.G_alloc || h.t_cap < n.t_cap)
             return false;
     }
     return true;
@@ -1043,9 +1061,13 @@ void destroy_graph(lcg_ctx* ctx) {
     }
     if (gb->soff) cudaFreeAsync(gb->soff, ctx->st);
     if (gb->sid) cudaFreeAsync(gb->sid, ctx->st);
-    // a live grammar of the graph keeps its memory (freed with the grammar)
+    // a live grammar of the graph keeps its memory (freed with the grammar);
+    // the rest of the graph's memory goes back to the device now, not when
+    // another graph would reuse it
     delete gb;
     ctx->graph = nullptr;
+    cudaStreamSynchronize(ctx->st);
+    cudaDeviceGraphMemTrim(ctx->device);
 }
 
 void graph_grammar_freed(lcg_ctx* ctx, const lcg_grammar* G) {
@@ -1065,7 +1087,7 @@ void capture_graph(lcg_ctx* ctx, const unsigned char* d_in, const std::vector<u6
     u64 t1 = 1, t2 = 1;
     for (u32 r = 1; r <= planned; r++) {
         const RoundPlan& p = plan[r];
-        const u64 tiles = (p.n_bound + parse_tile_positions(1) - 1) / parse_tile_positions(1);
+        const u64 tiles = (p.n_alloc + parse_tile_positions(1) - 1) / parse_tile_positions(1);
         t1 = std::max({t1, tiles, popscan_tiles_for(tiles * parse_tile_positions(1) / 32)});
         t2 = std::max({t2, scan2_tiles_for(tiles), scan2_tiles_for(std::max<u64>(1, p.g_alloc))});
     }

@@ -60,3 +60,28 @@ def test_invalid_settings_are_skipped(monkeypatch):
     rep = autotune.autotune(ctx, None, None, reps=1, candidates={"parse_blocks_per_sm": [0, 2, 3, 4]})
     assert rep["tuning"]["parse_blocks_per_sm"] == 2
     assert all(s["parse_blocks_per_sm"] != 4 for s, _ in rep["trials"])
+
+
+def test_config_class():
+    import numpy as np
+    dna = np.frombuffer(b"ACGTN" * 100, dtype=np.uint8)
+    text = np.arange(256, dtype=np.uint8)
+    assert autotune.config_class(12_400_000_000, 4, dna) == "dna/2^34B/1-8 strings"
+    assert autotune.config_class(320_000_000, 64, dna) == "dna/2^28B/9-256 strings"
+    assert autotune.config_class(8_000_000_000, 2000, dna) == "dna/2^33B/257+ strings"
+    assert autotune.config_class(1 << 20, 1, text).startswith("bytes/2^20B/")
+
+
+def test_tuned_uses_the_cache_and_records_new_classes(monkeypatch, tmp_path):
+    calls = []
+    monkeypatch.setattr(autotune, "autotune", lambda ctx, d, o, reps, sweeps: calls.append(1) or
+                        {"tuning": dict(START, table_load=0.6), "ms": 5.0, "trials": [1, 2, 3]})
+    path = str(tmp_path / "cache.json")
+    ctx = FakeCtx(START)
+    got = autotune.tuned(ctx, None, None, "dna/2^28B/9-256 strings", path=path)
+    assert got["source"] == "tuned" and got["tuning"]["table_load"] == 0.6 and calls == [1]
+    ctx2 = FakeCtx(START)
+    got2 = autotune.tuned(ctx2, None, None, "dna/2^28B/9-256 strings", path=path)
+    assert got2["source"] == "cache" and ctx2.tuning()["table_load"] == 0.6 and calls == [1]
+    got3 = autotune.tuned(FakeCtx(START), None, None, "dna/2^28B/9-256 strings", path=path, retune=True)
+    assert got3["source"] == "tuned" and calls == [1, 1]

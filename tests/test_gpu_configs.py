@@ -1,17 +1,25 @@
 """Full-size runs of the uneven batch (2000 strings, ~8 GB) and the large
-repetitive strings (4 x 3.1 Gbp over ACGTN, ~12.4 GB), in one batched build
-each, checked where the oracle can follow: the root of a string (its level and
-the fingerprint of its expansion) depends on that string only, so sampled
-strings are built alone by the oracle and their roots compared; every sampled
-string expands to its bytes.  The repetitive generator is also checked bit for
-bit against the oracle at a size the oracle finishes in seconds."""
+repetitive strings (4 x 3.1 Gbp over ACGTN, ~12.4 GB), each in one batched
+build, compared with the oracle's grammar of the same collection in full:
+every level's rhs_off, rhs and F, and the roots C, through SHA-256 digests
+that tests/golden/make_config_digests.py wrote from the oracle alone (the
+grammars are gigabytes; the oracle takes minutes on them).  The second build
+of each runs as a launch of its captured CUDA graph, as the benchmark times
+it.  The repetitive generator is also checked bit for bit against the oracle
+at a size the oracle finishes in seconds."""
+import json
+import os
+
 import numpy as np
 import pytest
 
 import lcg_inputs as li
 from oracle import oracle as O
+from tests.digests import first_digest_difference, grammar_digests
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config_digests.json")
 
 
 @pytest.fixture(scope="module")
@@ -23,10 +31,9 @@ def ctx(hf):
     return Context(hf, device=0)
 
 
-def _oracle_root(hf, s):
-    ex = O.build(li.from_strings([s]), hf).export()
-    lvl, r = int(ex["c_level"][0]), int(ex["c_rank"][0])
-    return lvl, int(ex["F0"][r] if lvl == 0 else ex["levels"][lvl - 1]["F"][r])
+def _golden(name):
+    with open(GOLDEN) as fh:
+        return json.load(fh)[name]
 
 
 def _expands(g, j, dev_data, off):
@@ -37,38 +44,43 @@ def _expands(g, j, dev_data, off):
     return torch.equal(out, dev_data[int(off[j]):int(off[j + 1])])
 
 
-def test_uneven_batch_8gb(ctx, hf):
+def _check_full(ctx, coll, want, samples):
     import torch
-    coll = li.uneven_collection()
-    assert coll.k == 2000 and 7.5e9 < coll.n < 8.5e9
+    assert coll.n == want["n"] and coll.k == want["k"]
     d = torch.from_numpy(coll.data).cuda()
     g = ctx.build(d, coll.offsets)
-    lv, _, fp = g.roots()
-    rng = np.random.default_rng(0)
-    for j in sorted(set(rng.integers(0, coll.k, size=6).tolist()) | {0, coll.k - 1}):
-        assert (int(lv[j]), int(fp[j])) == _oracle_root(hf, coll.string(j)), j
+    diff = first_digest_difference(grammar_digests(g.export()), want)
+    assert diff is None, diff
+    for j in samples:
         assert _expands(g, j, d, coll.offsets), j
-    print("uneven batch: levels", g.shape[1], "packed grammar bytes", g.packed_size())
+    g.free()
+    # the same shape again as one captured CUDA graph, then its launch
+    ctx.set_graph(True)
+    try:
+        modes = []
+        for _ in range(2):
+            g = ctx.build(d, coll.offsets)
+            modes.append(ctx.last_build_stats()["graph"])
+            if modes[-1] == 2:
+                diff = first_digest_difference(grammar_digests(g.export()), want)
+                assert diff is None, f"graph launch: {diff}"
+            g.free()
+    finally:
+        ctx.set_graph(False)
+    assert modes[-1] == 2, modes
 
 
-def test_repetitive_12gb(ctx, hf):
-    import torch
-    from paper_2411_12439_gb300 import Context
+def test_uneven_batch_8gb(ctx):
+    coll = li.uneven_collection()
+    rng = np.random.default_rng(0)
+    samples = sorted(set(rng.integers(0, coll.k, size=4).tolist()) | {0, coll.k - 1})
+    _check_full(ctx, coll, _golden("uneven"), samples)
+
+
+def test_repetitive_12gb(ctx):
     coll = li.repetitive_collection()
     assert coll.k == 4 and coll.n == 4 * 3_100_000_000
-    d = torch.from_numpy(coll.data).cuda()
-    g = ctx.build(d, coll.offsets)
-    lv, _, fp = g.roots()
-    for j in range(coll.k):
-        assert _expands(g, j, d, coll.offsets), j
-    # each string parsed alone has the same root (the oracle is too slow at 3.1 Gbp)
-    alone = Context(hf, device=0)
-    for j in range(coll.k):
-        sub = d[int(coll.offsets[j]):int(coll.offsets[j + 1])]
-        ga = alone.build(sub, np.array([0, sub.numel()], dtype=np.uint64))
-        la, _, fa = ga.roots()
-        assert (int(la[0]), int(fa[0])) == (int(lv[j]), int(fp[j])), j
-        ga.free()
+    _check_full(ctx, coll, _golden("repetitive"), range(coll.k))
 
 
 def test_repetitive_structure_against_oracle(ctx, hf):

@@ -426,3 +426,25 @@ def test_stable_cores(hf):
             lo, hi = cut[0], cut[-1]
             checked_levels = max(checked_levels, i + 1)
     assert checked_levels >= 4
+
+
+def test_grammar_digests_locate_differences(hf):
+    """The digests the full-size GPU tests compare: equal for equal grammars,
+    and a change anywhere (one rule symbol, one fingerprint, one root) names
+    its level and array."""
+    from tests.digests import first_digest_difference, grammar_digests
+    coll = li.tiny_dna_collection(base_len=20_000, k=3)
+    ex = O.build(coll, hf).export()
+    a = grammar_digests(ex)
+    assert first_digest_difference(a, grammar_digests(O.build(coll, hf).export())) is None
+    ex["levels"][1]["rhs"] = ex["levels"][1]["rhs"].copy()
+    ex["levels"][1]["rhs"][5] ^= 1
+    assert first_digest_difference(grammar_digests(ex), a) == "level 2: rhs differs"
+    ex = O.build(coll, hf).export()
+    ex["levels"][0]["F"] = ex["levels"][0]["F"].copy()
+    ex["levels"][0]["F"][0] ^= 1
+    assert first_digest_difference(grammar_digests(ex), a) == "level 1: F differs"
+    ex = O.build(coll, hf).export()
+    ex["c_rank"] = ex["c_rank"].copy()
+    ex["c_rank"][2] += 1
+    assert first_digest_difference(grammar_digests(ex), a) == "C differs"
