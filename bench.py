@@ -544,6 +544,67 @@ def run_profile(args):
     return 0
 
 
+def e2e_run(hf, local, coll, hd, tuning, lanes, args, barrier, max_over_ranks):
+    """End to end through the public API: page-locked host input, the whole
+    grammar to a page-locked host buffer in its packed form every step.
+    Steps run on `lanes` contexts (each with its own stream and host thread,
+    as a serving process would), so that one step's copies overlap another
+    step's kernels.  Raises when the lanes do not fit in device memory."""
+    import torch
+    from paper_2411_12439_gb300 import Context
+    streams = [torch.cuda.Stream(device=local) for _ in range(lanes)]
+    ectx = [Context(hf, device=local, stream=s.cuda_stream) for s in streams]
+    try:
+        outs = []
+        for c in ectx:
+            c.set_tuning(**tuning)
+            c.set_graph(not args.no_graph)  # host input goes through the context's upload buffer
+            for _ in range(2):  # a plan, then the graph's capture
+                g = c.build(hd, coll.offsets)
+                if len(outs) < len(ectx):
+                    outs.append(torch.empty(g.packed_size() * 5 // 4 + 4096, dtype=torch.uint8).pin_memory())
+                g.free()
+        barrier()
+        torch.cuda.synchronize()
+        e2e_steps = max(args.e2e_steps, lanes)
+        per_lane = [e2e_steps // lanes + (1 if i < e2e_steps % lanes else 0) for i in range(lanes)]
+        d2h_seen = [0] * lanes
+        errors = []
+
+        def e2e_lane(i, steps):
+            try:
+                for _ in range(steps):
+                    g = ectx[i].build(hd, coll.offsets)
+                    d2h_seen[i] = int(g.export_packed(outs[i]).numel())
+                    g.free()
+            except Exception as e:  # reported below
+                errors.append(repr(e))
+
+        def e2e_pass(steps):
+            threads = [threading.Thread(target=e2e_lane, args=(i, steps[i])) for i in range(lanes)]
+            for t in threads:
+                t.start()
+            for t in threads:
+                t.join()
+            torch.cuda.synchronize()
+            if errors:
+                raise RuntimeError("end-to-end step failed: " + errors[0])
+
+        e2e_pass([1] * lanes)  # untimed: the lanes' steps running together once, as they will when timed
+        barrier()
+        t0 = time.perf_counter()
+        e2e_pass(per_lane)
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps)
+        return {"value": coll.n / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(coll.n),
+                "d2h_bytes_per_step": max(d2h_seen), "ms_per_step": e2e_s * 1e3, "steps": e2e_steps,
+                "streams": lanes,
+                "result": "grammar in its packed form (lcg_export_packed) in page-locked host memory",
+                "timing": "host clock from the first step's start to the last step's grammar in host memory"}
+    finally:
+        for c in ectx:
+            c.close()
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -701,71 +762,19 @@ def run_ours(args):
         lanes = max(1, args.e2e_streams)
         lane_note = None
         while True:
-            streams = [torch.cuda.Stream(device=local) for _ in range(lanes)]
-            ectx = [Context(hf, device=local, stream=s.cuda_stream) for s in streams]
-            outs = []
             try:
-                for c in ectx:
-                    c.set_tuning(**tuned["tuning"])
-                    c.set_graph(not args.no_graph)  # host input goes through the context's upload buffer
-                    for _ in range(2):  # a plan, then the graph's capture
-                        g = c.build(hd, coll.offsets)
-                        if len(outs) < len(ectx):
-                            outs.append(torch.empty(g.packed_size() * 5 // 4 + 4096, dtype=torch.uint8).pin_memory())
-                        g.free()
-                # the lanes' steps running together once, untimed, as they will when timed
-                tmp = [c.build(hd, coll.offsets) for c in ectx]
-                for g in tmp:
-                    g.free()
-                torch.cuda.synchronize()
+                e2e = e2e_run(hf, local, coll, hd, tuned["tuning"], lanes, args, barrier, max_over_ranks)
                 break
-            except Exception as e:  # two lanes' working sets do not fit the device: one lane
-                for c in ectx:
-                    c.close()
+            except Exception as e:  # two lanes' working sets do not fit the device at once: one lane
                 torch.cuda.synchronize()
                 torch.cuda.empty_cache()
                 if lanes == 1 or "ENOMEM" not in repr(e):
                     raise
-                lane_note = f"{lanes} lanes did not fit in device memory ({e}); one lane"
+                lane_note = f"{lanes} lanes did not fit in device memory together ({e}); one lane"
                 lanes = 1
-        barrier()
-        torch.cuda.synchronize()
-        e2e_steps = max(args.e2e_steps, lanes)
-        per_lane = [e2e_steps // lanes + (1 if i < e2e_steps % lanes else 0) for i in range(lanes)]
-        d2h_seen = [0] * lanes
-        errors = []
-
-        def e2e_lane(i, steps):
-            try:
-                for _ in range(steps):
-                    g = ectx[i].build(hd, coll.offsets)
-                    d2h_seen[i] = int(g.export_packed(outs[i]).numel())
-                    g.free()
-            except Exception as e:  # reported below
-                errors.append(repr(e))
-
-        def e2e_pass(steps):
-            threads = [threading.Thread(target=e2e_lane, args=(i, steps[i])) for i in range(lanes)]
-            for t in threads:
-                t.start()
-            for t in threads:
-                t.join()
-            torch.cuda.synchronize()
-
-        barrier()
-        t0 = time.perf_counter()
-        e2e_pass(per_lane)
-        if errors:
-            raise RuntimeError("end-to-end step failed: " + errors[0])
-        e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps)
-        e2e = {"value": world * coll.n / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(coll.n),
-               "d2h_bytes_per_step": max(d2h_seen), "ms_per_step": e2e_s * 1e3, "steps": e2e_steps,
-               "streams": lanes, "streams_note": lane_note,
-               "result": "grammar in its packed form (lcg_export_packed) in page-locked host memory",
-               "timing": "host clock from the first step's start to the last step's grammar in host memory"}
-        for c in ectx:
-            c.close()
-        del hd, outs
+        e2e["value"] *= world
+        e2e["streams_note"] = lane_note
+        del hd
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
 

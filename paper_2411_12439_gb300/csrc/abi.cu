@@ -495,7 +495,7 @@ void alloc_round(lcg_ctx* ctx, RoundBufs& b, u64 n_bound, u32 kk, u64 t_cap) {
     b.sid_next = dalloc<u32>(ctx, kk);
     b.R_phr = dalloc<u64>(ctx, kk);
     b.R_sid = dalloc<u32>(ctx, kk);
-    b.P_slot = dalloc<u32>(ctx, b.tiles * parse_tile_positions(1));
+    b.P_slot = dalloc<u32>(ctx, parse_slot_entries(b.tiles, kk));
     b.tile_cnt = dalloc<u32>(ctx, b.tiles);
     b.tile_pfx = dalloc<u64>(ctx, b.tiles);
     if (t_cap) alloc_next(ctx, b, t_cap);

@@ -81,8 +81,8 @@ struct RoundArgs {
     u64 rtab_cap;
     const u32* rrhs;
     const u64* rrhs_off;
-    u32* P_slot;          // per phrase, tile-major (tile * TP + q): slot, or a resident rank
-                          // with the top bit set
+    u32* P_slot;          // per phrase (tile t's phrases from pslot_base(t) on): slot, or a
+                          // resident rank with the top bit set
     // strings pass
     u64* soff_next;
     u32* sid_next;
@@ -120,6 +120,7 @@ struct RoundArgs {
 };
 
 u64 parse_tile_positions(int sym_bytes);
+u64 parse_slot_entries(u64 tiles, u64 strings);  // entries of P_slot for a round's tiles and strings
 u64 popscan_tiles_for(u64 nw);
 size_t lb1_bytes(u64 tiles);
 size_t lb2_bytes(u64 tiles);

@@ -96,7 +96,8 @@ __device__ __forceinline__ u32 string_of(const u64* soff, u32 k, u64 pos) {
 // where a new content is claimed.  In byte rounds a per-block cache of packed
 // phrases (kept across the block's tiles) answers most lookups; the phrases
 // that miss are queued and looked up together, with full warps.  The slot of
-// phrase q of tile t goes to P_slot[t * kTP + q] (its order key); new entries
+// phrase q of tile t goes to P_slot[pslot_base(t) + q] (its order key is
+// t * kTP + q); new entries
 // (claims) are listed in shared memory and appended to the round's claim list
 // every few tiles.
 
@@ -104,6 +105,17 @@ constexpr int kParseThreads = 256;
 constexpr int kTP = 2048;          // positions per parse tile
 constexpr int kHalo = 64;          // positions staged past the tile end
 constexpr int kSP = kTP + kHalo;   // staged positions
+
+// Where the phrase slots of parse tile t begin in P_slot.  Every phrase but a
+// string's first is at least two symbols long, so a tile of kTP positions in
+// which s strings start holds at most kTP / 2 + 1 + s phrases: tile t's slots
+// begin at t (kTP / 2 + 1) plus the strings that start before the tile (j0
+// is the string holding the tile's first position, tile_str[t]).
+__device__ __forceinline__ u64 pslot_base(const RoundArgs& a, u64 t, u32 j0) {
+    const u64 t0 = t * (u64)kTP;
+    const u64 before = (__ldg(a.soff + j0) < t0) ? (u64)j0 + 1 : (u64)j0;
+    return t * (u64)(kTP / 2 + 1) + before;
+}
 constexpr int kCacheBits = 11;
 constexpr int kCacheSlots = 1 << kCacheBits;  // per-block phrase cache (byte rounds)
 constexpr int kCacheProbes = 8;
@@ -433,6 +445,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
     // byte rounds: queued cache misses: key, and order key | (cache slot + 1) << kOkeyBits
     __shared__ Key128 sMissKey[kLocal ? kMissBuf : 1];
     __shared__ u64 sMissOk[kLocal ? kMissBuf : 1];
+    __shared__ u64 sMissPs[kLocal ? kMissBuf : 1];  // where the queued phrase's slot goes in P_slot
     __shared__ u32 s_nmiss;
     __shared__ unsigned short sLong[kLongBuf];  // tile offsets (q) of the tile's long phrases
     __shared__ u32 s_nlong;
@@ -521,6 +534,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
         }
         // offsets of the strings from j0 on, for step 5 (read now, used at the tile's end)
         const u64 s_first = (warp == 0 && j0 + lane < kact) ? __ldg(a.soff + j0 + lane) : ~0ull;
+        const u64 pb0 = pslot_base(a, tile, j0);  // the tile's phrase slots in P_slot
         __syncthreads();
 
         // 3. phrase starts of the tile, in order: four threads per break word,
@@ -562,8 +576,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
         __syncthreads();
 
         // 4. lookups.  A phrase's order key is tile * kTP + q: it orders phrases
-        //    like their global index, and names the phrase's slot in the
-        //    tile-major P_slot array.
+        //    like their global index.
         const u64 tail = s_tail_end - t0;
         const u32 cntq = (u32)cnt;
         const u64 okey0 = tile * (u64)kTP;
@@ -751,6 +764,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                         if (m < (u32)kMissBuf) {
                             sMissKey[m] = key;
                             sMissOk[m] = (okey0 + q) | ((u64)(free_h + 1) << kOkeyBits);
+                            sMissPs[m] = pb0 + q;
                             continue;
                         }
                         bool claimed;  // queue full: at once (no cache entry)
@@ -758,7 +772,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                         if (claimed) claim_single(slot, len);
                     }
                 }
-                __stcs(a.P_slot + okey0 + q, slot);
+                __stcs(a.P_slot + pb0 + q, slot);
             }
             __syncthreads();
             const u32 nq = s_nmiss;
@@ -784,7 +798,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                                                       (unsigned long long)ck);
                             if (old == kEmpty) cval[free_h] = slot;
                         }
-                        __stcs(a.P_slot + okey, slot);
+                        __stcs(a.P_slot + sMissPs[i], slot);
                     }
                     claim_warp(claimed, slot, len);
                 }
@@ -805,7 +819,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                         len = 0;
                     } else {
                         slot = lookup(q, st, en, &claimed);
-                        __stcs(a.P_slot + okey0 + q, slot);
+                        __stcs(a.P_slot + pb0 + q, slot);
                     }
                 }
                 claim_warp(claimed, slot, len);
@@ -849,7 +863,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                 }
             }
             if (lane == 0) {
-                __stcs(a.P_slot + okey0 + q, slot);
+                __stcs(a.P_slot + pb0 + q, slot);
                 if (claimed) claim_single(slot, len);
             }
         }
@@ -859,7 +873,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
             __syncthreads();
         }
 
-        // 5. outputs: phrase slots (tile-major), the tile's phrase count, and
+        // 5. outputs: phrase slots (from pb0 on), the tile's phrase count, and
         //    the order key of the first phrase of every string starting here
         if (tid == 0) a.tile_cnt[tile] = cntq;
         if (warp == 0) {
@@ -1178,7 +1192,7 @@ __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) 
     for (u64 t = (u64)blockIdx.x * warps + (threadIdx.x >> 5); t < ntiles; t += (u64)gridDim.x * warps) {
         const u32 cnt = a.tile_cnt[t];
         const u64 pbase = a.tile_pfx[t];
-        const u32* ps = a.P_slot + t * (u64)kTP;
+        const u32* ps = a.P_slot + pslot_base(a, t, a.tile_str[t]);
         // kRwUnroll phrases per thread at a time: their reads are issued together
         for (u32 q0 = lane; q0 < cnt; q0 += kRwUnroll * 32) {
             u32 s[kRwUnroll];
@@ -1287,6 +1301,7 @@ static unsigned grid_for(u64 n, u64 cap = 152ull * 32) {
 }
 
 u64 parse_tile_positions(int) { return (u64)kTP; }
+u64 parse_slot_entries(u64 tiles, u64 strings) { return tiles * (u64)(kTP / 2 + 1) + strings + 1; }
 
 u64 popscan_tiles_for(u64 nw) { return (nw + kPopTile - 1) / kPopTile; }
 
