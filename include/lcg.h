@@ -146,14 +146,18 @@ int lcg_set_kernel_timing(lcg_ctx* ctx, int enable);
  *                       (0.3 .. 0.78; a table past 0.8 is regrown and the round rerun);
  *   parse_blocks_per_sm resident k_parse blocks per SM, 0 = as many as fit;
  *   miss_flush          byte rounds: queued cache misses that trigger a lookup pass
- *                       (32 .. 256).
- * Defaults: 0.5, 0, 64.  Out-of-range values give LCG_EINVAL. */
+ *                       (32 .. 256);
+ *   table_slots_max     0, or at most this many slots (>= 1024) in the first phrase
+ *                       table of every round: a table too small for the round fills
+ *                       past its load limit, is regrown (x4) and the parse rerun, so
+ *                       the regrowth path can be exercised; results are unchanged.
+ * Defaults: 0.5, 0, 64, 0.  Out-of-range values give LCG_EINVAL. */
 typedef struct lcg_tuning {
     double table_load;
     uint32_t parse_blocks_per_sm;
     uint32_t miss_flush;
+    uint32_t table_slots_max;
     uint32_t pad;
-    uint32_t pad2;
 } lcg_tuning;
 int lcg_set_tuning(lcg_ctx* ctx, const lcg_tuning* t);
 /* Run later lcg_build calls whose rounds are planned without host
@@ -184,6 +188,17 @@ typedef struct lcg_kernel_launch {
 /* Copy up to `cap` of the last call's timed launches, in launch order, into
  * `out` (host) and their number into *count. */
 int lcg_last_kernel_launches(const lcg_ctx* ctx, lcg_kernel_launch* out, uint32_t cap, uint32_t* count);
+
+/* Self-test of the bounded device waits (no counterpart in the paper; the
+ * failure detection of the library).  Runs the library's single-pass scan on
+ * a small array with its tile counter read one ahead, so that the first tile
+ * waits for a predecessor that never publishes.  The wait gives up after its
+ * iteration limit (about a second), the kernel records the timeout in the
+ * context's device status and returns, and the call returns LCG_ETIMEOUT.
+ * Nothing faults, traps or hangs, and later calls on the context work as
+ * before (look-back slots carry a launch epoch).  Any other return value means
+ * the bounded wait is broken. */
+int lcg_selftest_wait_timeout(lcg_ctx* ctx);
 
 /* BuildGram(T, H) (Sec. 3.3).
  * data: the k strings concatenated (uint8), `data_on_device` = 1 when it is a
@@ -223,21 +238,26 @@ int lcg_decompress(lcg_ctx* ctx, const lcg_grammar* G, uint32_t j, uint8_t* out,
                    uint64_t* out_len, int out_on_device);
 
 /* exp(C[j]) like lcg_decompress, but without allocating any device memory.
- * This entry point has no counterpart in the paper; it is a library service.
- * It is for callers that cannot allocate device memory at the time of the
- * call, e.g. code running while a stream is being captured into a CUDA graph,
- * allocator or memory-pressure callbacks, or services that reserve their
- * device memory up front.  Its scratch is a static device array of about
- * 20 MiB, which every GPU that loads the library keeps until the process
- * exits.  The context and the grammar must already exist.
- * out_dev: DEVICE buffer of `cap` bytes; *out_len receives |T_j|.
- * Limits and errors: strings longer than 1048576 bytes are rejected with
- * LCG_EOVERFLOW (use lcg_decompress); cap < |T_j| gives LCG_EINVAL.
+ * This entry point has no counterpart in the paper; it is a library service
+ * for callers that cannot allocate device memory when they expand a string:
+ * code running inside an allocator's or a memory-pressure callback (it cannot
+ * call back into the allocator), and services that reserve their device
+ * memory up front and keep no room for transient buffers.  Its scratch is a
+ * static device array of about 20 MiB, which every GPU that loads the library
+ * keeps until the process exits.  The context and the grammar must already
+ * exist.
+ * out_dev: DEVICE buffer of `cap` bytes; on success *out_len receives |T_j|.
+ * Limits and errors: a string longer than 1048576 bytes is rejected with
+ * LCG_EOVERFLOW, and *out_len then holds only a lower bound of its length (the
+ * expansion stops at the first level past the limit; use lcg_decompress);
+ * cap < |T_j| gives LCG_EINVAL with *out_len = |T_j|; j >= k gives LCG_EINVAL.
  * The first call on a device takes the scratch's device address
- * (cudaGetSymbolAddress): make that first call before any stream capture.
- * All calls share the scratch: calls whose device work overlaps (other
- * threads, other contexts or streams) race and must be serialised by the
- * caller.  The call is blocking. */
+ * (cudaGetSymbolAddress, once per device): make that first call before any
+ * stream capture.  All calls share the scratch and it keeps the last call's
+ * contents: calls whose device work overlaps (other threads, other contexts or
+ * streams) race and must be serialised by the caller.  The call blocks: it
+ * synchronises the context's stream at every level to read the size of the
+ * next level's expansion back from the device. */
 int lcg_decompress_static(lcg_ctx* ctx, const lcg_grammar* G, uint32_t j, uint8_t* out_dev, uint64_t cap,
                           uint64_t* out_len);
 

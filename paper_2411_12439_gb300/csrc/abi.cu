@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -748,6 +749,7 @@ void round_sync(lcg_ctx* ctx, lcg_grammar* R, RoundInput& in, u32 i, bool agains
         const double ratio = (i == 1) ? 0.02 : std::min(1.0, std::max(prev_ratio * 2.0, 0.05));
         cap = 2 * std::max<u64>(4096, std::min<u64>(P_est, (u64)(ratio * 1.3 * (double)P_est) + 1));
     }
+    if (ctx->tuning.table_slots_max) cap = std::min<u64>(cap, ctx->tuning.table_slots_max);
     u32 retries = 0;
     DevStatus st;
     RoundCounts rc;
@@ -847,6 +849,7 @@ std::vector<RoundPlan> plan_rounds(lcg_ctx* ctx, u64 n1, u32 kk, u32 planned) {
         const double sl = ctx->plan_slack;
         p.cap = std::min<u64>(bucket(std::max<u64>(8192, (u64)(p.g_est * 1.1 * sl / ctx->tuning.table_load) + 1024)),
                               kMaxRank + 1);
+        if (ctx->tuning.table_slots_max) p.cap = std::min<u64>(p.cap, ctx->tuning.table_slots_max);
         p.g_alloc = bucket((u64)(p.g_est * 1.25 * sl) + 1024);
         p.G_alloc = bucket((u64)(p.G_est * 1.25 * sl) + 4096);
         // the next sequence: the estimated phrases with the same slack (a
@@ -1475,13 +1478,16 @@ void decompress(lcg_ctx* ctx, const lcg_grammar* G, u32 j, uint8_t* out, u64 cap
 // exp(C[j]) without allocation: scratch in a static device array
 // --------------------------------------------------------------------------
 //
-// For callers that must not allocate device memory (code running while a
-// stream is being captured into a CUDA graph, allocator callbacks, services
-// that reserve all device memory up front).  The scratch lives in this
-// file-scope array, which every GPU that loads the library holds until the
-// process exits.  Its address is taken once per device with
-// cudaGetSymbolAddress (host code cannot use the array's name as a device
-// address).  Every call shares the array: calls that overlap on the GPU race.
+// For callers that must not allocate device memory when they expand a string:
+// code that runs inside an allocator's or a memory-pressure callback (it
+// cannot call back into the allocator), and services that reserve their
+// device memory up front and keep no room for transient buffers.  The scratch
+// lives in this file-scope array, which every GPU that loads the library
+// holds until the process exits.  Host code cannot use the array's name as a
+// device address: its address is taken once per device, with that device
+// current, by cudaGetSymbolAddress (under a lock, as contexts on several host
+// threads may make their first call at once).  Every call shares the array:
+// calls that overlap on the GPU race.
 
 constexpr u64 kStaticMaxSymbols = 1ull << 20;  // longest string expanded: 1 MiB
 constexpr u64 kStaticLbTiles = 1024;           // look-back slots for one scan of kStaticMaxSymbols
@@ -1498,8 +1504,10 @@ struct StaticScratch {
 static __device__ __align__(256) unsigned char g_static_scratch[sizeof(StaticScratch)];
 
 StaticScratch* static_scratch_of_device(lcg_ctx* ctx) {
+    static std::mutex mu;
     static StaticScratch* addr[256] = {nullptr};
     fail_if(ctx, ctx->device < 0 || ctx->device >= 256, LCG_EDEVICE, "device index out of range");
+    std::lock_guard<std::mutex> lock(mu);
     if (!addr[ctx->device]) {
         void* p = nullptr;
         ck(ctx, cudaGetSymbolAddress(&p, g_static_scratch), "cudaGetSymbolAddress");
@@ -1876,14 +1884,13 @@ int lcg_set_tuning(lcg_ctx* ctx, const lcg_tuning* t) {
     if (!ctx || !t) return LCG_EINVAL;
     const int maxb = std::max(parse_max_blocks(1), parse_max_blocks(4));
     if (!(t->table_load >= 0.3 && t->table_load <= 0.78) || t->parse_blocks_per_sm > (uint32_t)maxb ||
-        t->miss_flush < 32 || t->miss_flush > 256) {
+        t->miss_flush < 32 || t->miss_flush > 256 || (t->table_slots_max != 0 && t->table_slots_max < 1024)) {
         ctx->err = "tuning out of range: table_load in [0.3, 0.78], parse_blocks_per_sm <= " + std::to_string(maxb) +
-                   ", miss_flush in [32, 256]";
+                   ", miss_flush in [32, 256], table_slots_max 0 or >= 1024";
         return LCG_EINVAL;
     }
     ctx->tuning = *t;
     ctx->tuning.pad = 0;
-    ctx->tuning.pad2 = 0;
     return LCG_OK;
 }
 
@@ -2056,6 +2063,36 @@ int lcg_decompress_static(lcg_ctx* ctx, const lcg_grammar* G, uint32_t j, uint8_
     LCG_GUARD_BEGIN
     ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
     decompress_static(ctx, G, j, out_dev, cap, out_len);
+    return LCG_OK;
+    LCG_GUARD_END
+}
+
+int lcg_selftest_wait_timeout(lcg_ctx* ctx) {
+    if (!ctx) return LCG_EINVAL;
+    LCG_GUARD_BEGIN
+    ck(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+    kt_reset(ctx);
+    reset_status(ctx);
+    // A scan of 8 tiles whose tile counter is read one ahead: the first block
+    // takes tile 1 and waits for a tile 0 that no block takes.  Every block
+    // stays in bounds (tiles 1..8 of the 8 look-back slots sized below; tile 8
+    // returns at once), and the wait ends with kErrTimeout.
+    const u64 n = 16384;  // 8 tiles of the scan
+    const u64 tiles = scan2_tiles_for(n);
+    ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, tiles + 1, scan2_lb_bytes(tiles + 1));
+    u32* in = dalloc<u32>(ctx, n);
+    u64* out = dalloc<u64>(ctx, n);
+    ck(ctx, cudaMemsetAsync(in, 0, n * sizeof(u32), ctx->st), "memset");
+    ck(ctx, cudaMemsetAsync(ctx->ds, 0, sizeof(DevStatus), ctx->st), "reset status");
+    u64 grid = 0;
+    ck(ctx, launch_scan2(in, nullptr, n, out, nullptr, ctx->scratch + 1, ctx->lb2, ++ctx->epoch, ctx->ctr,
+                         ctx->ctr_val - 1, ctx->ds, ctx->st, &grid, nullptr),
+       "scan");
+    ctx->ctr_val += grid;
+    dfree(ctx, in);
+    dfree(ctx, out);
+    const DevStatus st = read_status(ctx);
+    check_device_status(ctx, st);
     return LCG_OK;
     LCG_GUARD_END
 }

@@ -29,7 +29,7 @@ SYMBOLS = [
     "lcg_export_start", "lcg_string_roots", "lcg_import", "lcg_packed_size", "lcg_export_packed", "lcg_import_packed",
     "lcg_grammar_free", "lcg_postprocess", "lcg_pp_stats_of", "lcg_pp_export", "lcg_pp_free",
     "lcg_vbyte_encode", "lcg_vbyte_decode", "lcg_vbyte_size", "lcg_export_vbyte", "lcg_import_vbyte",
-    "lcg_last_kernel_launches",
+    "lcg_last_kernel_launches", "lcg_selftest_wait_timeout",
 ]
 
 
@@ -63,7 +63,7 @@ class KernelLaunchC(ctypes.Structure):
 
 class TuningC(ctypes.Structure):
     _fields_ = [("table_load", ctypes.c_double), ("parse_blocks_per_sm", ctypes.c_uint32),
-                ("miss_flush", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("pad2", ctypes.c_uint32)]
+                ("miss_flush", ctypes.c_uint32), ("table_slots_max", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
 class PPStatsC(ctypes.Structure):
@@ -108,6 +108,7 @@ def load(build_if_missing: bool = True):
     lib.lcg_set_graph.argtypes = [P, I]
     lib.lcg_last_kernel_times.argtypes = [P, P, U32, ctypes.POINTER(U32)]
     lib.lcg_last_kernel_launches.argtypes = [P, P, U32, ctypes.POINTER(U32)]
+    lib.lcg_selftest_wait_timeout.argtypes = [P]
     lib.lcg_build.argtypes = [P, P, P, U32, I, PP]
     lib.lcg_build_into.argtypes = [P, P, P, P, U32, I]
     lib.lcg_merge.argtypes = [P, P, P]
@@ -308,17 +309,18 @@ class Context:
         t = TuningC()
         self._check(load().lcg_get_tuning(self._h, ctypes.byref(t)))
         return {"table_load": float(t.table_load), "parse_blocks_per_sm": int(t.parse_blocks_per_sm),
-                "miss_flush": int(t.miss_flush)}
+                "miss_flush": int(t.miss_flush), "table_slots_max": int(t.table_slots_max)}
 
     def set_tuning(self, **kw) -> None:
         """lcg_set_tuning: change some of table_load, parse_blocks_per_sm,
-        miss_flush (the others keep their values)."""
+        miss_flush, table_slots_max (the others keep their values)."""
         cur = self.tuning()
         unknown = set(kw) - set(cur)
         if unknown:
             raise LCGError(-1, f"unknown tuning parameters {sorted(unknown)}")
         cur.update(kw)
-        t = TuningC(float(cur["table_load"]), int(cur["parse_blocks_per_sm"]), int(cur["miss_flush"]), 0, 0)
+        t = TuningC(float(cur["table_load"]), int(cur["parse_blocks_per_sm"]), int(cur["miss_flush"]),
+                    int(cur["table_slots_max"]), 0)
         self._check(load().lcg_set_tuning(self._h, ctypes.byref(t)))
 
     def set_graph(self, enable: bool) -> None:
@@ -350,6 +352,11 @@ class Context:
         self._check(lib.lcg_last_kernel_launches(self._h, ctypes.cast(buf, ctypes.c_void_p), n, ctypes.byref(cnt)))
         return [{"name": buf[i].name.decode(), "round": int(buf[i].round), "ms": float(buf[i].ms),
                  "bytes": float(buf[i].bytes)} for i in range(min(n, cnt.value))]
+
+    def selftest_wait_timeout(self) -> int:
+        """lcg_selftest_wait_timeout: the return code (LCG_ETIMEOUT, -6, when
+        the bounded wait works)."""
+        return int(load().lcg_selftest_wait_timeout(self._h))
 
     def last_build_stats(self) -> dict:
         st = BuildStatsC()

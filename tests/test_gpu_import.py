@@ -116,9 +116,9 @@ def test_tuning_changes_speed_not_results(hf):
     coll = li.tiny_dna_collection(base_len=150_000, k=5)
     text = li.from_strings([li.zipf_text(np.random.default_rng(9), 120_000)])
     want = {id(c): O.build(c, hf).export() for c in (coll, text)}
-    for tun in ({"table_load": 0.3, "parse_blocks_per_sm": 1, "miss_flush": 32},
-                {"table_load": 0.78, "parse_blocks_per_sm": 2, "miss_flush": 256},
-                {"table_load": 0.5, "parse_blocks_per_sm": 0, "miss_flush": 64}):
+    for tun in ({"table_load": 0.3, "parse_blocks_per_sm": 1, "miss_flush": 32, "table_slots_max": 0},
+                {"table_load": 0.78, "parse_blocks_per_sm": 2, "miss_flush": 256, "table_slots_max": 0},
+                {"table_load": 0.5, "parse_blocks_per_sm": 0, "miss_flush": 64, "table_slots_max": 4096}):
         ctx.set_tuning(**tun)
         assert ctx.tuning() == tun
         for c in (coll, text, coll):

@@ -1,19 +1,56 @@
 """lcg_decompress_static: expansion without device allocation.
 
-Some callers cannot allocate device memory when they expand a string (code
-running during CUDA-graph stream capture, allocator callbacks, services that
-reserve their memory up front).  lcg_decompress_static serves them from a
-static scratch array inside the library.  These tests call it through the C
-ABI and check it against lcg_decompress, twice in a row (the scratch keeps
-the previous call's contents), and check that an over-long string is
-rejected.  This file is collected last on purpose.
+Some callers cannot allocate device memory when they expand a string: code
+inside an allocator's or a memory-pressure callback (it cannot call back into
+the allocator) and services that reserve their device memory up front.
+lcg_decompress_static serves them from a static scratch array inside the
+library.  These tests call it through the C ABI and check it against
+lcg_decompress, twice in a row (the scratch keeps the previous call's
+contents), check that the device's memory pool (which the library allocates
+from) and torch's allocator hold no more memory after a call, and check that
+an over-long string is rejected.  This file is collected last on purpose.
 """
+import ctypes
+import ctypes.util
+import glob
+import os
+
 import numpy as np
 import pytest
 
 import lcg_inputs as li
 
 pytestmark = pytest.mark.gpu
+
+
+def _cudart():
+    """The CUDA runtime as a shared library (to read the memory pool's use)."""
+    import torch
+    cands = [ctypes.util.find_library("cudart")]
+    tdir = os.path.dirname(torch.__file__)
+    cands += sorted(glob.glob(os.path.join(tdir, "lib", "libcudart.so*")))
+    cands += sorted(glob.glob(os.path.join(os.path.dirname(tdir), "nvidia", "*", "lib", "libcudart.so*")))
+    cands += sorted(glob.glob("/usr/local/cuda/lib64/libcudart.so*"))
+    for c in cands:
+        if not c:
+            continue
+        try:
+            return ctypes.CDLL(c)
+        except OSError:
+            continue
+    pytest.fail("no CUDA runtime library found to read the memory pool")
+
+
+def _pool_used(rt, device=0):
+    """Bytes in use in the device's current memory pool (cudaMallocAsync's)."""
+    import torch
+    torch.cuda.synchronize()
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetMemPool(ctypes.byref(pool), ctypes.c_int(device)) == 0
+    used = ctypes.c_uint64()
+    attr_used_mem_current = 7  # cudaMemPoolAttrUsedMemCurrent
+    assert rt.cudaMemPoolGetAttribute(pool, ctypes.c_int(attr_used_mem_current), ctypes.byref(used)) == 0
+    return used.value
 
 
 @pytest.fixture(scope="module")
@@ -33,13 +70,16 @@ def built(hf):
 def test_static_matches_regular_twice_in_a_row(built):
     import torch
     ctx, g, coll = built
+    rt = _cudart()
     for j in (0, 2, 3, 1, 5, 0):
         n = int(coll.offsets[j + 1] - coll.offsets[j])
         want = torch.zeros(n, dtype=torch.uint8, device="cuda:0")
         assert g.decompress(j, want) == n
         for _ in range(2):
             got = torch.full((n,), 7, dtype=torch.uint8, device="cuda:0")
+            pool0, torch0 = _pool_used(rt), torch.cuda.memory_allocated()
             assert g.decompress_static(j, got) == n
+            assert _pool_used(rt) == pool0 and torch.cuda.memory_allocated() == torch0  # nothing allocated
             assert torch.equal(got, want)
         assert bytes(want.cpu().numpy()) == coll.string(j).tobytes()
 
