@@ -7,14 +7,18 @@ batch stays under ``max_batch_bytes`` and the device-memory estimate of all
 running batches stays under the budget, and runs the batch's BuildGram
 (Sec. 3.3) at once, so that requests arriving while other batches are on the
 GPU start as soon as a lane and memory are free, and their work overlaps on
-the device.  Each finished batch is merged (MergeGrams, Sec. 3.6) into the
-grammar kept resident on the device.
+the device.  A batch's requests complete as soon as their roots are read;
+the batch's grammar then goes to a merge thread, which merges the batches
+(MergeGrams, Sec. 3.6) into the grammar kept resident on the device in the
+order they were handed over, on a context of its own, while the lanes build
+the next batches.
 
 A request's result is the root of its string: the level of its C entry and
 the fingerprint of its expansion (F^level[rank], Eq. fast_hash), which depend
 on the string's content only and are therefore the same whether the string
 was parsed alone or in any mix; plus the string's index in the resident
-grammar, from which it can be expanded.
+grammar (fixed when its batch is handed to the merge thread), from which it
+can be expanded once the batch is merged (``Request.wait_merged``).
 
 Memory admission: the context's allocations come from a stream-ordered pool
 that keeps freed memory, so the free memory the driver reports does not come
@@ -48,6 +52,7 @@ class Request:
         self.error = None
         self.batch = None
         self._done = threading.Event()
+        self._merged = threading.Event()
 
     @property
     def n(self) -> int:
@@ -60,6 +65,10 @@ class Request:
     def wait(self, timeout=None) -> bool:
         return self._done.wait(timeout)
 
+    def wait_merged(self, timeout=None) -> bool:
+        """Wait until the request's string is in the resident grammar (or failed)."""
+        return self._merged.wait(timeout)
+
 
 class CudaBackend:
     """Grammar operations on the GPU: one context per lane (each with its own
@@ -70,10 +79,18 @@ class CudaBackend:
         from .lcg import Context
         self.device = device
         self.res_ctx = Context(hash_family, device=device)
-        self.ctxs = [Context(hash_family, device=device) for _ in range(lanes)]
+        # every lane's context launches on a stream of its own
+        self.lane_streams = [torch.cuda.Stream(device=device) for _ in range(lanes)]
+        self.ctxs = [Context(hash_family, device=device, stream=s.cuda_stream) for s in self.lane_streams]
         self.staging = [None] * lanes
         self.dev_staging = [None] * lanes
         self.copy_streams = [torch.cuda.Stream(device=device) for _ in range(lanes)]
+        self.record_events = False
+        self.events = []
+        self._ev_lock = threading.Lock()
+        self.ref = torch.cuda.Event(enable_timing=True)
+        self.ref.record(torch.cuda.current_stream(device))
+        torch.cuda.synchronize(device)
 
     def empty(self):
         return self.res_ctx.import_grammar({"levels": [], "c_level": np.zeros(0, np.uint32),
@@ -111,7 +128,28 @@ class CudaBackend:
         return buf[:total]
 
     def build(self, lane: int, data, offsets: np.ndarray):
-        return self.ctxs[lane].build(data, offsets)
+        """BuildGram on the lane's context; with ``record_events`` the build is
+        bracketed by CUDA events on the lane's stream (device_intervals)."""
+        if not self.record_events:
+            return self.ctxs[lane].build(data, offsets)
+        import torch
+        ev = [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+        s = self.lane_streams[lane]
+        ev[0].record(s)
+        g = self.ctxs[lane].build(data, offsets)
+        ev[1].record(s)
+        with self._ev_lock:
+            self.events.append((lane, ev))
+        return g
+
+    def device_intervals(self):
+        """(lane, start ms, end ms) of every recorded build, on the device's
+        clock, relative to the backend's reference event."""
+        import torch
+        torch.cuda.synchronize(self.device)
+        with self._ev_lock:
+            evs = list(self.events)
+        return [(lane, self.ref.elapsed_time(a), self.ref.elapsed_time(b)) for lane, (a, b) in evs]
 
     def roots(self, lane: int, g):
         lv, _, fp = g.roots()
@@ -156,11 +194,13 @@ class CudaBackend:
 class Server:
     """Continuous-batching request loop over a grammar kept resident on the
     device.  ``submit`` may be called from any thread; ``start`` runs the
-    lanes in background threads, ``stop`` ends them after the pending work.
-    ``mode``: "merge" builds each batch on its lane (lanes in parallel) and
-    merges it into the resident grammar (MergeGrams, one at a time);
-    "resident" parses each batch against the resident grammar itself
-    (App. A.2, one at a time) after gathering it on its lane."""
+    lanes (and the merge thread) in background threads, ``stop`` ends them
+    after the pending work.  ``mode``: "merge" builds each batch on its lane
+    (lanes in parallel), completes its requests, and hands the batch's grammar
+    to the merge thread, which merges batches into the resident grammar
+    (MergeGrams) in hand-over order while the lanes go on; "resident" parses
+    each batch against the resident grammar itself (App. A.2, one at a time)
+    after gathering it on its lane."""
 
     def __init__(self, backend, lanes: int = 2, max_batch_bytes: int = 64 << 20, mem_factor: float = 12.0,
                  budget_bytes: int | None = None, budget_fraction: float = 0.5, mode: str = "merge"):
@@ -175,12 +215,16 @@ class Server:
         self.resident = backend.empty()
         self._pending = collections.deque()
         self._cv = threading.Condition()
-        self._merge_lock = threading.Lock()
+        self._merge_lock = threading.Lock()  # held while the resident grammar changes
+        self._mq = collections.deque()       # (base index, grammar, requests, bytes estimate, t handed over, phases)
+        self._mcv = threading.Condition()
+        self._assigned = 0                   # strings handed to the merge thread so far
+        self._merging = False
         self._inflight = 0.0
         self._running = False
         self._threads = []
         self.batches = []  # (lane, number of requests, input bytes, t_start, t_end)
-        self.phases = []   # per batch: seconds spent gathering, building, reading roots, merging
+        self.phases = []   # per batch: seconds spent gathering, building, reading roots, waiting, merging
         self.errors = []
 
     # -- requests -------------------------------------------------------------
@@ -199,7 +243,9 @@ class Server:
     # -- checkpoint -----------------------------------------------------------
     def snapshot(self) -> np.ndarray:
         """The resident grammar in its packed form (lcg_export_packed layout),
-        taken between merges: a checkpoint of everything served so far."""
+        taken once every batch handed over so far is merged: a checkpoint of
+        everything served so far."""
+        self.flush()
         with self._merge_lock:
             return self.backend.pack(self.resident)
 
@@ -207,17 +253,35 @@ class Server:
         """Continue from a snapshot: the resident grammar becomes the packed
         grammar ``buf`` (later requests get indexes after its strings)."""
         g = self.backend.unpack(buf)
-        with self._merge_lock:
+        self.flush()
+        with self._merge_lock, self._mcv:
             old, self.resident = self.resident, g
+            self._assigned = self.backend.size(g)
         self.backend.free(old)
+
+    def flush(self, timeout: float | None = None) -> bool:
+        """Wait until every batch handed to the merge thread is merged."""
+        end = None if timeout is None else time.perf_counter() + timeout
+        with self._mcv:
+            while self._mq or self._merging:
+                left = None if end is None else end - time.perf_counter()
+                if left is not None and left <= 0:
+                    return False
+                self._mcv.wait(0.05 if left is None else min(0.05, left))
+        return True
 
     # -- lanes ----------------------------------------------------------------
     def start(self):
         self._running = True
+        if self.mode == "merge":
+            self._assigned = self.backend.size(self.resident)
         for lane in range(self.lanes):
             t = threading.Thread(target=self._lane, args=(lane,), daemon=True)
             t.start()
             self._threads.append(t)
+        if self.mode == "merge":
+            self._mthread = threading.Thread(target=self._merger, daemon=True)
+            self._mthread.start()
 
     def stop(self, timeout: float | None = None):
         with self._cv:
@@ -226,13 +290,19 @@ class Server:
         for t in self._threads:
             t.join(timeout)
         self._threads = []
+        if self.mode == "merge" and getattr(self, "_mthread", None) is not None:
+            with self._mcv:
+                self._mcv.notify_all()
+            self._mthread.join(timeout)
+            self._mthread = None
 
-    def drain(self, requests, timeout: float | None = None) -> bool:
-        """Wait until every request in ``requests`` has its result."""
+    def drain(self, requests, timeout: float | None = None, merged: bool = True) -> bool:
+        """Wait until every request in ``requests`` has its result and, with
+        ``merged``, its string is in the resident grammar."""
         end = None if timeout is None else time.perf_counter() + timeout
         for r in requests:
             left = None if end is None else max(0.0, end - time.perf_counter())
-            if not r.wait(left):
+            if not (r.wait_merged(left) if merged else r.wait(left)):
                 return False
         return True
 
@@ -286,14 +356,16 @@ class Server:
                     g = self.backend.build(lane, data, offsets)
                     tb = time.perf_counter()
                     levels, fps = self.backend.roots(lane, g)
-                    tc = time.perf_counter()
-                    with self._merge_lock:
-                        base = self.backend.size(self.resident)
-                        self.resident = self.backend.merge(self.resident, g)
-                    self.backend.free(g)
                     t1 = time.perf_counter()
-                    ph = {"gather": ta - t0, "build": tb - ta, "roots": tc - tb, "merge": t1 - tc}
+                    ph = {"gather": ta - t0, "build": tb - ta, "roots": t1 - tb}
                     ph.update(self.backend.build_info(lane))
+                    # hand the grammar to the merge thread: the batch's strings
+                    # take the next indexes of the resident grammar
+                    with self._mcv:
+                        base = self._assigned
+                        self._assigned += len(batch)
+                        self._mq.append((base, g, batch, est, t1, ph))
+                        self._mcv.notify_all()
                 self.phases.append(ph)
                 for j, r in enumerate(batch):
                     r.result = (int(levels[j]), int(fps[j]))
@@ -306,12 +378,57 @@ class Server:
                 for r in batch:
                     r.error = repr(e)
                     r.t_done = t1
+                    r._merged.set()
+                with self._cv:
+                    self._inflight -= est
+                    self._cv.notify_all()
+                est = 0.0
             with self._cv:
-                self._inflight -= est
+                if self.mode == "resident":
+                    self._inflight -= est  # merge mode: released by the merge thread
                 self.batches.append((lane, len(batch), nbytes, t0, t1))
                 self._cv.notify_all()
             for r in batch:
+                if self.mode == "resident":
+                    r._merged.set()
                 r._done.set()
+
+    def _merger(self):
+        """Merges handed-over batch grammars into the resident grammar, in
+        hand-over order, on the resident grammar's context; releases each
+        batch's memory estimate once its grammar is freed."""
+        while True:
+            with self._mcv:
+                while not self._mq:
+                    if not self._running and not self._threads_alive():
+                        return
+                    self._mcv.wait(0.05)
+                base, g, batch, est, t_handed, ph = self._mq.popleft()
+                self._merging = True
+            t0 = time.perf_counter()
+            try:
+                with self._merge_lock:
+                    self.resident = self.backend.merge(self.resident, g)
+                self.backend.free(g)
+            except Exception as e:  # the batch's strings are not in the resident grammar
+                self.errors.append(repr(e))
+                for r in batch:
+                    r.error = repr(e)
+            t1 = time.perf_counter()
+            ph["merge_wait"] = t0 - t_handed
+            ph["merge"] = t1 - t0
+            with self._cv:
+                self._inflight -= est
+                self._cv.notify_all()
+            with self._mcv:
+                self._merging = False
+                self._mcv.notify_all()
+            for r in batch:
+                r.t_merged = t1
+                r._merged.set()
+
+    def _threads_alive(self) -> bool:
+        return any(t.is_alive() for t in self._threads)
 
 
 def latency_stats(requests) -> dict:

@@ -89,3 +89,43 @@ def test_snapshot_restore_on_the_gpu(hf):
     want = O.build(li.from_strings([r.data for r in order]), hf).export()
     assert O.grammars_equal(second.resident.export(), want)
 
+
+
+def test_lanes_overlap_on_the_device(hf):
+    """Two lanes build batches at the same time: their builds' CUDA-event
+    intervals (on the device's clock) overlap, each request's root equals the
+    root of its string built alone, and the resident grammar equals the
+    oracle's."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_12439_gb300 import Context, serving
+    rng = np.random.default_rng(61)
+    base = li.random_dna(rng, 6_000_000)
+    stream = []
+    for i in range(12):
+        s0 = int(rng.integers(0, base.shape[0] - 4_000_000))
+        stream.append(li.Request(0.0, li.apply_snps(rng, base[s0:s0 + 4_000_000], 0.005), "dna"))
+    backend = serving.CudaBackend(hf, device=0, lanes=2)
+    backend.record_events = True
+    srv = serving.Server(backend, lanes=2, max_batch_bytes=8 << 20)
+    for item in stream:  # a burst: both lanes get work at once
+        srv.submit(item.data)
+    reqs = list(srv._pending)
+    srv.start()
+    assert srv.drain(reqs, timeout=300)
+    srv.stop()
+    assert not srv.errors, srv.errors
+    iv = backend.device_intervals()
+    assert {lane for lane, _, _ in iv} == {0, 1}
+    overlap = [(a, b) for a in iv for b in iv if a[0] == 0 and b[0] == 1 and a[1] < b[2] and b[1] < a[2]]
+    assert overlap, iv
+    alone = Context(hf, device=0)
+    for r in reqs:
+        g = alone.build(r.data, np.array([0, r.n], dtype=np.uint64))
+        lv, _, fp = g.roots()
+        assert r.result == (int(lv[0]), int(fp[0]))
+        g.free()
+    order = sorted(reqs, key=lambda r: r.index)
+    want = O.build(li.from_strings([r.data for r in order]), hf).export()
+    assert O.grammars_equal(srv.resident.export(), want)

@@ -162,3 +162,41 @@ def test_snapshot_and_restore(hf):
     want = O.build(li.from_strings([r.data for r in order]), hf).export()
     assert O.grammars_equal(second.resident.export(), want)
 
+
+
+def test_merges_run_off_the_requests_path(hf):
+    """Requests complete when their roots are known; their batches are merged
+    afterwards by the merge thread, in hand-over order, while the lanes build
+    the next batches (a slow merge does not hold the lanes up)."""
+    import time
+
+    class SlowMerge(OracleBackend):
+        def __init__(self, hf):
+            super().__init__(hf)
+            self.merges = []
+
+        def merge(self, resident, g):
+            t0 = time.perf_counter()
+            time.sleep(0.05)
+            out = super().merge(resident, g)
+            self.merges.append((t0, time.perf_counter()))
+            return out
+
+    backend = SlowMerge(hf)
+    srv = serving.Server(backend, lanes=2, max_batch_bytes=6_000)
+    srv.start()
+    reqs = serving.replay(srv, _requests(12, 30))
+    assert srv.drain(reqs, timeout=120)
+    srv.stop()
+    assert not srv.errors
+    for r in reqs:
+        assert r.t_done <= r.t_merged
+        assert r.result == _alone(hf, r.data)
+    # some batch was taken by a lane while an earlier batch was being merged
+    starts = [t0 for _, _, _, t0, _ in srv.batches]
+    assert any(m0 < s < m1 for s in starts for m0, m1 in backend.merges)
+    order = sorted(reqs, key=lambda r: r.index)
+    assert [r.index for r in order] == list(range(len(reqs)))
+    want = O.build(li.from_strings([r.data for r in order]), hf).export()
+    assert O.grammars_equal(srv.resident.export(), want)
+    assert all("merge" in p and "merge_wait" in p for p in srv.phases)
