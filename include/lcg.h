@@ -150,14 +150,18 @@ int lcg_set_kernel_timing(lcg_ctx* ctx, int enable);
  *   table_slots_max     0, or at most this many slots (>= 1024) in the first phrase
  *                       table of every round: a table too small for the round fills
  *                       past its load limit, is regrown (x4) and the parse rerun, so
- *                       the regrowth path can be exercised; results are unchanged.
- * Defaults: 0.5, 0, 64, 0.  Out-of-range values give LCG_EINVAL. */
+ *                       the regrowth path can be exercised; results are unchanged;
+ *   tile_stripes        rounds >= 2 take their 2048-position tiles in this many
+ *                       interleaved stripes of the sequence (1 .. 16; 1 = in order),
+ *                       so that strings that are near-copies of one another at the
+ *                       same offsets are parsed side by side.
+ * Defaults: 0.5, 0, 64, 0, 1.  Out-of-range values give LCG_EINVAL. */
 typedef struct lcg_tuning {
     double table_load;
     uint32_t parse_blocks_per_sm;
     uint32_t miss_flush;
     uint32_t table_slots_max;
-    uint32_t pad;
+    uint32_t tile_stripes;
 } lcg_tuning;
 int lcg_set_tuning(lcg_ctx* ctx, const lcg_tuning* t);
 /* Run later lcg_build calls whose rounds are planned without host

@@ -1,11 +1,12 @@
 """Autotuner of the build's launch and sizing parameters (lcg_set_tuning),
 with a cache of the best setting per class of collection.
 
-The parse kernel's resident blocks per SM, the phrase tables' load factor and
-the byte rounds' miss-queue threshold change the build's speed, never its
-result.  ``autotune`` times builds of a sample collection on a context and
-keeps, one parameter at a time (coordinate descent, two sweeps), the value
-with the shortest median build time; the context keeps the best setting.
+The rank rounds' tile order (tiles taken in interleaved stripes), the parse
+kernel's resident blocks per SM, the phrase tables' load factor and the byte
+rounds' miss-queue threshold change the build's speed, never its result.
+``autotune`` times builds of a sample collection on a context and keeps, one
+parameter at a time (coordinate descent, two sweeps), the value with the
+shortest median build time; the context keeps the best setting.
 
 ``tuned`` looks the collection's class up in a JSON cache first (its alphabet,
 its size in powers of two and its number of strings: collections of one class
@@ -24,6 +25,7 @@ import time
 import numpy as np
 
 CANDIDATES = {
+    "tile_stripes": [1, 2, 4, 8],
     "parse_blocks_per_sm": [0, 2, 3, 4],
     "table_load": [0.4, 0.5, 0.6, 0.7],
     "miss_flush": [32, 64, 128],
@@ -56,6 +58,8 @@ def autotune(ctx, data, offsets, reps: int = 3, sweeps: int = 2, candidates=None
     for _ in range(sweeps):
         changed = False
         for name, values in cands.items():
+            if name not in best:
+                continue  # a parameter this context does not have
             for v in values:
                 if v == best[name]:
                     continue

@@ -60,7 +60,7 @@ struct lcg_ctx {
     cudaStream_t st = nullptr;
     std::vector<lcg_grammar*> live;  // grammars created here and not yet freed
     double plan_slack = 1.0;         // multiplier of the planned buffer sizes (adaptive)
-    lcg_tuning tuning{0.5, 0, 64, 0, 0};  // table load, k_parse blocks per SM, miss flush
+    lcg_tuning tuning{0.5, 0, 64, 0, 1};  // table load, k_parse blocks per SM, miss flush, slots cap, stripes
     bool own_stream = false;
     std::vector<u64> a, b, c;
     u32 levels = 0, m_bits = 32;
@@ -571,6 +571,7 @@ RoundArgs round_args(lcg_ctx* ctx, lcg_grammar* R, const RoundInput& in, RoundBu
     a.lh = level_hash(ctx, i);
     a.level = i;
     a.parse_blocks = ctx->tuning.parse_blocks_per_sm;
+    a.stripes = ctx->tuning.tile_stripes;
     a.miss_flush = ctx->tuning.miss_flush;
     a.tiles_bound = b.tiles;
     a.string_first = b.string_first;
@@ -1884,13 +1885,13 @@ int lcg_set_tuning(lcg_ctx* ctx, const lcg_tuning* t) {
     if (!ctx || !t) return LCG_EINVAL;
     const int maxb = std::max(parse_max_blocks(1), parse_max_blocks(4));
     if (!(t->table_load >= 0.3 && t->table_load <= 0.78) || t->parse_blocks_per_sm > (uint32_t)maxb ||
-        t->miss_flush < 32 || t->miss_flush > 256 || (t->table_slots_max != 0 && t->table_slots_max < 1024)) {
+        t->miss_flush < 32 || t->miss_flush > 256 || (t->table_slots_max != 0 && t->table_slots_max < 1024) ||
+        t->tile_stripes < 1 || t->tile_stripes > 16) {
         ctx->err = "tuning out of range: table_load in [0.3, 0.78], parse_blocks_per_sm <= " + std::to_string(maxb) +
-                   ", miss_flush in [32, 256], table_slots_max 0 or >= 1024";
+                   ", miss_flush in [32, 256], table_slots_max 0 or >= 1024, tile_stripes in [1, 16]";
         return LCG_EINVAL;
     }
     ctx->tuning = *t;
-    ctx->tuning.pad = 0;
     return LCG_OK;
 }
 

@@ -55,6 +55,7 @@ struct RoundArgs {
     LevelHash lh;         // parameters of h^i
     u32 level;            // i
     u32 parse_blocks;     // resident k_parse blocks per SM (0: as many as fit)
+    u32 stripes;          // rounds >= 2: tiles taken in this many interleaved stripes (1: in order)
     u32 miss_flush;       // byte rounds: queued cache misses that trigger a lookup pass
     // parse pass
     u64 tiles_bound;      // parse tiles the buffers were sized for

@@ -116,6 +116,26 @@ __device__ __forceinline__ u64 pslot_base(const RoundArgs& a, u64 t, u32 j0) {
     const u64 before = (__ldg(a.soff + j0) < t0) ? (u64)j0 + 1 : (u64)j0;
     return t * (u64)(kTP / 2 + 1) + before;
 }
+
+// Tile order of the rank rounds' parse and rewrite: with `stripes` = k > 1
+// the round's tiles are cut into k equal stripes and taken interleaved
+// (stripe 0's first tile, stripe 1's first tile, ..., then every stripe's
+// second tile), so that strings which are near-copies of one another at the
+// same offsets (k assemblies of one genome) are parsed side by side and the
+// later copies find the first copy's new table entries still in L2.  Logical
+// tile l in [0, k * ceil(T / k)) names tile (l % k) * ceil(T / k) + l / k, or
+// nothing (>= T).  Phrase order keys stay tile * kTP + q, so the result does
+// not depend on the order.
+__device__ __forceinline__ u64 stripe_tiles(u64 ntiles, u32 stripes) {
+    if (stripes <= 1) return ntiles;
+    const u64 per = (ntiles + stripes - 1) / stripes;
+    return per * stripes;
+}
+__device__ __forceinline__ u64 stripe_tile(u64 l, u64 ntiles, u32 stripes) {
+    if (stripes <= 1) return l;
+    const u64 per = (ntiles + stripes - 1) / stripes;
+    return (l % stripes) * per + l / stripes;
+}
 constexpr int kCacheBits = 11;
 constexpr int kCacheSlots = 1 << kCacheBits;  // per-block phrase cache (byte rounds)
 constexpr int kCacheProbes = 8;
@@ -509,8 +529,14 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
     };
 
     u64 iter = 0;
-    for (u64 tile = blockIdx.x; tile < ntiles; tile += gridDim.x, iter++) {
+    // rank rounds may take their tiles in stripes (stripe_tile); byte rounds in order
+    const u32 stripes = kByte ? 1u : a.stripes;
+    const u64 nlog = stripe_tiles(ntiles, stripes);
+    for (u64 lt = blockIdx.x; lt < nlog; lt += gridDim.x, iter++) {
         if ((iter & 15) == 0 && round_halted(a)) break;
+        const u64 tile = stripe_tile(lt, ntiles, stripes);
+        const bool last = lt + gridDim.x >= nlog;  // the block's last tile
+        if (tile >= ntiles) continue;  // no tile here (claims still buffered are flushed after the loop)
         const u64 t0 = tile * (u64)kTP;
         const u64 t_end = min(t0 + (u64)kTP, n), s_end = min(t0 + (u64)kSP, n);
         const int ns = (int)(s_end - t0), nt = (int)(t_end - t0);
@@ -523,7 +549,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
             if (tid * 16 < ns) *reinterpret_cast<uint4*>(sb + tid * 16) = pf_sym;
             if (tid < NWS) sbits[tid] = pf_bits;
             j0 = pf_j0;
-            if (tile + gridDim.x < ntiles) fetch(tile + gridDim.x);
+            if (tile + gridDim.x < ntiles) fetch(tile + gridDim.x);  // byte rounds: in order
         } else {
             j0 = a.tile_str[tile];
             stage_vec<u32>(sT, S + t0, ns, (reinterpret_cast<unsigned long long>(S + t0) & 15) == 0);
@@ -777,7 +803,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
             __syncthreads();
             const u32 nq = s_nmiss;
             if (nq >= min(a.miss_flush ? a.miss_flush : (u32)kMissFlushDefault, (u32)kMissBuf) ||
-                tile + gridDim.x >= ntiles) {
+                last) {
                 const u32 nm = min(nq, (u32)kMissBuf);
                 for (u32 i0 = 0; i0 < nm; i0 += kParseThreads) {  // whole warps take each step
                     const u32 i = i0 + tid;
@@ -891,7 +917,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
         const u32 ncl = s_nclaim;
         constexpr u32 kFlushAt = kByte ? (u32)kClaimBuf / 2 : (u32)(kClaimBuf - kTP);
         static_assert(kByte || kClaimBufR >= 2 * kTP, "a rank-round tile never overflows the buffer");
-        if (ncl >= kFlushAt || tile + gridDim.x >= ntiles) {
+        if (ncl >= kFlushAt || last) {
             const u32 nb = min(ncl, (u32)kClaimBuf);
             if (tid == 0 && ncl) {
                 const u64 base = atomicAdd(&a.ds->claims, (u64)nb);
@@ -912,6 +938,23 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
             }
         }
         __syncthreads();
+    }
+    // claims still buffered: a block whose last logical tiles were empty
+    // (striped order) did not flush after its last tile
+    __syncthreads();
+    const u32 ncl = s_nclaim;
+    if (ncl) {
+        const u32 nb = min(ncl, (u32)kClaimBuf);
+        if (tid == 0) {
+            const u64 base = atomicAdd(&a.ds->claims, (u64)nb);
+            s_claim_base = base;
+            atomicAdd(&a.ds->claim_len, s_claim_len);
+            if (base + nb > a.claim_limit) atomicExch(&a.ds->overflow, 1u);
+        }
+        __syncthreads();
+        const u64 base = s_claim_base;
+        for (u32 x = tid; x < nb; x += kParseThreads)
+            if (base + x < bt.cap) a.claims[base + x] = sClaim[x];
     }
 }
 
@@ -1189,7 +1232,11 @@ __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) 
     // one tile per warp: the tile's header reads and its first phrase reads
     // of every warp of the SM are in flight together
     const u32 lane = threadIdx.x & 31, warps = blockDim.x >> 5;
-    for (u64 t = (u64)blockIdx.x * warps + (threadIdx.x >> 5); t < ntiles; t += (u64)gridDim.x * warps) {
+    const u32 stripes = a.level > 1 ? a.stripes : 1u;
+    const u64 nlog = stripe_tiles(ntiles, stripes);
+    for (u64 lt = (u64)blockIdx.x * warps + (threadIdx.x >> 5); lt < nlog; lt += (u64)gridDim.x * warps) {
+        const u64 t = stripe_tile(lt, ntiles, stripes);
+        if (t >= ntiles) continue;
         const u32 cnt = a.tile_cnt[t];
         const u64 pbase = a.tile_pfx[t];
         const u32* ps = a.P_slot + pslot_base(a, t, a.tile_str[t]);
