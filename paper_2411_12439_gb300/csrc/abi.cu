@@ -76,6 +76,8 @@ struct lcg_ctx {
     u64* scratch = nullptr; // small device scalars: [0] phrases, [1..2] totals
     void* lb1 = nullptr;
     u64 lb1_tiles = 0;
+    void* heads = nullptr;  // k_breaks' look-ahead words (its own: epoch-tagged, nothing else writes them)
+    u64 heads_steps = 0;
     void* lb2 = nullptr;
     u64 lb2_tiles = 0;
     double ratio_hint[64] = {0};  // new rules per phrase, per level (decaying maximum over builds)
@@ -615,9 +617,11 @@ void enqueue_parse(lcg_ctx* ctx, RoundArgs& a, u64 n_for_bytes) {
     int ht = kt_begin(ctx, "k_tile_strings", 4.0 * (double)a.tiles_bound, a.level);
     ck(ctx, launch_tile_strings(a, ctx->st), "k_tile_strings");
     kt_end(ctx, ht);
-    // k_breaks' look-ahead words live in the look-back buffer (sized for the
-    // round's parse tiles, four per block step of k_breaks)
-    a.lb1 = ctx->lb1;
+    // k_breaks' look-ahead words: a buffer of their own, so that no other
+    // kernel's data can read as a head of this launch's epoch
+    const u64 steps = breaks_steps(a.tiles_bound);
+    ensure_lb(ctx, &ctx->heads, &ctx->heads_steps, steps, steps * sizeof(u64));
+    a.heads = reinterpret_cast<u64*>(ctx->heads);
     a.brk_epoch = ++ctx->epoch;
     int hb = kt_begin(ctx, "k_breaks", (a.sym_bytes == 1 ? 1.0 : 4.0) * n_for_bytes + (double)n_for_bytes / 8.0, a.level);
     ck(ctx, launch_breaks(a, ctx->st), "k_breaks");
@@ -1097,6 +1101,8 @@ void capture_graph(lcg_ctx* ctx, const unsigned char* d_in, const std::vector<u6
     }
     ensure_lb(ctx, &ctx->lb1, &ctx->lb1_tiles, t1, lb1_bytes(t1));
     ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, t2, scan2_lb_bytes(t2));
+    const u64 hs = breaks_steps(t1);
+    ensure_lb(ctx, &ctx->heads, &ctx->heads_steps, hs, hs * sizeof(u64));
     auto* gb = new GraphBuild;
     ctx->graph = gb;
     gb->d_in = d_in;
@@ -1126,6 +1132,8 @@ void capture_graph(lcg_ctx* ctx, const unsigned char* d_in, const std::vector<u6
         ck(ctx, cudaMemsetAsync(ctx->ctr, 0, sizeof(u64), ctx->st), "reset tile counter");
         ctx->ctr_val = 0;
         ck(ctx, cudaMemsetAsync(ctx->lb1, 0, lb1_bytes(ctx->lb1_tiles), ctx->st), "reset look-back");
+        // the graph's launches reuse its epochs: heads of the last launch must not read as published
+        ck(ctx, cudaMemsetAsync(ctx->heads, 0, ctx->heads_steps * sizeof(u64), ctx->st), "reset heads");
         ck(ctx, cudaMemsetAsync(ctx->lb2, 0, scan2_lb_bytes(ctx->lb2_tiles), ctx->st), "reset look-back");
         T = new_grammar(ctx, false);
         grow_c(ctx, T, k);
@@ -1848,6 +1856,7 @@ void lcg_ctx_destroy(lcg_ctx* ctx) {
     }
     for (auto e : ctx->evpool) cudaEventDestroy(e);
     if (ctx->lb1) cudaFree(ctx->lb1);
+    if (ctx->heads) cudaFree(ctx->heads);
     if (ctx->lb2) cudaFree(ctx->lb2);
     cudaFree(ctx->ds);
     cudaFree(ctx->rc);

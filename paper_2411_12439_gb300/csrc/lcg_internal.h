@@ -67,9 +67,10 @@ struct RoundArgs {
     u32* tile_cnt;        // per parse tile: phrases starting in it
     u64* tile_pfx;        // exclusive prefix of tile_cnt: global index of a tile's first phrase
     u64* string_first;    // order key (tile * TP + q) of each active string's first phrase
-    void* lb1;            // look-back slots (k_breaks: the heads of its block steps)
+    void* lb1;            // look-back slots
     u64 epoch;
-    u64 brk_epoch;        // epoch of k_breaks' look-ahead words
+    u64* heads;           // k_breaks: the head word of each block step (its own buffer)
+    u64 brk_epoch;        // epoch of k_breaks' head words
     u64* ctr;
     u64 ctr_base;
     u64* total;           // device: phrases of the round
@@ -122,6 +123,7 @@ struct RoundArgs {
 
 u64 parse_tile_positions(int sym_bytes);
 u64 parse_slot_entries(u64 tiles, u64 strings);  // entries of P_slot for a round's tiles and strings
+u64 breaks_steps(u64 tiles);                     // k_breaks' block steps over a round's parse tiles
 u64 popscan_tiles_for(u64 nw);
 size_t lb1_bytes(u64 tiles);
 size_t lb2_bytes(u64 tiles);

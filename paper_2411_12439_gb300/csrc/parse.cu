@@ -108,14 +108,10 @@ constexpr int kSP = kTP + kHalo;   // staged positions
 
 // Where the phrase slots of parse tile t begin in P_slot.  Every phrase but a
 // string's first is at least two symbols long, so a tile of kTP positions in
-// which s strings start holds at most kTP / 2 + 1 + s phrases: tile t's slots
-// begin at t (kTP / 2 + 1) plus the strings that start before the tile (j0
-// is the string holding the tile's first position, tile_str[t]).
-__device__ __forceinline__ u64 pslot_base(const RoundArgs& a, u64 t, u32 j0) {
-    const u64 t0 = t * (u64)kTP;
-    const u64 before = (__ldg(a.soff + j0) < t0) ? (u64)j0 + 1 : (u64)j0;
-    return t * (u64)(kTP / 2 + 1) + before;
-}
+// which s strings start holds at most kTP / 2 + 1 + s phrases.  With j0(t)
+// the string holding the tile's first position (tile_str[t]), s is at most
+// j0(t + 1) - j0(t) + 1, so tile t's slots can begin at t (kTP / 2 + 2) + j0(t).
+__device__ __forceinline__ u64 pslot_base(u64 t, u32 j0) { return t * (u64)(kTP / 2 + 2) + j0; }
 
 // Tile order of the rank rounds' parse and rewrite: with `stripes` = k > 1
 // the round's tiles are cut into k equal stripes and taken interleaved
@@ -294,7 +290,7 @@ __global__ void __launch_bounds__(kBrkThreads) k_breaks(const RoundArgs a, u64 n
                                : (reinterpret_cast<unsigned long long>(Sf) & 15) == 0;
     nblocks = min(nblocks, (n + kBrkSpan - 1) / kBrkSpan);
     if (blockIdx.x >= nblocks && blockIdx.x > 0) return;  // more blocks than steps: no counter traffic
-    u64* heads = reinterpret_cast<u64*>(a.lb1);
+    u64* heads = a.heads;
     const int warp = tid >> 5;
     while (true) {
         // the next block step, in decreasing order (the counter starts at 0 every round)
@@ -560,7 +556,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
         }
         // offsets of the strings from j0 on, for step 5 (read now, used at the tile's end)
         const u64 s_first = (warp == 0 && j0 + lane < kact) ? __ldg(a.soff + j0 + lane) : ~0ull;
-        const u64 pb0 = pslot_base(a, tile, j0);  // the tile's phrase slots in P_slot
+        const u64 pb0 = pslot_base(tile, j0);  // the tile's phrase slots in P_slot
         __syncthreads();
 
         // 3. phrase starts of the tile, in order: four threads per break word,
@@ -1239,7 +1235,7 @@ __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) 
         if (t >= ntiles) continue;
         const u32 cnt = a.tile_cnt[t];
         const u64 pbase = a.tile_pfx[t];
-        const u32* ps = a.P_slot + pslot_base(a, t, a.tile_str[t]);
+        const u32* ps = a.P_slot + pslot_base(t, a.tile_str[t]);
         // kRwUnroll phrases per thread at a time: their reads are issued together
         for (u32 q0 = lane; q0 < cnt; q0 += kRwUnroll * 32) {
             u32 s[kRwUnroll];
@@ -1348,7 +1344,8 @@ static unsigned grid_for(u64 n, u64 cap = 152ull * 32) {
 }
 
 u64 parse_tile_positions(int) { return (u64)kTP; }
-u64 parse_slot_entries(u64 tiles, u64 strings) { return tiles * (u64)(kTP / 2 + 1) + strings + 1; }
+u64 parse_slot_entries(u64 tiles, u64 strings) { return tiles * (u64)(kTP / 2 + 2) + strings + 1; }
+u64 breaks_steps(u64 tiles) { return (tiles * (u64)kTP + kBrkSpan - 1) / kBrkSpan + 1; }
 
 u64 popscan_tiles_for(u64 nw) { return (nw + kPopTile - 1) / kPopTile; }
 

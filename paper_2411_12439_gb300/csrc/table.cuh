@@ -115,6 +115,20 @@ __device__ __forceinline__ Key128 ld_key_relaxed(const Key128* p) {
     return k;
 }
 
+// A slot's key and value with one 32-byte load (one request for the sector).
+// The two halves need not be read at one instant: the key is checked as
+// before, and the value is only used as an upper bound of the stored value,
+// which never increases.
+__device__ __forceinline__ Key128 ld_slot_relaxed(const Slot* p, u64* val) {
+    Key128 k;
+    u64 spare;
+    asm volatile("ld.relaxed.gpu.global.v4.u64 {%0, %1, %2, %3}, [%4];"
+                 : "=l"(k.lo), "=l"(k.hi), "=l"(*val), "=l"(spare)
+                 : "l"(p)
+                 : "memory");
+    return k;
+}
+
 __device__ __forceinline__ Key128 cas_key(Key128* p, Key128 cmp, Key128 val) {
     Key128 old;
     asm volatile(
@@ -161,10 +175,13 @@ __device__ u64 table_claim_or_find(ContentTable t, const Key128& k, bool hashed,
         if ((++groups & 15) == 0 && vload(&ds->overflow)) return ~0ull;
         const u64 gend = min((s | (u64)(G - 1)) + 1, t.cap);
         const int m = (int)min(gend - s, limit - probe);
+        // every slot of the group whole (key and value, one request each): a
+        // found key whose value is already at most pidx needs no update
         Key128 c[G];
+        u64 cv[G];
 #pragma unroll
         for (int j = 0; j < G; j++)
-            if (j < m) c[j] = ld_key_relaxed(&t.slots[s + j].key);
+            if (j < m) c[j] = ld_slot_relaxed(&t.slots[s + j], &cv[j]);
 #pragma unroll
         for (int j = 0; j < G; j++) {
             if (j >= m) break;
@@ -178,12 +195,13 @@ __device__ u64 table_claim_or_find(ContentTable t, const Key128& k, bool hashed,
                     return s + j;
                 }
                 cur = old;
+                cv[j] = ~0ull;  // read before the slot was claimed
             }
             if (cur.hi == k.hi) {
                 // a pair read while being written shows the empty low half: read it again atomically
                 if (cur.lo == ~0ull) cur = cas_key(kp, empty, empty);
                 if (hashed ? same(cur.lo) : (cur.lo == k.lo)) {
-                    atomicMin(&t.slots[s + j].val, pidx);
+                    if (cv[j] > pidx) atomicMin(&t.slots[s + j].val, pidx);  // values only decrease
                     return s + j;
                 }
             }

@@ -54,6 +54,12 @@ def _check_full(ctx, coll, want, samples):
     for j in samples:
         assert _expands(g, j, d, coll.offsets), j
     g.free()
+    # again, all rounds enqueued at once from the plan of the build before
+    g = ctx.build(d, coll.offsets)
+    assert ctx.last_build_stats()["async_rounds"] > 0
+    diff = first_digest_difference(grammar_digests(g.export()), want)
+    assert diff is None, f"planned rounds: {diff}"
+    g.free()
     # the same shape again as one captured CUDA graph, then its launch
     ctx.set_graph(True)
     try:
