@@ -563,7 +563,11 @@ def e2e_run(hf, local, coll, hd, tuning, lanes, args, barrier, max_over_ranks):
     grammar to a page-locked host buffer in its packed form every step.
     Steps run on `lanes` contexts (each with its own stream and host thread,
     as a serving process would), so that one step's copies overlap another
-    step's kernels.  Raises when the lanes do not fit in device memory."""
+    step's kernels.  The lanes' builds run as launches, not captured graphs:
+    a graph keeps the memory of all its rounds, so two graphs of a large build
+    need twice its memory, while launches return each round's buffers to the
+    stream-ordered pool for the next.  Raises when the lanes do not fit in
+    device memory."""
     import torch
     from paper_2411_12439_gb300 import Context
     streams = [torch.cuda.Stream(device=local) for _ in range(lanes)]
@@ -572,8 +576,7 @@ def e2e_run(hf, local, coll, hd, tuning, lanes, args, barrier, max_over_ranks):
         outs = []
         for c in ectx:
             c.set_tuning(**tuning)
-            c.set_graph(not args.no_graph)  # host input goes through the context's upload buffer
-            for _ in range(2):  # a plan, then the graph's capture
+            for _ in range(2):  # a plan, then a build from it
                 g = c.build(hd, coll.offsets)
                 if len(outs) < len(ectx):
                     outs.append(torch.empty(g.packed_size() * 5 // 4 + 4096, dtype=torch.uint8).pin_memory())
@@ -613,6 +616,7 @@ def e2e_run(hf, local, coll, hd, tuning, lanes, args, barrier, max_over_ranks):
                 "d2h_bytes_per_step": max(d2h_seen), "ms_per_step": e2e_s * 1e3, "steps": e2e_steps,
                 "streams": lanes,
                 "result": "grammar in its packed form (lcg_export_packed) in page-locked host memory",
+                "builds": "launches (no graph capture), all rounds enqueued from the context's plan",
                 "timing": "host clock from the first step's start to the last step's grammar in host memory"}
     finally:
         for c in ectx:
