@@ -33,7 +33,6 @@
 
 namespace lcg {
 
-constexpr u64 kNone = 1ull << 32;          // "no different fingerprint to the right"
 constexpr u32 kResidentBit = 0x80000000u;  // P_slot entry names a resident rank
 
 template <typename T>

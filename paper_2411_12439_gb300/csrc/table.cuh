@@ -126,6 +126,7 @@ __device__ __forceinline__ Key128 ld_slot_relaxed(const Slot* p, u64* val) {
                  : "=l"(k.lo), "=l"(k.hi), "=l"(*val), "=l"(spare)
                  : "l"(p)
                  : "memory");
+    (void)spare;
     return k;
 }
 
