@@ -85,6 +85,8 @@ def parse_args():
     p.add_argument("--e2e-steps", type=int, default=4)
     p.add_argument("--e2e-streams", type=int, default=2, help="contexts (streams, host threads) of the e2e steps")
     p.add_argument("--serving-requests", type=int, default=2000)
+    p.add_argument("--serving-lanes", type=int, default=2)
+    p.add_argument("--serving-batch-mb", type=int, default=192)
     p.add_argument("--profile-builds", type=int, default=0,
                    help="only run this many batched builds of the workload inside the profiler range and exit")
     p.add_argument("--profile-warmup", type=int, default=1,
@@ -474,7 +476,8 @@ def extra_config(name, hf, local, stream, args):
     return out
 
 
-def run_serving(hf, device: int, count: int, loads=(0.1, 0.25, 0.5), mode: str = "merge"):
+def run_serving(hf, device: int, count: int, loads=(0.1, 0.25, 0.5), mode: str = "merge", lanes: int = 2,
+                max_batch_mb: int = 192):
     """The serving loop on the seeded serving stream: first all requests at
     once (the loop's capacity: input GB/s from first submission to last
     completion), then the same requests with Poisson arrivals paced so that the
@@ -496,8 +499,8 @@ def run_serving(hf, device: int, count: int, loads=(0.1, 0.25, 0.5), mode: str =
     mean_len = float(np.mean([r.data.shape[0] for r in stream]))
 
     def run(time_scale):
-        backend = serving.CudaBackend(hf, device=device, lanes=2)
-        srv = serving.Server(backend, lanes=2, max_batch_bytes=192 << 20, mode=mode)
+        backend = serving.CudaBackend(hf, device=device, lanes=lanes)
+        srv = serving.Server(backend, lanes=lanes, max_batch_bytes=max_batch_mb << 20, mode=mode)
         srv.start()
         warm = serving.replay(srv, warm_stream, time_scale=1e-4)
         srv.drain(warm, timeout=600)
@@ -530,7 +533,7 @@ def run_serving(hf, device: int, count: int, loads=(0.1, 0.25, 0.5), mode: str =
         r.update({"load": load, "offered_gbs": load * capacity})
         runs.append(r)
     return {"workload": SERVING_WORKLOAD, "stream_bytes": int(sum(r.data.shape[0] for r in stream)),
-            "max_batch_mb": 192, "lanes": 2, "mode": mode, "capacity": burst,
+            "max_batch_mb": max_batch_mb, "lanes": lanes, "mode": mode, "capacity": burst,
             "loads": "fractions of the capacity (all requests submitted at once)",
             "latency": "from submission to the request's root (its batch built); batches merge into the resident "
                        "grammar afterwards (batch_ms.merge_wait, .merge)",
@@ -810,7 +813,8 @@ def run_ours(args):
         cpu_threaded = cpu_baseline_threaded(coll, hf, cpu["value"] * 1e9)
     serving_line = None
     if world == 1 and not args.no_serving:
-        serving_line = run_serving(hf, local, args.serving_requests)
+        serving_line = run_serving(hf, local, args.serving_requests, lanes=args.serving_lanes,
+                                   max_batch_mb=args.serving_batch_mb)
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
