@@ -77,10 +77,20 @@ __device__ __forceinline__ u64 get_bits(u64 hi, u64 lo, int pos, int b) {
     return (low | (lo << (kHiBits - pos))) & m;
 }
 
+// The inline key of get(0..len-1): the symbols form the number
+// V = sum_j get(j) 2^(j b) (at most 124 bits), accumulated from the last
+// symbol with a 128-bit shift per symbol (no branch on where a symbol falls);
+// bits 0..59 of V go to hi under the length, bits 60..123 to lo.  This is the
+// layout put_bits / key_sym use.
 template <typename Get>
 __device__ __forceinline__ Key128 key_inline(Get get, u64 len, int b) {
-    u64 hi = len << kHiBits, lo = 0;
-    for (u64 j = 0; j < len; j++) put_bits(hi, lo, (int)j * b, (u64)get(j), b);
+    u64 vlo = 0, vhi = 0;  // V, 128 bits
+    for (u64 j = len; j-- > 0;) {
+        vhi = (vhi << b) | (vlo >> (64 - b));  // b in 1..31: both shifts defined
+        vlo = (vlo << b) | (u64)get(j);
+    }
+    const u64 hi = (len << kHiBits) | (vlo & ((1ull << kHiBits) - 1));
+    const u64 lo = (vlo >> kHiBits) | (vhi << (64 - kHiBits));
     return Key128{lo, hi};
 }
 
@@ -103,9 +113,12 @@ __device__ __forceinline__ u32 key_sym(const Key128& k, u64 j, int b) {
 
 // Home slot of a key: the high half of mix(key) * cap.  An inline key is the
 // content itself; a hashed key's high half carries the length and a hash of
-// the phrase's fingerprint (its low half names a location, not content).
+// the phrase's fingerprint (its low half names a location, not content).  The
+// mix is a multiply-xorshift of both halves (two 64-bit products).
 __device__ __forceinline__ u64 key_home(const Key128& k, u64 cap) {
-    const u64 m = key_is_hashed(k) ? fmix64(k.hi) : fmix64(k.hi ^ fmix64(k.lo + 0x9E3779B97F4A7C15ull));
+    const u64 lo = key_is_hashed(k) ? 0ull : k.lo;
+    u64 m = (lo ^ (k.hi * 0x9E3779B97F4A7C15ull)) * 0xD6E8FEB86659FD93ull;
+    m ^= m >> 32;
     return __umul64hi(m, cap);
 }
 
