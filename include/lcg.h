@@ -155,7 +155,7 @@ int lcg_set_kernel_timing(lcg_ctx* ctx, int enable);
  *                       interleaved stripes of the sequence (1 .. 16; 1 = in order),
  *                       so that strings that are near-copies of one another at the
  *                       same offsets are parsed side by side.
- * Defaults: 0.5, 0, 64, 0, 1.  Out-of-range values give LCG_EINVAL. */
+ * Defaults: 0.35, 0, 64, 0, 1.  Out-of-range values give LCG_EINVAL. */
 typedef struct lcg_tuning {
     double table_load;
     uint32_t parse_blocks_per_sm;

@@ -27,7 +27,7 @@ import numpy as np
 CANDIDATES = {
     "tile_stripes": [1, 2, 4, 8],
     "parse_blocks_per_sm": [0, 2, 3, 4],
-    "table_load": [0.4, 0.5, 0.6, 0.7],
+    "table_load": [0.3, 0.35, 0.45, 0.6],
     "miss_flush": [32, 64, 128],
 }
 

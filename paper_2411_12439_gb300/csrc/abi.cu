@@ -60,7 +60,7 @@ struct lcg_ctx {
     cudaStream_t st = nullptr;
     std::vector<lcg_grammar*> live;  // grammars created here and not yet freed
     double plan_slack = 1.0;         // multiplier of the planned buffer sizes (adaptive)
-    lcg_tuning tuning{0.5, 0, 64, 0, 1};  // table load, k_parse blocks per SM, miss flush, slots cap, stripes
+    lcg_tuning tuning{0.35, 0, 64, 0, 1};  // table load, k_parse blocks per SM, miss flush, slots cap, stripes
     bool own_stream = false;
     std::vector<u64> a, b, c;
     u32 levels = 0, m_bits = 32;

@@ -147,9 +147,12 @@ constexpr int kClaimBufR = 4096;  // rank rounds
 constexpr int kMissBuf = 256;
 constexpr int kMissFlushDefault = 64;  // queued misses that trigger a lookup pass
 constexpr u64 kOkeyBits = 44;  // order keys are below 2^44
-// Rank rounds read this many table slots per round trip (byte rounds look up
-// few, mostly cached phrases, and read one).
-constexpr int kProbeGroup = 2;
+// Table slots read per round trip.  One: a random DRAM read costs per 32-byte
+// sector (one slot), and at the default table load of 0.35 most lookups end
+// at their home slot; reading the home slot's group of two took more DRAM
+// sectors per lookup and was slower in the rank rounds, where those random
+// sectors bound k_parse.
+constexpr int kProbeGroup = 1;
 // Long phrases (hashed keys) in rank rounds: fingerprints read per round
 // trip for H, and symbols per round trip when a match is confirmed by content
 // (byte rounds read staged fingerprints and take one at a time).
