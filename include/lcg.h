@@ -146,22 +146,28 @@ int lcg_set_kernel_timing(lcg_ctx* ctx, int enable);
  *                       (0.3 .. 0.78; a table past 0.8 is regrown and the round rerun);
  *   parse_blocks_per_sm resident k_parse blocks per SM, 0 = as many as fit;
  *   miss_flush          byte rounds: queued cache misses that trigger a lookup pass
- *                       (32 .. 256);
+ *                       (32 .. 256; at most 128 take effect with 4096-position tiles);
  *   table_slots_max     0, or at most this many slots (>= 1024) in the first phrase
  *                       table of every round: a table too small for the round fills
  *                       past its load limit, is regrown (x4) and the parse rerun, so
  *                       the regrowth path can be exercised; results are unchanged;
- *   tile_stripes        rounds >= 2 take their 2048-position tiles in this many
- *                       interleaved stripes of the sequence (1 .. 16; 1 = in order),
- *                       so that strings that are near-copies of one another at the
- *                       same offsets are parsed side by side.
- * Defaults: 0.35, 0, 64, 0, 1.  Out-of-range values give LCG_EINVAL. */
+ *   tile_stripes        rounds >= 2 take their parse tiles in this many interleaved
+ *                       stripes of the sequence (1 .. 16; 1 = in order), so that
+ *                       strings that are near-copies of one another at the same
+ *                       offsets are parsed side by side;
+ *   parse_tile          positions per parse tile: 1024, 2048 or 4096.  A block of
+ *                       k_parse stages, lists and looks up one tile at a time (fewer
+ *                       barriers per phrase with larger tiles, more blocks' worth of
+ *                       tiles in flight with smaller ones).
+ * Defaults: 0.35, 0, 64, 0, 1, 4096.  Out-of-range values give LCG_EINVAL. */
 typedef struct lcg_tuning {
     double table_load;
     uint32_t parse_blocks_per_sm;
     uint32_t miss_flush;
     uint32_t table_slots_max;
     uint32_t tile_stripes;
+    uint32_t parse_tile;
+    uint32_t reserved;  /* 0 */
 } lcg_tuning;
 int lcg_set_tuning(lcg_ctx* ctx, const lcg_tuning* t);
 /* Run later lcg_build calls whose rounds are planned without host

@@ -1,9 +1,10 @@
 """Autotuner of the build's launch and sizing parameters (lcg_set_tuning),
 with a cache of the best setting per class of collection.
 
-The rank rounds' tile order (tiles taken in interleaved stripes), the parse
-kernel's resident blocks per SM, the phrase tables' load factor and the byte
-rounds' miss-queue threshold change the build's speed, never its result.
+The parse tile size, the rank rounds' tile order (tiles taken in interleaved
+stripes), the parse kernel's resident blocks per SM, the phrase tables' load
+factor and the byte rounds' miss-queue threshold change the build's speed,
+never its result.
 ``autotune`` times builds of a sample collection on a context and keeps, one
 parameter at a time (coordinate descent, two sweeps), the value with the
 shortest median build time; the context keeps the best setting.
@@ -25,6 +26,7 @@ import time
 import numpy as np
 
 CANDIDATES = {
+    "parse_tile": [4096, 2048, 1024],
     "tile_stripes": [1, 2, 4, 8],
     "parse_blocks_per_sm": [0, 2, 3, 4],
     "table_load": [0.3, 0.35, 0.45, 0.6],

@@ -60,7 +60,8 @@ struct lcg_ctx {
     cudaStream_t st = nullptr;
     std::vector<lcg_grammar*> live;  // grammars created here and not yet freed
     double plan_slack = 1.0;         // multiplier of the planned buffer sizes (adaptive)
-    lcg_tuning tuning{0.35, 0, 64, 0, 1};  // table load, k_parse blocks per SM, miss flush, slots cap, stripes
+    // table load, k_parse blocks per SM, miss flush, slots cap, stripes, parse tile
+    lcg_tuning tuning{0.35, 0, 64, 0, 1, 4096};
     bool own_stream = false;
     std::vector<u64> a, b, c;
     u32 levels = 0, m_bits = 32;
@@ -453,6 +454,7 @@ void free_round_input(lcg_ctx* ctx, RoundInput& in) {
 // Buffers of one round.
 struct RoundBufs {
     u64 tiles = 0, Pmax = 0, Tcap = 0, cap = 0, g_alloc = 0;
+    u32 tp = 4096;  // positions per parse tile
     u64* string_first = nullptr;
     u64* soff_next = nullptr;
     u32* sid_next = nullptr;
@@ -490,7 +492,8 @@ void alloc_next(lcg_ctx* ctx, RoundBufs& b, u64 t_cap) {
 }
 
 void alloc_round(lcg_ctx* ctx, RoundBufs& b, u64 n_bound, u32 kk, u64 t_cap) {
-    b.tiles = (n_bound + parse_tile_positions(1) - 1) / parse_tile_positions(1);
+    b.tp = ctx->tuning.parse_tile;
+    b.tiles = (n_bound + b.tp - 1) / b.tp;
     // every phrase but a string's first has length >= 2
     b.Pmax = n_bound / 2 + 2ull * kk + 1;
     b.string_first = dalloc<u64>(ctx, kk);
@@ -498,13 +501,13 @@ void alloc_round(lcg_ctx* ctx, RoundBufs& b, u64 n_bound, u32 kk, u64 t_cap) {
     b.sid_next = dalloc<u32>(ctx, kk);
     b.R_phr = dalloc<u64>(ctx, kk);
     b.R_sid = dalloc<u32>(ctx, kk);
-    b.P_slot = dalloc<u32>(ctx, parse_slot_entries(b.tiles, kk));
+    b.P_slot = dalloc<u32>(ctx, parse_slot_entries(b.tiles, kk, b.tp));
     b.tile_cnt = dalloc<u32>(ctx, b.tiles);
     b.tile_pfx = dalloc<u64>(ctx, b.tiles);
     if (t_cap) alloc_next(ctx, b, t_cap);
     b.tile_str = dalloc<u32>(ctx, b.tiles);
-    b.brk = dalloc<u32>(ctx, b.tiles * parse_tile_positions(1) / 32);
-    b.sbm_words = b.tiles * parse_tile_positions(1) / 32 + 2;  // positions 0 .. n inclusive
+    b.brk = dalloc<u32>(ctx, b.tiles * b.tp / 32);
+    b.sbm_words = b.tiles * b.tp / 32 + 2;  // positions 0 .. n inclusive
     b.sbm = dalloc<u32>(ctx, b.sbm_words);
     ck(ctx, cudaMemsetAsync(b.sbm, 0, b.sbm_words * sizeof(u32), ctx->st), "memset starts");
 }
@@ -528,7 +531,7 @@ void free_table(lcg_ctx* ctx, RoundBufs& b) {
 
 void alloc_naming(lcg_ctx* ctx, RoundBufs& b, u64 g_alloc) {
     b.g_alloc = g_alloc;
-    const u64 nw = b.tiles * parse_tile_positions(1) / 32;  // order keys tile * TP + q
+    const u64 nw = b.tiles * b.tp / 32;  // order keys tile * TP + q
     b.first_bits = dalloc<u32>(ctx, nw);
     b.first_prefix = dalloc<u32>(ctx, nw);
     b.slot_r = dalloc<u32>(ctx, g_alloc);
@@ -576,6 +579,7 @@ RoundArgs round_args(lcg_ctx* ctx, lcg_grammar* R, const RoundInput& in, RoundBu
     a.stripes = ctx->tuning.tile_stripes;
     a.miss_flush = ctx->tuning.miss_flush;
     a.tiles_bound = b.tiles;
+    a.tp = b.tp;
     a.string_first = b.string_first;
     a.tile_str = b.tile_str;
     a.brk = b.brk;
@@ -619,7 +623,7 @@ void enqueue_parse(lcg_ctx* ctx, RoundArgs& a, u64 n_for_bytes) {
     kt_end(ctx, ht);
     // k_breaks' look-ahead words: a buffer of their own, so that no other
     // kernel's data can read as a head of this launch's epoch
-    const u64 steps = breaks_steps(a.tiles_bound);
+    const u64 steps = breaks_steps(a.tiles_bound, a.tp);
     ensure_lb(ctx, &ctx->heads, &ctx->heads_steps, steps, steps * sizeof(u64));
     a.heads = reinterpret_cast<u64*>(ctx->heads);
     a.brk_epoch = ++ctx->epoch;
@@ -664,7 +668,7 @@ void enqueue_naming(lcg_ctx* ctx, RoundArgs& a, RoundBufs& b, double g_bytes, do
     int h = kt_begin(ctx, "k_mark", 12.0 * g_bytes, a.level);
     ck(ctx, launch_mark(a, g_grid, ctx->st), "k_mark");
     kt_end(ctx, h);
-    const u64 nw = b.tiles * parse_tile_positions(1) / 32;
+    const u64 nw = b.tiles * b.tp / 32;
     const u64 ptiles = std::max<u64>(1, popscan_tiles_for(nw));
     ensure_lb(ctx, &ctx->lb1, &ctx->lb1_tiles, ptiles, lb1_bytes(ptiles));
     a.lb1 = ctx->lb1;
@@ -1030,8 +1034,8 @@ struct GraphBuild {
 // What a graph's launches depend on besides the input and the planned buffer
 // sizes: the number of planned rounds and the launch parameters.
 std::vector<double> graph_params(lcg_ctx* ctx, u32 planned) {
-    return {(double)planned, (double)ctx->tuning.parse_blocks_per_sm, (double)ctx->tuning.miss_flush,
-            (double)ctx->ktime};
+    return {(double)planned,    (double)ctx->tuning.parse_blocks_per_sm, (double)ctx->tuning.miss_flush,
+            (double)ctx->ktime, (double)ctx->tuning.tile_stripes,        (double)ctx->tuning.parse_tile};
 }
 
 // A captured graph serves a new plan when each of its rounds' buffers holds
@@ -1093,15 +1097,16 @@ void capture_graph(lcg_ctx* ctx, const unsigned char* d_in, const std::vector<u6
     // look-back buffers and timing events for every launch, made before the
     // capture (the graph must not reallocate them)
     u64 t1 = 1, t2 = 1;
+    const u32 tp = ctx->tuning.parse_tile;
     for (u32 r = 1; r <= planned; r++) {
         const RoundPlan& p = plan[r];
-        const u64 tiles = (p.n_alloc + parse_tile_positions(1) - 1) / parse_tile_positions(1);
-        t1 = std::max({t1, tiles, popscan_tiles_for(tiles * parse_tile_positions(1) / 32)});
+        const u64 tiles = (p.n_alloc + tp - 1) / tp;
+        t1 = std::max({t1, tiles, popscan_tiles_for(tiles * tp / 32)});
         t2 = std::max({t2, scan2_tiles_for(tiles), scan2_tiles_for(std::max<u64>(1, p.g_alloc))});
     }
     ensure_lb(ctx, &ctx->lb1, &ctx->lb1_tiles, t1, lb1_bytes(t1));
     ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, t2, scan2_lb_bytes(t2));
-    const u64 hs = breaks_steps(t1);
+    const u64 hs = breaks_steps(t1, tp);
     ensure_lb(ctx, &ctx->heads, &ctx->heads_steps, hs, hs * sizeof(u64));
     auto* gb = new GraphBuild;
     ctx->graph = gb;
@@ -1895,9 +1900,10 @@ int lcg_set_tuning(lcg_ctx* ctx, const lcg_tuning* t) {
     const int maxb = std::max(parse_max_blocks(1), parse_max_blocks(4));
     if (!(t->table_load >= 0.3 && t->table_load <= 0.78) || t->parse_blocks_per_sm > (uint32_t)maxb ||
         t->miss_flush < 32 || t->miss_flush > 256 || (t->table_slots_max != 0 && t->table_slots_max < 1024) ||
-        t->tile_stripes < 1 || t->tile_stripes > 16) {
+        t->tile_stripes < 1 || t->tile_stripes > 16 || !parse_tile_valid(t->parse_tile)) {
         ctx->err = "tuning out of range: table_load in [0.3, 0.78], parse_blocks_per_sm <= " + std::to_string(maxb) +
-                   ", miss_flush in [32, 256], table_slots_max 0 or >= 1024, tile_stripes in [1, 16]";
+                   ", miss_flush in [32, 256], table_slots_max 0 or >= 1024, tile_stripes in [1, 16], "
+                   "parse_tile 1024, 2048 or 4096";
         return LCG_EINVAL;
     }
     ctx->tuning = *t;

@@ -57,6 +57,7 @@ struct RoundArgs {
     u32 parse_blocks;     // resident k_parse blocks per SM (0: as many as fit)
     u32 stripes;          // rounds >= 2: tiles taken in this many interleaved stripes (1: in order)
     u32 miss_flush;       // byte rounds: queued cache misses that trigger a lookup pass
+    u32 tp;               // positions per parse tile (1024, 2048 or 4096): order keys are tile * tp + q
     // parse pass
     u64 tiles_bound;      // parse tiles the buffers were sized for
     u64* d_tiles;         // parse tiles of the round (written by k_tile_strings)
@@ -121,9 +122,9 @@ struct RoundArgs {
     u32* c_rank;
 };
 
-u64 parse_tile_positions(int sym_bytes);
-u64 parse_slot_entries(u64 tiles, u64 strings);  // entries of P_slot for a round's tiles and strings
-u64 breaks_steps(u64 tiles);                     // k_breaks' block steps over a round's parse tiles
+bool parse_tile_valid(u32 tp);                           // 1024, 2048 or 4096 positions
+u64 parse_slot_entries(u64 tiles, u64 strings, u32 tp);  // entries of P_slot for a round's tiles and strings
+u64 breaks_steps(u64 tiles, u32 tp);                     // k_breaks' block steps over a round's parse tiles
 u64 popscan_tiles_for(u64 nw);
 size_t lb1_bytes(u64 tiles);
 size_t lb2_bytes(u64 tiles);

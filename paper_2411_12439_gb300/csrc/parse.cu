@@ -27,6 +27,8 @@
 //              retired strings
 // Every kernel of the round starts with pdl_wait(): it is launched with
 // programmatic dependent launch after the one before it.
+#include <algorithm>
+
 #include "lcg_dev.cuh"
 #include "lcg_internal.h"
 #include "table.cuh"
@@ -84,7 +86,7 @@ __device__ __forceinline__ u32 string_of(const u64* soff, u32 k, u64 pos) {
 // k_parse
 // --------------------------------------------------------------------------
 //
-// Persistent blocks take tiles of kTP positions.  A tile's symbols (and kHalo
+// Persistent blocks take tiles of TP positions.  A tile's symbols (and kHalo
 // more) and its words of the break bitmap are staged in shared memory (byte
 // rounds read the next tile's into registers while parsing the current one);
 // the phrase starts are listed in order by a block scan.  Each phrase gets a
@@ -96,21 +98,23 @@ __device__ __forceinline__ u32 string_of(const u64* soff, u32 k, u64 pos) {
 // phrases (kept across the block's tiles) answers most lookups; the phrases
 // that miss are queued and looked up together, with full warps.  The slot of
 // phrase q of tile t goes to P_slot[pslot_base(t) + q] (its order key is
-// t * kTP + q); new entries
+// t * TP + q); new entries
 // (claims) are listed in shared memory and appended to the round's claim list
 // every few tiles.
 
 constexpr int kParseThreads = 256;
-constexpr int kTP = 2048;          // positions per parse tile
+// Positions per parse tile, TP: 1024, 2048 or 4096 (the default), a launch
+// parameter (lcg_tuning.parse_tile) that every kernel of a round reads from
+// RoundArgs::tp; k_parse is compiled for each.
+constexpr int kTPMin = 1024, kTPMax = 4096;
 constexpr int kHalo = 64;          // positions staged past the tile end
-constexpr int kSP = kTP + kHalo;   // staged positions
 
 // Where the phrase slots of parse tile t begin in P_slot.  Every phrase but a
-// string's first is at least two symbols long, so a tile of kTP positions in
-// which s strings start holds at most kTP / 2 + 1 + s phrases.  With j0(t)
+// string's first is at least two symbols long, so a tile of TP positions in
+// which s strings start holds at most TP / 2 + 1 + s phrases.  With j0(t)
 // the string holding the tile's first position (tile_str[t]), s is at most
-// j0(t + 1) - j0(t) + 1, so tile t's slots can begin at t (kTP / 2 + 2) + j0(t).
-__device__ __forceinline__ u64 pslot_base(u64 t, u32 j0) { return t * (u64)(kTP / 2 + 2) + j0; }
+// j0(t + 1) - j0(t) + 1, so tile t's slots can begin at t (TP / 2 + 2) + j0(t).
+__device__ __forceinline__ u64 pslot_base(u64 t, u32 j0, u32 tp) { return t * (u64)(tp / 2 + 2) + j0; }
 
 // Tile order of the rank rounds' parse and rewrite: with `stripes` = k > 1
 // the round's tiles are cut into k equal stripes and taken interleaved
@@ -119,7 +123,7 @@ __device__ __forceinline__ u64 pslot_base(u64 t, u32 j0) { return t * (u64)(kTP 
 // same offsets (k assemblies of one genome) are parsed side by side and the
 // later copies find the first copy's new table entries still in L2.  Logical
 // tile l in [0, k * ceil(T / k)) names tile (l % k) * ceil(T / k) + l / k, or
-// nothing (>= T).  Phrase order keys stay tile * kTP + q, so the result does
+// nothing (>= T).  Phrase order keys stay tile * TP + q, so the result does
 // not depend on the order.
 __device__ __forceinline__ u64 stripe_tiles(u64 ntiles, u32 stripes) {
     if (stripes <= 1) return ntiles;
@@ -136,7 +140,7 @@ constexpr int kCacheSlots = 1 << kCacheBits;  // per-block phrase cache (byte ro
 constexpr int kCacheProbes = 8;
 // New table entries of a block are listed in shared memory and appended to
 // the round's claim list once the buffer is half full, or in rank rounds once
-// another tile could overflow it (a tile claims at most kTP entries), and
+// another tile could overflow it (a tile claims at most TP entries), and
 // after the block's last tile, so that the global counter is touched every
 // few tiles only.
 constexpr int kClaimBufB = 512;   // byte rounds (shared memory also holds the phrase cache)
@@ -161,16 +165,16 @@ constexpr int kCompareBatchR = 4;
 // Phrases longer than kLongLen (N-runs of DNA, repeated text) are hashed and
 // compared by a whole warp after the tile's other phrases: a thread alone
 // would spend a round trip per symbol on them while its block waits.  Their
-// starts are more than kLongLen apart, so a tile holds at most kLongBuf.
+// starts are more than kLongLen apart, so a tile holds at most
+// TP / (kLongLen + 1) + 1.
 constexpr int kLongLen = 32;
-constexpr int kLongBuf = kTP / (kLongLen + 1) + 1;
 
 // Load n_sym symbols of type V from src (16-byte aligned when `vec`) into the
 // shared array dst, with every 16-byte load issued before any is stored.
-template <typename V>
+template <int SP, typename V>
 __device__ __forceinline__ void stage_vec(V* dst, const V* src, int n_sym, bool vec) {
     constexpr int PER = 16 / sizeof(V);
-    constexpr int NV = (kSP + PER - 1) / PER;
+    constexpr int NV = (SP + PER - 1) / PER;
     constexpr int IT = (NV + kParseThreads - 1) / kParseThreads;
     uint4 buf[IT];
 #pragma unroll
@@ -221,7 +225,7 @@ __device__ __forceinline__ void stage_vec(V* dst, const V* src, int n_sym, bool 
 
 constexpr int kBrkThreads = 256;
 constexpr u64 kBrkSpan = (u64)kBrkThreads * 32;  // positions per block step
-static_assert(kBrkSpan % kTP == 0, "a block step starts a parse tile");
+static_assert(kBrkSpan % kTPMax == 0, "a block step starts a parse tile");
 
 // Head of block step b in the look-ahead words: (epoch << 8) | (state << 2) |
 // type, state 1 = open, 2 = decided.
@@ -436,11 +440,13 @@ __device__ __forceinline__ u32 block_scan32(u32 x, u32& total, u32* s_wsum) {
     return __shfl_sync(0xffffffffu, wi - w, wid) + incl - x;
 }
 
-template <typename T>
+template <typename T, int TP>
 __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse(const RoundArgs a, u64 ntiles) {
     pdl_wait();
+    constexpr int kSP = TP + kHalo;  // staged positions
     constexpr int NWS = kSP / 32;    // staged break words
-    constexpr int NWT = kTP / 32;    // tile break words
+    constexpr int NWT = TP / 32;     // tile break words
+    constexpr int kLongBuf = TP / (kLongLen + 1) + 1;
     constexpr bool kByte = sizeof(T) == 1;
     constexpr bool kLocal = kByte;
     static_assert(NWT <= kParseThreads, "one tile word per thread");
@@ -449,11 +455,12 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
     constexpr int kCompareBatch = kByte ? 1 : kCompareBatchR;
 
     __shared__ u32 sF0[kByte ? 256 : 1];
-    __shared__ __align__(16) unsigned char sb[kByte ? kSP : 16];  // bytes of tile positions
+    // bytes of tile positions (and 32 more: packed keys read whole 8-byte words past a phrase)
+    __shared__ __align__(16) unsigned char sb[kByte ? kSP + 32 : 16];
     __shared__ __align__(16) u32 sT[kByte ? 4 : kSP];             // ranks of tile positions
     __shared__ u32 sbits[NWS];
     __shared__ u32 swp[NWT];
-    __shared__ unsigned short sP[kTP];
+    __shared__ unsigned short sP[TP];
     // byte rounds: per-block cache of phrase (packed bytes) -> slot, kept across
     // the block's tiles (its entries always come from earlier tiles)
     __shared__ u64 ckey[kLocal ? kCacheSlots : 1];
@@ -461,9 +468,12 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
     __shared__ u32 sClaim[kClaimBuf];
     __shared__ u32 s_wsum[kParseThreads / 32];
     // byte rounds: queued cache misses: key, and order key | (cache slot + 1) << kOkeyBits
-    __shared__ Key128 sMissKey[kLocal ? kMissBuf : 1];
-    __shared__ u64 sMissOk[kLocal ? kMissBuf : 1];
-    __shared__ u64 sMissPs[kLocal ? kMissBuf : 1];  // where the queued phrase's slot goes in P_slot
+    // (half as many with 4096-position tiles, whose staged bytes and phrase
+    // list take that room: the block's static shared memory stays under 48 KB)
+    constexpr int kMissCap = TP >= 4096 ? kMissBuf / 2 : kMissBuf;
+    __shared__ Key128 sMissKey[kLocal ? kMissCap : 1];
+    __shared__ u64 sMissOk[kLocal ? kMissCap : 1];
+    __shared__ u64 sMissPs[kLocal ? kMissCap : 1];  // where the queued phrase's slot goes in P_slot
     __shared__ u32 s_nmiss;
     __shared__ unsigned short sLong[kLongBuf];  // tile offsets (q) of the tile's long phrases
     __shared__ u32 s_nlong;
@@ -477,7 +487,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
     const u64 n = round_n(a);
     const u32 kact = round_k(a);
     const u64 nwords = (n + 31) / 32;  // words of the break bitmap
-    ntiles = min(ntiles, (n + kTP - 1) / kTP);
+    ntiles = min(ntiles, (n + TP - 1) / TP);
     FpSource<T> fp;
     if constexpr (kByte) {
         for (int x = tid; x < 256; x += kParseThreads) sF0[x] = a.Fprev[x];
@@ -502,24 +512,30 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
 
     // persistent blocks: tiles blockIdx.x, blockIdx.x + gridDim.x, ...  Tiles
     // do not depend on one another.
-    // Byte rounds: a tile's bytes (16 per thread), break words and string
-    // index are read into registers while the block parses the tile before it.
-    static_assert(!kByte || (kSP + 15) / 16 <= kParseThreads, "one 16-byte load per thread");
+    // Byte rounds: a tile's bytes (16 per thread and load), break words and
+    // string index are read into registers while the block parses the tile
+    // before it.
+    constexpr int kFetch = (kSP + 16 * kParseThreads - 1) / (16 * kParseThreads);  // 16-byte loads per thread
     static_assert(NWS <= kParseThreads, "one break word per thread");
-    uint4 pf_sym = make_uint4(0u, 0u, 0u, 0u);
+    uint4 pf_sym[kFetch];
+#pragma unroll
+    for (int f = 0; f < kFetch; f++) pf_sym[f] = make_uint4(0u, 0u, 0u, 0u);
     u32 pf_bits = 0, pf_j0 = 0;
     auto fetch = [&](u64 tl) {
-        const u64 f0 = tl * (u64)kTP;
+        const u64 f0 = tl * (u64)TP;
         const int fns = (int)(min(f0 + (u64)kSP, n) - f0);
-        const int x0 = tid * 16;
         const unsigned char* src = (const unsigned char*)S + f0;
-        if (x0 + 16 <= fns && (reinterpret_cast<unsigned long long>(src) & 15) == 0) {
-            pf_sym = __ldcs(reinterpret_cast<const uint4*>(src + x0));  // streamed once: evict first
-        } else if (x0 < fns) {
-            unsigned char tmp[16];
 #pragma unroll
-            for (int e = 0; e < 16; e++) tmp[e] = (x0 + e < fns) ? src[x0 + e] : (unsigned char)0;
-            pf_sym = *reinterpret_cast<const uint4*>(tmp);
+        for (int f = 0; f < kFetch; f++) {
+            const int x0 = (tid + f * kParseThreads) * 16;
+            if (x0 + 16 <= fns && (reinterpret_cast<unsigned long long>(src) & 15) == 0) {
+                pf_sym[f] = __ldcs(reinterpret_cast<const uint4*>(src + x0));  // streamed once: evict first
+            } else if (x0 < fns) {
+                unsigned char tmp[16];
+#pragma unroll
+                for (int e = 0; e < 16; e++) tmp[e] = (x0 + e < fns) ? src[x0 + e] : (unsigned char)0;
+                pf_sym[f] = *reinterpret_cast<const uint4*>(tmp);
+            }
         }
         const u64 gw = f0 / 32 + (u64)tid;
         pf_bits = (tid < NWS && gw < nwords) ? __ldg(a.brk + gw) : 0u;
@@ -535,8 +551,8 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
         const u64 tile = stripe_tile(lt, ntiles, stripes);
         const bool last = lt + gridDim.x >= nlog;  // the block's last tile
         if (tile >= ntiles) continue;  // no tile here (claims still buffered are flushed after the loop)
-        const u64 t0 = tile * (u64)kTP;
-        const u64 t_end = min(t0 + (u64)kTP, n), s_end = min(t0 + (u64)kSP, n);
+        const u64 t0 = tile * (u64)TP;
+        const u64 t_end = min(t0 + (u64)TP, n), s_end = min(t0 + (u64)kSP, n);
         const int ns = (int)(s_end - t0), nt = (int)(t_end - t0);
 
         // 1. stage the tile's symbols (bytes in round 1, ranks afterwards) and
@@ -544,13 +560,17 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
         u32 j0;  // string holding t0
         if constexpr (kByte) {
             if (iter == 0) fetch(tile);
-            if (tid * 16 < ns) *reinterpret_cast<uint4*>(sb + tid * 16) = pf_sym;
+#pragma unroll
+            for (int f = 0; f < kFetch; f++) {
+                const int x0 = (tid + f * kParseThreads) * 16;
+                if (x0 < ns) *reinterpret_cast<uint4*>(sb + x0) = pf_sym[f];
+            }
             if (tid < NWS) sbits[tid] = pf_bits;
             j0 = pf_j0;
             if (tile + gridDim.x < ntiles) fetch(tile + gridDim.x);  // byte rounds: in order
         } else {
             j0 = a.tile_str[tile];
-            stage_vec<u32>(sT, S + t0, ns, (reinterpret_cast<unsigned long long>(S + t0) & 15) == 0);
+            stage_vec<kSP, u32>(sT, S + t0, ns, (reinterpret_cast<unsigned long long>(S + t0) & 15) == 0);
             for (int w = tid; w < NWS; w += kParseThreads) {
                 const u64 gw = t0 / 32 + (u64)w;
                 sbits[w] = gw < nwords ? __ldg(a.brk + gw) : 0u;
@@ -558,20 +578,21 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
         }
         // offsets of the strings from j0 on, for step 5 (read now, used at the tile's end)
         const u64 s_first = (warp == 0 && j0 + lane < kact) ? __ldg(a.soff + j0 + lane) : ~0ull;
-        const u64 pb0 = pslot_base(tile, j0);  // the tile's phrase slots in P_slot
+        const u64 pb0 = pslot_base(tile, j0, TP);  // the tile's phrase slots in P_slot
         __syncthreads();
 
-        // 3. phrase starts of the tile, in order: four threads per break word,
-        //    eight bits each
-        static_assert(NWT * 4 == kParseThreads, "four threads per tile word");
-        const int wq = tid >> 2, bq = (tid & 3) * 8;
+        // 3. phrase starts of the tile, in order: kTPW threads per break
+        //    word, kBPT bits each
+        constexpr int kTPW = kParseThreads / NWT, kBPT = 32 / kTPW;
+        static_assert(kTPW * NWT == kParseThreads && kTPW * kBPT == 32 && kBPT < 32, "threads per tile word");
+        const int wq = tid / kTPW, bq = (tid % kTPW) * kBPT;
         u32 word = sbits[wq];
         if (wq * 32 >= nt) word = 0;
         else if (nt - wq * 32 < 32) word &= (1u << (nt - wq * 32)) - 1u;
-        const u32 part = (word >> bq) & 0xFFu;
+        const u32 part = (word >> bq) & ((1u << kBPT) - 1u);
         u32 cnt;
         const u32 poff = block_scan32((u32)__popc(part), cnt, s_wsum);
-        if ((tid & 3) == 0) swp[wq] = (u32)poff;
+        if (tid % kTPW == 0) swp[wq] = (u32)poff;
         {
             u32 m = part, o = (u32)poff;
             while (m) {
@@ -599,11 +620,11 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
         }
         __syncthreads();
 
-        // 4. lookups.  A phrase's order key is tile * kTP + q: it orders phrases
+        // 4. lookups.  A phrase's order key is tile * TP + q: it orders phrases
         //    like their global index.
         const u64 tail = s_tail_end - t0;
         const u32 cntq = (u32)cnt;
-        const u64 okey0 = tile * (u64)kTP;
+        const u64 okey0 = tile * (u64)TP;
         auto phrase_end = [&](u32 q) -> u64 { return (q + 1 < cntq) ? (u64)sP[q + 1] : tail; };
         auto sym = [&](u64 x) -> u32 {  // symbol at tile offset x
             if (x < (u64)ns) {
@@ -785,7 +806,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
                     const Key128 key = (len <= (u64)kInlineMax && en <= (u64)ns) ? byte_key(st, (u32)len) : make_key(st, en, &ok);
                     if (ok) {
                         const u32 m = atomicAdd(&s_nmiss, 1u);
-                        if (m < (u32)kMissBuf) {
+                        if (m < (u32)kMissCap) {
                             sMissKey[m] = key;
                             sMissOk[m] = (okey0 + q) | ((u64)(free_h + 1) << kOkeyBits);
                             sMissPs[m] = pb0 + q;
@@ -800,9 +821,9 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
             }
             __syncthreads();
             const u32 nq = s_nmiss;
-            if (nq >= min(a.miss_flush ? a.miss_flush : (u32)kMissFlushDefault, (u32)kMissBuf) ||
+            if (nq >= min(a.miss_flush ? a.miss_flush : (u32)kMissFlushDefault, (u32)kMissCap) ||
                 last) {
-                const u32 nm = min(nq, (u32)kMissBuf);
+                const u32 nm = min(nq, (u32)kMissCap);
                 for (u32 i0 = 0; i0 < nm; i0 += kParseThreads) {  // whole warps take each step
                     const u32 i = i0 + tid;
                     bool claimed = false;
@@ -913,8 +934,8 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
         // 6. the block's new entries join the round's claim list when the
         //    buffer is half full, and after the block's last tile
         const u32 ncl = s_nclaim;
-        constexpr u32 kFlushAt = kByte ? (u32)kClaimBuf / 2 : (u32)(kClaimBuf - kTP);
-        static_assert(kByte || kClaimBufR >= 2 * kTP, "a rank-round tile never overflows the buffer");
+        constexpr u32 kFlushAt = kByte ? (u32)kClaimBuf / 2 : (u32)(kClaimBuf - TP);
+        static_assert(kByte || kClaimBufR >= TP, "a rank-round tile never overflows the buffer");
         if (ncl >= kFlushAt || last) {
             const u32 nb = min(ncl, (u32)kClaimBuf);
             if (tid == 0 && ncl) {
@@ -961,7 +982,7 @@ __global__ void k_tile_strings(const RoundArgs a, u64 tiles) {
     pdl_wait();
     const u64 n = round_n(a);
     const u32 k = round_k(a);
-    const u64 nt = (n + kTP - 1) / kTP;
+    const u64 nt = (n + a.tp - 1) / a.tp;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *a.d_tiles = nt;
         if (a.ds_prev && (vload(&a.ds_prev->error) != 0 || vload(&a.ds_prev->overflow) != 0))
@@ -972,7 +993,7 @@ __global__ void k_tile_strings(const RoundArgs a, u64 tiles) {
     if (round_halted(a)) return;
     tiles = min(tiles, nt);
     for (u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x; t < tiles; t += (u64)gridDim.x * blockDim.x)
-        a.tile_str[t] = string_of(a.soff, k, t * (u64)kTP);
+        a.tile_str[t] = string_of(a.soff, k, t * (u64)a.tp);
     // bitmap of string starts (and of n), zeroed by the host
     for (u64 j = blockIdx.x * (u64)blockDim.x + threadIdx.x; j <= k; j += (u64)gridDim.x * blockDim.x) {
         const u64 s0 = __ldg(a.soff + j);
@@ -995,7 +1016,7 @@ __global__ void __launch_bounds__(1024) k_strings(const RoundArgs a) {
         u64 first = 0, nextf = 0;
         bool retire = false;
         if (j < k) {
-            auto index_of = [&](u64 ok) { return a.tile_pfx[ok / kTP] + ok % kTP; };
+            auto index_of = [&](u64 ok) { return a.tile_pfx[ok / a.tp] + ok % a.tp; };
             first = index_of(a.string_first[j]);
             nextf = (j + 1 < k) ? index_of(a.string_first[j + 1]) : P;
             retire = (nextf - first == 1);
@@ -1041,7 +1062,7 @@ __global__ void k_mark(const RoundArgs a) {
     pdl_wait();
     if (round_halted(a)) return;
     const u64 g_new = round_gnew(a);
-    const u64 keys = a.tiles_bound * (u64)kTP;  // order keys the bitmap covers
+    const u64 keys = a.tiles_bound * (u64)a.tp;  // order keys the bitmap covers
     Key128* mkey = (Key128*)a.mkey;
     for (u64 c = blockIdx.x * (u64)blockDim.x + threadIdx.x; c < g_new; c += (u64)gridDim.x * blockDim.x) {
         const u32 s = a.claims[c];
@@ -1070,7 +1091,7 @@ constexpr int kPopTile = kPopThreads * kPopItems;
 __global__ void __launch_bounds__(kPopThreads) k_popscan(const RoundArgs a, u64 nw) {
     pdl_wait();
     const u64 tile = dynamic_tile(a.ctr, a.ctr_base);
-    nw = min(nw, *a.d_tiles * (u64)(kTP / 32));
+    nw = min(nw, *a.d_tiles * (u64)(a.tp / 32));
     if (tile > 0 && tile * (u64)kPopTile >= nw) return;  // beyond the count read on the device
     const u64 w0 = tile * (u64)kPopTile + (u64)threadIdx.x * kPopItems;
     static_assert(kPopItems % 4 == 0, "16-byte words");
@@ -1123,7 +1144,7 @@ __global__ void k_rank(const RoundArgs a) {
     for (u64 c = blockIdx.x * (u64)blockDim.x + threadIdx.x; c < g_new; c += (u64)gridDim.x * blockDim.x) {
         const u32 s = a.claims[c];
         const u64 m = a.mval[c];  // k_mark's copy of the slot, in claim order
-        if (m >= a.tiles_bound * (u64)kTP) continue;  // k_mark flagged it
+        if (m >= a.tiles_bound * (u64)a.tp) continue;  // k_mark flagged it
         const Key128 key = mkey[c];
         const u32 w = (u32)(m >> 5);
         const u64 r = a.first_prefix[w] + __popc(a.first_bits[w] & ((1u << (m & 31)) - 1u));
@@ -1237,7 +1258,7 @@ __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) 
         if (t >= ntiles) continue;
         const u32 cnt = a.tile_cnt[t];
         const u64 pbase = a.tile_pfx[t];
-        const u32* ps = a.P_slot + pslot_base(t, a.tile_str[t]);
+        const u32* ps = a.P_slot + pslot_base(t, a.tile_str[t], a.tp);
         // kRwUnroll phrases per thread at a time: their reads are issued together
         for (u32 q0 = lane; q0 < cnt; q0 += kRwUnroll * 32) {
             u32 s[kRwUnroll];
@@ -1345,9 +1366,9 @@ static unsigned grid_for(u64 n, u64 cap = 152ull * 32) {
     return (unsigned)(b < cap ? b : cap);
 }
 
-u64 parse_tile_positions(int) { return (u64)kTP; }
-u64 parse_slot_entries(u64 tiles, u64 strings) { return tiles * (u64)(kTP / 2 + 2) + strings + 1; }
-u64 breaks_steps(u64 tiles) { return (tiles * (u64)kTP + kBrkSpan - 1) / kBrkSpan + 1; }
+bool parse_tile_valid(u32 tp) { return tp == 1024 || tp == 2048 || tp == 4096; }
+u64 parse_slot_entries(u64 tiles, u64 strings, u32 tp) { return tiles * (u64)(tp / 2 + 2) + strings + 1; }
+u64 breaks_steps(u64 tiles, u32 tp) { return (tiles * (u64)tp + kBrkSpan - 1) / kBrkSpan + 1; }
 
 u64 popscan_tiles_for(u64 nw) { return (nw + kPopTile - 1) / kPopTile; }
 
@@ -1355,14 +1376,14 @@ cudaError_t launch_tile_strings(const RoundArgs& a, cudaStream_t st) {
     return launch_pdl(k_tile_strings, grid_for(a.tiles_bound), 256, st, a, a.tiles_bound);
 }
 
-template <typename T>
+template <typename T, int TP>
 static int parse_occupancy(int* sms_out) {
     static int occ = 0, sms = 0;
     if (occ == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_parse<T>, kParseThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_parse<T, TP>, kParseThreads, 0);
         if (occ <= 0) occ = 1;
     }
     if (sms_out) *sms_out = sms;
@@ -1370,17 +1391,22 @@ static int parse_occupancy(int* sms_out) {
 }
 
 // Persistent grid: `per_sm` blocks per SM (0 or more than fit: as many as fit).
-template <typename T>
+template <typename T, int TP>
 static unsigned persistent_grid(u64 tiles, u32 per_sm) {
     int sms = 0;
-    const int occ = parse_occupancy<T>(&sms);
+    const int occ = parse_occupancy<T, TP>(&sms);
     const u64 b = (per_sm == 0 || per_sm > (u32)occ) ? (u64)occ : (u64)per_sm;
     const u64 g = b * (u64)sms;
     return (unsigned)(tiles < g ? (tiles ? tiles : 1) : g);
 }
 
+// Most k_parse blocks that fit on an SM, over every tile size.
 int parse_max_blocks(int sym_bytes) {
-    return sym_bytes == 1 ? parse_occupancy<unsigned char>(nullptr) : parse_occupancy<u32>(nullptr);
+    if (sym_bytes == 1)
+        return std::max({parse_occupancy<unsigned char, 1024>(nullptr), parse_occupancy<unsigned char, 2048>(nullptr),
+                         parse_occupancy<unsigned char, 4096>(nullptr)});
+    return std::max({parse_occupancy<u32, 1024>(nullptr), parse_occupancy<u32, 2048>(nullptr),
+                     parse_occupancy<u32, 4096>(nullptr)});
 }
 
 template <typename T>
@@ -1398,18 +1424,31 @@ static unsigned breaks_grid(u64 blocks) {
 }
 
 cudaError_t launch_breaks(const RoundArgs& a, cudaStream_t st) {
-    const u64 blocks = (a.tiles_bound * (u64)kTP + kBrkSpan - 1) / kBrkSpan;
+    const u64 blocks = (a.tiles_bound * (u64)a.tp + kBrkSpan - 1) / kBrkSpan;
     if (a.sym_bytes == 1)
         return launch_pdl(k_breaks<unsigned char>, breaks_grid<unsigned char>(blocks), kBrkThreads, st, a, blocks);
     return launch_pdl(k_breaks<u32>, breaks_grid<u32>(blocks), kBrkThreads, st, a, blocks);
 }
 
-cudaError_t launch_parse(const RoundArgs& a, cudaStream_t st) {
+template <typename T, int TP>
+static cudaError_t launch_parse_tp(const RoundArgs& a, cudaStream_t st) {
     const u64 tiles = a.tiles_bound;
-    if (a.sym_bytes == 1)
-        return launch_pdl(k_parse<unsigned char>, persistent_grid<unsigned char>(tiles, a.parse_blocks), kParseThreads,
-                          st, a, tiles);
-    return launch_pdl(k_parse<u32>, persistent_grid<u32>(tiles, a.parse_blocks), kParseThreads, st, a, tiles);
+    return launch_pdl(k_parse<T, TP>, persistent_grid<T, TP>(tiles, a.parse_blocks), kParseThreads, st, a, tiles);
+}
+
+template <typename T>
+static cudaError_t launch_parse_t(const RoundArgs& a, cudaStream_t st) {
+    switch (a.tp) {
+        case 1024: return launch_parse_tp<T, 1024>(a, st);
+        case 2048: return launch_parse_tp<T, 2048>(a, st);
+        case 4096: return launch_parse_tp<T, 4096>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_parse(const RoundArgs& a, cudaStream_t st) {
+    if (a.sym_bytes == 1) return launch_parse_t<unsigned char>(a, st);
+    return launch_parse_t<u32>(a, st);
 }
 
 cudaError_t launch_strings(const RoundArgs& a, cudaStream_t st) {

@@ -89,6 +89,43 @@ def test_runs_longer_than_tiles(ctx, hf):
     check_build(ctx, hf, li.from_strings([s1, s2, s3, s4]))
 
 
+@pytest.mark.parametrize("tp", [1024, 2048, 4096])
+def test_every_parse_tile(hf, tp):
+    """Every parse tile size (lcg_tuning.parse_tile) gives the oracle's
+    grammar: ragged tiles, string starts inside tiles, runs over many tiles,
+    text with long phrases, many short strings; as launches, from a plan and
+    as a CUDA graph launch."""
+    import torch
+    from paper_2411_12439_gb300 import Context
+    ctx = Context(hf, device=0)
+    ctx.set_tuning(parse_tile=tp)
+    assert ctx.tuning()["parse_tile"] == tp
+    rng = np.random.default_rng(tp)
+    lens = [tp, tp - 1, tp + 1, 5 * tp + 3, 33, 31, 2, 1, 70001]
+    check_build(ctx, hf, li.from_strings([li.random_dna(rng, n) for n in lens]))
+    check_build(ctx, hf, li.edge_collection())
+    s1 = li.random_dna(rng, 3000).tobytes() + b"N" * 60_000 + li.random_dna(rng, 3000).tobytes()
+    check_build(ctx, hf, li.from_strings([s1, b"A" * 9000 + b"C" + b"A" * 9000, li.zipf_text(rng, 80_000)]))
+    check_build(ctx, hf, li.from_strings([li.random_dna(rng, int(rng.integers(1, 400))) for _ in range(600)]))
+    coll = li.tiny_dna_collection(seed=tp, base_len=300_000, k=4)
+    want = O.build(coll, hf).export()
+    d = torch.from_numpy(coll.data).cuda()
+    ctx.build(d, coll.offsets).free()
+    g = ctx.build(d, coll.offsets)  # planned rounds
+    assert ctx.last_build_stats()["async_rounds"] > 0
+    assert_same(g.export(), want)
+    g.free()
+    ctx.set_graph(True)
+    try:
+        for _ in range(2):
+            g = ctx.build(d, coll.offsets)
+            assert_same(g.export(), want)
+            g.free()
+        assert ctx.last_build_stats()["graph"] == 2
+    finally:
+        ctx.set_graph(False)
+
+
 def test_text_bytes(ctx, hf):
     rng = np.random.default_rng(4)
     coll = li.from_strings([li.zipf_text(rng, 200_000), li.zipf_text(rng, 50_000, copy_frac=0.0),
