@@ -113,7 +113,6 @@ namespace {
 
 constexpr u64 kMaxRank = 0x7fffffffull;  // ranks are tagged with one bit in the phrase slots
 constexpr u32 kMaxRounds = 63;
-constexpr double kL2Bytes = 126.5 * 1024 * 1024;  // GB300 L2 (for algorithmic-byte accounting)
 
 struct Fail {
     int code;

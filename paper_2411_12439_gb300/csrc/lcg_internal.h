@@ -122,6 +122,7 @@ struct RoundArgs {
     u32* c_rank;
 };
 
+constexpr double kL2Bytes = 126.5 * 1024 * 1024;  // GB300 L2 (byte accounting, launch choices)
 bool parse_tile_valid(u32 tp);                           // 1024, 2048 or 4096 positions
 u64 parse_slot_entries(u64 tiles, u64 strings, u32 tp);  // entries of P_slot for a round's tiles and strings
 u64 breaks_steps(u64 tiles, u32 tp);                     // k_breaks' block steps over a round's parse tiles

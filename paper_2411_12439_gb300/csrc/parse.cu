@@ -1233,13 +1233,19 @@ __global__ void k_rules(const RoundArgs a) {
 // k_rewrite: T^{i+1} and retired strings
 // --------------------------------------------------------------------------
 
-constexpr int kRwUnroll = 4;
+// Phrases a thread of k_rewrite reads at once: many when the per-slot array
+// it gathers from is small enough to stay in L2 (the rewrite then streams, and
+// more reads in flight bring it closer to DRAM bandwidth), few when that array
+// is far beyond L2 (random DRAM sectors bound it, and fewer registers keep
+// more warps resident).
+constexpr int kRwUnrollStream = 16, kRwUnrollGather = 4;
 
 // T^{i+1}[p] = rank of phrase p and f^{i+1}[p] = its fingerprint F^i[rank]
 // (so that the next round reads fingerprints without gathers).  Strings that
 // became one phrase take their C entry instead.  The (fingerprint, rank) pair
 // of a slot comes from the dense array k_rules wrote (read-only here: small
 // and cached in L1 in early rounds, in L2 after its writes later on).
+template <int kRwUnroll>
 __global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) {
     pdl_wait();
     if (round_halted(a)) return;
@@ -1478,7 +1484,9 @@ cudaError_t launch_rewrite(const RoundArgs& a, cudaStream_t st) {
     const u64 tiles = a.tiles_bound;
     const u64 blocks = (tiles + 7) / 8;  // 8 warps per block, one tile each
     const u64 g = blocks < 152ull * 8 ? (blocks ? blocks : 1) : 152ull * 8;
-    return launch_pdl(k_rewrite, (unsigned)g, 256, st, a, tiles);
+    if ((double)a.tab_cap * sizeof(u64) <= kL2Bytes)
+        return launch_pdl(k_rewrite<kRwUnrollStream>, (unsigned)g, 256, st, a, tiles);
+    return launch_pdl(k_rewrite<kRwUnrollGather>, (unsigned)g, 256, st, a, tiles);
 }
 
 cudaError_t launch_level0(const unsigned char* data, const u64* pos, const u32* ids, u32 cnt, u32* c_level,
