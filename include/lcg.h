@@ -158,8 +158,11 @@ int lcg_set_kernel_timing(lcg_ctx* ctx, int enable);
  *   parse_tile          positions per parse tile: 1024, 2048 or 4096.  A block of
  *                       k_parse stages, lists and looks up one tile at a time (fewer
  *                       barriers per phrase with larger tiles, more blocks' worth of
- *                       tiles in flight with smaller ones).
- * Defaults: 0.35, 0, 64, 0, 1, 4096.  Out-of-range values give LCG_EINVAL. */
+ *                       tiles in flight with smaller ones);
+ *   parse_tile_min      a round's tile is halved (down to 1024 positions) while the
+ *                       round would have fewer than this many tiles per SM (0 .. 1024;
+ *                       0 keeps every round at parse_tile).
+ * Defaults: 0.35, 0, 64, 0, 1, 4096, 16.  Out-of-range values give LCG_EINVAL. */
 typedef struct lcg_tuning {
     double table_load;
     uint32_t parse_blocks_per_sm;
@@ -167,7 +170,7 @@ typedef struct lcg_tuning {
     uint32_t table_slots_max;
     uint32_t tile_stripes;
     uint32_t parse_tile;
-    uint32_t reserved;  /* 0 */
+    uint32_t parse_tile_min;
 } lcg_tuning;
 int lcg_set_tuning(lcg_ctx* ctx, const lcg_tuning* t);
 /* Run later lcg_build calls whose rounds are planned without host

@@ -27,6 +27,7 @@ import numpy as np
 
 CANDIDATES = {
     "parse_tile": [4096, 2048, 1024],
+    "parse_tile_min": [16, 4, 64],
     "tile_stripes": [1, 2, 4, 8],
     "parse_blocks_per_sm": [0, 2, 3, 4],
     "table_load": [0.3, 0.35, 0.45, 0.6],

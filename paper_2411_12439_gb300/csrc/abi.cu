@@ -55,13 +55,14 @@ struct GraphBuild;
 
 struct lcg_ctx {
     int device = 0;
+    int sms = 1;                         // SMs of the device
     bool use_graph = false;              // builds may run as a captured CUDA graph
     GraphBuild* graph = nullptr;         // the graph of the last shape
     cudaStream_t st = nullptr;
     std::vector<lcg_grammar*> live;  // grammars created here and not yet freed
     double plan_slack = 1.0;         // multiplier of the planned buffer sizes (adaptive)
     // table load, k_parse blocks per SM, miss flush, slots cap, stripes, parse tile
-    lcg_tuning tuning{0.35, 0, 64, 0, 1, 4096};
+    lcg_tuning tuning{0.35, 0, 64, 0, 1, 4096, 16};
     bool own_stream = false;
     std::vector<u64> a, b, c;
     u32 levels = 0, m_bits = 32;
@@ -490,8 +491,19 @@ void alloc_next(lcg_ctx* ctx, RoundBufs& b, u64 t_cap) {
     b.Fnext = dalloc<u32>(ctx, b.Tcap);
 }
 
+// Positions per parse tile of a round of at most n symbols: the tuning's
+// tile, halved (down to 1024) while the round would have fewer than
+// parse_tile_min tiles per SM, so that short rounds (late rounds, small
+// batches) still give every resident k_parse block several tiles.
+u32 round_tile(const lcg_ctx* ctx, u64 n) {
+    u32 tp = ctx->tuning.parse_tile;
+    const u64 want = (u64)ctx->tuning.parse_tile_min * (u64)ctx->sms;
+    while (tp > 1024 && (n + tp - 1) / tp < want) tp >>= 1;
+    return tp;
+}
+
 void alloc_round(lcg_ctx* ctx, RoundBufs& b, u64 n_bound, u32 kk, u64 t_cap) {
-    b.tp = ctx->tuning.parse_tile;
+    b.tp = round_tile(ctx, n_bound);
     b.tiles = (n_bound + b.tp - 1) / b.tp;
     // every phrase but a string's first has length >= 2
     b.Pmax = n_bound / 2 + 2ull * kk + 1;
@@ -1034,7 +1046,8 @@ struct GraphBuild {
 // sizes: the number of planned rounds and the launch parameters.
 std::vector<double> graph_params(lcg_ctx* ctx, u32 planned) {
     return {(double)planned,    (double)ctx->tuning.parse_blocks_per_sm, (double)ctx->tuning.miss_flush,
-            (double)ctx->ktime, (double)ctx->tuning.tile_stripes,        (double)ctx->tuning.parse_tile};
+            (double)ctx->ktime, (double)ctx->tuning.tile_stripes,        (double)ctx->tuning.parse_tile,
+            (double)ctx->tuning.parse_tile_min};
 }
 
 // A captured graph serves a new plan when each of its rounds' buffers holds
@@ -1095,17 +1108,17 @@ void capture_graph(lcg_ctx* ctx, const unsigned char* d_in, const std::vector<u6
     std::vector<RoundPlan> plan = plan_rounds(ctx, n1, k, planned);
     // look-back buffers and timing events for every launch, made before the
     // capture (the graph must not reallocate them)
-    u64 t1 = 1, t2 = 1;
-    const u32 tp = ctx->tuning.parse_tile;
+    u64 t1 = 1, t2 = 1, hs = 1;
     for (u32 r = 1; r <= planned; r++) {
         const RoundPlan& p = plan[r];
+        const u32 tp = round_tile(ctx, p.n_alloc);
         const u64 tiles = (p.n_alloc + tp - 1) / tp;
         t1 = std::max({t1, tiles, popscan_tiles_for(tiles * tp / 32)});
         t2 = std::max({t2, scan2_tiles_for(tiles), scan2_tiles_for(std::max<u64>(1, p.g_alloc))});
+        hs = std::max(hs, breaks_steps(tiles, tp));
     }
     ensure_lb(ctx, &ctx->lb1, &ctx->lb1_tiles, t1, lb1_bytes(t1));
     ensure_lb(ctx, &ctx->lb2, &ctx->lb2_tiles, t2, scan2_lb_bytes(t2));
-    const u64 hs = breaks_steps(t1, tp);
     ensure_lb(ctx, &ctx->heads, &ctx->heads_steps, hs, hs * sizeof(u64));
     auto* gb = new GraphBuild;
     ctx->graph = gb;
@@ -1815,6 +1828,8 @@ int lcg_ctx_create(int device, const lcg_hash_family* H, void* stream, lcg_ctx**
     ctx->tag = (tag ^ ctx->mmask) * 1099511628211ull;
     try {
         ck(ctx, cudaSetDevice(device), "cudaSetDevice");
+        ck(ctx, cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device), "device attribute");
+        if (ctx->sms < 1) ctx->sms = 1;
         if (stream) {
             ctx->st = (cudaStream_t)stream;
         } else {
@@ -1899,10 +1914,11 @@ int lcg_set_tuning(lcg_ctx* ctx, const lcg_tuning* t) {
     const int maxb = std::max(parse_max_blocks(1), parse_max_blocks(4));
     if (!(t->table_load >= 0.3 && t->table_load <= 0.78) || t->parse_blocks_per_sm > (uint32_t)maxb ||
         t->miss_flush < 32 || t->miss_flush > 256 || (t->table_slots_max != 0 && t->table_slots_max < 1024) ||
-        t->tile_stripes < 1 || t->tile_stripes > 16 || !parse_tile_valid(t->parse_tile)) {
+        t->tile_stripes < 1 || t->tile_stripes > 16 || !parse_tile_valid(t->parse_tile) ||
+        t->parse_tile_min > 1024) {
         ctx->err = "tuning out of range: table_load in [0.3, 0.78], parse_blocks_per_sm <= " + std::to_string(maxb) +
                    ", miss_flush in [32, 256], table_slots_max 0 or >= 1024, tile_stripes in [1, 16], "
-                   "parse_tile 1024, 2048 or 4096";
+                   "parse_tile 1024, 2048 or 4096, parse_tile_min <= 1024";
         return LCG_EINVAL;
     }
     ctx->tuning = *t;

@@ -64,7 +64,7 @@ class KernelLaunchC(ctypes.Structure):
 class TuningC(ctypes.Structure):
     _fields_ = [("table_load", ctypes.c_double), ("parse_blocks_per_sm", ctypes.c_uint32),
                 ("miss_flush", ctypes.c_uint32), ("table_slots_max", ctypes.c_uint32),
-                ("tile_stripes", ctypes.c_uint32), ("parse_tile", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("tile_stripes", ctypes.c_uint32), ("parse_tile", ctypes.c_uint32), ("parse_tile_min", ctypes.c_uint32)]
 
 
 class PPStatsC(ctypes.Structure):
@@ -311,19 +311,21 @@ class Context:
         self._check(load().lcg_get_tuning(self._h, ctypes.byref(t)))
         return {"table_load": float(t.table_load), "parse_blocks_per_sm": int(t.parse_blocks_per_sm),
                 "miss_flush": int(t.miss_flush), "table_slots_max": int(t.table_slots_max),
-                "tile_stripes": int(t.tile_stripes), "parse_tile": int(t.parse_tile)}
+                "tile_stripes": int(t.tile_stripes), "parse_tile": int(t.parse_tile),
+                "parse_tile_min": int(t.parse_tile_min)}
 
     def set_tuning(self, **kw) -> None:
         """lcg_set_tuning: change some of table_load, parse_blocks_per_sm,
-        miss_flush, table_slots_max, tile_stripes, parse_tile (the others keep
-        their values)."""
+        miss_flush, table_slots_max, tile_stripes, parse_tile, parse_tile_min
+        (the others keep their values)."""
         cur = self.tuning()
         unknown = set(kw) - set(cur)
         if unknown:
             raise LCGError(-1, f"unknown tuning parameters {sorted(unknown)}")
         cur.update(kw)
         t = TuningC(float(cur["table_load"]), int(cur["parse_blocks_per_sm"]), int(cur["miss_flush"]),
-                    int(cur["table_slots_max"]), int(cur["tile_stripes"]), int(cur["parse_tile"]), 0)
+                    int(cur["table_slots_max"]), int(cur["tile_stripes"]), int(cur["parse_tile"]),
+                    int(cur["parse_tile_min"]))
         self._check(load().lcg_set_tuning(self._h, ctypes.byref(t)))
 
     def set_graph(self, enable: bool) -> None:

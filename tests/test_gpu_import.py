@@ -117,19 +117,20 @@ def test_tuning_changes_speed_not_results(hf):
     text = li.from_strings([li.zipf_text(np.random.default_rng(9), 120_000)])
     want = {id(c): O.build(c, hf).export() for c in (coll, text)}
     for tun in ({"table_load": 0.3, "parse_blocks_per_sm": 1, "miss_flush": 32, "table_slots_max": 0,
-                 "tile_stripes": 4, "parse_tile": 1024},
+                 "tile_stripes": 4, "parse_tile": 1024, "parse_tile_min": 0},
                 {"table_load": 0.78, "parse_blocks_per_sm": 2, "miss_flush": 256, "table_slots_max": 0,
-                 "tile_stripes": 3, "parse_tile": 4096},
+                 "tile_stripes": 3, "parse_tile": 4096, "parse_tile_min": 0},
                 {"table_load": 0.5, "parse_blocks_per_sm": 0, "miss_flush": 64, "table_slots_max": 4096,
-                 "tile_stripes": 16, "parse_tile": 2048},
+                 "tile_stripes": 16, "parse_tile": 2048, "parse_tile_min": 1024},
                 {"table_load": 0.35, "parse_blocks_per_sm": 0, "miss_flush": 64, "table_slots_max": 0,
-                 "tile_stripes": 1, "parse_tile": 2048}):
+                 "tile_stripes": 1, "parse_tile": 4096, "parse_tile_min": 16}):
         ctx.set_tuning(**tun)
         assert ctx.tuning() == tun
         for c in (coll, text, coll):
             assert O.grammars_equal(ctx.build(c.data, c.offsets).export(), want[id(c)])
     for bad in ({"table_load": 0.9}, {"miss_flush": 8}, {"parse_blocks_per_sm": 999}, {"tile_stripes": 0},
-                {"tile_stripes": 17}, {"parse_tile": 3072}, {"parse_tile": 8192}):
+                {"tile_stripes": 17}, {"parse_tile": 3072}, {"parse_tile": 8192},
+                {"parse_tile_min": 1025}):
         with pytest.raises(LCGError) as e:
             ctx.set_tuning(**bad)
         assert e.value.code == -1

@@ -98,7 +98,7 @@ def test_every_parse_tile(hf, tp):
     import torch
     from paper_2411_12439_gb300 import Context
     ctx = Context(hf, device=0)
-    ctx.set_tuning(parse_tile=tp)
+    ctx.set_tuning(parse_tile=tp, parse_tile_min=0)  # every round at tp, however short
     assert ctx.tuning()["parse_tile"] == tp
     rng = np.random.default_rng(tp)
     lens = [tp, tp - 1, tp + 1, 5 * tp + 3, 33, 31, 2, 1, 70001]
