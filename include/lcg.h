@@ -135,7 +135,8 @@ const char* lcg_last_error(const lcg_ctx* ctx);
 /* Statistics of the last build call of this context (host struct filled). */
 int lcg_last_build_stats(const lcg_ctx* ctx, lcg_build_stats* out);
 /* Per-kernel CUDA-event timing in later calls: 0 off, 1 every kernel launch,
- * 2 only the parse launches (k_parse, the kernel with most device time; few
+ * 2 only the parse launches (k_parse, the kernel with most device time, and
+ * k_parse_small, the single-block parse of a short round; few
  * events, so the call's own time is barely changed).  Timed launches are
  * bracketed by two events on the context's stream; the sums are read with
  * lcg_last_kernel_times.  Other values give LCG_EINVAL. */

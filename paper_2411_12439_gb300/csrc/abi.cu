@@ -180,7 +180,8 @@ void kt_reset(lcg_ctx* ctx) {
 // Record the start of a launch of kernel `name` that moves `bytes` algorithmic
 // bytes; returns a handle for kt_end (or -1 when timing is off).
 int kt_begin(lcg_ctx* ctx, const char* name, double bytes, u32 round = 0) {
-    if (ctx->ktime == 0 || (ctx->ktime == 2 && std::strcmp(name, "k_parse") != 0)) return -1;
+    // mode 2: the parse launches only (k_parse, and k_parse_small of short rounds)
+    if (ctx->ktime == 0 || (ctx->ktime == 2 && std::strncmp(name, "k_parse", 7) != 0)) return -1;
     lcg_ctx::KRec r{name, kt_event(ctx), kt_event(ctx), bytes, round, false};
     ck(ctx, record_event(ctx, r.a), "cudaEventRecord");
     ctx->krecs.push_back(r);
@@ -629,15 +630,27 @@ void set_table(RoundArgs& a, RoundBufs& b) {
 // Parse: tile strings, k_parse, tile scan, strings.
 void enqueue_parse(lcg_ctx* ctx, RoundArgs& a, u64 n_for_bytes) {
     const Range range("parse, round", a.level);
-    int ht = kt_begin(ctx, "k_tile_strings", 4.0 * (double)a.tiles_bound, a.level);
-    ck(ctx, launch_tile_strings(a, ctx->st), "k_tile_strings");
-    kt_end(ctx, ht);
+    if (!round_is_small(a)) {
+        const int ht = kt_begin(ctx, "k_tile_strings", 4.0 * (double)a.tiles_bound, a.level);
+        ck(ctx, launch_tile_strings(a, ctx->st), "k_tile_strings");
+        kt_end(ctx, ht);
+    }
     // k_breaks' look-ahead words: a buffer of their own, so that no other
     // kernel's data can read as a head of this launch's epoch
     const u64 steps = breaks_steps(a.tiles_bound, a.tp);
     ensure_lb(ctx, &ctx->heads, &ctx->heads_steps, steps, steps * sizeof(u64));
     a.heads = reinterpret_cast<u64*>(ctx->heads);
     a.brk_epoch = ++ctx->epoch;
+    if (round_is_small(a)) {
+        // a short round: tile strings, breaks, parse, scan and strings in one cooperative launch
+        const int hs = kt_begin(ctx, "k_parse_small", 5.0 * (double)n_for_bytes, a.level);
+        const u64 bar = ctx->ctr_val;  // the grid barriers' counter values
+        ctx->ctr_val += (u64)kSmallParseBarriers * small_round_grid(a);
+        ck(ctx, launch_parse_small(a, bar, ctx->st), "k_parse_small");
+        kt_end(ctx, hs);
+        ctx->launches += 1;
+        return;
+    }
     int hb = kt_begin(ctx, "k_breaks", (a.sym_bytes == 1 ? 1.0 : 4.0) * n_for_bytes + (double)n_for_bytes / 8.0, a.level);
     ck(ctx, launch_breaks(a, ctx->st), "k_breaks");
     kt_end(ctx, hb);
@@ -676,6 +689,17 @@ void enqueue_naming(lcg_ctx* ctx, RoundArgs& a, RoundBufs& b, double g_bytes, do
     a.rkey = b.rkey;
     a.g_alloc = b.g_alloc;
     const u64 g_grid = std::max<u64>(1, b.g_alloc);
+    if (round_is_small(a)) {
+        // a short round: marks, popcount prefix, ranks, length scan, rules and rewrite in one
+        // cooperative launch
+        const int hs = kt_begin(ctx, "k_naming_small", 12.0 * P_bytes, a.level);
+        const u64 bar = ctx->ctr_val;
+        ctx->ctr_val += (u64)kSmallNamingBarriers * small_round_grid(a);
+        ck(ctx, launch_naming_small(a, b.tiles * b.tp / 32, g_grid, bar, ctx->st), "k_naming_small");
+        kt_end(ctx, hs);
+        ctx->launches += 1;
+        return;
+    }
     int h = kt_begin(ctx, "k_mark", 12.0 * g_bytes, a.level);
     ck(ctx, launch_mark(a, g_grid, ctx->st), "k_mark");
     kt_end(ctx, h);

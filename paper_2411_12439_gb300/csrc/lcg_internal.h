@@ -30,6 +30,26 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStre
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// A cooperative launch (every block resident at once: the kernel's blocks
+// may wait for one another), with programmatic dependent launch like the
+// others (the kernel's first steps wait for the grid before it).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_coop(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Counts written by k_strings for the host.
 struct RoundCounts {
     u64 phrases;  // phrases of the round (= |T^{i+1}| before retiring)
@@ -123,7 +143,10 @@ struct RoundArgs {
 };
 
 constexpr double kL2Bytes = 126.5 * 1024 * 1024;  // GB300 L2 (byte accounting, launch choices)
-bool parse_tile_valid(u32 tp);                           // 1024, 2048 or 4096 positions
+bool parse_tile_valid(u32 tp);
+bool round_is_small(const RoundArgs& a);  // the round runs as k_parse_small and k_naming_small
+u32 small_round_grid(const RoundArgs& a);  // their blocks (one launch of each per round)
+constexpr u32 kSmallParseBarriers = 3, kSmallNamingBarriers = 5;  // grid barriers of each                           // 1024, 2048 or 4096 positions
 u64 parse_slot_entries(u64 tiles, u64 strings, u32 tp);  // entries of P_slot for a round's tiles and strings
 u64 breaks_steps(u64 tiles, u32 tp);                     // k_breaks' block steps over a round's parse tiles
 u64 popscan_tiles_for(u64 nw);
@@ -134,6 +157,8 @@ size_t slot_bytes();  // bytes of one phrase-table slot
 cudaError_t launch_tile_strings(const RoundArgs& a, cudaStream_t st);
 cudaError_t launch_breaks(const RoundArgs& a, cudaStream_t st);
 cudaError_t launch_parse(const RoundArgs& a, cudaStream_t st);
+cudaError_t launch_parse_small(const RoundArgs& a, u64 bar_base, cudaStream_t st);
+cudaError_t launch_naming_small(const RoundArgs& a, u64 nw, u64 g_bound, u64 bar_base, cudaStream_t st);
 int parse_max_blocks(int sym_bytes);  // resident k_parse blocks per SM at most
 cudaError_t launch_strings(const RoundArgs& a, cudaStream_t st);
 cudaError_t launch_mark(const RoundArgs& a, u64 g_grid, cudaStream_t st);

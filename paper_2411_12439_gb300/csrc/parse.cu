@@ -107,6 +107,11 @@ constexpr int kParseThreads = 256;
 // parameter (lcg_tuning.parse_tile) that every kernel of a round reads from
 // RoundArgs::tp; k_parse is compiled for each.
 constexpr int kTPMin = 1024, kTPMax = 4096;
+// Rounds of at most kSmallTiles tiles of kTPMin positions run as two
+// cooperative launches (parse; naming and rewrite) whose steps are separated
+// by grid barriers, instead of eleven launches: launch latency, not work,
+// bounds such rounds.
+constexpr u64 kSmallTiles = 128;
 constexpr int kHalo = 64;          // positions staged past the tile end
 
 // Where the phrase slots of parse tile t begin in P_slot.  Every phrase but a
@@ -271,8 +276,11 @@ __device__ __forceinline__ u32 spread_down(u32 src, u32 pass) {
     return y;
 }
 
+// Kernel bodies are device functions: k_X launches body_X on a grid, and the
+// single-block round kernels (k_parse_small, k_naming_small) run several of
+// them in one launch.
 template <typename T>
-__global__ void __launch_bounds__(kBrkThreads) k_breaks(const RoundArgs a, u64 nblocks) {
+__device__ __forceinline__ void body_breaks(const RoundArgs& a, u64 nblocks) {
     pdl_wait();
     constexpr bool kByte = sizeof(T) == 1;
     constexpr u32 kTypeU = 0, kTypeS = 1, kTypeL = 2, kUndecided = 3;
@@ -441,7 +449,7 @@ __device__ __forceinline__ u32 block_scan32(u32 x, u32& total, u32* s_wsum) {
 }
 
 template <typename T, int TP>
-__global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse(const RoundArgs a, u64 ntiles) {
+__device__ __forceinline__ void body_parse(const RoundArgs& a, u64 ntiles) {
     pdl_wait();
     constexpr int kSP = TP + kHalo;  // staged positions
     constexpr int NWS = kSP / 32;    // staged break words
@@ -978,7 +986,7 @@ __global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse
 }
 
 // Per parse tile: the string that holds its first position.
-__global__ void k_tile_strings(const RoundArgs a, u64 tiles) {
+__device__ __forceinline__ void body_tile_strings(const RoundArgs& a, u64 tiles) {
     pdl_wait();
     const u64 n = round_n(a);
     const u32 k = round_k(a);
@@ -1005,7 +1013,7 @@ __global__ void k_tile_strings(const RoundArgs a, u64 tiles) {
 // k_strings: per-string phrase ranges, retirement, next offsets (one block)
 // --------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(1024) k_strings(const RoundArgs a) {
+__device__ __forceinline__ void body_strings(const RoundArgs& a) {
     pdl_wait();
     if (round_halted(a)) return;
     const u64 P = *a.total;
@@ -1058,7 +1066,7 @@ __device__ __forceinline__ u64 round_gnew(const RoundArgs& a) {
     return g;
 }
 
-__global__ void k_mark(const RoundArgs a) {
+__device__ __forceinline__ void body_mark(const RoundArgs& a) {
     pdl_wait();
     if (round_halted(a)) return;
     const u64 g_new = round_gnew(a);
@@ -1135,7 +1143,7 @@ __global__ void __launch_bounds__(kPopThreads) k_popscan(const RoundArgs a, u64 
 }
 
 // Rank of every new phrase: the marks before its first occurrence.
-__global__ void k_rank(const RoundArgs a) {
+__device__ __forceinline__ void body_rank(const RoundArgs& a) {
     pdl_wait();
     if (round_halted(a)) return;
     const u64 g_new = round_gnew(a);
@@ -1159,7 +1167,7 @@ __global__ void k_rank(const RoundArgs a) {
 // (Eq. fast_hash over F^{i-1}).  When the grammar keeps a table of its rules,
 // the new rules enter it.
 template <typename T>
-__global__ void k_rules(const RoundArgs a) {
+__device__ __forceinline__ void body_rules(const RoundArgs& a) {
     pdl_wait();
     const T* S = (const T*)a.S;
     const ContentTable rw{(Slot*)a.rtab_w, a.rtab_w_cap};
@@ -1246,7 +1254,7 @@ constexpr int kRwUnrollStream = 16, kRwUnrollGather = 4;
 // of a slot comes from the dense array k_rules wrote (read-only here: small
 // and cached in L1 in early rounds, in L2 after its writes later on).
 template <int kRwUnroll>
-__global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) {
+__device__ __forceinline__ void body_rewrite(const RoundArgs& a, u64 ntiles) {
     pdl_wait();
     if (round_halted(a)) return;
     const u64 nr = a.rc->retired;
@@ -1366,6 +1374,133 @@ __global__ void k_gather_strings(const unsigned char* __restrict__ data, const u
 // host launchers
 // --------------------------------------------------------------------------
 
+// --------------------------------------------------------------------------
+// the round's kernels, and the single-block rounds
+// --------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(kBrkThreads) k_breaks(const RoundArgs a, u64 nblocks) { body_breaks<T>(a, nblocks); }
+template <typename T, int TP>
+__global__ void __launch_bounds__(kParseThreads, sizeof(T) == 1 ? 5 : 4) k_parse(const RoundArgs a, u64 ntiles) {
+    body_parse<T, TP>(a, ntiles);
+}
+__global__ void k_tile_strings(const RoundArgs a, u64 tiles) { body_tile_strings(a, tiles); }
+__global__ void __launch_bounds__(1024) k_strings(const RoundArgs a) { body_strings(a); }
+__global__ void k_mark(const RoundArgs a) { body_mark(a); }
+__global__ void k_rank(const RoundArgs a) { body_rank(a); }
+template <typename T>
+__global__ void k_rules(const RoundArgs a) { body_rules<T>(a); }
+template <int kRwUnroll>
+__global__ void __launch_bounds__(256) k_rewrite(const RoundArgs a, u64 ntiles) { body_rewrite<kRwUnroll>(a, ntiles); }
+
+// Exclusive prefix of in[0 .. n) (n: the smaller of the bound and *n_dev when
+// given) into out, the sum into totals[0] and 0 into totals[1] (what k_scan2
+// gives for one column), by one block of kSmallThreads threads.
+constexpr int kSmallThreads = 256;
+constexpr int kSmallItems = 16;
+template <typename Get>
+__device__ void block_scan_small(Get get, u64 n, const u64* n_dev, u64* out64, u32* out32, u64* totals) {
+    if (n_dev != nullptr) n = min(*n_dev, n);
+    u64 carry = 0;
+    for (u64 base = 0; base < n; base += (u64)kSmallThreads * kSmallItems) {
+        const u64 p0 = base + (u64)threadIdx.x * kSmallItems;
+        u32 v[kSmallItems];
+        u64 sum = 0;
+#pragma unroll
+        for (int i = 0; i < kSmallItems; i++) {
+            v[i] = p0 + i < n ? get(p0 + i) : 0u;
+            sum += v[i];
+        }
+        u64 tot;
+        u64 e = block_excl_scan(sum, tot) + carry;
+#pragma unroll
+        for (int i = 0; i < kSmallItems; i++) {
+            if (p0 + i < n) {
+                if (out64) out64[p0 + i] = e;
+                if (out32) out32[p0 + i] = (u32)e;
+            }
+            e += v[i];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && totals != nullptr) {
+        totals[0] = carry;
+        totals[1] = 0;
+    }
+    __syncthreads();
+}
+
+// Barrier over the grid of a cooperative launch: the k-th barrier of a launch
+// waits until the round's counter has reached base + k * gridDim.x (every
+// block arrived).  Bounded: after kSpinLimit polls the round fails with
+// kErrTimeout and the kernel's later steps return at once.
+__device__ void grid_barrier(u64* ctr, u64 target, DevStatus* ds) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1ull);
+        u64 it = 0;
+        u32 backoff = 32;
+        while (true) {
+            u64 v;
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
+            if (v >= target) break;
+            if (++it > kSpinLimit) {
+                set_error(ds, kErrTimeout);
+                break;
+            }
+            __nanosleep(backoff);
+            if (backoff < 256) backoff <<= 1;
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// A short round's parse in one cooperative launch instead of five: tile
+// strings, breaks, k_parse over the tiles (grid-stride, like the launches),
+// then block 0 scans the tiles' phrase counts and runs the per-string pass.
+// Grid barriers separate the steps.  Same buffers and results as the launches.
+template <typename T>
+__global__ void __launch_bounds__(kSmallThreads) k_parse_small(const RoundArgs a, u64 tiles, u64 nsteps,
+                                                                u64 bar_base) {
+    static_assert(kSmallThreads == kParseThreads && kSmallThreads == kBrkThreads, "one block shape");
+    const u64 g = gridDim.x;
+    body_tile_strings(a, tiles);
+    grid_barrier(a.ctr, bar_base + g, a.ds);
+    body_breaks<T>(a, nsteps);
+    grid_barrier(a.ctr, bar_base + 2 * g, a.ds);
+    body_parse<T, kTPMin>(a, tiles);
+    grid_barrier(a.ctr, bar_base + 3 * g, a.ds);
+    if (blockIdx.x == 0) {
+        block_scan_small([&](u64 i) { return a.tile_cnt[i]; }, tiles, a.d_tiles, a.tile_pfx, nullptr, a.total);
+        body_strings(a);
+    }
+}
+
+// A short round's naming and rewrite in one cooperative launch instead of
+// six: marks, (block 0) the prefix of the marks' popcounts, ranks, (block 0)
+// the scan of the rule lengths, rules and the rewrite.
+template <typename T>
+__global__ void __launch_bounds__(kSmallThreads) k_naming_small(const RoundArgs a, u64 nw, u64 g_bound,
+                                                                 u64 bar_base) {
+    const u64 g = gridDim.x;
+    body_mark(a);
+    grid_barrier(a.ctr, bar_base + g, a.ds);
+    if (blockIdx.x == 0)
+        block_scan_small([&](u64 w) { return (u32)__popc(a.first_bits[w]); },
+                         min(nw, *a.d_tiles * (u64)(a.tp / 32)), nullptr, nullptr, a.first_prefix, nullptr);
+    grid_barrier(a.ctr, bar_base + 2 * g, a.ds);
+    body_rank(a);
+    grid_barrier(a.ctr, bar_base + 3 * g, a.ds);
+    if (blockIdx.x == 0)
+        block_scan_small([&](u64 i) { return a.len_r[i]; }, g_bound, a.d_gnew, a.xlen, nullptr, a.total + 1);
+    grid_barrier(a.ctr, bar_base + 4 * g, a.ds);
+    body_rules<T>(a);
+    grid_barrier(a.ctr, bar_base + 5 * g, a.ds);
+    body_rewrite<kRwUnrollGather>(a, a.tiles_bound);
+}
+
 static unsigned grid_for(u64 n, u64 cap = 152ull * 32) {
     u64 b = (n + 255) / 256;
     if (b == 0) b = 1;
@@ -1455,6 +1590,41 @@ static cudaError_t launch_parse_t(const RoundArgs& a, cudaStream_t st) {
 cudaError_t launch_parse(const RoundArgs& a, cudaStream_t st) {
     if (a.sym_bytes == 1) return launch_parse_t<unsigned char>(a, st);
     return launch_parse_t<u32>(a, st);
+}
+
+bool round_is_small(const RoundArgs& a) { return a.tp == (u32)kTPMin && a.tiles_bound <= kSmallTiles; }
+
+// Blocks of a short round's cooperative launches: one per tile, at most one
+// per SM (and never more than can be resident at once).
+u32 small_round_grid(const RoundArgs& a) {
+    static int cap = 0;
+    if (cap == 0) {
+        int dev = 0, sms = 0, o1 = 0, o2 = 0, o3 = 0, o4 = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_parse_small<unsigned char>, kSmallThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_parse_small<u32>, kSmallThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o3, k_naming_small<unsigned char>, kSmallThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o4, k_naming_small<u32>, kSmallThreads, 0);
+        // one block per SM (a cooperative launch checks that they fit)
+        cap = (std::min({o1, o2, o3, o4}) >= 1 && sms > 0) ? sms : 1;
+    }
+    return (u32)std::min<u64>((u64)cap, std::max<u64>(1, a.tiles_bound));
+}
+
+cudaError_t launch_parse_small(const RoundArgs& a, u64 bar_base, cudaStream_t st) {
+    const u64 nsteps = (a.tiles_bound * (u64)a.tp + kBrkSpan - 1) / kBrkSpan;
+    const u32 g = small_round_grid(a);
+    if (a.sym_bytes == 1)
+        return launch_coop(k_parse_small<unsigned char>, g, kSmallThreads, st, a, a.tiles_bound, nsteps, bar_base);
+    return launch_coop(k_parse_small<u32>, g, kSmallThreads, st, a, a.tiles_bound, nsteps, bar_base);
+}
+
+cudaError_t launch_naming_small(const RoundArgs& a, u64 nw, u64 g_bound, u64 bar_base, cudaStream_t st) {
+    const u32 g = small_round_grid(a);
+    if (a.sym_bytes == 1)
+        return launch_coop(k_naming_small<unsigned char>, g, kSmallThreads, st, a, nw, g_bound, bar_base);
+    return launch_coop(k_naming_small<u32>, g, kSmallThreads, st, a, nw, g_bound, bar_base);
 }
 
 cudaError_t launch_strings(const RoundArgs& a, cudaStream_t st) {

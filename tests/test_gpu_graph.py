@@ -62,8 +62,10 @@ def test_graph_capture_replay_and_fallback(hf):
         modes.append(st["graph"])
         assert O.grammars_equal(g.export(), want["a"])
         kt = ctx2.last_kernel_times()
-        # planned rounds past the last one launch and find no active string
-        assert kt["k_parse"]["launches"] >= st["rounds"] and kt["k_parse"]["ms"] > 0
+        # planned rounds past the last one launch and find no active string;
+        # short rounds parse in k_parse_small
+        parse = [kt[k] for k in ("k_parse", "k_parse_small") if k in kt]
+        assert sum(p["launches"] for p in parse) >= st["rounds"] and sum(p["ms"] for p in parse) > 0
         g.free()
     assert modes == [0, 1, 2, 2]
     # host input: copied into the context's upload buffer, then the same graph steps
