@@ -82,7 +82,7 @@ def parse_args():
     p.add_argument("--no-postprocess", action="store_true")
     p.add_argument("--no-vbyte", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--e2e-steps", type=int, default=4)
+    p.add_argument("--e2e-steps", type=int, default=8)
     p.add_argument("--e2e-streams", type=int, default=2, help="contexts (streams, host threads) of the e2e steps")
     p.add_argument("--serving-requests", type=int, default=2000)
     p.add_argument("--serving-lanes", type=int, default=2)
