@@ -416,7 +416,9 @@ void free_grammar_now(lcg_grammar* G) {
 // changing make-up (a serving loop) keeps plans that fit.
 void record_hints(lcg_ctx* ctx, u32 i, u64 n, u64 P, u64 g, u64 G) {
     if (i >= 64) return;
-    auto keep = [](double old, double x) { return std::max(x, 0.9 * old); };
+    // the largest ratio seen, fading by 2 % per build: a context fed collections
+    // of changing make-up (a serving lane) keeps plans that fit its larger ones
+    auto keep = [](double old, double x) { return std::max(x, 0.98 * old); };
     ctx->ratio_hint[i] = keep(ctx->ratio_hint[i], P ? (double)g / (double)P : 0.0);
     ctx->p_hint[i] = keep(ctx->p_hint[i], n ? (double)P / (double)n : 0.0);
     ctx->glen_hint[i] = keep(ctx->glen_hint[i], g ? (double)G / (double)g : 2.0);

@@ -84,7 +84,6 @@ class CudaBackend:
         self.ctxs = [Context(hash_family, device=device, stream=s.cuda_stream) for s in self.lane_streams]
         self.staging = [None] * lanes
         self.dev_staging = [None] * lanes
-        self.copy_streams = [torch.cuda.Stream(device=device) for _ in range(lanes)]
         self.record_events = False
         self.events = []
         self._ev_lock = threading.Lock()
@@ -99,7 +98,7 @@ class CudaBackend:
     def gather(self, lane: int, parts, total: int):
         """The batch's strings back to back.  Requests received into
         page-locked memory are copied straight into the lane's device buffer
-        (one asynchronous copy each); others are first gathered into the
+        (one asynchronous copy each, on the lane's stream); others are first gathered into the
         lane's page-locked host buffer, so that the build's upload runs at
         link speed.  Buffers grow as needed."""
         import torch
@@ -107,18 +106,20 @@ class CudaBackend:
             warnings.filterwarnings("ignore", message="The given NumPy array is not writable")
             ts = [torch.from_numpy(x) for x in parts]
         if all(t.is_pinned() for t in ts):
-            dev = self.dev_staging[lane]
-            if dev is None or dev.numel() < total:
-                dev = torch.empty(max(total, 1 << 20) * 5 // 4, dtype=torch.uint8, device=self.device)
-                self.dev_staging[lane] = dev
-            st = self.copy_streams[lane]
-            with torch.cuda.stream(st):
+            # on the lane's own stream: the build that follows reads the buffer
+            # in stream order, and the host does not wait for the copies (the
+            # buffer belongs to that stream's pool, so replacing it is ordered too)
+            with torch.cuda.stream(self.lane_streams[lane]):
+                dev = self.dev_staging[lane]
+                if dev is None or dev.numel() < total:
+                    self.dev_staging[lane] = None
+                    dev = torch.empty(max(total, 1 << 20) * 5 // 4, dtype=torch.uint8, device=self.device)
+                    self.dev_staging[lane] = dev
                 off = 0
                 for t in ts:
                     n = t.numel()
                     dev[off:off + n].copy_(t, non_blocking=True)
                     off += n
-            st.synchronize()  # the lane's build reads the buffer on its own stream
             return dev[:total]
         buf = self.staging[lane]
         if buf is None or buf.numel() < total:
