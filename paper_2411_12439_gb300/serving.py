@@ -98,7 +98,8 @@ class CudaBackend:
     def gather(self, lane: int, parts, total: int):
         """The batch's strings back to back.  Requests received into
         page-locked memory are copied straight into the lane's device buffer
-        (one asynchronous copy each, on the lane's stream); others are first gathered into the
+        (one asynchronous copy each, on the lane's stream, which the host then
+        waits for); others are first gathered into the
         lane's page-locked host buffer, so that the build's upload runs at
         link speed.  Buffers grow as needed."""
         import torch
@@ -106,10 +107,12 @@ class CudaBackend:
             warnings.filterwarnings("ignore", message="The given NumPy array is not writable")
             ts = [torch.from_numpy(x) for x in parts]
         if all(t.is_pinned() for t in ts):
-            # on the lane's own stream: the build that follows reads the buffer
-            # in stream order, and the host does not wait for the copies (the
-            # buffer belongs to that stream's pool, so replacing it is ordered too)
-            with torch.cuda.stream(self.lane_streams[lane]):
+            # on the lane's own stream (the buffer belongs to that stream's
+            # pool, so replacing it is ordered too); the host waits for the
+            # copies, as a resident-mode build reads the buffer on the resident
+            # grammar's stream
+            ls = self.lane_streams[lane]
+            with torch.cuda.stream(ls):
                 dev = self.dev_staging[lane]
                 if dev is None or dev.numel() < total:
                     self.dev_staging[lane] = None
@@ -120,6 +123,7 @@ class CudaBackend:
                     n = t.numel()
                     dev[off:off + n].copy_(t, non_blocking=True)
                     off += n
+            ls.synchronize()
             return dev[:total]
         buf = self.staging[lane]
         if buf is None or buf.numel() < total:
