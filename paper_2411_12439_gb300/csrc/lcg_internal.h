@@ -143,10 +143,10 @@ struct RoundArgs {
 };
 
 constexpr double kL2Bytes = 126.5 * 1024 * 1024;  // GB300 L2 (byte accounting, launch choices)
-bool parse_tile_valid(u32 tp);
-bool round_is_small(const RoundArgs& a);  // the round runs as k_parse_small and k_naming_small
-u32 small_round_grid(const RoundArgs& a);  // their blocks (one launch of each per round)
-constexpr u32 kSmallParseBarriers = 3, kSmallNamingBarriers = 5;  // grid barriers of each                           // 1024, 2048 or 4096 positions
+bool parse_tile_valid(u32 tp);                 // 1024, 2048 or 4096 positions
+bool round_is_small(const RoundArgs& a);        // the round runs as k_parse_small and k_naming_small
+u32 small_round_grid(const RoundArgs& a);       // their blocks (one launch of each per round)
+constexpr u32 kSmallParseBarriers = 3, kSmallNamingBarriers = 5;  // grid barriers of each
 u64 parse_slot_entries(u64 tiles, u64 strings, u32 tp);  // entries of P_slot for a round's tiles and strings
 u64 breaks_steps(u64 tiles, u32 tp);                     // k_breaks' block steps over a round's parse tiles
 u64 popscan_tiles_for(u64 nw);

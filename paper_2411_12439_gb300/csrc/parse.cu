@@ -25,9 +25,13 @@
 //              (F^i, rank) pair of every table slot
 //   k_rewrite  T^{i+1}[p] = rank of phrase p and its fingerprint, compacting
 //              retired strings
+// A short round (at most kSmallTiles tiles) runs the same steps as two
+// cooperative launches instead: k_parse_small (tile strings to strings) and
+// k_naming_small (marks to rewrite), with grid barriers between the steps.
 // Every kernel of the round starts with pdl_wait(): it is launched with
 // programmatic dependent launch after the one before it.
 #include <algorithm>
+#include <utility>
 
 #include "lcg_dev.cuh"
 #include "lcg_internal.h"
@@ -277,7 +281,7 @@ __device__ __forceinline__ u32 spread_down(u32 src, u32 pass) {
 }
 
 // Kernel bodies are device functions: k_X launches body_X on a grid, and the
-// single-block round kernels (k_parse_small, k_naming_small) run several of
+// short rounds' cooperative kernels (k_parse_small, k_naming_small) run several of
 // them in one launch.
 template <typename T>
 __device__ __forceinline__ void body_breaks(const RoundArgs& a, u64 nblocks) {
@@ -1375,7 +1379,7 @@ __global__ void k_gather_strings(const unsigned char* __restrict__ data, const u
 // --------------------------------------------------------------------------
 
 // --------------------------------------------------------------------------
-// the round's kernels, and the single-block rounds
+// the round's kernels, and the short rounds' cooperative kernels
 // --------------------------------------------------------------------------
 
 template <typename T>
@@ -1519,16 +1523,17 @@ cudaError_t launch_tile_strings(const RoundArgs& a, cudaStream_t st) {
 
 template <typename T, int TP>
 static int parse_occupancy(int* sms_out) {
-    static int occ = 0, sms = 0;
-    if (occ == 0) {
-        int dev = 0;
+    // queried once per instantiation (thread-safe static initialisation:
+    // contexts on several host threads launch at once)
+    static const std::pair<int, int> occ_sms = [] {
+        int dev = 0, sms = 0, occ = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_parse<T, TP>, kParseThreads, 0);
-        if (occ <= 0) occ = 1;
-    }
-    if (sms_out) *sms_out = sms;
-    return occ;
+        return std::make_pair(occ > 0 ? occ : 1, sms);
+    }();
+    if (sms_out) *sms_out = occ_sms.second;
+    return occ_sms.first;
 }
 
 // Persistent grid: `per_sm` blocks per SM (0 or more than fit: as many as fit).
@@ -1552,15 +1557,13 @@ int parse_max_blocks(int sym_bytes) {
 
 template <typename T>
 static unsigned breaks_grid(u64 blocks) {
-    static int occ = 0, sms = 0;
-    if (occ == 0) {
-        int dev = 0;
+    static const u64 cap = [] {
+        int dev = 0, sms = 0, occ = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_breaks<T>, kBrkThreads, 0);
-        if (occ <= 0) occ = 1;
-    }
-    const u64 cap = (u64)occ * (u64)sms;
+        return (u64)(occ > 0 ? occ : 1) * (u64)sms;
+    }();
     return (unsigned)(blocks < cap ? (blocks ? blocks : 1) : cap);
 }
 
@@ -1597,8 +1600,7 @@ bool round_is_small(const RoundArgs& a) { return a.tp == (u32)kTPMin && a.tiles_
 // Blocks of a short round's cooperative launches: one per tile, at most one
 // per SM (and never more than can be resident at once).
 u32 small_round_grid(const RoundArgs& a) {
-    static int cap = 0;
-    if (cap == 0) {
+    static const int cap = [] {
         int dev = 0, sms = 0, o1 = 0, o2 = 0, o3 = 0, o4 = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1607,8 +1609,8 @@ u32 small_round_grid(const RoundArgs& a) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o3, k_naming_small<unsigned char>, kSmallThreads, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o4, k_naming_small<u32>, kSmallThreads, 0);
         // one block per SM (a cooperative launch checks that they fit)
-        cap = (std::min({o1, o2, o3, o4}) >= 1 && sms > 0) ? sms : 1;
-    }
+        return (std::min({o1, o2, o3, o4}) >= 1 && sms > 0) ? sms : 1;
+    }();
     return (u32)std::min<u64>((u64)cap, std::max<u64>(1, a.tiles_bound));
 }
 
