@@ -85,3 +85,26 @@ def test_tuned_uses_the_cache_and_records_new_classes(monkeypatch, tmp_path):
     assert got2["source"] == "cache" and ctx2.tuning()["table_load"] == 0.6 and calls == [1]
     got3 = autotune.tuned(FakeCtx(START), None, None, "dna/2^28B/9-256 strings", path=path, retune=True)
     assert got3["source"] == "tuned" and calls == [1, 1]
+
+
+def test_candidates_and_cache_name_tuning_fields():
+    """Every searched parameter, and every parameter of every cached setting,
+    is a field of lcg_tuning, with values the library accepts (the ranges of
+    lcg_set_tuning, restated)."""
+    import json
+    from paper_2411_12439_gb300 import lcg
+    fields = {f for f, _ in lcg.TuningC._fields_}
+    assert set(autotune.CANDIDATES) <= fields
+    ok = {"table_load": lambda v: 0.3 <= v <= 0.78, "parse_blocks_per_sm": lambda v: v >= 0,
+          "miss_flush": lambda v: 32 <= v <= 256, "table_slots_max": lambda v: v == 0 or v >= 1024,
+          "tile_stripes": lambda v: 1 <= v <= 16, "parse_tile": lambda v: v in (1024, 2048, 4096),
+          "parse_tile_min": lambda v: 0 <= v <= 1024}
+    assert set(ok) == fields
+    for name, values in autotune.CANDIDATES.items():
+        assert all(ok[name](v) for v in values), name
+    with open(autotune.CACHE) as fh:
+        cache = json.load(fh)
+    assert cache
+    for cls, entry in cache.items():
+        assert set(entry["tuning"]) <= fields, cls
+        assert all(ok[k](v) for k, v in entry["tuning"].items()), cls
