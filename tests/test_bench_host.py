@@ -80,3 +80,23 @@ def test_clock_summary():
               ["0", "2070", "2070", "1100", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"]]
     got = s.stop()
     assert got == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+
+
+def test_algorithmic_bytes_follow_the_stated_formulas():
+    """The roofline's byte counts, recomputed by hand for a two-round build:
+    round 1 reads its bytes (1 B each), round 2 its ranks (4 B each); a table
+    larger than L2 adds one 32-byte sector per phrase; the whole path counts
+    the input once, each round's next sequence written and read (8 B per
+    phrase) and its new rules (4 B per symbol, 12 B per rule)."""
+    import bench
+    small = 1024                                   # slots: 32 KB, inside L2
+    big = int(bench.L2_BYTES // 32) + 1            # one slot past L2
+    r1 = {"n": 1000, "phrases": 300, "g": 20, "G": 70, "table_cap": small}
+    r2 = {"n": 300, "phrases": 100, "g": 60, "G": 200, "table_cap": big}
+    assert bench.parse_alg_bytes(r1, 1) == 1000.0
+    assert bench.parse_alg_bytes(r2, 2) == 4 * 300 + 32 * 100
+    assert bench.parse_alg_bytes(r2, 2, tables=False) == 4 * 300
+    streams = 1000 + (8 * 300 + 4 * 70 + 12 * 20) + (8 * 100 + 4 * 200 + 12 * 60)
+    assert bench.path_alg_bytes([r1, r2], tables=False) == streams
+    assert bench.path_alg_bytes([r1, r2]) == streams + 32 * 100
+    assert bench.path_alg_bytes([]) == 0.0
